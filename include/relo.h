@@ -1,0 +1,280 @@
+/*
+ * relo.h -- C ABI of the GB300-native inter-agent relocalisation path.
+ *
+ * Golodetz et al., "Collaborative Large-Scale Dense 3D Reconstruction with
+ * Online Inter-Agent Pose Optimisation" (TVCG 2018), Sec. 3.3.1 and Fig. 3:
+ * to relate agent b's sub-scene to agent a's, render a synthetic RGB-D view of
+ * b's voxel scene from a frame's pose, relocalise that view with a's
+ * regression-forest relocaliser (trained as in Cavallari et al., Sec. 3.3 (b)),
+ * and accept the proposed pose only if a depth raycast of a's scene from it
+ * agrees with b's depth (the Omega_s / mu test of Sec. 3.3.1).  The accepted
+ * pose gives the relative transform sample a_T_b of Sec. 3.3.1.
+ *
+ * Conventions for every entry point:
+ *   - Poses are camera->scene, 4x4 row-major double (the inverse of the
+ *     paper's f_T_s).  Hence a_T_b = P_a * P_b^-1.
+ *   - Images are row-major [H][W]: depth uint16 millimetres (0 = invalid),
+ *     colour uint8 RGBA (4 bytes per pixel; alpha 255 where depth is valid).
+ *   - "_dev" pointers are CUDA device pointers, "_host" pointers host memory.
+ *     The caller owns every buffer it passes and the stream; the library owns
+ *     its opaque handles (scene, forest) and the device memory behind them.
+ *   - Calls are asynchronous on the given stream unless stated otherwise.
+ *     Outputs are valid once the stream has synchronised.
+ *   - Every call returns RELO_OK (0) or a negative relo_status; on error the
+ *     call has launched nothing, and relo_last_error() returns a message
+ *     (thread-local).  Kernels never trap: a device-side bounds or wait
+ *     failure sets RELO_EDEVICE / RELO_ETIMEOUT in the per-attempt status.
+ *   - There is no CPU fallback: every step runs in this library's sm_103a kernels.
+ */
+#ifndef RELO_H_
+#define RELO_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* relo_stream; /* same object as cudaStream_t; NULL = legacy default stream */
+
+typedef int relo_status;
+#define RELO_OK 0
+#define RELO_EINVAL (-1)    /* bad argument (size, pointer, alignment) */
+#define RELO_ENOMEM (-2)    /* device allocation failed (scene / forest creation only) */
+#define RELO_ECUDA (-3)     /* a CUDA runtime call failed */
+#define RELO_ETIMEOUT (-4)  /* a bounded device loop gave up */
+#define RELO_EDEVICE (-5)   /* a device-side bounds check failed */
+#define RELO_ENOTFOUND (-6) /* no valid pose hypothesis */
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* relo_last_error(void);
+
+/* Pinhole camera.  The ray through pixel (u, v) is C + lam * R ((u-cx)/fx, (v-cy)/fy, 1),
+ * lam = camera-space z, marched over [depth_min, depth_max] metres. */
+typedef struct relo_intrinsics {
+  int32_t width, height;
+  double fx, fy, cx, cy;
+  double depth_min, depth_max;
+} relo_intrinsics;
+
+/* ---------------------------------------------------------------------------------------
+ * Voxel sub-scene (the InfiniTAM-style map of Sec. 3.3 (a); its size, Sec. 4.3.2).
+ * Blocks of 8x8x8 voxels: voxel (i,j,k) is the scene point (i,j,k) * voxel_size and lives
+ * in block floor((i,j,k) / 8) at local index (i&7) + 8 (j&7) + 64 (k&7).  tsdf is the
+ * truncated signed distance / mu in [-1, 1], positive in free space.  Voxels of blocks not
+ * in the list read tsdf +1 and colour 0.  Block coordinates must lie in [-32768, 32767];
+ * a repeated block coordinate keeps its first occurrence.  The library builds a spatial
+ * hash with 2^log2_buckets buckets (chained, entries of 16 bytes) and copies everything to
+ * the device (synchronously; about 4 KB per block plus 16 B per bucket).
+ * Errors: RELO_EINVAL (n_blocks < 0, null arrays with n_blocks > 0, log2_buckets outside
+ * [4, 30], voxel_size or mu <= 0, coordinates out of range), RELO_ENOMEM, RELO_ECUDA.
+ * ------------------------------------------------------------------------------------- */
+typedef struct relo_scene relo_scene;
+
+relo_status relo_create_scene(const int32_t* coords_host /* [n][3] */, const float* tsdf_host /* [n][512] */,
+                              const uint8_t* rgba_host /* [n][512][4] */, int64_t n_blocks, double voxel_size,
+                              double mu, int32_t log2_buckets, relo_scene** out);
+void relo_destroy_scene(relo_scene* scene);
+
+/* Input index of the block holding each block coordinate (n x int32 xyz, device), -1 where
+ * unallocated (the hash lookup used by the raycast).  keys_dev and out_dev are device arrays. */
+relo_status relo_scene_lookup(const relo_scene* scene, const int32_t* keys_dev, int64_t n, int64_t* out_dev,
+                              relo_stream stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Synthetic raycast (Sec. 3.3.1, Fig. 3: the query is a colour + depth render of scene b from
+ * the frame's pose; the appendix on global map rendering names the usual voxel raycast).
+ * March, per ray: start at depth_min; a sample in an unallocated block counts as +1 and jumps
+ * just past the block's exit; otherwise f = trilinear tsdf, and while f > 0 the next sample is
+ * max(f mu, voxel) / |d| further; the first f <= 0 after a positive sample ends the march at
+ * the secant root of the last two samples (f <= 0 on the first sample: invalid).  Depth is the
+ * hit's camera z in mm rounded half up, clamped to [1, 65535]; with noise_dev (one standard
+ * normal per pixel, float32 [H][W]) 1.5 mm * z^2 * n is added first (the quadratic axial noise
+ * model of the appendix on depth sensors).  Colour (rgba_dev may be NULL) is the trilinear
+ * voxel colour at the hit, rounded half up.  Computed in FP32.
+ * Errors: RELO_EINVAL (null scene/intrinsics/pose/depth, width or height outside [1, 16384]).
+ * ------------------------------------------------------------------------------------- */
+relo_status relo_raycast_view(const relo_scene* scene, const relo_intrinsics* intr, const double pose_c2s[16],
+                              const float* noise_dev, uint16_t* depth_dev, uint8_t* rgba_dev, relo_stream stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Regression forest (the relocaliser of Sec. 3.3 (b), after Cavallari et al.).
+ * n_trees complete binary trees of the given depth, stored breadth first (children of node n
+ * at 2n+1, 2n+2), 2^depth - 1 split nodes of 16 bytes each:
+ *   {int16 dx1, dy1, dx2, dy2; uint8 kind, c1, c2, pad; int32 tau}.
+ * At a pixel x with depth d mm > 0 each probe is q = x + trunc(delta * 1000 / d) per axis
+ * (integer division toward zero), clamped to the image; kind 0 compares the probes' depths
+ * (0 where invalid), kind 1 compares colour channel c1 of q1 with channel c2 of q2; the pixel
+ * goes left iff V(q1) - V(q2) < tau.  Leaf = node - (2^depth - 1).
+ * Leaves hold up to max_modes modes of 12 floats: mean xyz, inverse covariance (xx, xy, xz,
+ * yy, yz, zz), log(weight) - 0.5 log det(2 pi Sigma), weight, pad; modes sorted by support,
+ * mode 0 the most supported.  modes_host / n_modes_host may be NULL (empty leaves) and be
+ * filled later by training (relo_forest_train_*).  Copies to the device synchronously.
+ * Errors: RELO_EINVAL (n_trees outside [1, 16], depth outside [1, 16], max_modes outside
+ * [1, 64], null nodes), RELO_ENOMEM, RELO_ECUDA.
+ * ------------------------------------------------------------------------------------- */
+typedef struct relo_forest relo_forest;
+
+relo_status relo_create_forest(const void* nodes_host, int32_t n_trees, int32_t depth, const float* modes_host,
+                               const uint8_t* n_modes_host, int32_t max_modes, relo_forest** out);
+void relo_destroy_forest(relo_forest* forest);
+
+/* Copy the forest's modes / mode counts back to host arrays of the layout above (synchronous). */
+relo_status relo_forest_get_modes(const relo_forest* forest, float* modes_host, uint8_t* n_modes_host);
+
+/* Leaf index of every pixel in every tree: leaves_dev [T][H][W] uint16, 0xFFFF where d = 0.
+ * Integer-exact.  Errors: RELO_EINVAL (null pointers, W or H outside [1, 16384]). */
+relo_status relo_forest_eval(const relo_forest* forest, const uint16_t* depth_dev, const uint8_t* rgba_dev,
+                             int32_t width, int32_t height, uint16_t* leaves_dev, relo_stream stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Relocaliser training (Sec. 3.3 (b): leaves filled online as per Cavallari et al.).
+ * relo_forest_train_frame routes the pixels of one posed training frame on the stride grid
+ * (u % stride == 0 and v % stride == 0, depth > 0, raster order) through every tree on the
+ * device and offers each pixel's scene coordinate P * backproject(depth) to its leaf's
+ * reservoir (Algorithm R, capacity per leaf, Philox4x32-10 draws keyed by seed at counter
+ * (3, tree * 2^depth + leaf, n_lo, n_hi) for the n-th offer, n from 0; the offer replaces
+ * slot floor(word0 * (n+1) / 2^32) if that is below capacity).  Reservoir updates run on the
+ * host in frame order (synchronous call).  relo_forest_train_finish runs mean shift on every
+ * leaf (Gaussian kernel of the given bandwidth from every sample, until the shift is below
+ * tol or max_iter steps; a converged point joins the first mode whose opening point lies
+ * within merge_dist; per mode: mean and covariance of its members + cov_floor I; keep the
+ * max_modes most supported, ties by opening order) on the device and replaces the modes.
+ * ------------------------------------------------------------------------------------- */
+typedef struct relo_train_params {
+  int32_t capacity, stride, max_iter, pad;
+  uint64_t seed;
+  double bandwidth, tol, merge_dist, cov_floor;
+} relo_train_params;
+
+relo_status relo_forest_train_begin(relo_forest* forest, const relo_train_params* p);
+relo_status relo_forest_train_frame(relo_forest* forest, const relo_intrinsics* intr, const double pose_c2s[16],
+                                    const uint16_t* depth_dev, const uint8_t* rgba_dev, relo_stream stream);
+relo_status relo_forest_train_finish(relo_forest* forest, relo_stream stream);
+/* Reservoir contents (host copies, synchronous): samples [T][2^D][capacity][3], count [T][2^D]. */
+relo_status relo_forest_train_reservoirs(const relo_forest* forest, float* samples_host, int32_t* count_host);
+
+/* ---------------------------------------------------------------------------------------
+ * Preemptive RANSAC (the relocaliser's pose solver, after Cavallari et al.; paper-silent,
+ * readings stated here and identically in the CPU oracle).
+ * Hypotheses: hypothesis h tries j = 0..max_tries-1; try j is the Philox4x32-10 block at
+ * counter (1, h, j, 0) under key (seed_lo, seed_hi): words 0..2 pick three pixels uniformly
+ * among the valid pixels (depth > 0, raster order; floor(w * n / 2^32)), byte k of word 3
+ * picks the tree of correspondence k as floor(byte * T / 256), each correspondence uses its
+ * leaf's mode 0; the first try whose leaves are non-empty, whose pixels differ, whose three
+ * camera/scene distance pairs agree within rigidity metres and whose two triangles have
+ * |cross| >= min_area is fitted by Kabsch (FP32 covariance, FP64 rotation).
+ * Rounds: while more than one hypothesis is alive, draw batch pixels (with replacement) at
+ * counters (2, r, i, 0); add to each alive hypothesis's energy the sum over those pixels of
+ * min(-log 1e-30, -max over trees and modes of [logw - 0.5 log det 2 pi Sigma - 0.5 (x-mu)^T
+ * Sigma^-1 (x-mu)]), x = R c + t; keep the ceil(n/2) lowest (energy, index); re-fit each
+ * survivor by Kabsch on its inliers among all pixels drawn so far (best mode within
+ * inlier_dist of x; at least 3 inliers, else the pose is kept).
+ * ------------------------------------------------------------------------------------- */
+typedef struct relo_ransac_params {
+  int32_t n_hyps;       /* K, 1 .. 4096 */
+  int32_t batch;        /* B pixels added per round, 1 .. 4096 */
+  int32_t max_tries;    /* tries per hypothesis, 1 .. 1 << 24 */
+  int32_t pad;
+  double rigidity;      /* metres */
+  double min_area;      /* square metres */
+  double inlier_dist;   /* metres */
+  uint64_t seed;
+} relo_ransac_params;
+
+/* Result of one attempt (device or host copy; 328 bytes). */
+typedef struct relo_pose_result {
+  double pose_c2s[16];     /* proposed camera -> scene a pose */
+  double rel_a_b[16];      /* a_T_b = P_a P_b^-1 (filled by relo_relocalise_batch) */
+  double energy;           /* accumulated energy of the final hypothesis */
+  int32_t n_inliers;       /* inliers of its last re-fit */
+  int32_t status;          /* RELO_OK, RELO_ENOTFOUND, RELO_EDEVICE, RELO_ETIMEOUT */
+  int32_t verified;        /* 1 iff 2 |Omega_a| > |Omega| and |Omega_ab| > 0 and sum < 50 |Omega_ab| */
+  int32_t n_valid;         /* valid query pixels */
+  int32_t hypothesis;      /* index of the final hypothesis */
+  int32_t n_rounds;
+  uint64_t omega, omega_a, omega_b, omega_ab, sum_absdiff_mm; /* Sec. 3.3.1 verification counts */
+} relo_pose_result;
+
+/* Bytes of device workspace relo_ransac_relocalise needs for a width x height view. */
+size_t relo_ransac_workspace_size(int32_t width, int32_t height, const relo_ransac_params* p);
+
+/* Relocalise one view: depth_dev + leaves_dev (from relo_forest_eval) -> result_dev (device
+ * relo_pose_result; the verification fields are zero).  workspace_dev (256-byte aligned, at
+ * least relo_ransac_workspace_size bytes) is scratch the call overwrites.
+ * Errors: RELO_EINVAL (bad sizes/params/pointers or workspace too small). */
+relo_status relo_ransac_relocalise(const relo_forest* forest, const uint16_t* depth_dev, const uint16_t* leaves_dev,
+                                   const relo_intrinsics* intr, const relo_ransac_params* p, void* workspace_dev,
+                                   size_t workspace_bytes, relo_pose_result* result_dev, relo_stream stream);
+
+/* Stage-isolated RANSAC steps (the same kernels as relo_ransac_relocalise), for checking each
+ * step against the oracle under teacher forcing.  Workspace as above.
+ * relo_ransac_hypotheses: poses_dev [K][12] (row-major R | t, camera -> scene), valid_dev [K],
+ * tries_dev [K] (index of the kept try, max_tries if none).
+ * relo_ransac_round: one round r from the given state: alive_dev [n_alive] hypothesis indices,
+ * poses_dev [K][12] and energy_dev [K] updated in place, drawn_dev [(r+1) * batch] pixel
+ * indices drawn in rounds 0..r (only round r's slice is written), survivors_dev
+ * [ceil(n_alive/2)] and inliers_dev [K] written. */
+relo_status relo_ransac_hypotheses(const relo_forest* forest, const uint16_t* depth_dev, const uint16_t* leaves_dev,
+                                   const relo_intrinsics* intr, const relo_ransac_params* p, void* workspace_dev,
+                                   size_t workspace_bytes, double* poses_dev, int32_t* valid_dev, int32_t* tries_dev,
+                                   relo_stream stream);
+relo_status relo_ransac_round(const relo_forest* forest, const uint16_t* depth_dev, const uint16_t* leaves_dev,
+                              const relo_intrinsics* intr, const relo_ransac_params* p, int32_t round,
+                              const int32_t* alive_dev, int32_t n_alive, const int32_t* valid_dev, double* poses_dev,
+                              double* energy_dev, int32_t* drawn_dev, int32_t* survivors_dev, int32_t* inliers_dev,
+                              void* workspace_dev, size_t workspace_bytes, relo_stream stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Depth-difference verification (Sec. 3.3.1): raycast scene a's depth from the proposed pose
+ * in result_dev->pose_c2s and compare with depth_b_dev; writes omega (= W H), omega_a,
+ * omega_b, omega_ab, sum_absdiff_mm and verified into result_dev (integer-exact).
+ * depth_a_dev (nullable) receives scene a's depth.  A result whose status is not RELO_OK is
+ * left unverified.
+ * ------------------------------------------------------------------------------------- */
+relo_status relo_verify(const relo_scene* scene_a, const relo_intrinsics* intr, const uint16_t* depth_b_dev,
+                        relo_pose_result* result_dev, uint16_t* depth_a_dev, relo_stream stream);
+
+/* ---------------------------------------------------------------------------------------
+ * A batch of whole attempts (Fig. 3 end to end: raycast b, forest of a, RANSAC, verify
+ * against a), all stages batched across attempts in one launch per stage.
+ * ------------------------------------------------------------------------------------- */
+typedef struct relo_attempt {
+  const relo_scene* scene_b;
+  const relo_forest* forest_a;
+  const relo_scene* scene_a;
+  relo_intrinsics intr;
+  double pose_b[16];        /* camera -> scene b pose of the query frame */
+  const float* noise_dev;   /* nullable: per-pixel standard normals for the query depth */
+  int32_t n_hyps;           /* overrides p->n_hyps when > 0 */
+  int32_t pad;
+  uint64_t seed;            /* Philox key of this attempt's RANSAC */
+} relo_attempt;
+
+/* Workspace bytes for a batch (includes the query images and per-attempt RANSAC scratch). */
+size_t relo_batch_workspace_size(const relo_attempt* attempts_host, int32_t n, const relo_ransac_params* p);
+
+/* Run n attempts.  results_host receives n results (the call synchronises the stream).
+ * Errors: RELO_EINVAL (n < 1, bad attempt, workspace too small), RELO_ECUDA. */
+relo_status relo_relocalise_batch(const relo_attempt* attempts_host, int32_t n, const relo_ransac_params* p,
+                                  void* workspace_dev, size_t workspace_bytes, relo_pose_result* results_host,
+                                  relo_stream stream);
+
+/* Device-resident form for timing and graph capture.  relo_batch_prepare lays the batch out in
+ * the workspace and copies its descriptors there (synchronous); relo_batch_run launches every
+ * stage on the stream with no host synchronisation and no host-side copies, then copies the n
+ * results to results_dev; it may be replayed (or captured in a CUDA graph) any number of times
+ * while the workspace, scenes and forests live.  relo_batch_launch_count gives the number of
+ * kernel launches one run issues.  relo_batch_destroy frees the host-side plan only. */
+typedef struct relo_batch relo_batch;
+relo_status relo_batch_prepare(const relo_attempt* attempts_host, int32_t n, const relo_ransac_params* p,
+                               void* workspace_dev, size_t workspace_bytes, relo_batch** out);
+relo_status relo_batch_run(relo_batch* batch, relo_pose_result* results_dev, relo_stream stream);
+int32_t relo_batch_launch_count(const relo_batch* batch);
+void relo_batch_destroy(relo_batch* batch);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RELO_H_ */

@@ -435,6 +435,35 @@ def pixel_energies(pose, cam, pix, leaves, forest: Forest):
     return e, mu, found, x
 
 
+def decision_margins(pose, cam, pix, leaves, forest: Forest, inlier_dist: float):
+    """Distance of each pixel's discrete decisions from their thresholds under one pose:
+    (| |x - mu_best| - inlier_dist |, best score - second best score).  Used by the parity
+    tests to tell genuine disagreements from near-ties that FP32 may resolve either way."""
+    R, t = pose[:3, :3], pose[:3, 3]
+    x = cam @ R.T + t
+    T = forest.n_trees
+    lf = leaves.reshape(T, -1)[:, pix].astype(np.int64).T
+    M = forest.modes.shape[2]
+    md = forest.modes[np.arange(T)[None, :], lf].astype(np.float64)
+    nm = forest.n_modes[np.arange(T)[None, :], lf].astype(np.int64)
+    present = np.arange(M)[None, None, :] < nm[..., None]
+    dlt = x[:, None, None, :] - md[..., :3]
+    i00, i01, i02, i11, i12, i22 = (md[..., k] for k in range(3, 9))
+    q = (dlt[..., 0] * (i00 * dlt[..., 0] + i01 * dlt[..., 1] + i02 * dlt[..., 2]) +
+         dlt[..., 1] * (i01 * dlt[..., 0] + i11 * dlt[..., 1] + i12 * dlt[..., 2]) +
+         dlt[..., 2] * (i02 * dlt[..., 0] + i12 * dlt[..., 1] + i22 * dlt[..., 2]))
+    score = np.where(present, md[..., 9] - 0.5 * q, -np.inf).reshape(len(pix), -1)
+    srt = np.sort(score, axis=1)
+    best = srt[:, -1]
+    second = srt[:, -2] if srt.shape[1] > 1 else np.full(len(pix), -np.inf)
+    arg = score.argmax(1)
+    mu = md[..., :3].reshape(len(pix), -1, 3)[np.arange(len(pix)), arg]
+    dist = np.where(np.isfinite(best), _dist(x, mu), np.inf)
+    dm = np.abs(dist - inlier_dist)
+    am = np.where(np.isfinite(second), best - second, np.inf)
+    return dm, am
+
+
 @dataclass
 class RansacTrace:
     poses0: np.ndarray                       # hypotheses [K,4,4]

@@ -1,0 +1,338 @@
+"""ctypes binding of include/relo.h (argument marshalling only).
+
+Every function keeps the C name without its ``relo_`` prefix and takes torch CUDA tensors
+for device buffers (their ``data_ptr()`` is passed through) and a CUDA stream (default: the
+current torch stream).  All arithmetic happens in the sm_103a kernels of ``librelo.so``;
+``lib()`` raises if the library has not been built, and there is no other code path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librelo.so")
+_LIB = None
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EDEVICE, ENOTFOUND = 0, -1, -2, -3, -4, -5, -6
+STATUS_NAMES = {0: "RELO_OK", -1: "RELO_EINVAL", -2: "RELO_ENOMEM", -3: "RELO_ECUDA", -4: "RELO_ETIMEOUT",
+                -5: "RELO_EDEVICE", -6: "RELO_ENOTFOUND"}
+
+c_i32, c_i64, c_u64, c_dbl, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p
+
+
+class ReloError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Intrinsics(ctypes.Structure):
+    _fields_ = [("width", c_i32), ("height", c_i32), ("fx", c_dbl), ("fy", c_dbl), ("cx", c_dbl), ("cy", c_dbl),
+                ("depth_min", c_dbl), ("depth_max", c_dbl)]
+
+
+class TrainParams(ctypes.Structure):
+    _fields_ = [("capacity", c_i32), ("stride", c_i32), ("max_iter", c_i32), ("pad", c_i32), ("seed", c_u64),
+                ("bandwidth", c_dbl), ("tol", c_dbl), ("merge_dist", c_dbl), ("cov_floor", c_dbl)]
+
+
+class RansacParams(ctypes.Structure):
+    _fields_ = [("n_hyps", c_i32), ("batch", c_i32), ("max_tries", c_i32), ("pad", c_i32), ("rigidity", c_dbl),
+                ("min_area", c_dbl), ("inlier_dist", c_dbl), ("seed", c_u64)]
+
+
+class PoseResult(ctypes.Structure):
+    _fields_ = [("pose_c2s", c_dbl * 16), ("rel_a_b", c_dbl * 16), ("energy", c_dbl), ("n_inliers", c_i32),
+                ("status", c_i32), ("verified", c_i32), ("n_valid", c_i32), ("hypothesis", c_i32),
+                ("n_rounds", c_i32), ("omega", c_u64), ("omega_a", c_u64), ("omega_b", c_u64),
+                ("omega_ab", c_u64), ("sum_absdiff_mm", c_u64)]
+
+    def to_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("pose_c2s", "rel_a_b")}
+        d["pose"] = np.array(self.pose_c2s[:], dtype=np.float64).reshape(4, 4)
+        d["rel_a_b"] = np.array(self.rel_a_b[:], dtype=np.float64).reshape(4, 4)
+        return d
+
+
+class Attempt(ctypes.Structure):
+    _fields_ = [("scene_b", c_vp), ("forest_a", c_vp), ("scene_a", c_vp), ("intr", Intrinsics),
+                ("pose_b", c_dbl * 16), ("noise_dev", c_vp), ("n_hyps", c_i32), ("pad", c_i32), ("seed", c_u64)]
+
+
+RESULT_BYTES = ctypes.sizeof(PoseResult)
+
+_SIGS = {
+    "relo_last_error": (ctypes.c_char_p, []),
+    "relo_create_scene": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_dbl, c_dbl, c_i32, ctypes.POINTER(c_vp)]),
+    "relo_destroy_scene": (None, [c_vp]),
+    "relo_scene_lookup": (c_i32, [c_vp, c_vp, c_i64, c_vp, c_vp]),
+    "relo_raycast_view": (c_i32, [c_vp, ctypes.POINTER(Intrinsics), ctypes.POINTER(c_dbl), c_vp, c_vp, c_vp, c_vp]),
+    "relo_create_forest": (c_i32, [c_vp, c_i32, c_i32, c_vp, c_vp, c_i32, ctypes.POINTER(c_vp)]),
+    "relo_destroy_forest": (None, [c_vp]),
+    "relo_forest_get_modes": (c_i32, [c_vp, c_vp, c_vp]),
+    "relo_forest_eval": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_i32, c_vp, c_vp]),
+    "relo_forest_train_begin": (c_i32, [c_vp, ctypes.POINTER(TrainParams)]),
+    "relo_forest_train_frame": (c_i32, [c_vp, ctypes.POINTER(Intrinsics), ctypes.POINTER(c_dbl), c_vp, c_vp, c_vp]),
+    "relo_forest_train_finish": (c_i32, [c_vp, c_vp]),
+    "relo_forest_train_reservoirs": (c_i32, [c_vp, c_vp, c_vp]),
+    "relo_ransac_workspace_size": (ctypes.c_size_t, [c_i32, c_i32, ctypes.POINTER(RansacParams)]),
+    "relo_ransac_relocalise": (c_i32, [c_vp, c_vp, c_vp, ctypes.POINTER(Intrinsics), ctypes.POINTER(RansacParams),
+                                       c_vp, ctypes.c_size_t, c_vp, c_vp]),
+    "relo_ransac_hypotheses": (c_i32, [c_vp, c_vp, c_vp, ctypes.POINTER(Intrinsics), ctypes.POINTER(RansacParams),
+                                       c_vp, ctypes.c_size_t, c_vp, c_vp, c_vp, c_vp]),
+    "relo_ransac_round": (c_i32, [c_vp, c_vp, c_vp, ctypes.POINTER(Intrinsics), ctypes.POINTER(RansacParams), c_i32,
+                                  c_vp, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, ctypes.c_size_t, c_vp]),
+    "relo_verify": (c_i32, [c_vp, ctypes.POINTER(Intrinsics), c_vp, c_vp, c_vp, c_vp]),
+    "relo_batch_workspace_size": (ctypes.c_size_t, [ctypes.POINTER(Attempt), c_i32, ctypes.POINTER(RansacParams)]),
+    "relo_relocalise_batch": (c_i32, [ctypes.POINTER(Attempt), c_i32, ctypes.POINTER(RansacParams), c_vp,
+                                      ctypes.c_size_t, ctypes.POINTER(PoseResult), c_vp]),
+    "relo_batch_prepare": (c_i32, [ctypes.POINTER(Attempt), c_i32, ctypes.POINTER(RansacParams), c_vp,
+                                   ctypes.c_size_t, ctypes.POINTER(c_vp)]),
+    "relo_batch_run": (c_i32, [c_vp, c_vp, c_vp]),
+    "relo_batch_launch_count": (c_i32, [c_vp]),
+    "relo_batch_destroy": (None, [c_vp]),
+}
+
+EXPORTED = sorted(_SIGS)
+
+
+def lib():
+    """The loaded library; raises if it is missing (there is no fallback)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1801_08361_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(status):
+    if status != OK:
+        raise ReloError(status, lib().relo_last_error().decode(errors="replace"))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return c_vp(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return c_vp(stream)
+    return c_vp(stream.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else c_vp(t.data_ptr())
+
+
+def intrinsics(intr) -> Intrinsics:
+    """From any object with width, height, fx, fy, cx, cy, depth_min, depth_max."""
+    return Intrinsics(int(intr.width), int(intr.height), float(intr.fx), float(intr.fy), float(intr.cx),
+                      float(intr.cy), float(intr.depth_min), float(intr.depth_max))
+
+
+def _pose(p):
+    a = np.ascontiguousarray(np.asarray(p, dtype=np.float64).reshape(16))
+    return (c_dbl * 16)(*a.tolist())
+
+
+def ransac_params(n_hyps=64, batch=500, max_tries=10000, rigidity=0.05, min_area=1e-3, inlier_dist=0.1, seed=0):
+    return RansacParams(int(n_hyps), int(batch), int(max_tries), 0, float(rigidity), float(min_area),
+                        float(inlier_dist), int(seed))
+
+
+def train_params(capacity=64, stride=1, max_iter=50, seed=0, bandwidth=0.05, tol=1e-5, merge_dist=0.025,
+                 cov_floor=1e-4):
+    return TrainParams(int(capacity), int(stride), int(max_iter), 0, int(seed), float(bandwidth), float(tol),
+                       float(merge_dist), float(cov_floor))
+
+
+# ------------------------------------------------------------------------------------------------
+# Handles
+# ------------------------------------------------------------------------------------------------
+
+class Scene:
+    """Device-resident voxel sub-scene (relo_create_scene)."""
+
+    def __init__(self, blocks, log2_buckets: int = 20):
+        self._keep = (np.ascontiguousarray(blocks.coords, dtype=np.int32),
+                      np.ascontiguousarray(blocks.tsdf, dtype=np.float32),
+                      np.ascontiguousarray(blocks.rgba, dtype=np.uint8))
+        h = c_vp()
+        _check(lib().relo_create_scene(self._keep[0].ctypes.data, self._keep[1].ctypes.data,
+                                       self._keep[2].ctypes.data, len(self._keep[0]), float(blocks.voxel_size),
+                                       float(blocks.mu), int(log2_buckets), ctypes.byref(h)))
+        self._keep = None
+        self.handle = h.value
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.relo_destroy_scene(self.handle)
+            self.handle = None
+
+
+class Forest:
+    """Device-resident regression forest (relo_create_forest)."""
+
+    def __init__(self, nodes, modes=None, n_modes=None, max_modes: int = 10):
+        nodes = np.ascontiguousarray(nodes)
+        T, n_int = nodes.shape
+        self.n_trees, self.depth, self.max_modes = T, int(round(np.log2(n_int + 1))), int(max_modes)
+        m = None if modes is None else np.ascontiguousarray(modes, dtype=np.float32)
+        nm = None if n_modes is None else np.ascontiguousarray(n_modes, dtype=np.uint8)
+        h = c_vp()
+        _check(lib().relo_create_forest(nodes.ctypes.data, T, self.depth, None if m is None else m.ctypes.data,
+                                        None if nm is None else nm.ctypes.data, self.max_modes, ctypes.byref(h)))
+        self.handle = h.value
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.relo_destroy_forest(self.handle)
+            self.handle = None
+
+    def get_modes(self):
+        L = 1 << self.depth
+        modes = np.zeros((self.n_trees, L, self.max_modes, 12), np.float32)
+        nm = np.zeros((self.n_trees, L), np.uint8)
+        _check(lib().relo_forest_get_modes(self.handle, modes.ctypes.data, nm.ctypes.data))
+        return modes, nm
+
+
+# ------------------------------------------------------------------------------------------------
+# Entry points
+# ------------------------------------------------------------------------------------------------
+
+def scene_lookup(scene, keys_dev, out_dev, stream=None):
+    _check(lib().relo_scene_lookup(scene.handle, _ptr(keys_dev), int(keys_dev.shape[0]), _ptr(out_dev),
+                                   _stream(stream)))
+
+
+def raycast_view(scene, intr, pose, depth_dev, rgba_dev=None, noise_dev=None, stream=None):
+    ci = intrinsics(intr)
+    _check(lib().relo_raycast_view(scene.handle, ctypes.byref(ci), _pose(pose), _ptr(noise_dev), _ptr(depth_dev),
+                                   _ptr(rgba_dev), _stream(stream)))
+
+
+def forest_eval(forest, depth_dev, rgba_dev, leaves_dev, stream=None):
+    H, W = depth_dev.shape[-2:]
+    _check(lib().relo_forest_eval(forest.handle, _ptr(depth_dev), _ptr(rgba_dev), int(W), int(H), _ptr(leaves_dev),
+                                  _stream(stream)))
+
+
+def forest_train_begin(forest, params: TrainParams):
+    _check(lib().relo_forest_train_begin(forest.handle, ctypes.byref(params)))
+
+
+def forest_train_frame(forest, intr, pose, depth_dev, rgba_dev, stream=None):
+    ci = intrinsics(intr)
+    _check(lib().relo_forest_train_frame(forest.handle, ctypes.byref(ci), _pose(pose), _ptr(depth_dev),
+                                         _ptr(rgba_dev), _stream(stream)))
+
+
+def forest_train_finish(forest, stream=None):
+    _check(lib().relo_forest_train_finish(forest.handle, _stream(stream)))
+
+
+def forest_train_reservoirs(forest, capacity):
+    L = 1 << forest.depth
+    samples = np.zeros((forest.n_trees, L, capacity, 3), np.float32)
+    count = np.zeros((forest.n_trees, L), np.int32)
+    _check(lib().relo_forest_train_reservoirs(forest.handle, samples.ctypes.data, count.ctypes.data))
+    return samples, count
+
+
+def ransac_workspace_size(width, height, params: RansacParams) -> int:
+    return int(lib().relo_ransac_workspace_size(int(width), int(height), ctypes.byref(params)))
+
+
+def ransac_relocalise(forest, depth_dev, leaves_dev, intr, params, workspace_dev, result_dev, stream=None):
+    ci = intrinsics(intr)
+    _check(lib().relo_ransac_relocalise(forest.handle, _ptr(depth_dev), _ptr(leaves_dev), ctypes.byref(ci),
+                                        ctypes.byref(params), _ptr(workspace_dev), workspace_dev.numel(),
+                                        _ptr(result_dev), _stream(stream)))
+
+
+def ransac_hypotheses(forest, depth_dev, leaves_dev, intr, params, workspace_dev, poses_dev, valid_dev, tries_dev,
+                      stream=None):
+    ci = intrinsics(intr)
+    _check(lib().relo_ransac_hypotheses(forest.handle, _ptr(depth_dev), _ptr(leaves_dev), ctypes.byref(ci),
+                                        ctypes.byref(params), _ptr(workspace_dev), workspace_dev.numel(),
+                                        _ptr(poses_dev), _ptr(valid_dev), _ptr(tries_dev), _stream(stream)))
+
+
+def ransac_round(forest, depth_dev, leaves_dev, intr, params, rnd, alive_dev, valid_dev, poses_dev, energy_dev,
+                 drawn_dev, survivors_dev, inliers_dev, workspace_dev, stream=None):
+    ci = intrinsics(intr)
+    _check(lib().relo_ransac_round(forest.handle, _ptr(depth_dev), _ptr(leaves_dev), ctypes.byref(ci),
+                                   ctypes.byref(params), int(rnd), _ptr(alive_dev), int(alive_dev.numel()),
+                                   _ptr(valid_dev), _ptr(poses_dev), _ptr(energy_dev), _ptr(drawn_dev),
+                                   _ptr(survivors_dev), _ptr(inliers_dev), _ptr(workspace_dev),
+                                   workspace_dev.numel(), _stream(stream)))
+
+
+def verify(scene_a, intr, depth_b_dev, result_dev, depth_a_dev=None, stream=None):
+    ci = intrinsics(intr)
+    _check(lib().relo_verify(scene_a.handle, ctypes.byref(ci), _ptr(depth_b_dev), _ptr(result_dev),
+                             _ptr(depth_a_dev), _stream(stream)))
+
+
+def result_from_bytes(t) -> dict:
+    """Decode a relo_pose_result held in a (CPU) uint8 tensor / bytes."""
+    raw = bytes(t.cpu().numpy().tobytes()) if hasattr(t, "cpu") else bytes(t)
+    return PoseResult.from_buffer_copy(raw[:RESULT_BYTES]).to_dict()
+
+
+def make_attempts(items) -> "ctypes.Array":
+    """items: dicts with scene_b, forest_a, scene_a, intr, pose_b, noise (tensor or None), n_hyps, seed."""
+    arr = (Attempt * len(items))()
+    for i, it in enumerate(items):
+        a = arr[i]
+        a.scene_b, a.forest_a, a.scene_a = it["scene_b"].handle, it["forest_a"].handle, it["scene_a"].handle
+        a.intr = intrinsics(it["intr"])
+        a.pose_b = _pose(it["pose_b"])
+        a.noise_dev = None if it.get("noise") is None else it["noise"].data_ptr()
+        a.n_hyps = int(it.get("n_hyps", 0))
+        a.seed = int(it.get("seed", 0))
+    return arr
+
+
+def batch_workspace_size(attempts, params) -> int:
+    return int(lib().relo_batch_workspace_size(attempts, len(attempts), ctypes.byref(params)))
+
+
+def relocalise_batch(attempts, params, workspace_dev, stream=None):
+    res = (PoseResult * len(attempts))()
+    _check(lib().relo_relocalise_batch(attempts, len(attempts), ctypes.byref(params), _ptr(workspace_dev),
+                                       workspace_dev.numel(), res, _stream(stream)))
+    return [r.to_dict() for r in res]
+
+
+class Batch:
+    """Prepared batch (relo_batch_prepare / run / launch_count / destroy)."""
+
+    def __init__(self, attempts, params, workspace_dev):
+        h = c_vp()
+        _check(lib().relo_batch_prepare(attempts, len(attempts), ctypes.byref(params), _ptr(workspace_dev),
+                                        workspace_dev.numel(), ctypes.byref(h)))
+        self.handle = h.value
+        self.n = len(attempts)
+        self._ws = workspace_dev
+
+    def run(self, results_dev, stream=None):
+        _check(lib().relo_batch_run(self.handle, _ptr(results_dev), _stream(stream)))
+
+    @property
+    def launch_count(self) -> int:
+        return int(lib().relo_batch_launch_count(self.handle))
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.relo_batch_destroy(self.handle)
+            self.handle = None

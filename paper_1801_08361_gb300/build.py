@@ -1,0 +1,71 @@
+"""Builds the package's native code in-tree.
+
+librelo.so: the sm_103a CUDA library behind include/relo.h (nvcc, one -gencode, translation
+units compiled in parallel, static CUDA runtime).  _scene_sampler.so: the seeded input
+generator's C helper (gcc).  Both are git-ignored build products.
+"""
+from __future__ import annotations
+
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+LIB = os.path.join(HERE, "librelo.so")
+SOURCES = ["scene.cu", "forest.cu", "ransac.cu", "api.cu"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
+
+
+def _nvcc() -> str:
+    for cand in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
+        if cand and (os.path.sep not in cand or os.path.exists(cand)):
+            return cand
+    return "nvcc"
+
+
+def _stale(out: str, deps: list[str]) -> bool:
+    if not os.path.exists(out):
+        return True
+    t = os.path.getmtime(out)
+    return any(os.path.getmtime(d) > t for d in deps)
+
+
+def build_cuda(force: bool = False, verbose: bool = False) -> str:
+    hdrs = [os.path.join(CSRC, "relo_internal.cuh"), os.path.join(ROOT, "include", "relo.h")]
+    srcs = [os.path.join(CSRC, s) for s in SOURCES]
+    if not force and not _stale(LIB, srcs + hdrs):
+        return LIB
+    bdir = os.path.join(ROOT, "_build", "relo")
+    os.makedirs(bdir, exist_ok=True)
+    nvcc = _nvcc()
+    procs, objs = [], []
+    for s in srcs:
+        o = os.path.join(bdir, os.path.basename(s).replace(".cu", ".o"))
+        objs.append(o)
+        if force or _stale(o, [s] + hdrs):
+            cmd = [nvcc] + NVCC_FLAGS + ["-c", s, "-o", o]
+            if verbose:
+                print(" ".join(cmd), file=sys.stderr)
+            procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+    for cmd, p in procs:
+        out, _ = p.communicate()
+        if p.returncode != 0:
+            raise RuntimeError("nvcc failed: " + " ".join(cmd) + "\n" + out.decode(errors="replace"))
+    tmp = LIB + f".tmp{os.getpid()}"
+    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
+    subprocess.check_call(cmd)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+def build(force: bool = False, verbose: bool = False) -> None:
+    from .synth import build as build_synth
+    build_cuda(force=force, verbose=verbose)
+    build_synth(force=force)
+
+
+if __name__ == "__main__":
+    build(force="--force" in sys.argv, verbose=True)

@@ -1,0 +1,872 @@
+// api.cu -- the C ABI (include/relo.h): handle management, argument checks, workspace layout and
+// the launch sequence of one relocalisation attempt / a batch of attempts (Sec. 3.3.1, Fig. 3).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "relo_internal.cuh"
+
+using namespace relo;
+
+static_assert(sizeof(relo_pose_result) == 328, "relo_pose_result layout is part of the ABI");
+static_assert(sizeof(relo_attempt) == 232, "relo_attempt layout is part of the ABI");
+static_assert(sizeof(relo_intrinsics) == 56, "relo_intrinsics layout is part of the ABI");
+
+namespace {
+
+thread_local std::string g_error;
+
+relo_status fail(relo_status code, const std::string& msg) {
+  g_error = msg;
+  return code;
+}
+
+relo_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(RELO_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define RELO_CUDA(call)                                  \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+bool bad_size(int w, int h) { return w < 1 || h < 1 || w > 16384 || h > 16384; }
+
+relo_status check_intr(const relo_intrinsics* in) {
+  if (!in) return fail(RELO_EINVAL, "intrinsics is null");
+  if (bad_size(in->width, in->height)) return fail(RELO_EINVAL, "image size outside [1, 16384]");
+  if (!(in->fx > 0) || !(in->fy > 0)) return fail(RELO_EINVAL, "focal lengths must be positive");
+  if (!(in->depth_min > 0) || !(in->depth_max > in->depth_min)) return fail(RELO_EINVAL, "bad depth range");
+  return RELO_OK;
+}
+
+relo_status check_params(const relo_ransac_params* p) {
+  if (!p) return fail(RELO_EINVAL, "ransac params is null");
+  if (p->n_hyps < 1 || p->n_hyps > 4096) return fail(RELO_EINVAL, "n_hyps outside [1, 4096]");
+  if (p->batch < 1 || p->batch > 4096) return fail(RELO_EINVAL, "batch outside [1, 4096]");
+  if (p->max_tries < 1 || p->max_tries > (1 << 24)) return fail(RELO_EINVAL, "max_tries outside [1, 2^24]");
+  if (!(p->rigidity > 0) || !(p->inlier_dist > 0) || !(p->min_area >= 0)) return fail(RELO_EINVAL, "bad thresholds");
+  return RELO_OK;
+}
+
+int rounds_for(int K) {
+  int r = 0;
+  while (K > 1) {
+    K = (K + 1) / 2;
+    ++r;
+  }
+  return r;
+}
+
+// Per-attempt RANSAC scratch, carved from a workspace.
+void carve_ransac(Carver& c, RansacJob& j, int W, int H, int K, int B, int n_rounds) {
+  const int n_pix = W * H;
+  j.valid = c.take<int32_t>(n_pix);
+  j.chunk_count = c.take<int32_t>((n_pix + kCompactChunk - 1) / kCompactChunk);
+  j.n_valid = c.take<int32_t>(1);
+  j.poses = c.take<double>((size_t)K * 12);
+  j.hyp_ok = c.take<int32_t>(K);
+  j.tries = c.take<int32_t>(K);
+  j.energy = c.take<double>(K);
+  j.alive_a = c.take<int32_t>(K);
+  j.alive_b = c.take<int32_t>(K);
+  j.drawn = c.take<int32_t>((size_t)std::max(n_rounds, 1) * B);
+  j.inliers = c.take<int32_t>(K);
+  j.err = c.take<int32_t>(1);
+}
+
+void fill_ransac_job(RansacJob& j, const relo_forest* f, const uint16_t* depth, const uint16_t* leaves,
+                     const relo_intrinsics& in, const relo_ransac_params& p, int K, uint64_t seed) {
+  j.forest = f->view;
+  j.depth = depth;
+  j.leaves = leaves;
+  j.W = in.width;
+  j.H = in.height;
+  j.fx = in.fx;
+  j.fy = in.fy;
+  j.cx = in.cx;
+  j.cy = in.cy;
+  j.K = K;
+  j.B = p.batch;
+  j.max_tries = p.max_tries;
+  j.n_rounds = rounds_for(K);
+  j.rigidity = p.rigidity;
+  j.min_area = p.min_area;
+  j.inlier_dist = p.inlier_dist;
+  j.key0 = (uint32_t)(seed & 0xFFFFFFFFu);
+  j.key1 = (uint32_t)(seed >> 32);
+}
+
+// Alive / survivor prefix tables for rounds 0..R-1 (each n_jobs + 1 ints).
+void round_tables(const std::vector<int>& K, int R, std::vector<int32_t>& alive, std::vector<int32_t>& surv,
+                  std::vector<int>& tot_alive, std::vector<int>& tot_surv) {
+  const int n = (int)K.size();
+  alive.assign((size_t)R * (n + 1), 0);
+  surv.assign((size_t)R * (n + 1), 0);
+  tot_alive.assign(R, 0);
+  tot_surv.assign(R, 0);
+  std::vector<int> cur(K);
+  for (int r = 0; r < R; ++r) {
+    int a = 0, s = 0;
+    for (int j = 0; j < n; ++j) {
+      alive[(size_t)r * (n + 1) + j] = a;
+      surv[(size_t)r * (n + 1) + j] = s;
+      if (cur[j] > 1) {
+        a += cur[j];
+        s += (cur[j] + 1) / 2;
+        cur[j] = (cur[j] + 1) / 2;
+      }
+    }
+    alive[(size_t)r * (n + 1) + n] = a;
+    surv[(size_t)r * (n + 1) + n] = s;
+    tot_alive[r] = a;
+    tot_surv[r] = s;
+  }
+}
+
+}  // namespace
+
+// =============================================================================================
+// Batch plan (host side of relo_batch_*; also used by the single-attempt RANSAC entry points)
+// =============================================================================================
+struct relo_batch {
+  int n = 0;
+  int R = 0;
+  bool full = false;          // full attempts (render + forest + RANSAC + verify) or RANSAC only
+  RayJob* d_query = nullptr;
+  ForestJob* d_forest = nullptr;
+  RansacJob* d_ransac = nullptr;
+  RayJob* d_verify = nullptr;
+  int32_t* d_alive_prefix = nullptr;
+  int32_t* d_surv_prefix = nullptr;
+  relo_pose_result* d_results = nullptr;
+  std::vector<int> tot_alive, tot_surv;
+  int query_tiles = 0, verify_tiles = 0, chunks = 0, hyps = 0;
+  int64_t pixels = 0;
+  int32_t* d_errs = nullptr;
+  int launches = 0;
+};
+
+namespace {
+
+struct Layout {
+  size_t bytes = 0;
+};
+
+// Lays out (base == nullptr: sizes only) the workspace of a batch.  Fills host job arrays.
+relo_status layout_batch(const relo_attempt* at, int n, const relo_ransac_params& p, char* base, size_t* bytes,
+                         std::vector<RayJob>& q, std::vector<ForestJob>& fj, std::vector<RansacJob>& rj,
+                         std::vector<RayJob>& vj, relo_batch* plan, std::vector<int32_t>& alive_tab,
+                         std::vector<int32_t>& surv_tab) {
+  Carver c{base, 0};
+  auto* d_query = c.take<RayJob>(n);
+  auto* d_forest = c.take<ForestJob>(n);
+  auto* d_ransac = c.take<RansacJob>(n);
+  auto* d_verify = c.take<RayJob>(n);
+  std::vector<int> K(n);
+  int R = 0;
+  for (int i = 0; i < n; ++i) {
+    K[i] = at[i].n_hyps > 0 ? at[i].n_hyps : p.n_hyps;
+    R = std::max(R, rounds_for(K[i]));
+  }
+  auto* d_alive = c.take<int32_t>((size_t)std::max(R, 1) * (n + 1));
+  auto* d_surv = c.take<int32_t>((size_t)std::max(R, 1) * (n + 1));
+  auto* d_results = c.take<relo_pose_result>(n);
+  auto* d_errs = c.take<int32_t>(n);
+  q.assign(n, RayJob{});
+  fj.assign(n, ForestJob{});
+  rj.assign(n, RansacJob{});
+  vj.assign(n, RayJob{});
+  int tiles = 0, chunks = 0, hyps = 0;
+  int64_t pixels = 0;
+  for (int i = 0; i < n; ++i) {
+    const relo_attempt& a = at[i];
+    const int W = a.intr.width, H = a.intr.height, T = a.forest_a->T;
+    const size_t n_pix = (size_t)W * H;
+    uint16_t* depth = c.take<uint16_t>(n_pix);
+    uint32_t* rgba = c.take<uint32_t>(n_pix);
+    uint16_t* leaves = c.take<uint16_t>(n_pix * T);
+    // query render of scene b
+    RayJob& r = q[i];
+    r = make_ray_job(a.scene_b->view, a.intr, a.pose_b);
+    r.noise = a.noise_dev;
+    r.depth = depth;
+    r.rgba = rgba;
+    r.tile_begin = tiles;
+    // forest of a
+    ForestJob& f = fj[i];
+    f.forest = a.forest_a->view;
+    f.depth = depth;
+    f.rgba = rgba;
+    f.leaves = leaves;
+    f.W = W;
+    f.H = H;
+    f.pixel_begin = pixels;
+    // RANSAC
+    RansacJob& j = rj[i];
+    fill_ransac_job(j, a.forest_a, depth, leaves, a.intr, p, K[i], a.seed);
+    carve_ransac(c, j, W, H, K[i], p.batch, j.n_rounds);
+    j.err = d_errs ? d_errs + i : nullptr;
+    j.result = d_results + i;
+    j.chunk_begin = chunks;
+    j.hyp_begin = hyps;
+    j.has_pose_b = 1;
+    for (int k = 0; k < 16; ++k) j.pose_b[k] = a.pose_b[k];
+    // verification render of scene a at the proposed pose, compared with the query depth
+    RayJob& v = vj[i];
+    v = make_ray_job(a.scene_a->view, a.intr, nullptr);
+    v.pose_dev = d_results ? d_results[i].pose_c2s : nullptr;
+    v.status_dev = d_results ? &d_results[i].status : nullptr;
+    v.depth_ref = depth;
+    v.counts = d_results ? (unsigned long long*)&d_results[i].omega_a : nullptr;
+    v.err = j.err;
+    v.tile_begin = tiles;
+    r.err = j.err;
+    tiles += ray_tiles(W, H);
+    pixels += (int64_t)n_pix;
+    chunks += (int)((n_pix + kCompactChunk - 1) / kCompactChunk);
+    hyps += K[i];
+  }
+  *bytes = c.off;
+  if (plan) {
+    plan->n = n;
+    plan->R = R;
+    plan->d_query = d_query;
+    plan->d_forest = d_forest;
+    plan->d_ransac = d_ransac;
+    plan->d_verify = d_verify;
+    plan->d_alive_prefix = d_alive;
+    plan->d_surv_prefix = d_surv;
+    plan->d_results = d_results;
+    plan->query_tiles = plan->verify_tiles = tiles;
+    plan->pixels = pixels;
+    plan->chunks = chunks;
+    plan->hyps = hyps;
+    round_tables(K, R, alive_tab, surv_tab, plan->tot_alive, plan->tot_surv);
+    plan->d_errs = d_errs;
+  }
+  return RELO_OK;
+}
+
+relo_status check_attempts(const relo_attempt* at, int n, const relo_ransac_params* p) {
+  if (!at || n < 1) return fail(RELO_EINVAL, "need at least one attempt");
+  relo_status st = check_params(p);
+  if (st) return st;
+  for (int i = 0; i < n; ++i) {
+    if (!at[i].scene_b || !at[i].scene_a || !at[i].forest_a) return fail(RELO_EINVAL, "attempt has a null handle");
+    st = check_intr(&at[i].intr);
+    if (st) return st;
+    if (at[i].n_hyps < 0 || at[i].n_hyps > 4096) return fail(RELO_EINVAL, "attempt n_hyps outside [0, 4096]");
+  }
+  return RELO_OK;
+}
+
+relo_status run_ransac_stages(relo_batch* b, cudaStream_t s, int* launches) {
+  int L = 0;
+  RELO_CUDA(launch_compact(b->d_ransac, b->n, b->chunks, s));
+  L += 2;
+  RELO_CUDA(launch_hypotheses(b->d_ransac, b->n, b->hyps, s));
+  L += 1;
+  for (int r = 0; r < b->R; ++r) {
+    if (b->tot_alive[r] == 0) continue;
+    RELO_CUDA(launch_round(b->d_ransac, b->n, r, b->d_alive_prefix + (size_t)r * (b->n + 1), b->tot_alive[r],
+                           b->d_surv_prefix + (size_t)r * (b->n + 1), b->tot_surv[r], s));
+    L += 4;
+  }
+  RELO_CUDA(launch_finalise(b->d_ransac, b->n, s));
+  L += 1;
+  *launches = L;
+  return RELO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* relo_last_error(void) { return g_error.c_str(); }
+
+// ---------------------------------------------------------------------------------------------
+// Scenes
+// ---------------------------------------------------------------------------------------------
+relo_status relo_create_scene(const int32_t* coords, const float* tsdf, const uint8_t* rgba, int64_t n,
+                              double voxel, double mu, int32_t log2_buckets, relo_scene** out) {
+  if (!out) return fail(RELO_EINVAL, "out is null");
+  *out = nullptr;
+  if (n < 0 || n > (int64_t)INT32_MAX - 1) return fail(RELO_EINVAL, "n_blocks out of range");
+  if (n > 0 && (!coords || !tsdf || !rgba)) return fail(RELO_EINVAL, "null block arrays");
+  if (log2_buckets < 4 || log2_buckets > 30) return fail(RELO_EINVAL, "log2_buckets outside [4, 30]");
+  if (!(voxel > 0) || !(mu > 0)) return fail(RELO_EINVAL, "voxel_size and mu must be positive");
+  const uint32_t nb = 1u << log2_buckets, mask = nb - 1;
+  std::vector<int4> buckets(nb, pack_entry(0, 0, 0, -1, -1));
+  std::vector<int4> excess;
+  std::vector<int> chain(nb, 0);
+  int max_chain = 0;
+  for (int64_t b = 0; b < n; ++b) {
+    const int x = coords[3 * b], y = coords[3 * b + 1], z = coords[3 * b + 2];
+    if (x < -32768 || x > 32767 || y < -32768 || y > 32767 || z < -32768 || z > 32767)
+      return fail(RELO_EINVAL, "block coordinate outside int16 range");
+    const uint32_t h = block_hash(x, y, z) & mask;
+    const int4 key = pack_entry(x, y, z, (int)b, -1);
+    int4* e = &buckets[h];
+    if (e->z < 0) {
+      *e = key;
+      chain[h] = 1;
+      max_chain = std::max(max_chain, 1);
+      continue;
+    }
+    bool dup = false;
+    int4* last = e;
+    while (true) {
+      if (last->x == key.x && (last->y & 0xFFFF) == (key.y & 0xFFFF)) {
+        dup = true;
+        break;
+      }
+      if (last->w < 0) break;
+      last = &excess[last->w];
+    }
+    if (dup) continue;
+    last->w = (int)excess.size();
+    excess.push_back(key);  // may reallocate: 'last' is not used after this
+    chain[h] += 1;
+    max_chain = std::max(max_chain, chain[h]);
+  }
+  if (excess.empty()) excess.push_back(pack_entry(0, 0, 0, -1, -1));
+  relo_scene* s = new relo_scene();
+  s->n_blocks = n;
+  auto cleanup = [&]() {
+    cudaFree(s->d_buckets);
+    cudaFree(s->d_excess);
+    cudaFree(s->d_tsdf);
+    cudaFree(s->d_rgba);
+    delete s;
+  };
+  const size_t nv = (size_t)std::max<int64_t>(n, 1) * kVoxelsPerBlock;
+  if (cudaMalloc(&s->d_buckets, nb * sizeof(int4)) != cudaSuccess ||
+      cudaMalloc(&s->d_excess, excess.size() * sizeof(int4)) != cudaSuccess ||
+      cudaMalloc(&s->d_tsdf, nv * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&s->d_rgba, nv * sizeof(uint32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return fail(RELO_ENOMEM, "device allocation for the scene failed");
+  }
+  cudaError_t e = cudaMemcpy(s->d_buckets, buckets.data(), nb * sizeof(int4), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(s->d_excess, excess.data(), excess.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && n > 0) e = cudaMemcpy(s->d_tsdf, tsdf, (size_t)n * kVoxelsPerBlock * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && n > 0) e = cudaMemcpy(s->d_rgba, rgba, (size_t)n * kVoxelsPerBlock * 4, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "scene upload");
+  }
+  SceneView& v = s->view;
+  v.buckets = (const int4*)s->d_buckets;
+  v.excess = (const int4*)s->d_excess;
+  v.tsdf = (const float*)s->d_tsdf;
+  v.rgba = (const uint32_t*)s->d_rgba;
+  v.mask = mask;
+  v.n_blocks = (int32_t)n;
+  v.max_chain = max_chain + 1;
+  v.voxel = (float)voxel;
+  v.inv_voxel = (float)(1.0 / voxel);
+  v.mu = (float)mu;
+  v.block_size = (float)(8.0 * voxel);
+  v.inv_block = (float)(1.0 / (8.0 * voxel));
+  *out = s;
+  return RELO_OK;
+}
+
+void relo_destroy_scene(relo_scene* s) {
+  if (!s) return;
+  cudaFree(s->d_buckets);
+  cudaFree(s->d_excess);
+  cudaFree(s->d_tsdf);
+  cudaFree(s->d_rgba);
+  delete s;
+}
+
+relo_status relo_scene_lookup(const relo_scene* scene, const int32_t* keys, int64_t n, int64_t* out,
+                              relo_stream stream) {
+  if (!scene || (n > 0 && (!keys || !out)) || n < 0) return fail(RELO_EINVAL, "bad lookup arguments");
+  RELO_CUDA(launch_scene_lookup(scene->view, keys, n, out, nullptr, (cudaStream_t)stream));
+  return RELO_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Raycast
+// ---------------------------------------------------------------------------------------------
+relo_status relo_raycast_view(const relo_scene* scene, const relo_intrinsics* intr, const double pose[16],
+                              const float* noise, uint16_t* depth, uint8_t* rgba, relo_stream stream) {
+  if (!scene || !pose || !depth) return fail(RELO_EINVAL, "null scene, pose or depth");
+  relo_status st = check_intr(intr);
+  if (st) return st;
+  RayJob j = make_ray_job(scene->view, *intr, pose);
+  j.noise = noise;
+  j.depth = depth;
+  j.rgba = (uint32_t*)rgba;
+  RELO_CUDA(launch_raycast(nullptr, 1, &j, ray_tiles(intr->width, intr->height), rgba != nullptr, false,
+                           (cudaStream_t)stream));
+  return RELO_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Forests
+// ---------------------------------------------------------------------------------------------
+relo_status relo_create_forest(const void* nodes, int32_t T, int32_t D, const float* modes, const uint8_t* n_modes,
+                               int32_t M, relo_forest** out) {
+  if (!out) return fail(RELO_EINVAL, "out is null");
+  *out = nullptr;
+  if (T < 1 || T > kMaxTrees) return fail(RELO_EINVAL, "n_trees outside [1, 16]");
+  if (D < 1 || D > 16) return fail(RELO_EINVAL, "depth outside [1, 16]");
+  if (M < 1 || M > 64) return fail(RELO_EINVAL, "max_modes outside [1, 64]");
+  if (!nodes) return fail(RELO_EINVAL, "nodes is null");
+  const size_t n_int = ((size_t)1 << D) - 1, L = (size_t)1 << D;
+  relo_forest* f = new relo_forest();
+  f->T = T;
+  f->D = D;
+  f->M = M;
+  const size_t n_modes_bytes = (size_t)T * L, modes_bytes = (size_t)T * L * M * kModeFloats * sizeof(float);
+  if (cudaMalloc(&f->d_nodes, (size_t)T * n_int * 16) != cudaSuccess ||
+      cudaMalloc(&f->d_modes, modes_bytes) != cudaSuccess || cudaMalloc(&f->d_n_modes, n_modes_bytes) != cudaSuccess ||
+      cudaMalloc(&f->d_top, (size_t)T * L * sizeof(float4)) != cudaSuccess) {
+    cudaGetLastError();
+    relo_destroy_forest(f);
+    return fail(RELO_ENOMEM, "device allocation for the forest failed");
+  }
+  cudaError_t e = cudaMemcpy(f->d_nodes, nodes, (size_t)T * n_int * 16, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = modes ? cudaMemcpy(f->d_modes, modes, modes_bytes, cudaMemcpyHostToDevice)
+                                  : cudaMemset(f->d_modes, 0, modes_bytes);
+  if (e == cudaSuccess) e = n_modes ? cudaMemcpy(f->d_n_modes, n_modes, n_modes_bytes, cudaMemcpyHostToDevice)
+                                    : cudaMemset(f->d_n_modes, 0, n_modes_bytes);
+  if (e == cudaSuccess) e = launch_top_modes((const float*)f->d_modes, (const uint8_t*)f->d_n_modes, (int)(T * L), M,
+                                             (float4*)f->d_top, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    relo_destroy_forest(f);
+    return cuda_fail(e, "forest upload");
+  }
+  f->view.nodes = (const int4*)f->d_nodes;
+  f->view.modes = (const float*)f->d_modes;
+  f->view.n_modes = (const uint8_t*)f->d_n_modes;
+  f->view.top = (const float4*)f->d_top;
+  f->view.T = T;
+  f->view.D = D;
+  f->view.M = M;
+  *out = f;
+  return RELO_OK;
+}
+
+void relo_destroy_forest(relo_forest* f) {
+  if (!f) return;
+  cudaFree(f->d_nodes);
+  cudaFree(f->d_modes);
+  cudaFree(f->d_n_modes);
+  cudaFree(f->d_top);
+  free(f->res_samples);
+  free(f->res_count);
+  free(f->res_seen);
+  delete f;
+}
+
+relo_status relo_forest_get_modes(const relo_forest* f, float* modes, uint8_t* n_modes) {
+  if (!f) return fail(RELO_EINVAL, "forest is null");
+  const size_t L = (size_t)1 << f->D;
+  if (modes) RELO_CUDA(cudaMemcpy(modes, f->d_modes, (size_t)f->T * L * f->M * kModeFloats * 4, cudaMemcpyDeviceToHost));
+  if (n_modes) RELO_CUDA(cudaMemcpy(n_modes, f->d_n_modes, (size_t)f->T * L, cudaMemcpyDeviceToHost));
+  return RELO_OK;
+}
+
+relo_status relo_forest_eval(const relo_forest* f, const uint16_t* depth, const uint8_t* rgba, int32_t W, int32_t H,
+                             uint16_t* leaves, relo_stream stream) {
+  if (!f || !depth || !rgba || !leaves) return fail(RELO_EINVAL, "null forest or buffer");
+  if (bad_size(W, H)) return fail(RELO_EINVAL, "image size outside [1, 16384]");
+  ForestJob j{};
+  j.forest = f->view;
+  j.depth = depth;
+  j.rgba = (const uint32_t*)rgba;
+  j.leaves = leaves;
+  j.W = W;
+  j.H = H;
+  j.pixel_begin = 0;
+  RELO_CUDA(launch_forest(nullptr, 1, &j, (int64_t)W * H, (cudaStream_t)stream));
+  return RELO_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Relocaliser training
+// ---------------------------------------------------------------------------------------------
+relo_status relo_forest_train_begin(relo_forest* f, const relo_train_params* p) {
+  if (!f || !p) return fail(RELO_EINVAL, "null forest or params");
+  if (p->capacity < 1 || p->capacity > 4096) return fail(RELO_EINVAL, "capacity outside [1, 4096]");
+  if (p->stride < 1 || p->max_iter < 1 || !(p->bandwidth > 0)) return fail(RELO_EINVAL, "bad training params");
+  const size_t L = (size_t)f->T << f->D;
+  free(f->res_samples);
+  free(f->res_count);
+  free(f->res_seen);
+  f->res_samples = (float*)calloc(L * p->capacity * 3, sizeof(float));
+  f->res_count = (int32_t*)calloc(L, sizeof(int32_t));
+  f->res_seen = (int64_t*)calloc(L, sizeof(int64_t));
+  if (!f->res_samples || !f->res_count || !f->res_seen) return fail(RELO_ENOMEM, "host reservoirs");
+  f->train = *p;
+  f->training = true;
+  return RELO_OK;
+}
+
+relo_status relo_forest_train_frame(relo_forest* f, const relo_intrinsics* intr, const double pose[16],
+                                    const uint16_t* depth, const uint8_t* rgba, relo_stream stream) {
+  if (!f || !f->training) return fail(RELO_EINVAL, "training not begun");
+  if (!pose || !depth || !rgba) return fail(RELO_EINVAL, "null pose or image");
+  relo_status st = check_intr(intr);
+  if (st) return st;
+  const int W = intr->width, H = intr->height, S = f->train.stride, T = f->T;
+  const int gw = (W + S - 1) / S, gh = (H + S - 1) / S;
+  const size_t n_pix = (size_t)W * H;
+  cudaStream_t s = (cudaStream_t)stream;
+  uint16_t* d_leaves = nullptr;
+  float* d_coords = nullptr;
+  RELO_CUDA(cudaMalloc(&d_leaves, n_pix * T * sizeof(uint16_t)));
+  if (cudaMalloc(&d_coords, (size_t)gw * gh * 3 * sizeof(float)) != cudaSuccess) {
+    cudaFree(d_leaves);
+    return fail(RELO_ENOMEM, "training scratch");
+  }
+  ForestJob j{};
+  j.forest = f->view;
+  j.depth = depth;
+  j.rgba = (const uint32_t*)rgba;
+  j.leaves = d_leaves;
+  j.W = W;
+  j.H = H;
+  std::vector<uint16_t> leaves(n_pix * T), dep(n_pix);
+  std::vector<float> coords((size_t)gw * gh * 3);
+  cudaError_t e = launch_forest(nullptr, 1, &j, (int64_t)n_pix, s);
+  if (e == cudaSuccess) e = launch_scene_coords(depth, W, H, S, intr->fx, intr->fy, intr->cx, intr->cy, pose, d_coords, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(leaves.data(), d_leaves, leaves.size() * 2, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dep.data(), depth, n_pix * 2, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(coords.data(), d_coords, coords.size() * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_leaves);
+  cudaFree(d_coords);
+  if (e != cudaSuccess) return cuda_fail(e, "training frame");
+  // Algorithm R per leaf, offers in raster order, trees in order (host, sequential by definition)
+  const int cap = f->train.capacity;
+  const int64_t L = (int64_t)1 << f->D;
+  const uint32_t k0 = (uint32_t)(f->train.seed & 0xFFFFFFFFu), k1 = (uint32_t)(f->train.seed >> 32);
+  for (int v = 0; v < H; v += S) {
+    for (int u = 0; u < W; u += S) {
+      const size_t pix = (size_t)v * W + u;
+      if (dep[pix] == 0) continue;
+      const float* w = &coords[3 * ((size_t)(v / S) * gw + u / S)];
+      for (int t = 0; t < T; ++t) {
+        const int64_t id = (int64_t)t * L + leaves[(size_t)t * n_pix + pix];
+        const int64_t n = f->res_seen[id]++;
+        int64_t slot = -1;
+        if (n < cap) {
+          slot = n;
+          f->res_count[id] = (int32_t)(n + 1);
+        } else {
+          const uint4 x = philox4x32_10(make_uint4(3u, (uint32_t)id, (uint32_t)(n & 0xFFFFFFFF), (uint32_t)(n >> 32)), k0, k1);
+          const uint64_t jj = ((uint64_t)x.x * (uint64_t)(n + 1)) >> 32;
+          if (jj < (uint64_t)cap) slot = (int64_t)jj;
+        }
+        if (slot >= 0) std::memcpy(&f->res_samples[((size_t)id * cap + slot) * 3], w, 3 * sizeof(float));
+      }
+    }
+  }
+  return RELO_OK;
+}
+
+relo_status relo_forest_train_reservoirs(const relo_forest* f, float* samples, int32_t* count) {
+  if (!f || !f->training) return fail(RELO_EINVAL, "training not begun");
+  const size_t L = (size_t)f->T << f->D;
+  if (samples) std::memcpy(samples, f->res_samples, L * f->train.capacity * 3 * sizeof(float));
+  if (count) std::memcpy(count, f->res_count, L * sizeof(int32_t));
+  return RELO_OK;
+}
+
+relo_status relo_forest_train_finish(relo_forest* f, relo_stream stream) {
+  if (!f || !f->training) return fail(RELO_EINVAL, "training not begun");
+  const size_t L = (size_t)f->T << f->D;
+  const int cap = f->train.capacity;
+  cudaStream_t s = (cudaStream_t)stream;
+  float* d_samples = nullptr;
+  int32_t* d_count = nullptr;
+  RELO_CUDA(cudaMalloc(&d_samples, L * cap * 3 * sizeof(float)));
+  if (cudaMalloc(&d_count, L * sizeof(int32_t)) != cudaSuccess) {
+    cudaFree(d_samples);
+    return fail(RELO_ENOMEM, "training scratch");
+  }
+  cudaError_t e = cudaMemcpyAsync(d_samples, f->res_samples, L * cap * 3 * sizeof(float), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_count, f->res_count, L * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(f->d_modes, 0, L * f->M * kModeFloats * sizeof(float), s);
+  if (e == cudaSuccess)
+    e = launch_mean_shift(d_samples, d_count, cap, (int)L, (float)f->train.bandwidth, (float)f->train.tol,
+                          f->train.max_iter, (float)f->train.merge_dist, (float)f->train.cov_floor, f->M,
+                          (float*)f->d_modes, (uint8_t*)f->d_n_modes, s);
+  if (e == cudaSuccess) e = launch_top_modes((const float*)f->d_modes, (const uint8_t*)f->d_n_modes, (int)L, f->M,
+                                             (float4*)f->d_top, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_samples);
+  cudaFree(d_count);
+  if (e != cudaSuccess) return cuda_fail(e, "mean shift");
+  return RELO_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// RANSAC on one view
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+struct Single {
+  RansacJob job{};
+  RansacJob* d_job = nullptr;
+  int32_t* d_alive = nullptr;
+  int32_t* d_surv = nullptr;
+  size_t bytes = 0;
+  int chunks = 0;
+};
+
+// Workspace of one view: [job | alive prefix tables | surv tables | per-attempt scratch]
+void layout_single(char* base, int W, int H, int K, int B, int T, Single& s) {
+  (void)T;
+  Carver c{base, 0};
+  s.d_job = c.take<RansacJob>(1);
+  const int R = std::max(rounds_for(K), 1);
+  s.d_alive = c.take<int32_t>((size_t)R * 2);
+  s.d_surv = c.take<int32_t>((size_t)R * 2);
+  carve_ransac(c, s.job, W, H, K, B, rounds_for(K));
+  s.bytes = c.off;
+  s.chunks = (W * H + kCompactChunk - 1) / kCompactChunk;
+}
+
+relo_status single_setup(const relo_forest* f, const uint16_t* depth, const uint16_t* leaves,
+                         const relo_intrinsics* intr, const relo_ransac_params* p, void* ws, size_t ws_bytes,
+                         Single& s) {
+  if (!f || !depth || !leaves || !ws) return fail(RELO_EINVAL, "null forest, image or workspace");
+  relo_status st = check_intr(intr);
+  if (st) return st;
+  st = check_params(p);
+  if (st) return st;
+  if (((uintptr_t)ws & 255) != 0) return fail(RELO_EINVAL, "workspace must be 256-byte aligned");
+  layout_single(nullptr, intr->width, intr->height, p->n_hyps, p->batch, f->T, s);
+  if (s.bytes > ws_bytes) return fail(RELO_EINVAL, "workspace too small");
+  layout_single((char*)ws, intr->width, intr->height, p->n_hyps, p->batch, f->T, s);
+  fill_ransac_job(s.job, f, depth, leaves, *intr, *p, p->n_hyps, p->seed);
+  s.job.chunk_begin = 0;
+  s.job.hyp_begin = 0;
+  return RELO_OK;
+}
+
+}  // namespace
+
+size_t relo_ransac_workspace_size(int32_t W, int32_t H, const relo_ransac_params* p) {
+  if (!p || bad_size(W, H) || p->n_hyps < 1 || p->batch < 1) return 0;
+  Single s;
+  layout_single(nullptr, W, H, p->n_hyps, p->batch, 1, s);
+  return s.bytes;
+}
+
+relo_status relo_ransac_relocalise(const relo_forest* f, const uint16_t* depth, const uint16_t* leaves,
+                                   const relo_intrinsics* intr, const relo_ransac_params* p, void* ws,
+                                   size_t ws_bytes, relo_pose_result* result, relo_stream stream) {
+  Single s;
+  relo_status st = single_setup(f, depth, leaves, intr, p, ws, ws_bytes, s);
+  if (st) return st;
+  if (!result) return fail(RELO_EINVAL, "result is null");
+  cudaStream_t cs = (cudaStream_t)stream;
+  s.job.result = result;
+  std::vector<int> K(1, p->n_hyps);
+  std::vector<int32_t> at, su;
+  relo_batch b;
+  b.n = 1;
+  b.R = rounds_for(p->n_hyps);
+  round_tables(K, std::max(b.R, 1), at, su, b.tot_alive, b.tot_surv);
+  b.d_ransac = s.d_job;
+  b.d_alive_prefix = s.d_alive;
+  b.d_surv_prefix = s.d_surv;
+  b.chunks = s.chunks;
+  b.hyps = p->n_hyps;
+  RELO_CUDA(cudaMemcpyAsync(s.d_job, &s.job, sizeof(RansacJob), cudaMemcpyHostToDevice, cs));
+  RELO_CUDA(cudaMemcpyAsync(s.d_alive, at.data(), at.size() * 4, cudaMemcpyHostToDevice, cs));
+  RELO_CUDA(cudaMemcpyAsync(s.d_surv, su.data(), su.size() * 4, cudaMemcpyHostToDevice, cs));
+  RELO_CUDA(cudaMemsetAsync(s.job.err, 0, sizeof(int32_t), cs));
+  int launches = 0;
+  return run_ransac_stages(&b, cs, &launches);
+}
+
+relo_status relo_ransac_hypotheses(const relo_forest* f, const uint16_t* depth, const uint16_t* leaves,
+                                   const relo_intrinsics* intr, const relo_ransac_params* p, void* ws,
+                                   size_t ws_bytes, double* poses, int32_t* valid, int32_t* tries,
+                                   relo_stream stream) {
+  Single s;
+  relo_status st = single_setup(f, depth, leaves, intr, p, ws, ws_bytes, s);
+  if (st) return st;
+  if (!poses || !valid || !tries) return fail(RELO_EINVAL, "null output");
+  cudaStream_t cs = (cudaStream_t)stream;
+  RELO_CUDA(cudaMemcpyAsync(s.d_job, &s.job, sizeof(RansacJob), cudaMemcpyHostToDevice, cs));
+  RELO_CUDA(cudaMemsetAsync(s.job.err, 0, sizeof(int32_t), cs));
+  RELO_CUDA(launch_compact(s.d_job, 1, s.chunks, cs));
+  RELO_CUDA(launch_hypotheses(s.d_job, 1, p->n_hyps, cs));
+  RELO_CUDA(cudaMemcpyAsync(poses, s.job.poses, (size_t)p->n_hyps * 12 * 8, cudaMemcpyDeviceToDevice, cs));
+  RELO_CUDA(cudaMemcpyAsync(valid, s.job.hyp_ok, (size_t)p->n_hyps * 4, cudaMemcpyDeviceToDevice, cs));
+  RELO_CUDA(cudaMemcpyAsync(tries, s.job.tries, (size_t)p->n_hyps * 4, cudaMemcpyDeviceToDevice, cs));
+  return RELO_OK;
+}
+
+relo_status relo_ransac_round(const relo_forest* f, const uint16_t* depth, const uint16_t* leaves,
+                              const relo_intrinsics* intr, const relo_ransac_params* p, int32_t round,
+                              const int32_t* alive, int32_t n_alive, const int32_t* valid, double* poses,
+                              double* energy, int32_t* drawn, int32_t* survivors, int32_t* inliers, void* ws,
+                              size_t ws_bytes, relo_stream stream) {
+  Single s;
+  relo_status st = single_setup(f, depth, leaves, intr, p, ws, ws_bytes, s);
+  if (st) return st;
+  if (!alive || !valid || !poses || !energy || !drawn || !survivors || !inliers)
+    return fail(RELO_EINVAL, "null buffer");
+  if (round < 0 || n_alive < 2 || n_alive > p->n_hyps) return fail(RELO_EINVAL, "bad round or alive count");
+  cudaStream_t cs = (cudaStream_t)stream;
+  RansacJob j = s.job;
+  j.poses = poses;
+  j.energy = energy;
+  j.hyp_ok = (int32_t*)valid;
+  j.drawn = drawn;
+  j.inliers = inliers;
+  if (round & 1) {
+    j.alive_b = (int32_t*)alive;
+    j.alive_a = survivors;
+  } else {
+    j.alive_a = (int32_t*)alive;
+    j.alive_b = survivors;
+  }
+  const int32_t ap[2] = {0, n_alive}, sp[2] = {0, (n_alive + 1) / 2};
+  RELO_CUDA(cudaMemcpyAsync(s.d_job, &j, sizeof(RansacJob), cudaMemcpyHostToDevice, cs));
+  RELO_CUDA(cudaMemcpyAsync(s.d_alive, ap, sizeof(ap), cudaMemcpyHostToDevice, cs));
+  RELO_CUDA(cudaMemcpyAsync(s.d_surv, sp, sizeof(sp), cudaMemcpyHostToDevice, cs));
+  RELO_CUDA(cudaMemsetAsync(j.err, 0, sizeof(int32_t), cs));
+  RELO_CUDA(launch_compact(s.d_job, 1, s.chunks, cs));
+  RELO_CUDA(launch_round(s.d_job, 1, round, s.d_alive, n_alive, s.d_surv, (n_alive + 1) / 2, cs));
+  return RELO_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Verification
+// ---------------------------------------------------------------------------------------------
+relo_status relo_verify(const relo_scene* scene_a, const relo_intrinsics* intr, const uint16_t* depth_b,
+                        relo_pose_result* result, uint16_t* depth_a, relo_stream stream) {
+  if (!scene_a || !depth_b || !result) return fail(RELO_EINVAL, "null scene, depth or result");
+  relo_status st = check_intr(intr);
+  if (st) return st;
+  cudaStream_t cs = (cudaStream_t)stream;
+  RayJob v = make_ray_job(scene_a->view, *intr, nullptr);
+  v.pose_dev = result->pose_c2s;
+  v.status_dev = &result->status;
+  v.depth_ref = depth_b;
+  v.depth = depth_a;
+  v.counts = (unsigned long long*)&result->omega_a;
+  RELO_CUDA(cudaMemsetAsync(&result->omega, 0, 5 * sizeof(uint64_t), cs));
+  RELO_CUDA(launch_raycast(nullptr, 1, &v, ray_tiles(intr->width, intr->height), false, true, cs));
+  RELO_CUDA(launch_verify_decide_one(result, (uint64_t)intr->width * intr->height, cs));
+  return RELO_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Batches
+// ---------------------------------------------------------------------------------------------
+size_t relo_batch_workspace_size(const relo_attempt* at, int32_t n, const relo_ransac_params* p) {
+  if (check_attempts(at, n, p) != RELO_OK) return 0;
+  std::vector<RayJob> q, v;
+  std::vector<ForestJob> fj;
+  std::vector<RansacJob> rj;
+  std::vector<int32_t> a, s;
+  size_t bytes = 0;
+  layout_batch(at, n, *p, nullptr, &bytes, q, fj, rj, v, nullptr, a, s);
+  return bytes;
+}
+
+relo_status relo_batch_prepare(const relo_attempt* at, int32_t n, const relo_ransac_params* p, void* ws,
+                               size_t ws_bytes, relo_batch** out) {
+  if (!out) return fail(RELO_EINVAL, "out is null");
+  *out = nullptr;
+  relo_status st = check_attempts(at, n, p);
+  if (st) return st;
+  if (!ws || ((uintptr_t)ws & 255) != 0) return fail(RELO_EINVAL, "workspace must be non-null and 256-byte aligned");
+  std::vector<RayJob> q, v;
+  std::vector<ForestJob> fj;
+  std::vector<RansacJob> rj;
+  std::vector<int32_t> atab, stab;
+  size_t bytes = 0;
+  layout_batch(at, n, *p, nullptr, &bytes, q, fj, rj, v, nullptr, atab, stab);
+  if (bytes > ws_bytes) return fail(RELO_EINVAL, "workspace too small");
+  relo_batch* b = new relo_batch();
+  b->full = true;
+  layout_batch(at, n, *p, (char*)ws, &bytes, q, fj, rj, v, b, atab, stab);
+  cudaError_t e = cudaMemcpy(b->d_query, q.data(), n * sizeof(RayJob), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_forest, fj.data(), n * sizeof(ForestJob), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_ransac, rj.data(), n * sizeof(RansacJob), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_verify, v.data(), n * sizeof(RayJob), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !atab.empty())
+    e = cudaMemcpy(b->d_alive_prefix, atab.data(), atab.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !stab.empty())
+    e = cudaMemcpy(b->d_surv_prefix, stab.data(), stab.size() * 4, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    delete b;
+    return cuda_fail(e, "batch descriptors");
+  }
+  *out = b;
+  return RELO_OK;
+}
+
+relo_status relo_batch_run(relo_batch* b, relo_pose_result* results, relo_stream stream) {
+  if (!b || !b->full) return fail(RELO_EINVAL, "batch not prepared");
+  cudaStream_t s = (cudaStream_t)stream;
+  int L = 0;
+  RELO_CUDA(cudaMemsetAsync(b->d_errs, 0, b->n * sizeof(int32_t), s));
+  RELO_CUDA(launch_raycast(b->d_query, b->n, nullptr, b->query_tiles, true, false, s));
+  RELO_CUDA(launch_forest(b->d_forest, b->n, nullptr, b->pixels, s));
+  L += 2;
+  int Lr = 0;
+  relo_status st = run_ransac_stages(b, s, &Lr);
+  if (st) return st;
+  L += Lr;
+  RELO_CUDA(launch_raycast(b->d_verify, b->n, nullptr, b->verify_tiles, false, true, s));
+  RELO_CUDA(launch_verify_decide(b->d_ransac, b->n, s));
+  L += 2;
+  if (results && results != b->d_results)
+    RELO_CUDA(cudaMemcpyAsync(results, b->d_results, b->n * sizeof(relo_pose_result), cudaMemcpyDeviceToDevice, s));
+  b->launches = L;
+  return RELO_OK;
+}
+
+int32_t relo_batch_launch_count(const relo_batch* b) {
+  if (!b) return 0;
+  int L = 2 + 2 + 1 + 1 + 2;
+  for (int r = 0; r < b->R; ++r)
+    if (b->tot_alive[r] > 0) L += 4;
+  return L;
+}
+
+void relo_batch_destroy(relo_batch* b) { delete b; }
+
+relo_status relo_relocalise_batch(const relo_attempt* at, int32_t n, const relo_ransac_params* p, void* ws,
+                                  size_t ws_bytes, relo_pose_result* results_host, relo_stream stream) {
+  if (!results_host) return fail(RELO_EINVAL, "results is null");
+  relo_batch* b = nullptr;
+  relo_status st = relo_batch_prepare(at, n, p, ws, ws_bytes, &b);
+  if (st) return st;
+  st = relo_batch_run(b, nullptr, stream);
+  if (st == RELO_OK) {
+    cudaError_t e = cudaMemcpyAsync(results_host, b->d_results, n * sizeof(relo_pose_result), cudaMemcpyDeviceToHost,
+                                    (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) st = cuda_fail(e, "batch results");
+  }
+  relo_batch_destroy(b);
+  return st;
+}
+
+}  // extern "C"

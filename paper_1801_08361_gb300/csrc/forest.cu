@@ -1,0 +1,271 @@
+// forest.cu -- regression-forest evaluation and relocaliser training kernels.
+//
+// Sec. 3.3 (b): each agent's relocaliser is a scene-coordinate regression forest trained online
+// as per Cavallari et al.; Sec. 3.3.1: a query view is evaluated through another agent's forest.
+// The split-node features (depth-adaptive pixel-pair differences, integer form), the leaf
+// reservoirs and mean-shift modes are the library's readings of that paper-silent relocaliser.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "relo_internal.cuh"
+
+namespace relo {
+
+// Offsets are pixel-metres: probe = x + trunc(delta * 1000 / d), integer division toward zero.
+__device__ __forceinline__ int probe(int x, int delta, int d, int limit) {
+  const int q = x + (delta * 1000) / d;
+  return min(max(q, 0), limit);
+}
+
+__global__ void __launch_bounds__(256)
+    forest_kernel(const ForestJob* __restrict__ jobs, int n_jobs, const ForestJob single) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int lo = 0, hi = n_jobs - 1;
+  while (jobs && lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].pixel_begin <= gid) lo = mid;
+    else hi = mid - 1;
+  }
+  const ForestJob& job = jobs ? jobs[lo] : single;
+  const int64_t pix = gid - job.pixel_begin;
+  const int64_t n_pix = (int64_t)job.W * job.H;
+  if (pix < 0 || pix >= n_pix) return;
+  const int W = job.W, H = job.H;
+  const int u = (int)(pix % W), v = (int)(pix / W);
+  const ForestView& f = job.forest;
+  const int d = __ldg(&job.depth[pix]);
+  if (d == 0) {
+    for (int t = 0; t < f.T; ++t) job.leaves[(size_t)t * n_pix + pix] = 0xFFFF;
+    return;
+  }
+  const int n_int = (1 << f.D) - 1;
+  for (int t = 0; t < f.T; ++t) {
+    const int4* tree = f.nodes + (size_t)t * n_int;
+    int n = 0;
+    for (int level = 0; level < f.D; ++level) {
+      const int4 nd = __ldg(&tree[n]);
+      const int dx1 = (int)(int16_t)(nd.x & 0xFFFF), dy1 = nd.x >> 16;
+      const int dx2 = (int)(int16_t)(nd.y & 0xFFFF), dy2 = nd.y >> 16;
+      const int q1 = probe(v, dy1, d, H - 1) * W + probe(u, dx1, d, W - 1);
+      const int q2 = probe(v, dy2, d, H - 1) * W + probe(u, dx2, d, W - 1);
+      int a, b;
+      if ((nd.z & 0xFF) == 0) {
+        a = __ldg(&job.depth[q1]);
+        b = __ldg(&job.depth[q2]);
+      } else {
+        const int c1 = (nd.z >> 8) & 0xFF, c2 = (nd.z >> 16) & 0xFF;
+        a = (__ldg(&job.rgba[q1]) >> (8 * c1)) & 0xFF;
+        b = (__ldg(&job.rgba[q2]) >> (8 * c2)) & 0xFF;
+      }
+      n = (a - b < nd.w) ? 2 * n + 1 : 2 * n + 2;
+    }
+    job.leaves[(size_t)t * n_pix + pix] = (uint16_t)(n - n_int);
+  }
+}
+
+cudaError_t launch_forest(const ForestJob* jobs_dev, int n_jobs, const ForestJob* single, int64_t total_pixels,
+                          cudaStream_t s) {
+  if (total_pixels <= 0) return cudaSuccess;
+  ForestJob one{};
+  if (single) one = *single;
+  forest_kernel<<<(unsigned)((total_pixels + 255) / 256), 256, 0, s>>>(jobs_dev, n_jobs, one);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Training: scene coordinates of the stride-grid pixels, FP64 rounded to float32 (the values
+// the reservoirs store).  out[(v/stride) * ceil(W/stride) + u/stride] = P * backproject(d).
+// ---------------------------------------------------------------------------------------------
+struct Pose16 {
+  double p[16];
+};
+
+__global__ void scene_coords_kernel(const uint16_t* __restrict__ depth, int W, int H, int stride, double fx,
+                                    double fy, double cx, double cy, Pose16 P, float* __restrict__ out) {
+  const int gw = (W + stride - 1) / stride, gh = (H + stride - 1) / stride;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= gw * gh) return;
+  const int u = (i % gw) * stride, v = (i / gw) * stride;
+  const int d = depth[(size_t)v * W + u];
+  float* o = out + 3 * (size_t)i;
+  if (d == 0) {
+    o[0] = o[1] = o[2] = 0.f;
+    return;
+  }
+  // explicit rounding steps: no contraction, the same operation order as a plain C evaluation
+  const double z = __ddiv_rn((double)d, 1000.0);
+  const double c0 = __ddiv_rn(__dmul_rn(z, __dsub_rn((double)u, cx)), fx);
+  const double c1 = __ddiv_rn(__dmul_rn(z, __dsub_rn((double)v, cy)), fy);
+  for (int k = 0; k < 3; ++k) {
+    const double w = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(P.p[4 * k], c0), __dmul_rn(P.p[4 * k + 1], c1)),
+                                         __dmul_rn(P.p[4 * k + 2], z)),
+                               P.p[4 * k + 3]);
+    o[k] = (float)w;
+  }
+}
+
+cudaError_t launch_scene_coords(const uint16_t* depth, int W, int H, int stride, double fx, double fy, double cx,
+                                double cy, const double* P, float* out, cudaStream_t s) {
+  Pose16 p;
+  for (int k = 0; k < 16; ++k) p.p[k] = P[k];
+  const int n = ((W + stride - 1) / stride) * ((H + stride - 1) / stride);
+  scene_coords_kernel<<<(n + 255) / 256, 256, 0, s>>>(depth, W, H, stride, fx, fy, cx, cy, p, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Mean shift, one CTA per leaf.  Ascents run in FP32 from every sample (one seed per thread
+// at a time, samples broadcast from shared memory); the merge, ranking and per-mode statistics
+// follow in seed order, the statistics in FP64.
+// ---------------------------------------------------------------------------------------------
+constexpr int kMsThreads = 128;
+
+__global__ void __launch_bounds__(kMsThreads)
+    mean_shift_kernel(const float* __restrict__ samples, const int32_t* __restrict__ count, int capacity,
+                      float bandwidth, float tol, int max_iter, float merge_dist, float cov_floor, int max_modes,
+                      float* __restrict__ modes, uint8_t* __restrict__ n_modes_out) {
+  extern __shared__ float sm[];
+  const int leaf = blockIdx.x;
+  const int n = count[leaf];
+  float* xs = sm;                           // [cap][3]
+  float* zs = sm + 3 * capacity;            // [cap][3] converged points
+  int* member = (int*)(zs + 3 * capacity);  // [cap]
+  int* support = member + capacity;         // [cap]
+  int* rank = support + capacity;           // [cap]
+  __shared__ int s_modes;
+  const float* src = samples + (size_t)leaf * capacity * 3;
+  for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) xs[i] = src[i];
+  __syncthreads();
+  const float inv2h2 = 1.0f / (2.0f * bandwidth * bandwidth);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    float y0 = xs[3 * i], y1 = xs[3 * i + 1], y2 = xs[3 * i + 2];
+    for (int it = 0; it < max_iter; ++it) {
+      float n0 = 0.f, n1 = 0.f, n2 = 0.f, den = 0.f;
+      for (int j = 0; j < n; ++j) {
+        const float a = y0 - xs[3 * j], b = y1 - xs[3 * j + 1], c = y2 - xs[3 * j + 2];
+        const float k = expf(-(a * a + b * b + c * c) * inv2h2);
+        n0 += k * xs[3 * j];
+        n1 += k * xs[3 * j + 1];
+        n2 += k * xs[3 * j + 2];
+        den += k;
+      }
+      const float m0 = n0 / den, m1 = n1 / den, m2 = n2 / den;
+      const float sh = sqrtf((m0 - y0) * (m0 - y0) + (m1 - y1) * (m1 - y1) + (m2 - y2) * (m2 - y2));
+      y0 = m0;
+      y1 = m1;
+      y2 = m2;
+      if (sh < tol) break;
+    }
+    zs[3 * i] = y0;
+    zs[3 * i + 1] = y1;
+    zs[3 * i + 2] = y2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // merge in seed order: a converged point joins the first mode opened within merge_dist
+    int nm = 0;
+    for (int i = 0; i < n; ++i) {
+      int found = -1;
+      for (int m = 0; m < nm; ++m) {
+        const int o = rank[m];  // rank[] temporarily holds the opening seed of each mode
+        const float a = zs[3 * i] - zs[3 * o], b = zs[3 * i + 1] - zs[3 * o + 1], c = zs[3 * i + 2] - zs[3 * o + 2];
+        if (sqrtf(a * a + b * b + c * c) < merge_dist) {
+          found = m;
+          break;
+        }
+      }
+      if (found < 0) {
+        found = nm;
+        rank[nm] = i;
+        support[nm] = 0;
+        ++nm;
+      }
+      member[i] = found;
+      support[found]++;
+    }
+    // rank by support, descending; stable for ties (opening order)
+    for (int m = 0; m < nm; ++m) rank[m] = m;
+    for (int a = 1; a < nm; ++a) {
+      const int v = rank[a];
+      int b = a - 1;
+      while (b >= 0 && support[rank[b]] < support[v]) {
+        rank[b + 1] = rank[b];
+        --b;
+      }
+      rank[b + 1] = v;
+    }
+    s_modes = nm < max_modes ? nm : max_modes;
+    n_modes_out[leaf] = (uint8_t)s_modes;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < s_modes; q += blockDim.x) {
+    const int m = rank[q];
+    double mean[3] = {0, 0, 0};
+    int cnt = 0;
+    for (int i = 0; i < n; ++i)
+      if (member[i] == m) {
+        mean[0] += xs[3 * i];
+        mean[1] += xs[3 * i + 1];
+        mean[2] += xs[3 * i + 2];
+        ++cnt;
+      }
+    for (int k = 0; k < 3; ++k) mean[k] /= cnt;
+    double S[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < n; ++i)
+      if (member[i] == m) {
+        const double e[3] = {xs[3 * i] - mean[0], xs[3 * i + 1] - mean[1], xs[3 * i + 2] - mean[2]};
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) S[3 * a + b] += e[a] * e[b];
+      }
+    for (int k = 0; k < 9; ++k) S[k] /= cnt;
+    S[0] += cov_floor;
+    S[4] += cov_floor;
+    S[8] += cov_floor;
+    const double det = S[0] * (S[4] * S[8] - S[5] * S[7]) - S[1] * (S[3] * S[8] - S[5] * S[6]) +
+                       S[2] * (S[3] * S[7] - S[4] * S[6]);
+    const double weight = (double)cnt / n;
+    const double two_pi = 6.283185307179586;
+    float* o = modes + ((size_t)leaf * max_modes + q) * kModeFloats;
+    o[0] = (float)mean[0];
+    o[1] = (float)mean[1];
+    o[2] = (float)mean[2];
+    o[3] = (float)((S[4] * S[8] - S[5] * S[7]) / det);
+    o[4] = (float)((S[2] * S[7] - S[1] * S[8]) / det);
+    o[5] = (float)((S[1] * S[5] - S[2] * S[4]) / det);
+    o[6] = (float)((S[0] * S[8] - S[2] * S[6]) / det);
+    o[7] = (float)((S[2] * S[3] - S[0] * S[5]) / det);
+    o[8] = (float)((S[0] * S[4] - S[1] * S[3]) / det);
+    o[9] = (float)(log(weight) - 0.5 * log(two_pi * two_pi * two_pi * det));
+    o[10] = (float)weight;
+    o[11] = 0.f;
+  }
+}
+
+cudaError_t launch_mean_shift(const float* samples, const int32_t* count, int capacity, int n_leaves_total,
+                              float bandwidth, float tol, int max_iter, float merge_dist, float cov_floor,
+                              int max_modes, float* modes, uint8_t* n_modes, cudaStream_t s) {
+  const size_t smem = (size_t)capacity * (6 * sizeof(float) + 3 * sizeof(int));
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(mean_shift_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  mean_shift_kernel<<<n_leaves_total, kMsThreads, smem, s>>>(samples, count, capacity, bandwidth, tol, max_iter,
+                                                            merge_dist, cov_floor, max_modes, modes, n_modes);
+  return cudaGetLastError();
+}
+
+__global__ void top_modes_kernel(const float* __restrict__ modes, const uint8_t* __restrict__ n_modes, int n,
+                                 int max_modes, float4* __restrict__ top) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float* m = modes + (size_t)i * max_modes * kModeFloats;
+  top[i] = make_float4(m[0], m[1], m[2], (float)n_modes[i]);
+}
+
+cudaError_t launch_top_modes(const float* modes, const uint8_t* n_modes, int n_leaves_total, int max_modes,
+                             float4* top, cudaStream_t s) {
+  top_modes_kernel<<<(n_leaves_total + 255) / 256, 256, 0, s>>>(modes, n_modes, n_leaves_total, max_modes, top);
+  return cudaGetLastError();
+}
+
+}  // namespace relo

@@ -1,0 +1,348 @@
+// relo_internal.cuh -- device data layouts and helpers shared by the library's translation units.
+//
+// Everything here belongs to the CUDA path; nothing is shared with the CPU oracle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/relo.h"
+
+namespace relo {
+
+constexpr int kBlockSide = 8;
+constexpr int kVoxelsPerBlock = 512;
+constexpr int kMaxTrees = 16;
+constexpr int kModeFloats = 12;
+constexpr float kLogEps = 69.07755278982137f;  // -log(1e-30): energy of a pixel no mode explains
+constexpr int kMaxMarchSamples = 100000;
+
+// ---------------------------------------------------------------------------------------------
+// Spatial hash of a voxel scene.  Entry = 16 bytes {int16 x, y, z, pad; int32 block; int32 next},
+// loaded as one int4.  Bucket h holds the first block hashing to h; later ones are chained
+// through the excess list (next = index into it, -1 ends the chain).
+// ---------------------------------------------------------------------------------------------
+struct SceneView {
+  const int4* buckets;
+  const int4* excess;
+  const float* tsdf;      // [n_blocks][512]
+  const uint32_t* rgba;   // [n_blocks][512] packed r | g << 8 | b << 16 | a << 24
+  uint32_t mask;          // n_buckets - 1
+  int32_t n_blocks;
+  int32_t max_chain;      // longest chain at build time (bounds the walk)
+  float voxel, inv_voxel, mu, block_size, inv_block;
+};
+
+__host__ __device__ inline uint32_t block_hash(int x, int y, int z) {
+  return ((uint32_t)x * 73856093u) ^ ((uint32_t)y * 19349669u) ^ ((uint32_t)z * 83492791u);
+}
+
+__host__ __device__ inline int4 pack_entry(int x, int y, int z, int block, int next) {
+  int4 e;
+  e.x = (int)((uint32_t)(uint16_t)(int16_t)x | ((uint32_t)(uint16_t)(int16_t)y << 16));
+  e.y = (int)((uint32_t)(uint16_t)(int16_t)z);
+  e.z = block;
+  e.w = next;
+  return e;
+}
+
+// Block index of block coordinate (x, y, z), -1 if absent; *err set if the chain walk exceeds
+// its bound (a corrupted table).
+__device__ __forceinline__ int lookup_block(const SceneView& s, int x, int y, int z, int* err) {
+  if (x < -32768 || x > 32767 || y < -32768 || y > 32767 || z < -32768 || z > 32767) return -1;
+  const int k0 = (int)((uint32_t)(uint16_t)(int16_t)x | ((uint32_t)(uint16_t)(int16_t)y << 16));
+  const int k1 = (int)((uint32_t)(uint16_t)(int16_t)z);
+  int4 e = __ldg(&s.buckets[block_hash(x, y, z) & s.mask]);
+  for (int steps = 0; steps <= s.max_chain; ++steps) {
+    if (e.z >= 0 && e.x == k0 && (e.y & 0xFFFF) == k1) return e.z;
+    if (e.w < 0) return -1;
+    e = __ldg(&s.excess[e.w]);
+  }
+  *err = 1;
+  return -1;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Forest
+// ---------------------------------------------------------------------------------------------
+struct ForestView {
+  const int4* nodes;        // [T][2^D - 1] split nodes, 16 bytes each
+  const float* modes;       // [T][2^D][M][12]
+  const uint8_t* n_modes;   // [T][2^D]
+  const float4* top;        // [T][2^D]: mode 0 mean xyz, w = number of modes
+  int32_t T, D, M;
+};
+
+// ---------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011): 10 rounds, multipliers 0xD2511F53 and
+// 0xCD9E8D57, Weyl key increments 0x9E3779B9 and 0xBB67AE85.
+// ---------------------------------------------------------------------------------------------
+__host__ __device__ inline uint32_t mulhi32(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+  return __umulhi(a, b);
+#else
+  return (uint32_t)(((uint64_t)a * b) >> 32);
+#endif
+}
+
+__host__ __device__ inline uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const uint32_t hi0 = mulhi32(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = mulhi32(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__host__ __device__ inline uint32_t uniform_below(uint32_t x, uint32_t n) { return mulhi32(x, n); }
+
+// ---------------------------------------------------------------------------------------------
+// Poses: 12 doubles, row-major [R | t], camera -> scene.
+// ---------------------------------------------------------------------------------------------
+struct PoseF {
+  float r[9], t[3];
+};
+
+__device__ __forceinline__ PoseF pose_to_float(const double* p) {
+  PoseF q;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) q.r[3 * i + j] = (float)p[4 * i + j];
+    q.t[i] = (float)p[4 * i + 3];
+  }
+  return q;
+}
+
+__device__ __forceinline__ float3 apply(const PoseF& P, float3 c) {
+  return make_float3(fmaf(P.r[0], c.x, fmaf(P.r[1], c.y, fmaf(P.r[2], c.z, P.t[0]))),
+                     fmaf(P.r[3], c.x, fmaf(P.r[4], c.y, fmaf(P.r[5], c.z, P.t[1]))),
+                     fmaf(P.r[6], c.x, fmaf(P.r[7], c.y, fmaf(P.r[8], c.z, P.t[2]))));
+}
+
+// Rigid transform from centroids and cross-covariance by Horn's closed form (1987): the rotation is
+// the unit quaternion of the largest eigenvalue of the symmetric 4x4 matrix N(S), S = sum of
+// (c - cbar)(w - wbar)^T.  The eigenproblem is solved by cyclic Jacobi rotations in FP64, which
+// keeps the decomposition stable for near-degenerate point sets.  Writes 12 doubles [R | t].
+__device__ inline void horn_pose(const double S[9], const double cbar[3], const double wbar[3], double* out) {
+  const double Sxx = S[0], Sxy = S[1], Sxz = S[2], Syx = S[3], Syy = S[4], Syz = S[5], Szx = S[6], Szy = S[7],
+               Szz = S[8];
+  double A[4][4] = {{Sxx + Syy + Szz, Syz - Szy, Szx - Sxz, Sxy - Syx},
+                    {Syz - Szy, Sxx - Syy - Szz, Sxy + Syx, Szx + Sxz},
+                    {Szx - Sxz, Sxy + Syx, -Sxx + Syy - Szz, Syz + Szy},
+                    {Sxy - Syx, Szx + Sxz, Syz + Szy, -Sxx - Syy + Szz}};
+  double V[4][4] = {{1, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, 1, 0}, {0, 0, 0, 1}};
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int p = 0; p < 4; ++p) {
+      diag += A[p][p] * A[p][p];
+      for (int q = p + 1; q < 4; ++q) off += A[p][q] * A[p][q];
+    }
+    if (off <= 1e-30 * (diag + 1e-300)) break;
+    for (int p = 0; p < 3; ++p) {
+      for (int q = p + 1; q < 4; ++q) {
+        const double apq = A[p][q];
+        if (fabs(apq) < 1e-300) continue;
+        const double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
+        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < 4; ++k) {  // A <- J^T A J
+          const double akp = A[k][p], akq = A[k][q];
+          A[k][p] = c * akp - s * akq;
+          A[k][q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < 4; ++k) {
+          const double apk = A[p][k], aqk = A[q][k];
+          A[p][k] = c * apk - s * aqk;
+          A[q][k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < 4; ++k) {
+          const double vkp = V[k][p], vkq = V[k][q];
+          V[k][p] = c * vkp - s * vkq;
+          V[k][q] = s * vkp + c * vkq;
+        }
+      }
+    }
+  }
+  int best = 0;
+  for (int k = 1; k < 4; ++k)
+    if (A[k][k] > A[best][best]) best = k;
+  double w = V[0][best], x = V[1][best], y = V[2][best], z = V[3][best];
+  const double n = sqrt(w * w + x * x + y * y + z * z);
+  w /= n; x /= n; y /= n; z /= n;
+  const double R[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - w * z),     2 * (x * z + w * y),
+                       2 * (x * y + w * z),     1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                       2 * (x * z - w * y),     2 * (y * z + w * x),     1 - 2 * (x * x + y * y)};
+  for (int i = 0; i < 3; ++i) {
+    out[4 * i + 0] = R[3 * i + 0];
+    out[4 * i + 1] = R[3 * i + 1];
+    out[4 * i + 2] = R[3 * i + 2];
+    out[4 * i + 3] = wbar[i] - (R[3 * i] * cbar[0] + R[3 * i + 1] * cbar[1] + R[3 * i + 2] * cbar[2]);
+  }
+}
+
+// Warp-wide sum (all lanes get the result).
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ int warp_sum_i(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Round half up of a non-negative float to an integer in [lo, hi].
+__device__ __forceinline__ int round_half_up_clamp(float x, int lo, int hi) {
+  float r = floorf(x + 0.5f);
+  r = fminf(fmaxf(r, (float)lo), (float)hi);
+  return (int)r;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Raycast jobs (query renders, training renders, verification renders)
+// ---------------------------------------------------------------------------------------------
+struct RayJob {
+  SceneView scene;
+  float R[9], t[3];            // camera -> scene (ignored when pose_dev is set)
+  const double* pose_dev;      // device pose (12 doubles, row-major R | t) overriding R, t
+  const int32_t* status_dev;   // when set, the job is skipped unless *status_dev == RELO_OK
+  float fx, fy, cx, cy, dmin, dmax;
+  int32_t W, H;
+  const float* noise;          // nullable
+  uint16_t* depth;             // nullable in compare mode
+  uint32_t* rgba;              // nullable
+  const uint16_t* depth_ref;   // compare mode: reference depth (D_b)
+  unsigned long long* counts;  // compare mode: {omega_a, omega_b, omega_ab, sum |D_a - D_b|}
+  int32_t* err;                // device error flag (nullable)
+  int32_t tile_begin;          // first 16 x 16 tile of this job in the flattened launch
+  int32_t pad;
+};
+
+// ---------------------------------------------------------------------------------------------
+// Forest jobs (one image through one forest)
+// ---------------------------------------------------------------------------------------------
+struct ForestJob {
+  ForestView forest;
+  const uint16_t* depth;
+  const uint32_t* rgba;
+  uint16_t* leaves;            // [T][H][W]
+  int32_t W, H;
+  int64_t pixel_begin;         // first pixel of this job in the flattened launch
+};
+
+// ---------------------------------------------------------------------------------------------
+// RANSAC jobs (one query view, one forest) and their workspace
+// ---------------------------------------------------------------------------------------------
+struct RansacJob {
+  ForestView forest;
+  const uint16_t* depth;
+  const uint16_t* leaves;      // [T][H][W]
+  int32_t W, H;
+  double fx, fy, cx, cy;       // FP64 intrinsics: exact re-checks match the oracle bit for bit
+  int32_t K, B, max_tries, n_rounds;
+  double rigidity, min_area, inlier_dist;
+  uint32_t key0, key1;
+  // workspace
+  int32_t* valid;              // [W*H] valid pixel indices (raster order)
+  int32_t* chunk_count;        // [n_chunks]
+  int32_t* n_valid;            // [1]
+  double* poses;               // [K][12]
+  int32_t* hyp_ok;             // [K]
+  int32_t* tries;              // [K]
+  double* energy;              // [K]
+  int32_t* alive_a;            // [K]
+  int32_t* alive_b;            // [K]
+  int32_t* drawn;              // [n_rounds * B]
+  float4* drawn_cam;           // [n_rounds * B]
+  int32_t* inliers;            // [K]
+  int32_t* err;                // [1]
+  relo_pose_result* result;    // device
+  int32_t chunk_begin;         // flattened compaction chunks
+  int32_t hyp_begin;           // flattened hypotheses
+  int32_t has_pose_b;          // finalise also writes a_T_b = P_a P_b^-1
+  int32_t pad2;
+  double pose_b[16];           // camera -> scene b pose of the query
+};
+
+constexpr int kCompactChunk = 4096;
+
+// Workspace carving helper (256-byte aligned sub-buffers).
+struct Carver {
+  char* base;
+  size_t off;
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+// ---------------------------------------------------------------------------------------------
+// Launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------------------------
+// jobs_dev == nullptr: the single job is passed by value.
+cudaError_t launch_raycast(const RayJob* jobs_dev, int n_jobs, const RayJob* single, int total_tiles,
+                           bool with_colour, bool compare, cudaStream_t s);
+cudaError_t launch_forest(const ForestJob* jobs_dev, int n_jobs, const ForestJob* single, int64_t total_pixels,
+                          cudaStream_t s);
+int ray_tiles(int W, int H);
+cudaError_t launch_verify_decide(const RansacJob* jobs, int n_jobs, cudaStream_t s);
+cudaError_t launch_verify_decide_one(relo_pose_result* res, uint64_t omega, cudaStream_t s);
+cudaError_t launch_scene_lookup(SceneView sv, const int32_t* keys, int64_t n, int64_t* out, int32_t* err,
+                                cudaStream_t s);
+
+// RANSAC stages over a device array of jobs.
+cudaError_t launch_compact(const RansacJob* jobs, int n_jobs, int total_chunks, cudaStream_t s);
+cudaError_t launch_hypotheses(const RansacJob* jobs, int n_jobs, int total_hyps, cudaStream_t s);
+// round r: prefix[n_jobs + 1] = flattened alive-hypothesis offsets of the jobs still running
+cudaError_t launch_round(const RansacJob* jobs, int n_jobs, int round, const int32_t* alive_prefix_dev,
+                         int total_alive, const int32_t* surv_prefix_dev, int total_surv, cudaStream_t s);
+cudaError_t launch_finalise(const RansacJob* jobs, int n_jobs, cudaStream_t s);
+
+
+// Training
+cudaError_t launch_scene_coords(const uint16_t* depth, int W, int H, int stride, double fx, double fy, double cx,
+                                double cy, const double* P /*16 host values passed by value*/, float* out,
+                                cudaStream_t s);
+cudaError_t launch_mean_shift(const float* samples, const int32_t* count, int capacity, int n_leaves_total,
+                              float bandwidth, float tol, int max_iter, float merge_dist, float cov_floor,
+                              int max_modes, float* modes, uint8_t* n_modes, cudaStream_t s);
+cudaError_t launch_top_modes(const float* modes, const uint8_t* n_modes, int n_leaves_total, int max_modes,
+                             float4* top, cudaStream_t s);
+
+// Helpers for ray jobs
+RayJob make_ray_job(const SceneView& sv, const relo_intrinsics& in, const double* pose_host);
+
+}  // namespace relo
+
+// Opaque handles (C ABI)
+struct relo_scene {
+  relo::SceneView view;
+  void* d_buckets;
+  void* d_excess;
+  void* d_tsdf;
+  void* d_rgba;
+  int64_t n_blocks;
+};
+
+struct relo_forest {
+  relo::ForestView view;
+  void* d_nodes;
+  void* d_modes;
+  void* d_n_modes;
+  void* d_top;
+  int32_t T, D, M;
+  // training state (host)
+  relo_train_params train;
+  bool training;
+  float* res_samples;   // [T][L][cap][3]
+  int32_t* res_count;   // [T][L]
+  int64_t* res_seen;    // [T][L]
+};

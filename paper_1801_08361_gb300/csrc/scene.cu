@@ -1,0 +1,279 @@
+// scene.cu -- voxel-hashed TSDF scene: host-side table build, device lookup, the raycast
+// kernel used for query renders, training renders and depth-difference verification.
+//
+// Sec. 3.3 (a): each agent's sub-scene is an InfiniTAM-style voxel map; Sec. 3.3.1 / Fig. 3:
+// relocalisation renders colour + depth of scene b from a frame's pose and verifies a proposed
+// pose with a depth render of scene a (Omega_s and mu).  The march below is the library's
+// reading of the usual voxel raycast (the paper names it in its appendix on global map
+// rendering without giving its steps).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <vector>
+
+#include "relo_internal.cuh"
+
+namespace relo {
+
+// ---------------------------------------------------------------------------------------------
+// Trilinear sampling with a per-thread cache of the block holding the previous sample.
+// ---------------------------------------------------------------------------------------------
+struct BlockCache {
+  int bx, by, bz, ptr;
+};
+
+__device__ __forceinline__ int cached_block(const SceneView& s, BlockCache& c, int bx, int by, int bz, int* err) {
+  if (bx != c.bx || by != c.by || bz != c.bz) {
+    c.bx = bx;
+    c.by = by;
+    c.bz = bz;
+    c.ptr = lookup_block(s, bx, by, bz, err);
+  }
+  return c.ptr;
+}
+
+// Value of voxel (i, j, k): tsdf, or +1 when its block is unallocated.
+__device__ __forceinline__ float voxel_tsdf(const SceneView& s, BlockCache& c, int i, int j, int k, int* err) {
+  const int b = cached_block(s, c, i >> 3, j >> 3, k >> 3, err);
+  if (b < 0) return 1.0f;
+  return __ldg(&s.tsdf[(size_t)b * kVoxelsPerBlock + (i & 7) + 8 * (j & 7) + 64 * (k & 7)]);
+}
+
+__device__ __forceinline__ uint32_t voxel_rgba(const SceneView& s, BlockCache& c, int i, int j, int k, int* err) {
+  const int b = cached_block(s, c, i >> 3, j >> 3, k >> 3, err);
+  if (b < 0) return 0u;
+  return __ldg(&s.rgba[(size_t)b * kVoxelsPerBlock + (i & 7) + 8 * (j & 7) + 64 * (k & 7)]);
+}
+
+// Trilinear tsdf at voxel-space point q (= p / voxel), given the block b0 holding floor(q).
+__device__ __forceinline__ float trilinear_tsdf(const SceneView& s, BlockCache& c, int b0, int i, int j, int k,
+                                                float fx, float fy, float fz, int* err) {
+  float v[8];
+  if ((i & 7) != 7 && (j & 7) != 7 && (k & 7) != 7) {
+    // all eight corners inside block b0: one contiguous neighbourhood
+    const float* base = s.tsdf + (size_t)b0 * kVoxelsPerBlock + (i & 7) + 8 * (j & 7) + 64 * (k & 7);
+    v[0] = __ldg(base);
+    v[1] = __ldg(base + 1);
+    v[2] = __ldg(base + 8);
+    v[3] = __ldg(base + 9);
+    v[4] = __ldg(base + 64);
+    v[5] = __ldg(base + 65);
+    v[6] = __ldg(base + 72);
+    v[7] = __ldg(base + 73);
+  } else {
+#pragma unroll
+    for (int n = 0; n < 8; ++n) v[n] = voxel_tsdf(s, c, i + (n & 1), j + ((n >> 1) & 1), k + (n >> 2), err);
+  }
+  const float x00 = v[0] + fx * (v[1] - v[0]);
+  const float x10 = v[2] + fx * (v[3] - v[2]);
+  const float x01 = v[4] + fx * (v[5] - v[4]);
+  const float x11 = v[6] + fx * (v[7] - v[6]);
+  const float y0 = x00 + fy * (x10 - x00);
+  const float y1 = x01 + fy * (x11 - x01);
+  return y0 + fz * (y1 - y0);
+}
+
+__device__ uint32_t trilinear_rgba(const SceneView& s, BlockCache& c, float3 p, int* err) {
+  const float qx = p.x * s.inv_voxel, qy = p.y * s.inv_voxel, qz = p.z * s.inv_voxel;
+  const float flx = floorf(qx), fly = floorf(qy), flz = floorf(qz);
+  const int i = (int)flx, j = (int)fly, k = (int)flz;
+  const float fx = qx - flx, fy = qy - fly, fz = qz - flz;
+  float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    const int dx = n & 1, dy = (n >> 1) & 1, dz = n >> 2;
+    const float w = (dx ? fx : 1.f - fx) * (dy ? fy : 1.f - fy) * (dz ? fz : 1.f - fz);
+    const uint32_t col = voxel_rgba(s, c, i + dx, j + dy, k + dz, err);
+    acc[0] += w * (float)(col & 0xFF);
+    acc[1] += w * (float)((col >> 8) & 0xFF);
+    acc[2] += w * (float)((col >> 16) & 0xFF);
+  }
+  const uint32_t r = (uint32_t)round_half_up_clamp(acc[0], 0, 255);
+  const uint32_t g = (uint32_t)round_half_up_clamp(acc[1], 0, 255);
+  const uint32_t b = (uint32_t)round_half_up_clamp(acc[2], 0, 255);
+  return r | (g << 8) | (b << 16) | (255u << 24);
+}
+
+// One ray.  Returns the hit depth parameter (camera z, metres) or a negative value if none.
+__device__ float march_ray(const SceneView& s, float3 C, float3 d, float dmin, float dmax, BlockCache& c, int* err) {
+  const float dn = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
+  const float inv_dn = 1.0f / dn;
+  float lam = dmin, lam_prev = 0.f, f_prev = 0.f;
+  bool have_prev = false;
+  for (int it = 0; it < kMaxMarchSamples && lam <= dmax; ++it) {
+    const float px = fmaf(lam, d.x, C.x), py = fmaf(lam, d.y, C.y), pz = fmaf(lam, d.z, C.z);
+    const float qx = px * s.inv_voxel, qy = py * s.inv_voxel, qz = pz * s.inv_voxel;
+    const float flx = floorf(qx), fly = floorf(qy), flz = floorf(qz);
+    const int i = (int)flx, j = (int)fly, k = (int)flz;
+    const int bx = i >> 3, by = j >> 3, bz = k >> 3;
+    const int b = cached_block(s, c, bx, by, bz, err);
+    if (b < 0) {
+      // free space: jump just past this block's exit along the ray
+      float lx = INFINITY, ly = INFINITY, lz = INFINITY;
+      if (d.x > 0.f) lx = ((float)(bx + 1) * s.block_size - C.x) / d.x;
+      else if (d.x < 0.f) lx = ((float)bx * s.block_size - C.x) / d.x;
+      if (d.y > 0.f) ly = ((float)(by + 1) * s.block_size - C.y) / d.y;
+      else if (d.y < 0.f) ly = ((float)by * s.block_size - C.y) / d.y;
+      if (d.z > 0.f) lz = ((float)(bz + 1) * s.block_size - C.z) / d.z;
+      else if (d.z < 0.f) lz = ((float)bz * s.block_size - C.z) / d.z;
+      const float lexit = fminf(lx, fminf(ly, lz));
+      lam_prev = lam;
+      f_prev = 1.0f;
+      have_prev = true;
+      lam = fmaxf(lexit, lam) + 1e-5f;
+      continue;
+    }
+    const float f = trilinear_tsdf(s, c, b, i, j, k, qx - flx, qy - fly, qz - flz, err);
+    if (f <= 0.0f) {
+      if (!have_prev) return -1.0f;
+      return lam_prev + (lam - lam_prev) * f_prev / (f_prev - f);
+    }
+    lam_prev = lam;
+    f_prev = f;
+    have_prev = true;
+    lam += fmaxf(f * s.mu, s.voxel) * inv_dn;
+  }
+  return -1.0f;
+}
+
+constexpr int kTile = 16;
+
+template <bool kColour, bool kCompare>
+__global__ void __launch_bounds__(kTile* kTile)
+    raycast_kernel(const RayJob* __restrict__ jobs, int n_jobs, const RayJob single) {
+  // locate the job owning this tile (jobs are few; binary search on tile_begin)
+  int lo = 0, hi = n_jobs - 1;
+  while (jobs && lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].tile_begin <= (int)blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  const RayJob& job = jobs ? jobs[lo] : single;
+  const int tiles_x = (job.W + kTile - 1) / kTile;
+  const int tile = (int)blockIdx.x - job.tile_begin;
+  const int u = (tile % tiles_x) * kTile + (threadIdx.x % kTile);
+  const int v = (tile / tiles_x) * kTile + (threadIdx.x / kTile);
+  const bool active = u < job.W && v < job.H && (job.status_dev == nullptr || *job.status_dev == RELO_OK);
+
+  int err = 0;
+  int depth_mm = 0;
+  if (active) {
+    float R[9], t[3];
+    if (job.pose_dev) {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) R[3 * r + q] = (float)job.pose_dev[4 * r + q];
+        t[r] = (float)job.pose_dev[4 * r + 3];
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) R[q] = job.R[q];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) t[q] = job.t[q];
+    }
+    const float dcx = ((float)u - job.cx) / job.fx, dcy = ((float)v - job.cy) / job.fy;
+    const float3 d = make_float3(R[0] * dcx + R[1] * dcy + R[2], R[3] * dcx + R[4] * dcy + R[5],
+                                 R[6] * dcx + R[7] * dcy + R[8]);
+    const float3 C = make_float3(t[0], t[1], t[2]);
+    BlockCache cache{INT32_MIN, INT32_MIN, INT32_MIN, -1};
+    const float lam = march_ray(job.scene, C, d, job.dmin, job.dmax, cache, &err);
+    const size_t pix = (size_t)v * job.W + u;
+    uint32_t col = 0u;
+    if (lam >= job.dmin && lam <= job.dmax) {
+      float z_mm = lam * 1000.0f;
+      if (job.noise) z_mm += 1.5f * lam * lam * __ldg(&job.noise[pix]);
+      depth_mm = round_half_up_clamp(z_mm, 1, 65535);
+      if (kColour) col = trilinear_rgba(job.scene, cache, make_float3(fmaf(lam, d.x, C.x), fmaf(lam, d.y, C.y),
+                                                                      fmaf(lam, d.z, C.z)), &err);
+    }
+    if (job.depth) job.depth[pix] = (uint16_t)depth_mm;
+    if (kColour && job.rgba) job.rgba[pix] = col;
+    if (err && job.err) atomicExch(job.err, RELO_EDEVICE);
+  }
+  if (kCompare) {
+    // Sec. 3.3.1: |Omega_a|, |Omega_b|, |Omega_ab| and sum over Omega_ab of |D_a - D_b| (integers)
+    unsigned oa = 0, ob = 0, oab = 0, sum = 0;
+    if (active) {
+      const int db = job.depth_ref[(size_t)v * job.W + u];
+      oa = depth_mm > 0;
+      ob = db > 0;
+      oab = oa & ob;
+      sum = oab ? (unsigned)abs(depth_mm - db) : 0u;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      oa += __shfl_xor_sync(0xffffffffu, oa, o);
+      ob += __shfl_xor_sync(0xffffffffu, ob, o);
+      oab += __shfl_xor_sync(0xffffffffu, oab, o);
+      sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    }
+    __shared__ unsigned red[4][kTile * kTile / 32];
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+      red[0][w] = oa;
+      red[1][w] = ob;
+      red[2][w] = oab;
+      red[3][w] = sum;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+      unsigned long long acc = 0;
+      for (int q = 0; q < kTile * kTile / 32; ++q) acc += red[threadIdx.x][q];
+      if (acc && (job.status_dev == nullptr || *job.status_dev == RELO_OK)) atomicAdd(&job.counts[threadIdx.x], acc);
+    }
+  }
+}
+
+cudaError_t launch_raycast(const RayJob* jobs_dev, int n_jobs, const RayJob* single, int total_tiles,
+                           bool with_colour, bool compare, cudaStream_t s) {
+  if (total_tiles <= 0) return cudaSuccess;
+  const dim3 grid(total_tiles), block(kTile * kTile);
+  RayJob one{};
+  if (single) one = *single;
+  if (compare) raycast_kernel<false, true><<<grid, block, 0, s>>>(jobs_dev, n_jobs, one);
+  else if (with_colour) raycast_kernel<true, false><<<grid, block, 0, s>>>(jobs_dev, n_jobs, one);
+  else raycast_kernel<false, false><<<grid, block, 0, s>>>(jobs_dev, n_jobs, one);
+  return cudaGetLastError();
+}
+
+__global__ void scene_lookup_kernel(SceneView sv, const int32_t* __restrict__ keys, int64_t n,
+                                    int64_t* __restrict__ out, int32_t* err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int e = 0;
+  out[i] = lookup_block(sv, keys[3 * i], keys[3 * i + 1], keys[3 * i + 2], &e);
+  if (e && err) atomicExch(err, RELO_EDEVICE);
+}
+
+cudaError_t launch_scene_lookup(SceneView sv, const int32_t* keys, int64_t n, int64_t* out, int32_t* err,
+                                cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  scene_lookup_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sv, keys, n, out, err);
+  return cudaGetLastError();
+}
+
+RayJob make_ray_job(const SceneView& sv, const relo_intrinsics& in, const double* pose) {
+  RayJob j{};
+  j.scene = sv;
+  if (pose) {
+    for (int r = 0; r < 3; ++r) {
+      for (int q = 0; q < 3; ++q) j.R[3 * r + q] = (float)pose[4 * r + q];
+      j.t[r] = (float)pose[4 * r + 3];
+    }
+  }
+  j.fx = (float)in.fx;
+  j.fy = (float)in.fy;
+  j.cx = (float)in.cx;
+  j.cy = (float)in.cy;
+  j.dmin = (float)in.depth_min;
+  j.dmax = (float)in.depth_max;
+  j.W = in.width;
+  j.H = in.height;
+  return j;
+}
+
+int ray_tiles(int W, int H) { return ((W + kTile - 1) / kTile) * ((H + kTile - 1) / kTile); }
+
+}  // namespace relo

@@ -13,6 +13,13 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built relocalisation library")
 
 
+def pytest_runtest_setup(item):
+    if item.get_closest_marker("gpu") is not None:
+        import torch
+        if not torch.cuda.is_available():
+            pytest.skip("no CUDA device")
+
+
 @pytest.fixture(scope="session")
 def room():
     """Tiny workload: 4 x 4 x 3 m room with 20 boxes, 5 mm voxels (seed 1)."""
@@ -25,3 +32,26 @@ def room():
 def oracle_room(room):
     import oracle
     return oracle.Scene(room[1])
+
+
+@pytest.fixture(scope="session")
+def room_training(room, oracle_room):
+    """Ten noisy 320 x 240 training renders of the tiny room and their poses (oracle renders)."""
+    from paper_1801_08361_gb300 import synth
+    world, _ = room
+    intr = synth.Intrinsics.for_size(320, 240)
+    train = synth.training_poses(world, 10, seed=11)
+    frames = []
+    for i, P in enumerate(train):
+        d, c = oracle_room.raycast(intr, P, noise=synth.depth_noise(240, 320, 100 + i))
+        frames.append((intr, P, d, c))
+    return frames
+
+
+@pytest.fixture(scope="session")
+def room_forest(room_training):
+    """Tiny-workload forest (5 trees, depth 10, reservoirs of 64, <= 10 modes) filled by the oracle."""
+    import oracle
+    from paper_1801_08361_gb300 import synth
+    nodes = synth.random_forest_nodes(5, 10, seed=5, depth_tau=100, colour_tau=32)
+    return oracle.train_forest(nodes, room_training, oracle.LeafParams(capacity=64, max_modes=10, seed=7))

@@ -11,16 +11,8 @@ from paper_1801_08361_gb300 import synth
 
 
 @pytest.fixture(scope="module")
-def tiny_forest(room, oracle_room):
-    world, _ = room
-    intr = synth.Intrinsics.for_size(320, 240)
-    train = synth.training_poses(world, 10, seed=11)
-    frames = []
-    for i, P in enumerate(train):
-        d, c = oracle_room.raycast(intr, P, noise=synth.depth_noise(240, 320, 100 + i))
-        frames.append((intr, P, d, c))
-    nodes = synth.random_forest_nodes(5, 10, seed=5, depth_tau=100, colour_tau=32)
-    return oracle.train_forest(nodes, frames, oracle.LeafParams(capacity=64, max_modes=10, seed=7)), train
+def tiny_forest(room_training, room_forest):
+    return room_forest, [f[1] for f in room_training]
 
 
 def test_tiny_room_attempts_succeed_and_verify(room, oracle_room, tiny_forest):
