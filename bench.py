@@ -1,0 +1,412 @@
+"""Relocalisation attempts per second on the paper-sized workload (one JSON line on rank 0).
+
+Workload (synthetic, seeded): a 10 x 8 x 3 m house of 2 x 3 rooms (0.1 m interior walls with
+1 x 2 m doorways, 200 furniture boxes) sampled into a 5 mm voxel-hash TSDF (2^20 buckets); a
+regression forest of 5 trees of depth 15 with random pixel-pair splits, its leaves filled on the
+GPU from noisy 640 x 480 training renders along a trajectory (reservoirs of 1024, <= 10
+mean-shift modes); queries are 640 x 480 views near that trajectory with depth noise
+sigma = 1.5 mm z^2.  One attempt (Sec. 3.3.1, Fig. 3) = raycast the query RGB-D view of scene b,
+evaluate it through a's forest, preemptive RANSAC (1024 hypotheses, 64 pixels per round, 10
+halvings), depth raycast of scene a at the proposed pose and the Omega / mu verification.
+Scene a and b are the same house here (an agent relocalising against its own map).
+
+A step = one batch of ``--batch`` attempts through relo_batch_run (inputs resident in HBM; the
+L2 is flushed between steps; each step timed with CUDA events on the launching stream).
+``e2e`` = the same metric through relo_relocalise_batch with the query noise images copied from
+pinned host memory and the results copied back inside the timed region.
+``--impl reference`` times the CPU oracle (the deliberately slow FP64 reference) instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "reloc attempts/s at 640x480 (forest vs learned, same success); % HBM roofline"
+UNIT = "attempts/s"
+WORKLOAD = "house 10x8x3 m, 5 mm voxels, 2^20 buckets; 640x480 queries, depth noise 1.5 mm z^2; forest T=5 D=15, " \
+           "reservoir 1024, <=10 modes; preemptive RANSAC K=1024, B=64"
+W, H = 640, 480
+T_TREES, DEPTH, MAX_MODES, CAPACITY = 5, 15, 10, 1024
+K_HYPS, B_PIX = 1024, 64
+TRAIN_PER_ROOM = 16
+L2_FLUSH_BYTES = 512 << 20
+
+# Algorithmic bytes per unit (stated in DESIGN.md, "Roofline"): per query pixel the raycast
+# must write depth (2 B) + colour (4 B) and the verification raycast must read D_b (2 B) and
+# each touches the distinct scene data its samples need; the per-pixel scene-data figures below
+# are the oracle's exact counts of distinct voxels (4 B tsdf, 4 B colour) and block-table
+# entries (16 B) touched, averaged over 8 query views of this workload
+# (oracle/algorithmic_bytes.py).
+ALG_BYTES_PER_PIXEL = {
+    "query_raycast": None,
+    "verify_raycast": None,
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=128, help="attempts per step")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=0, help="(ncu) run this many steps and exit, no JSON")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------------------------------------
+# Workload construction (not timed)
+# ------------------------------------------------------------------------------------------------
+def build_workload(seed_offset=0):
+    from paper_1801_08361_gb300 import synth
+    world = synth.house_world(2)
+    blocks = synth.sample_scene(world)
+    intr = synth.Intrinsics.for_size(W, H, 12.0)
+    train = synth.training_poses(world, TRAIN_PER_ROOM, seed=11)
+    nodes = synth.random_forest_nodes(T_TREES, DEPTH, seed=5, depth_tau=100, colour_tau=32)
+    return world, blocks, intr, train, nodes
+
+
+def query_set(world, train, n, seed):
+    from paper_1801_08361_gb300 import synth
+    return synth.query_poses(world, train, n, seed=seed)
+
+
+def clocks_sampler(local_rank):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+    try:
+        return subprocess.Popen(["nvidia-smi", f"--id={local_rank}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except OSError:
+        return None
+
+
+def clocks_summary(proc):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        out, _ = proc.communicate(timeout=5)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+        out, _ = proc.communicate()
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in out.strip().splitlines():
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sm.append(float(f[1]))
+            mx.append(float(f[2]))
+        except ValueError:
+            continue
+        for n, v in zip(names, f[5:9]):
+            if v.lower() == "active":
+                reasons.add(n)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample)
+# ------------------------------------------------------------------------------------------------
+def oracle_sample(blocks, intr, train, nodes, world, budget_s=25.0, seed=0):
+    """Seconds per attempt of the FP64 oracle on this workload, from a bounded sample:
+    one attempt's stages, the two raycasts on every 4th row and column (1/16 of the rays, scaled
+    by 16), the forest on the full image, hypothesis generation for 64 of the 1024 hypotheses
+    (scaled by 16), and the rounds of a 1024-hypothesis RANSAC, against a forest trained by the
+    oracle on 6 training renders (stride 4).  Returns (seconds per attempt, description)."""
+    import oracle
+    from paper_1801_08361_gb300 import synth
+    sc = oracle.Scene(blocks)
+    frames = []
+    for i, P in enumerate(train[::max(1, len(train) // 6)][:6]):
+        d, c = sc.raycast(intr, P, noise=synth.depth_noise(H, W, 100 + i))
+        frames.append((intr, P, d, c))
+    forest = oracle.train_forest(nodes, frames, oracle.LeafParams(capacity=CAPACITY, max_modes=MAX_MODES, seed=7,
+                                                                  stride=4))
+    P = synth.query_poses(world, train, 1, seed=1000 + seed)[0]
+    v, u = np.mgrid[0:H:4, 0:W:4]
+    sub = (v * W + u).reshape(-1)
+    t0 = time.perf_counter()
+    sc.raycast(intr, P, noise=synth.depth_noise(H, W, 7), pixels=sub)
+    t_ray = (time.perf_counter() - t0) * 16
+    d, c = sc.raycast(intr, P, noise=synth.depth_noise(H, W, 7))          # full image, untimed input
+    t0 = time.perf_counter()
+    leaves = oracle.forest_eval(nodes, d, c)
+    t_forest = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    poses, ok, _ = oracle.generate_hypotheses(d, intr, leaves, forest,
+                                              oracle.RansacParams(n_hyps=64, batch=B_PIX, seed=seed))
+    t_hyp = (time.perf_counter() - t0) * (K_HYPS / 64)
+    reps = K_HYPS // 64
+    t0 = time.perf_counter()
+    res = oracle.preemptive_ransac(d, intr, leaves, forest, oracle.RansacParams(n_hyps=K_HYPS, batch=B_PIX, seed=seed),
+                                   hypotheses=(np.tile(poses, (reps, 1, 1)), np.tile(ok, reps)))
+    t_rounds = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    sc.raycast(intr, res["pose"], pixels=sub)
+    t_ver = (time.perf_counter() - t0) * 16
+    total = t_ray + t_forest + t_hyp + t_rounds + t_ver
+    desc = ("one 640x480 attempt, sampled: raycasts on 1/16 of the rays (x16), forest on all pixels, hypotheses for "
+            "64 of 1024 (x16), the 10 rounds of a 1024-hypothesis RANSAC (those 64 hypotheses repeated 16 times); " +
+            f"stage s: raycast {t_ray:.2f}, forest {t_forest:.2f}, hypotheses {t_hyp:.2f}, rounds {t_rounds:.2f}, "
+            f"verify {t_ver:.2f}")
+    return total, desc
+
+
+def cores_used():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------------------------------------
+# Reference arm: the CPU oracle, bounded per step
+# ------------------------------------------------------------------------------------------------
+def run_reference(args):
+    rank, world_size, _ = dist_env()
+    if rank != 0:
+        return 0
+    world, blocks, intr, train, nodes = build_workload()
+    times = []
+    desc = ""
+    for s in range(args.warmup + args.steps):
+        sec, desc = oracle_sample(blocks, intr, train, nodes, world, seed=s)
+        if s >= args.warmup:
+            times.append(sec)
+    sec = sum(times) / len(times)
+    value = 1.0 / sec
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sec * 1000.0, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "attempts_per_step": 1},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------------
+# Our arm
+# ------------------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    from paper_1801_08361_gb300 import binding as B
+    from paper_1801_08361_gb300 import synth
+
+    rank, world_size, local = dist_env()
+    if world_size > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world_size > 1 else 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    world, blocks, intr, train, nodes = build_workload()
+    scene = B.Scene(blocks, 20)
+    forest = B.Forest(nodes, max_modes=MAX_MODES)
+    # relocaliser training on the GPU: noisy renders along the trajectory, stride 2
+    B.forest_train_begin(forest, B.train_params(capacity=CAPACITY, stride=2, seed=7))
+    depth = torch.zeros((H, W), dtype=torch.int16, device=dev)
+    rgba = torch.zeros((H, W, 4), dtype=torch.uint8, device=dev)
+    for i, P in enumerate(train):
+        nz = torch.from_numpy(synth.depth_noise(H, W, 100 + i)).to(dev)
+        B.raycast_view(scene, intr, P, depth, rgba, noise_dev=nz)
+        B.forest_train_frame(forest, intr, P, depth, rgba)
+    B.forest_train_finish(forest)
+    del depth, rgba
+
+    A = args.batch
+    n_sets = max(1, min(4, args.warmup + args.steps))
+    prm = B.ransac_params(n_hyps=K_HYPS, batch=B_PIX, max_tries=10000)
+    sets = []
+    for si in range(n_sets):
+        qs = query_set(world, train, A, seed=1000 * (rank + 1) + si)
+        noise = torch.from_numpy(np.stack([synth.depth_noise(H, W, 5000 + 1000 * rank + 100 * si + k)
+                                           for k in range(A)])).to(dev)
+        items = [dict(scene_b=scene, forest_a=forest, scene_a=scene, intr=intr, pose_b=qs[k], noise=noise[k],
+                      seed=(rank << 40) + (si << 20) + k) for k in range(A)]
+        att = B.make_attempts(items)
+        ws = torch.empty(B.batch_workspace_size(att, prm), dtype=torch.uint8, device=dev)
+        bt = B.Batch(att, prm, ws)
+        bt.enable_timing(True)
+        res = torch.zeros(A * B.RESULT_BYTES, dtype=torch.uint8, device=dev)
+        sets.append(dict(qs=qs, noise=noise, att=att, ws=ws, batch=bt, res=res))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    if args.profile_steps:
+        # profiler runs: the steps sit in an NVTX range named "steps" (ncu --nvtx-include steps/)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("steps")
+        for s in range(args.profile_steps):
+            sets[s % n_sets]["batch"].run(sets[s % n_sets]["res"])
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        return 0
+
+    for s in range(args.warmup):
+        flush.zero_()
+        sets[s % n_sets]["batch"].run(sets[s % n_sets]["res"])
+    torch.cuda.synchronize()
+
+    # ---- device-resident timing -----------------------------------------------------------
+    if world_size > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = clocks_sampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stage_tot = {k: 0.0 for k in B.STAGES}
+    results = []
+    for s in range(args.steps):
+        st = sets[(args.warmup + s) % n_sets]
+        flush.zero_()
+        ev[s][0].record(stream)
+        st["batch"].run(st["res"])
+        ev[s][1].record(stream)
+        torch.cuda.synchronize()
+        for k, v in st["batch"].stage_ms().items():
+            stage_tot[k] += v
+        results.append((st, st["res"].cpu()))
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    clocks = clocks_summary(clk)
+    elapsed = sum(step_ms) / 1000.0
+    if world_size > 1:
+        t = torch.tensor([elapsed], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = A * args.steps * world_size / elapsed
+
+    # success (Sec. 4.2.1 criterion: <= 5 cm and <= 5 degrees) and verification rate
+    succ = ver = n = 0
+    tries_per_step = 0
+    for st, raw in results:
+        for k in range(A):
+            r = B.result_from_bytes(raw[k * B.RESULT_BYTES:(k + 1) * B.RESULT_BYTES])
+            P = st["qs"][k]
+            dt = float(np.linalg.norm(r["pose"][:3, 3] - P[:3, 3]))
+            cang = (np.trace(r["pose"][:3, :3] @ P[:3, :3].T) - 1) / 2
+            dr = math.degrees(math.acos(max(-1.0, min(1.0, cang))))
+            succ += int(r["status"] == 0 and dt <= 0.05 and dr <= 5.0)
+            tries_per_step += r["tries"]
+            ver += int(r["verified"])
+            n += 1
+
+    # ---- end to end through the public API (host buffers) ----------------------------------
+    host_noise = [torch.empty((A, H, W), dtype=torch.float32, pin_memory=True) for _ in range(n_sets)]
+    for si in range(n_sets):
+        host_noise[si].copy_(sets[si]["noise"].cpu())
+    e2e_t = 0.0
+    for s in range(args.steps):
+        st = sets[(args.warmup + s) % n_sets]
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st["noise"].copy_(host_noise[(args.warmup + s) % n_sets], non_blocking=True)
+        B.relocalise_batch(st["att"], prm, st["ws"])       # prepares, runs, copies results back, syncs
+        e2e_t += time.perf_counter() - t0
+    e2e_value = A * args.steps * world_size / e2e_t
+
+    # ---- roofline of the dominant stage ---------------------------------------------------
+    dom = max(stage_tot, key=stage_tot.get)
+    avg_ms = stage_tot[dom] / args.steps
+    roof = roofline(dom, avg_ms, A, tries_per_step / args.steps, clocks)
+
+    cpu = None
+    if rank == 0 and world_size == 1 and not args.no_cpu_baseline:
+        sec, desc = oracle_sample(blocks, intr, train, nodes, world)
+        cpu = {"value": 1.0 / sec, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world_size, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": elapsed * 1000.0 / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "attempts_per_step": A, "path": "forest",
+                           "l2": "flushed between steps (512 MiB write)",
+                           "success_rate": succ / n, "verified_rate": ver / n,
+                           "stage_ms_per_step": {k: v / args.steps for k, v in stage_tot.items()}},
+                "e2e": {"value": e2e_value, "unit": UNIT,
+                        "h2d_bytes_per_step": A * H * W * 4 + A * ctypes_attempt_bytes(),
+                        "d2h_bytes_per_step": A * B.RESULT_BYTES},
+                "gpu_launches": sets[0]["batch"].launch_count * args.steps,
+                "roofline": roof, "cpu_baseline": cpu, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if world_size > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+# Hypothesis search, ALU view: each try is one Philox4x32-10 block (10 rounds of two 32 x 32 -> 64
+# bit products = 40 integer multiply instructions) plus the rigidity and area tests; the peak is
+# the integer multiply-add issue rate, 64 per clock per SM (half the 128 FP32 lanes), x 152 SMs x
+# the SM clock, i.e. one Philox block per 40 IMAD slots.
+IMAD_PER_TRY = 40
+IMAD_PER_CLK_SM = 64
+N_SMS = 152
+
+
+def roofline(kernel, avg_ms, attempts, tries_per_launch, clocks):
+    if kernel == "hypotheses":
+        mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+        peak = IMAD_PER_CLK_SM * N_SMS * mhz * 1e6 / IMAD_PER_TRY / 1e9      # G tries / s
+        achieved = tries_per_launch / (avg_ms / 1000.0) / 1e9
+        return {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gtries/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "derived: 64 IMAD/clk/SM x 152 SMs x max SM clock / 40 IMAD per try"}
+    peak, peak_kind = measured_peaks()
+    per_px = ALG_BYTES_PER_PIXEL.get(kernel)
+    achieved = None if per_px is None else per_px * W * H * attempts / (avg_ms / 1000.0) / 1e9
+    return {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": None if achieved is None else achieved / peak, "traffic": None, "peak_source": peak_kind}
+
+
+def ctypes_attempt_bytes():
+    from paper_1801_08361_gb300 import binding as B
+    import ctypes
+    return ctypes.sizeof(B.Attempt)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -183,7 +183,7 @@ typedef struct relo_ransac_params {
   uint64_t seed;
 } relo_ransac_params;
 
-/* Result of one attempt (device or host copy; 328 bytes). */
+/* Result of one attempt (device or host copy; 336 bytes). */
 typedef struct relo_pose_result {
   double pose_c2s[16];     /* proposed camera -> scene a pose */
   double rel_a_b[16];      /* a_T_b = P_a P_b^-1 (filled by relo_relocalise_batch) */
@@ -195,6 +195,8 @@ typedef struct relo_pose_result {
   int32_t hypothesis;      /* index of the final hypothesis */
   int32_t n_rounds;
   uint64_t omega, omega_a, omega_b, omega_ab, sum_absdiff_mm; /* Sec. 3.3.1 verification counts */
+  uint64_t tries;          /* hypothesis tries a sequential scan makes: sum over h of (kept try + 1), or
+                              max_tries for a hypothesis without a passing try */
 } relo_pose_result;
 
 /* Bytes of device workspace relo_ransac_relocalise needs for a width x height view. */
@@ -213,9 +215,9 @@ relo_status relo_ransac_relocalise(const relo_forest* forest, const uint16_t* de
  * relo_ransac_hypotheses: poses_dev [K][12] (row-major R | t, camera -> scene), valid_dev [K],
  * tries_dev [K] (index of the kept try, max_tries if none).
  * relo_ransac_round: one round r from the given state: alive_dev [n_alive] hypothesis indices,
- * poses_dev [K][12] and energy_dev [K] updated in place, drawn_dev [(r+1) * batch] pixel
- * indices drawn in rounds 0..r (only round r's slice is written), survivors_dev
- * [ceil(n_alive/2)] and inliers_dev [K] written. */
+ * poses_dev [K][12] and energy_dev [K] updated in place, drawn_dev [(r+1) * batch] positions in
+ * the valid-pixel list (depth > 0, raster order) of the pixels drawn in rounds 0..r (only
+ * round r's slice is written), survivors_dev [ceil(n_alive/2)] and inliers_dev [K] written. */
 relo_status relo_ransac_hypotheses(const relo_forest* forest, const uint16_t* depth_dev, const uint16_t* leaves_dev,
                                    const relo_intrinsics* intr, const relo_ransac_params* p, void* workspace_dev,
                                    size_t workspace_bytes, double* poses_dev, int32_t* valid_dev, int32_t* tries_dev,
@@ -273,6 +275,15 @@ relo_status relo_batch_prepare(const relo_attempt* attempts_host, int32_t n, con
 relo_status relo_batch_run(relo_batch* batch, relo_pose_result* results_dev, relo_stream stream);
 int32_t relo_batch_launch_count(const relo_batch* batch);
 void relo_batch_destroy(relo_batch* batch);
+
+/* Stage timing, for roofline measurements.  Once enabled, relo_batch_run records CUDA events on
+ * its stream at the stage boundaries; relo_batch_stage_ms writes the milliseconds each stage of
+ * the last run took (call it after that run's stream has synchronised), in this order: query
+ * raycast, forest evaluation, valid-pixel compaction, hypotheses, RANSAC rounds, finalise,
+ * verification raycast, verification decision.  It returns the number of stages written (8),
+ * or 0 if timing is off or capacity is too small. */
+relo_status relo_batch_enable_timing(relo_batch* batch, int32_t enable);
+int32_t relo_batch_stage_ms(const relo_batch* batch, float* ms, int32_t capacity);
 
 #ifdef __cplusplus
 }

@@ -471,7 +471,8 @@ class RansacTrace:
     rounds: list = field(default_factory=list)   # per round: dict(pixels, energy, alive_before, survivors, poses, inliers)
 
 
-def preemptive_ransac(depth_img, intr, leaves, forest: Forest, p: RansacParams, trace: bool = False):
+def preemptive_ransac(depth_img, intr, leaves, forest: Forest, p: RansacParams, trace: bool = False,
+                      hypotheses=None):
     """Preemptive RANSAC (reading, after Cavallari et al.):
 
     hypotheses from generate_hypotheses; K_0 = K; while K_r > 1: draw B pixels
@@ -481,11 +482,15 @@ def preemptive_ransac(depth_img, intr, leaves, forest: Forest, p: RansacParams, 
     keep the first ceil(K_r / 2); re-fit every survivor by Kabsch on its inliers
     among all pixels drawn so far (pixel inlier when its best mode lies within
     ``inlier_dist`` of R c + t), keeping the pose when fewer than 3 inliers.
+    ``hypotheses`` = (poses [K,4,4], valid [K]) skips generation and starts the rounds from them.
     Returns dict(pose [4,4], energy, inliers, valid, trace).
     """
     key = seed_key(p.seed)
     valid = valid_pixels(depth_img)
-    poses, ok, _ = generate_hypotheses(depth_img, intr, leaves, forest, p)
+    if hypotheses is None:
+        poses, ok, _ = generate_hypotheses(depth_img, intr, leaves, forest, p)
+    else:
+        poses, ok = np.array(hypotheses[0], dtype=np.float64), np.array(hypotheses[1], dtype=bool)
     K = p.n_hyps
     E = np.where(ok, 0.0, np.inf)
     alive = np.arange(K)

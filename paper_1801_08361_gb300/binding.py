@@ -48,7 +48,7 @@ class PoseResult(ctypes.Structure):
     _fields_ = [("pose_c2s", c_dbl * 16), ("rel_a_b", c_dbl * 16), ("energy", c_dbl), ("n_inliers", c_i32),
                 ("status", c_i32), ("verified", c_i32), ("n_valid", c_i32), ("hypothesis", c_i32),
                 ("n_rounds", c_i32), ("omega", c_u64), ("omega_a", c_u64), ("omega_b", c_u64),
-                ("omega_ab", c_u64), ("sum_absdiff_mm", c_u64)]
+                ("omega_ab", c_u64), ("sum_absdiff_mm", c_u64), ("tries", c_u64)]
 
     def to_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("pose_c2s", "rel_a_b")}
@@ -94,7 +94,12 @@ _SIGS = {
     "relo_batch_run": (c_i32, [c_vp, c_vp, c_vp]),
     "relo_batch_launch_count": (c_i32, [c_vp]),
     "relo_batch_destroy": (None, [c_vp]),
+    "relo_batch_enable_timing": (c_i32, [c_vp, c_i32]),
+    "relo_batch_stage_ms": (c_i32, [c_vp, ctypes.POINTER(ctypes.c_float), c_i32]),
 }
+
+STAGES = ["query_raycast", "forest_eval", "compact", "hypotheses", "ransac_rounds", "finalise", "verify_raycast",
+          "verify_decide"]
 
 EXPORTED = sorted(_SIGS)
 
@@ -331,6 +336,14 @@ class Batch:
     @property
     def launch_count(self) -> int:
         return int(lib().relo_batch_launch_count(self.handle))
+
+    def enable_timing(self, on: bool = True):
+        _check(lib().relo_batch_enable_timing(self.handle, 1 if on else 0))
+
+    def stage_ms(self) -> dict:
+        buf = (ctypes.c_float * 8)()
+        n = lib().relo_batch_stage_ms(self.handle, buf, 8)
+        return {STAGES[k]: float(buf[k]) for k in range(n)}
 
     def __del__(self):
         if getattr(self, "handle", None) and _LIB is not None:

@@ -14,7 +14,7 @@
 
 using namespace relo;
 
-static_assert(sizeof(relo_pose_result) == 328, "relo_pose_result layout is part of the ABI");
+static_assert(sizeof(relo_pose_result) == 336, "relo_pose_result layout is part of the ABI");
 static_assert(sizeof(relo_attempt) == 232, "relo_attempt layout is part of the ABI");
 static_assert(sizeof(relo_intrinsics) == 56, "relo_intrinsics layout is part of the ABI");
 
@@ -66,9 +66,11 @@ int rounds_for(int K) {
 }
 
 // Per-attempt RANSAC scratch, carved from a workspace.
-void carve_ransac(Carver& c, RansacJob& j, int W, int H, int K, int B, int n_rounds) {
+void carve_ransac(Carver& c, RansacJob& j, int W, int H, int K, int B, int n_rounds, int T) {
   const int n_pix = W * H;
-  j.valid = c.take<int32_t>(n_pix);
+  j.nv = table_words(T);
+  j.table = c.take<uint4>((size_t)n_pix * j.nv);
+  j.refit = c.take<float>((size_t)K * 24);
   j.chunk_count = c.take<int32_t>((n_pix + kCompactChunk - 1) / kCompactChunk);
   j.n_valid = c.take<int32_t>(1);
   j.poses = c.take<double>((size_t)K * 12);
@@ -152,7 +154,17 @@ struct relo_batch {
   int64_t pixels = 0;
   int32_t* d_errs = nullptr;
   int launches = 0;
+  bool timing = false;
+  cudaEvent_t ev[9] = {};
+  ~relo_batch() {
+    for (cudaEvent_t& e : ev)
+      if (e) cudaEventDestroy(e);
+  }
 };
+
+namespace {
+constexpr int kStages = 8;
+}  // namespace
 
 namespace {
 
@@ -212,7 +224,7 @@ relo_status layout_batch(const relo_attempt* at, int n, const relo_ransac_params
     // RANSAC
     RansacJob& j = rj[i];
     fill_ransac_job(j, a.forest_a, depth, leaves, a.intr, p, K[i], a.seed);
-    carve_ransac(c, j, W, H, K[i], p.batch, j.n_rounds);
+    carve_ransac(c, j, W, H, K[i], p.batch, j.n_rounds, T);
     j.err = d_errs ? d_errs + i : nullptr;
     j.result = d_results + i;
     j.chunk_begin = chunks;
@@ -268,18 +280,26 @@ relo_status check_attempts(const relo_attempt* at, int n, const relo_ransac_para
   return RELO_OK;
 }
 
+// Records stage boundary k when timing is on (events 0..8 bracket the 8 stages).
+cudaError_t mark(relo_batch* b, int k, cudaStream_t s) {
+  return b->timing ? cudaEventRecord(b->ev[k], s) : cudaSuccess;
+}
+
 relo_status run_ransac_stages(relo_batch* b, cudaStream_t s, int* launches) {
   int L = 0;
   RELO_CUDA(launch_compact(b->d_ransac, b->n, b->chunks, s));
   L += 2;
+  RELO_CUDA(mark(b, 3, s));
   RELO_CUDA(launch_hypotheses(b->d_ransac, b->n, b->hyps, s));
-  L += 1;
+  L += 2;
+  RELO_CUDA(mark(b, 4, s));
   for (int r = 0; r < b->R; ++r) {
     if (b->tot_alive[r] == 0) continue;
     RELO_CUDA(launch_round(b->d_ransac, b->n, r, b->d_alive_prefix + (size_t)r * (b->n + 1), b->tot_alive[r],
                            b->d_surv_prefix + (size_t)r * (b->n + 1), b->tot_surv[r], s));
-    L += 4;
+    L += 5;
   }
+  RELO_CUDA(mark(b, 5, s));
   RELO_CUDA(launch_finalise(b->d_ransac, b->n, s));
   L += 1;
   *launches = L;
@@ -633,13 +653,12 @@ struct Single {
 
 // Workspace of one view: [job | alive prefix tables | surv tables | per-attempt scratch]
 void layout_single(char* base, int W, int H, int K, int B, int T, Single& s) {
-  (void)T;
   Carver c{base, 0};
   s.d_job = c.take<RansacJob>(1);
   const int R = std::max(rounds_for(K), 1);
   s.d_alive = c.take<int32_t>((size_t)R * 2);
   s.d_surv = c.take<int32_t>((size_t)R * 2);
-  carve_ransac(c, s.job, W, H, K, B, rounds_for(K));
+  carve_ransac(c, s.job, W, H, K, B, rounds_for(K), T);
   s.bytes = c.off;
   s.chunks = (W * H + kCompactChunk - 1) / kCompactChunk;
 }
@@ -667,7 +686,7 @@ relo_status single_setup(const relo_forest* f, const uint16_t* depth, const uint
 size_t relo_ransac_workspace_size(int32_t W, int32_t H, const relo_ransac_params* p) {
   if (!p || bad_size(W, H) || p->n_hyps < 1 || p->batch < 1) return 0;
   Single s;
-  layout_single(nullptr, W, H, p->n_hyps, p->batch, 1, s);
+  layout_single(nullptr, W, H, p->n_hyps, p->batch, kMaxTrees, s);  // enough for any forest
   return s.bytes;
 }
 
@@ -826,15 +845,21 @@ relo_status relo_batch_run(relo_batch* b, relo_pose_result* results, relo_stream
   cudaStream_t s = (cudaStream_t)stream;
   int L = 0;
   RELO_CUDA(cudaMemsetAsync(b->d_errs, 0, b->n * sizeof(int32_t), s));
+  RELO_CUDA(mark(b, 0, s));
   RELO_CUDA(launch_raycast(b->d_query, b->n, nullptr, b->query_tiles, true, false, s));
+  RELO_CUDA(mark(b, 1, s));
   RELO_CUDA(launch_forest(b->d_forest, b->n, nullptr, b->pixels, s));
+  RELO_CUDA(mark(b, 2, s));
   L += 2;
   int Lr = 0;
   relo_status st = run_ransac_stages(b, s, &Lr);
   if (st) return st;
   L += Lr;
+  RELO_CUDA(mark(b, 6, s));
   RELO_CUDA(launch_raycast(b->d_verify, b->n, nullptr, b->verify_tiles, false, true, s));
+  RELO_CUDA(mark(b, 7, s));
   RELO_CUDA(launch_verify_decide(b->d_ransac, b->n, s));
+  RELO_CUDA(mark(b, 8, s));
   L += 2;
   if (results && results != b->d_results)
     RELO_CUDA(cudaMemcpyAsync(results, b->d_results, b->n * sizeof(relo_pose_result), cudaMemcpyDeviceToDevice, s));
@@ -844,13 +869,30 @@ relo_status relo_batch_run(relo_batch* b, relo_pose_result* results, relo_stream
 
 int32_t relo_batch_launch_count(const relo_batch* b) {
   if (!b) return 0;
-  int L = 2 + 2 + 1 + 1 + 2;
+  int L = 2 + 2 + 2 + 1 + 2;  // render + forest, compaction, search + fit, finalise, verify + decide
   for (int r = 0; r < b->R; ++r)
-    if (b->tot_alive[r] > 0) L += 4;
+    if (b->tot_alive[r] > 0) L += 5;
   return L;
 }
 
 void relo_batch_destroy(relo_batch* b) { delete b; }
+
+relo_status relo_batch_enable_timing(relo_batch* b, int32_t enable) {
+  if (!b) return fail(RELO_EINVAL, "batch is null");
+  if (enable) {
+    for (cudaEvent_t& e : b->ev)
+      if (!e) RELO_CUDA(cudaEventCreate(&e));
+  }
+  b->timing = enable != 0;
+  return RELO_OK;
+}
+
+int32_t relo_batch_stage_ms(const relo_batch* b, float* ms, int32_t capacity) {
+  if (!b || !b->timing || !ms || capacity < kStages) return 0;
+  for (int k = 0; k < kStages; ++k)
+    if (cudaEventElapsedTime(&ms[k], b->ev[k], b->ev[k + 1]) != cudaSuccess) return 0;
+  return kStages;
+}
 
 relo_status relo_relocalise_batch(const relo_attempt* at, int32_t n, const relo_ransac_params* p, void* ws,
                                   size_t ws_bytes, relo_pose_result* results_host, relo_stream stream) {

@@ -2,14 +2,18 @@
 // after Cavallari et al. as used in Sec. 3.3.1; every rule is a stated reading, see relo.h).
 //
 // Stages, each one launch over all jobs of a batch:
-//   compact   : ordered list of valid pixels (two passes: chunk counts, then scatter);
-//   hypotheses: one CTA per hypothesis evaluates 256 tries at a time and keeps the first passing
-//               try (so the result equals a sequential scan of the tries); the 3-point Kabsch fit
-//               runs in FP64 (Horn's quaternion form);
-//   per round : draw B pixels; energies (warp per hypothesis, lanes over pixels, FP32 with an FP64
-//               running total); halving (CTA per job, bitonic sort of (energy, index)); re-fit
-//               (warp per survivor: FP32 centroids and cross-covariance reduced with shuffles,
-//               FP64 rotation).
+//   compact    : ordered table of valid pixels, each entry packing {u, v, depth, leaf per tree}
+//                in 16-byte words so that one load serves a correspondence (two passes: chunk
+//                counts, then an ordered scatter with warp ballots);
+//   search     : one CTA per hypothesis evaluates 256 tries at a time and keeps the first passing
+//                try, so the result equals a sequential scan of the tries.  The rigidity / area
+//                tests run in FP32 with a guard band; a try inside the band is settled in FP64 in
+//                the oracle's operation order;
+//   fit        : one thread per hypothesis: 3-point Kabsch in FP64 (Horn's quaternion form);
+//   per round  : draw B pixels; energies (warp per hypothesis, lanes over pixels, FP32 with an
+//                FP64 running total); halving (CTA per job, bitonic sort of (energy, index));
+//                re-fit sums (warp per survivor, one pass of shifted FP32 sums reduced with
+//                shuffles); re-fit solve (thread per survivor, FP64 Horn).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -30,11 +34,52 @@ __device__ __forceinline__ int find_job_by(const int32_t* prefix, int n_jobs, in
   return lo;
 }
 
+// u16 number k (0..7) of a 16-byte word
+__device__ __forceinline__ uint32_t u16_of(uint4 q, int k) {
+  const uint32_t w = (k < 4) ? ((k < 2) ? q.x : q.y) : ((k < 6) ? q.z : q.w);
+  return (k & 1) ? (w >> 16) : (w & 0xFFFFu);
+}
+
+struct TableEntry {
+  int u, v, depth;
+  uint4 w0;  // first word (u, v, depth, leaf[0..4])
+};
+
+__device__ __forceinline__ TableEntry load_entry(const RansacJob& job, int idx) {
+  TableEntry e;
+  e.w0 = __ldg(&job.table[(size_t)idx * job.nv]);
+  e.u = (int)(e.w0.x & 0xFFFFu);
+  e.v = (int)(e.w0.x >> 16);
+  e.depth = (int)(e.w0.y & 0xFFFFu);
+  return e;
+}
+
+// Leaf of tree t for a table entry (field 3 + t of the packed entry).
+__device__ __forceinline__ int entry_leaf(const RansacJob& job, int idx, const TableEntry& e, int t) {
+  const int f = 3 + t;
+  if (f < 8) return (int)u16_of(e.w0, f);
+  return (int)u16_of(__ldg(&job.table[(size_t)idx * job.nv + (f >> 3)]), f & 7);
+}
+
+__device__ __forceinline__ float3 cam_point_f(int u, int v, int d, float fx, float fy, float cx, float cy) {
+  const float z = (float)d * 0.001f;
+  return make_float3(z * ((float)u - cx) / fx, z * ((float)v - cy) / fy, z);
+}
+
+// FP64 camera point in the oracle's operation order: z = d / 1000; x = (z (u - cx)) / fx.
+__device__ __forceinline__ void cam_point_d(int u, int v, int d, double fx, double fy, double cx, double cy,
+                                            double out[3]) {
+  const double z = __ddiv_rn((double)d, 1000.0);
+  out[0] = __ddiv_rn(__dmul_rn(z, __dsub_rn((double)u, cx)), fx);
+  out[1] = __ddiv_rn(__dmul_rn(z, __dsub_rn((double)v, cy)), fy);
+  out[2] = z;
+}
+
 // ---------------------------------------------------------------------------------------------
-// Valid-pixel compaction
+// Valid-pixel table
 // ---------------------------------------------------------------------------------------------
 constexpr int kCompactThreads = 256;
-constexpr int kPerThread = kCompactChunk / kCompactThreads;  // 16
+constexpr int kIters = kCompactChunk / kCompactThreads;  // 16 coalesced passes of 256 pixels
 
 __device__ __forceinline__ int chunk_job(const RansacJob* jobs, int n_jobs, int gid) {
   int lo = 0, hi = n_jobs - 1;
@@ -51,10 +96,9 @@ __global__ void __launch_bounds__(kCompactThreads) compact_count_kernel(const Ra
   const RansacJob& job = jobs[chunk_job(jobs, n_jobs, blockIdx.x)];
   const int chunk = blockIdx.x - job.chunk_begin;
   const int n_pix = job.W * job.H;
-  const int base = chunk * kCompactChunk + threadIdx.x * kPerThread;
   int c = 0;
-  for (int k = 0; k < kPerThread; ++k) {
-    const int p = base + k;
+  for (int it = 0; it < kIters; ++it) {
+    const int p = chunk * kCompactChunk + it * kCompactThreads + threadIdx.x;
     if (p < n_pix && job.depth[p] > 0) ++c;
   }
   c = warp_sum_i(c);
@@ -74,34 +118,47 @@ __global__ void __launch_bounds__(kCompactThreads) compact_scatter_kernel(const 
   const int chunk = blockIdx.x - job.chunk_begin;
   const int n_pix = job.W * job.H;
   const int n_chunks = (n_pix + kCompactChunk - 1) / kCompactChunk;
+  const int T = job.forest.T, nv = job.nv;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __shared__ int s_off;
-  __shared__ int scan[kCompactThreads];
+  __shared__ int s_warp[kCompactThreads / 32];
   if (threadIdx.x < 32) {
     int s = 0;
     for (int c = threadIdx.x; c < chunk; c += 32) s += job.chunk_count[c];
     s = warp_sum_i(s);
     if (threadIdx.x == 0) s_off = s;
   }
-  const int base = chunk * kCompactChunk + threadIdx.x * kPerThread;
-  int mine = 0;
-  for (int k = 0; k < kPerThread; ++k) {
-    const int p = base + k;
-    if (p < n_pix && job.depth[p] > 0) ++mine;
-  }
-  scan[threadIdx.x] = mine;
   __syncthreads();
-  for (int o = 1; o < kCompactThreads; o <<= 1) {  // inclusive Hillis-Steele scan
-    const int v = threadIdx.x >= o ? scan[threadIdx.x - o] : 0;
+  int off = s_off;
+  for (int it = 0; it < kIters; ++it) {
+    const int p = chunk * kCompactChunk + it * kCompactThreads + threadIdx.x;
+    const int d = p < n_pix ? job.depth[p] : 0;
+    const unsigned ball = __ballot_sync(0xffffffffu, d > 0);
+    if (lane == 0) s_warp[warp] = __popc(ball);
     __syncthreads();
-    scan[threadIdx.x] += v;
+    int before = 0, total = 0;
+    for (int w = 0; w < kCompactThreads / 32; ++w) {
+      const int c = s_warp[w];
+      before += (w < warp) ? c : 0;
+      total += c;
+    }
+    if (d > 0) {
+      const int pos = off + before + __popc(ball & ((1u << lane) - 1u));
+      uint16_t f[24];
+      f[0] = (uint16_t)(p % job.W);
+      f[1] = (uint16_t)(p / job.W);
+      f[2] = (uint16_t)d;
+      for (int t = 0; t < T; ++t) f[3 + t] = job.leaves[(size_t)t * n_pix + p];
+      for (int k = 3 + T; k < 8 * nv; ++k) f[k] = 0;
+      uint4* dst = job.table + (size_t)pos * nv;
+      for (int q = 0; q < nv; ++q)
+        dst[q] = make_uint4(f[8 * q] | ((uint32_t)f[8 * q + 1] << 16), f[8 * q + 2] | ((uint32_t)f[8 * q + 3] << 16),
+                            f[8 * q + 4] | ((uint32_t)f[8 * q + 5] << 16), f[8 * q + 6] | ((uint32_t)f[8 * q + 7] << 16));
+    }
+    off += total;
     __syncthreads();
   }
-  int w = s_off + scan[threadIdx.x] - mine;
-  for (int k = 0; k < kPerThread; ++k) {
-    const int p = base + k;
-    if (p < n_pix && job.depth[p] > 0) job.valid[w++] = p;
-  }
-  if (chunk == n_chunks - 1 && threadIdx.x == kCompactThreads - 1) *job.n_valid = s_off + scan[threadIdx.x];
+  if (chunk == n_chunks - 1 && threadIdx.x == 0) *job.n_valid = off;
 }
 
 cudaError_t launch_compact(const RansacJob* jobs, int n_jobs, int total_chunks, cudaStream_t s) {
@@ -112,27 +169,11 @@ cudaError_t launch_compact(const RansacJob* jobs, int n_jobs, int total_chunks, 
 }
 
 // ---------------------------------------------------------------------------------------------
-// Hypotheses
+// Hypothesis search
 // ---------------------------------------------------------------------------------------------
 constexpr int kHypThreads = 256;
-constexpr float kGuardRigid = 1e-4f;  // FP32 error of a distance difference is < 2e-5 m here
-constexpr float kGuardArea = 2e-4f;   // and of |cross| < 2e-5 m^2
-
-__device__ __forceinline__ float3 cam_point_f(int pix, int W, int d, float fx, float fy, float cx, float cy) {
-  const float z = (float)d * 0.001f;
-  const int u = pix % W, v = pix / W;
-  return make_float3(z * ((float)u - cx) / fx, z * ((float)v - cy) / fy, z);
-}
-
-// FP64 camera point in the oracle's operation order: z = d / 1000; x = (z (u - cx)) / fx.
-__device__ __forceinline__ void cam_point_d(int pix, int W, int d, double fx, double fy, double cx, double cy,
-                                            double out[3]) {
-  const double z = __ddiv_rn((double)d, 1000.0);
-  const int u = pix % W, v = pix / W;
-  out[0] = __ddiv_rn(__dmul_rn(z, __dsub_rn((double)u, cx)), fx);
-  out[1] = __ddiv_rn(__dmul_rn(z, __dsub_rn((double)v, cy)), fy);
-  out[2] = z;
-}
+constexpr float kGuardRigid = 1e-4f;  // FP32 error of a distance difference stays below 2e-5 m here
+constexpr float kGuardArea = 2e-4f;   // and that of |cross| below 2e-5 m^2
 
 __device__ __forceinline__ double dist_d(const double* a, const double* b) {
   const double d0 = __dsub_rn(a[0], b[0]), d1 = __dsub_rn(a[1], b[1]), d2 = __dsub_rn(a[2], b[2]);
@@ -160,80 +201,85 @@ __device__ __forceinline__ float cross_norm_f(float3 p0, float3 p1, float3 p2) {
   return sqrtf(x * x + y * y + z * z);
 }
 
-struct TryDraw {
-  int pix[3];
-  int tree[3];
-  int leaf[3];
+struct Corr {
+  int idx[3], tree[3], leaf[3];
+  TableEntry e[3];
 };
 
-__device__ __forceinline__ TryDraw draw_try(const RansacJob& job, int h, int j, int n_valid) {
+__device__ __forceinline__ Corr draw_try(const RansacJob& job, int h, int j, int n_valid) {
   const uint4 x = philox4x32_10(make_uint4(1u, (uint32_t)h, (uint32_t)j, 0u), job.key0, job.key1);
-  TryDraw t;
+  Corr c;
   const uint32_t w[3] = {x.x, x.y, x.z};
-  const int n_pix = job.W * job.H;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    t.pix[k] = __ldg(&job.valid[uniform_below(w[k], (uint32_t)n_valid)]);
-    t.tree[k] = (int)((((x.w >> (8 * k)) & 0xFFu) * (uint32_t)job.forest.T) >> 8);
-    t.leaf[k] = __ldg(&job.leaves[(size_t)t.tree[k] * n_pix + t.pix[k]]);
+    c.idx[k] = (int)uniform_below(w[k], (uint32_t)n_valid);
+    c.tree[k] = (int)((((x.w >> (8 * k)) & 0xFFu) * (uint32_t)job.forest.T) >> 8);
   }
-  return t;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) c.e[k] = load_entry(job, c.idx[k]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) c.leaf[k] = entry_leaf(job, c.idx[k], c.e[k], c.tree[k]);
+  return c;
 }
 
 // Exact decision of the rigidity and area tests in FP64, in the oracle's operation order.
-__device__ bool exact_geometry(const RansacJob& job, const TryDraw& t, const float4* mode) {
-  double c[3][3], w[3][3];
+__device__ __noinline__ bool exact_geometry(const RansacJob& job, int h, int j, int n_valid) {
+  const Corr c = draw_try(job, h, j, n_valid);
+  const int L = 1 << job.forest.D;
+  double cp[3][3], wp[3][3];
   for (int k = 0; k < 3; ++k) {
-    cam_point_d(t.pix[k], job.W, job.depth[t.pix[k]], job.fx, job.fy, job.cx, job.cy, c[k]);
-    w[k][0] = (double)mode[k].x;
-    w[k][1] = (double)mode[k].y;
-    w[k][2] = (double)mode[k].z;
+    cam_point_d(c.e[k].u, c.e[k].v, c.e[k].depth, job.fx, job.fy, job.cx, job.cy, cp[k]);
+    const float4 m = __ldg(&job.forest.top[(size_t)c.tree[k] * L + c.leaf[k]]);
+    wp[k][0] = (double)m.x;
+    wp[k][1] = (double)m.y;
+    wp[k][2] = (double)m.z;
   }
   const int pr[3][2] = {{0, 1}, {0, 2}, {1, 2}};
   bool ok = true;
   for (int q = 0; q < 3; ++q) {
-    const double dc = dist_d(c[pr[q][0]], c[pr[q][1]]), dw = dist_d(w[pr[q][0]], w[pr[q][1]]);
+    const double dc = dist_d(cp[pr[q][0]], cp[pr[q][1]]), dw = dist_d(wp[pr[q][0]], wp[pr[q][1]]);
     ok = ok && (fabs(__dsub_rn(dc, dw)) <= job.rigidity);
   }
-  ok = ok && (cross_norm_d(c[0], c[1], c[2]) >= job.min_area) && (cross_norm_d(w[0], w[1], w[2]) >= job.min_area);
-  return ok;
+  return ok && (cross_norm_d(cp[0], cp[1], cp[2]) >= job.min_area) &&
+         (cross_norm_d(wp[0], wp[1], wp[2]) >= job.min_area);
 }
 
-__device__ bool try_passes(const RansacJob& job, int h, int j, int n_valid) {
-  const TryDraw t = draw_try(job, h, j, n_valid);
+// 0: the try fails; 1: it passes; 2: a test lies inside the FP32 guard band (settle in FP64).
+__device__ __forceinline__ int try_status(const RansacJob& job, int h, int j, int n_valid, float rig, float area,
+                                          float fx, float fy, float cx, float cy) {
+  const Corr c = draw_try(job, h, j, n_valid);
   const int L = 1 << job.forest.D;
   float4 m[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    if (t.leaf[k] >= L) return false;  // invalid pixel (0xFFFF) or a leaf id outside the forest
-    m[k] = __ldg(&job.forest.top[(size_t)t.tree[k] * L + t.leaf[k]]);
-    if (m[k].w < 0.5f) return false;  // empty leaf
+    if (c.leaf[k] >= L) return 0;  // a leaf id outside the forest
+    m[k] = __ldg(&job.forest.top[(size_t)c.tree[k] * L + c.leaf[k]]);
   }
-  if (t.pix[0] == t.pix[1] || t.pix[0] == t.pix[2] || t.pix[1] == t.pix[2]) return false;
-  float3 c[3], w[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    if (m[k].w < 0.5f) return 0;  // empty leaf
+  if (c.idx[0] == c.idx[1] || c.idx[0] == c.idx[2] || c.idx[1] == c.idx[2]) return 0;
+  float3 p[3], q[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    c[k] = cam_point_f(t.pix[k], job.W, job.depth[t.pix[k]], (float)job.fx, (float)job.fy, (float)job.cx,
-                       (float)job.cy);
-    w[k] = make_float3(m[k].x, m[k].y, m[k].z);
+    p[k] = cam_point_f(c.e[k].u, c.e[k].v, c.e[k].depth, fx, fy, cx, cy);
+    q[k] = make_float3(m[k].x, m[k].y, m[k].z);
   }
-  const float rig = (float)job.rigidity, area = (float)job.min_area;
   bool ambiguous = false;
   const int pr[3][2] = {{0, 1}, {0, 2}, {1, 2}};
 #pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    const float diff = fabsf(dist_f(c[pr[q][0]], c[pr[q][1]]) - dist_f(w[pr[q][0]], w[pr[q][1]]));
-    if (diff > rig + kGuardRigid) return false;
+  for (int s = 0; s < 3; ++s) {
+    const float diff = fabsf(dist_f(p[pr[s][0]], p[pr[s][1]]) - dist_f(q[pr[s][0]], q[pr[s][1]]));
+    if (diff > rig + kGuardRigid) return 0;
     if (diff >= rig - kGuardRigid) ambiguous = true;
   }
-  const float ac = cross_norm_f(c[0], c[1], c[2]), aw = cross_norm_f(w[0], w[1], w[2]);
-  if (ac < area - kGuardArea || aw < area - kGuardArea) return false;
+  const float ac = cross_norm_f(p[0], p[1], p[2]), aw = cross_norm_f(q[0], q[1], q[2]);
+  if (ac < area - kGuardArea || aw < area - kGuardArea) return 0;
   if (ac <= area + kGuardArea || aw <= area + kGuardArea) ambiguous = true;
-  if (!ambiguous) return true;
-  return exact_geometry(job, t, m);
+  return ambiguous ? 2 : 1;
 }
 
-__global__ void __launch_bounds__(kHypThreads) hypotheses_kernel(const RansacJob* __restrict__ jobs, int n_jobs) {
+__global__ void __launch_bounds__(kHypThreads, 4) search_kernel(const RansacJob* __restrict__ jobs, int n_jobs) {
   int lo = 0, hi = n_jobs - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -244,58 +290,88 @@ __global__ void __launch_bounds__(kHypThreads) hypotheses_kernel(const RansacJob
   const int h = blockIdx.x - job.hyp_begin;
   if (h >= job.K) return;
   const int n_valid = *job.n_valid;
-  __shared__ int s_win;
-  if (threadIdx.x == 0) s_win = INT_MAX;
-  __syncthreads();
+  const float rig = (float)job.rigidity, area = (float)job.min_area;
+  const float fx = (float)job.fx, fy = (float)job.fy, cx = (float)job.cx, cy = (float)job.cy;
+  __shared__ int s_win, s_res;
+  int found = INT_MAX;
   if (n_valid > 0) {
-    for (int base = 0; base < job.max_tries; base += kHypThreads) {
+    for (int base = 0; base < job.max_tries && found == INT_MAX; base += kHypThreads) {
       const int j = base + threadIdx.x;
-      if (j < job.max_tries && try_passes(job, h, j, n_valid)) atomicMin(&s_win, j);
-      __syncthreads();
-      const bool done = s_win != INT_MAX;
-      __syncthreads();
-      if (done) break;
+      const int st = j < job.max_tries ? try_status(job, h, j, n_valid, rig, area, fx, fy, cx, cy) : 0;
+      int rejected = -1;
+      // settle this block of tries in order: the first try not failing is accepted unless it is
+      // in the guard band and the FP64 test rejects it, in which case the next one is considered
+      while (true) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_win = INT_MAX;
+        __syncthreads();
+        if (st != 0 && j > rejected) atomicMin(&s_win, j);
+        __syncthreads();
+        const int w = s_win;
+        if (w == INT_MAX) break;
+        if (j == w) s_res = (st == 1) ? 1 : (exact_geometry(job, h, j, n_valid) ? 1 : 0);
+        __syncthreads();
+        if (s_res) {
+          found = w;
+          break;
+        }
+        rejected = w;
+      }
     }
   }
   if (threadIdx.x == 0) {
-    const int win = s_win;
-    double* pose = job.poses + 12 * (size_t)h;
-    const bool ok = win != INT_MAX;
-    if (ok) {
-      // FP64 Kabsch (Horn) on the winning try's three correspondences
-      const TryDraw t = draw_try(job, h, win, n_valid);
-      const int L = 1 << job.forest.D;
-      double c[3][3], w[3][3], cb[3] = {0, 0, 0}, wb[3] = {0, 0, 0};
-      for (int k = 0; k < 3; ++k) {
-        cam_point_d(t.pix[k], job.W, job.depth[t.pix[k]], job.fx, job.fy, job.cx, job.cy, c[k]);
-        const float4 m = job.forest.top[(size_t)t.tree[k] * L + t.leaf[k]];
-        w[k][0] = m.x;
-        w[k][1] = m.y;
-        w[k][2] = m.z;
-        for (int a = 0; a < 3; ++a) {
-          cb[a] += c[k][a] / 3.0;
-          wb[a] += w[k][a] / 3.0;
-        }
-      }
-      double S[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-      for (int k = 0; k < 3; ++k)
-        for (int a = 0; a < 3; ++a)
-          for (int b = 0; b < 3; ++b) S[3 * a + b] += (c[k][a] - cb[a]) * (w[k][b] - wb[b]);
-      horn_pose(S, cb, wb, pose);
-    } else {
-      for (int q = 0; q < 12; ++q) pose[q] = (q % 5 == 0) ? 1.0 : 0.0;
-    }
-    job.hyp_ok[h] = ok ? 1 : 0;
-    job.tries[h] = ok ? win : job.max_tries;
-    job.energy[h] = ok ? 0.0 : (double)INFINITY;
-    job.alive_a[h] = h;
-    job.inliers[h] = 0;
+    job.hyp_ok[h] = found != INT_MAX;
+    job.tries[h] = found != INT_MAX ? found : job.max_tries;
   }
+}
+
+// FP64 Kabsch (Horn) of each hypothesis's kept try; also initialises the round state.
+__global__ void __launch_bounds__(128) fit_kernel(const RansacJob* __restrict__ jobs, int n_jobs, int total) {
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= total) return;
+  int lo = 0, hi = n_jobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].hyp_begin <= gid) lo = mid;
+    else hi = mid - 1;
+  }
+  const RansacJob& job = jobs[lo];
+  const int h = gid - job.hyp_begin;
+  if (h >= job.K) return;
+  double* pose = job.poses + 12 * (size_t)h;
+  const bool ok = job.hyp_ok[h] != 0;
+  if (ok) {
+    const Corr c = draw_try(job, h, job.tries[h], *job.n_valid);
+    const int L = 1 << job.forest.D;
+    double cp[3][3], wp[3][3], cb[3] = {0, 0, 0}, wb[3] = {0, 0, 0};
+    for (int k = 0; k < 3; ++k) {
+      cam_point_d(c.e[k].u, c.e[k].v, c.e[k].depth, job.fx, job.fy, job.cx, job.cy, cp[k]);
+      const float4 m = job.forest.top[(size_t)c.tree[k] * L + c.leaf[k]];
+      wp[k][0] = m.x;
+      wp[k][1] = m.y;
+      wp[k][2] = m.z;
+      for (int a = 0; a < 3; ++a) {
+        cb[a] += cp[k][a] / 3.0;
+        wb[a] += wp[k][a] / 3.0;
+      }
+    }
+    double S[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < 3; ++k)
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) S[3 * a + b] += (cp[k][a] - cb[a]) * (wp[k][b] - wb[b]);
+    horn_pose(S, cb, wb, pose);
+  } else {
+    for (int q = 0; q < 12; ++q) pose[q] = (q % 5 == 0) ? 1.0 : 0.0;
+  }
+  job.energy[h] = ok ? 0.0 : (double)INFINITY;
+  job.alive_a[h] = h;
+  job.inliers[h] = 0;
 }
 
 cudaError_t launch_hypotheses(const RansacJob* jobs, int n_jobs, int total_hyps, cudaStream_t s) {
   if (total_hyps <= 0) return cudaSuccess;
-  hypotheses_kernel<<<total_hyps, kHypThreads, 0, s>>>(jobs, n_jobs);
+  search_kernel<<<total_hyps, kHypThreads, 0, s>>>(jobs, n_jobs);
+  fit_kernel<<<(total_hyps + 127) / 128, 128, 0, s>>>(jobs, n_jobs, total_hyps);
   return cudaGetLastError();
 }
 
@@ -305,7 +381,7 @@ cudaError_t launch_hypotheses(const RansacJob* jobs, int n_jobs, int total_hyps,
 __device__ __forceinline__ const int32_t* alive_in(const RansacJob& j, int r) { return (r & 1) ? j.alive_b : j.alive_a; }
 __device__ __forceinline__ int32_t* alive_out(const RansacJob& j, int r) { return (r & 1) ? j.alive_a : j.alive_b; }
 
-// Draw round r's B pixels (one CTA per job).
+// Draw round r's B pixels (positions in the valid table), one CTA per job.
 __global__ void draw_kernel(const RansacJob* __restrict__ jobs, const int32_t* __restrict__ alive_prefix, int r) {
   const int jid = blockIdx.x;
   if (alive_prefix[jid + 1] - alive_prefix[jid] == 0) return;
@@ -314,18 +390,19 @@ __global__ void draw_kernel(const RansacJob* __restrict__ jobs, const int32_t* _
   if (n_valid == 0) return;
   for (int i = threadIdx.x; i < job.B; i += blockDim.x) {
     const uint4 x = philox4x32_10(make_uint4(2u, (uint32_t)r, (uint32_t)i, 0u), job.key0, job.key1);
-    job.drawn[(size_t)r * job.B + i] = job.valid[uniform_below(x.x, (uint32_t)n_valid)];
+    job.drawn[(size_t)r * job.B + i] = (int32_t)uniform_below(x.x, (uint32_t)n_valid);
   }
 }
 
-// Best mode of pixel pix under x: returns score (-inf if none) and the mode's mean.
-__device__ __forceinline__ float best_mode(const RansacJob& job, int pix, float3 x, float3* mu_best) {
+// Best mode of a drawn pixel under x: returns its score (-inf if none) and the mode's mean.
+__device__ __forceinline__ float best_mode(const RansacJob& job, int idx, const TableEntry& e, float3 x,
+                                           float3* mu_best) {
   const ForestView& f = job.forest;
-  const int n_pix = job.W * job.H, L = 1 << f.D;
+  const int L = 1 << f.D;
   float best = -INFINITY;
   for (int t = 0; t < f.T; ++t) {
-    const int leaf = __ldg(&job.leaves[(size_t)t * n_pix + pix]);
-    if (leaf >= L) continue;  // invalid pixel (0xFFFF) or a leaf id outside the forest
+    const int leaf = entry_leaf(job, idx, e, t);
+    if (leaf >= L) continue;  // a leaf id outside the forest
     const int nm = min((int)__ldg(&f.n_modes[(size_t)t * L + leaf]), f.M);
     const float4* m = reinterpret_cast<const float4*>(f.modes + ((size_t)t * L + leaf) * f.M * kModeFloats);
     for (int k = 0; k < nm; ++k) {
@@ -344,10 +421,6 @@ __device__ __forceinline__ float best_mode(const RansacJob& job, int pix, float3
   return best;
 }
 
-__device__ __forceinline__ float3 drawn_cam(const RansacJob& job, int pix) {
-  return cam_point_f(pix, job.W, __ldg(&job.depth[pix]), (float)job.fx, (float)job.fy, (float)job.cx, (float)job.cy);
-}
-
 // Energies of round r: warp per alive hypothesis.
 __global__ void __launch_bounds__(256) energy_kernel(const RansacJob* __restrict__ jobs, int n_jobs,
                                                      const int32_t* __restrict__ alive_prefix, int total, int r) {
@@ -359,12 +432,14 @@ __global__ void __launch_bounds__(256) energy_kernel(const RansacJob* __restrict
   const int h = alive_in(job, r)[gw - alive_prefix[jid]];
   if (!job.hyp_ok[h] || *job.n_valid == 0) return;
   const PoseF P = pose_to_float(job.poses + 12 * (size_t)h);
+  const float fx = (float)job.fx, fy = (float)job.fy, cx = (float)job.cx, cy = (float)job.cy;
   float sum = 0.f;
   const int32_t* px = job.drawn + (size_t)r * job.B;
   for (int i = lane; i < job.B; i += 32) {
-    const int pix = __ldg(&px[i]);
-    const float3 x = apply(P, drawn_cam(job, pix));
-    const float best = best_mode(job, pix, x, nullptr);
+    const int idx = __ldg(&px[i]);
+    const TableEntry e = load_entry(job, idx);
+    const float3 x = apply(P, cam_point_f(e.u, e.v, e.depth, fx, fy, cx, cy));
+    const float best = best_mode(job, idx, e, x, nullptr);
     sum += fminf(kLogEps, -best);
   }
   sum = warp_sum(sum);
@@ -424,7 +499,12 @@ __global__ void __launch_bounds__(1024) select_kernel(const RansacJob* __restric
   for (int i = threadIdx.x; i < keep; i += blockDim.x) out[i] = sidx[i];
 }
 
-// Re-fit: warp per survivor over all pixels drawn in rounds 0..r.
+// Re-fit sums: warp per survivor over all pixels drawn in rounds 0..r.  Sums are taken about a
+// reference correspondence (the first drawn pixel and its predicted scene point) so one FP32
+// pass gives well-conditioned centroids and cross-covariance:
+//   refit[h] = {n, sum dc (3), sum dw (3), sum dc dw^T (9), c_ref (3), w_ref (3), 0, 0}.
+constexpr int kRefitFloats = 24;
+
 __global__ void __launch_bounds__(256) refine_kernel(const RansacJob* __restrict__ jobs, int n_jobs,
                                                      const int32_t* __restrict__ surv_prefix, int total, int r) {
   const int gw = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
@@ -435,64 +515,77 @@ __global__ void __launch_bounds__(256) refine_kernel(const RansacJob* __restrict
   const int h = alive_out(job, r)[gw - surv_prefix[jid]];
   if (!job.hyp_ok[h] || *job.n_valid == 0) return;
   const PoseF P = pose_to_float(job.poses + 12 * (size_t)h);
+  const float fx = (float)job.fx, fy = (float)job.fy, cx = (float)job.cx, cy = (float)job.cy;
   const int n_drawn = (r + 1) * job.B;
   const float r2 = (float)(job.inlier_dist * job.inlier_dist);
-  // pass 1: inlier count and centroids
-  int cnt = 0;
-  float sc[3] = {0, 0, 0}, sw[3] = {0, 0, 0};
+  const TableEntry e0 = load_entry(job, __ldg(&job.drawn[0]));
+  const float3 cref = cam_point_f(e0.u, e0.v, e0.depth, fx, fy, cx, cy);
+  const float3 wref = apply(P, cref);
+  float acc[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) acc[q] = 0.f;
   for (int i = lane; i < n_drawn; i += 32) {
-    const int pix = __ldg(&job.drawn[i]);
-    const float3 c = drawn_cam(job, pix);
+    const int idx = __ldg(&job.drawn[i]);
+    const TableEntry e = load_entry(job, idx);
+    const float3 c = cam_point_f(e.u, e.v, e.depth, fx, fy, cx, cy);
     const float3 x = apply(P, c);
     float3 mu;
-    const float best = best_mode(job, pix, x, &mu);
+    const float best = best_mode(job, idx, e, x, &mu);
     if (best == -INFINITY) continue;
     const float dx = x.x - mu.x, dy = x.y - mu.y, dz = x.z - mu.z;
     if (dx * dx + dy * dy + dz * dz < r2) {
-      ++cnt;
-      sc[0] += c.x; sc[1] += c.y; sc[2] += c.z;
-      sw[0] += mu.x; sw[1] += mu.y; sw[2] += mu.z;
-    }
-  }
-  cnt = warp_sum_i(cnt);
+      const float a[3] = {c.x - cref.x, c.y - cref.y, c.z - cref.z};
+      const float b[3] = {mu.x - wref.x, mu.y - wref.y, mu.z - wref.z};
+      acc[0] += 1.f;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    sc[a] = warp_sum(sc[a]);
-    sw[a] = warp_sum(sw[a]);
-  }
-  if (lane == 0) job.inliers[h] = cnt;
-  if (cnt < 3) return;
-  const float inv = 1.0f / (float)cnt;
-  const float cb[3] = {sc[0] * inv, sc[1] * inv, sc[2] * inv}, wb[3] = {sw[0] * inv, sw[1] * inv, sw[2] * inv};
-  // pass 2: cross-covariance about the centroids
-  float S[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-  for (int i = lane; i < n_drawn; i += 32) {
-    const int pix = __ldg(&job.drawn[i]);
-    const float3 c = drawn_cam(job, pix);
-    const float3 x = apply(P, c);
-    float3 mu;
-    const float best = best_mode(job, pix, x, &mu);
-    if (best == -INFINITY) continue;
-    const float dx = x.x - mu.x, dy = x.y - mu.y, dz = x.z - mu.z;
-    if (dx * dx + dy * dy + dz * dz < r2) {
-      const float e[3] = {c.x - cb[0], c.y - cb[1], c.z - cb[2]}, g[3] = {mu.x - wb[0], mu.y - wb[1], mu.z - wb[2]};
+      for (int k = 0; k < 3; ++k) {
+        acc[1 + k] += a[k];
+        acc[4 + k] += b[k];
+      }
 #pragma unroll
-      for (int a = 0; a < 3; ++a)
+      for (int p = 0; p < 3; ++p)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) S[3 * a + b] = fmaf(e[a], g[b], S[3 * a + b]);
+        for (int q = 0; q < 3; ++q) acc[7 + 3 * p + q] = fmaf(a[p], b[q], acc[7 + 3 * p + q]);
     }
   }
 #pragma unroll
-  for (int q = 0; q < 9; ++q) S[q] = warp_sum(S[q]);
-  if (lane == 0) {
-    double Sd[9], cbd[3], wbd[3];
-    for (int q = 0; q < 9; ++q) Sd[q] = S[q];
-    for (int a = 0; a < 3; ++a) {
-      cbd[a] = cb[a];
-      wbd[a] = wb[a];
-    }
-    horn_pose(Sd, cbd, wbd, job.poses + 12 * (size_t)h);
+  for (int q = 0; q < 16; ++q) acc[q] = warp_sum(acc[q]);
+  if (lane < 16) {
+    float v = acc[0];
+#pragma unroll
+    for (int q = 1; q < 16; ++q)
+      if (lane == q) v = acc[q];
+    job.refit[(size_t)h * kRefitFloats + lane] = v;
+  } else if (lane < 22) {
+    const float v = lane == 16 ? cref.x : lane == 17 ? cref.y : lane == 18 ? cref.z
+                  : lane == 19 ? wref.x : lane == 20 ? wref.y : wref.z;
+    job.refit[(size_t)h * kRefitFloats + lane] = v;
   }
+  if (lane == 0) job.inliers[h] = (int)acc[0];
+}
+
+// Re-fit solve: thread per survivor; FP64 Horn on the centroids and cross-covariance.
+__global__ void __launch_bounds__(128) refit_kernel(const RansacJob* __restrict__ jobs, int n_jobs,
+                                                    const int32_t* __restrict__ surv_prefix, int total, int r) {
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= total) return;
+  const int jid = find_job_by(surv_prefix, n_jobs, gid);
+  const RansacJob& job = jobs[jid];
+  const int h = alive_out(job, r)[gid - surv_prefix[jid]];
+  if (!job.hyp_ok[h] || *job.n_valid == 0) return;
+  const float* f = job.refit + (size_t)h * kRefitFloats;
+  const double n = f[0];
+  if (n < 3.0) return;
+  double mc[3], mw[3], cb[3], wb[3], S[9];
+  for (int k = 0; k < 3; ++k) {
+    mc[k] = f[1 + k] / n;
+    mw[k] = f[4 + k] / n;
+    cb[k] = (double)f[16 + k] + mc[k];
+    wb[k] = (double)f[19 + k] + mw[k];
+  }
+  for (int p = 0; p < 3; ++p)
+    for (int q = 0; q < 3; ++q) S[3 * p + q] = (double)f[7 + 3 * p + q] - n * mc[p] * mw[q];
+  horn_pose(S, cb, wb, job.poses + 12 * (size_t)h);
 }
 
 cudaError_t launch_round(const RansacJob* jobs, int n_jobs, int round, const int32_t* alive_prefix_dev,
@@ -501,11 +594,13 @@ cudaError_t launch_round(const RansacJob* jobs, int n_jobs, int round, const int
   draw_kernel<<<n_jobs, 256, 0, s>>>(jobs, alive_prefix_dev, round);
   energy_kernel<<<(unsigned)((total_alive * 32 + 255) / 256), 256, 0, s>>>(jobs, n_jobs, alive_prefix_dev,
                                                                            total_alive, round);
-  // the largest alive set bounds the shared memory of the sort
+  // the largest alive set (4096) bounds the shared memory of the sort
   select_kernel<<<n_jobs, 1024, 4096 * (sizeof(unsigned long long) + sizeof(int)), s>>>(jobs, alive_prefix_dev,
                                                                                         round);
   refine_kernel<<<(unsigned)((total_surv * 32 + 255) / 256), 256, 0, s>>>(jobs, n_jobs, surv_prefix_dev,
                                                                           total_surv, round);
+  refit_kernel<<<(unsigned)((total_surv + 127) / 128), 128, 0, s>>>(jobs, n_jobs, surv_prefix_dev, total_surv,
+                                                                     round);
   return cudaGetLastError();
 }
 
@@ -530,6 +625,9 @@ __global__ void finalise_kernel(const RansacJob* __restrict__ jobs, int n_jobs) 
   res->hypothesis = h;
   res->n_rounds = job.n_rounds;
   res->omega = res->omega_a = res->omega_b = res->omega_ab = res->sum_absdiff_mm = 0;
+  unsigned long long tries = 0;
+  for (int q = 0; q < job.K; ++q) tries += job.hyp_ok[q] ? (unsigned long long)job.tries[q] + 1 : job.max_tries;
+  res->tries = tries;
   for (int q = 0; q < 16; ++q) res->rel_a_b[q] = (q % 5 == 0) ? 1.0 : 0.0;
   if (job.has_pose_b) {
     // a_T_b = P_a P_b^-1 with P_b^-1 = [R_b^T | -R_b^T t_b]

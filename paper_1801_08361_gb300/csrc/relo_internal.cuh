@@ -248,7 +248,9 @@ struct RansacJob {
   double rigidity, min_area, inlier_dist;
   uint32_t key0, key1;
   // workspace
-  int32_t* valid;              // [W*H] valid pixel indices (raster order)
+  uint4* table;                // [W*H][nv] valid pixels in raster order, packed u16 {u, v, depth, leaf[T]}
+  int32_t nv;                  // uint4 words per table entry: ceil((3 + T) / 8)
+  int32_t pad1;
   int32_t* chunk_count;        // [n_chunks]
   int32_t* n_valid;            // [1]
   double* poses;               // [K][12]
@@ -257,9 +259,9 @@ struct RansacJob {
   double* energy;              // [K]
   int32_t* alive_a;            // [K]
   int32_t* alive_b;            // [K]
-  int32_t* drawn;              // [n_rounds * B]
-  float4* drawn_cam;           // [n_rounds * B]
+  int32_t* drawn;              // [n_rounds * B] positions in the valid-pixel table
   int32_t* inliers;            // [K]
+  float* refit;                // [K][16] per-survivor sums for the FP64 re-fit
   int32_t* err;                // [1]
   relo_pose_result* result;    // device
   int32_t chunk_begin;         // flattened compaction chunks
@@ -299,6 +301,7 @@ cudaError_t launch_scene_lookup(SceneView sv, const int32_t* keys, int64_t n, in
                                 cudaStream_t s);
 
 // RANSAC stages over a device array of jobs.
+inline int table_words(int T) { return (3 + T + 7) / 8; }
 cudaError_t launch_compact(const RansacJob* jobs, int n_jobs, int total_chunks, cudaStream_t s);
 cudaError_t launch_hypotheses(const RansacJob* jobs, int n_jobs, int total_hyps, cudaStream_t s);
 // round r: prefix[n_jobs + 1] = flattened alive-hypothesis offsets of the jobs still running

@@ -196,6 +196,7 @@ def test_rounds_teacher_forced(room_forest, gpu_forest, room_query):
     poses_prev = tr.poses0[:, :3, :].copy()
     E_prev = np.where(tr.valid0, 0.0, np.inf)
     drawn_prev = np.zeros(0, np.int64)
+    vpix = oracle.valid_pixels(d)          # the GPU draws positions in this raster-order list
     strict_rounds = 0
     for r, rd in enumerate(tr.rounds):
         alive = rd["alive_before"]
@@ -204,7 +205,7 @@ def test_rounds_teacher_forced(room_forest, gpu_forest, room_query):
         poses = torch.from_numpy(poses_prev.reshape(K, 12).copy()).to(DEV)
         energy = torch.from_numpy(E_prev.copy()).to(DEV)
         drawn = torch.zeros((r + 1) * Bn, dtype=torch.int32, device=DEV)
-        drawn[: r * Bn] = torch.from_numpy(drawn_prev.astype(np.int32)).to(DEV)
+        drawn[: r * Bn] = torch.from_numpy(np.searchsorted(vpix, drawn_prev).astype(np.int32)).to(DEV)
         surv = torch.zeros(keep, dtype=torch.int32, device=DEV)
         inl = torch.zeros(K, dtype=torch.int32, device=DEV)
         if r > 0:
@@ -213,7 +214,7 @@ def test_rounds_teacher_forced(room_forest, gpu_forest, room_query):
                        poses, energy, drawn, surv, inl, ws)
         torch.cuda.synchronize()
         # draws are integer-exact
-        assert np.array_equal(drawn.cpu().numpy()[r * Bn:], rd["pixels"])
+        assert np.array_equal(vpix[drawn.cpu().numpy()[r * Bn:]], rd["pixels"])
         # energies of the alive hypotheses
         Eg, Eo = energy.cpu().numpy(), rd["energy"]
         fin = np.isfinite(Eo[alive])
@@ -355,7 +356,7 @@ def test_batch_prepared_replay_is_deterministic(room, gpu_room, gpu_forest, room
     bt.run(out2)
     torch.cuda.synchronize()
     assert torch.equal(out1, out2)
-    assert bt.launch_count == 2 + 2 + 1 + 4 * 5 + 1 + 2
+    assert bt.launch_count == 2 + 2 + 2 + 5 * 5 + 1 + 2
 
 
 # ------------------------------------------------------------------------------------------------
