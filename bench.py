@@ -50,8 +50,8 @@ L2_FLUSH_BYTES = 512 << 20
 # entries (16 B) touched, averaged over 8 query views of this workload
 # (oracle/algorithmic_bytes.py).
 ALG_BYTES_PER_PIXEL = {
-    "query_raycast": None,
-    "verify_raycast": None,
+    "query_raycast": 50.66,
+    "verify_raycast": 35.87,
 }
 
 

@@ -82,6 +82,14 @@ void relo_destroy_scene(relo_scene* scene);
 relo_status relo_scene_lookup(const relo_scene* scene, const int32_t* keys_dev, int64_t n, int64_t* out_dev,
                               relo_stream stream);
 
+/* Raycast acceleration (no counterpart in the paper; results are unchanged).  When the blocks'
+ * bounding box holds at most 2^28 block coordinates, creation also builds a dense block-index
+ * grid over it (4 bytes per coordinate) and one occupancy byte per 8 x 8 x 8 blocks; the raycast
+ * then reads block indices from the grid instead of walking the hash, and crosses empty 8^3-block
+ * cells in one step.  relo_scene_use_grid(scene, 0) makes later raycasts use the hash alone, 1
+ * restores the grid (if one was built).  Errors: RELO_EINVAL (null scene). */
+relo_status relo_scene_use_grid(relo_scene* scene, int32_t enable);
+
 /* ---------------------------------------------------------------------------------------
  * Synthetic raycast (Sec. 3.3.1, Fig. 3: the query is a colour + depth render of scene b from
  * the frame's pose; the appendix on global map rendering names the usual voxel raycast).

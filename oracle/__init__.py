@@ -63,6 +63,9 @@ def _lib():
         lib.orc_scene_find_many.argtypes = [vp, vp, ctypes.c_long, vp]
         lib.orc_raycast.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, dp, vp, vp,
                                     ctypes.c_long, vp, vp]
+        lib.orc_raycast_touched.restype = ctypes.c_int
+        lib.orc_raycast_touched.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, dp,
+                                            ctypes.c_int, vp]
         lib.orc_forest_eval.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, vp]
         lib.orc_verify_counts.argtypes = [vp, vp, ctypes.c_long, vp]
         lib.orc_reservoirs_create.restype = vp
@@ -165,6 +168,19 @@ class Scene:
         _lib().orc_raycast(self._h, W, H, _d(K), intr.depth_min, intr.depth_max, _d(P),
                            nz.ctypes.data if nz is not None else None, pp, n, depth.ctypes.data, rgba.ctypes.data)
         return depth, rgba
+
+
+def raycast_touched(scene: Scene, intr, pose, with_colour: bool) -> dict:
+    """Distinct data one view's raycast reads: tsdf voxels, colour voxels (query renders only)
+    and block keys looked up -- the algorithmic input bytes of that raycast."""
+    K = np.array([intr.fx, intr.fy, intr.cx, intr.cy], dtype=np.float64)
+    out = np.zeros(3, dtype=np.int64)
+    rc = _lib().orc_raycast_touched(scene._h, intr.width, intr.height, _d(K), intr.depth_min, intr.depth_max,
+                                    _d(np.asarray(pose, dtype=np.float64).reshape(16)), int(with_colour),
+                                    out.ctypes.data)
+    if rc != 0:
+        raise MemoryError("raycast_touched")
+    return dict(tsdf_voxels=int(out[0]), colour_voxels=int(out[1]), block_keys=int(out[2]))
 
 
 def forest_eval(nodes, depth_img, rgba_img) -> np.ndarray:

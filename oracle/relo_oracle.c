@@ -106,7 +106,30 @@ void orc_scene_destroy(orc_scene* s) {
 
 /* Index of block (bx,by,bz) in the input block list, or -1 if it is not allocated.
  * Duplicate block coordinates resolve to the lowest input index. */
+/* Optional recorder of the distinct data a raycast touches (for the algorithmic-bytes count of
+ * the roofline): block keys looked up, and tsdf / colour voxels read.  NULL when not counting. */
+typedef struct {
+  uint8_t* tsdf_seen;   /* [n_blocks * 512] */
+  uint8_t* rgba_seen;   /* [n_blocks * 512] */
+  int64_t* keys;        /* open-addressing set of packed block keys, capacity 2^key_bits, 0 = empty */
+  int key_bits;
+  int64_t n_keys;
+} orc_touch;
+static orc_touch* g_touch = NULL;
+
+static void touch_key(int bx, int by, int bz) {
+  const int64_t k = 1 + (((int64_t)(bx + 32768) << 34) | ((int64_t)(by + 32768) << 17) | (int64_t)(bz + 32768));
+  const uint64_t mask = ((uint64_t)1 << g_touch->key_bits) - 1;
+  uint64_t h = ((uint64_t)k * 0x9E3779B97F4A7C15ull) >> (64 - g_touch->key_bits);
+  while (g_touch->keys[h] != 0 && g_touch->keys[h] != k) h = (h + 1) & mask;
+  if (g_touch->keys[h] == 0) {
+    g_touch->keys[h] = k;
+    g_touch->n_keys++;
+  }
+}
+
 long orc_scene_find_block(const orc_scene* s, int bx, int by, int bz) {
+  if (g_touch) touch_key(bx, by, bz);
   long lo = 0, hi = s->n_blocks; /* first element >= key */
   while (lo < hi) {
     long mid = lo + (hi - lo) / 2;
@@ -134,6 +157,10 @@ static int voxel_at(const orc_scene* s, long i, long j, long k, double* tsdf, do
     return 0;
   }
   long li = (i - 8 * bx) + 8 * (j - 8 * by) + 64 * (k - 8 * bz);
+  if (g_touch) {
+    g_touch->tsdf_seen[b * 512 + li] = 1;
+    if (rgb) g_touch->rgba_seen[b * 512 + li] = 1;
+  }
   *tsdf = (double)s->tsdf[b * 512 + li];
   if (rgb)
     for (int c = 0; c < 3; ++c) rgb[c] = (double)s->rgba[(b * 512 + li) * 4 + c];
@@ -173,9 +200,10 @@ static double round_half_up(double x) { return floor(x + 0.5); }
  * Reading of the march:
  *   the ray is p(lam) = C + lam * R * ((u-cx)/fx, (v-cy)/fy, 1), lam = camera z;
  *   start at lam = depth_min; at each sample, if the containing block is
- *   unallocated the sample counts as f = +1 and the next sample is just past the
- *   block's exit (1e-5 in lam), otherwise f = trilinear tsdf and, while f > 0, the
- *   next sample is max(f * mu, voxel) / |d| further;
+ *   unallocated the march moves to the block's exit lam_exit, which becomes the
+ *   previous sample with f = +1 (free space up to there), and the next sample is
+ *   1e-5 past it; otherwise f = trilinear tsdf and, while f > 0, the next sample is
+ *   max(f * mu, voxel) / |d| further;
  *   the first sample with f <= 0 ends the march: if it is the very first sample
  *   the pixel is invalid, else the surface is the secant root between the last
  *   two samples;
@@ -215,10 +243,10 @@ static int raycast_pixel(const orc_scene* s, const double K[4], double dmin, dou
           if (l < lam_exit) lam_exit = l;
         }
       }
-      lam_prev = lam;
+      lam_prev = lam_exit > lam ? lam_exit : lam;
       f_prev = 1.0;
       have_prev = 1;
-      lam = (lam_exit > lam ? lam_exit : lam) + 1e-5;
+      lam = lam_prev + 1e-5;
       continue;
     }
     double f = trilinear(s, p, NULL);
@@ -271,6 +299,37 @@ void orc_raycast(const orc_scene* s, int W, int H, const double K[4], double dmi
     int u = (int)(pix % W), v = (int)(pix / W);
     raycast_pixel(s, K, dmin, dmax, P, u, v, noise ? noise + pix : NULL, depth + k, rgba ? rgba + 4 * k : NULL);
   }
+}
+
+/* Distinct data one view's raycast touches: out = {tsdf voxels, colour voxels, block keys
+ * looked up}.  Colour is counted only when with_colour (the query render; verification renders
+ * need depth only).  Returns 0, or -1 if scratch allocation fails. */
+int orc_raycast_touched(const orc_scene* s, int W, int H, const double K[4], double dmin, double dmax,
+                        const double P[16], int with_colour, int64_t out[3]) {
+  orc_touch t;
+  t.key_bits = 24;
+  t.tsdf_seen = (uint8_t*)calloc((size_t)(s->n_blocks > 0 ? s->n_blocks : 1) * 512, 1);
+  t.rgba_seen = (uint8_t*)calloc((size_t)(s->n_blocks > 0 ? s->n_blocks : 1) * 512, 1);
+  t.keys = (int64_t*)calloc((size_t)1 << t.key_bits, sizeof(int64_t));
+  t.n_keys = 0;
+  if (!t.tsdf_seen || !t.rgba_seen || !t.keys) {
+    free(t.tsdf_seen); free(t.rgba_seen); free(t.keys);
+    return -1;
+  }
+  uint16_t* depth = (uint16_t*)malloc(sizeof(uint16_t) * (size_t)W * H);
+  uint8_t* rgba = with_colour ? (uint8_t*)malloc((size_t)W * H * 4) : NULL;
+  g_touch = &t;
+  for (long k = 0; k < (long)W * H; ++k)
+    raycast_pixel(s, K, dmin, dmax, P, (int)(k % W), (int)(k / W), NULL, depth + k, rgba ? rgba + 4 * k : NULL);
+  g_touch = NULL;
+  int64_t nt = 0, nc = 0;
+  for (long i = 0; i < s->n_blocks * 512; ++i) {
+    nt += t.tsdf_seen[i];
+    nc += t.rgba_seen[i];
+  }
+  out[0] = nt; out[1] = nc; out[2] = t.n_keys;
+  free(depth); free(rgba); free(t.tsdf_seen); free(t.rgba_seen); free(t.keys);
+  return 0;
 }
 
 /* ------------------------------------------------------------------------------------------ */

@@ -69,6 +69,7 @@ _SIGS = {
     "relo_create_scene": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_dbl, c_dbl, c_i32, ctypes.POINTER(c_vp)]),
     "relo_destroy_scene": (None, [c_vp]),
     "relo_scene_lookup": (c_i32, [c_vp, c_vp, c_i64, c_vp, c_vp]),
+    "relo_scene_use_grid": (c_i32, [c_vp, c_i32]),
     "relo_raycast_view": (c_i32, [c_vp, ctypes.POINTER(Intrinsics), ctypes.POINTER(c_dbl), c_vp, c_vp, c_vp, c_vp]),
     "relo_create_forest": (c_i32, [c_vp, c_i32, c_i32, c_vp, c_vp, c_i32, ctypes.POINTER(c_vp)]),
     "relo_destroy_forest": (None, [c_vp]),
@@ -176,6 +177,9 @@ class Scene:
                                        float(blocks.mu), int(log2_buckets), ctypes.byref(h)))
         self._keep = None
         self.handle = h.value
+
+    def use_grid(self, enable: bool):
+        _check(lib().relo_scene_use_grid(self.handle, 1 if enable else 0))
 
     def __del__(self):
         if getattr(self, "handle", None) and _LIB is not None:

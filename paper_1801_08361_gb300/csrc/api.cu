@@ -358,6 +358,35 @@ relo_status relo_create_scene(const int32_t* coords, const float* tsdf, const ui
     max_chain = std::max(max_chain, chain[h]);
   }
   if (excess.empty()) excess.push_back(pack_entry(0, 0, 0, -1, -1));
+  // Dense block-index grid and 8^3-block macro occupancy over the bounding box (origin and
+  // extent on multiples of 8 blocks); skipped when the box exceeds 2^28 blocks.
+  std::vector<int32_t> grid;
+  std::vector<uint8_t> macro;
+  int g0[3] = {0, 0, 0}, gd[3] = {0, 0, 0};
+  if (n > 0) {
+    int lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+    for (int64_t b = 0; b < n; ++b)
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = std::min(lo[a], (int)coords[3 * b + a]);
+        hi[a] = std::max(hi[a], (int)coords[3 * b + a]);
+      }
+    size_t cells = 1;
+    for (int a = 0; a < 3; ++a) {
+      g0[a] = (int)std::floor(lo[a] / 8.0) * 8;
+      gd[a] = ((hi[a] - g0[a]) / 8 + 1) * 8;
+      cells *= (size_t)gd[a];
+    }
+    if (cells <= ((size_t)1 << 28)) {
+      grid.assign(cells, -1);
+      macro.assign(cells / 512, 0);
+      for (int64_t b = 0; b < n; ++b) {
+        const int x = coords[3 * b] - g0[0], y = coords[3 * b + 1] - g0[1], z = coords[3 * b + 2] - g0[2];
+        int32_t& cell = grid[((size_t)z * gd[1] + y) * gd[0] + x];
+        if (cell < 0) cell = (int32_t)b;  // a repeated coordinate keeps its first block, as in the hash
+        macro[((size_t)(z >> 3) * (gd[1] >> 3) + (y >> 3)) * (gd[0] >> 3) + (x >> 3)] = 1;
+      }
+    }
+  }
   relo_scene* s = new relo_scene();
   s->n_blocks = n;
   auto cleanup = [&]() {
@@ -365,8 +394,18 @@ relo_status relo_create_scene(const int32_t* coords, const float* tsdf, const ui
     cudaFree(s->d_excess);
     cudaFree(s->d_tsdf);
     cudaFree(s->d_rgba);
+    cudaFree(s->d_grid);
+    cudaFree(s->d_macro);
     delete s;
   };
+  if (!grid.empty() &&
+      (cudaMalloc(&s->d_grid, grid.size() * 4) != cudaSuccess || cudaMalloc(&s->d_macro, macro.size()) != cudaSuccess ||
+       cudaMemcpy(s->d_grid, grid.data(), grid.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+       cudaMemcpy(s->d_macro, macro.data(), macro.size(), cudaMemcpyHostToDevice) != cudaSuccess)) {
+    cudaGetLastError();
+    cleanup();
+    return fail(RELO_ENOMEM, "device allocation for the scene grid failed");
+  }
   const size_t nv = (size_t)std::max<int64_t>(n, 1) * kVoxelsPerBlock;
   if (cudaMalloc(&s->d_buckets, nb * sizeof(int4)) != cudaSuccess ||
       cudaMalloc(&s->d_excess, excess.size() * sizeof(int4)) != cudaSuccess ||
@@ -398,6 +437,14 @@ relo_status relo_create_scene(const int32_t* coords, const float* tsdf, const ui
   v.mu = (float)mu;
   v.block_size = (float)(8.0 * voxel);
   v.inv_block = (float)(1.0 / (8.0 * voxel));
+  v.grid = (const int32_t*)s->d_grid;
+  v.macro = (const uint8_t*)s->d_macro;
+  v.ox = g0[0];
+  v.oy = g0[1];
+  v.oz = g0[2];
+  v.gx = gd[0];
+  v.gy = gd[1];
+  v.gz = gd[2];
   *out = s;
   return RELO_OK;
 }
@@ -408,7 +455,16 @@ void relo_destroy_scene(relo_scene* s) {
   cudaFree(s->d_excess);
   cudaFree(s->d_tsdf);
   cudaFree(s->d_rgba);
+  cudaFree(s->d_grid);
+  cudaFree(s->d_macro);
   delete s;
+}
+
+relo_status relo_scene_use_grid(relo_scene* s, int32_t enable) {
+  if (!s) return fail(RELO_EINVAL, "scene is null");
+  s->view.grid = enable ? (const int32_t*)s->d_grid : nullptr;
+  s->view.macro = enable ? (const uint8_t*)s->d_macro : nullptr;
+  return RELO_OK;
 }
 
 relo_status relo_scene_lookup(const relo_scene* scene, const int32_t* keys, int64_t n, int64_t* out,

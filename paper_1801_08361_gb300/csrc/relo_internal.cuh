@@ -31,7 +31,29 @@ struct SceneView {
   int32_t n_blocks;
   int32_t max_chain;      // longest chain at build time (bounds the walk)
   float voxel, inv_voxel, mu, block_size, inv_block;
+  // Dense acceleration grids over the blocks' bounding box (null when the box is too large):
+  // grid holds the block index of every block coordinate in the box (-1 = unallocated) and
+  // macro one byte per 8 x 8 x 8 blocks (1 = some block inside is allocated).  Origins are
+  // multiples of 8 blocks so macro cells sit on the absolute lattice floor(block / 8).
+  const int32_t* grid;
+  const uint8_t* macro;
+  int32_t ox, oy, oz;     // grid origin (block coordinates)
+  int32_t gx, gy, gz;     // grid extent in blocks (multiples of 8)
 };
+
+// Block index through the dense grid (caller checks s.grid != nullptr).
+__device__ __forceinline__ int grid_block(const SceneView& s, int x, int y, int z) {
+  const unsigned a = (unsigned)(x - s.ox), b = (unsigned)(y - s.oy), c = (unsigned)(z - s.oz);
+  if (a >= (unsigned)s.gx || b >= (unsigned)s.gy || c >= (unsigned)s.gz) return -1;
+  return __ldg(&s.grid[((size_t)c * s.gy + b) * s.gx + a]);
+}
+
+// True if the 8 x 8 x 8-block macro cell holding block (x, y, z) has no allocated block.
+__device__ __forceinline__ bool macro_empty(const SceneView& s, int x, int y, int z) {
+  const unsigned a = (unsigned)(x - s.ox), b = (unsigned)(y - s.oy), c = (unsigned)(z - s.oz);
+  if (a >= (unsigned)s.gx || b >= (unsigned)s.gy || c >= (unsigned)s.gz) return true;
+  return __ldg(&s.macro[((size_t)(c >> 3) * (s.gy >> 3) + (b >> 3)) * (s.gx >> 3) + (a >> 3)]) == 0;
+}
 
 __host__ __device__ inline uint32_t block_hash(int x, int y, int z) {
   return ((uint32_t)x * 73856093u) ^ ((uint32_t)y * 19349669u) ^ ((uint32_t)z * 83492791u);
@@ -332,6 +354,8 @@ struct relo_scene {
   void* d_excess;
   void* d_tsdf;
   void* d_rgba;
+  void* d_grid;
+  void* d_macro;
   int64_t n_blocks;
 };
 

@@ -28,9 +28,22 @@ __device__ __forceinline__ int cached_block(const SceneView& s, BlockCache& c, i
     c.bx = bx;
     c.by = by;
     c.bz = bz;
-    c.ptr = lookup_block(s, bx, by, bz, err);
+    c.ptr = s.grid ? grid_block(s, bx, by, bz) : lookup_block(s, bx, by, bz, err);
   }
   return c.ptr;
+}
+
+// Parameter of the ray's exit from the axis-aligned cell [lo, lo + size)^3 (per-axis lo).
+__device__ __forceinline__ float cell_exit(float3 C, float3 d, float lox, float loy, float loz, float hix, float hiy,
+                                           float hiz) {
+  float lx = INFINITY, ly = INFINITY, lz = INFINITY;
+  if (d.x > 0.f) lx = (hix - C.x) / d.x;
+  else if (d.x < 0.f) lx = (lox - C.x) / d.x;
+  if (d.y > 0.f) ly = (hiy - C.y) / d.y;
+  else if (d.y < 0.f) ly = (loy - C.y) / d.y;
+  if (d.z > 0.f) lz = (hiz - C.z) / d.z;
+  else if (d.z < 0.f) lz = (loz - C.z) / d.z;
+  return fminf(lx, fminf(ly, lz));
 }
 
 // Value of voxel (i, j, k): tsdf, or +1 when its block is unallocated.
@@ -109,19 +122,24 @@ __device__ float march_ray(const SceneView& s, float3 C, float3 d, float dmin, f
     const int bx = i >> 3, by = j >> 3, bz = k >> 3;
     const int b = cached_block(s, c, bx, by, bz, err);
     if (b < 0) {
-      // free space: jump just past this block's exit along the ray
-      float lx = INFINITY, ly = INFINITY, lz = INFINITY;
-      if (d.x > 0.f) lx = ((float)(bx + 1) * s.block_size - C.x) / d.x;
-      else if (d.x < 0.f) lx = ((float)bx * s.block_size - C.x) / d.x;
-      if (d.y > 0.f) ly = ((float)(by + 1) * s.block_size - C.y) / d.y;
-      else if (d.y < 0.f) ly = ((float)by * s.block_size - C.y) / d.y;
-      if (d.z > 0.f) lz = ((float)(bz + 1) * s.block_size - C.z) / d.z;
-      else if (d.z < 0.f) lz = ((float)bz * s.block_size - C.z) / d.z;
-      const float lexit = fminf(lx, fminf(ly, lz));
-      lam_prev = lam;
+      // free space up to the exit of this block -- or, when the 8^3-block macro cell around it
+      // is empty, of that cell: stepping block by block through an empty cell ends on the same
+      // exit plane, so the skip changes no sample the march evaluates
+      float lexit;
+      if (s.grid && macro_empty(s, bx, by, bz)) {
+        const int mx = bx >> 3, my = by >> 3, mz = bz >> 3;
+        const float ms = 8.0f * s.block_size;
+        lexit = cell_exit(C, d, (float)mx * ms, (float)my * ms, (float)mz * ms, (float)(mx + 1) * ms,
+                          (float)(my + 1) * ms, (float)(mz + 1) * ms);
+      } else {
+        lexit = cell_exit(C, d, (float)bx * s.block_size, (float)by * s.block_size, (float)bz * s.block_size,
+                          (float)(bx + 1) * s.block_size, (float)(by + 1) * s.block_size,
+                          (float)(bz + 1) * s.block_size);
+      }
+      lam_prev = fmaxf(lexit, lam);
       f_prev = 1.0f;
       have_prev = true;
-      lam = fmaxf(lexit, lam) + 1e-5f;
+      lam = lam_prev + 1e-5f;
       continue;
     }
     const float f = trilinear_tsdf(s, c, b, i, j, k, qx - flx, qy - fly, qz - flz, err);

@@ -67,11 +67,22 @@ def test_lookup_bit_exact(room, oracle_room, gpu_room):
 # ------------------------------------------------------------------------------------------------
 @pytest.mark.parametrize("size", [(320, 240), (100, 75), (17, 9), (1, 1)])
 @pytest.mark.parametrize("noisy", [False, True])
-def test_raycast_parity(room, oracle_room, gpu_room, size, noisy):
+@pytest.mark.parametrize("grid", [True, False])
+def test_raycast_parity(room, oracle_room, gpu_room, size, noisy, grid):
+    """Both lookup paths of the raycast (dense grid with empty-cell skipping, hash walk)."""
     world, _ = room
     W, H = size
     intr = synth.Intrinsics.for_size(W, H)
     poses = synth.training_poses(world, 3, seed=21)
+    gpu_room.use_grid(grid)
+    try:
+        _raycast_parity_poses(oracle_room, gpu_room, intr, poses, noisy)
+    finally:
+        gpu_room.use_grid(True)
+
+
+def _raycast_parity_poses(oracle_room, gpu_room, intr, poses, noisy):
+    W, H = intr.width, intr.height
     for i, P in enumerate(poses):
         noise = synth.depth_noise(H, W, 50 + i) if noisy else None
         dg, cg = gpu_render(gpu_room, intr, P, noise)
