@@ -150,7 +150,7 @@ struct relo_batch {
   int32_t* d_surv_prefix = nullptr;
   relo_pose_result* d_results = nullptr;
   std::vector<int> tot_alive, tot_surv;
-  int query_tiles = 0, verify_tiles = 0, chunks = 0, hyps = 0;
+  int query_tiles = 0, verify_tiles = 0, chunks = 0, hyps = 0, max_trees = 1;
   int64_t pixels = 0;
   int32_t* d_errs = nullptr;
   int launches = 0;
@@ -258,6 +258,8 @@ relo_status layout_batch(const relo_attempt* at, int n, const relo_ransac_params
     plan->d_surv_prefix = d_surv;
     plan->d_results = d_results;
     plan->query_tiles = plan->verify_tiles = tiles;
+    plan->max_trees = 1;
+    for (int i = 0; i < n; ++i) plan->max_trees = std::max(plan->max_trees, at[i].forest_a->T);
     plan->pixels = pixels;
     plan->chunks = chunks;
     plan->hyps = hyps;
@@ -570,7 +572,7 @@ relo_status relo_forest_eval(const relo_forest* f, const uint16_t* depth, const 
   j.W = W;
   j.H = H;
   j.pixel_begin = 0;
-  RELO_CUDA(launch_forest(nullptr, 1, &j, (int64_t)W * H, (cudaStream_t)stream));
+  RELO_CUDA(launch_forest(nullptr, 1, &j, (int64_t)W * H, (cudaStream_t)stream, f->T));
   return RELO_OK;
 }
 
@@ -620,7 +622,7 @@ relo_status relo_forest_train_frame(relo_forest* f, const relo_intrinsics* intr,
   j.H = H;
   std::vector<uint16_t> leaves(n_pix * T), dep(n_pix);
   std::vector<float> coords((size_t)gw * gh * 3);
-  cudaError_t e = launch_forest(nullptr, 1, &j, (int64_t)n_pix, s);
+  cudaError_t e = launch_forest(nullptr, 1, &j, (int64_t)n_pix, s, T);
   if (e == cudaSuccess) e = launch_scene_coords(depth, W, H, S, intr->fx, intr->fy, intr->cx, intr->cy, pose, d_coords, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(leaves.data(), d_leaves, leaves.size() * 2, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dep.data(), depth, n_pix * 2, cudaMemcpyDeviceToHost, s);
@@ -904,7 +906,7 @@ relo_status relo_batch_run(relo_batch* b, relo_pose_result* results, relo_stream
   RELO_CUDA(mark(b, 0, s));
   RELO_CUDA(launch_raycast(b->d_query, b->n, nullptr, b->query_tiles, true, false, s));
   RELO_CUDA(mark(b, 1, s));
-  RELO_CUDA(launch_forest(b->d_forest, b->n, nullptr, b->pixels, s));
+  RELO_CUDA(launch_forest(b->d_forest, b->n, nullptr, b->pixels, s, b->max_trees));
   RELO_CUDA(mark(b, 2, s));
   L += 2;
   int Lr = 0;

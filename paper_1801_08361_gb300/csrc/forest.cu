@@ -12,11 +12,34 @@
 namespace relo {
 
 // Offsets are pixel-metres: probe = x + trunc(delta * 1000 / d), integer division toward zero.
-__device__ __forceinline__ int probe(int x, int delta, int d, int limit) {
-  const int q = x + (delta * 1000) / d;
-  return min(max(q, 0), limit);
+// The division by the pixel's depth d uses one multiply-shift per probe: for 0 <= a < 2^25 and
+// 1 <= d < 2^16, floor(a / d) = (a * M) >> (25 + l) with l = ceil(log2 d) and
+// M = floor(2^(25+l) / d) + 1 (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994, round-up method); |delta| * 1000 <= 32768000 < 2^25.
+struct DepthDivisor {
+  unsigned long long M;
+  int shift;
+};
+
+__device__ __forceinline__ DepthDivisor make_divisor(int d) {
+  const int l = d > 1 ? 32 - __clz(d - 1) : 0;
+  DepthDivisor q;
+  q.shift = 25 + l;
+  q.M = (1ull << q.shift) / (unsigned long long)d + 1ull;
+  return q;
 }
 
+__device__ __forceinline__ int probe(int x, int delta, const DepthDivisor& dv, int limit) {
+  const int n = delta * 1000;
+  const unsigned a = (unsigned)(n < 0 ? -n : n);
+  const int q = (int)(((unsigned long long)a * dv.M) >> dv.shift);
+  const int p = x + (n < 0 ? -q : q);
+  return min(max(p, 0), limit);
+}
+
+// One thread per pixel; the trees' descents are interleaved level by level so each level issues
+// T independent node loads instead of a chain of T * D dependent ones.
+template <int MT>
 __global__ void __launch_bounds__(256)
     forest_kernel(const ForestJob* __restrict__ jobs, int n_jobs, const ForestJob single) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -33,42 +56,53 @@ __global__ void __launch_bounds__(256)
   const int W = job.W, H = job.H;
   const int u = (int)(pix % W), v = (int)(pix / W);
   const ForestView& f = job.forest;
+  const int T = f.T;
   const int d = __ldg(&job.depth[pix]);
   if (d == 0) {
-    for (int t = 0; t < f.T; ++t) job.leaves[(size_t)t * n_pix + pix] = 0xFFFF;
+    for (int t = 0; t < T; ++t) job.leaves[(size_t)t * n_pix + pix] = 0xFFFF;
     return;
   }
+  const DepthDivisor dv = make_divisor(d);
   const int n_int = (1 << f.D) - 1;
-  for (int t = 0; t < f.T; ++t) {
-    const int4* tree = f.nodes + (size_t)t * n_int;
-    int n = 0;
-    for (int level = 0; level < f.D; ++level) {
-      const int4 nd = __ldg(&tree[n]);
-      const int dx1 = (int)(int16_t)(nd.x & 0xFFFF), dy1 = nd.x >> 16;
-      const int dx2 = (int)(int16_t)(nd.y & 0xFFFF), dy2 = nd.y >> 16;
-      const int q1 = probe(v, dy1, d, H - 1) * W + probe(u, dx1, d, W - 1);
-      const int q2 = probe(v, dy2, d, H - 1) * W + probe(u, dx2, d, W - 1);
-      int a, b;
-      if ((nd.z & 0xFF) == 0) {
-        a = __ldg(&job.depth[q1]);
-        b = __ldg(&job.depth[q2]);
-      } else {
-        const int c1 = (nd.z >> 8) & 0xFF, c2 = (nd.z >> 16) & 0xFF;
-        a = (__ldg(&job.rgba[q1]) >> (8 * c1)) & 0xFF;
-        b = (__ldg(&job.rgba[q2]) >> (8 * c2)) & 0xFF;
+  int node[MT];
+#pragma unroll
+  for (int t = 0; t < MT; ++t) node[t] = 0;
+  for (int level = 0; level < f.D; ++level) {
+#pragma unroll
+    for (int t = 0; t < MT; ++t) {
+      if (t < T) {
+        const int4 nd = __ldg(&f.nodes[(size_t)t * n_int + node[t]]);
+        const int dx1 = (int)(int16_t)(nd.x & 0xFFFF), dy1 = nd.x >> 16;
+        const int dx2 = (int)(int16_t)(nd.y & 0xFFFF), dy2 = nd.y >> 16;
+        const int q1 = probe(v, dy1, dv, H - 1) * W + probe(u, dx1, dv, W - 1);
+        const int q2 = probe(v, dy2, dv, H - 1) * W + probe(u, dx2, dv, W - 1);
+        int a, b;
+        if ((nd.z & 0xFF) == 0) {
+          a = __ldg(&job.depth[q1]);
+          b = __ldg(&job.depth[q2]);
+        } else {
+          const int c1 = (nd.z >> 8) & 0xFF, c2 = (nd.z >> 16) & 0xFF;
+          a = (__ldg(&job.rgba[q1]) >> (8 * c1)) & 0xFF;
+          b = (__ldg(&job.rgba[q2]) >> (8 * c2)) & 0xFF;
+        }
+        node[t] = (a - b < nd.w) ? 2 * node[t] + 1 : 2 * node[t] + 2;
       }
-      n = (a - b < nd.w) ? 2 * n + 1 : 2 * n + 2;
     }
-    job.leaves[(size_t)t * n_pix + pix] = (uint16_t)(n - n_int);
   }
+#pragma unroll
+  for (int t = 0; t < MT; ++t)
+    if (t < T) job.leaves[(size_t)t * n_pix + pix] = (uint16_t)(node[t] - n_int);
 }
 
 cudaError_t launch_forest(const ForestJob* jobs_dev, int n_jobs, const ForestJob* single, int64_t total_pixels,
-                          cudaStream_t s) {
+                          cudaStream_t s, int max_trees) {
   if (total_pixels <= 0) return cudaSuccess;
   ForestJob one{};
   if (single) one = *single;
-  forest_kernel<<<(unsigned)((total_pixels + 255) / 256), 256, 0, s>>>(jobs_dev, n_jobs, one);
+  const unsigned grid = (unsigned)((total_pixels + 255) / 256);
+  if (max_trees <= 4) forest_kernel<4><<<grid, 256, 0, s>>>(jobs_dev, n_jobs, one);
+  else if (max_trees <= 8) forest_kernel<8><<<grid, 256, 0, s>>>(jobs_dev, n_jobs, one);
+  else forest_kernel<kMaxTrees><<<grid, 256, 0, s>>>(jobs_dev, n_jobs, one);
   return cudaGetLastError();
 }
 

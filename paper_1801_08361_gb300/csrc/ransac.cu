@@ -245,35 +245,51 @@ __device__ __noinline__ bool exact_geometry(const RansacJob& job, int h, int j, 
 }
 
 // 0: the try fails; 1: it passes; 2: a test lies inside the FP32 guard band (settle in FP64).
+// Loads one correspondence of a try: its camera point and its leaf's mode-0 mean; false when the
+// leaf id is outside the forest or the leaf is empty.
+__device__ __forceinline__ bool load_corr(const RansacJob& job, int idx, int tree, int L, float fx, float fy, float cx,
+                                          float cy, float3* p, float3* q) {
+  const TableEntry e = load_entry(job, idx);
+  const int leaf = entry_leaf(job, idx, e, tree);
+  if (leaf >= L) return false;
+  const float4 m = __ldg(&job.forest.top[(size_t)tree * L + leaf]);
+  if (m.w < 0.5f) return false;
+  *p = cam_point_f(e.u, e.v, e.depth, fx, fy, cx, cy);
+  *q = make_float3(m.x, m.y, m.z);
+  return true;
+}
+
+// Rigidity of one pair: 0 fails, 1 passes, 2 inside the guard band.
+__device__ __forceinline__ int pair_status(float3 pa, float3 pb, float3 qa, float3 qb, float rig) {
+  const float diff = fabsf(dist_f(pa, pb) - dist_f(qa, qb));
+  if (diff > rig + kGuardRigid) return 0;
+  return diff >= rig - kGuardRigid ? 2 : 1;
+}
+
+// The tests are a conjunction, so they can run in any order: the pair (0, 1) is tested before the
+// third correspondence is loaded, which most tries never reach.
 __device__ __forceinline__ int try_status(const RansacJob& job, int h, int j, int n_valid, float rig, float area,
                                           float fx, float fy, float cx, float cy) {
-  const Corr c = draw_try(job, h, j, n_valid);
+  const uint4 x = philox4x32_10(make_uint4(1u, (uint32_t)h, (uint32_t)j, 0u), job.key0, job.key1);
+  const int i0 = (int)uniform_below(x.x, (uint32_t)n_valid), i1 = (int)uniform_below(x.y, (uint32_t)n_valid);
+  const int i2 = (int)uniform_below(x.z, (uint32_t)n_valid);
+  if (i0 == i1 || i0 == i2 || i1 == i2) return 0;
+  const uint32_t T = (uint32_t)job.forest.T;
+  const int t0 = (int)(((x.w & 0xFFu) * T) >> 8), t1 = (int)((((x.w >> 8) & 0xFFu) * T) >> 8);
+  const int t2 = (int)((((x.w >> 16) & 0xFFu) * T) >> 8);
   const int L = 1 << job.forest.D;
-  float4 m[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    if (c.leaf[k] >= L) return 0;  // a leaf id outside the forest
-    m[k] = __ldg(&job.forest.top[(size_t)c.tree[k] * L + c.leaf[k]]);
-  }
-#pragma unroll
-  for (int k = 0; k < 3; ++k)
-    if (m[k].w < 0.5f) return 0;  // empty leaf
-  if (c.idx[0] == c.idx[1] || c.idx[0] == c.idx[2] || c.idx[1] == c.idx[2]) return 0;
-  float3 p[3], q[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    p[k] = cam_point_f(c.e[k].u, c.e[k].v, c.e[k].depth, fx, fy, cx, cy);
-    q[k] = make_float3(m[k].x, m[k].y, m[k].z);
-  }
-  bool ambiguous = false;
-  const int pr[3][2] = {{0, 1}, {0, 2}, {1, 2}};
-#pragma unroll
-  for (int s = 0; s < 3; ++s) {
-    const float diff = fabsf(dist_f(p[pr[s][0]], p[pr[s][1]]) - dist_f(q[pr[s][0]], q[pr[s][1]]));
-    if (diff > rig + kGuardRigid) return 0;
-    if (diff >= rig - kGuardRigid) ambiguous = true;
-  }
-  const float ac = cross_norm_f(p[0], p[1], p[2]), aw = cross_norm_f(q[0], q[1], q[2]);
+  float3 p0, p1, p2, q0, q1, q2;
+  if (!load_corr(job, i0, t0, L, fx, fy, cx, cy, &p0, &q0)) return 0;
+  if (!load_corr(job, i1, t1, L, fx, fy, cx, cy, &p1, &q1)) return 0;
+  const int s01 = pair_status(p0, p1, q0, q1, rig);
+  if (s01 == 0) return 0;
+  if (!load_corr(job, i2, t2, L, fx, fy, cx, cy, &p2, &q2)) return 0;
+  const int s02 = pair_status(p0, p2, q0, q2, rig);
+  if (s02 == 0) return 0;
+  const int s12 = pair_status(p1, p2, q1, q2, rig);
+  if (s12 == 0) return 0;
+  bool ambiguous = s01 == 2 || s02 == 2 || s12 == 2;
+  const float ac = cross_norm_f(p0, p1, p2), aw = cross_norm_f(q0, q1, q2);
   if (ac < area - kGuardArea || aw < area - kGuardArea) return 0;
   if (ac <= area + kGuardArea || aw <= area + kGuardArea) ambiguous = true;
   return ambiguous ? 2 : 1;

@@ -314,8 +314,9 @@ struct Carver {
 // jobs_dev == nullptr: the single job is passed by value.
 cudaError_t launch_raycast(const RayJob* jobs_dev, int n_jobs, const RayJob* single, int total_tiles,
                            bool with_colour, bool compare, cudaStream_t s);
+// max_trees: the largest tree count among the jobs (selects the kernel's unrolled width)
 cudaError_t launch_forest(const ForestJob* jobs_dev, int n_jobs, const ForestJob* single, int64_t total_pixels,
-                          cudaStream_t s);
+                          cudaStream_t s, int max_trees);
 int ray_tiles(int W, int H);
 cudaError_t launch_verify_decide(const RansacJob* jobs, int n_jobs, cudaStream_t s);
 cudaError_t launch_verify_decide_one(relo_pose_result* res, uint64_t omega, cudaStream_t s);
