@@ -226,6 +226,27 @@ relo_status relo_ransac_relocalise(const relo_forest* forest, const uint16_t* de
  * poses_dev [K][12] and energy_dev [K] updated in place, drawn_dev [(r+1) * batch] positions in
  * the valid-pixel list (depth > 0, raster order) of the pixels drawn in rounds 0..r (only
  * round r's slice is written), survivors_dev [ceil(n_alive/2)] and inliers_dev [K] written. */
+/* Allocation-free variant of relo_ransac_relocalise (the paper has no counterpart; this serves
+ * callers, not the method).  Some callers may not allocate device memory when they relocalise:
+ * a process whose device memory is owned and budgeted by another allocator, or a latency-bound
+ * loop where an allocation could block, synchronise the device or fail under memory pressure.
+ * This entry point takes no workspace and allocates nothing: its scratch is one array of
+ * RELO_STATIC_SCRATCH_BYTES (8 MiB) compiled into the library, which every GPU that loads the
+ * library holds until the process exits.  The caller still passes the inputs and the result.
+ * The first call on a device looks the array's device address up (with that device current)
+ * and caches it; make that first call before any stream capture.  All calls share the one
+ * array, which keeps the last call's contents (each call clears what must start at zero): calls
+ * that may overlap on the GPU -- on different streams, or from different host threads -- race,
+ * so serialise them.  Results equal relo_ransac_relocalise's for the same inputs.
+ * Errors: as relo_ransac_relocalise, plus RELO_EINVAL when the view needs more scratch than the
+ * array holds (for T <= 5 trees: about 16 bytes per pixel plus 230 bytes per hypothesis, e.g.
+ * 640 x 480 with 1024 hypotheses fits) or the device ordinal is 64 or more. */
+#define RELO_STATIC_SCRATCH_BYTES (8u << 20)
+relo_status relo_ransac_relocalise_noalloc(const relo_forest* forest, const uint16_t* depth_dev,
+                                           const uint16_t* leaves_dev, const relo_intrinsics* intr,
+                                           const relo_ransac_params* p, relo_pose_result* result_dev,
+                                           relo_stream stream);
+
 relo_status relo_ransac_hypotheses(const relo_forest* forest, const uint16_t* depth_dev, const uint16_t* leaves_dev,
                                    const relo_intrinsics* intr, const relo_ransac_params* p, void* workspace_dev,
                                    size_t workspace_bytes, double* poses_dev, int32_t* valid_dev, int32_t* tries_dev,

@@ -82,6 +82,8 @@ _SIGS = {
     "relo_ransac_workspace_size": (ctypes.c_size_t, [c_i32, c_i32, ctypes.POINTER(RansacParams)]),
     "relo_ransac_relocalise": (c_i32, [c_vp, c_vp, c_vp, ctypes.POINTER(Intrinsics), ctypes.POINTER(RansacParams),
                                        c_vp, ctypes.c_size_t, c_vp, c_vp]),
+    "relo_ransac_relocalise_noalloc": (c_i32, [c_vp, c_vp, c_vp, ctypes.POINTER(Intrinsics),
+                                               ctypes.POINTER(RansacParams), c_vp, c_vp]),
     "relo_ransac_hypotheses": (c_i32, [c_vp, c_vp, c_vp, ctypes.POINTER(Intrinsics), ctypes.POINTER(RansacParams),
                                        c_vp, ctypes.c_size_t, c_vp, c_vp, c_vp, c_vp]),
     "relo_ransac_round": (c_i32, [c_vp, c_vp, c_vp, ctypes.POINTER(Intrinsics), ctypes.POINTER(RansacParams), c_i32,
@@ -266,6 +268,16 @@ def ransac_relocalise(forest, depth_dev, leaves_dev, intr, params, workspace_dev
     _check(lib().relo_ransac_relocalise(forest.handle, _ptr(depth_dev), _ptr(leaves_dev), ctypes.byref(ci),
                                         ctypes.byref(params), _ptr(workspace_dev), workspace_dev.numel(),
                                         _ptr(result_dev), _stream(stream)))
+
+
+STATIC_SCRATCH_BYTES = 8 << 20
+
+
+def ransac_relocalise_noalloc(forest, depth_dev, leaves_dev, intr, params, result_dev, stream=None):
+    """relo_ransac_relocalise_noalloc: no workspace; the library's fixed scratch array is used."""
+    ci = intrinsics(intr)
+    _check(lib().relo_ransac_relocalise_noalloc(forest.handle, _ptr(depth_dev), _ptr(leaves_dev), ctypes.byref(ci),
+                                                ctypes.byref(params), _ptr(result_dev), _stream(stream)))
 
 
 def ransac_hypotheses(forest, depth_dev, leaves_dev, intr, params, workspace_dev, poses_dev, valid_dev, tries_dev,

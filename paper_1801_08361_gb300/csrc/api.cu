@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "relo_internal.cuh"
@@ -774,6 +775,58 @@ relo_status relo_ransac_relocalise(const relo_forest* f, const uint16_t* depth, 
   RELO_CUDA(cudaMemsetAsync(s.job.err, 0, sizeof(int32_t), cs));
   int launches = 0;
   return run_ransac_stages(&b, cs, &launches);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free RANSAC: the same stages as relo_ransac_relocalise, with the scratch taken from
+// a fixed array compiled into this library instead of a caller-allocated workspace.  Its device
+// address is looked up once per device (cudaGetSymbolAddress with that device current) and cached;
+// every call on a device reuses the same array.
+// ---------------------------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_static_scratch[RELO_STATIC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+void* g_static_addr[kMaxDevices] = {};
+
+relo_status static_scratch(void** out) {
+  int dev = -1;
+  RELO_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(RELO_EINVAL, "device ordinal outside [0, 64)");
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return RELO_OK;
+}
+}  // namespace
+
+extern "C" {
+
+relo_status relo_ransac_relocalise_noalloc(const relo_forest* f, const uint16_t* depth, const uint16_t* leaves,
+                                           const relo_intrinsics* intr, const relo_ransac_params* p,
+                                           relo_pose_result* result, relo_stream stream) {
+  if (!f || !intr || !p) return fail(RELO_EINVAL, "null forest, intrinsics or params");
+  relo_status st = check_intr(intr);
+  if (st) return st;
+  st = check_params(p);
+  if (st) return st;
+  Single need;
+  layout_single(nullptr, intr->width, intr->height, p->n_hyps, p->batch, f->T, need);
+  if (need.bytes > (size_t)RELO_STATIC_SCRATCH_BYTES)
+    return fail(RELO_EINVAL, "view needs " + std::to_string(need.bytes) + " bytes of scratch; the static scratch holds " +
+                                 std::to_string((size_t)RELO_STATIC_SCRATCH_BYTES));
+  void* scratch = nullptr;
+  st = static_scratch(&scratch);
+  if (st) return st;
+  return relo_ransac_relocalise(f, depth, leaves, intr, p, scratch, (size_t)RELO_STATIC_SCRATCH_BYTES, result, stream);
 }
 
 relo_status relo_ransac_hypotheses(const relo_forest* f, const uint16_t* depth, const uint16_t* leaves,
