@@ -93,10 +93,12 @@ relo_status relo_scene_use_grid(relo_scene* scene, int32_t enable);
 /* ---------------------------------------------------------------------------------------
  * Synthetic raycast (Sec. 3.3.1, Fig. 3: the query is a colour + depth render of scene b from
  * the frame's pose; the appendix on global map rendering names the usual voxel raycast).
- * March, per ray: start at depth_min; a sample in an unallocated block counts as +1 and jumps
- * just past the block's exit; otherwise f = trilinear tsdf, and while f > 0 the next sample is
- * max(f mu, voxel) / |d| further; the first f <= 0 after a positive sample ends the march at
- * the secant root of the last two samples (f <= 0 on the first sample: invalid).  Depth is the
+ * March, per ray: start at depth_min; at a sample in an unallocated block the march moves to the
+ * block's exit, which becomes the previous sample with f = +1, and samples again 1e-5 (in z)
+ * past it; otherwise f = trilinear tsdf, and while f > 0 the next sample is max(f mu, voxel) / |d|
+ * further; the first f <= 0 after a positive sample ends the march at the secant root of the last
+ * two samples (f <= 0 on the first sample: invalid); the march gives up past depth_max or after
+ * 100000 samples.  Depth is the
  * hit's camera z in mm rounded half up, clamped to [1, 65535]; with noise_dev (one standard
  * normal per pixel, float32 [H][W]) 1.5 mm * z^2 * n is added first (the quadratic axial noise
  * model of the appendix on depth sensors).  Colour (rgba_dev may be NULL) is the trilinear
