@@ -5,7 +5,7 @@
 //   compact    : ordered table of valid pixels, each entry packing {u, v, depth, leaf per tree}
 //                in 16-byte words so that one load serves a correspondence (two passes: chunk
 //                counts, then an ordered scatter with warp ballots);
-//   search     : one CTA per hypothesis evaluates 256 tries at a time and keeps the first passing
+//   search     : one warp per hypothesis evaluates 32 tries at a time and keeps the first passing
 //                try, so the result equals a sequential scan of the tries.  The rigidity / area
 //                tests run in FP32 with a guard band; a try inside the band is settled in FP64 in
 //                the oracle's operation order;
@@ -171,7 +171,6 @@ cudaError_t launch_compact(const RansacJob* jobs, int n_jobs, int total_chunks, 
 // ---------------------------------------------------------------------------------------------
 // Hypothesis search
 // ---------------------------------------------------------------------------------------------
-constexpr int kHypThreads = 256;
 constexpr float kGuardRigid = 1e-4f;  // FP32 error of a distance difference stays below 2e-5 m here
 constexpr float kGuardArea = 2e-4f;   // and that of |cross| below 2e-5 m^2
 
@@ -295,47 +294,55 @@ __device__ __forceinline__ int try_status(const RansacJob& job, int h, int j, in
   return ambiguous ? 2 : 1;
 }
 
-__global__ void __launch_bounds__(kHypThreads, 4) search_kernel(const RansacJob* __restrict__ jobs, int n_jobs) {
+// One warp per hypothesis (four per CTA, no block-wide barriers): each step evaluates 32 tries
+// and keeps the first one not failing, settling guard-band tries in FP64 in order.
+constexpr int kSearchWarps = 4;
+
+// CTAs per SM for the search (8 x 128 threads: the fastest setting of a sweep on the house workload)
+#ifndef RELO_SEARCH_MIN_BLOCKS
+#define RELO_SEARCH_MIN_BLOCKS 8
+#endif
+__global__ void __launch_bounds__(kSearchWarps * 32, RELO_SEARCH_MIN_BLOCKS)
+    search_kernel(const RansacJob* __restrict__ jobs, int n_jobs, int total) {
+  const int gw = blockIdx.x * kSearchWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (gw >= total) return;
   int lo = 0, hi = n_jobs - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (jobs[mid].hyp_begin <= (int)blockIdx.x) lo = mid;
+    if (jobs[mid].hyp_begin <= gw) lo = mid;
     else hi = mid - 1;
   }
   const RansacJob& job = jobs[lo];
-  const int h = blockIdx.x - job.hyp_begin;
+  const int h = gw - job.hyp_begin;
   if (h >= job.K) return;
   const int n_valid = *job.n_valid;
   const float rig = (float)job.rigidity, area = (float)job.min_area;
   const float fx = (float)job.fx, fy = (float)job.fy, cx = (float)job.cx, cy = (float)job.cy;
-  __shared__ int s_win, s_res;
   int found = INT_MAX;
   if (n_valid > 0) {
-    for (int base = 0; base < job.max_tries && found == INT_MAX; base += kHypThreads) {
-      const int j = base + threadIdx.x;
+    for (int base = 0; base < job.max_tries && found == INT_MAX; base += 32) {
+      const int j = base + lane;
       const int st = j < job.max_tries ? try_status(job, h, j, n_valid, rig, area, fx, fy, cx, cy) : 0;
-      int rejected = -1;
-      // settle this block of tries in order: the first try not failing is accepted unless it is
-      // in the guard band and the FP64 test rejects it, in which case the next one is considered
-      while (true) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_win = INT_MAX;
-        __syncthreads();
-        if (st != 0 && j > rejected) atomicMin(&s_win, j);
-        __syncthreads();
-        const int w = s_win;
-        if (w == INT_MAX) break;
-        if (j == w) s_res = (st == 1) ? 1 : (exact_geometry(job, h, j, n_valid) ? 1 : 0);
-        __syncthreads();
-        if (s_res) {
-          found = w;
+      unsigned mask = __ballot_sync(0xffffffffu, st != 0);
+      while (mask) {
+        const int w = __ffs(mask) - 1;
+        const int sw = __shfl_sync(0xffffffffu, st, w);
+        int ok = sw == 1;
+        if (!ok) {
+          int e = 0;
+          if (lane == w) e = exact_geometry(job, h, j, n_valid) ? 1 : 0;
+          ok = __shfl_sync(0xffffffffu, e, w);
+        }
+        if (ok) {
+          found = base + w;
           break;
         }
-        rejected = w;
+        mask &= mask - 1;  // rejected in FP64: consider the next try of this step
       }
     }
   }
-  if (threadIdx.x == 0) {
+  if (lane == 0) {
     job.hyp_ok[h] = found != INT_MAX;
     job.tries[h] = found != INT_MAX ? found : job.max_tries;
   }
@@ -386,7 +393,7 @@ __global__ void __launch_bounds__(128) fit_kernel(const RansacJob* __restrict__ 
 
 cudaError_t launch_hypotheses(const RansacJob* jobs, int n_jobs, int total_hyps, cudaStream_t s) {
   if (total_hyps <= 0) return cudaSuccess;
-  search_kernel<<<total_hyps, kHypThreads, 0, s>>>(jobs, n_jobs);
+  search_kernel<<<(total_hyps + kSearchWarps - 1) / kSearchWarps, kSearchWarps * 32, 0, s>>>(jobs, n_jobs, total_hyps);
   fit_kernel<<<(total_hyps + 127) / 128, 128, 0, s>>>(jobs, n_jobs, total_hyps);
   return cudaGetLastError();
 }

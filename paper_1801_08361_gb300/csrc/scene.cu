@@ -33,16 +33,30 @@ __device__ __forceinline__ int cached_block(const SceneView& s, BlockCache& c, i
   return c.ptr;
 }
 
-// Parameter of the ray's exit from the axis-aligned cell [lo, lo + size)^3 (per-axis lo).
-__device__ __forceinline__ float cell_exit(float3 C, float3 d, float lox, float loy, float loz, float hix, float hiy,
-                                           float hiz) {
-  float lx = INFINITY, ly = INFINITY, lz = INFINITY;
-  if (d.x > 0.f) lx = (hix - C.x) / d.x;
-  else if (d.x < 0.f) lx = (lox - C.x) / d.x;
-  if (d.y > 0.f) ly = (hiy - C.y) / d.y;
-  else if (d.y < 0.f) ly = (loy - C.y) / d.y;
-  if (d.z > 0.f) lz = (hiz - C.z) / d.z;
-  else if (d.z < 0.f) lz = (loz - C.z) / d.z;
+// Per-ray constants for cell exits: reciprocal direction, which face each axis leaves through.
+struct RayExit {
+  float3 inv;
+  int px, py, pz;      // 1 if the ray moves toward +axis
+  bool zx, zy, zz;     // the ray is parallel to that axis' faces
+};
+
+__device__ __forceinline__ RayExit ray_exit(float3 d) {
+  RayExit r;
+  r.inv = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+  r.px = d.x > 0.f;
+  r.py = d.y > 0.f;
+  r.pz = d.z > 0.f;
+  r.zx = d.x == 0.f;
+  r.zy = d.y == 0.f;
+  r.zz = d.z == 0.f;
+  return r;
+}
+
+// Ray parameter at which the ray leaves the axis-aligned cell (cx, cy, cz) of the given size.
+__device__ __forceinline__ float cell_exit(float3 C, const RayExit& r, int cx, int cy, int cz, float size) {
+  const float lx = r.zx ? INFINITY : ((float)(cx + r.px) * size - C.x) * r.inv.x;
+  const float ly = r.zy ? INFINITY : ((float)(cy + r.py) * size - C.y) * r.inv.y;
+  const float lz = r.zz ? INFINITY : ((float)(cz + r.pz) * size - C.z) * r.inv.z;
   return fminf(lx, fminf(ly, lz));
 }
 
@@ -112,6 +126,7 @@ __device__ uint32_t trilinear_rgba(const SceneView& s, BlockCache& c, float3 p, 
 __device__ float march_ray(const SceneView& s, float3 C, float3 d, float dmin, float dmax, BlockCache& c, int* err) {
   const float dn = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
   const float inv_dn = 1.0f / dn;
+  const RayExit rx = ray_exit(d);
   float lam = dmin, lam_prev = 0.f, f_prev = 0.f;
   bool have_prev = false;
   for (int it = 0; it < kMaxMarchSamples && lam <= dmax; ++it) {
@@ -126,16 +141,8 @@ __device__ float march_ray(const SceneView& s, float3 C, float3 d, float dmin, f
       // is empty, of that cell: stepping block by block through an empty cell ends on the same
       // exit plane, so the skip changes no sample the march evaluates
       float lexit;
-      if (s.grid && macro_empty(s, bx, by, bz)) {
-        const int mx = bx >> 3, my = by >> 3, mz = bz >> 3;
-        const float ms = 8.0f * s.block_size;
-        lexit = cell_exit(C, d, (float)mx * ms, (float)my * ms, (float)mz * ms, (float)(mx + 1) * ms,
-                          (float)(my + 1) * ms, (float)(mz + 1) * ms);
-      } else {
-        lexit = cell_exit(C, d, (float)bx * s.block_size, (float)by * s.block_size, (float)bz * s.block_size,
-                          (float)(bx + 1) * s.block_size, (float)(by + 1) * s.block_size,
-                          (float)(bz + 1) * s.block_size);
-      }
+      if (s.grid && macro_empty(s, bx, by, bz)) lexit = cell_exit(C, rx, bx >> 3, by >> 3, bz >> 3, 8.0f * s.block_size);
+      else lexit = cell_exit(C, rx, bx, by, bz, s.block_size);
       lam_prev = fmaxf(lexit, lam);
       f_prev = 1.0f;
       have_prev = true;
@@ -156,9 +163,14 @@ __device__ float march_ray(const SceneView& s, float3 C, float3 d, float dmin, f
 }
 
 constexpr int kTile = 16;
+// CTAs per SM the compiler must fit (depth-only renders; colour renders one fewer), from a
+// sweep on the house workload
+#ifndef RELO_RAYCAST_MIN_BLOCKS
+#define RELO_RAYCAST_MIN_BLOCKS 5
+#endif
 
 template <bool kColour, bool kCompare>
-__global__ void __launch_bounds__(kTile* kTile)
+__global__ void __launch_bounds__(kTile* kTile, kColour ? RELO_RAYCAST_MIN_BLOCKS - 1 : RELO_RAYCAST_MIN_BLOCKS)
     raycast_kernel(const RayJob* __restrict__ jobs, int n_jobs, const RayJob single) {
   // locate the job owning this tile (jobs are few; binary search on tile_begin)
   int lo = 0, hi = n_jobs - 1;
@@ -170,8 +182,10 @@ __global__ void __launch_bounds__(kTile* kTile)
   const RayJob& job = jobs ? jobs[lo] : single;
   const int tiles_x = (job.W + kTile - 1) / kTile;
   const int tile = (int)blockIdx.x - job.tile_begin;
-  const int u = (tile % tiles_x) * kTile + (threadIdx.x % kTile);
-  const int v = (tile / tiles_x) * kTile + (threadIdx.x / kTile);
+  // each warp covers an 8 x 4 footprint of the 16 x 16 tile (neighbouring rays march alike)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int u = (tile % tiles_x) * kTile + (warp & 1) * 8 + (lane & 7);
+  const int v = (tile / tiles_x) * kTile + (warp >> 1) * 4 + (lane >> 3);
   const bool active = u < job.W && v < job.H && (job.status_dev == nullptr || *job.status_dev == RELO_OK);
 
   int err = 0;
