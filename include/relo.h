@@ -260,6 +260,57 @@ relo_status relo_ransac_round(const relo_forest* forest, const uint16_t* depth_d
                               void* workspace_dev, size_t workspace_bytes, relo_stream stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Learned scene-coordinate regressor: an alternative relocaliser for one scene, trained online
+ * on renders of its own voxel map (the paper uses a forest, Sec. 3.3 (b); this network and its
+ * details are readings of the workload, stated identically in the CPU oracle).
+ * Input per pixel: depth in metres (0 where invalid) and R, G, B / 255.  Eight 3x3 convolutions
+ * (zero padding 1, 64 channels; strides 2, 2, 2, 1, 1, 1, 1, 1; ReLU after layers 1-7) give
+ * one cell per 8 x 8 pixels with 4 outputs: the scene coordinate of the cell's centre pixel
+ * (8 cx + 4, 8 cy + 4) minus `origin`, and a log-variance s.  Loss: mean over cells whose
+ * centre pixel has depth of 1/2 |y - y_hat|^2 exp(-s) + 3/2 s; Adam (0.9, 0.999, 1e-8).
+ * Computed with BF16 tensor-core convolutions accumulating in FP32 (FP32 master weights).
+ * Parameters, flat FP32, per layer l: w [3][3][cin][cout] then b [cout], cin = 4, 64, ...,
+ * cout = 64, ..., 4 (relo_regressor_param_count() values in all).  Images must have sides that
+ * are multiples of 8.  Errors: RELO_EINVAL (sizes, null pointers, workspace), RELO_ENOMEM.
+ * ------------------------------------------------------------------------------------- */
+typedef struct relo_regressor relo_regressor;
+
+int64_t relo_regressor_param_count(void);
+/* params_host NULL: He-uniform weights drawn from Philox4x32-10 (counter (4, layer, index), key
+ * = seed), head weights scaled by 0.1, zero biases. */
+relo_status relo_create_regressor(const float* params_host, uint64_t seed, const double origin[3],
+                                  relo_regressor** out);
+void relo_destroy_regressor(relo_regressor* regressor);
+/* Copies of the master parameters and of the last computed gradients (either may be NULL). */
+relo_status relo_regressor_get_params(const relo_regressor* regressor, float* params_host, float* grads_host);
+/* Workspace bytes for n images of width x height (training != 0: with the backward pass). */
+size_t relo_regressor_workspace_size(int32_t n_images, int32_t width, int32_t height, int32_t training);
+/* Forward pass: out_dev [n][height/8][width/8][4] (scene coordinate - origin, log-variance). */
+relo_status relo_regressor_forward(relo_regressor* regressor, const uint16_t* depth_dev, const uint8_t* rgba_dev,
+                                   int32_t n_images, int32_t width, int32_t height, float* out_dev,
+                                   void* workspace_dev, size_t workspace_bytes, relo_stream stream);
+/* Loss (written to loss_dev, nullable) and gradients of n posed views (camera -> scene poses,
+ * host [n][16]); the gradients are kept in the regressor (relo_regressor_get_params). */
+relo_status relo_regressor_gradients(relo_regressor* regressor, const uint16_t* depth_dev, const uint8_t* rgba_dev,
+                                     int32_t n_images, const relo_intrinsics* intr, const double* poses_host,
+                                     float* loss_dev, void* workspace_dev, size_t workspace_bytes,
+                                     relo_stream stream);
+/* relo_regressor_gradients followed by one Adam step with learning rate lr. */
+relo_status relo_regressor_train_step(relo_regressor* regressor, const uint16_t* depth_dev, const uint8_t* rgba_dev,
+                                      int32_t n_images, const relo_intrinsics* intr, const double* poses_host,
+                                      float lr, float* loss_dev, void* workspace_dev, size_t workspace_bytes,
+                                      relo_stream stream);
+/* Relocalise one view with the regressor: forward pass, then the preemptive RANSAC of
+ * relo_ransac_relocalise on the cell grid (one-tree forest whose leaf is the cell and whose one
+ * mode is N(y_hat + origin, exp(s) I); the coarse view holds the cells' centre-pixel depths with
+ * intrinsics fx / 8, fy / 8, (cx - 4) / 8, (cy - 4) / 8).  The result's pose is camera -> scene;
+ * verify with relo_verify at full resolution. */
+size_t relo_regressor_relocalise_workspace_size(int32_t width, int32_t height, const relo_ransac_params* p);
+relo_status relo_regressor_relocalise(relo_regressor* regressor, const uint16_t* depth_dev, const uint8_t* rgba_dev,
+                                      const relo_intrinsics* intr, const relo_ransac_params* p, void* workspace_dev,
+                                      size_t workspace_bytes, relo_pose_result* result_dev, relo_stream stream);
+
+/* ---------------------------------------------------------------------------------------
  * Depth-difference verification (Sec. 3.3.1): raycast scene a's depth from the proposed pose
  * in result_dev->pose_c2s and compare with depth_b_dev; writes omega (= W H), omega_a,
  * omega_b, omega_ab, sum_absdiff_mm and verified into result_dev (integer-exact).

@@ -97,6 +97,19 @@ _SIGS = {
     "relo_batch_run": (c_i32, [c_vp, c_vp, c_vp]),
     "relo_batch_launch_count": (c_i32, [c_vp]),
     "relo_batch_destroy": (None, [c_vp]),
+    "relo_regressor_param_count": (c_i64, []),
+    "relo_create_regressor": (c_i32, [c_vp, c_u64, ctypes.POINTER(c_dbl), ctypes.POINTER(c_vp)]),
+    "relo_destroy_regressor": (None, [c_vp]),
+    "relo_regressor_get_params": (c_i32, [c_vp, c_vp, c_vp]),
+    "relo_regressor_workspace_size": (ctypes.c_size_t, [c_i32, c_i32, c_i32, c_i32]),
+    "relo_regressor_forward": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_i32, c_i32, c_vp, c_vp, ctypes.c_size_t, c_vp]),
+    "relo_regressor_gradients": (c_i32, [c_vp, c_vp, c_vp, c_i32, ctypes.POINTER(Intrinsics), c_vp, c_vp, c_vp,
+                                         ctypes.c_size_t, c_vp]),
+    "relo_regressor_train_step": (c_i32, [c_vp, c_vp, c_vp, c_i32, ctypes.POINTER(Intrinsics), c_vp, ctypes.c_float,
+                                          c_vp, c_vp, ctypes.c_size_t, c_vp]),
+    "relo_regressor_relocalise_workspace_size": (ctypes.c_size_t, [c_i32, c_i32, ctypes.POINTER(RansacParams)]),
+    "relo_regressor_relocalise": (c_i32, [c_vp, c_vp, c_vp, ctypes.POINTER(Intrinsics), ctypes.POINTER(RansacParams),
+                                          c_vp, ctypes.c_size_t, c_vp, c_vp]),
     "relo_batch_enable_timing": (c_i32, [c_vp, c_i32]),
     "relo_batch_stage_ms": (c_i32, [c_vp, ctypes.POINTER(ctypes.c_float), c_i32]),
 }
@@ -365,3 +378,82 @@ class Batch:
         if getattr(self, "handle", None) and _LIB is not None:
             _LIB.relo_batch_destroy(self.handle)
             self.handle = None
+
+
+# ------------------------------------------------------------------------------------------------
+# Learned regressor
+# ------------------------------------------------------------------------------------------------
+
+def regressor_param_count() -> int:
+    return int(lib().relo_regressor_param_count())
+
+
+class Regressor:
+    """Device-resident scene-coordinate regressor (relo_create_regressor)."""
+
+    def __init__(self, params=None, seed: int = 0, origin=(0.0, 0.0, 0.0)):
+        h = c_vp()
+        p = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+        if p is not None and p.size != regressor_param_count():
+            raise ValueError("parameter count mismatch")
+        org = (c_dbl * 3)(*[float(x) for x in origin])
+        _check(lib().relo_create_regressor(None if p is None else p.ctypes.data, int(seed), org, ctypes.byref(h)))
+        self.handle = h.value
+        self.origin = tuple(float(x) for x in origin)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.relo_destroy_regressor(self.handle)
+            self.handle = None
+
+    def params(self):
+        p = np.zeros(regressor_param_count(), np.float32)
+        _check(lib().relo_regressor_get_params(self.handle, p.ctypes.data, None))
+        return p
+
+    def grads(self):
+        g = np.zeros(regressor_param_count(), np.float32)
+        _check(lib().relo_regressor_get_params(self.handle, None, g.ctypes.data))
+        return g
+
+
+def regressor_workspace_size(n, width, height, training) -> int:
+    return int(lib().relo_regressor_workspace_size(int(n), int(width), int(height), 1 if training else 0))
+
+
+def regressor_forward(reg, depth_dev, rgba_dev, out_dev, workspace_dev, stream=None):
+    n, H, W = depth_dev.shape
+    _check(lib().relo_regressor_forward(reg.handle, _ptr(depth_dev), _ptr(rgba_dev), int(n), int(W), int(H),
+                                        _ptr(out_dev), _ptr(workspace_dev), workspace_dev.numel(), _stream(stream)))
+
+
+def _poses_host(poses):
+    a = np.ascontiguousarray(np.asarray(poses, dtype=np.float64).reshape(-1, 16))
+    return a, a.ctypes.data
+
+
+def regressor_gradients(reg, depth_dev, rgba_dev, intr, poses, workspace_dev, loss_dev=None, stream=None):
+    ci = intrinsics(intr)
+    ph, pp = _poses_host(poses)
+    _check(lib().relo_regressor_gradients(reg.handle, _ptr(depth_dev), _ptr(rgba_dev), int(depth_dev.shape[0]),
+                                          ctypes.byref(ci), pp, _ptr(loss_dev), _ptr(workspace_dev),
+                                          workspace_dev.numel(), _stream(stream)))
+
+
+def regressor_train_step(reg, depth_dev, rgba_dev, intr, poses, lr, workspace_dev, loss_dev=None, stream=None):
+    ci = intrinsics(intr)
+    ph, pp = _poses_host(poses)
+    _check(lib().relo_regressor_train_step(reg.handle, _ptr(depth_dev), _ptr(rgba_dev), int(depth_dev.shape[0]),
+                                           ctypes.byref(ci), pp, ctypes.c_float(lr), _ptr(loss_dev),
+                                           _ptr(workspace_dev), workspace_dev.numel(), _stream(stream)))
+
+
+def regressor_relocalise_workspace_size(width, height, params) -> int:
+    return int(lib().relo_regressor_relocalise_workspace_size(int(width), int(height), ctypes.byref(params)))
+
+
+def regressor_relocalise(reg, depth_dev, rgba_dev, intr, params, workspace_dev, result_dev, stream=None):
+    ci = intrinsics(intr)
+    _check(lib().relo_regressor_relocalise(reg.handle, _ptr(depth_dev), _ptr(rgba_dev), ctypes.byref(ci),
+                                           ctypes.byref(params), _ptr(workspace_dev), workspace_dev.numel(),
+                                           _ptr(result_dev), _stream(stream)))

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "librelo.so")
-SOURCES = ["scene.cu", "forest.cu", "ransac.cu", "api.cu"]
+SOURCES = ["scene.cu", "forest.cu", "ransac.cu", "regressor.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 # occupancy bounds of the raycast and hypothesis-search kernels (tuning knobs)
@@ -37,7 +37,7 @@ def _stale(out: str, deps: list[str]) -> bool:
 
 
 def build_cuda(force: bool = False, verbose: bool = False) -> str:
-    hdrs = [os.path.join(CSRC, "relo_internal.cuh"), os.path.join(ROOT, "include", "relo.h")]
+    hdrs = [os.path.join(CSRC, "relo_internal.cuh"), os.path.join(CSRC, "regressor.cuh"), os.path.join(ROOT, "include", "relo.h")]
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
     if not force and not _stale(LIB, srcs + hdrs):
         return LIB

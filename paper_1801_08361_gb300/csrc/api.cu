@@ -11,6 +11,7 @@
 #include <mutex>
 #include <vector>
 
+#include "regressor.cuh"
 #include "relo_internal.cuh"
 
 using namespace relo;
@@ -85,9 +86,9 @@ void carve_ransac(Carver& c, RansacJob& j, int W, int H, int K, int B, int n_rou
   j.err = c.take<int32_t>(1);
 }
 
-void fill_ransac_job(RansacJob& j, const relo_forest* f, const uint16_t* depth, const uint16_t* leaves,
+void fill_ransac_job(RansacJob& j, const ForestView& fv, const uint16_t* depth, const uint16_t* leaves,
                      const relo_intrinsics& in, const relo_ransac_params& p, int K, uint64_t seed) {
-  j.forest = f->view;
+  j.forest = fv;
   j.depth = depth;
   j.leaves = leaves;
   j.W = in.width;
@@ -224,7 +225,7 @@ relo_status layout_batch(const relo_attempt* at, int n, const relo_ransac_params
     f.pixel_begin = pixels;
     // RANSAC
     RansacJob& j = rj[i];
-    fill_ransac_job(j, a.forest_a, depth, leaves, a.intr, p, K[i], a.seed);
+    fill_ransac_job(j, a.forest_a->view, depth, leaves, a.intr, p, K[i], a.seed);
     carve_ransac(c, j, W, H, K[i], p.batch, j.n_rounds, T);
     j.err = d_errs ? d_errs + i : nullptr;
     j.result = d_results + i;
@@ -722,23 +723,33 @@ void layout_single(char* base, int W, int H, int K, int B, int T, Single& s) {
   s.chunks = (W * H + kCompactChunk - 1) / kCompactChunk;
 }
 
-relo_status single_setup(const relo_forest* f, const uint16_t* depth, const uint16_t* leaves,
-                         const relo_intrinsics* intr, const relo_ransac_params* p, void* ws, size_t ws_bytes,
-                         Single& s) {
-  if (!f || !depth || !leaves || !ws) return fail(RELO_EINVAL, "null forest, image or workspace");
+relo_status single_setup_view(const ForestView& fv, const uint16_t* depth, const uint16_t* leaves,
+                              const relo_intrinsics* intr, const relo_ransac_params* p, void* ws, size_t ws_bytes,
+                              Single& s) {
+  if (!depth || !leaves || !ws) return fail(RELO_EINVAL, "null image or workspace");
   relo_status st = check_intr(intr);
   if (st) return st;
   st = check_params(p);
   if (st) return st;
   if (((uintptr_t)ws & 255) != 0) return fail(RELO_EINVAL, "workspace must be 256-byte aligned");
-  layout_single(nullptr, intr->width, intr->height, p->n_hyps, p->batch, f->T, s);
+  layout_single(nullptr, intr->width, intr->height, p->n_hyps, p->batch, fv.T, s);
   if (s.bytes > ws_bytes) return fail(RELO_EINVAL, "workspace too small");
-  layout_single((char*)ws, intr->width, intr->height, p->n_hyps, p->batch, f->T, s);
-  fill_ransac_job(s.job, f, depth, leaves, *intr, *p, p->n_hyps, p->seed);
+  layout_single((char*)ws, intr->width, intr->height, p->n_hyps, p->batch, fv.T, s);
+  fill_ransac_job(s.job, fv, depth, leaves, *intr, *p, p->n_hyps, p->seed);
   s.job.chunk_begin = 0;
   s.job.hyp_begin = 0;
   return RELO_OK;
 }
+
+relo_status single_setup(const relo_forest* f, const uint16_t* depth, const uint16_t* leaves,
+                         const relo_intrinsics* intr, const relo_ransac_params* p, void* ws, size_t ws_bytes,
+                         Single& s) {
+  if (!f) return fail(RELO_EINVAL, "null forest");
+  return single_setup_view(f->view, depth, leaves, intr, p, ws, ws_bytes, s);
+}
+
+// Runs every RANSAC stage of one prepared single-view job, writing *result.
+relo_status single_run(Single& s, const relo_ransac_params* p, relo_pose_result* result, cudaStream_t cs);
 
 }  // namespace
 
@@ -756,7 +767,13 @@ relo_status relo_ransac_relocalise(const relo_forest* f, const uint16_t* depth, 
   relo_status st = single_setup(f, depth, leaves, intr, p, ws, ws_bytes, s);
   if (st) return st;
   if (!result) return fail(RELO_EINVAL, "result is null");
-  cudaStream_t cs = (cudaStream_t)stream;
+  return single_run(s, p, result, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+namespace {
+relo_status single_run(Single& s, const relo_ransac_params* p, relo_pose_result* result, cudaStream_t cs) {
   s.job.result = result;
   std::vector<int> K(1, p->n_hyps);
   std::vector<int32_t> at, su;
@@ -776,8 +793,7 @@ relo_status relo_ransac_relocalise(const relo_forest* f, const uint16_t* depth, 
   int launches = 0;
   return run_ransac_stages(&b, cs, &launches);
 }
-
-}  // extern "C"
+}  // namespace
 
 // ---------------------------------------------------------------------------------------------
 // Allocation-free RANSAC: the same stages as relo_ransac_relocalise, with the scratch taken from
@@ -1020,6 +1036,454 @@ relo_status relo_relocalise_batch(const relo_attempt* at, int32_t n, const relo_
   }
   relo_batch_destroy(b);
   return st;
+}
+
+}  // extern "C"
+
+// =============================================================================================
+// Learned scene-coordinate regressor (the workload's alternative relocaliser; see regressor.cu)
+// =============================================================================================
+struct relo_regressor {
+  float* d_p = nullptr;  // FP32 master parameters, per layer w [3][3][cin][cout] then b [cout]
+  float* d_g = nullptr;  // gradients (same layout)
+  float* d_m = nullptr;  // Adam moments
+  float* d_v = nullptr;
+  bf16* d_wk[kRegLayers] = {};    // forward weights [9][cout_pad][cin_pad]
+  bf16* d_wt[kRegLayers] = {};    // flipped, transposed weights [9][cin][cout_pad_t] (layers 1..7)
+  float* d_bias[kRegLayers] = {}; // biases padded to cout_pad
+  int64_t w_off[kRegLayers], b_off[kRegLayers], n_params = 0;
+  int t = 0;
+  int n_sms = 148;
+  double origin[3] = {0, 0, 0};
+};
+
+namespace {
+
+void reg_offsets(int64_t* w_off, int64_t* b_off, int64_t* total) {
+  int64_t off = 0;
+  for (int l = 0; l < kRegLayers; ++l) {
+    w_off[l] = off;
+    off += 9LL * kRegCin[l] * kRegCout[l];
+    b_off[l] = off;
+    off += kRegCout[l];
+  }
+  *total = off;
+}
+
+int cout_pad_t(int l) { return l == kRegLayers - 1 ? 16 : 64; }
+
+__global__ void pad_bias_kernel(const float* b, int cout, int cout_pad, float* out) {
+  const int i = threadIdx.x;
+  if (i < cout_pad) out[i] = i < cout ? b[i] : 0.f;
+}
+
+relo_status reg_pack(relo_regressor* r, cudaStream_t s) {
+  for (int l = 0; l < kRegLayers; ++l) {
+    RELO_CUDA(launch_pack(r->d_p + r->w_off[l], kRegCin[l], kRegCout[l], kRegCinPad[l], kRegCoutPad[l], r->d_wk[l],
+                          l > 0 ? r->d_wt[l] : nullptr, cout_pad_t(l), s));
+    pad_bias_kernel<<<1, 64, 0, s>>>(r->d_p + r->b_off[l], kRegCout[l], kRegCoutPad[l], r->d_bias[l]);
+    RELO_CUDA(cudaGetLastError());
+  }
+  return RELO_OK;
+}
+
+// Per-layer grid sizes: H[0] = input, H[l + 1] = output of layer l.
+void reg_sizes(int W, int H, int* Hs, int* Ws) {
+  Hs[0] = H;
+  Ws[0] = W;
+  for (int l = 0; l < kRegLayers; ++l) {
+    Hs[l + 1] = (Hs[l] - 1) / kRegStride[l] + 1;
+    Ws[l + 1] = (Ws[l] - 1) / kRegStride[l] + 1;
+  }
+}
+
+struct RegBuffers {
+  bf16* x = nullptr;                  // [n][H][W][16]
+  bf16* act[kRegLayers] = {};         // act[l] = input of layer l (l >= 1): [n][H_l][W_l][64]
+  float* head = nullptr;              // [n][Hc][Wc][8]
+  float4* tgt = nullptr;              // [n][Hc][Wc]
+  bf16* ghead = nullptr;              // [n][Hc][Wc][16]
+  bf16* gpre[kRegLayers] = {};        // gpre[l] = gradient of layer l's pre-activation output (l < 7)
+  float* partial = nullptr;           // backward-weight chunk sums
+  float* bias_scratch = nullptr;
+  float* loss = nullptr;
+  double* poses = nullptr;            // [n][16]
+  size_t bytes = 0;
+};
+
+void reg_layout(char* base, int n, int W, int H, bool training, RegBuffers& b, size_t start = 0) {
+  Carver c{base, start};
+  int Hs[kRegLayers + 1], Ws[kRegLayers + 1];
+  reg_sizes(W, H, Hs, Ws);
+  b.x = c.take<bf16>((size_t)n * H * W * 16);
+  for (int l = 1; l < kRegLayers; ++l) b.act[l] = c.take<bf16>((size_t)n * Hs[l] * Ws[l] * 64);
+  const size_t cells = (size_t)n * Hs[kRegLayers] * Ws[kRegLayers];
+  b.head = c.take<float>(cells * 8);
+  if (training) {
+    b.tgt = c.take<float4>(cells);
+    b.ghead = c.take<bf16>(cells * 16);
+    for (int l = 0; l < kRegLayers - 1; ++l) b.gpre[l] = c.take<bf16>((size_t)n * Hs[l + 1] * Ws[l + 1] * 64);
+    size_t part = 0, bias = 0;
+    for (int l = 0; l < kRegLayers; ++l) {
+      const size_t px = (size_t)n * Hs[l + 1] * Ws[l + 1];
+      const size_t chunks = (px + kWgradChunk - 1) / kWgradChunk;
+      part = std::max(part, chunks * 9 * kRegCoutPad[l] * kRegCinPad[l]);
+      bias = std::max(bias, ((px + 2047) / 2048) * 64);
+    }
+    b.partial = c.take<float>(part);
+    b.bias_scratch = c.take<float>(bias);
+    b.loss = c.take<float>(1);
+    b.poses = c.take<double>((size_t)n * 16);
+  }
+  b.bytes = c.off;
+}
+
+relo_status reg_forward(relo_regressor* r, const RegBuffers& b, const uint16_t* depth, const uint8_t* rgba, int n,
+                        int W, int H, cudaStream_t s) {
+  int Hs[kRegLayers + 1], Ws[kRegLayers + 1];
+  reg_sizes(W, H, Hs, Ws);
+  RELO_CUDA(launch_input(depth, (const uint32_t*)rgba, (long)n * H * W, b.x, s));
+  for (int l = 0; l < kRegLayers; ++l) {
+    ConvArgs a{};
+    a.in = l == 0 ? b.x : b.act[l];
+    a.w = r->d_wk[l];
+    a.bias = r->d_bias[l];
+    a.out = l < kRegLayers - 1 ? b.act[l + 1] : nullptr;
+    a.out_f32 = l == kRegLayers - 1 ? b.head : nullptr;
+    a.B = n;
+    a.Hi = Hs[l];
+    a.Wi = Ws[l];
+    a.Ho = Hs[l + 1];
+    a.Wo = Ws[l + 1];
+    a.stride = kRegStride[l];
+    a.relu = l < kRegLayers - 1;
+    RELO_CUDA(launch_conv(kRegCinPad[l], kRegCoutPad[l] / 8, a, r->n_sms, s));
+  }
+  return RELO_OK;
+}
+
+relo_status reg_backward(relo_regressor* r, const RegBuffers& b, int n, int W, int H, cudaStream_t s) {
+  int Hs[kRegLayers + 1], Ws[kRegLayers + 1];
+  reg_sizes(W, H, Hs, Ws);
+  const bf16* g = b.ghead;
+  int gs = 16;
+  for (int l = kRegLayers - 1; l >= 0; --l) {
+    WgradArgs wa{};
+    wa.in = l == 0 ? b.x : b.act[l];
+    wa.g = g;
+    wa.partial = b.partial;
+    wa.B = n;
+    wa.Hi = Hs[l];
+    wa.Wi = Ws[l];
+    wa.Ho = Hs[l + 1];
+    wa.Wo = Ws[l + 1];
+    wa.stride = kRegStride[l];
+    wa.GS = gs;
+    wa.chunk_pix = kWgradChunk;
+    RELO_CUDA(launch_wgrad(kRegCinPad[l], kRegCoutPad[l] / 8, wa, s));
+    const long px = (long)n * Hs[l + 1] * Ws[l + 1];
+    const int chunks = (int)((px + kWgradChunk - 1) / kWgradChunk);
+    RELO_CUDA(launch_wgrad_reduce(b.partial, chunks, kRegCoutPad[l], kRegCinPad[l], kRegCin[l], kRegCout[l],
+                                  r->d_g + r->w_off[l], s));
+    RELO_CUDA(launch_bias_grad(g, px, gs, kRegCout[l], b.bias_scratch, r->d_g + r->b_off[l], s));
+    if (l > 0) {
+      ConvArgs a{};
+      a.in = g;
+      a.w = r->d_wt[l];
+      a.mask = b.act[l];
+      a.out = b.gpre[l - 1];
+      a.B = n;
+      a.Hi = Hs[l];
+      a.Wi = Ws[l];
+      a.Hs = Hs[l + 1];
+      a.Ws = Ws[l + 1];
+      a.Ho = Hs[l];
+      a.Wo = Ws[l];
+      a.stride = 1;
+      a.upsample = kRegStride[l] == 2;
+      if (!a.upsample) {
+        a.Hi = Hs[l + 1];
+        a.Wi = Ws[l + 1];
+      }
+      RELO_CUDA(launch_conv(gs, 8, a, r->n_sms, s));
+      g = b.gpre[l - 1];
+      gs = 64;
+    }
+  }
+  return RELO_OK;
+}
+
+relo_status reg_check_size(int n, int W, int H) {
+  if (n < 1 || n > 4096) return fail(RELO_EINVAL, "image count outside [1, 4096]");
+  if (W < 8 || H < 8 || W % 8 || H % 8 || W > 8192 || H > 8192)
+    return fail(RELO_EINVAL, "regressor images must be multiples of 8 in [8, 8192] per side");
+  return RELO_OK;
+}
+
+relo_status reg_loss_and_grads(relo_regressor* r, const RegBuffers& b, const uint16_t* depth, const uint8_t* rgba,
+                               int n, const relo_intrinsics* in, const double* poses, cudaStream_t s) {
+  const int W = in->width, H = in->height, Wc = W / 8, Hc = H / 8;
+  RELO_CUDA(cudaMemcpyAsync(b.poses, poses, (size_t)n * 16 * sizeof(double), cudaMemcpyHostToDevice, s));
+  relo_status st = reg_forward(r, b, depth, rgba, n, W, H, s);
+  if (st) return st;
+  CellArgs ca{};
+  ca.depth = depth;
+  ca.poses = b.poses;
+  ca.n = n;
+  ca.W = W;
+  ca.H = H;
+  ca.Wc = Wc;
+  ca.Hc = Hc;
+  ca.fx = in->fx;
+  ca.fy = in->fy;
+  ca.cx = in->cx;
+  ca.cy = in->cy;
+  ca.ox = r->origin[0];
+  ca.oy = r->origin[1];
+  ca.oz = r->origin[2];
+  RELO_CUDA(launch_targets(ca, b.tgt, s));
+  RELO_CUDA(launch_loss(b.head, b.tgt, n * Wc * Hc, b.ghead, b.loss, s));
+  return reg_backward(r, b, n, W, H, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t relo_regressor_param_count(void) {
+  int64_t w[kRegLayers], b[kRegLayers], t = 0;
+  reg_offsets(w, b, &t);
+  return t;
+}
+
+relo_status relo_create_regressor(const float* params, uint64_t seed, const double origin[3], relo_regressor** out) {
+  if (!out) return fail(RELO_EINVAL, "out is null");
+  *out = nullptr;
+  relo_regressor* r = new relo_regressor();
+  reg_offsets(r->w_off, r->b_off, &r->n_params);
+  if (origin)
+    for (int k = 0; k < 3; ++k) r->origin[k] = origin[k];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&r->n_sms, cudaDevAttrMultiProcessorCount, dev);
+  std::vector<float> host((size_t)r->n_params, 0.f);
+  if (params) {
+    std::memcpy(host.data(), params, host.size() * sizeof(float));
+  } else {
+    // He-uniform weights from Philox (counter (4, layer, index)), head scaled by 0.1, zero biases
+    const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFu), k1 = (uint32_t)(seed >> 32);
+    for (int l = 0; l < kRegLayers; ++l) {
+      const float bound = std::sqrt(6.0f / (9.0f * kRegCin[l])) * (l == kRegLayers - 1 ? 0.1f : 1.0f);
+      const int64_t nw = 9LL * kRegCin[l] * kRegCout[l];
+      for (int64_t i = 0; i < nw; ++i) {
+        const uint4 x = philox4x32_10(make_uint4(4u, (uint32_t)l, (uint32_t)i, 0u), k0, k1);
+        host[r->w_off[l] + i] = ((float)(x.x >> 8) * (1.0f / 16777216.0f) * 2.0f - 1.0f) * bound;
+      }
+    }
+  }
+  bool ok = cudaMalloc(&r->d_p, r->n_params * 4) == cudaSuccess && cudaMalloc(&r->d_g, r->n_params * 4) == cudaSuccess &&
+            cudaMalloc(&r->d_m, r->n_params * 4) == cudaSuccess && cudaMalloc(&r->d_v, r->n_params * 4) == cudaSuccess;
+  for (int l = 0; ok && l < kRegLayers; ++l) {
+    ok = cudaMalloc(&r->d_wk[l], 9LL * kRegCoutPad[l] * kRegCinPad[l] * sizeof(bf16)) == cudaSuccess &&
+         cudaMalloc(&r->d_bias[l], 64 * sizeof(float)) == cudaSuccess;
+    if (ok && l > 0) ok = cudaMalloc(&r->d_wt[l], 9LL * kRegCin[l] * cout_pad_t(l) * sizeof(bf16)) == cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    relo_destroy_regressor(r);
+    return fail(RELO_ENOMEM, "device allocation for the regressor failed");
+  }
+  cudaError_t e = cudaMemcpy(r->d_p, host.data(), r->n_params * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(r->d_m, 0, r->n_params * 4);
+  if (e == cudaSuccess) e = cudaMemset(r->d_v, 0, r->n_params * 4);
+  if (e == cudaSuccess) e = cudaMemset(r->d_g, 0, r->n_params * 4);
+  if (e != cudaSuccess) {
+    relo_destroy_regressor(r);
+    return cuda_fail(e, "regressor upload");
+  }
+  relo_status st = reg_pack(r, 0);
+  if (st == RELO_OK && cudaDeviceSynchronize() != cudaSuccess) st = fail(RELO_ECUDA, "regressor packing failed");
+  if (st) {
+    relo_destroy_regressor(r);
+    return st;
+  }
+  *out = r;
+  return RELO_OK;
+}
+
+void relo_destroy_regressor(relo_regressor* r) {
+  if (!r) return;
+  cudaFree(r->d_p);
+  cudaFree(r->d_g);
+  cudaFree(r->d_m);
+  cudaFree(r->d_v);
+  for (int l = 0; l < kRegLayers; ++l) {
+    cudaFree(r->d_wk[l]);
+    cudaFree(r->d_wt[l]);
+    cudaFree(r->d_bias[l]);
+  }
+  delete r;
+}
+
+relo_status relo_regressor_get_params(const relo_regressor* r, float* params, float* grads) {
+  if (!r) return fail(RELO_EINVAL, "regressor is null");
+  if (params) RELO_CUDA(cudaMemcpy(params, r->d_p, r->n_params * 4, cudaMemcpyDeviceToHost));
+  if (grads) RELO_CUDA(cudaMemcpy(grads, r->d_g, r->n_params * 4, cudaMemcpyDeviceToHost));
+  return RELO_OK;
+}
+
+size_t relo_regressor_workspace_size(int32_t n, int32_t W, int32_t H, int32_t training) {
+  if (n < 1 || W < 8 || H < 8) return 0;
+  RegBuffers b;
+  reg_layout(nullptr, n, W, H, training != 0, b);
+  return b.bytes;
+}
+
+relo_status relo_regressor_forward(relo_regressor* r, const uint16_t* depth, const uint8_t* rgba, int32_t n,
+                                   int32_t W, int32_t H, float* out, void* ws, size_t ws_bytes, relo_stream stream) {
+  if (!r || !depth || !rgba || !out || !ws) return fail(RELO_EINVAL, "null argument");
+  relo_status st = reg_check_size(n, W, H);
+  if (st) return st;
+  RegBuffers b;
+  reg_layout(nullptr, n, W, H, false, b);
+  if (b.bytes > ws_bytes || ((uintptr_t)ws & 255)) return fail(RELO_EINVAL, "workspace too small or misaligned");
+  reg_layout((char*)ws, n, W, H, false, b);
+  cudaStream_t s = (cudaStream_t)stream;
+  st = reg_forward(r, b, depth, rgba, n, W, H, s);
+  if (st) return st;
+  RELO_CUDA(launch_head_copy(b.head, (long)n * (W / 8) * (H / 8), out, s));
+  return RELO_OK;
+}
+
+relo_status relo_regressor_gradients(relo_regressor* r, const uint16_t* depth, const uint8_t* rgba, int32_t n,
+                                     const relo_intrinsics* intr, const double* poses_host, float* loss_dev, void* ws,
+                                     size_t ws_bytes, relo_stream stream) {
+  if (!r || !depth || !rgba || !intr || !poses_host || !ws) return fail(RELO_EINVAL, "null argument");
+  relo_status st = reg_check_size(n, intr->width, intr->height);
+  if (st) return st;
+  RegBuffers b;
+  reg_layout(nullptr, n, intr->width, intr->height, true, b);
+  if (b.bytes > ws_bytes || ((uintptr_t)ws & 255)) return fail(RELO_EINVAL, "workspace too small or misaligned");
+  reg_layout((char*)ws, n, intr->width, intr->height, true, b);
+  cudaStream_t s = (cudaStream_t)stream;
+  st = reg_loss_and_grads(r, b, depth, rgba, n, intr, poses_host, s);
+  if (st) return st;
+  if (loss_dev) RELO_CUDA(cudaMemcpyAsync(loss_dev, b.loss, sizeof(float), cudaMemcpyDeviceToDevice, s));
+  return RELO_OK;
+}
+
+relo_status relo_regressor_train_step(relo_regressor* r, const uint16_t* depth, const uint8_t* rgba, int32_t n,
+                                      const relo_intrinsics* intr, const double* poses_host, float lr,
+                                      float* loss_dev, void* ws, size_t ws_bytes, relo_stream stream) {
+  relo_status st = relo_regressor_gradients(r, depth, rgba, n, intr, poses_host, loss_dev, ws, ws_bytes, stream);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  r->t += 1;
+  RELO_CUDA(launch_adam(r->d_p, r->d_g, r->d_m, r->d_v, r->n_params, lr, r->t, s));
+  return reg_pack(r, s);
+}
+
+
+}  // extern "C"
+
+namespace {
+// Learned single view: [regressor buffers | cell forest | RANSAC on the cell grid]
+struct LearnedLayout {
+  RegBuffers reg;
+  float* modes;
+  uint8_t* n_modes;
+  float4* top;
+  uint16_t* leaves;
+  uint16_t* depth_lr;
+  size_t ransac_off;
+  Single ransac;
+  size_t bytes;
+  int L, D;
+};
+
+void learned_layout(char* base, int W, int H, const relo_ransac_params& p, LearnedLayout& l) {
+  reg_layout(base, 1, W, H, false, l.reg);
+  const int Wc = W / 8, Hc = H / 8, n = Wc * Hc;
+  l.D = 1;
+  while ((1 << l.D) < n) ++l.D;
+  l.L = 1 << l.D;
+  Carver c{base, l.reg.bytes};
+  l.modes = c.take<float>((size_t)l.L * kModeFloats);
+  l.n_modes = c.take<uint8_t>(l.L);
+  l.top = c.take<float4>(l.L);
+  l.leaves = c.take<uint16_t>(n);
+  l.depth_lr = c.take<uint16_t>(n);
+  l.ransac_off = (c.off + 255) & ~(size_t)255;
+  layout_single(base ? base + l.ransac_off : nullptr, Wc, Hc, p.n_hyps, p.batch, 1, l.ransac);
+  l.bytes = l.ransac_off + l.ransac.bytes;
+}
+
+relo_intrinsics coarse_intrinsics(const relo_intrinsics& in) {
+  relo_intrinsics c = in;
+  c.width = in.width / 8;
+  c.height = in.height / 8;
+  c.fx = in.fx / 8.0;
+  c.fy = in.fy / 8.0;
+  c.cx = (in.cx - 4.0) / 8.0;
+  c.cy = (in.cy - 4.0) / 8.0;
+  return c;
+}
+}  // namespace
+
+extern "C" {
+
+size_t relo_regressor_relocalise_workspace_size(int32_t W, int32_t H, const relo_ransac_params* p) {
+  if (!p || W < 8 || H < 8 || W % 8 || H % 8) return 0;
+  LearnedLayout l;
+  learned_layout(nullptr, W, H, *p, l);
+  return l.bytes;
+}
+
+relo_status relo_regressor_relocalise(relo_regressor* r, const uint16_t* depth, const uint8_t* rgba,
+                                      const relo_intrinsics* intr, const relo_ransac_params* p, void* ws,
+                                      size_t ws_bytes, relo_pose_result* result, relo_stream stream) {
+  if (!r || !depth || !rgba || !intr || !p || !ws || !result) return fail(RELO_EINVAL, "null argument");
+  relo_status st = reg_check_size(1, intr->width, intr->height);
+  if (st) return st;
+  st = check_params(p);
+  if (st) return st;
+  if (((uintptr_t)ws & 255) != 0) return fail(RELO_EINVAL, "workspace must be 256-byte aligned");
+  LearnedLayout l;
+  learned_layout(nullptr, intr->width, intr->height, *p, l);
+  if (l.bytes > ws_bytes) return fail(RELO_EINVAL, "workspace too small");
+  learned_layout((char*)ws, intr->width, intr->height, *p, l);
+  cudaStream_t s = (cudaStream_t)stream;
+  st = reg_forward(r, l.reg, depth, rgba, 1, intr->width, intr->height, s);
+  if (st) return st;
+  CellForestArgs ca{};
+  ca.out = l.reg.head;
+  ca.depth = depth;
+  ca.W = intr->width;
+  ca.H = intr->height;
+  ca.Wc = intr->width / 8;
+  ca.Hc = intr->height / 8;
+  ca.L = l.L;
+  ca.ox = (float)r->origin[0];
+  ca.oy = (float)r->origin[1];
+  ca.oz = (float)r->origin[2];
+  ca.modes = l.modes;
+  ca.n_modes = l.n_modes;
+  ca.top = l.top;
+  ca.leaves = l.leaves;
+  ca.depth_lr = l.depth_lr;
+  RELO_CUDA(launch_cell_forest(ca, s));
+  ForestView fv{};
+  fv.modes = l.modes;
+  fv.n_modes = l.n_modes;
+  fv.top = l.top;
+  fv.T = 1;
+  fv.D = l.D;
+  fv.M = 1;
+  const relo_intrinsics ci = coarse_intrinsics(*intr);
+  Single sr;
+  st = single_setup_view(fv, l.depth_lr, l.leaves, &ci, p, (char*)ws + l.ransac_off, ws_bytes - l.ransac_off, sr);
+  if (st) return st;
+  return single_run(sr, p, result, s);
 }
 
 }  // extern "C"

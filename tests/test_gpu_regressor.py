@@ -1,0 +1,190 @@
+"""GPU parity of the learned regressor (BF16 tensor-core convolutions, FP32 accumulation)
+against the FP64 oracle: forward output, loss and per-layer gradients on the same operands
+(relative L2 <= 1e-2 forward, gradient cosine >= 0.999 per layer), a short training run, and the
+learned RANSAC against the oracle's RANSAC on the same cell grid."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import regressor as R
+from paper_1801_08361_gb300 import binding as B
+from paper_1801_08361_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+ORIGIN = (2.0, 2.0, 1.5)
+
+
+def _u16(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint16).view(np.int16)).to(DEV)
+
+
+def _bf16(a):
+    """Round to the nearest bfloat16 (ties to even): the value the tensor cores multiply."""
+    u = np.asarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _operands(params: R.Params, x):
+    """The oracle's inputs for a like-for-like comparison: the kernels multiply BF16 copies of
+    the FP32 master weights and of the input (biases stay FP32), so the FP64 oracle is given
+    exactly those values; rounding the weights alone moves layer-1 gradients by ~1 % on a
+    64 x 48 view, far above the parity bar."""
+    pq = _unflat(_flat(params), params)
+    return R.Params([_bf16(w) for w in pq.w], list(pq.b)), _bf16(x)
+
+
+def _flat(params: R.Params):
+    return np.concatenate([p.reshape(-1) for p in params.flat()]).astype(np.float32)
+
+
+def _unflat(flat, like: R.Params):
+    out, off = [], 0
+    for p in like.flat():
+        out.append(flat[off:off + p.size].reshape(p.shape).astype(np.float64))
+        off += p.size
+    return R.Params(out[0::2], out[1::2])
+
+
+@pytest.fixture(scope="module")
+def views(room, oracle_room):
+    world, _ = room
+    intr = synth.Intrinsics.for_size(64, 48)
+    poses = synth.training_poses(world, 2, seed=91)
+    ds, cs = zip(*[oracle_room.raycast(intr, P) for P in poses])
+    return intr, poses, np.stack(ds), np.stack(cs)
+
+
+@pytest.fixture(scope="module")
+def params():
+    p = R.init_params(5)
+    rng = np.random.default_rng(6)
+    for b in p.b:
+        b += rng.normal(0, 0.05, b.shape)
+    return p
+
+
+def test_forward_matches_oracle(views, params):
+    intr, poses, d, c = views
+    reg = B.Regressor(_flat(params), origin=ORIGIN)
+    n = d.shape[0]
+    out = torch.zeros((n, 6, 8, 4), dtype=torch.float32, device=DEV)
+    ws = torch.empty(B.regressor_workspace_size(n, 64, 48, False), dtype=torch.uint8, device=DEV)
+    B.regressor_forward(reg, _u16(d), torch.from_numpy(c).to(DEV), out, ws)
+    torch.cuda.synchronize()
+    pq, x = _operands(params, np.stack([R.network_input(d[i], c[i]) for i in range(n)]))
+    want, _ = R.forward(pq, x)
+    got = out.cpu().numpy()
+    rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert rel <= 1e-2, rel
+
+
+def _forward_bf16_storage(params: R.Params, x):
+    """The oracle's layers composed the way the kernels store activations: each layer computed in
+    FP64 from its (BF16) input, its ReLU output rounded to BF16 before the next layer reads it."""
+    acts, h = [x], x
+    for l in range(len(params.w)):
+        z = R.conv3x3(h, params.w[l], params.b[l], R.STRIDES[l])
+        h = _bf16(np.maximum(z, 0.0)) if l < len(params.w) - 1 else z
+        acts.append(h)
+    return h, acts
+
+
+def _gpu_gradients(views, params):
+    intr, poses, d, c = views
+    reg = B.Regressor(_flat(params), origin=ORIGIN)
+    n = d.shape[0]
+    ws = torch.empty(B.regressor_workspace_size(n, 64, 48, True), dtype=torch.uint8, device=DEV)
+    loss = torch.zeros(1, dtype=torch.float32, device=DEV)
+    B.regressor_gradients(reg, _u16(d), torch.from_numpy(c).to(DEV), intr, poses, ws, loss)
+    torch.cuda.synchronize()
+    return float(loss.item()), _unflat(reg.grads(), params)
+
+
+def _oracle_gradients(views, params, bf16_storage):
+    intr, poses, d, c = views
+    n = d.shape[0]
+    pq, x = _operands(params, np.stack([R.network_input(d[i], c[i]) for i in range(n)]))
+    out, acts = _forward_bf16_storage(pq, x) if bf16_storage else R.forward(pq, x)
+    tg = [R.cell_targets(d[i], intr, poses[i], ORIGIN) for i in range(n)]
+    lo, g = R.loss_and_grad_output(out, np.stack([t[0] for t in tg]), np.stack([t[1] for t in tg]))
+    return lo, R.backward(pq, acts, g)
+
+
+def _cosines(got, want):
+    out = []
+    for gw, ww, gb, wb in zip(got.w, want.w, got.b, want.b):
+        a, b = np.concatenate([gw.ravel(), gb.ravel()]), np.concatenate([ww.ravel(), wb.ravel()])
+        out.append(float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b))))
+    return out
+
+
+def test_gradients_match_oracle_stage_isolated(views, params):
+    """Each layer's gradients against the FP64 oracle evaluated on the same operands the kernels
+    use: BF16 weights, input and stored activations (cosine >= 0.999 per layer)."""
+    lg, got = _gpu_gradients(views, params)
+    lo, want = _oracle_gradients(views, params, bf16_storage=True)
+    assert abs(lg - lo) <= 1e-3 * abs(lo)
+    cos = _cosines(got, want)
+    assert min(cos) >= 0.999, cos
+
+
+def test_gradients_against_the_fp64_network(views, params):
+    """End to end against the FP64 network with BF16 weights and input: storing activations in
+    BF16 costs up to ~1 % (cosine ~0.994) in the first layers' gradients on a 64 x 48 view, as the
+    same storage rounding applied inside the oracle reproduces; the bar is cosine >= 0.99."""
+    lg, got = _gpu_gradients(views, params)
+    lo, want = _oracle_gradients(views, params, bf16_storage=False)
+    assert abs(lg - lo) <= 1e-2 * abs(lo)
+    cos = _cosines(got, want)
+    assert min(cos) >= 0.99, cos
+
+
+def test_training_reduces_loss(views):
+    intr, poses, d, c = views
+    reg = B.Regressor(seed=3, origin=ORIGIN)
+    n = d.shape[0]
+    ws = torch.empty(B.regressor_workspace_size(n, 64, 48, True), dtype=torch.uint8, device=DEV)
+    loss = torch.zeros(1, dtype=torch.float32, device=DEV)
+    dd, cc = _u16(d), torch.from_numpy(c).to(DEV)
+    first = None
+    for step in range(60):
+        B.regressor_train_step(reg, dd, cc, intr, poses, 1e-3, ws, loss)
+        torch.cuda.synchronize()
+        if first is None:
+            first = float(loss.item())
+    assert float(loss.item()) < first - 1.0
+
+
+def test_learned_ransac_matches_oracle_on_the_cell_grid(room, oracle_room):
+    """The learned path's RANSAC (relo_regressor_relocalise) against the oracle's RANSAC on the
+    cell forest built from the same network output."""
+    world, _ = room
+    intr = synth.Intrinsics.for_size(320, 240)
+    reg = B.Regressor(seed=4, origin=ORIGIN)
+    P = synth.training_poses(world, 2, seed=93)[0]
+    d, c = oracle_room.raycast(intr, P)
+    dd, cc = _u16(d)[None], torch.from_numpy(c).to(DEV)[None]
+    out = torch.zeros((1, 30, 40, 4), dtype=torch.float32, device=DEV)
+    ws = torch.empty(B.regressor_workspace_size(1, 320, 240, False), dtype=torch.uint8, device=DEV)
+    B.regressor_forward(reg, dd, cc, out, ws)
+    prm = B.ransac_params(n_hyps=32, batch=64, seed=2, max_tries=2000)
+    wsr = torch.empty(B.regressor_relocalise_workspace_size(320, 240, prm), dtype=torch.uint8, device=DEV)
+    res = torch.zeros(B.RESULT_BYTES, dtype=torch.uint8, device=DEV)
+    B.regressor_relocalise(reg, dd[0], cc[0], intr, prm, wsr, res)
+    torch.cuda.synchronize()
+    r = B.result_from_bytes(res)
+    o = out.cpu().numpy()[0].astype(np.float64)
+    dl, ci = R.cell_view(d, intr)
+    forest, leaves = R.cell_forest(o, ORIGIN, dl > 0)
+    ro = oracle.preemptive_ransac(dl, ci, leaves, forest, oracle.RansacParams(n_hyps=32, batch=64, seed=2,
+                                                                              max_tries=2000))
+    assert r["n_valid"] == int((dl > 0).sum())
+    assert bool(r["status"] == 0) == ro["valid"]
+    if ro["valid"]:
+        assert r["hypothesis"] == ro["index"]
+        assert np.abs(r["pose"][:3] - ro["pose"][:3]).max() < 1e-3
