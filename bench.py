@@ -43,15 +43,16 @@ K_HYPS, B_PIX = 1024, 64
 TRAIN_PER_ROOM = 16
 L2_FLUSH_BYTES = 512 << 20
 
-# Algorithmic bytes per unit (stated in DESIGN.md, "Roofline"): per query pixel the raycast
-# must write depth (2 B) + colour (4 B) and the verification raycast must read D_b (2 B) and
-# each touches the distinct scene data its samples need; the per-pixel scene-data figures below
-# are the oracle's exact counts of distinct voxels (4 B tsdf, 4 B colour) and block-table
-# entries (16 B) touched, averaged over 8 query views of this workload
-# (oracle/algorithmic_bytes.py).
+# Algorithmic bytes per unit: per query pixel the raycast must write depth (2 B) + colour (4 B)
+# and the verification raycast must read D_b (2 B); each touches the distinct scene data its
+# samples need. The per-pixel scene-data figures below are the oracle's exact counts of distinct
+# voxels (4 B tsdf, 4 B colour) and block-table entries (16 B) touched, averaged over 8 query views
+# of this workload (oracle/algorithmic_bytes.py). A verification stage is its raycast plus a
+# one-block-per-attempt decision whose bytes are negligible.
 ALG_BYTES_PER_PIXEL = {
     "query_raycast": 50.66,
-    "verify_raycast": 35.87,
+    "forest_verify": 35.87,
+    "learned_verify": 35.87,
 }
 
 
@@ -381,7 +382,7 @@ N_SMS = 152
 
 
 def roofline(kernel, avg_ms, attempts, tries_per_launch, clocks):
-    if kernel == "hypotheses":
+    if kernel in ("forest_hypotheses", "learned_hypotheses"):
         mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
         peak = IMAD_PER_CLK_SM * N_SMS * mhz * 1e6 / IMAD_PER_TRY / 1e9      # G tries / s
         achieved = tries_per_launch / (avg_ms / 1000.0) / 1e9

@@ -193,7 +193,7 @@ typedef struct relo_ransac_params {
   uint64_t seed;
 } relo_ransac_params;
 
-/* Result of one attempt (device or host copy; 336 bytes). */
+/* Result of one attempt (device or host copy; 344 bytes). */
 typedef struct relo_pose_result {
   double pose_c2s[16];     /* proposed camera -> scene a pose */
   double rel_a_b[16];      /* a_T_b = P_a P_b^-1 (filled by relo_relocalise_batch) */
@@ -207,7 +207,13 @@ typedef struct relo_pose_result {
   uint64_t omega, omega_a, omega_b, omega_ab, sum_absdiff_mm; /* Sec. 3.3.1 verification counts */
   uint64_t tries;          /* hypothesis tries a sequential scan makes: sum over h of (kept try + 1), or
                               max_tries for a hypothesis without a passing try */
+  int32_t path;            /* batches: RELO_PATH_FOREST, RELO_PATH_LEARNED or RELO_PATH_FALLBACK */
+  int32_t pad;
 } relo_pose_result;
+
+#define RELO_PATH_FOREST 0    /* relocalised with the forest */
+#define RELO_PATH_LEARNED 1   /* relocalised (and verified, or without a forest) with the regressor */
+#define RELO_PATH_FALLBACK 2  /* the regressor's pose failed verification; the forest's result */
 
 /* Bytes of device workspace relo_ransac_relocalise needs for a width x height view. */
 size_t relo_ransac_workspace_size(int32_t width, int32_t height, const relo_ransac_params* p);
@@ -326,7 +332,7 @@ relo_status relo_verify(const relo_scene* scene_a, const relo_intrinsics* intr, 
  * ------------------------------------------------------------------------------------- */
 typedef struct relo_attempt {
   const relo_scene* scene_b;
-  const relo_forest* forest_a;
+  const relo_forest* forest_a;        /* nullable when regressor_a is set (then no fallback) */
   const relo_scene* scene_a;
   relo_intrinsics intr;
   double pose_b[16];        /* camera -> scene b pose of the query frame */
@@ -334,9 +340,15 @@ typedef struct relo_attempt {
   int32_t n_hyps;           /* overrides p->n_hyps when > 0 */
   int32_t pad;
   uint64_t seed;            /* Philox key of this attempt's RANSAC */
+  const relo_regressor* regressor_a;  /* nullable: relocalise with a's regressor first (learned path) */
 } relo_attempt;
 
-/* Workspace bytes for a batch (includes the query images and per-attempt RANSAC scratch). */
+/* Learned attempts (regressor_a set): the regressor's RANSAC runs on the cell grid (as in
+ * relo_regressor_relocalise) and its pose is verified; when verification fails and forest_a is
+ * set, the forest path runs for that attempt in the same launch sequence (each forest stage
+ * skips, on the device, the attempts whose learned pose verified) and its result is reported.
+ * All learned attempts of a batch must share one regressor and one image size.
+ * Workspace bytes for a batch (includes the query images and per-attempt RANSAC scratch). */
 size_t relo_batch_workspace_size(const relo_attempt* attempts_host, int32_t n, const relo_ransac_params* p);
 
 /* Run n attempts.  results_host receives n results (the call synchronises the stream).
@@ -361,11 +373,14 @@ void relo_batch_destroy(relo_batch* batch);
 /* Stage timing, for roofline measurements.  Once enabled, relo_batch_run records CUDA events on
  * its stream at the stage boundaries; relo_batch_stage_ms writes the milliseconds each stage of
  * the last run took (call it after that run's stream has synchronised), in this order: query
- * raycast, forest evaluation, valid-pixel compaction, hypotheses, RANSAC rounds, finalise,
- * verification raycast, verification decision.  It returns the number of stages written (8),
- * or 0 if timing is off or capacity is too small. */
+ * raycast; learned pass: regressor forward and cell forests, compaction + hypotheses, rounds +
+ * finalise, verification; forest pass: forest evaluation, compaction + hypotheses, rounds +
+ * finalise, verification; merge.  It returns the number of stages written (10), or 0 if timing
+ * is off or capacity is too small. */
 relo_status relo_batch_enable_timing(relo_batch* batch, int32_t enable);
 int32_t relo_batch_stage_ms(const relo_batch* batch, float* ms, int32_t capacity);
+/* Name of stage k of relo_batch_stage_ms ("" outside [0, 10)). */
+const char* relo_batch_stage_name(int32_t k);
 
 #ifdef __cplusplus
 }

@@ -48,7 +48,7 @@ class PoseResult(ctypes.Structure):
     _fields_ = [("pose_c2s", c_dbl * 16), ("rel_a_b", c_dbl * 16), ("energy", c_dbl), ("n_inliers", c_i32),
                 ("status", c_i32), ("verified", c_i32), ("n_valid", c_i32), ("hypothesis", c_i32),
                 ("n_rounds", c_i32), ("omega", c_u64), ("omega_a", c_u64), ("omega_b", c_u64),
-                ("omega_ab", c_u64), ("sum_absdiff_mm", c_u64), ("tries", c_u64)]
+                ("omega_ab", c_u64), ("sum_absdiff_mm", c_u64), ("tries", c_u64), ("path", c_i32), ("pad", c_i32)]
 
     def to_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("pose_c2s", "rel_a_b")}
@@ -59,7 +59,8 @@ class PoseResult(ctypes.Structure):
 
 class Attempt(ctypes.Structure):
     _fields_ = [("scene_b", c_vp), ("forest_a", c_vp), ("scene_a", c_vp), ("intr", Intrinsics),
-                ("pose_b", c_dbl * 16), ("noise_dev", c_vp), ("n_hyps", c_i32), ("pad", c_i32), ("seed", c_u64)]
+                ("pose_b", c_dbl * 16), ("noise_dev", c_vp), ("n_hyps", c_i32), ("pad", c_i32), ("seed", c_u64),
+                ("regressor_a", c_vp)]
 
 
 RESULT_BYTES = ctypes.sizeof(PoseResult)
@@ -112,10 +113,12 @@ _SIGS = {
                                           c_vp, ctypes.c_size_t, c_vp, c_vp]),
     "relo_batch_enable_timing": (c_i32, [c_vp, c_i32]),
     "relo_batch_stage_ms": (c_i32, [c_vp, ctypes.POINTER(ctypes.c_float), c_i32]),
+    "relo_batch_stage_name": (ctypes.c_char_p, [c_i32]),
 }
 
-STAGES = ["query_raycast", "forest_eval", "compact", "hypotheses", "ransac_rounds", "finalise", "verify_raycast",
-          "verify_decide"]
+STAGES = ["query_raycast", "learned_forward", "learned_hypotheses", "learned_rounds", "learned_verify", "forest_eval",
+          "forest_hypotheses", "forest_rounds", "forest_verify", "merge"]
+PATH_FOREST, PATH_LEARNED, PATH_FALLBACK = 0, 1, 2
 
 EXPORTED = sorted(_SIGS)
 
@@ -324,11 +327,14 @@ def result_from_bytes(t) -> dict:
 
 
 def make_attempts(items) -> "ctypes.Array":
-    """items: dicts with scene_b, forest_a, scene_a, intr, pose_b, noise (tensor or None), n_hyps, seed."""
+    """items: dicts with scene_b, scene_a, forest_a and/or regressor_a, intr, pose_b, noise (tensor or
+    None), n_hyps, seed."""
     arr = (Attempt * len(items))()
     for i, it in enumerate(items):
         a = arr[i]
-        a.scene_b, a.forest_a, a.scene_a = it["scene_b"].handle, it["forest_a"].handle, it["scene_a"].handle
+        a.scene_b, a.scene_a = it["scene_b"].handle, it["scene_a"].handle
+        a.forest_a = None if it.get("forest_a") is None else it["forest_a"].handle
+        a.regressor_a = None if it.get("regressor_a") is None else it["regressor_a"].handle
         a.intr = intrinsics(it["intr"])
         a.pose_b = _pose(it["pose_b"])
         a.noise_dev = None if it.get("noise") is None else it["noise"].data_ptr()
@@ -370,9 +376,9 @@ class Batch:
         _check(lib().relo_batch_enable_timing(self.handle, 1 if on else 0))
 
     def stage_ms(self) -> dict:
-        buf = (ctypes.c_float * 8)()
-        n = lib().relo_batch_stage_ms(self.handle, buf, 8)
-        return {STAGES[k]: float(buf[k]) for k in range(n)}
+        buf = (ctypes.c_float * len(STAGES))()
+        n = lib().relo_batch_stage_ms(self.handle, buf, len(STAGES))
+        return {lib().relo_batch_stage_name(k).decode(): float(buf[k]) for k in range(n)}
 
     def __del__(self):
         if getattr(self, "handle", None) and _LIB is not None:

@@ -16,8 +16,8 @@
 
 using namespace relo;
 
-static_assert(sizeof(relo_pose_result) == 336, "relo_pose_result layout is part of the ABI");
-static_assert(sizeof(relo_attempt) == 232, "relo_attempt layout is part of the ABI");
+static_assert(sizeof(relo_pose_result) == 344, "relo_pose_result layout is part of the ABI");
+static_assert(sizeof(relo_attempt) == 240, "relo_attempt layout is part of the ABI");
 static_assert(sizeof(relo_intrinsics) == 56, "relo_intrinsics layout is part of the ABI");
 
 namespace {
@@ -106,6 +106,8 @@ void fill_ransac_job(RansacJob& j, const ForestView& fv, const uint16_t* depth, 
   j.inlier_dist = p.inlier_dist;
   j.key0 = (uint32_t)(seed & 0xFFFFFFFFu);
   j.key1 = (uint32_t)(seed >> 32);
+  j.vW = in.width;
+  j.vH = in.height;
 }
 
 // Alive / survivor prefix tables for rounds 0..R-1 (each n_jobs + 1 ints).
@@ -138,176 +140,48 @@ void round_tables(const std::vector<int>& K, int R, std::vector<int32_t>& alive,
 }  // namespace
 
 // =============================================================================================
-// Batch plan (host side of relo_batch_*; also used by the single-attempt RANSAC entry points)
+// A RANSAC pass: every stage launched once over a set of jobs (one job for the single-view entry
+// points, many for batches).
 // =============================================================================================
-struct relo_batch {
-  int n = 0;
-  int R = 0;
-  bool full = false;          // full attempts (render + forest + RANSAC + verify) or RANSAC only
-  RayJob* d_query = nullptr;
-  ForestJob* d_forest = nullptr;
-  RansacJob* d_ransac = nullptr;
-  RayJob* d_verify = nullptr;
+namespace {
+
+struct RansacPass {
+  RansacJob* d_jobs = nullptr;
+  int n = 0, R = 0, chunks = 0, hyps = 0;
   int32_t* d_alive_prefix = nullptr;
   int32_t* d_surv_prefix = nullptr;
-  relo_pose_result* d_results = nullptr;
   std::vector<int> tot_alive, tot_surv;
-  int query_tiles = 0, verify_tiles = 0, chunks = 0, hyps = 0, max_trees = 1;
-  int64_t pixels = 0;
-  int32_t* d_errs = nullptr;
-  int launches = 0;
-  bool timing = false;
-  cudaEvent_t ev[9] = {};
-  ~relo_batch() {
-    for (cudaEvent_t& e : ev)
-      if (e) cudaEventDestroy(e);
-  }
 };
 
-namespace {
-constexpr int kStages = 8;
-}  // namespace
-
-namespace {
-
-struct Layout {
-  size_t bytes = 0;
-};
-
-// Lays out (base == nullptr: sizes only) the workspace of a batch.  Fills host job arrays.
-relo_status layout_batch(const relo_attempt* at, int n, const relo_ransac_params& p, char* base, size_t* bytes,
-                         std::vector<RayJob>& q, std::vector<ForestJob>& fj, std::vector<RansacJob>& rj,
-                         std::vector<RayJob>& vj, relo_batch* plan, std::vector<int32_t>& alive_tab,
-                         std::vector<int32_t>& surv_tab) {
-  Carver c{base, 0};
-  auto* d_query = c.take<RayJob>(n);
-  auto* d_forest = c.take<ForestJob>(n);
-  auto* d_ransac = c.take<RansacJob>(n);
-  auto* d_verify = c.take<RayJob>(n);
-  std::vector<int> K(n);
-  int R = 0;
-  for (int i = 0; i < n; ++i) {
-    K[i] = at[i].n_hyps > 0 ? at[i].n_hyps : p.n_hyps;
-    R = std::max(R, rounds_for(K[i]));
-  }
-  auto* d_alive = c.take<int32_t>((size_t)std::max(R, 1) * (n + 1));
-  auto* d_surv = c.take<int32_t>((size_t)std::max(R, 1) * (n + 1));
-  auto* d_results = c.take<relo_pose_result>(n);
-  auto* d_errs = c.take<int32_t>(n);
-  q.assign(n, RayJob{});
-  fj.assign(n, ForestJob{});
-  rj.assign(n, RansacJob{});
-  vj.assign(n, RayJob{});
-  int tiles = 0, chunks = 0, hyps = 0;
-  int64_t pixels = 0;
-  for (int i = 0; i < n; ++i) {
-    const relo_attempt& a = at[i];
-    const int W = a.intr.width, H = a.intr.height, T = a.forest_a->T;
-    const size_t n_pix = (size_t)W * H;
-    uint16_t* depth = c.take<uint16_t>(n_pix);
-    uint32_t* rgba = c.take<uint32_t>(n_pix);
-    uint16_t* leaves = c.take<uint16_t>(n_pix * T);
-    // query render of scene b
-    RayJob& r = q[i];
-    r = make_ray_job(a.scene_b->view, a.intr, a.pose_b);
-    r.noise = a.noise_dev;
-    r.depth = depth;
-    r.rgba = rgba;
-    r.tile_begin = tiles;
-    // forest of a
-    ForestJob& f = fj[i];
-    f.forest = a.forest_a->view;
-    f.depth = depth;
-    f.rgba = rgba;
-    f.leaves = leaves;
-    f.W = W;
-    f.H = H;
-    f.pixel_begin = pixels;
-    // RANSAC
-    RansacJob& j = rj[i];
-    fill_ransac_job(j, a.forest_a->view, depth, leaves, a.intr, p, K[i], a.seed);
-    carve_ransac(c, j, W, H, K[i], p.batch, j.n_rounds, T);
-    j.err = d_errs ? d_errs + i : nullptr;
-    j.result = d_results + i;
-    j.chunk_begin = chunks;
-    j.hyp_begin = hyps;
-    j.has_pose_b = 1;
-    for (int k = 0; k < 16; ++k) j.pose_b[k] = a.pose_b[k];
-    // verification render of scene a at the proposed pose, compared with the query depth
-    RayJob& v = vj[i];
-    v = make_ray_job(a.scene_a->view, a.intr, nullptr);
-    v.pose_dev = d_results ? d_results[i].pose_c2s : nullptr;
-    v.status_dev = d_results ? &d_results[i].status : nullptr;
-    v.depth_ref = depth;
-    v.counts = d_results ? (unsigned long long*)&d_results[i].omega_a : nullptr;
-    v.err = j.err;
-    v.tile_begin = tiles;
-    r.err = j.err;
-    tiles += ray_tiles(W, H);
-    pixels += (int64_t)n_pix;
-    chunks += (int)((n_pix + kCompactChunk - 1) / kCompactChunk);
-    hyps += K[i];
-  }
-  *bytes = c.off;
-  if (plan) {
-    plan->n = n;
-    plan->R = R;
-    plan->d_query = d_query;
-    plan->d_forest = d_forest;
-    plan->d_ransac = d_ransac;
-    plan->d_verify = d_verify;
-    plan->d_alive_prefix = d_alive;
-    plan->d_surv_prefix = d_surv;
-    plan->d_results = d_results;
-    plan->query_tiles = plan->verify_tiles = tiles;
-    plan->max_trees = 1;
-    for (int i = 0; i < n; ++i) plan->max_trees = std::max(plan->max_trees, at[i].forest_a->T);
-    plan->pixels = pixels;
-    plan->chunks = chunks;
-    plan->hyps = hyps;
-    round_tables(K, R, alive_tab, surv_tab, plan->tot_alive, plan->tot_surv);
-    plan->d_errs = d_errs;
-  }
-  return RELO_OK;
-}
-
-relo_status check_attempts(const relo_attempt* at, int n, const relo_ransac_params* p) {
-  if (!at || n < 1) return fail(RELO_EINVAL, "need at least one attempt");
-  relo_status st = check_params(p);
-  if (st) return st;
-  for (int i = 0; i < n; ++i) {
-    if (!at[i].scene_b || !at[i].scene_a || !at[i].forest_a) return fail(RELO_EINVAL, "attempt has a null handle");
-    st = check_intr(&at[i].intr);
-    if (st) return st;
-    if (at[i].n_hyps < 0 || at[i].n_hyps > 4096) return fail(RELO_EINVAL, "attempt n_hyps outside [0, 4096]");
-  }
-  return RELO_OK;
-}
-
-// Records stage boundary k when timing is on (events 0..8 bracket the 8 stages).
-cudaError_t mark(relo_batch* b, int k, cudaStream_t s) {
-  return b->timing ? cudaEventRecord(b->ev[k], s) : cudaSuccess;
-}
-
-relo_status run_ransac_stages(relo_batch* b, cudaStream_t s, int* launches) {
+// ev_hyp / ev_rounds (nullable) are recorded after the hypotheses and after the rounds.
+relo_status run_pass(const RansacPass& p, cudaStream_t s, int* launches, cudaEvent_t ev_hyp, cudaEvent_t ev_rounds) {
   int L = 0;
-  RELO_CUDA(launch_compact(b->d_ransac, b->n, b->chunks, s));
-  L += 2;
-  RELO_CUDA(mark(b, 3, s));
-  RELO_CUDA(launch_hypotheses(b->d_ransac, b->n, b->hyps, s));
-  L += 2;
-  RELO_CUDA(mark(b, 4, s));
-  for (int r = 0; r < b->R; ++r) {
-    if (b->tot_alive[r] == 0) continue;
-    RELO_CUDA(launch_round(b->d_ransac, b->n, r, b->d_alive_prefix + (size_t)r * (b->n + 1), b->tot_alive[r],
-                           b->d_surv_prefix + (size_t)r * (b->n + 1), b->tot_surv[r], s));
+  if (p.n > 0) {
+    RELO_CUDA(launch_compact(p.d_jobs, p.n, p.chunks, s));
+    RELO_CUDA(launch_hypotheses(p.d_jobs, p.n, p.hyps, s));
+    L += 4;
+  }
+  if (ev_hyp) RELO_CUDA(cudaEventRecord(ev_hyp, s));
+  for (int r = 0; r < p.R; ++r) {
+    if (p.tot_alive[r] == 0) continue;
+    RELO_CUDA(launch_round(p.d_jobs, p.n, r, p.d_alive_prefix + (size_t)r * (p.n + 1), p.tot_alive[r],
+                           p.d_surv_prefix + (size_t)r * (p.n + 1), p.tot_surv[r], s));
     L += 5;
   }
-  RELO_CUDA(mark(b, 5, s));
-  RELO_CUDA(launch_finalise(b->d_ransac, b->n, s));
-  L += 1;
-  *launches = L;
+  if (p.n > 0) {
+    RELO_CUDA(launch_finalise(p.d_jobs, p.n, s));
+    L += 1;
+  }
+  if (ev_rounds) RELO_CUDA(cudaEventRecord(ev_rounds, s));
+  *launches += L;
   return RELO_OK;
+}
+
+int pass_launches(const RansacPass& p) {
+  int L = p.n > 0 ? 5 : 0;
+  for (int r = 0; r < p.R; ++r)
+    if (p.tot_alive[r] > 0) L += 5;
+  return L;
 }
 
 }  // namespace
@@ -777,11 +651,11 @@ relo_status single_run(Single& s, const relo_ransac_params* p, relo_pose_result*
   s.job.result = result;
   std::vector<int> K(1, p->n_hyps);
   std::vector<int32_t> at, su;
-  relo_batch b;
+  RansacPass b;
   b.n = 1;
   b.R = rounds_for(p->n_hyps);
   round_tables(K, std::max(b.R, 1), at, su, b.tot_alive, b.tot_surv);
-  b.d_ransac = s.d_job;
+  b.d_jobs = s.d_job;
   b.d_alive_prefix = s.d_alive;
   b.d_surv_prefix = s.d_surv;
   b.chunks = s.chunks;
@@ -791,7 +665,7 @@ relo_status single_run(Single& s, const relo_ransac_params* p, relo_pose_result*
   RELO_CUDA(cudaMemcpyAsync(s.d_surv, su.data(), su.size() * 4, cudaMemcpyHostToDevice, cs));
   RELO_CUDA(cudaMemsetAsync(s.job.err, 0, sizeof(int32_t), cs));
   int launches = 0;
-  return run_ransac_stages(&b, cs, &launches);
+  return run_pass(b, cs, &launches, nullptr, nullptr);
 }
 }  // namespace
 
@@ -918,124 +792,6 @@ relo_status relo_verify(const relo_scene* scene_a, const relo_intrinsics* intr, 
   RELO_CUDA(launch_raycast(nullptr, 1, &v, ray_tiles(intr->width, intr->height), false, true, cs));
   RELO_CUDA(launch_verify_decide_one(result, (uint64_t)intr->width * intr->height, cs));
   return RELO_OK;
-}
-
-// ---------------------------------------------------------------------------------------------
-// Batches
-// ---------------------------------------------------------------------------------------------
-size_t relo_batch_workspace_size(const relo_attempt* at, int32_t n, const relo_ransac_params* p) {
-  if (check_attempts(at, n, p) != RELO_OK) return 0;
-  std::vector<RayJob> q, v;
-  std::vector<ForestJob> fj;
-  std::vector<RansacJob> rj;
-  std::vector<int32_t> a, s;
-  size_t bytes = 0;
-  layout_batch(at, n, *p, nullptr, &bytes, q, fj, rj, v, nullptr, a, s);
-  return bytes;
-}
-
-relo_status relo_batch_prepare(const relo_attempt* at, int32_t n, const relo_ransac_params* p, void* ws,
-                               size_t ws_bytes, relo_batch** out) {
-  if (!out) return fail(RELO_EINVAL, "out is null");
-  *out = nullptr;
-  relo_status st = check_attempts(at, n, p);
-  if (st) return st;
-  if (!ws || ((uintptr_t)ws & 255) != 0) return fail(RELO_EINVAL, "workspace must be non-null and 256-byte aligned");
-  std::vector<RayJob> q, v;
-  std::vector<ForestJob> fj;
-  std::vector<RansacJob> rj;
-  std::vector<int32_t> atab, stab;
-  size_t bytes = 0;
-  layout_batch(at, n, *p, nullptr, &bytes, q, fj, rj, v, nullptr, atab, stab);
-  if (bytes > ws_bytes) return fail(RELO_EINVAL, "workspace too small");
-  relo_batch* b = new relo_batch();
-  b->full = true;
-  layout_batch(at, n, *p, (char*)ws, &bytes, q, fj, rj, v, b, atab, stab);
-  cudaError_t e = cudaMemcpy(b->d_query, q.data(), n * sizeof(RayJob), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(b->d_forest, fj.data(), n * sizeof(ForestJob), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(b->d_ransac, rj.data(), n * sizeof(RansacJob), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(b->d_verify, v.data(), n * sizeof(RayJob), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && !atab.empty())
-    e = cudaMemcpy(b->d_alive_prefix, atab.data(), atab.size() * 4, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && !stab.empty())
-    e = cudaMemcpy(b->d_surv_prefix, stab.data(), stab.size() * 4, cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) {
-    delete b;
-    return cuda_fail(e, "batch descriptors");
-  }
-  *out = b;
-  return RELO_OK;
-}
-
-relo_status relo_batch_run(relo_batch* b, relo_pose_result* results, relo_stream stream) {
-  if (!b || !b->full) return fail(RELO_EINVAL, "batch not prepared");
-  cudaStream_t s = (cudaStream_t)stream;
-  int L = 0;
-  RELO_CUDA(cudaMemsetAsync(b->d_errs, 0, b->n * sizeof(int32_t), s));
-  RELO_CUDA(mark(b, 0, s));
-  RELO_CUDA(launch_raycast(b->d_query, b->n, nullptr, b->query_tiles, true, false, s));
-  RELO_CUDA(mark(b, 1, s));
-  RELO_CUDA(launch_forest(b->d_forest, b->n, nullptr, b->pixels, s, b->max_trees));
-  RELO_CUDA(mark(b, 2, s));
-  L += 2;
-  int Lr = 0;
-  relo_status st = run_ransac_stages(b, s, &Lr);
-  if (st) return st;
-  L += Lr;
-  RELO_CUDA(mark(b, 6, s));
-  RELO_CUDA(launch_raycast(b->d_verify, b->n, nullptr, b->verify_tiles, false, true, s));
-  RELO_CUDA(mark(b, 7, s));
-  RELO_CUDA(launch_verify_decide(b->d_ransac, b->n, s));
-  RELO_CUDA(mark(b, 8, s));
-  L += 2;
-  if (results && results != b->d_results)
-    RELO_CUDA(cudaMemcpyAsync(results, b->d_results, b->n * sizeof(relo_pose_result), cudaMemcpyDeviceToDevice, s));
-  b->launches = L;
-  return RELO_OK;
-}
-
-int32_t relo_batch_launch_count(const relo_batch* b) {
-  if (!b) return 0;
-  int L = 2 + 2 + 2 + 1 + 2;  // render + forest, compaction, search + fit, finalise, verify + decide
-  for (int r = 0; r < b->R; ++r)
-    if (b->tot_alive[r] > 0) L += 5;
-  return L;
-}
-
-void relo_batch_destroy(relo_batch* b) { delete b; }
-
-relo_status relo_batch_enable_timing(relo_batch* b, int32_t enable) {
-  if (!b) return fail(RELO_EINVAL, "batch is null");
-  if (enable) {
-    for (cudaEvent_t& e : b->ev)
-      if (!e) RELO_CUDA(cudaEventCreate(&e));
-  }
-  b->timing = enable != 0;
-  return RELO_OK;
-}
-
-int32_t relo_batch_stage_ms(const relo_batch* b, float* ms, int32_t capacity) {
-  if (!b || !b->timing || !ms || capacity < kStages) return 0;
-  for (int k = 0; k < kStages; ++k)
-    if (cudaEventElapsedTime(&ms[k], b->ev[k], b->ev[k + 1]) != cudaSuccess) return 0;
-  return kStages;
-}
-
-relo_status relo_relocalise_batch(const relo_attempt* at, int32_t n, const relo_ransac_params* p, void* ws,
-                                  size_t ws_bytes, relo_pose_result* results_host, relo_stream stream) {
-  if (!results_host) return fail(RELO_EINVAL, "results is null");
-  relo_batch* b = nullptr;
-  relo_status st = relo_batch_prepare(at, n, p, ws, ws_bytes, &b);
-  if (st) return st;
-  st = relo_batch_run(b, nullptr, stream);
-  if (st == RELO_OK) {
-    cudaError_t e = cudaMemcpyAsync(results_host, b->d_results, n * sizeof(relo_pose_result), cudaMemcpyDeviceToHost,
-                                    (cudaStream_t)stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
-    if (e != cudaSuccess) st = cuda_fail(e, "batch results");
-  }
-  relo_batch_destroy(b);
-  return st;
 }
 
 }  // extern "C"
@@ -1458,6 +1214,7 @@ relo_status relo_regressor_relocalise(relo_regressor* r, const uint16_t* depth, 
   CellForestArgs ca{};
   ca.out = l.reg.head;
   ca.depth = depth;
+  ca.n = 1;
   ca.W = intr->width;
   ca.H = intr->height;
   ca.Wc = intr->width / 8;
@@ -1484,6 +1241,445 @@ relo_status relo_regressor_relocalise(relo_regressor* r, const uint16_t* depth, 
   st = single_setup_view(fv, l.depth_lr, l.leaves, &ci, p, (char*)ws + l.ransac_off, ws_bytes - l.ransac_off, sr);
   if (st) return st;
   return single_run(sr, p, result, s);
+}
+
+}  // extern "C"
+
+// =============================================================================================
+// Batches of whole attempts (Fig. 3 end to end).  Pass L (learned attempts): regressor forward,
+// cell forests, RANSAC on the cell grids, verification.  Pass F (forest attempts and the forest
+// fallbacks of learned attempts): forest evaluation, RANSAC, verification -- a fallback job skips
+// every stage on the device when its learned pose verified.  A merge kernel writes each attempt's
+// final result.  Every stage is one launch over all jobs of its pass.
+// =============================================================================================
+namespace {
+constexpr int kStages = 10;
+const char* const kStageNames[kStages] = {"query_raycast",   "learned_forward", "learned_hypotheses",
+                                          "learned_rounds",  "learned_verify",  "forest_eval",
+                                          "forest_hypotheses", "forest_rounds", "forest_verify",
+                                          "merge"};
+}  // namespace
+
+struct relo_batch {
+  int n = 0, nL = 0, nF = 0;
+  RayJob* d_query = nullptr;
+  RayJob* d_verify_L = nullptr;
+  RayJob* d_verify_F = nullptr;
+  ForestJob* d_forest = nullptr;
+  RansacPass passL, passF;
+  relo_pose_result* d_res_L = nullptr;
+  relo_pose_result* d_res_F = nullptr;
+  relo_pose_result* d_res = nullptr;
+  int32_t* d_kind = nullptr;
+  int32_t* d_errs = nullptr;  // nL + nF words
+  int query_tiles = 0, verify_L_tiles = 0, verify_F_tiles = 0, max_trees = 1;
+  int64_t forest_pixels = 0;
+  // learned pass
+  relo_regressor* reg = nullptr;
+  int lW = 0, lH = 0;
+  uint16_t* depth_L = nullptr;  // learned query images [nL][H][W] (contiguous)
+  uint32_t* rgba_L = nullptr;
+  RegBuffers regbuf;
+  CellForestArgs cells{};
+  bool timing = false;
+  cudaEvent_t ev[kStages + 1] = {};
+  ~relo_batch() {
+    for (cudaEvent_t& e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+};
+
+namespace {
+
+relo_status check_attempts(const relo_attempt* at, int n, const relo_ransac_params* p) {
+  if (!at || n < 1) return fail(RELO_EINVAL, "need at least one attempt");
+  relo_status st = check_params(p);
+  if (st) return st;
+  const relo_regressor* reg = nullptr;
+  int lw = 0, lh = 0;
+  for (int i = 0; i < n; ++i) {
+    const relo_attempt& a = at[i];
+    if (!a.scene_b || !a.scene_a) return fail(RELO_EINVAL, "attempt has a null scene");
+    if (!a.forest_a && !a.regressor_a) return fail(RELO_EINVAL, "attempt has neither a forest nor a regressor");
+    st = check_intr(&a.intr);
+    if (st) return st;
+    if (a.n_hyps < 0 || a.n_hyps > 4096) return fail(RELO_EINVAL, "attempt n_hyps outside [0, 4096]");
+    if (a.regressor_a) {
+      st = reg_check_size(1, a.intr.width, a.intr.height);
+      if (st) return st;
+      if (reg && (a.regressor_a != reg || a.intr.width != lw || a.intr.height != lh))
+        return fail(RELO_EINVAL, "learned attempts of a batch must share one regressor and one image size");
+      reg = a.regressor_a;
+      lw = a.intr.width;
+      lh = a.intr.height;
+    }
+  }
+  return RELO_OK;
+}
+
+struct HostJobs {
+  std::vector<RayJob> query, verify_L, verify_F;
+  std::vector<ForestJob> forest;
+  std::vector<RansacJob> ransac_L, ransac_F;
+  std::vector<int32_t> alive_L, surv_L, alive_F, surv_F, kind;
+};
+
+// Lays out (base == nullptr: sizes only) the workspace of a batch and fills the host job arrays.
+void layout_batch(const relo_attempt* at, int n, const relo_ransac_params& p, char* base, size_t* bytes,
+                  relo_batch& b, HostJobs& h) {
+  // attempt kinds and the learned group
+  std::vector<int> kind(n), iL(n, -1), iF(n, -1);
+  int nL = 0, nF = 0, lW = 0, lH = 0;
+  relo_regressor* reg = nullptr;
+  for (int i = 0; i < n; ++i) {
+    kind[i] = at[i].regressor_a ? (at[i].forest_a ? 2 : 1) : 0;
+    if (kind[i] != 0) {
+      iL[i] = nL++;
+      reg = const_cast<relo_regressor*>(at[i].regressor_a);
+      lW = at[i].intr.width;
+      lH = at[i].intr.height;
+    }
+    if (kind[i] != 1) iF[i] = nF++;
+  }
+  Carver c{base, 0};
+  b.n = n;
+  b.nL = nL;
+  b.nF = nF;
+  b.d_query = c.take<RayJob>(n);
+  b.d_verify_L = c.take<RayJob>(std::max(nL, 1));
+  b.d_verify_F = c.take<RayJob>(std::max(nF, 1));
+  b.d_forest = c.take<ForestJob>(std::max(nF, 1));
+  b.passL.d_jobs = c.take<RansacJob>(std::max(nL, 1));
+  b.passF.d_jobs = c.take<RansacJob>(std::max(nF, 1));
+  b.d_res_L = c.take<relo_pose_result>(n);
+  b.d_res_F = c.take<relo_pose_result>(n);
+  b.d_res = c.take<relo_pose_result>(n);
+  b.d_kind = c.take<int32_t>(n);
+  b.d_errs = c.take<int32_t>(nL + nF + 1);
+  std::vector<int> KL, KF;
+  for (int i = 0; i < n; ++i) {
+    const int K = at[i].n_hyps > 0 ? at[i].n_hyps : p.n_hyps;
+    if (iL[i] >= 0) KL.push_back(K);
+    if (iF[i] >= 0) KF.push_back(K);
+  }
+  int RL = 0, RF = 0;
+  for (int K : KL) RL = std::max(RL, rounds_for(K));
+  for (int K : KF) RF = std::max(RF, rounds_for(K));
+  b.passL.d_alive_prefix = c.take<int32_t>((size_t)std::max(RL, 1) * (nL + 1));
+  b.passL.d_surv_prefix = c.take<int32_t>((size_t)std::max(RL, 1) * (nL + 1));
+  b.passF.d_alive_prefix = c.take<int32_t>((size_t)std::max(RF, 1) * (nF + 1));
+  b.passF.d_surv_prefix = c.take<int32_t>((size_t)std::max(RF, 1) * (nF + 1));
+  // learned images first (contiguous for the batched forward), then the rest
+  uint16_t* depth_L = nullptr;
+  uint32_t* rgba_L = nullptr;
+  const int Wc = lW / 8, Hc = lH / 8, cells = Wc * Hc;
+  int D = 1;
+  while ((1 << D) < cells) ++D;
+  const int Lv = 1 << D;
+  if (nL > 0) {
+    depth_L = c.take<uint16_t>((size_t)nL * lW * lH);
+    rgba_L = c.take<uint32_t>((size_t)nL * lW * lH);
+    b.reg = reg;
+    b.lW = lW;
+    b.lH = lH;
+    b.depth_L = depth_L;
+    b.rgba_L = rgba_L;
+    RegBuffers rb;
+    reg_layout(nullptr, nL, lW, lH, false, rb);
+    char* rbase = c.take<char>(rb.bytes);
+    reg_layout(rbase, nL, lW, lH, false, b.regbuf);
+    CellForestArgs& ca = b.cells;
+    ca = CellForestArgs{};
+    ca.out = b.regbuf.head;
+    ca.depth = depth_L;
+    ca.n = nL;
+    ca.W = lW;
+    ca.H = lH;
+    ca.Wc = Wc;
+    ca.Hc = Hc;
+    ca.L = Lv;
+    ca.ox = (float)reg->origin[0];
+    ca.oy = (float)reg->origin[1];
+    ca.oz = (float)reg->origin[2];
+    ca.modes = c.take<float>((size_t)nL * Lv * kModeFloats);
+    ca.n_modes = c.take<uint8_t>((size_t)nL * Lv);
+    ca.top = c.take<float4>((size_t)nL * Lv);
+    ca.leaves = c.take<uint16_t>((size_t)nL * cells);
+    ca.depth_lr = c.take<uint16_t>((size_t)nL * cells);
+  }
+  h = HostJobs{};
+  h.query.assign(n, RayJob{});
+  h.verify_L.assign(nL, RayJob{});
+  h.verify_F.assign(nF, RayJob{});
+  h.forest.assign(nF, ForestJob{});
+  h.ransac_L.assign(nL, RansacJob{});
+  h.ransac_F.assign(nF, RansacJob{});
+  h.kind.assign(kind.begin(), kind.end());
+  int qt = 0, vtL = 0, vtF = 0, chL = 0, chF = 0, hyL = 0, hyF = 0, maxT = 1;
+  int64_t fpix = 0;
+  for (int i = 0; i < n; ++i) {
+    const relo_attempt& a = at[i];
+    const int W = a.intr.width, H = a.intr.height, K = a.n_hyps > 0 ? a.n_hyps : p.n_hyps;
+    const size_t n_pix = (size_t)W * H;
+    uint16_t* depth;
+    uint32_t* rgba;
+    if (iL[i] >= 0) {
+      depth = depth_L ? depth_L + (size_t)iL[i] * n_pix : nullptr;
+      rgba = rgba_L ? rgba_L + (size_t)iL[i] * n_pix : nullptr;
+    } else {
+      depth = c.take<uint16_t>(n_pix);
+      rgba = c.take<uint32_t>(n_pix);
+    }
+    RayJob& q = h.query[i];
+    q = make_ray_job(a.scene_b->view, a.intr, a.pose_b);
+    q.noise = a.noise_dev;
+    q.depth = depth;
+    q.rgba = rgba;
+    q.tile_begin = qt;
+    qt += ray_tiles(W, H);
+    if (iL[i] >= 0) {
+      const int j = iL[i];
+      ForestView fv{};
+      fv.modes = b.cells.modes ? b.cells.modes + (size_t)j * Lv * kModeFloats : nullptr;
+      fv.n_modes = b.cells.n_modes ? b.cells.n_modes + (size_t)j * Lv : nullptr;
+      fv.top = b.cells.top ? b.cells.top + (size_t)j * Lv : nullptr;
+      fv.T = 1;
+      fv.D = D;
+      fv.M = 1;
+      const relo_intrinsics ci = coarse_intrinsics(a.intr);
+      RansacJob& r = h.ransac_L[j];
+      fill_ransac_job(r, fv, b.cells.depth_lr ? b.cells.depth_lr + (size_t)j * cells : nullptr,
+                      b.cells.leaves ? b.cells.leaves + (size_t)j * cells : nullptr, ci, p, K, a.seed);
+      carve_ransac(c, r, Wc, Hc, K, p.batch, r.n_rounds, 1);
+      r.vW = W;
+      r.vH = H;
+      r.err = b.d_errs + j;
+      r.result = b.d_res_L + i;
+      r.chunk_begin = chL;
+      r.hyp_begin = hyL;
+      r.has_pose_b = 1;
+      for (int k = 0; k < 16; ++k) r.pose_b[k] = a.pose_b[k];
+      chL += (cells + kCompactChunk - 1) / kCompactChunk;
+      hyL += K;
+      RayJob& v = h.verify_L[j];
+      v = make_ray_job(a.scene_a->view, a.intr, nullptr);
+      v.pose_dev = b.d_res_L[i].pose_c2s;
+      v.status_dev = &b.d_res_L[i].status;
+      v.depth_ref = depth;
+      v.counts = (unsigned long long*)&b.d_res_L[i].omega_a;
+      v.err = r.err;
+      v.tile_begin = vtL;
+      vtL += ray_tiles(W, H);
+    }
+    if (iF[i] >= 0) {
+      const int j = iF[i];
+      const int T = a.forest_a->T;
+      maxT = std::max(maxT, T);
+      uint16_t* leaves = c.take<uint16_t>(n_pix * T);
+      const int32_t* skip = kind[i] == 2 ? &b.d_res_L[i].verified : nullptr;
+      ForestJob& f = h.forest[j];
+      f.forest = a.forest_a->view;
+      f.depth = depth;
+      f.rgba = rgba;
+      f.leaves = leaves;
+      f.W = W;
+      f.H = H;
+      f.pixel_begin = fpix;
+      f.skip = skip;
+      fpix += (int64_t)n_pix;
+      RansacJob& r = h.ransac_F[j];
+      fill_ransac_job(r, a.forest_a->view, depth, leaves, a.intr, p, K, a.seed);
+      carve_ransac(c, r, W, H, K, p.batch, r.n_rounds, T);
+      r.err = b.d_errs + nL + j;
+      r.result = b.d_res_F + i;
+      r.chunk_begin = chF;
+      r.hyp_begin = hyF;
+      r.has_pose_b = 1;
+      r.skip = skip;
+      for (int k = 0; k < 16; ++k) r.pose_b[k] = a.pose_b[k];
+      chF += (int)((n_pix + kCompactChunk - 1) / kCompactChunk);
+      hyF += K;
+      RayJob& v = h.verify_F[j];
+      v = make_ray_job(a.scene_a->view, a.intr, nullptr);
+      v.pose_dev = b.d_res_F[i].pose_c2s;
+      v.status_dev = &b.d_res_F[i].status;
+      v.depth_ref = depth;
+      v.counts = (unsigned long long*)&b.d_res_F[i].omega_a;
+      v.err = r.err;
+      v.tile_begin = vtF;
+      vtF += ray_tiles(W, H);
+    }
+  }
+  b.query_tiles = qt;
+  b.verify_L_tiles = vtL;
+  b.verify_F_tiles = vtF;
+  b.forest_pixels = fpix;
+  b.max_trees = maxT;
+  b.passL.n = nL;
+  b.passL.R = RL;
+  b.passL.chunks = chL;
+  b.passL.hyps = hyL;
+  b.passF.n = nF;
+  b.passF.R = RF;
+  b.passF.chunks = chF;
+  b.passF.hyps = hyF;
+  round_tables(KL, std::max(RL, 1), h.alive_L, h.surv_L, b.passL.tot_alive, b.passL.tot_surv);
+  round_tables(KF, std::max(RF, 1), h.alive_F, h.surv_F, b.passF.tot_alive, b.passF.tot_surv);
+  b.passL.tot_alive.resize(RL);
+  b.passL.tot_surv.resize(RL);
+  b.passF.tot_alive.resize(RF);
+  b.passF.tot_surv.resize(RF);
+  *bytes = c.off;
+}
+
+template <class T>
+cudaError_t upload(T* dst, const std::vector<T>& v) {
+  return v.empty() ? cudaSuccess : cudaMemcpy(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+cudaError_t mark(relo_batch* b, int k, cudaStream_t s) { return b->timing ? cudaEventRecord(b->ev[k], s) : cudaSuccess; }
+
+}  // namespace
+
+extern "C" {
+
+size_t relo_batch_workspace_size(const relo_attempt* at, int32_t n, const relo_ransac_params* p) {
+  if (check_attempts(at, n, p) != RELO_OK) return 0;
+  relo_batch b;
+  HostJobs h;
+  size_t bytes = 0;
+  layout_batch(at, n, *p, nullptr, &bytes, b, h);
+  return bytes;
+}
+
+relo_status relo_batch_prepare(const relo_attempt* at, int32_t n, const relo_ransac_params* p, void* ws,
+                               size_t ws_bytes, relo_batch** out) {
+  if (!out) return fail(RELO_EINVAL, "out is null");
+  *out = nullptr;
+  relo_status st = check_attempts(at, n, p);
+  if (st) return st;
+  if (!ws || ((uintptr_t)ws & 255) != 0) return fail(RELO_EINVAL, "workspace must be non-null and 256-byte aligned");
+  size_t bytes = 0;
+  {
+    relo_batch probe;
+    HostJobs h;
+    layout_batch(at, n, *p, nullptr, &bytes, probe, h);
+  }
+  if (bytes > ws_bytes) return fail(RELO_EINVAL, "workspace too small");
+  relo_batch* b = new relo_batch();
+  HostJobs h;
+  layout_batch(at, n, *p, (char*)ws, &bytes, *b, h);
+  cudaError_t e = upload(b->d_query, h.query);
+  if (e == cudaSuccess) e = upload(b->d_verify_L, h.verify_L);
+  if (e == cudaSuccess) e = upload(b->d_verify_F, h.verify_F);
+  if (e == cudaSuccess) e = upload(b->d_forest, h.forest);
+  if (e == cudaSuccess) e = upload(b->passL.d_jobs, h.ransac_L);
+  if (e == cudaSuccess) e = upload(b->passF.d_jobs, h.ransac_F);
+  if (e == cudaSuccess) e = upload(b->passL.d_alive_prefix, h.alive_L);
+  if (e == cudaSuccess) e = upload(b->passL.d_surv_prefix, h.surv_L);
+  if (e == cudaSuccess) e = upload(b->passF.d_alive_prefix, h.alive_F);
+  if (e == cudaSuccess) e = upload(b->passF.d_surv_prefix, h.surv_F);
+  if (e == cudaSuccess) e = upload(b->d_kind, h.kind);
+  if (e != cudaSuccess) {
+    delete b;
+    return cuda_fail(e, "batch descriptors");
+  }
+  *out = b;
+  return RELO_OK;
+}
+
+relo_status relo_batch_run(relo_batch* b, relo_pose_result* results, relo_stream stream) {
+  if (!b) return fail(RELO_EINVAL, "batch not prepared");
+  cudaStream_t s = (cudaStream_t)stream;
+  int L = 0;
+  RELO_CUDA(cudaMemsetAsync(b->d_errs, 0, (b->nL + b->nF + 1) * sizeof(int32_t), s));
+  RELO_CUDA(launch_init_results(b->d_res_F, b->n, s));
+  RELO_CUDA(mark(b, 0, s));
+  RELO_CUDA(launch_raycast(b->d_query, b->n, nullptr, b->query_tiles, true, false, s));
+  L += 2;
+  RELO_CUDA(mark(b, 1, s));
+  // pass L: learned attempts
+  if (b->nL > 0) {
+    relo_status st = reg_forward(b->reg, b->regbuf, b->depth_L, (const uint8_t*)b->rgba_L, b->nL, b->lW, b->lH, s);
+    if (st) return st;
+    RELO_CUDA(launch_cell_forest(b->cells, s));
+    L += 1 + kRegLayers + 1;
+  }
+  RELO_CUDA(mark(b, 2, s));
+  relo_status st = run_pass(b->passL, s, &L, b->timing ? b->ev[3] : nullptr, b->timing ? b->ev[4] : nullptr);
+  if (st) return st;
+  if (b->nL > 0) {
+    RELO_CUDA(launch_raycast(b->d_verify_L, b->nL, nullptr, b->verify_L_tiles, false, true, s));
+    RELO_CUDA(launch_verify_decide(b->passL.d_jobs, b->nL, s));
+    L += 2;
+  }
+  RELO_CUDA(mark(b, 5, s));
+  // pass F: forest attempts and fallbacks (skipped on the device where the learned pose verified)
+  if (b->nF > 0) {
+    RELO_CUDA(launch_forest(b->d_forest, b->nF, nullptr, b->forest_pixels, s, b->max_trees));
+    L += 1;
+  }
+  RELO_CUDA(mark(b, 6, s));
+  st = run_pass(b->passF, s, &L, b->timing ? b->ev[7] : nullptr, b->timing ? b->ev[8] : nullptr);
+  if (st) return st;
+  if (b->nF > 0) {
+    RELO_CUDA(launch_raycast(b->d_verify_F, b->nF, nullptr, b->verify_F_tiles, false, true, s));
+    RELO_CUDA(launch_verify_decide(b->passF.d_jobs, b->nF, s));
+    L += 2;
+  }
+  RELO_CUDA(mark(b, 9, s));
+  RELO_CUDA(launch_merge_results(b->d_res_L, b->d_res_F, b->d_kind, b->n, b->d_res, s));
+  L += 1;
+  RELO_CUDA(mark(b, 10, s));
+  if (results && results != b->d_res)
+    RELO_CUDA(cudaMemcpyAsync(results, b->d_res, b->n * sizeof(relo_pose_result), cudaMemcpyDeviceToDevice, s));
+  return RELO_OK;
+}
+
+int32_t relo_batch_launch_count(const relo_batch* b) {
+  if (!b) return 0;
+  int L = 2 + 1;  // result init + query raycast, merge
+  if (b->nL > 0) L += 1 + kRegLayers + 1 + 2 + pass_launches(b->passL);
+  if (b->nF > 0) L += 1 + 2 + pass_launches(b->passF);
+  return L;
+}
+
+void relo_batch_destroy(relo_batch* b) { delete b; }
+
+relo_status relo_batch_enable_timing(relo_batch* b, int32_t enable) {
+  if (!b) return fail(RELO_EINVAL, "batch is null");
+  if (enable) {
+    for (cudaEvent_t& e : b->ev)
+      if (!e) RELO_CUDA(cudaEventCreate(&e));
+  }
+  b->timing = enable != 0;
+  return RELO_OK;
+}
+
+int32_t relo_batch_stage_ms(const relo_batch* b, float* ms, int32_t capacity) {
+  if (!b || !b->timing || !ms || capacity < kStages) return 0;
+  for (int k = 0; k < kStages; ++k)
+    if (cudaEventElapsedTime(&ms[k], b->ev[k], b->ev[k + 1]) != cudaSuccess) return 0;
+  return kStages;
+}
+
+const char* relo_batch_stage_name(int32_t k) { return (k >= 0 && k < kStages) ? kStageNames[k] : ""; }
+
+relo_status relo_relocalise_batch(const relo_attempt* at, int32_t n, const relo_ransac_params* p, void* ws,
+                                  size_t ws_bytes, relo_pose_result* results_host, relo_stream stream) {
+  if (!results_host) return fail(RELO_EINVAL, "results is null");
+  relo_batch* b = nullptr;
+  relo_status st = relo_batch_prepare(at, n, p, ws, ws_bytes, &b);
+  if (st) return st;
+  st = relo_batch_run(b, nullptr, stream);
+  if (st == RELO_OK) {
+    cudaError_t e = cudaMemcpyAsync(results_host, b->d_res, n * sizeof(relo_pose_result), cudaMemcpyDeviceToHost,
+                                    (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) st = cuda_fail(e, "batch results");
+  }
+  relo_batch_destroy(b);
+  return st;
 }
 
 }  // extern "C"

@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(256)
     else hi = mid - 1;
   }
   const ForestJob& job = jobs ? jobs[lo] : single;
+  if (job_skipped(job.skip)) return;
   const int64_t pix = gid - job.pixel_begin;
   const int64_t n_pix = (int64_t)job.W * job.H;
   if (pix < 0 || pix >= n_pix) return;

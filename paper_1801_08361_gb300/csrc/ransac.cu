@@ -94,6 +94,7 @@ __device__ __forceinline__ int chunk_job(const RansacJob* jobs, int n_jobs, int 
 __global__ void __launch_bounds__(kCompactThreads) compact_count_kernel(const RansacJob* __restrict__ jobs,
                                                                        int n_jobs) {
   const RansacJob& job = jobs[chunk_job(jobs, n_jobs, blockIdx.x)];
+  if (job_skipped(job.skip)) return;
   const int chunk = blockIdx.x - job.chunk_begin;
   const int n_pix = job.W * job.H;
   int c = 0;
@@ -115,6 +116,7 @@ __global__ void __launch_bounds__(kCompactThreads) compact_count_kernel(const Ra
 __global__ void __launch_bounds__(kCompactThreads) compact_scatter_kernel(const RansacJob* __restrict__ jobs,
                                                                          int n_jobs) {
   const RansacJob& job = jobs[chunk_job(jobs, n_jobs, blockIdx.x)];
+  if (job_skipped(job.skip)) return;
   const int chunk = blockIdx.x - job.chunk_begin;
   const int n_pix = job.W * job.H;
   const int n_chunks = (n_pix + kCompactChunk - 1) / kCompactChunk;
@@ -315,7 +317,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32, RELO_SEARCH_MIN_BLOCKS)
   }
   const RansacJob& job = jobs[lo];
   const int h = gw - job.hyp_begin;
-  if (h >= job.K) return;
+  if (h >= job.K || job_skipped(job.skip)) return;
   const int n_valid = *job.n_valid;
   const float rig = (float)job.rigidity, area = (float)job.min_area;
   const float fx = (float)job.fx, fy = (float)job.fy, cx = (float)job.cx, cy = (float)job.cy;
@@ -360,7 +362,7 @@ __global__ void __launch_bounds__(128) fit_kernel(const RansacJob* __restrict__ 
   }
   const RansacJob& job = jobs[lo];
   const int h = gid - job.hyp_begin;
-  if (h >= job.K) return;
+  if (h >= job.K || job_skipped(job.skip)) return;
   double* pose = job.poses + 12 * (size_t)h;
   const bool ok = job.hyp_ok[h] != 0;
   if (ok) {
@@ -409,6 +411,7 @@ __global__ void draw_kernel(const RansacJob* __restrict__ jobs, const int32_t* _
   const int jid = blockIdx.x;
   if (alive_prefix[jid + 1] - alive_prefix[jid] == 0) return;
   const RansacJob& job = jobs[jid];
+  if (job_skipped(job.skip)) return;
   const int n_valid = *job.n_valid;
   if (n_valid == 0) return;
   for (int i = threadIdx.x; i < job.B; i += blockDim.x) {
@@ -452,6 +455,7 @@ __global__ void __launch_bounds__(256) energy_kernel(const RansacJob* __restrict
   if (gw >= total) return;
   const int jid = find_job_by(alive_prefix, n_jobs, gw);
   const RansacJob& job = jobs[jid];
+  if (job_skipped(job.skip)) return;
   const int h = alive_in(job, r)[gw - alive_prefix[jid]];
   if (!job.hyp_ok[h] || *job.n_valid == 0) return;
   const PoseF P = pose_to_float(job.poses + 12 * (size_t)h);
@@ -482,6 +486,7 @@ __global__ void __launch_bounds__(1024) select_kernel(const RansacJob* __restric
   const int n = alive_prefix[jid + 1] - alive_prefix[jid];
   if (n == 0) return;
   const RansacJob& job = jobs[jid];
+  if (job_skipped(job.skip)) return;
   int npow = 1;
   while (npow < n) npow <<= 1;
   int* sidx = reinterpret_cast<int*>(skey + npow);
@@ -535,6 +540,7 @@ __global__ void __launch_bounds__(256) refine_kernel(const RansacJob* __restrict
   if (gw >= total) return;
   const int jid = find_job_by(surv_prefix, n_jobs, gw);
   const RansacJob& job = jobs[jid];
+  if (job_skipped(job.skip)) return;
   const int h = alive_out(job, r)[gw - surv_prefix[jid]];
   if (!job.hyp_ok[h] || *job.n_valid == 0) return;
   const PoseF P = pose_to_float(job.poses + 12 * (size_t)h);
@@ -594,6 +600,7 @@ __global__ void __launch_bounds__(128) refit_kernel(const RansacJob* __restrict_
   if (gid >= total) return;
   const int jid = find_job_by(surv_prefix, n_jobs, gid);
   const RansacJob& job = jobs[jid];
+  if (job_skipped(job.skip)) return;
   const int h = alive_out(job, r)[gid - surv_prefix[jid]];
   if (!job.hyp_ok[h] || *job.n_valid == 0) return;
   const float* f = job.refit + (size_t)h * kRefitFloats;
@@ -632,6 +639,7 @@ __global__ void finalise_kernel(const RansacJob* __restrict__ jobs, int n_jobs) 
   const int jid = blockIdx.x * blockDim.x + threadIdx.x;
   if (jid >= n_jobs) return;
   const RansacJob& job = jobs[jid];
+  if (job_skipped(job.skip)) return;
   const int32_t* fin = (job.n_rounds & 1) ? job.alive_b : job.alive_a;
   const int h = fin[0];
   relo_pose_result* res = job.result;
@@ -651,6 +659,8 @@ __global__ void finalise_kernel(const RansacJob* __restrict__ jobs, int n_jobs) 
   unsigned long long tries = 0;
   for (int q = 0; q < job.K; ++q) tries += job.hyp_ok[q] ? (unsigned long long)job.tries[q] + 1 : job.max_tries;
   res->tries = tries;
+  res->path = RELO_PATH_FOREST;
+  res->pad = 0;
   for (int q = 0; q < 16; ++q) res->rel_a_b[q] = (q % 5 == 0) ? 1.0 : 0.0;
   if (job.has_pose_b) {
     // a_T_b = P_a P_b^-1 with P_b^-1 = [R_b^T | -R_b^T t_b]
@@ -682,8 +692,8 @@ __device__ __forceinline__ void decide(relo_pose_result* res, unsigned long long
 
 __global__ void verify_decide_kernel(const RansacJob* __restrict__ jobs, int n_jobs) {
   const int jid = blockIdx.x * blockDim.x + threadIdx.x;
-  if (jid >= n_jobs) return;
-  decide(jobs[jid].result, (unsigned long long)jobs[jid].W * jobs[jid].H);
+  if (jid >= n_jobs || job_skipped(jobs[jid].skip)) return;
+  decide(jobs[jid].result, (unsigned long long)jobs[jid].vW * jobs[jid].vH);
 }
 
 __global__ void verify_decide_one_kernel(relo_pose_result* res, unsigned long long omega) { decide(res, omega); }
@@ -700,6 +710,45 @@ cudaError_t launch_verify_decide_one(relo_pose_result* res, uint64_t omega, cuda
 
 cudaError_t launch_finalise(const RansacJob* jobs, int n_jobs, cudaStream_t s) {
   finalise_kernel<<<(n_jobs + 127) / 128, 128, 0, s>>>(jobs, n_jobs);
+  return cudaGetLastError();
+}
+
+// Fallback results start as "not run" (a skipped job writes nothing).
+__global__ void init_results_kernel(relo_pose_result* res, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  res[i].status = RELO_ENOTFOUND;
+  res[i].verified = 0;
+}
+
+cudaError_t launch_init_results(relo_pose_result* res, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  init_results_kernel<<<(n + 127) / 128, 128, 0, s>>>(res, n);
+  return cudaGetLastError();
+}
+
+// kind[i]: 0 forest only (fallback[i] holds the result), 1 learned without forest, 2 learned with
+// a forest fallback.  A learned attempt keeps its learned result when it verified.
+__global__ void merge_results_kernel(const relo_pose_result* learned, const relo_pose_result* fallback,
+                                     const int32_t* kind, int n, relo_pose_result* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int k = kind[i];
+  if (k == 0) {
+    out[i] = fallback[i];
+    out[i].path = RELO_PATH_FOREST;
+  } else if (k == 1 || learned[i].verified) {
+    out[i] = learned[i];
+    out[i].path = RELO_PATH_LEARNED;
+  } else {
+    out[i] = fallback[i];
+    out[i].path = RELO_PATH_FALLBACK;
+  }
+}
+
+cudaError_t launch_merge_results(const relo_pose_result* learned, const relo_pose_result* fallback,
+                                 const int32_t* kind, int n, relo_pose_result* out, cudaStream_t s) {
+  merge_results_kernel<<<(n + 127) / 128, 128, 0, s>>>(learned, fallback, kind, n, out);
   return cudaGetLastError();
 }
 

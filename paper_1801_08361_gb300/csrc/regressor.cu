@@ -447,17 +447,20 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long n, fl
 
 __global__ void cell_forest_kernel(CellForestArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int img = blockIdx.y;
   if (i >= a.L) return;
   const int n = a.Wc * a.Hc;
-  float* m = a.modes + (size_t)i * kModeFloats;
+  float* m = a.modes + ((size_t)img * a.L + i) * kModeFloats;
+  uint8_t* nm = a.n_modes + (size_t)img * a.L;
+  float4* top = a.top + (size_t)img * a.L;
   if (i >= n) {
-    a.n_modes[i] = 0;
-    a.top[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    nm[i] = 0;
+    top[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     return;
   }
   const int cx = i % a.Wc, cy = i / a.Wc;
-  const int d = a.depth[(size_t)(cy * 8 + 4) * a.W + cx * 8 + 4];
-  const float* o = a.out + (size_t)i * 8;
+  const int d = a.depth[(size_t)img * a.W * a.H + (size_t)(cy * 8 + 4) * a.W + cx * 8 + 4];
+  const float* o = a.out + ((size_t)img * n + i) * 8;
   const float s = o[3], inv = expf(-s);
   const float mx = o[0] + a.ox, my = o[1] + a.oy, mz = o[2] + a.oz;
   m[0] = mx;
@@ -472,14 +475,15 @@ __global__ void cell_forest_kernel(CellForestArgs a) {
   m[9] = -1.5f * 1.8378770664093453f - 1.5f * s;  // log w - 0.5 log det(2 pi exp(s) I), w = 1
   m[10] = 1.f;
   m[11] = 0.f;
-  a.n_modes[i] = d > 0 ? 1 : 0;
-  a.top[i] = make_float4(mx, my, mz, d > 0 ? 1.f : 0.f);
-  a.leaves[i] = (uint16_t)i;
-  a.depth_lr[i] = (uint16_t)d;
+  nm[i] = d > 0 ? 1 : 0;
+  top[i] = make_float4(mx, my, mz, d > 0 ? 1.f : 0.f);
+  a.leaves[(size_t)img * n + i] = (uint16_t)i;
+  a.depth_lr[(size_t)img * n + i] = (uint16_t)d;
 }
 
 cudaError_t launch_cell_forest(const CellForestArgs& a, cudaStream_t s) {
-  cell_forest_kernel<<<(a.L + 255) / 256, 256, 0, s>>>(a);
+  if (a.n <= 0) return cudaSuccess;
+  cell_forest_kernel<<<dim3((a.L + 255) / 256, a.n), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

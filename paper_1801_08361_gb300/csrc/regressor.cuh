@@ -46,15 +46,15 @@ struct CellArgs {
 
 // Cell forest (see cell_forest_kernel)
 struct CellForestArgs {
-  const float* out;        // [Hc][Wc][8] head output of one image
-  const uint16_t* depth;   // [H][W] full-resolution depth
-  int W, H, Wc, Hc, L;     // L = leaves per tree (power of two >= Wc Hc)
+  const float* out;        // [n][Hc][Wc][8] head output
+  const uint16_t* depth;   // [n][H][W] full-resolution depth
+  int n, W, H, Wc, Hc, L;  // L = leaves per tree (power of two >= Wc Hc)
   float ox, oy, oz;
-  float* modes;            // [L][1][12]
-  uint8_t* n_modes;        // [L]
-  float4* top;             // [L]
-  uint16_t* leaves;        // [Hc][Wc]
-  uint16_t* depth_lr;      // [Hc][Wc]
+  float* modes;            // [n][L][1][12]
+  uint8_t* n_modes;        // [n][L]
+  float4* top;             // [n][L]
+  uint16_t* leaves;        // [n][Hc][Wc]
+  uint16_t* depth_lr;      // [n][Hc][Wc]
 };
 
 constexpr int kRegLayers = 8;

@@ -255,6 +255,7 @@ struct ForestJob {
   uint16_t* leaves;            // [T][H][W]
   int32_t W, H;
   int64_t pixel_begin;         // first pixel of this job in the flattened launch
+  const int32_t* skip;         // when set and non-zero the job does nothing (fallback not needed)
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -289,9 +290,13 @@ struct RansacJob {
   int32_t chunk_begin;         // flattened compaction chunks
   int32_t hyp_begin;           // flattened hypotheses
   int32_t has_pose_b;          // finalise also writes a_T_b = P_a P_b^-1
+  int32_t vW, vH;              // size of the view the pose is verified on (the full image)
   int32_t pad2;
   double pose_b[16];           // camera -> scene b pose of the query
+  const int32_t* skip;         // when set and non-zero every stage skips the job (fallback not needed)
 };
+
+__device__ __forceinline__ bool job_skipped(const int32_t* skip) { return skip != nullptr && *skip != 0; }
 
 constexpr int kCompactChunk = 4096;
 
@@ -320,6 +325,10 @@ cudaError_t launch_forest(const ForestJob* jobs_dev, int n_jobs, const ForestJob
 int ray_tiles(int W, int H);
 cudaError_t launch_verify_decide(const RansacJob* jobs, int n_jobs, cudaStream_t s);
 cudaError_t launch_verify_decide_one(relo_pose_result* res, uint64_t omega, cudaStream_t s);
+// Learned batches: mark fallback results not run, then pick each attempt's final result.
+cudaError_t launch_init_results(relo_pose_result* res, int n, cudaStream_t s);
+cudaError_t launch_merge_results(const relo_pose_result* learned, const relo_pose_result* fallback,
+                                 const int32_t* kind, int n, relo_pose_result* out, cudaStream_t s);
 cudaError_t launch_scene_lookup(SceneView sv, const int32_t* keys, int64_t n, int64_t* out, int32_t* err,
                                 cudaStream_t s);
 

@@ -367,7 +367,9 @@ def test_batch_prepared_replay_is_deterministic(room, gpu_room, gpu_forest, room
     bt.run(out2)
     torch.cuda.synchronize()
     assert torch.equal(out1, out2)
-    assert bt.launch_count == 2 + 2 + 2 + 5 * 5 + 1 + 2
+    # result init + query raycast, merge; forest pass: forest, compaction (2), search + fit, 5 rounds
+    # of draw / energy / select / refine / refit, finalise, verification raycast + decision
+    assert bt.launch_count == 2 + 1 + 1 + 2 + 2 + 5 * 5 + 1 + 2
 
 
 # ------------------------------------------------------------------------------------------------

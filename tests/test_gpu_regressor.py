@@ -188,3 +188,68 @@ def test_learned_ransac_matches_oracle_on_the_cell_grid(room, oracle_room):
     if ro["valid"]:
         assert r["hypothesis"] == ro["index"]
         assert np.abs(r["pose"][:3] - ro["pose"][:3]).max() < 1e-3
+
+
+@pytest.fixture(scope="module")
+def gpu_room_scene(room):
+    return B.Scene(room[1], 16)
+
+
+def _learned_items(room, room_training, scene, reg, forest, n, seed):
+    world, _ = room
+    intr = synth.Intrinsics.for_size(160, 120)
+    qs = synth.query_poses(world, [f[1] for f in room_training], n, seed=seed)
+    return [dict(scene_b=scene, scene_a=scene, regressor_a=reg, forest_a=forest, intr=intr, pose_b=P, seed=10 + i)
+            for i, P in enumerate(qs)]
+
+
+def test_learned_batch_equals_single_calls(room, room_training, gpu_room_scene):
+    """Learned attempts in a batch give exactly the results of relo_regressor_relocalise +
+    relo_verify on the same query (same kernels, same inputs)."""
+    reg = B.Regressor(seed=7, origin=ORIGIN)
+    items = _learned_items(room, room_training, gpu_room_scene, reg, None, 3, seed=61)
+    prm = B.ransac_params(n_hyps=32, batch=64, max_tries=2000)
+    att = B.make_attempts(items)
+    ws = torch.empty(B.batch_workspace_size(att, prm), dtype=torch.uint8, device=DEV)
+    got = B.relocalise_batch(att, prm, ws)
+    for it, g in zip(items, got):
+        intr = it["intr"]
+        depth = torch.zeros((intr.height, intr.width), dtype=torch.int16, device=DEV)
+        rgba = torch.zeros((intr.height, intr.width, 4), dtype=torch.uint8, device=DEV)
+        B.raycast_view(gpu_room_scene, intr, it["pose_b"], depth, rgba)
+        p1 = B.ransac_params(n_hyps=32, batch=64, max_tries=2000, seed=it["seed"])
+        wsr = torch.empty(B.regressor_relocalise_workspace_size(intr.width, intr.height, p1), dtype=torch.uint8,
+                          device=DEV)
+        res = torch.zeros(B.RESULT_BYTES, dtype=torch.uint8, device=DEV)
+        B.regressor_relocalise(reg, depth, rgba, intr, p1, wsr, res)
+        B.verify(gpu_room_scene, intr, depth, res)
+        torch.cuda.synchronize()
+        s = B.result_from_bytes(res)
+        assert g["path"] == B.PATH_LEARNED
+        for k in ("hypothesis", "status", "n_valid", "omega", "omega_a", "omega_ab", "sum_absdiff_mm", "verified"):
+            assert g[k] == s[k], k
+        assert np.array_equal(g["pose"], s["pose"])
+
+
+def test_fallback_reports_the_forest_result(room, room_training, gpu_room_scene, room_forest):
+    """An untrained regressor fails verification; the forest fallback then runs on the device and
+    its result equals the forest-only batch's."""
+    reg = B.Regressor(seed=8, origin=ORIGIN)
+    forest = B.Forest(room_forest.nodes, room_forest.modes, room_forest.n_modes, max_modes=10)
+    learned = _learned_items(room, room_training, gpu_room_scene, reg, forest, 4, seed=62)
+    plain = [dict(it, regressor_a=None) for it in learned]
+    prm = B.ransac_params(n_hyps=32, batch=64, max_tries=2000)
+    out = []
+    for items in (learned, plain):
+        att = B.make_attempts(items)
+        ws = torch.empty(B.batch_workspace_size(att, prm), dtype=torch.uint8, device=DEV)
+        out.append(B.relocalise_batch(att, prm, ws))
+    for l, f in zip(*out):
+        assert f["path"] == B.PATH_FOREST
+        if l["path"] == B.PATH_FALLBACK:
+            for k in ("hypothesis", "status", "omega_a", "omega_ab", "sum_absdiff_mm", "verified", "energy"):
+                assert l[k] == f[k], k
+            assert np.array_equal(l["pose"], f["pose"])
+        else:
+            assert l["path"] == B.PATH_LEARNED and l["verified"] == 1
+    assert any(l["path"] == B.PATH_FALLBACK for l in out[0])
