@@ -10,8 +10,9 @@ evaluate it through a's forest, preemptive RANSAC (1024 hypotheses, 64 pixels pe
 halvings), depth raycast of scene a at the proposed pose and the Omega / mu verification.
 Scene a and b are the same house here (an agent relocalising against its own map).
 
-A step = one batch of ``--batch`` attempts through relo_batch_run (inputs resident in HBM; the
-L2 is flushed between steps; each step timed with CUDA events on the launching stream).
+A step = one batch of ``--batch`` attempts: one replay of the CUDA graph relo_batch_capture
+recorded from relo_batch_run (inputs resident in HBM; the L2 is flushed between steps; each step
+timed with CUDA events on the launching stream).
 ``e2e`` = the same metric through relo_relocalise_batch with the query noise images copied from
 pinned host memory and the results copied back inside the timed region.
 ``--impl reference`` times the CPU oracle (the deliberately slow FP64 reference) instead.
@@ -268,6 +269,7 @@ def run_ours(args):
         bt = B.Batch(att, prm, ws)
         bt.enable_timing(True)
         res = torch.zeros(A * B.RESULT_BYTES, dtype=torch.uint8, device=dev)
+        bt.capture(res)            # one CUDA graph per batch; its replays carry the stage events
         sets.append(dict(qs=qs, noise=noise, att=att, ws=ws, batch=bt, res=res))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -283,7 +285,7 @@ def run_ours(args):
 
     for s in range(args.warmup):
         flush.zero_()
-        sets[s % n_sets]["batch"].run(sets[s % n_sets]["res"])
+        sets[s % n_sets]["batch"].replay()
     torch.cuda.synchronize()
 
     # ---- device-resident timing -----------------------------------------------------------
@@ -298,7 +300,7 @@ def run_ours(args):
         st = sets[(args.warmup + s) % n_sets]
         flush.zero_()
         ev[s][0].record(stream)
-        st["batch"].run(st["res"])
+        st["batch"].replay()
         ev[s][1].record(stream)
         torch.cuda.synchronize()
         for k, v in st["batch"].stage_ms().items():

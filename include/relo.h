@@ -370,6 +370,24 @@ relo_status relo_batch_run(relo_batch* batch, relo_pose_result* results_dev, rel
 int32_t relo_batch_launch_count(const relo_batch* batch);
 void relo_batch_destroy(relo_batch* batch);
 
+/* One CUDA graph per batch (no counterpart in the paper, whose attempts run one at a time in the
+ * background): relo_batch_capture records every launch of one relo_batch_run that writes
+ * results_dev (nullable: results stay in the workspace) into a graph owned by the batch,
+ * replacing any earlier one; relo_batch_replay launches that graph on a stream, one host call
+ * for the whole batch, with the same device work and results as relo_batch_run.  When stage
+ * timing was enabled at capture, the graph records the stage events too.  The graph refers to the workspace, scenes, forests, regressor and noise
+ * images by address: they must outlive it (relo_batch_destroy frees it).
+ * Errors: RELO_EINVAL (null batch, replay before capture), RELO_ECUDA (capture failed). */
+relo_status relo_batch_capture(relo_batch* batch, relo_pose_result* results_dev);
+relo_status relo_batch_replay(relo_batch* batch, relo_stream stream);
+
+/* Device addresses, inside the workspace, of attempt k's query depth (u16 mm [H][W]), query
+ * colour (RGBA u8 [H][W][4]) and forest leaves (u16 [T][H][W]; NULL for an attempt without a
+ * forest); their contents are those of the last run (for inspection).  Any output pointer may be
+ * NULL.  Errors: RELO_EINVAL (null batch, k outside [0, n)). */
+relo_status relo_batch_attempt_images(const relo_batch* batch, int32_t k, const uint16_t** depth_dev,
+                                      const uint8_t** rgba_dev, const uint16_t** leaves_dev);
+
 /* Stage timing, for roofline measurements.  Once enabled, relo_batch_run records CUDA events on
  * its stream at the stage boundaries; relo_batch_stage_ms writes the milliseconds each stage of
  * the last run took (call it after that run's stream has synchronised), in this order: query

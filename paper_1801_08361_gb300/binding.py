@@ -114,6 +114,10 @@ _SIGS = {
     "relo_batch_enable_timing": (c_i32, [c_vp, c_i32]),
     "relo_batch_stage_ms": (c_i32, [c_vp, ctypes.POINTER(ctypes.c_float), c_i32]),
     "relo_batch_stage_name": (ctypes.c_char_p, [c_i32]),
+    "relo_batch_capture": (c_i32, [c_vp, c_vp]),
+    "relo_batch_replay": (c_i32, [c_vp, c_vp]),
+    "relo_batch_attempt_images": (c_i32, [c_vp, c_i32, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp),
+                                          ctypes.POINTER(c_vp)]),
 }
 
 STAGES = ["query_raycast", "learned_forward", "learned_hypotheses", "learned_rounds", "learned_verify", "forest_eval",
@@ -367,6 +371,33 @@ class Batch:
 
     def run(self, results_dev, stream=None):
         _check(lib().relo_batch_run(self.handle, _ptr(results_dev), _stream(stream)))
+
+    def capture(self, results_dev=None):
+        """Record one run into the batch's CUDA graph (relo_batch_capture)."""
+        _check(lib().relo_batch_capture(self.handle, _ptr(results_dev)))
+
+    def replay(self, stream=None):
+        _check(lib().relo_batch_replay(self.handle, _stream(stream)))
+
+    def attempt_images(self, k, width, height, trees=0):
+        """Views into the workspace of attempt k's query depth (int16 bits of u16 [H][W]), colour
+        (u8 [H][W][4]) and forest leaves (int16 bits of u16 [T][H][W], None without a forest)."""
+        d, c, lv = c_vp(), c_vp(), c_vp()
+        _check(lib().relo_batch_attempt_images(self.handle, int(k), ctypes.byref(d), ctypes.byref(c),
+                                               ctypes.byref(lv)))
+        base, n = self._ws.data_ptr(), width * height
+
+        def view(addr, nbytes):
+            off = addr - base
+            if off < 0 or off + nbytes > self._ws.numel():
+                raise ReloError(EINVAL, "attempt image outside the workspace")
+            return self._ws[off:off + nbytes]
+
+        import torch
+        depth = view(d.value, 2 * n).view(torch.int16).view(height, width)
+        rgba = view(c.value, 4 * n).view(height, width, 4)
+        leaves = None if not lv.value else view(lv.value, 2 * n * trees).view(torch.int16).view(trees, height, width)
+        return depth, rgba, leaves
 
     @property
     def launch_count(self) -> int:

@@ -153,15 +153,22 @@ struct RansacPass {
   std::vector<int> tot_alive, tot_surv;
 };
 
+// Records ev (nullable) on s; external: as an event-record node when s is being captured.
+cudaError_t record(cudaEvent_t ev, cudaStream_t s, bool external) {
+  if (!ev) return cudaSuccess;
+  return external ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal) : cudaEventRecord(ev, s);
+}
+
 // ev_hyp / ev_rounds (nullable) are recorded after the hypotheses and after the rounds.
-relo_status run_pass(const RansacPass& p, cudaStream_t s, int* launches, cudaEvent_t ev_hyp, cudaEvent_t ev_rounds) {
+relo_status run_pass(const RansacPass& p, cudaStream_t s, int* launches, cudaEvent_t ev_hyp, cudaEvent_t ev_rounds,
+                     bool external = false) {
   int L = 0;
   if (p.n > 0) {
     RELO_CUDA(launch_compact(p.d_jobs, p.n, p.chunks, s));
     RELO_CUDA(launch_hypotheses(p.d_jobs, p.n, p.hyps, s));
     L += 4;
   }
-  if (ev_hyp) RELO_CUDA(cudaEventRecord(ev_hyp, s));
+  RELO_CUDA(record(ev_hyp, s, external));
   for (int r = 0; r < p.R; ++r) {
     if (p.tot_alive[r] == 0) continue;
     RELO_CUDA(launch_round(p.d_jobs, p.n, r, p.d_alive_prefix + (size_t)r * (p.n + 1), p.tot_alive[r],
@@ -172,7 +179,7 @@ relo_status run_pass(const RansacPass& p, cudaStream_t s, int* launches, cudaEve
     RELO_CUDA(launch_finalise(p.d_jobs, p.n, s));
     L += 1;
   }
-  if (ev_rounds) RELO_CUDA(cudaEventRecord(ev_rounds, s));
+  RELO_CUDA(record(ev_rounds, s, external));
   *launches += L;
   return RELO_OK;
 }
@@ -1283,9 +1290,15 @@ struct relo_batch {
   CellForestArgs cells{};
   bool timing = false;
   cudaEvent_t ev[kStages + 1] = {};
+  // per attempt: its query images and forest leaves inside the workspace (for inspection)
+  std::vector<uint16_t*> a_depth, a_leaves;
+  std::vector<uint32_t*> a_rgba;
+  // the captured run (relo_batch_capture)
+  cudaGraphExec_t graph = nullptr;
   ~relo_batch() {
     for (cudaEvent_t& e : ev)
       if (e) cudaEventDestroy(e);
+    if (graph) cudaGraphExecDestroy(graph);
   }
 };
 
@@ -1408,6 +1421,9 @@ void layout_batch(const relo_attempt* at, int n, const relo_ransac_params& p, ch
     ca.depth_lr = c.take<uint16_t>((size_t)nL * cells);
   }
   h = HostJobs{};
+  b.a_depth.assign(n, nullptr);
+  b.a_rgba.assign(n, nullptr);
+  b.a_leaves.assign(n, nullptr);
   h.query.assign(n, RayJob{});
   h.verify_L.assign(nL, RayJob{});
   h.verify_F.assign(nF, RayJob{});
@@ -1430,6 +1446,8 @@ void layout_batch(const relo_attempt* at, int n, const relo_ransac_params& p, ch
       depth = c.take<uint16_t>(n_pix);
       rgba = c.take<uint32_t>(n_pix);
     }
+    b.a_depth[i] = depth;
+    b.a_rgba[i] = rgba;
     RayJob& q = h.query[i];
     q = make_ray_job(a.scene_b->view, a.intr, a.pose_b);
     q.noise = a.noise_dev;
@@ -1476,6 +1494,7 @@ void layout_batch(const relo_attempt* at, int n, const relo_ransac_params& p, ch
       const int T = a.forest_a->T;
       maxT = std::max(maxT, T);
       uint16_t* leaves = c.take<uint16_t>(n_pix * T);
+      b.a_leaves[i] = leaves;
       const int32_t* skip = kind[i] == 2 ? &b.d_res_L[i].verified : nullptr;
       ForestJob& f = h.forest[j];
       f.forest = a.forest_a->view;
@@ -1537,7 +1556,58 @@ cudaError_t upload(T* dst, const std::vector<T>& v) {
   return v.empty() ? cudaSuccess : cudaMemcpy(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
 }
 
-cudaError_t mark(relo_batch* b, int k, cudaStream_t s) { return b->timing ? cudaEventRecord(b->ev[k], s) : cudaSuccess; }
+cudaError_t mark(relo_batch* b, int k, cudaStream_t s, bool capturing) {
+  return b->timing ? record(b->ev[k], s, capturing) : cudaSuccess;
+}
+
+// Every launch of one run, in stream order, with no host synchronisation (capturable).  While
+// capturing, the stage-timing events become event-record nodes of the graph.
+relo_status issue_batch(relo_batch* b, relo_pose_result* results, cudaStream_t s, bool capturing) {
+  int L = 0;
+  RELO_CUDA(cudaMemsetAsync(b->d_errs, 0, (b->nL + b->nF + 1) * sizeof(int32_t), s));
+  RELO_CUDA(launch_init_results(b->d_res_F, b->n, s));
+  RELO_CUDA(mark(b, 0, s, capturing));
+  RELO_CUDA(launch_raycast(b->d_query, b->n, nullptr, b->query_tiles, true, false, s));
+  L += 2;
+  RELO_CUDA(mark(b, 1, s, capturing));
+  // pass L: learned attempts
+  if (b->nL > 0) {
+    relo_status st = reg_forward(b->reg, b->regbuf, b->depth_L, (const uint8_t*)b->rgba_L, b->nL, b->lW, b->lH, s);
+    if (st) return st;
+    RELO_CUDA(launch_cell_forest(b->cells, s));
+    L += 1 + kRegLayers + 1;
+  }
+  RELO_CUDA(mark(b, 2, s, capturing));
+  const bool ev = b->timing;
+  relo_status st = run_pass(b->passL, s, &L, ev ? b->ev[3] : nullptr, ev ? b->ev[4] : nullptr, capturing);
+  if (st) return st;
+  if (b->nL > 0) {
+    RELO_CUDA(launch_raycast(b->d_verify_L, b->nL, nullptr, b->verify_L_tiles, false, true, s));
+    RELO_CUDA(launch_verify_decide(b->passL.d_jobs, b->nL, s));
+    L += 2;
+  }
+  RELO_CUDA(mark(b, 5, s, capturing));
+  // pass F: forest attempts and fallbacks (skipped on the device where the learned pose verified)
+  if (b->nF > 0) {
+    RELO_CUDA(launch_forest(b->d_forest, b->nF, nullptr, b->forest_pixels, s, b->max_trees));
+    L += 1;
+  }
+  RELO_CUDA(mark(b, 6, s, capturing));
+  st = run_pass(b->passF, s, &L, ev ? b->ev[7] : nullptr, ev ? b->ev[8] : nullptr, capturing);
+  if (st) return st;
+  if (b->nF > 0) {
+    RELO_CUDA(launch_raycast(b->d_verify_F, b->nF, nullptr, b->verify_F_tiles, false, true, s));
+    RELO_CUDA(launch_verify_decide(b->passF.d_jobs, b->nF, s));
+    L += 2;
+  }
+  RELO_CUDA(mark(b, 9, s, capturing));
+  RELO_CUDA(launch_merge_results(b->d_res_L, b->d_res_F, b->d_kind, b->n, b->d_res, s));
+  L += 1;
+  RELO_CUDA(mark(b, 10, s, capturing));
+  if (results && results != b->d_res)
+    RELO_CUDA(cudaMemcpyAsync(results, b->d_res, b->n * sizeof(relo_pose_result), cudaMemcpyDeviceToDevice, s));
+  return RELO_OK;
+}
 
 }  // namespace
 
@@ -1590,49 +1660,48 @@ relo_status relo_batch_prepare(const relo_attempt* at, int32_t n, const relo_ran
 
 relo_status relo_batch_run(relo_batch* b, relo_pose_result* results, relo_stream stream) {
   if (!b) return fail(RELO_EINVAL, "batch not prepared");
-  cudaStream_t s = (cudaStream_t)stream;
-  int L = 0;
-  RELO_CUDA(cudaMemsetAsync(b->d_errs, 0, (b->nL + b->nF + 1) * sizeof(int32_t), s));
-  RELO_CUDA(launch_init_results(b->d_res_F, b->n, s));
-  RELO_CUDA(mark(b, 0, s));
-  RELO_CUDA(launch_raycast(b->d_query, b->n, nullptr, b->query_tiles, true, false, s));
-  L += 2;
-  RELO_CUDA(mark(b, 1, s));
-  // pass L: learned attempts
-  if (b->nL > 0) {
-    relo_status st = reg_forward(b->reg, b->regbuf, b->depth_L, (const uint8_t*)b->rgba_L, b->nL, b->lW, b->lH, s);
-    if (st) return st;
-    RELO_CUDA(launch_cell_forest(b->cells, s));
-    L += 1 + kRegLayers + 1;
+  return issue_batch(b, results, (cudaStream_t)stream, false);
+}
+
+relo_status relo_batch_capture(relo_batch* b, relo_pose_result* results) {
+  if (!b) return fail(RELO_EINVAL, "batch not prepared");
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
   }
-  RELO_CUDA(mark(b, 2, s));
-  relo_status st = run_pass(b->passL, s, &L, b->timing ? b->ev[3] : nullptr, b->timing ? b->ev[4] : nullptr);
+  cudaStream_t cs = nullptr;
+  RELO_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  relo_status st = RELO_OK;
+  if (e == cudaSuccess) {
+    st = issue_batch(b, results, cs, true);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &g);  // ends the capture even when issuing failed
+    if (st == RELO_OK && e2 != cudaSuccess) e = e2;
+  }
+  if (st == RELO_OK && e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
   if (st) return st;
-  if (b->nL > 0) {
-    RELO_CUDA(launch_raycast(b->d_verify_L, b->nL, nullptr, b->verify_L_tiles, false, true, s));
-    RELO_CUDA(launch_verify_decide(b->passL.d_jobs, b->nL, s));
-    L += 2;
+  if (e != cudaSuccess) {
+    b->graph = nullptr;
+    return cuda_fail(e, "batch graph capture");
   }
-  RELO_CUDA(mark(b, 5, s));
-  // pass F: forest attempts and fallbacks (skipped on the device where the learned pose verified)
-  if (b->nF > 0) {
-    RELO_CUDA(launch_forest(b->d_forest, b->nF, nullptr, b->forest_pixels, s, b->max_trees));
-    L += 1;
-  }
-  RELO_CUDA(mark(b, 6, s));
-  st = run_pass(b->passF, s, &L, b->timing ? b->ev[7] : nullptr, b->timing ? b->ev[8] : nullptr);
-  if (st) return st;
-  if (b->nF > 0) {
-    RELO_CUDA(launch_raycast(b->d_verify_F, b->nF, nullptr, b->verify_F_tiles, false, true, s));
-    RELO_CUDA(launch_verify_decide(b->passF.d_jobs, b->nF, s));
-    L += 2;
-  }
-  RELO_CUDA(mark(b, 9, s));
-  RELO_CUDA(launch_merge_results(b->d_res_L, b->d_res_F, b->d_kind, b->n, b->d_res, s));
-  L += 1;
-  RELO_CUDA(mark(b, 10, s));
-  if (results && results != b->d_res)
-    RELO_CUDA(cudaMemcpyAsync(results, b->d_res, b->n * sizeof(relo_pose_result), cudaMemcpyDeviceToDevice, s));
+  return RELO_OK;
+}
+
+relo_status relo_batch_replay(relo_batch* b, relo_stream stream) {
+  if (!b || !b->graph) return fail(RELO_EINVAL, "batch has no captured graph");
+  RELO_CUDA(cudaGraphLaunch(b->graph, (cudaStream_t)stream));
+  return RELO_OK;
+}
+
+relo_status relo_batch_attempt_images(const relo_batch* b, int32_t k, const uint16_t** depth_dev,
+                                      const uint8_t** rgba_dev, const uint16_t** leaves_dev) {
+  if (!b || k < 0 || k >= b->n) return fail(RELO_EINVAL, "attempt index out of range");
+  if (depth_dev) *depth_dev = b->a_depth[k];
+  if (rgba_dev) *rgba_dev = (const uint8_t*)b->a_rgba[k];
+  if (leaves_dev) *leaves_dev = b->a_leaves[k];
   return RELO_OK;
 }
 

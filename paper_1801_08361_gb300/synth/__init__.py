@@ -76,6 +76,7 @@ class World:
     free_lo: np.ndarray               # camera-placement region (world)
     free_hi: np.ndarray
     room_centres: list = field(default_factory=list)
+    rooms: list = field(default_factory=list)  # (i, j, x0, y0, x1, y1) per room of a house grid
 
     def sdf(self, pts: np.ndarray) -> np.ndarray:
         pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
@@ -162,7 +163,31 @@ def house_world(seed: int = 2, size=(10.0, 8.0, 3.0), grid=(3, 2), n_boxes: int 
     rooms = [(xs[i] + hw, ys[j] + hw, xs[i + 1] - hw, ys[j + 1] - hw) for i in range(nx) for j in range(ny)]
     comps += _furniture(rng, rooms, n_boxes, doors)
     centres = [np.array([(r[0] + r[2]) / 2, (r[1] + r[3]) / 2]) for r in rooms]
-    return World(np.asarray(comps, dtype=np.float64), np.array([0.0, 0.0, 1.0]), np.array([sx, sy, 2.0]), centres)
+    cells = [(i, j, xs[i], ys[j], xs[i + 1], ys[j + 1]) for i in range(nx) for j in range(ny)]
+    return World(np.asarray(comps, dtype=np.float64), np.array([0.0, 0.0, 1.0]), np.array([sx, sy, 2.0]), centres,
+                 cells)
+
+
+def house_fragments(world: World, n: int, seed: int, max_rooms: int = 3, max_t: float = 2.0) -> list:
+    """n sub-scenes cut from a house, each a rectangle of 1 to max_rooms adjacent rooms (13-40 m^2
+    of floor for the 10 x 8 m, 3 x 2-room house) in its own random rigid frame, so that the
+    relative transform between any two is known.  Each is a dict: crop (world box, walls
+    included), scene_to_world, rooms (indices into world.rooms / world.room_centres)."""
+    rng = np.random.default_rng(seed)
+    nx = max(r[0] for r in world.rooms) + 1
+    ny = max(r[1] for r in world.rooms) + 1
+    shapes = [(w, h) for w in range(1, nx + 1) for h in range(1, ny + 1) if w * h <= max_rooms]
+    out = []
+    for _ in range(n):
+        w, h = shapes[rng.integers(len(shapes))]
+        i0, j0 = int(rng.integers(nx - w + 1)), int(rng.integers(ny - h + 1))
+        idx = [k for k, r in enumerate(world.rooms) if i0 <= r[0] < i0 + w and j0 <= r[1] < j0 + h]
+        lo = np.array([min(world.rooms[k][2] for k in idx), min(world.rooms[k][3] for k in idx)])
+        hi = np.array([max(world.rooms[k][4] for k in idx), max(world.rooms[k][5] for k in idx)])
+        top = world.comps[0][6]
+        crop = np.array([lo[0] - 0.15, lo[1] - 0.15, -0.1, hi[0] + 0.15, hi[1] + 0.15, top + 0.1])
+        out.append(dict(crop=crop, scene_to_world=random_rigid(rng, max_t=max_t), rooms=idx))
+    return out
 
 
 # --------------------------------------------------------------------------------------------
@@ -269,11 +294,12 @@ def _free_point(world: World, rng, centre_xy, spread, zr=(1.0, 2.0), clearance=0
     raise RuntimeError("no free camera position")
 
 
-def training_poses(world: World, n_per_room: int, seed: int) -> list:
-    """An agent's trajectory: n_per_room views per room from near its centre, yaw sweeping a full turn."""
+def training_poses(world: World, n_per_room: int, seed: int, rooms=None) -> list:
+    """An agent's trajectory: n_per_room views per room (all rooms, or the given room indices)
+    from near its centre, yaw sweeping a full turn."""
     rng = np.random.default_rng(seed)
     out = []
-    for c in world.room_centres:
+    for c in (world.room_centres if rooms is None else [world.room_centres[k] for k in rooms]):
         for k in range(n_per_room):
             p = _free_point(world, rng, c, 0.35)
             yaw = 2 * math.pi * k / n_per_room + rng.uniform(-0.05, 0.05)
