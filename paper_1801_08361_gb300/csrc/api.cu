@@ -193,6 +193,44 @@ int pass_launches(const RansacPass& p) {
 
 }  // namespace
 
+namespace {
+
+// Free cells of the block grid (value < 0) become -(Chebyshev distance, in blocks, to the nearest
+// allocated cell).  The Chebyshev distance is the length of the shortest path through the 26
+// neighbours of each cell, which the two raster passes of the unit-weight 3 x 3 x 3 chamfer mask
+// compute exactly (Rosenfeld and Pfaltz's sequential distance transform).
+void chebyshev_free_distance(std::vector<int32_t>& grid, const int gd[3]) {
+  const int X = gd[0], Y = gd[1], Z = gd[2];
+  const int32_t kFar = 1 << 24;
+  std::vector<int32_t> d(grid.size());
+  for (size_t i = 0; i < grid.size(); ++i) d[i] = grid[i] >= 0 ? 0 : kFar;
+  auto at = [&](int x, int y, int z) { return ((size_t)z * Y + y) * X + x; };
+  for (int pass = 0; pass < 2; ++pass) {
+    const int s = pass == 0 ? 1 : -1;  // forward: neighbours earlier in raster order; backward: later
+    for (int zi = 0; zi < Z; ++zi)
+      for (int yi = 0; yi < Y; ++yi)
+        for (int xi = 0; xi < X; ++xi) {
+          const int x = s > 0 ? xi : X - 1 - xi, y = s > 0 ? yi : Y - 1 - yi, z = s > 0 ? zi : Z - 1 - zi;
+          int32_t& v = d[at(x, y, z)];
+          if (v == 0) continue;
+          int32_t m = v;
+          for (int dz = -1; dz <= 0; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+              for (int dx = -1; dx <= 1; ++dx) {
+                if (dz == 0 && (dy > 0 || (dy == 0 && dx >= 0))) continue;
+                const int xx = x + s * dx, yy = y + s * dy, zz = z + s * dz;
+                if (xx < 0 || yy < 0 || zz < 0 || xx >= X || yy >= Y || zz >= Z) continue;
+                m = std::min(m, d[at(xx, yy, zz)] + 1);
+              }
+          v = m;
+        }
+  }
+  for (size_t i = 0; i < grid.size(); ++i)
+    if (grid[i] < 0) grid[i] = -d[i];
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* relo_last_error(void) { return g_error.c_str(); }
@@ -243,10 +281,10 @@ relo_status relo_create_scene(const int32_t* coords, const float* tsdf, const ui
     max_chain = std::max(max_chain, chain[h]);
   }
   if (excess.empty()) excess.push_back(pack_entry(0, 0, 0, -1, -1));
-  // Dense block-index grid and 8^3-block macro occupancy over the bounding box (origin and
-  // extent on multiples of 8 blocks); skipped when the box exceeds 2^28 blocks.
+  // Dense block-index grid over the bounding box (origin and extent on multiples of 8 blocks;
+  // skipped when the box exceeds 2^28 blocks), free blocks holding -(Chebyshev distance to the
+  // nearest allocated block).
   std::vector<int32_t> grid;
-  std::vector<uint8_t> macro;
   int g0[3] = {0, 0, 0}, gd[3] = {0, 0, 0};
   if (n > 0) {
     int lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
@@ -263,13 +301,12 @@ relo_status relo_create_scene(const int32_t* coords, const float* tsdf, const ui
     }
     if (cells <= ((size_t)1 << 28)) {
       grid.assign(cells, -1);
-      macro.assign(cells / 512, 0);
       for (int64_t b = 0; b < n; ++b) {
         const int x = coords[3 * b] - g0[0], y = coords[3 * b + 1] - g0[1], z = coords[3 * b + 2] - g0[2];
         int32_t& cell = grid[((size_t)z * gd[1] + y) * gd[0] + x];
         if (cell < 0) cell = (int32_t)b;  // a repeated coordinate keeps its first block, as in the hash
-        macro[((size_t)(z >> 3) * (gd[1] >> 3) + (y >> 3)) * (gd[0] >> 3) + (x >> 3)] = 1;
       }
+      chebyshev_free_distance(grid, gd);
     }
   }
   relo_scene* s = new relo_scene();
@@ -280,13 +317,10 @@ relo_status relo_create_scene(const int32_t* coords, const float* tsdf, const ui
     cudaFree(s->d_tsdf);
     cudaFree(s->d_rgba);
     cudaFree(s->d_grid);
-    cudaFree(s->d_macro);
     delete s;
   };
-  if (!grid.empty() &&
-      (cudaMalloc(&s->d_grid, grid.size() * 4) != cudaSuccess || cudaMalloc(&s->d_macro, macro.size()) != cudaSuccess ||
-       cudaMemcpy(s->d_grid, grid.data(), grid.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-       cudaMemcpy(s->d_macro, macro.data(), macro.size(), cudaMemcpyHostToDevice) != cudaSuccess)) {
+  if (!grid.empty() && (cudaMalloc(&s->d_grid, grid.size() * 4) != cudaSuccess ||
+                        cudaMemcpy(s->d_grid, grid.data(), grid.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)) {
     cudaGetLastError();
     cleanup();
     return fail(RELO_ENOMEM, "device allocation for the scene grid failed");
@@ -323,7 +357,6 @@ relo_status relo_create_scene(const int32_t* coords, const float* tsdf, const ui
   v.block_size = (float)(8.0 * voxel);
   v.inv_block = (float)(1.0 / (8.0 * voxel));
   v.grid = (const int32_t*)s->d_grid;
-  v.macro = (const uint8_t*)s->d_macro;
   v.ox = g0[0];
   v.oy = g0[1];
   v.oz = g0[2];
@@ -341,14 +374,12 @@ void relo_destroy_scene(relo_scene* s) {
   cudaFree(s->d_tsdf);
   cudaFree(s->d_rgba);
   cudaFree(s->d_grid);
-  cudaFree(s->d_macro);
   delete s;
 }
 
 relo_status relo_scene_use_grid(relo_scene* s, int32_t enable) {
   if (!s) return fail(RELO_EINVAL, "scene is null");
   s->view.grid = enable ? (const int32_t*)s->d_grid : nullptr;
-  s->view.macro = enable ? (const uint8_t*)s->d_macro : nullptr;
   return RELO_OK;
 }
 

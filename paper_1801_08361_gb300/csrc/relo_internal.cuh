@@ -31,28 +31,26 @@ struct SceneView {
   int32_t n_blocks;
   int32_t max_chain;      // longest chain at build time (bounds the walk)
   float voxel, inv_voxel, mu, block_size, inv_block;
-  // Dense acceleration grids over the blocks' bounding box (null when the box is too large):
-  // grid holds the block index of every block coordinate in the box (-1 = unallocated) and
-  // macro one byte per 8 x 8 x 8 blocks (1 = some block inside is allocated).  Origins are
-  // multiples of 8 blocks so macro cells sit on the absolute lattice floor(block / 8).
+  // Dense grid over the blocks' bounding box (null when the box is too large): per block
+  // coordinate the block index, or -D for an unallocated block whose nearest allocated block is
+  // D >= 1 blocks away in the Chebyshev metric (every block within D - 1 of it is unallocated).
   const int32_t* grid;
-  const uint8_t* macro;
   int32_t ox, oy, oz;     // grid origin (block coordinates)
   int32_t gx, gy, gz;     // grid extent in blocks (multiples of 8)
 };
 
-// Block index through the dense grid (caller checks s.grid != nullptr).
+// Block index, or -D (see SceneView::grid), through the dense grid (caller checks s.grid).
+// Outside the box D is the Chebyshev distance to the box, a lower bound of the distance to any
+// allocated block.
 __device__ __forceinline__ int grid_block(const SceneView& s, int x, int y, int z) {
-  const unsigned a = (unsigned)(x - s.ox), b = (unsigned)(y - s.oy), c = (unsigned)(z - s.oz);
-  if (a >= (unsigned)s.gx || b >= (unsigned)s.gy || c >= (unsigned)s.gz) return -1;
+  const int a = x - s.ox, b = y - s.oy, c = z - s.oz;
+  if ((unsigned)a >= (unsigned)s.gx || (unsigned)b >= (unsigned)s.gy || (unsigned)c >= (unsigned)s.gz) {
+    const int da = a < 0 ? -a : a - (s.gx - 1);
+    const int db = b < 0 ? -b : b - (s.gy - 1);
+    const int dc = c < 0 ? -c : c - (s.gz - 1);
+    return -max(da, max(db, dc));
+  }
   return __ldg(&s.grid[((size_t)c * s.gy + b) * s.gx + a]);
-}
-
-// True if the 8 x 8 x 8-block macro cell holding block (x, y, z) has no allocated block.
-__device__ __forceinline__ bool macro_empty(const SceneView& s, int x, int y, int z) {
-  const unsigned a = (unsigned)(x - s.ox), b = (unsigned)(y - s.oy), c = (unsigned)(z - s.oz);
-  if (a >= (unsigned)s.gx || b >= (unsigned)s.gy || c >= (unsigned)s.gz) return true;
-  return __ldg(&s.macro[((size_t)(c >> 3) * (s.gy >> 3) + (b >> 3)) * (s.gx >> 3) + (a >> 3)]) == 0;
 }
 
 __host__ __device__ inline uint32_t block_hash(int x, int y, int z) {
@@ -365,7 +363,6 @@ struct relo_scene {
   void* d_tsdf;
   void* d_rgba;
   void* d_grid;
-  void* d_macro;
   int64_t n_blocks;
 };
 

@@ -52,11 +52,13 @@ __device__ __forceinline__ RayExit ray_exit(float3 d) {
   return r;
 }
 
-// Ray parameter at which the ray leaves the axis-aligned cell (cx, cy, cz) of the given size.
-__device__ __forceinline__ float cell_exit(float3 C, const RayExit& r, int cx, int cy, int cz, float size) {
-  const float lx = r.zx ? INFINITY : ((float)(cx + r.px) * size - C.x) * r.inv.x;
-  const float ly = r.zy ? INFINITY : ((float)(cy + r.py) * size - C.y) * r.inv.y;
-  const float lz = r.zz ? INFINITY : ((float)(cz + r.pz) * size - C.z) * r.inv.z;
+// Ray parameter at which the ray leaves the cube of blocks b - (r - 1) ... b + (r - 1) per axis
+// (r = 1: block b itself).  Its faces are block faces, (float)(integer) * block size as for a
+// single block, so the exit equals that of the last block a block-by-block walk would visit.
+__device__ __forceinline__ float cube_exit(float3 C, const RayExit& e, int bx, int by, int bz, int r, float bs) {
+  const float lx = e.zx ? INFINITY : ((float)(bx + (e.px ? r : 1 - r)) * bs - C.x) * e.inv.x;
+  const float ly = e.zy ? INFINITY : ((float)(by + (e.py ? r : 1 - r)) * bs - C.y) * e.inv.y;
+  const float lz = e.zz ? INFINITY : ((float)(bz + (e.pz ? r : 1 - r)) * bs - C.z) * e.inv.z;
   return fminf(lx, fminf(ly, lz));
 }
 
@@ -137,12 +139,11 @@ __device__ float march_ray(const SceneView& s, float3 C, float3 d, float dmin, f
     const int bx = i >> 3, by = j >> 3, bz = k >> 3;
     const int b = cached_block(s, c, bx, by, bz, err);
     if (b < 0) {
-      // free space up to the exit of this block -- or, when the 8^3-block macro cell around it
-      // is empty, of that cell: stepping block by block through an empty cell ends on the same
-      // exit plane, so the skip changes no sample the march evaluates
-      float lexit;
-      if (s.grid && macro_empty(s, bx, by, bz)) lexit = cell_exit(C, rx, bx >> 3, by >> 3, bz >> 3, 8.0f * s.block_size);
-      else lexit = cell_exit(C, rx, bx, by, bz, s.block_size);
+      // free space up to the exit of this block -- or, through the grid, of the cube of blocks
+      // around it that holds no allocated block (-b = its Chebyshev distance to one, so the
+      // cube's half-size is -b - 1 blocks): stepping block by block through that cube ends on
+      // the same exit plane, so the skip changes no sample the march evaluates
+      const float lexit = cube_exit(C, rx, bx, by, bz, -b, s.block_size);
       lam_prev = fmaxf(lexit, lam);
       f_prev = 1.0f;
       have_prev = true;

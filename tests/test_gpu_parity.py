@@ -100,6 +100,26 @@ def _raycast_parity_poses(oracle_room, gpu_room, intr, poses, noisy):
         assert (cg[dg == 0] == 0).all()
 
 
+def test_raycast_grid_skips_match_the_block_walk(room, gpu_room):
+    """Through the grid the march jumps over whole cubes of unallocated blocks; through the hash
+    it steps one block at a time.  Both end each free run on the same block face, so both
+    evaluate the same samples: the images agree (up to a last-bit difference of an exit
+    parameter where a ray crosses a block edge exactly)."""
+    world, _ = room
+    intr = synth.Intrinsics.for_size(320, 240)
+    for i, P in enumerate(synth.training_poses(world, 4, seed=23)):
+        noise = synth.depth_noise(240, 320, 90 + i)
+        dg, cg = gpu_render(gpu_room, intr, P, noise)
+        gpu_room.use_grid(False)
+        try:
+            dh, ch = gpu_render(gpu_room, intr, P, noise)
+        finally:
+            gpu_room.use_grid(True)
+        assert (dg == dh).mean() >= 0.9999
+        assert np.abs(dg.astype(int) - dh.astype(int)).max() <= 1
+        assert (np.abs(cg.astype(int) - ch.astype(int)).max(-1) <= 1).all()
+
+
 def test_raycast_empty_scene():
     from scenes import empty_blocks
     sc = B.Scene(empty_blocks(), 8)
