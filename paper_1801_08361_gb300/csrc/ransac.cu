@@ -61,9 +61,11 @@ __device__ __forceinline__ int entry_leaf(const RansacJob& job, int idx, const T
   return (int)u16_of(__ldg(&job.table[(size_t)idx * job.nv + (f >> 3)]), f & 7);
 }
 
-__device__ __forceinline__ float3 cam_point_f(int u, int v, int d, float fx, float fy, float cx, float cy) {
+// FP32 camera point with reciprocal focal lengths ifx = 1 / fx, ify = 1 / fy (a few ulp from the
+// FP64 point; the FP32 tests and scores that use it tolerate that).
+__device__ __forceinline__ float3 cam_point_f(int u, int v, int d, float ifx, float ify, float cx, float cy) {
   const float z = (float)d * 0.001f;
-  return make_float3(z * ((float)u - cx) / fx, z * ((float)v - cy) / fy, z);
+  return make_float3(z * ((float)u - cx) * ifx, z * ((float)v - cy) * ify, z);
 }
 
 // FP64 camera point in the oracle's operation order: z = d / 1000; x = (z (u - cx)) / fx.
@@ -190,16 +192,20 @@ __device__ __forceinline__ double cross_norm_d(const double* p0, const double* p
   return __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z)));
 }
 
+// Distance through the hardware reciprocal square root (relative error about 2^-22, i.e. below
+// 1e-5 m on the few-metre distances here and inside the guard band of the tests using it).
 __device__ __forceinline__ float dist_f(float3 a, float3 b) {
   const float x = a.x - b.x, y = a.y - b.y, z = a.z - b.z;
-  return sqrtf(x * x + y * y + z * z);
+  const float s = x * x + y * y + z * z;
+  return s > 0.f ? s * rsqrtf(s) : 0.f;
 }
 
-__device__ __forceinline__ float cross_norm_f(float3 p0, float3 p1, float3 p2) {
+// |cross(p1 - p0, p2 - p0)|^2 (compared against squared area bounds).
+__device__ __forceinline__ float cross_norm2_f(float3 p0, float3 p1, float3 p2) {
   const float ax = p1.x - p0.x, ay = p1.y - p0.y, az = p1.z - p0.z;
   const float bx = p2.x - p0.x, by = p2.y - p0.y, bz = p2.z - p0.z;
   const float x = ay * bz - az * by, y = az * bx - ax * bz, z = ax * by - ay * bx;
-  return sqrtf(x * x + y * y + z * z);
+  return x * x + y * y + z * z;
 }
 
 struct Corr {
@@ -245,19 +251,10 @@ __device__ __noinline__ bool exact_geometry(const RansacJob& job, int h, int j, 
          (cross_norm_d(wp[0], wp[1], wp[2]) >= job.min_area);
 }
 
-// 0: the try fails; 1: it passes; 2: a test lies inside the FP32 guard band (settle in FP64).
-// Loads one correspondence of a try: its camera point and its leaf's mode-0 mean; false when the
-// leaf id is outside the forest or the leaf is empty.
-__device__ __forceinline__ bool load_corr(const RansacJob& job, int idx, int tree, int L, float fx, float fy, float cx,
-                                          float cy, float3* p, float3* q) {
-  const TableEntry e = load_entry(job, idx);
-  const int leaf = entry_leaf(job, idx, e, tree);
-  if (leaf >= L) return false;
-  const float4 m = __ldg(&job.forest.top[(size_t)tree * L + leaf]);
-  if (m.w < 0.5f) return false;
-  *p = cam_point_f(e.u, e.v, e.depth, fx, fy, cx, cy);
-  *q = make_float3(m.x, m.y, m.z);
-  return true;
+// Mode-0 mean of a correspondence's leaf (w = its count; w < 0.5: empty leaf), or w = -1 when the
+// leaf id is outside the forest.
+__device__ __forceinline__ float4 corr_mode(const RansacJob& job, int tree, int leaf, int L) {
+  return leaf < L ? __ldg(&job.forest.top[(size_t)tree * L + leaf]) : make_float4(0.f, 0.f, 0.f, -1.f);
 }
 
 // Rigidity of one pair: 0 fails, 1 passes, 2 inside the guard band.
@@ -267,10 +264,12 @@ __device__ __forceinline__ int pair_status(float3 pa, float3 pb, float3 qa, floa
   return diff >= rig - kGuardRigid ? 2 : 1;
 }
 
-// The tests are a conjunction, so they can run in any order: the pair (0, 1) is tested before the
-// third correspondence is loaded, which most tries never reach.
-__device__ __forceinline__ int try_status(const RansacJob& job, int h, int j, int n_valid, float rig, float area,
-                                          float fx, float fy, float cx, float cy) {
+// 0: the try fails; 1: it passes; 2: a test lies inside the FP32 guard band (settle in FP64).
+// The tests are a conjunction of pure conditions, so their order does not change the outcome:
+// the two entries of the pair (0, 1) are loaded together, then their two modes, and that pair is
+// tested before the third correspondence is loaded, which most tries never reach.
+__device__ __forceinline__ int try_status(const RansacJob& job, int h, int j, int n_valid, float rig, float area_lo2,
+                                          float area_hi2, float ifx, float ify, float cx, float cy) {
   const uint4 x = philox4x32_10(make_uint4(1u, (uint32_t)h, (uint32_t)j, 0u), job.key0, job.key1);
   const int i0 = (int)uniform_below(x.x, (uint32_t)n_valid), i1 = (int)uniform_below(x.y, (uint32_t)n_valid);
   const int i2 = (int)uniform_below(x.z, (uint32_t)n_valid);
@@ -279,20 +278,28 @@ __device__ __forceinline__ int try_status(const RansacJob& job, int h, int j, in
   const int t0 = (int)(((x.w & 0xFFu) * T) >> 8), t1 = (int)((((x.w >> 8) & 0xFFu) * T) >> 8);
   const int t2 = (int)((((x.w >> 16) & 0xFFu) * T) >> 8);
   const int L = 1 << job.forest.D;
-  float3 p0, p1, p2, q0, q1, q2;
-  if (!load_corr(job, i0, t0, L, fx, fy, cx, cy, &p0, &q0)) return 0;
-  if (!load_corr(job, i1, t1, L, fx, fy, cx, cy, &p1, &q1)) return 0;
+  const TableEntry e0 = load_entry(job, i0), e1 = load_entry(job, i1);
+  const float4 m0 = corr_mode(job, t0, entry_leaf(job, i0, e0, t0), L);
+  const float4 m1 = corr_mode(job, t1, entry_leaf(job, i1, e1, t1), L);
+  if (m0.w < 0.5f || m1.w < 0.5f) return 0;
+  const float3 p0 = cam_point_f(e0.u, e0.v, e0.depth, ifx, ify, cx, cy);
+  const float3 p1 = cam_point_f(e1.u, e1.v, e1.depth, ifx, ify, cx, cy);
+  const float3 q0 = make_float3(m0.x, m0.y, m0.z), q1 = make_float3(m1.x, m1.y, m1.z);
   const int s01 = pair_status(p0, p1, q0, q1, rig);
   if (s01 == 0) return 0;
-  if (!load_corr(job, i2, t2, L, fx, fy, cx, cy, &p2, &q2)) return 0;
+  const TableEntry e2 = load_entry(job, i2);
+  const float4 m2 = corr_mode(job, t2, entry_leaf(job, i2, e2, t2), L);
+  if (m2.w < 0.5f) return 0;
+  const float3 p2 = cam_point_f(e2.u, e2.v, e2.depth, ifx, ify, cx, cy);
+  const float3 q2 = make_float3(m2.x, m2.y, m2.z);
   const int s02 = pair_status(p0, p2, q0, q2, rig);
   if (s02 == 0) return 0;
   const int s12 = pair_status(p1, p2, q1, q2, rig);
   if (s12 == 0) return 0;
   bool ambiguous = s01 == 2 || s02 == 2 || s12 == 2;
-  const float ac = cross_norm_f(p0, p1, p2), aw = cross_norm_f(q0, q1, q2);
-  if (ac < area - kGuardArea || aw < area - kGuardArea) return 0;
-  if (ac <= area + kGuardArea || aw <= area + kGuardArea) ambiguous = true;
+  const float ac2 = cross_norm2_f(p0, p1, p2), aw2 = cross_norm2_f(q0, q1, q2);
+  if (ac2 < area_lo2 || aw2 < area_lo2) return 0;
+  if (ac2 <= area_hi2 || aw2 <= area_hi2) ambiguous = true;
   return ambiguous ? 2 : 1;
 }
 
@@ -320,12 +327,15 @@ __global__ void __launch_bounds__(kSearchWarps * 32, RELO_SEARCH_MIN_BLOCKS)
   if (h >= job.K || job_skipped(job.skip)) return;
   const int n_valid = *job.n_valid;
   const float rig = (float)job.rigidity, area = (float)job.min_area;
-  const float fx = (float)job.fx, fy = (float)job.fy, cx = (float)job.cx, cy = (float)job.cy;
+  // the area test |cross| >= area with its guard band, on squares (both sides non-negative)
+  const float area_lo = fmaxf(area - kGuardArea, 0.f), area_hi = area + kGuardArea;
+  const float area_lo2 = area_lo * area_lo, area_hi2 = area_hi * area_hi;
+  const float ifx = (float)(1.0 / job.fx), ify = (float)(1.0 / job.fy), cx = (float)job.cx, cy = (float)job.cy;
   int found = INT_MAX;
   if (n_valid > 0) {
     for (int base = 0; base < job.max_tries && found == INT_MAX; base += 32) {
       const int j = base + lane;
-      const int st = j < job.max_tries ? try_status(job, h, j, n_valid, rig, area, fx, fy, cx, cy) : 0;
+      const int st = j < job.max_tries ? try_status(job, h, j, n_valid, rig, area_lo2, area_hi2, ifx, ify, cx, cy) : 0;
       unsigned mask = __ballot_sync(0xffffffffu, st != 0);
       while (mask) {
         const int w = __ffs(mask) - 1;
@@ -459,13 +469,13 @@ __global__ void __launch_bounds__(256) energy_kernel(const RansacJob* __restrict
   const int h = alive_in(job, r)[gw - alive_prefix[jid]];
   if (!job.hyp_ok[h] || *job.n_valid == 0) return;
   const PoseF P = pose_to_float(job.poses + 12 * (size_t)h);
-  const float fx = (float)job.fx, fy = (float)job.fy, cx = (float)job.cx, cy = (float)job.cy;
+  const float ifx = (float)(1.0 / job.fx), ify = (float)(1.0 / job.fy), cx = (float)job.cx, cy = (float)job.cy;
   float sum = 0.f;
   const int32_t* px = job.drawn + (size_t)r * job.B;
   for (int i = lane; i < job.B; i += 32) {
     const int idx = __ldg(&px[i]);
     const TableEntry e = load_entry(job, idx);
-    const float3 x = apply(P, cam_point_f(e.u, e.v, e.depth, fx, fy, cx, cy));
+    const float3 x = apply(P, cam_point_f(e.u, e.v, e.depth, ifx, ify, cx, cy));
     const float best = best_mode(job, idx, e, x, nullptr);
     sum += fminf(kLogEps, -best);
   }
@@ -544,11 +554,11 @@ __global__ void __launch_bounds__(256) refine_kernel(const RansacJob* __restrict
   const int h = alive_out(job, r)[gw - surv_prefix[jid]];
   if (!job.hyp_ok[h] || *job.n_valid == 0) return;
   const PoseF P = pose_to_float(job.poses + 12 * (size_t)h);
-  const float fx = (float)job.fx, fy = (float)job.fy, cx = (float)job.cx, cy = (float)job.cy;
+  const float ifx = (float)(1.0 / job.fx), ify = (float)(1.0 / job.fy), cx = (float)job.cx, cy = (float)job.cy;
   const int n_drawn = (r + 1) * job.B;
   const float r2 = (float)(job.inlier_dist * job.inlier_dist);
   const TableEntry e0 = load_entry(job, __ldg(&job.drawn[0]));
-  const float3 cref = cam_point_f(e0.u, e0.v, e0.depth, fx, fy, cx, cy);
+  const float3 cref = cam_point_f(e0.u, e0.v, e0.depth, ifx, ify, cx, cy);
   const float3 wref = apply(P, cref);
   float acc[16];
 #pragma unroll
@@ -556,7 +566,7 @@ __global__ void __launch_bounds__(256) refine_kernel(const RansacJob* __restrict
   for (int i = lane; i < n_drawn; i += 32) {
     const int idx = __ldg(&job.drawn[i]);
     const TableEntry e = load_entry(job, idx);
-    const float3 c = cam_point_f(e.u, e.v, e.depth, fx, fy, cx, cy);
+    const float3 c = cam_point_f(e.u, e.v, e.depth, ifx, ify, cx, cy);
     const float3 x = apply(P, c);
     float3 mu;
     const float best = best_mode(job, idx, e, x, &mu);
