@@ -72,7 +72,12 @@ void carve_ransac(Carver& c, RansacJob& j, int W, int H, int K, int B, int n_rou
   const int n_pix = W * H;
   j.nv = table_words(T);
   j.table = c.take<uint4>((size_t)n_pix * j.nv);
-  j.refit = c.take<float>((size_t)K * 24);
+  const int R = std::max(n_rounds, 1);
+  j.hs = 1 + (T + 1) / 2;
+  j.refit_parts = (R * B + kRefinePixels - 1) / kRefinePixels;
+  j.refit = c.take<float>((size_t)K * j.refit_parts * 16);
+  j.refit_ref = c.take<float>((size_t)K * 8);
+  j.pix = c.take<int4>((size_t)R * B * j.hs);
   j.chunk_count = c.take<int32_t>((n_pix + kCompactChunk - 1) / kCompactChunk);
   j.n_valid = c.take<int32_t>(1);
   j.poses = c.take<double>((size_t)K * 12);
@@ -111,13 +116,18 @@ void fill_ransac_job(RansacJob& j, const ForestView& fv, const uint16_t* depth, 
 }
 
 // Alive / survivor prefix tables for rounds 0..R-1 (each n_jobs + 1 ints).
+// Per round: prefix tables of the jobs' alive and surviving hypothesis counts, their totals and
+// their largest per-job values.
 void round_tables(const std::vector<int>& K, int R, std::vector<int32_t>& alive, std::vector<int32_t>& surv,
-                  std::vector<int>& tot_alive, std::vector<int>& tot_surv) {
+                  std::vector<int>& tot_alive, std::vector<int>& tot_surv, std::vector<int>& max_alive,
+                  std::vector<int>& max_surv) {
   const int n = (int)K.size();
   alive.assign((size_t)R * (n + 1), 0);
   surv.assign((size_t)R * (n + 1), 0);
   tot_alive.assign(R, 0);
   tot_surv.assign(R, 0);
+  max_alive.assign(R, 0);
+  max_surv.assign(R, 0);
   std::vector<int> cur(K);
   for (int r = 0; r < R; ++r) {
     int a = 0, s = 0;
@@ -127,6 +137,8 @@ void round_tables(const std::vector<int>& K, int R, std::vector<int32_t>& alive,
       if (cur[j] > 1) {
         a += cur[j];
         s += (cur[j] + 1) / 2;
+        max_alive[r] = std::max(max_alive[r], cur[j]);
+        max_surv[r] = std::max(max_surv[r], (cur[j] + 1) / 2);
         cur[j] = (cur[j] + 1) / 2;
       }
     }
@@ -147,10 +159,10 @@ namespace {
 
 struct RansacPass {
   RansacJob* d_jobs = nullptr;
-  int n = 0, R = 0, chunks = 0, hyps = 0;
+  int n = 0, R = 0, chunks = 0, hyps = 0, B = 0;
   int32_t* d_alive_prefix = nullptr;
   int32_t* d_surv_prefix = nullptr;
-  std::vector<int> tot_alive, tot_surv;
+  std::vector<int> tot_alive, tot_surv, max_alive, max_surv;
 };
 
 // Records ev (nullable) on s; external: as an event-record node when s is being captured.
@@ -172,7 +184,8 @@ relo_status run_pass(const RansacPass& p, cudaStream_t s, int* launches, cudaEve
   for (int r = 0; r < p.R; ++r) {
     if (p.tot_alive[r] == 0) continue;
     RELO_CUDA(launch_round(p.d_jobs, p.n, r, p.d_alive_prefix + (size_t)r * (p.n + 1), p.tot_alive[r],
-                           p.d_surv_prefix + (size_t)r * (p.n + 1), p.tot_surv[r], s));
+                           p.max_alive[r], p.d_surv_prefix + (size_t)r * (p.n + 1), p.tot_surv[r], p.max_surv[r],
+                           p.B, s));
     L += 5;
   }
   if (p.n > 0) {
@@ -692,7 +705,8 @@ relo_status single_run(Single& s, const relo_ransac_params* p, relo_pose_result*
   RansacPass b;
   b.n = 1;
   b.R = rounds_for(p->n_hyps);
-  round_tables(K, std::max(b.R, 1), at, su, b.tot_alive, b.tot_surv);
+  round_tables(K, std::max(b.R, 1), at, su, b.tot_alive, b.tot_surv, b.max_alive, b.max_surv);
+  b.B = p->batch;
   b.d_jobs = s.d_job;
   b.d_alive_prefix = s.d_alive;
   b.d_surv_prefix = s.d_surv;
@@ -807,7 +821,8 @@ relo_status relo_ransac_round(const relo_forest* f, const uint16_t* depth, const
   RELO_CUDA(cudaMemcpyAsync(s.d_surv, sp, sizeof(sp), cudaMemcpyHostToDevice, cs));
   RELO_CUDA(cudaMemsetAsync(j.err, 0, sizeof(int32_t), cs));
   RELO_CUDA(launch_compact(s.d_job, 1, s.chunks, cs));
-  RELO_CUDA(launch_round(s.d_job, 1, round, s.d_alive, n_alive, s.d_surv, (n_alive + 1) / 2, cs));
+  RELO_CUDA(launch_round(s.d_job, 1, round, s.d_alive, n_alive, n_alive, s.d_surv, (n_alive + 1) / 2,
+                         (n_alive + 1) / 2, p->batch, cs));
   return RELO_OK;
 }
 
@@ -1573,12 +1588,17 @@ void layout_batch(const relo_attempt* at, int n, const relo_ransac_params& p, ch
   b.passF.R = RF;
   b.passF.chunks = chF;
   b.passF.hyps = hyF;
-  round_tables(KL, std::max(RL, 1), h.alive_L, h.surv_L, b.passL.tot_alive, b.passL.tot_surv);
-  round_tables(KF, std::max(RF, 1), h.alive_F, h.surv_F, b.passF.tot_alive, b.passF.tot_surv);
-  b.passL.tot_alive.resize(RL);
-  b.passL.tot_surv.resize(RL);
-  b.passF.tot_alive.resize(RF);
-  b.passF.tot_surv.resize(RF);
+  round_tables(KL, std::max(RL, 1), h.alive_L, h.surv_L, b.passL.tot_alive, b.passL.tot_surv, b.passL.max_alive,
+               b.passL.max_surv);
+  round_tables(KF, std::max(RF, 1), h.alive_F, h.surv_F, b.passF.tot_alive, b.passF.tot_surv, b.passF.max_alive,
+               b.passF.max_surv);
+  b.passL.B = b.passF.B = p.batch;
+  for (RansacPass* q : {&b.passL, &b.passF}) {
+    q->tot_alive.resize(q->R);
+    q->tot_surv.resize(q->R);
+    q->max_alive.resize(q->R);
+    q->max_surv.resize(q->R);
+  }
   *bytes = c.off;
 }
 

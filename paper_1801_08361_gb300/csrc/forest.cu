@@ -15,9 +15,10 @@ namespace relo {
 // The division by the pixel's depth d uses one multiply-shift per probe: for 0 <= a < 2^25 and
 // 1 <= d < 2^16, floor(a / d) = (a * M) >> (25 + l) with l = ceil(log2 d) and
 // M = floor(2^(25+l) / d) + 1 (Granlund and Montgomery, "Division by invariant integers using
-// multiplication", PLDI 1994, round-up method); |delta| * 1000 <= 32768000 < 2^25.
+// multiplication", PLDI 1994, round-up method); |delta| * 1000 <= 32768000 < 2^25.  Since
+// 2^(l-1) < d, M <= 2^26 + 1 fits in 32 bits and the product is one 32 x 32 -> 64-bit multiply.
 struct DepthDivisor {
-  unsigned long long M;
+  uint32_t M;
   int shift;
 };
 
@@ -25,14 +26,14 @@ __device__ __forceinline__ DepthDivisor make_divisor(int d) {
   const int l = d > 1 ? 32 - __clz(d - 1) : 0;
   DepthDivisor q;
   q.shift = 25 + l;
-  q.M = (1ull << q.shift) / (unsigned long long)d + 1ull;
+  q.M = (uint32_t)((1ull << q.shift) / (unsigned long long)d + 1ull);
   return q;
 }
 
 __device__ __forceinline__ int probe(int x, int delta, const DepthDivisor& dv, int limit) {
   const int n = delta * 1000;
   const unsigned a = (unsigned)(n < 0 ? -n : n);
-  const int q = (int)(((unsigned long long)a * dv.M) >> dv.shift);
+  const int q = (int)(((unsigned long long)a * (unsigned long long)dv.M) >> dv.shift);
   const int p = x + (n < 0 ? -q : q);
   return min(max(p, 0), limit);
 }

@@ -416,7 +416,18 @@ cudaError_t launch_hypotheses(const RansacJob* jobs, int n_jobs, int total_hyps,
 __device__ __forceinline__ const int32_t* alive_in(const RansacJob& j, int r) { return (r & 1) ? j.alive_b : j.alive_a; }
 __device__ __forceinline__ int32_t* alive_out(const RansacJob& j, int r) { return (r & 1) ? j.alive_a : j.alive_b; }
 
-// Draw round r's B pixels (positions in the valid table), one CTA per job.
+// (first mode, mode count) of an entry's leaf in tree t: its modes are f.modes[first ..
+// first + count) in units of kModeFloats; count 0 for a leaf id outside the forest.
+__device__ __forceinline__ int2 tree_modes(const RansacJob& job, int idx, const TableEntry& e, int t, int L) {
+  const ForestView& f = job.forest;
+  const int leaf = entry_leaf(job, idx, e, t);
+  if (leaf >= L) return make_int2(0, 0);
+  const int node = t * L + leaf;
+  return make_int2(node * f.M, min((int)__ldg(&f.n_modes[node]), f.M));
+}
+
+// Draw round r's B pixels (positions in the valid table), one CTA per job, and write each drawn
+// pixel's record (camera point and where its modes are), which every hypothesis then reads.
 __global__ void draw_kernel(const RansacJob* __restrict__ jobs, const int32_t* __restrict__ alive_prefix, int r) {
   const int jid = blockIdx.x;
   if (alive_prefix[jid + 1] - alive_prefix[jid] == 0) return;
@@ -424,23 +435,35 @@ __global__ void draw_kernel(const RansacJob* __restrict__ jobs, const int32_t* _
   if (job_skipped(job.skip)) return;
   const int n_valid = *job.n_valid;
   if (n_valid == 0) return;
+  const float ifx = (float)(1.0 / job.fx), ify = (float)(1.0 / job.fy), cx = (float)job.cx, cy = (float)job.cy;
+  const int T = job.forest.T, L = 1 << job.forest.D;
   for (int i = threadIdx.x; i < job.B; i += blockDim.x) {
     const uint4 x = philox4x32_10(make_uint4(2u, (uint32_t)r, (uint32_t)i, 0u), job.key0, job.key1);
-    job.drawn[(size_t)r * job.B + i] = (int32_t)uniform_below(x.x, (uint32_t)n_valid);
+    const int idx = (int)uniform_below(x.x, (uint32_t)n_valid);
+    job.drawn[(size_t)r * job.B + i] = idx;
+    const TableEntry e = load_entry(job, idx);
+    const float3 c = cam_point_f(e.u, e.v, e.depth, ifx, ify, cx, cy);
+    int4* rec = job.pix + ((size_t)r * job.B + i) * job.hs;
+    rec[0] = make_int4(__float_as_int(c.x), __float_as_int(c.y), __float_as_int(c.z), 0);
+    for (int t = 0; t < T; t += 2) {
+      const int2 a = tree_modes(job, idx, e, t, L);
+      const int2 b = t + 1 < T ? tree_modes(job, idx, e, t + 1, L) : make_int2(0, 0);
+      rec[1 + t / 2] = make_int4(a.x, a.y, b.x, b.y);
+    }
   }
 }
 
-// Best mode of a drawn pixel under x: returns its score (-inf if none) and the mode's mean.
-__device__ __forceinline__ float best_mode(const RansacJob& job, int idx, const TableEntry& e, float3 x,
-                                           float3* mu_best) {
+// Best mode of a drawn pixel (its record) under x = P c, over trees then modes in order (the first
+// of equal scores wins): its score (-inf if none) and mean.  Every lane of a warp reads the same
+// record and modes, so each load is one broadcast.
+__device__ __forceinline__ float record_best(const RansacJob& job, const int4* __restrict__ rec, float3 x,
+                                             float3* mu_best) {
   const ForestView& f = job.forest;
-  const int L = 1 << f.D;
   float best = -INFINITY;
   for (int t = 0; t < f.T; ++t) {
-    const int leaf = entry_leaf(job, idx, e, t);
-    if (leaf >= L) continue;  // a leaf id outside the forest
-    const int nm = min((int)__ldg(&f.n_modes[(size_t)t * L + leaf]), f.M);
-    const float4* m = reinterpret_cast<const float4*>(f.modes + ((size_t)t * L + leaf) * f.M * kModeFloats);
+    const int4 w = __ldg(&rec[1 + t / 2]);
+    const int first = (t & 1) ? w.z : w.x, nm = (t & 1) ? w.w : w.y;
+    const float4* m = reinterpret_cast<const float4*>(f.modes + (size_t)first * kModeFloats);
     for (int k = 0; k < nm; ++k) {
       const float4 a = __ldg(&m[3 * k]), b = __ldg(&m[3 * k + 1]), c = __ldg(&m[3 * k + 2]);
       const float dx = x.x - a.x, dy = x.y - a.y, dz = x.z - a.z;
@@ -457,32 +480,46 @@ __device__ __forceinline__ float best_mode(const RansacJob& job, int idx, const 
   return best;
 }
 
-// Energies of round r: warp per alive hypothesis.
-__global__ void __launch_bounds__(256) energy_kernel(const RansacJob* __restrict__ jobs, int n_jobs,
-                                                     const int32_t* __restrict__ alive_prefix, int total, int r) {
-  const int gw = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (gw >= total) return;
-  const int jid = find_job_by(alive_prefix, n_jobs, gw);
-  const RansacJob& job = jobs[jid];
-  if (job_skipped(job.skip)) return;
-  const int h = alive_in(job, r)[gw - alive_prefix[jid]];
-  if (!job.hyp_ok[h] || *job.n_valid == 0) return;
-  const PoseF P = pose_to_float(job.poses + 12 * (size_t)h);
-  const float ifx = (float)(1.0 / job.fx), ify = (float)(1.0 / job.fy), cx = (float)job.cx, cy = (float)job.cy;
-  float sum = 0.f;
-  const int32_t* px = job.drawn + (size_t)r * job.B;
-  for (int i = lane; i < job.B; i += 32) {
-    const int idx = __ldg(&px[i]);
-    const TableEntry e = load_entry(job, idx);
-    const float3 x = apply(P, cam_point_f(e.u, e.v, e.depth, ifx, ify, cx, cy));
-    const float best = best_mode(job, idx, e, x, nullptr);
-    sum += fminf(kLogEps, -best);
-  }
-  sum = warp_sum(sum);
-  if (lane == 0) job.energy[h] += (double)sum;
+__device__ __forceinline__ float3 record_point(const int4* __restrict__ rec) {
+  const int4 w = __ldg(&rec[0]);
+  return make_float3(__int_as_float(w.x), __int_as_float(w.y), __int_as_float(w.z));
 }
 
+// Round kernels: a CTA takes 32 hypotheses of one job (one per lane) and its warps split the
+// pixels, each warp walking every kRoundWarps-th pixel; per-warp partial sums are combined in
+// warp order, so the result does not depend on scheduling.
+constexpr int kRoundWarps = 8;
+
+// Energies of round r: grid (hypothesis chunks, jobs).
+__global__ void __launch_bounds__(kRoundWarps * 32) energy_kernel(const RansacJob* __restrict__ jobs,
+                                                                  const int32_t* __restrict__ alive_prefix, int r) {
+  const int jid = blockIdx.y;
+  const int n_alive = alive_prefix[jid + 1] - alive_prefix[jid];
+  if ((int)blockIdx.x * 32 >= n_alive) return;
+  const RansacJob& job = jobs[jid];
+  if (job_skipped(job.skip) || *job.n_valid == 0) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int a = (int)blockIdx.x * 32 + lane;
+  const int h = a < n_alive ? alive_in(job, r)[a] : 0;
+  const bool valid = a < n_alive && job.hyp_ok[h];
+  const PoseF P = pose_to_float(job.poses + 12 * (size_t)h);
+  float sum = 0.f;
+  const int4* recs = job.pix + (size_t)r * job.B * job.hs;
+  for (int i = warp; i < job.B; i += kRoundWarps) {
+    const int4* rec = recs + (size_t)i * job.hs;
+    const float best = record_best(job, rec, apply(P, record_point(rec)), nullptr);
+    sum += fminf(kLogEps, -best);
+  }
+  __shared__ float part[kRoundWarps][32];
+  part[warp][lane] = sum;
+  __syncthreads();
+  if (warp == 0 && valid) {
+    float e = 0.f;
+#pragma unroll
+    for (int w = 0; w < kRoundWarps; ++w) e += part[w][lane];
+    job.energy[h] += (double)e;
+  }
+}
 __device__ __forceinline__ unsigned long long order_key(double e) {
   unsigned long long b = (unsigned long long)__double_as_longlong(e);
   return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
@@ -537,73 +574,79 @@ __global__ void __launch_bounds__(1024) select_kernel(const RansacJob* __restric
   for (int i = threadIdx.x; i < keep; i += blockDim.x) out[i] = sidx[i];
 }
 
-// Re-fit sums: warp per survivor over all pixels drawn in rounds 0..r.  Sums are taken about a
-// reference correspondence (the first drawn pixel and its predicted scene point) so one FP32
-// pass gives well-conditioned centroids and cross-covariance:
-//   refit[h] = {n, sum dc (3), sum dw (3), sum dc dw^T (9), c_ref (3), w_ref (3), 0, 0}.
-constexpr int kRefitFloats = 24;
-
-__global__ void __launch_bounds__(256) refine_kernel(const RansacJob* __restrict__ jobs, int n_jobs,
-                                                     const int32_t* __restrict__ surv_prefix, int total, int r) {
-  const int gw = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (gw >= total) return;
-  const int jid = find_job_by(surv_prefix, n_jobs, gw);
+// Re-fit sums over all pixels drawn in rounds 0..r: grid (survivor chunks, parts of kRefinePixels
+// pixels, jobs).  Sums are taken about a reference correspondence (the first drawn pixel and its
+// predicted scene point) so one FP32 pass gives well-conditioned centroids and cross-covariance:
+//   refit[h][part] = {n, sum dc (3), sum dw (3), sum dc dw^T (9)},  refit_ref[h] = {c_ref, w_ref}.
+__global__ void __launch_bounds__(kRoundWarps * 32) refine_kernel(const RansacJob* __restrict__ jobs,
+                                                                  const int32_t* __restrict__ surv_prefix, int r) {
+  const int jid = blockIdx.z, part = blockIdx.y;
+  const int n_surv = surv_prefix[jid + 1] - surv_prefix[jid];
+  if ((int)blockIdx.x * 32 >= n_surv) return;
   const RansacJob& job = jobs[jid];
-  if (job_skipped(job.skip)) return;
-  const int h = alive_out(job, r)[gw - surv_prefix[jid]];
-  if (!job.hyp_ok[h] || *job.n_valid == 0) return;
-  const PoseF P = pose_to_float(job.poses + 12 * (size_t)h);
-  const float ifx = (float)(1.0 / job.fx), ify = (float)(1.0 / job.fy), cx = (float)job.cx, cy = (float)job.cy;
   const int n_drawn = (r + 1) * job.B;
+  const int p0 = part * kRefinePixels;
+  if (p0 >= n_drawn || job_skipped(job.skip) || *job.n_valid == 0) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int a = (int)blockIdx.x * 32 + lane;
+  const int h = a < n_surv ? alive_out(job, r)[a] : 0;
+  const bool valid = a < n_surv && job.hyp_ok[h];
+  const PoseF P = pose_to_float(job.poses + 12 * (size_t)h);
   const float r2 = (float)(job.inlier_dist * job.inlier_dist);
-  const TableEntry e0 = load_entry(job, __ldg(&job.drawn[0]));
-  const float3 cref = cam_point_f(e0.u, e0.v, e0.depth, ifx, ify, cx, cy);
+  const float3 cref = record_point(job.pix);
   const float3 wref = apply(P, cref);
   float acc[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) acc[q] = 0.f;
-  for (int i = lane; i < n_drawn; i += 32) {
-    const int idx = __ldg(&job.drawn[i]);
-    const TableEntry e = load_entry(job, idx);
-    const float3 c = cam_point_f(e.u, e.v, e.depth, ifx, ify, cx, cy);
+  const int p1 = min(p0 + kRefinePixels, n_drawn);
+  for (int i = p0 + warp; i < p1; i += kRoundWarps) {
+    const int4* rec = job.pix + (size_t)i * job.hs;
+    const float3 c = record_point(rec);
     const float3 x = apply(P, c);
     float3 mu;
-    const float best = best_mode(job, idx, e, x, &mu);
+    const float best = record_best(job, rec, x, &mu);
     if (best == -INFINITY) continue;
     const float dx = x.x - mu.x, dy = x.y - mu.y, dz = x.z - mu.z;
     if (dx * dx + dy * dy + dz * dz < r2) {
-      const float a[3] = {c.x - cref.x, c.y - cref.y, c.z - cref.z};
-      const float b[3] = {mu.x - wref.x, mu.y - wref.y, mu.z - wref.z};
+      const float u[3] = {c.x - cref.x, c.y - cref.y, c.z - cref.z};
+      const float w[3] = {mu.x - wref.x, mu.y - wref.y, mu.z - wref.z};
       acc[0] += 1.f;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        acc[1 + k] += a[k];
-        acc[4 + k] += b[k];
+        acc[1 + k] += u[k];
+        acc[4 + k] += w[k];
       }
 #pragma unroll
       for (int p = 0; p < 3; ++p)
 #pragma unroll
-        for (int q = 0; q < 3; ++q) acc[7 + 3 * p + q] = fmaf(a[p], b[q], acc[7 + 3 * p + q]);
+        for (int q = 0; q < 3; ++q) acc[7 + 3 * p + q] = fmaf(u[p], w[q], acc[7 + 3 * p + q]);
     }
   }
+  __shared__ float red[kRoundWarps][16][32];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) acc[q] = warp_sum(acc[q]);
-  if (lane < 16) {
-    float v = acc[0];
+  for (int q = 0; q < 16; ++q) red[warp][q][lane] = acc[q];
+  __syncthreads();
+  if (!valid) return;
+  // warps w then write one sum each: sum q over the kRoundWarps partials, in warp order
+  for (int q = warp; q < 16; q += kRoundWarps) {
+    float v = 0.f;
 #pragma unroll
-    for (int q = 1; q < 16; ++q)
-      if (lane == q) v = acc[q];
-    job.refit[(size_t)h * kRefitFloats + lane] = v;
-  } else if (lane < 22) {
-    const float v = lane == 16 ? cref.x : lane == 17 ? cref.y : lane == 18 ? cref.z
-                  : lane == 19 ? wref.x : lane == 20 ? wref.y : wref.z;
-    job.refit[(size_t)h * kRefitFloats + lane] = v;
+    for (int w = 0; w < kRoundWarps; ++w) v += red[w][q][lane];
+    job.refit[((size_t)h * job.refit_parts + part) * 16 + q] = v;
   }
-  if (lane == 0) job.inliers[h] = (int)acc[0];
+  if (part == 0 && warp == 0) {
+    float* ref = job.refit_ref + (size_t)h * 8;
+    ref[0] = cref.x;
+    ref[1] = cref.y;
+    ref[2] = cref.z;
+    ref[3] = wref.x;
+    ref[4] = wref.y;
+    ref[5] = wref.z;
+  }
 }
 
-// Re-fit solve: thread per survivor; FP64 Horn on the centroids and cross-covariance.
+// Re-fit solve: thread per survivor; the parts' sums are added in order in FP64, then FP64 Horn on
+// the centroids and cross-covariance (>= 3 inliers, else the pose is kept).
 __global__ void __launch_bounds__(128) refit_kernel(const RansacJob* __restrict__ jobs, int n_jobs,
                                                     const int32_t* __restrict__ surv_prefix, int total, int r) {
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -613,32 +656,40 @@ __global__ void __launch_bounds__(128) refit_kernel(const RansacJob* __restrict_
   if (job_skipped(job.skip)) return;
   const int h = alive_out(job, r)[gid - surv_prefix[jid]];
   if (!job.hyp_ok[h] || *job.n_valid == 0) return;
-  const float* f = job.refit + (size_t)h * kRefitFloats;
+  const int parts = ((r + 1) * job.B + kRefinePixels - 1) / kRefinePixels;
+  double f[16];
+  for (int q = 0; q < 16; ++q) f[q] = 0.0;
+  for (int p = 0; p < parts; ++p) {
+    const float* src = job.refit + ((size_t)h * job.refit_parts + p) * 16;
+    for (int q = 0; q < 16; ++q) f[q] += (double)src[q];
+  }
+  job.inliers[h] = (int)f[0];
   const double n = f[0];
   if (n < 3.0) return;
+  const float* ref = job.refit_ref + (size_t)h * 8;
   double mc[3], mw[3], cb[3], wb[3], S[9];
   for (int k = 0; k < 3; ++k) {
     mc[k] = f[1 + k] / n;
     mw[k] = f[4 + k] / n;
-    cb[k] = (double)f[16 + k] + mc[k];
-    wb[k] = (double)f[19 + k] + mw[k];
+    cb[k] = (double)ref[k] + mc[k];
+    wb[k] = (double)ref[3 + k] + mw[k];
   }
   for (int p = 0; p < 3; ++p)
-    for (int q = 0; q < 3; ++q) S[3 * p + q] = (double)f[7 + 3 * p + q] - n * mc[p] * mw[q];
+    for (int q = 0; q < 3; ++q) S[3 * p + q] = f[7 + 3 * p + q] - n * mc[p] * mw[q];
   horn_pose(S, cb, wb, job.poses + 12 * (size_t)h);
 }
 
 cudaError_t launch_round(const RansacJob* jobs, int n_jobs, int round, const int32_t* alive_prefix_dev,
-                         int total_alive, const int32_t* surv_prefix_dev, int total_surv, cudaStream_t s) {
+                         int total_alive, int max_alive, const int32_t* surv_prefix_dev, int total_surv, int max_surv,
+                         int B, cudaStream_t s) {
   if (total_alive <= 0) return cudaSuccess;
   draw_kernel<<<n_jobs, 256, 0, s>>>(jobs, alive_prefix_dev, round);
-  energy_kernel<<<(unsigned)((total_alive * 32 + 255) / 256), 256, 0, s>>>(jobs, n_jobs, alive_prefix_dev,
-                                                                           total_alive, round);
+  energy_kernel<<<dim3((max_alive + 31) / 32, n_jobs), kRoundWarps * 32, 0, s>>>(jobs, alive_prefix_dev, round);
   // the largest alive set (4096) bounds the shared memory of the sort
   select_kernel<<<n_jobs, 1024, 4096 * (sizeof(unsigned long long) + sizeof(int)), s>>>(jobs, alive_prefix_dev,
                                                                                         round);
-  refine_kernel<<<(unsigned)((total_surv * 32 + 255) / 256), 256, 0, s>>>(jobs, n_jobs, surv_prefix_dev,
-                                                                          total_surv, round);
+  const int parts = ((round + 1) * B + kRefinePixels - 1) / kRefinePixels;
+  refine_kernel<<<dim3((max_surv + 31) / 32, parts, n_jobs), kRoundWarps * 32, 0, s>>>(jobs, surv_prefix_dev, round);
   refit_kernel<<<(unsigned)((total_surv + 127) / 128), 128, 0, s>>>(jobs, n_jobs, surv_prefix_dev, total_surv,
                                                                      round);
   return cudaGetLastError();

@@ -282,7 +282,13 @@ struct RansacJob {
   int32_t* alive_b;            // [K]
   int32_t* drawn;              // [n_rounds * B] positions in the valid-pixel table
   int32_t* inliers;            // [K]
-  float* refit;                // [K][16] per-survivor sums for the FP64 re-fit
+  float* refit;                // [K][refit_parts][16] per-survivor inlier sums, one block per part of
+                               // kRefinePixels drawn pixels (summed in order by the FP64 re-fit)
+  float* refit_ref;            // [K][8] reference correspondence of those sums: c_ref (3), w_ref (3)
+  int4* pix;                   // [n_rounds * B][hs] drawn pixels: camera point (FP32 bits), then
+                               // (first mode, mode count) of the pixel's leaf in each tree, two per word
+  int32_t hs;                  // int4 words per drawn-pixel record: 1 + ceil(T / 2)
+  int32_t refit_parts;         // blocks per hypothesis in refit: ceil(n_rounds * B / kRefinePixels)
   int32_t* err;                // [1]
   relo_pose_result* result;    // device
   int32_t chunk_begin;         // flattened compaction chunks
@@ -297,6 +303,7 @@ struct RansacJob {
 __device__ __forceinline__ bool job_skipped(const int32_t* skip) { return skip != nullptr && *skip != 0; }
 
 constexpr int kCompactChunk = 4096;
+constexpr int kRefinePixels = 64;  // drawn pixels per part of the re-fit sums
 
 // Workspace carving helper (256-byte aligned sub-buffers).
 struct Carver {
@@ -336,7 +343,8 @@ cudaError_t launch_compact(const RansacJob* jobs, int n_jobs, int total_chunks, 
 cudaError_t launch_hypotheses(const RansacJob* jobs, int n_jobs, int total_hyps, cudaStream_t s);
 // round r: prefix[n_jobs + 1] = flattened alive-hypothesis offsets of the jobs still running
 cudaError_t launch_round(const RansacJob* jobs, int n_jobs, int round, const int32_t* alive_prefix_dev,
-                         int total_alive, const int32_t* surv_prefix_dev, int total_surv, cudaStream_t s);
+                         int total_alive, int max_alive, const int32_t* surv_prefix_dev, int total_surv, int max_surv,
+                         int B, cudaStream_t s);
 cudaError_t launch_finalise(const RansacJob* jobs, int n_jobs, cudaStream_t s);
 
 
