@@ -39,9 +39,17 @@ def _stale(out: str, deps: list[str]) -> bool:
 def build_cuda(force: bool = False, verbose: bool = False) -> str:
     hdrs = [os.path.join(CSRC, "relo_internal.cuh"), os.path.join(CSRC, "regressor.cuh"), os.path.join(ROOT, "include", "relo.h")]
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
+    bdir = os.path.join(ROOT, "_build", "relo")
+    # the objects depend on the compile flags too: a change of flags rebuilds everything
+    stamp = os.path.join(bdir, "flags")
+    flags = " ".join(NVCC_FLAGS)
+    try:
+        with open(stamp) as f:
+            force = force or f.read() != flags
+    except OSError:
+        force = True
     if not force and not _stale(LIB, srcs + hdrs):
         return LIB
-    bdir = os.path.join(ROOT, "_build", "relo")
     os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
     procs, objs = [], []
@@ -61,6 +69,8 @@ def build_cuda(force: bool = False, verbose: bool = False) -> str:
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
     subprocess.check_call(cmd)
     os.replace(tmp, LIB)
+    with open(stamp, "w") as f:
+        f.write(flags)
     return LIB
 
 

@@ -264,31 +264,54 @@ __device__ __forceinline__ int pair_status(float3 pa, float3 pb, float3 qa, floa
   return diff >= rig - kGuardRigid ? 2 : 1;
 }
 
+// The draws of one try: three table positions and three trees.
+struct TryDraw {
+  int i0, i1, i2, t0, t1, t2;
+};
+
+__device__ __forceinline__ TryDraw draw_indices(const RansacJob& job, int h, int j, int n_valid) {
+  const uint4 x = philox4x32_10(make_uint4(1u, (uint32_t)h, (uint32_t)j, 0u), job.key0, job.key1);
+  const uint32_t T = (uint32_t)job.forest.T;
+  TryDraw d;
+  d.i0 = (int)uniform_below(x.x, (uint32_t)n_valid);
+  d.i1 = (int)uniform_below(x.y, (uint32_t)n_valid);
+  d.i2 = (int)uniform_below(x.z, (uint32_t)n_valid);
+  d.t0 = (int)(((x.w & 0xFFu) * T) >> 8);
+  d.t1 = (int)((((x.w >> 8) & 0xFFu) * T) >> 8);
+  d.t2 = (int)((((x.w >> 16) & 0xFFu) * T) >> 8);
+  return d;
+}
+
+// The first pair of a try, loaded: entries and mode-0 means of correspondences 0 and 1.
+struct TryPair {
+  TableEntry e0, e1;
+  float4 m0, m1;
+};
+
+__device__ __forceinline__ TryPair load_pair(const RansacJob& job, const TryDraw& d, int L) {
+  TryPair p;
+  p.e0 = load_entry(job, d.i0);
+  p.e1 = load_entry(job, d.i1);
+  p.m0 = corr_mode(job, d.t0, entry_leaf(job, d.i0, p.e0, d.t0), L);
+  p.m1 = corr_mode(job, d.t1, entry_leaf(job, d.i1, p.e1, d.t1), L);
+  return p;
+}
+
 // 0: the try fails; 1: it passes; 2: a test lies inside the FP32 guard band (settle in FP64).
 // The tests are a conjunction of pure conditions, so their order does not change the outcome:
-// the two entries of the pair (0, 1) are loaded together, then their two modes, and that pair is
-// tested before the third correspondence is loaded, which most tries never reach.
-__device__ __forceinline__ int try_status(const RansacJob& job, int h, int j, int n_valid, float rig, float area_lo2,
-                                          float area_hi2, float ifx, float ify, float cx, float cy) {
-  const uint4 x = philox4x32_10(make_uint4(1u, (uint32_t)h, (uint32_t)j, 0u), job.key0, job.key1);
-  const int i0 = (int)uniform_below(x.x, (uint32_t)n_valid), i1 = (int)uniform_below(x.y, (uint32_t)n_valid);
-  const int i2 = (int)uniform_below(x.z, (uint32_t)n_valid);
-  if (i0 == i1 || i0 == i2 || i1 == i2) return 0;
-  const uint32_t T = (uint32_t)job.forest.T;
-  const int t0 = (int)(((x.w & 0xFFu) * T) >> 8), t1 = (int)((((x.w >> 8) & 0xFFu) * T) >> 8);
-  const int t2 = (int)((((x.w >> 16) & 0xFFu) * T) >> 8);
-  const int L = 1 << job.forest.D;
-  const TableEntry e0 = load_entry(job, i0), e1 = load_entry(job, i1);
-  const float4 m0 = corr_mode(job, t0, entry_leaf(job, i0, e0, t0), L);
-  const float4 m1 = corr_mode(job, t1, entry_leaf(job, i1, e1, t1), L);
-  if (m0.w < 0.5f || m1.w < 0.5f) return 0;
-  const float3 p0 = cam_point_f(e0.u, e0.v, e0.depth, ifx, ify, cx, cy);
-  const float3 p1 = cam_point_f(e1.u, e1.v, e1.depth, ifx, ify, cx, cy);
-  const float3 q0 = make_float3(m0.x, m0.y, m0.z), q1 = make_float3(m1.x, m1.y, m1.z);
+// the pair (0, 1) (already loaded) is tested before the third correspondence is loaded, which
+// most tries never reach.
+__device__ __forceinline__ int try_status(const RansacJob& job, const TryDraw& d, const TryPair& pr, int L, float rig,
+                                          float area_lo2, float area_hi2, float ifx, float ify, float cx, float cy) {
+  if (d.i0 == d.i1 || d.i0 == d.i2 || d.i1 == d.i2) return 0;
+  if (pr.m0.w < 0.5f || pr.m1.w < 0.5f) return 0;
+  const float3 p0 = cam_point_f(pr.e0.u, pr.e0.v, pr.e0.depth, ifx, ify, cx, cy);
+  const float3 p1 = cam_point_f(pr.e1.u, pr.e1.v, pr.e1.depth, ifx, ify, cx, cy);
+  const float3 q0 = make_float3(pr.m0.x, pr.m0.y, pr.m0.z), q1 = make_float3(pr.m1.x, pr.m1.y, pr.m1.z);
   const int s01 = pair_status(p0, p1, q0, q1, rig);
   if (s01 == 0) return 0;
-  const TableEntry e2 = load_entry(job, i2);
-  const float4 m2 = corr_mode(job, t2, entry_leaf(job, i2, e2, t2), L);
+  const TableEntry e2 = load_entry(job, d.i2);
+  const float4 m2 = corr_mode(job, d.t2, entry_leaf(job, d.i2, e2, d.t2), L);
   if (m2.w < 0.5f) return 0;
   const float3 p2 = cam_point_f(e2.u, e2.v, e2.depth, ifx, ify, cx, cy);
   const float3 q2 = make_float3(m2.x, m2.y, m2.z);
@@ -303,13 +326,33 @@ __device__ __forceinline__ int try_status(const RansacJob& job, int h, int j, in
   return ambiguous ? 2 : 1;
 }
 
-// One warp per hypothesis (four per CTA, no block-wide barriers): each step evaluates 32 tries
-// and keeps the first one not failing, settling guard-band tries in FP64 in order.
+// One warp per hypothesis (four per CTA, no block-wide barriers): each step evaluates 64 tries,
+// two per lane (tries base + lane and base + 32 + lane, whose loads are issued together), and
+// keeps the first one not failing in try order, settling guard-band tries in FP64 in order.
 constexpr int kSearchWarps = 4;
 
-// CTAs per SM for the search (8 x 128 threads: the fastest setting of a sweep on the house workload)
+// first try of mask (bits = lanes) that passes, settling guard-band statuses in FP64; -1 if none
+__device__ __forceinline__ int first_passing(const RansacJob& job, int h, int n_valid, unsigned mask, int st,
+                                             int j, int lane) {
+  while (mask) {
+    const int w = __ffs(mask) - 1;
+    const int sw = __shfl_sync(0xffffffffu, st, w);
+    int ok = sw == 1;
+    if (!ok) {
+      int e = 0;
+      if (lane == w) e = exact_geometry(job, h, j, n_valid) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, e, w);
+    }
+    if (ok) return w;
+    mask &= mask - 1;  // rejected in FP64: consider the next try of this step
+  }
+  return -1;
+}
+
+// CTAs per SM for the search (4 x 128 threads, i.e. up to 128 registers for the two tries in
+// flight per lane: the fastest of 4, 5, 6 and 8 on the house workload)
 #ifndef RELO_SEARCH_MIN_BLOCKS
-#define RELO_SEARCH_MIN_BLOCKS 8
+#define RELO_SEARCH_MIN_BLOCKS 4
 #endif
 __global__ void __launch_bounds__(kSearchWarps * 32, RELO_SEARCH_MIN_BLOCKS)
     search_kernel(const RansacJob* __restrict__ jobs, int n_jobs, int total) {
@@ -331,27 +374,22 @@ __global__ void __launch_bounds__(kSearchWarps * 32, RELO_SEARCH_MIN_BLOCKS)
   const float area_lo = fmaxf(area - kGuardArea, 0.f), area_hi = area + kGuardArea;
   const float area_lo2 = area_lo * area_lo, area_hi2 = area_hi * area_hi;
   const float ifx = (float)(1.0 / job.fx), ify = (float)(1.0 / job.fy), cx = (float)job.cx, cy = (float)job.cy;
+  const int L = 1 << job.forest.D;
   int found = INT_MAX;
   if (n_valid > 0) {
-    for (int base = 0; base < job.max_tries && found == INT_MAX; base += 32) {
-      const int j = base + lane;
-      const int st = j < job.max_tries ? try_status(job, h, j, n_valid, rig, area_lo2, area_hi2, ifx, ify, cx, cy) : 0;
-      unsigned mask = __ballot_sync(0xffffffffu, st != 0);
-      while (mask) {
-        const int w = __ffs(mask) - 1;
-        const int sw = __shfl_sync(0xffffffffu, st, w);
-        int ok = sw == 1;
-        if (!ok) {
-          int e = 0;
-          if (lane == w) e = exact_geometry(job, h, j, n_valid) ? 1 : 0;
-          ok = __shfl_sync(0xffffffffu, e, w);
-        }
-        if (ok) {
-          found = base + w;
-          break;
-        }
-        mask &= mask - 1;  // rejected in FP64: consider the next try of this step
+    for (int base = 0; base < job.max_tries && found == INT_MAX; base += 64) {
+      const int ja = base + lane, jb = base + 32 + lane;
+      const TryDraw da = draw_indices(job, h, ja, n_valid), db = draw_indices(job, h, jb, n_valid);
+      const TryPair pa = load_pair(job, da, L), pb = load_pair(job, db, L);
+      const int sa = ja < job.max_tries ? try_status(job, da, pa, L, rig, area_lo2, area_hi2, ifx, ify, cx, cy) : 0;
+      const int sb = jb < job.max_tries ? try_status(job, db, pb, L, rig, area_lo2, area_hi2, ifx, ify, cx, cy) : 0;
+      int w = first_passing(job, h, n_valid, __ballot_sync(0xffffffffu, sa != 0), sa, ja, lane);
+      if (w >= 0) {
+        found = base + w;
+        break;
       }
+      w = first_passing(job, h, n_valid, __ballot_sync(0xffffffffu, sb != 0), sb, jb, lane);
+      if (w >= 0) found = base + 32 + w;
     }
   }
   if (lane == 0) {
