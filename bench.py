@@ -50,10 +50,21 @@ L2_FLUSH_BYTES = 512 << 20
 # voxels (4 B tsdf, 4 B colour) and block-table entries (16 B) touched, averaged over 8 query views
 # of this workload (oracle/algorithmic_bytes.py). A verification stage is its raycast plus a
 # one-block-per-attempt decision whose bytes are negligible.
+# The forest stage reads each query pixel's depth (2 B) and colour (4 B) once and writes T = 5
+# leaf ids (10 B); its 2.6 MB of nodes per launch are negligible.
 ALG_BYTES_PER_PIXEL = {
     "query_raycast": 50.66,
+    "forest_eval": 16.0,
     "forest_verify": 35.87,
     "learned_verify": 35.87,
+}
+# DRAM bytes (read + write) per launch of the stage's main kernel, from the ncu capture summarised
+# in profiles/attempt_kernels_house_640x480_batch128.md (None: not captured for the current code).
+PROFILED_TRAFFIC_BYTES = {
+    "query_raycast": 3.039e9 + 0.236e9,
+    "forest_eval": 0.241e9 + 0.352e9,
+    "forest_hypotheses": 0.636e9 + 0.005e9,
+    "forest_verify": None,
 }
 
 
@@ -66,6 +77,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=0, help="(ncu) run this many steps and exit, no JSON")
+    ap.add_argument("--train-steps", type=int, default=2000,
+                    help="online training steps of the learned regressor (0: skip the learned path)")
     return ap.parse_args()
 
 
@@ -321,14 +334,16 @@ def run_ours(args):
     for st, raw in results:
         for k in range(A):
             r = B.result_from_bytes(raw[k * B.RESULT_BYTES:(k + 1) * B.RESULT_BYTES])
-            P = st["qs"][k]
-            dt = float(np.linalg.norm(r["pose"][:3, 3] - P[:3, 3]))
-            cang = (np.trace(r["pose"][:3, :3] @ P[:3, :3].T) - 1) / 2
-            dr = math.degrees(math.acos(max(-1.0, min(1.0, cang))))
-            succ += int(r["status"] == 0 and dt <= 0.05 and dr <= 5.0)
+            succ += int(success(r, st["qs"][k]))
             tries_per_step += r["tries"]
             ver += int(r["verified"])
             n += 1
+
+    # ---- the learned path (not part of the timed forest steps) -----------------------------
+    learned = None
+    if args.train_steps > 0 and rank == 0:
+        learned = learned_section(args, B, synth, torch, dev, scene, forest, world, intr, train, sets[0], prm,
+                                  stream)
 
     # ---- end to end through the public API (host buffers) ----------------------------------
     host_noise = [torch.empty((A, H, W), dtype=torch.float32, pin_memory=True) for _ in range(n_sets)]
@@ -347,8 +362,9 @@ def run_ours(args):
 
     # ---- roofline of the dominant stage ---------------------------------------------------
     dom = max(stage_tot, key=stage_tot.get)
-    avg_ms = stage_tot[dom] / args.steps
-    roof = roofline(dom, avg_ms, A, tries_per_step / args.steps, clocks)
+    roofs = {k: roofline(k, stage_tot[k] / args.steps, A, tries_per_step / args.steps, clocks)
+             for k in ("query_raycast", "forest_eval", "forest_hypotheses", "forest_verify") if stage_tot[k] > 0}
+    roof = roofs.get(dom) or roofline(dom, stage_tot[dom] / args.steps, A, tries_per_step / args.steps, clocks)
 
     cpu = None
     if rank == 0 and world_size == 1 and not args.no_cpu_baseline:
@@ -362,16 +378,112 @@ def run_ours(args):
                 "config": {"workload": WORKLOAD, "attempts_per_step": A, "path": "forest",
                            "l2": "flushed between steps (512 MiB write)",
                            "success_rate": succ / n, "verified_rate": ver / n,
-                           "stage_ms_per_step": {k: v / args.steps for k, v in stage_tot.items()}},
+                           "stage_ms_per_step": {k: v / args.steps for k, v in stage_tot.items()},
+                           "learned": learned},
                 "e2e": {"value": e2e_value, "unit": UNIT,
                         "h2d_bytes_per_step": A * H * W * 4 + A * ctypes_attempt_bytes(),
                         "d2h_bytes_per_step": A * B.RESULT_BYTES},
                 "gpu_launches": sets[0]["batch"].launch_count * args.steps,
-                "roofline": roof, "cpu_baseline": cpu, "clocks": clocks}
+                "roofline": roof, "roofline_stages": roofs, "cpu_baseline": cpu, "clocks": clocks}
         print(json.dumps(line), flush=True)
     if world_size > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+# ------------------------------------------------------------------------------------------------
+# Learned path: online training of the regressor on renders of the house, then the same attempts
+# relocalised with it (learned only, and with the forest as fallback)
+# ------------------------------------------------------------------------------------------------
+TRAIN_BATCH, TRAIN_LR = 16, 3e-4
+REG_ORIGIN = (5.0, 4.0, 1.5)   # centre of the house
+
+
+def regressor_flops_per_view():
+    """Multiply-adds x 2 of one 640 x 480 forward pass (padded channel counts, as computed)."""
+    chans = [(16, 64, 2), (64, 64, 2), (64, 64, 2)] + [(64, 64, 1)] * 4 + [(64, 8, 1)]
+    h, w, fl = H, W, 0
+    for cin, cout, st in chans:
+        h, w = h // st, w // st
+        fl += 2 * h * w * 9 * cin * cout
+    return fl
+
+
+def learned_section(args, B, synth, torch, dev, scene, forest, world, intr, train, st, prm, stream):
+    nb = TRAIN_BATCH
+    pool = synth.query_poses(world, train, args.train_steps * nb, seed=77)
+    noise = torch.from_numpy(np.stack([synth.depth_noise(H, W, 9000 + k) for k in range(32)])).to(dev)
+    reg = B.Regressor(seed=3, origin=REG_ORIGIN)
+    depth = torch.zeros((nb, H, W), dtype=torch.int16, device=dev)
+    rgba = torch.zeros((nb, H, W, 4), dtype=torch.uint8, device=dev)
+    ws = torch.empty(B.regressor_workspace_size(nb, W, H, True), dtype=torch.uint8, device=dev)
+    loss = torch.zeros(args.train_steps, dtype=torch.float32, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    render_ms = train_ms = 0.0
+    for s in range(args.train_steps):
+        P = pool[s * nb:(s + 1) * nb]
+        ev[0].record(stream)
+        for k in range(nb):
+            B.raycast_view(scene, intr, P[k], depth[k], rgba[k], noise_dev=noise[(s * nb + k) % len(noise)])
+        ev[1].record(stream)
+        lr = TRAIN_LR * (0.1 if s >= 0.75 * args.train_steps else 1.0)
+        B.regressor_train_step(reg, depth, rgba, intr, P, lr, ws, loss[s:s + 1])
+        ev[2].record(stream)
+        ev[2].synchronize()
+        render_ms += ev[0].elapsed_time(ev[1])
+        train_ms += ev[1].elapsed_time(ev[2])
+    L = loss.cpu().numpy()
+    train_step_ms = train_ms / args.train_steps
+    # forward + backward-data + backward-weight: about 3 forward passes of work per view
+    train_tflops = 3 * regressor_flops_per_view() * nb / (train_step_ms / 1000.0) / 1e12
+    out = {"train_steps": args.train_steps, "train_batch": nb, "lr": TRAIN_LR,
+           "train_ms_per_step": train_step_ms, "render_ms_per_step": render_ms / args.train_steps,
+           "train_tflops": train_tflops, "loss_first_last_100": [float(L[:100].mean()), float(L[-100:].mean())]}
+    A = len(st["qs"])
+    for name, with_forest in (("learned_only", False), ("learned_with_fallback", True)):
+        items = [dict(scene_b=scene, forest_a=forest if with_forest else None, scene_a=scene, regressor_a=reg,
+                      intr=intr, pose_b=st["qs"][k], noise=st["noise"][k], seed=k) for k in range(A)]
+        att = B.make_attempts(items)
+        wsb = torch.empty(B.batch_workspace_size(att, prm), dtype=torch.uint8, device=dev)
+        bt = B.Batch(att, prm, wsb)
+        bt.enable_timing(True)
+        res = torch.zeros(A * B.RESULT_BYTES, dtype=torch.uint8, device=dev)
+        bt.capture(res)
+        for _ in range(2):
+            bt.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        times, stages = [], {}
+        for _ in range(3):
+            e0.record(stream)
+            bt.replay()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            for k, v in bt.stage_ms().items():
+                stages[k] = stages.get(k, 0.0) + v / 3
+        raw = res.cpu()
+        succ = ver = 0
+        paths = [0, 0, 0]
+        for k in range(A):
+            r = B.result_from_bytes(raw[k * B.RESULT_BYTES:(k + 1) * B.RESULT_BYTES])
+            succ += int(success(r, st["qs"][k]))
+            ver += int(r["verified"])
+            paths[r["path"]] += 1
+        ms = sorted(times)[1]
+        out[name] = {"attempts_per_s": A / (ms / 1000.0), "ms_per_batch": ms, "success_rate": succ / A,
+                     "verified_rate": ver / A, "paths_forest_learned_fallback": paths,
+                     "learned_forward_ms": stages.get("learned_forward", 0.0),
+                     "learned_forward_tflops": regressor_flops_per_view() * A / max(stages.get("learned_forward", 0.0), 1e-9) / 1e9}
+    return out
+
+
+def success(r, P):
+    """Sec. 4.2.1's criterion: within 5 cm and 5 degrees of the ground-truth pose."""
+    dt = float(np.linalg.norm(r["pose"][:3, 3] - P[:3, 3]))
+    cang = (np.trace(r["pose"][:3, :3] @ P[:3, :3].T) - 1) / 2
+    dr = math.degrees(math.acos(max(-1.0, min(1.0, cang))))
+    return r["status"] == 0 and dt <= 0.05 and dr <= 5.0
 
 
 # Hypothesis search, ALU view: each try is one Philox4x32-10 block (10 rounds of two 32 x 32 -> 64
@@ -389,13 +501,14 @@ def roofline(kernel, avg_ms, attempts, tries_per_launch, clocks):
         peak = IMAD_PER_CLK_SM * N_SMS * mhz * 1e6 / IMAD_PER_TRY / 1e9      # G tries / s
         achieved = tries_per_launch / (avg_ms / 1000.0) / 1e9
         return {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gtries/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": PROFILED_TRAFFIC_BYTES.get(kernel), "ms": avg_ms,
                 "peak_source": "derived: 64 IMAD/clk/SM x 152 SMs x max SM clock / 40 IMAD per try"}
     peak, peak_kind = measured_peaks()
     per_px = ALG_BYTES_PER_PIXEL.get(kernel)
     achieved = None if per_px is None else per_px * W * H * attempts / (avg_ms / 1000.0) / 1e9
     return {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": None if achieved is None else achieved / peak, "traffic": None, "peak_source": peak_kind}
+            "frac": None if achieved is None else achieved / peak, "traffic": PROFILED_TRAFFIC_BYTES.get(kernel),
+            "ms": avg_ms, "peak_source": peak_kind}
 
 
 def ctypes_attempt_bytes():
