@@ -328,7 +328,7 @@ def run_ours(args):
         elapsed = float(t.item())
     value = A * args.steps * world_size / elapsed
 
-    # success (Sec. 4.2.1 criterion: <= 5 cm and <= 5 degrees) and verification rate
+    # success (the criterion of Sec. 4.2.2: <= 5 cm and <= 5 degrees) and verification rate
     succ = ver = n = 0
     tries_per_step = 0
     for st, raw in results:
@@ -479,7 +479,7 @@ def learned_section(args, B, synth, torch, dev, scene, forest, world, intr, trai
 
 
 def success(r, P):
-    """Sec. 4.2.1's criterion: within 5 cm and 5 degrees of the ground-truth pose."""
+    """The success criterion of Sec. 4.2.2: within 5 cm and 5 degrees of the ground-truth pose."""
     dt = float(np.linalg.norm(r["pose"][:3, 3] - P[:3, 3]))
     cang = (np.trace(r["pose"][:3, :3] @ P[:3, :3].T) - 1) / 2
     dr = math.degrees(math.acos(max(-1.0, min(1.0, cang))))

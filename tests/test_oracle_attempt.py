@@ -1,6 +1,6 @@
 """End-to-end oracle attempt on the tiny room (Sec. 3.3.1, Fig. 3): a view of the room rendered
 near the training trajectory relocalises to within 5 cm / 5 degrees (the paper's success
-criterion, Sec. 4.2.1) and passes depth-difference verification; a wrong pose is rejected."""
+criterion, Sec. 4.2.2) and passes depth-difference verification; a wrong pose is rejected."""
 import math
 
 import numpy as np
