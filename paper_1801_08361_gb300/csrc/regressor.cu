@@ -39,58 +39,120 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
 __device__ __forceinline__ uint32_t ld32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
 
 
-constexpr int kConvPix = 64;  // output pixels per tile (4 warps x 16)
+constexpr int kConvPix = 64;  // output pixels per backward-weight tile (wgrad_kernel)
+
+// ldmatrix: four (or two) 8 x 8 b16 matrices from shared memory, rows addressed by lanes 8q..8q+7
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const bf16* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+
+__device__ __forceinline__ void ldsm_x2(uint32_t& r0, uint32_t& r1, const bf16* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(a));
+}
+
+// Forward / backward-data convolution.  A CTA of 8 warps keeps all 9 taps of the weights in shared
+// memory and loops over tiles of 128 output pixels (16 per warp, all N output channels per warp).
+// Per tap the tile's input rows (one per output pixel) are gathered into shared memory; the next
+// tap's rows are loaded into registers while the current tap's MMAs run, so the gathers overlap
+// the tensor-core work.  Fragments come from shared memory by ldmatrix; rows are padded to
+// CIN + 8 elements, which keeps every ldmatrix phase free of bank conflicts.
+constexpr int kConvThreads = 256;
+constexpr int kConvTile = 128;
+
+template <int CIN>
+struct ConvGather {
+  static constexpr int CH = CIN / 8;                              // 16-B chunks per pixel
+  static constexpr int PER = kConvTile * CH / kConvThreads;       // chunks per thread per tap
+  static_assert(PER >= 1 && kConvTile * CH % kConvThreads == 0, "tile / channel split");
+  int b[PER], oy[PER], ox[PER], m[PER], c8[PER];
+  bool ok[PER];
+
+  __device__ __forceinline__ void setup(const ConvArgs& a, long m0, long total, int tid) {
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int v = tid + i * kConvThreads;
+      m[i] = v / CH;
+      c8[i] = v % CH;
+      const long p = m0 + m[i];
+      ok[i] = p < total;
+      ox[i] = ok[i] ? (int)(p % a.Wo) : 0;
+      oy[i] = ok[i] ? (int)((p / a.Wo) % a.Ho) : 0;
+      b[i] = ok[i] ? (int)(p / ((long)a.Wo * a.Ho)) : 0;
+    }
+  }
+
+  __device__ __forceinline__ void load(const ConvArgs& a, int tap, uint4 (&val)[PER]) const {
+    const int ky = tap / 3, kx = tap % 3;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      val[i] = make_uint4(0u, 0u, 0u, 0u);
+      const int iy = oy[i] * a.stride + ky - 1, ix = ox[i] * a.stride + kx - 1;
+      if (ok[i] && iy >= 0 && ix >= 0 && iy < a.Hi && ix < a.Wi) {
+        if (!a.upsample) {
+          val[i] = __ldg(reinterpret_cast<const uint4*>(a.in + (((size_t)b[i] * a.Hi + iy) * a.Wi + ix) * CIN) + c8[i]);
+        } else if (!(iy & 1) && !(ix & 1) && (iy >> 1) < a.Hs && (ix >> 1) < a.Ws) {
+          val[i] = __ldg(reinterpret_cast<const uint4*>(a.in + (((size_t)b[i] * a.Hs + (iy >> 1)) * a.Ws + (ix >> 1)) *
+                                                                  CIN) + c8[i]);
+        }
+      }
+    }
+  }
+};
 
 template <int CIN, int NT>
-__global__ void __launch_bounds__(128) conv_kernel(ConvArgs a) {
+__global__ void __launch_bounds__(kConvThreads) conv_kernel(ConvArgs a) {
   constexpr int N = NT * 8;
-  constexpr int RS = CIN + 8;  // padded row stride (bf16) of the shared tiles: no bank conflicts
+  constexpr int RS = CIN + 8;  // padded row stride (bf16) of the shared tiles
+  using G = ConvGather<CIN>;
   extern __shared__ __align__(16) unsigned char conv_smem[];
   bf16* sW = reinterpret_cast<bf16*>(conv_smem);   // [9][N][RS]
-  bf16* sA = sW + 9 * N * RS;                       // [64][RS]
+  bf16* sA = sW + 9 * N * RS;                       // [kConvTile][RS]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-  for (int v = tid; v < 9 * N * (CIN / 8); v += 128) {
+  for (int v = tid; v < 9 * N * (CIN / 8); v += kConvThreads) {
     const int row = v / (CIN / 8), c8 = v % (CIN / 8);
     *reinterpret_cast<uint4*>(sW + row * RS + c8 * 8) = __ldg(reinterpret_cast<const uint4*>(a.w + (size_t)row * CIN) + c8);
   }
   const long total = (long)a.B * a.Ho * a.Wo;
-  const long n_tiles = (total + kConvPix - 1) / kConvPix;
+  const long n_tiles = (total + kConvTile - 1) / kConvTile;
+  // ldmatrix row addresses of this lane: A rows warp * 16 + (lane & 7) + 8 * ((lane >> 3) & 1),
+  // k half (lane >> 4); B rows (n) (lane & 7) + 8 * (lane >> 4), k half ((lane >> 3) & 1)
+  const int a_row = warp * 16 + (lane & 7) + 8 * ((lane >> 3) & 1), a_k = 8 * (lane >> 4);
+  const int b_row = (lane & 7) + 8 * (lane >> 4), b_k = 8 * ((lane >> 3) & 1);
   for (long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const long m0 = tile * kConvPix;
+    const long m0 = tile * kConvTile;
+    G gat;
+    gat.setup(a, m0, total, tid);
+    uint4 pre[G::PER];
+    gat.load(a, 0, pre);
     float acc[NT][4];
 #pragma unroll
     for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
     for (int tap = 0; tap < 9; ++tap) {
-      const int ky = tap / 3, kx = tap % 3;
-      __syncthreads();  // previous readers of sA (and, on the first pass, the weight stores)
-      for (int v = tid; v < kConvPix * (CIN / 8); v += 128) {
-        const int m = v / (CIN / 8), c8 = v % (CIN / 8);
-        const long p = m0 + m;
-        uint4 val = make_uint4(0u, 0u, 0u, 0u);
-        if (p < total) {
-          const int ox = (int)(p % a.Wo), oy = (int)((p / a.Wo) % a.Ho), b = (int)(p / ((long)a.Wo * a.Ho));
-          const int iy = oy * a.stride + ky - 1, ix = ox * a.stride + kx - 1;
-          if (iy >= 0 && ix >= 0 && iy < a.Hi && ix < a.Wi) {
-            if (!a.upsample) {
-              val = __ldg(reinterpret_cast<const uint4*>(a.in + (((size_t)b * a.Hi + iy) * a.Wi + ix) * CIN) + c8);
-            } else if (!(iy & 1) && !(ix & 1) && (iy >> 1) < a.Hs && (ix >> 1) < a.Ws) {
-              val = __ldg(reinterpret_cast<const uint4*>(a.in + (((size_t)b * a.Hs + (iy >> 1)) * a.Ws + (ix >> 1)) * CIN) + c8);
-            }
-          }
-        }
-        *reinterpret_cast<uint4*>(sA + m * RS + c8 * 8) = val;
-      }
+      __syncthreads();  // readers of the previous tap's rows (and, first, the weight stores) are done
+#pragma unroll
+      for (int i = 0; i < G::PER; ++i) *reinterpret_cast<uint4*>(sA + gat.m[i] * RS + gat.c8[i] * 8) = pre[i];
       __syncthreads();
-      const bf16* Ar = sA + (warp * 16 + g) * RS;
+      if (tap < 8) gat.load(a, tap + 1, pre);  // in flight during this tap's MMAs
       const bf16* Wt = sW + tap * N * RS;
 #pragma unroll
       for (int ks = 0; ks < CIN / 16; ++ks) {
-        const int k0 = ks * 16 + 2 * t;
-        uint32_t af[4] = {ld32(Ar + k0), ld32(Ar + 8 * RS + k0), ld32(Ar + k0 + 8), ld32(Ar + 8 * RS + k0 + 8)};
+        uint32_t af[4];
+        ldsm_x4(af, sA + a_row * RS + ks * 16 + a_k);
 #pragma unroll
-        for (int j = 0; j < NT; ++j) {
-          const bf16* Br = Wt + (j * 8 + g) * RS;
-          mma_bf16(acc[j], af, ld32(Br + k0), ld32(Br + k0 + 8));
+        for (int j = 0; j + 1 < NT; j += 2) {
+          uint32_t bf[4];
+          ldsm_x4(bf, Wt + (j * 8 + b_row) * RS + ks * 16 + b_k);
+          mma_bf16(acc[j], af, bf[0], bf[1]);
+          mma_bf16(acc[j + 1], af, bf[2], bf[3]);
+        }
+        if (NT & 1) {
+          uint32_t b0, b1;
+          ldsm_x2(b0, b1, Wt + ((NT - 1) * 8 + (lane & 7)) * RS + ks * 16 + 8 * ((lane >> 3) & 1));
+          mma_bf16(acc[NT - 1], af, b0, b1);
         }
       }
     }
@@ -126,14 +188,21 @@ __global__ void __launch_bounds__(128) conv_kernel(ConvArgs a) {
 template <int CIN, int NT>
 cudaError_t launch_conv_t(const ConvArgs& a, int n_sms, cudaStream_t s) {
   constexpr int N = NT * 8, RS = CIN + 8;
-  const size_t smem = (size_t)(9 * N + kConvPix) * RS * sizeof(bf16);
-  cudaError_t e = cudaFuncSetAttribute(conv_kernel<CIN, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  const size_t smem = (size_t)(9 * N + kConvTile) * RS * sizeof(bf16);
+  static int per_sm = 0;  // resident CTAs per SM (first call)
+  if (per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(conv_kernel<CIN, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_kernel<CIN, NT>, kConvThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+  }
   const long total = (long)a.B * a.Ho * a.Wo;
-  const long tiles = (total + kConvPix - 1) / kConvPix;
-  const long grid = tiles < (long)n_sms * 2 ? tiles : (long)n_sms * 2;
+  const long tiles = (total + kConvTile - 1) / kConvTile;
+  const long slots = (long)n_sms * per_sm;
+  const long grid = tiles < slots ? tiles : slots;
   if (grid <= 0) return cudaSuccess;
-  conv_kernel<CIN, NT><<<(unsigned)grid, 128, smem, s>>>(a);
+  conv_kernel<CIN, NT><<<(unsigned)grid, kConvThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -147,73 +216,129 @@ cudaError_t launch_conv(int cin, int nt, const ConvArgs& a, int n_sms, cudaStrea
 // ---------------------------------------------------------------------------------------------
 // Backward-weight: partial[chunk][tap][n][k] = sum over the chunk's output pixels p of
 // g[p, n] * in[src(p, tap), k]; a second kernel sums the chunks in a fixed order.
+// A CTA (8 warps) owns one tap and one chunk of pixels; per 64-pixel tile it stages the gradient
+// rows and the tap's gathered input rows as stored (pixel-major, 16-byte vectors, the next tile
+// prefetched into registers) and contracts over the pixels with ldmatrix.trans fragments:
+// M = input channels, N = output channels, K = pixels.
 // ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const bf16* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
 
+__device__ __forceinline__ void ldsm_x2_t(uint32_t& r0, uint32_t& r1, const bf16* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(a));
+}
+
+constexpr int kWgradThreads = 256;
 
 template <int CIN, int NT>
-__global__ void __launch_bounds__(128) wgrad_kernel(WgradArgs a) {
+__global__ void __launch_bounds__(kWgradThreads) wgrad_kernel(WgradArgs a) {
   constexpr int N = NT * 8;
-  constexpr int MT = (N + 15) / 16;   // m16 tiles over the output channels
-  constexpr int PS = kConvPix + 8;    // padded pixel stride of the transposed tiles
-  __shared__ __align__(16) bf16 sG[MT * 16][PS];  // g^T: [n][pixel]
-  __shared__ __align__(16) bf16 sI[CIN][PS];      // in^T: [k][pixel]
+  constexpr int MT = CIN / 16;                          // m16 tiles over the input channels
+  constexpr int WM = (MT >= 2 && MT * NT >= 32) ? 2 : 1;  // m16 tiles per warp
+  constexpr int WN = (NT >= 2 && MT * NT >= 32) ? 2 : 1;  // n8 tiles per warp
+  constexpr int MG = MT / WM, NG = NT / WN;
+  static_assert(MG * NG <= kWgradThreads / 32, "warp split");
+  constexpr int RI = CIN + 8;                           // row strides (bf16): conflict-free ldmatrix
+  constexpr int RG = (N < 16 ? 16 : N) + 8;
+  constexpr int CI = CIN / 8, CG = N / 8;               // 16-B chunks per pixel row
+  constexpr int PI = (kConvPix * CI + kWgradThreads - 1) / kWgradThreads;
+  constexpr int PG = (kConvPix * CG + kWgradThreads - 1) / kWgradThreads;
+  __shared__ __align__(16) bf16 sI[kConvPix][RI];
+  __shared__ __align__(16) bf16 sG[kConvPix][RG];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
   const int tap = blockIdx.y, ky = tap / 3, kx = tap % 3;
   const long total = (long)a.B * a.Ho * a.Wo;
   const long p_begin = (long)blockIdx.x * a.chunk_pix;
-  float acc[CIN / 8][4];
+  const long p_end = min(p_begin + (long)a.chunk_pix, total);
+  const int mg = warp % MG, ng = warp / MG;
+  const bool mma_warp = warp < MG * NG;
+  float acc[WM][WN][4];
 #pragma unroll
-  for (int j = 0; j < CIN / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-  for (long p0 = p_begin; p0 < p_begin + a.chunk_pix && p0 < total; p0 += kConvPix) {
-    __syncthreads();
-    // staged transposed; consecutive threads read consecutive channels of a pixel (coalesced)
-    for (int v = tid; v < kConvPix * (MT * 16); v += 128) {
-      const int n = v % (MT * 16), m = v / (MT * 16);
-      const long p = p0 + m;
-      bf16 val = __float2bfloat16(0.f);
-      if (p < total && n < N) val = a.g[(size_t)p * a.GS + n];
-      sG[n][m] = val;
-    }
-    for (int v = tid; v < kConvPix * CIN; v += 128) {
-      const int k = v % CIN, m = v / CIN;
-      const long p = p0 + m;
-      bf16 val = __float2bfloat16(0.f);
-      if (p < total) {
+  for (int i = 0; i < WM; ++i)
+#pragma unroll
+    for (int j = 0; j < WN; ++j) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.f;
+
+  uint4 vi[PI], vg[PG];
+  auto fetch = [&](long p0) {
+#pragma unroll
+    for (int i = 0; i < PI; ++i) {
+      const int v = tid + i * kWgradThreads;
+      vi[i] = make_uint4(0u, 0u, 0u, 0u);
+      const long p = p0 + v / CI;
+      if (v < kConvPix * CI && p < p_end) {
         const int ox = (int)(p % a.Wo), oy = (int)((p / a.Wo) % a.Ho), b = (int)(p / ((long)a.Wo * a.Ho));
         const int iy = oy * a.stride + ky - 1, ix = ox * a.stride + kx - 1;
-        if (iy >= 0 && ix >= 0 && iy < a.Hi && ix < a.Wi) val = a.in[(((size_t)b * a.Hi + iy) * a.Wi + ix) * CIN + k];
+        if (iy >= 0 && ix >= 0 && iy < a.Hi && ix < a.Wi)
+          vi[i] = __ldg(reinterpret_cast<const uint4*>(a.in + (((size_t)b * a.Hi + iy) * a.Wi + ix) * CIN) + v % CI);
       }
-      sI[k][m] = val;
+    }
+#pragma unroll
+    for (int i = 0; i < PG; ++i) {
+      const int v = tid + i * kWgradThreads;
+      vg[i] = make_uint4(0u, 0u, 0u, 0u);
+      const long p = p0 + v / CG;
+      if (v < kConvPix * CG && p < p_end)
+        vg[i] = __ldg(reinterpret_cast<const uint4*>(a.g + (size_t)p * a.GS) + v % CG);
+    }
+  };
+  fetch(p_begin);
+  for (long p0 = p_begin; p0 < p_end; p0 += kConvPix) {
+    __syncthreads();  // the previous tile's fragments are read
+#pragma unroll
+    for (int i = 0; i < PI; ++i) {
+      const int v = tid + i * kWgradThreads;
+      if (v < kConvPix * CI) *reinterpret_cast<uint4*>(&sI[v / CI][(v % CI) * 8]) = vi[i];
+    }
+#pragma unroll
+    for (int i = 0; i < PG; ++i) {
+      const int v = tid + i * kWgradThreads;
+      if (v < kConvPix * CG) *reinterpret_cast<uint4*>(&sG[v / CG][(v % CG) * 8]) = vg[i];
     }
     __syncthreads();
-    if (warp < MT) {
+    if (p0 + kConvPix < p_end) fetch(p0 + kConvPix);  // in flight during this tile's MMAs
+    if (mma_warp) {
 #pragma unroll
       for (int ks = 0; ks < kConvPix / 16; ++ks) {
-        const int k0 = ks * 16 + 2 * t;
-        const bf16* Ar = &sG[warp * 16 + g][0];
-        uint32_t af[4] = {ld32(Ar + k0), ld32(Ar + 8 * PS + k0), ld32(Ar + k0 + 8), ld32(Ar + 8 * PS + k0 + 8)};
+        const int q = lane >> 3, r = lane & 7;
+        uint32_t af[WM][4];
 #pragma unroll
-        for (int j = 0; j < CIN / 8; ++j) {
-          const bf16* Br = &sI[j * 8 + g][0];
-          mma_bf16(acc[j], af, ld32(Br + k0), ld32(Br + k0 + 8));
+        for (int wm = 0; wm < WM; ++wm)
+          ldsm_x4_t(af[wm], &sI[ks * 16 + r + 8 * (q >> 1)][(mg * WM + wm) * 16 + 8 * (q & 1)]);
+        uint32_t bf[WN][2];
+        if (WN == 2) {
+          uint32_t b4[4];
+          ldsm_x4_t(b4, &sG[ks * 16 + r + 8 * (q & 1)][ng * 16 + 8 * (q >> 1)]);
+          bf[0][0] = b4[0];
+          bf[0][1] = b4[1];
+          bf[WN - 1][0] = b4[2];
+          bf[WN - 1][1] = b4[3];
+        } else {
+          ldsm_x2_t(bf[0][0], bf[0][1], &sG[ks * 16 + r + 8 * (q & 1)][ng * 8]);
         }
+#pragma unroll
+        for (int wm = 0; wm < WM; ++wm)
+#pragma unroll
+          for (int wn = 0; wn < WN; ++wn) mma_bf16(acc[wm][wn], af[wm], bf[wn][0], bf[wn][1]);
       }
     }
   }
-  if (warp < MT) {
+  if (mma_warp) {
     float* out = a.partial + ((size_t)blockIdx.x * 9 + tap) * N * CIN;
 #pragma unroll
-    for (int j = 0; j < CIN / 8; ++j) {
-      const int k0 = j * 8 + 2 * t;
+    for (int wm = 0; wm < WM; ++wm)
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int n = warp * 16 + g + 8 * h;
-        if (n < N) {
-          out[(size_t)n * CIN + k0] = acc[j][2 * h];
-          out[(size_t)n * CIN + k0 + 1] = acc[j][2 * h + 1];
-        }
+      for (int wn = 0; wn < WN; ++wn) {
+        const int k = (mg * WM + wm) * 16 + g, n = (ng * WN + wn) * 8 + 2 * t;
+        out[(size_t)n * CIN + k] = acc[wm][wn][0];
+        out[(size_t)(n + 1) * CIN + k] = acc[wm][wn][1];
+        out[(size_t)n * CIN + k + 8] = acc[wm][wn][2];
+        out[(size_t)(n + 1) * CIN + k + 8] = acc[wm][wn][3];
       }
-    }
   }
 }
 
@@ -221,35 +346,47 @@ cudaError_t launch_wgrad(int cin, int nt, const WgradArgs& a, cudaStream_t s) {
   const long total = (long)a.B * a.Ho * a.Wo;
   const unsigned chunks = (unsigned)((total + a.chunk_pix - 1) / a.chunk_pix);
   const dim3 grid(chunks, 9);
-  if (cin == 16 && nt == 8) wgrad_kernel<16, 8><<<grid, 128, 0, s>>>(a);
-  else if (cin == 64 && nt == 8) wgrad_kernel<64, 8><<<grid, 128, 0, s>>>(a);
-  else if (cin == 64 && nt == 1) wgrad_kernel<64, 1><<<grid, 128, 0, s>>>(a);
+  if (cin == 16 && nt == 8) wgrad_kernel<16, 8><<<grid, kWgradThreads, 0, s>>>(a);
+  else if (cin == 64 && nt == 8) wgrad_kernel<64, 8><<<grid, kWgradThreads, 0, s>>>(a);
+  else if (cin == 64 && nt == 1) wgrad_kernel<64, 1><<<grid, kWgradThreads, 0, s>>>(a);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
 // Sum of the chunk partials in chunk order into the master-layout gradient [3][3][cin][cout]
-// (only the real channels: cin_real, cout_real), one thread per weight.
+// (only the real channels: cin_real, cout_real), one thread per weight; neighbouring threads take
+// neighbouring input channels, which are contiguous in the partials.
 __global__ void wgrad_reduce_kernel(const float* __restrict__ partial, int n_chunks, int N, int CIN, int cin_real,
                                     int cout_real, float* __restrict__ gw) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int per_tap = cin_real * cout_real;
   if (i >= 9 * per_tap) return;
-  const int tap = i / per_tap, r = i % per_tap, ci = r / cout_real, co = r % cout_real;
+  const int tap = i / per_tap, r = i % per_tap, co = r / cin_real, ci = r % cin_real;
   float s = 0.f;
   for (int c = 0; c < n_chunks; ++c) s += partial[(((size_t)c * 9 + tap) * N + co) * CIN + ci];
-  gw[i] = s;
+  gw[(size_t)tap * per_tap + (size_t)ci * cout_real + co] = s;
 }
 
-// Bias gradient: sum over pixels of g[p, n] (two passes for a fixed summation order).
+// Bias gradient: sum over pixels of g[p, n] in a fixed order: per chunk, 4 pixel groups x the
+// channels (neighbouring threads read neighbouring channels), groups added in order; then the
+// chunks in order.
+constexpr int kBiasGroups = 4;
+
 __global__ void bias_partial_kernel(const bf16* __restrict__ g, long total, int GS, int n_real, int chunk,
                                     float* __restrict__ partial) {
-  const int n = threadIdx.x;
-  if (n >= n_real) return;
+  __shared__ float part[kBiasGroups][64];
+  const int n = threadIdx.x & 63, grp = threadIdx.x >> 6;
   float s = 0.f;
   const long p0 = (long)blockIdx.x * chunk;
-  for (long p = p0; p < p0 + chunk && p < total; ++p) s += __bfloat162float(g[(size_t)p * GS + n]);
-  partial[(size_t)blockIdx.x * n_real + n] = s;
+  if (n < n_real)
+    for (long p = p0 + grp; p < p0 + chunk && p < total; p += kBiasGroups) s += __bfloat162float(g[(size_t)p * GS + n]);
+  part[grp][n] = s;
+  __syncthreads();
+  if (grp == 0 && n < n_real) {
+    float v = part[0][n];
+    for (int q = 1; q < kBiasGroups; ++q) v += part[q][n];
+    partial[(size_t)blockIdx.x * n_real + n] = v;
+  }
 }
 
 __global__ void bias_reduce_kernel(const float* __restrict__ partial, int n_chunks, int n_real, float* __restrict__ gb) {
@@ -263,7 +400,7 @@ __global__ void bias_reduce_kernel(const float* __restrict__ partial, int n_chun
 cudaError_t launch_bias_grad(const bf16* g, long total, int GS, int n_real, float* scratch, float* gb, cudaStream_t s) {
   const int chunk = 2048;
   const int chunks = (int)((total + chunk - 1) / chunk);
-  bias_partial_kernel<<<chunks, 64, 0, s>>>(g, total, GS, n_real, chunk, scratch);
+  bias_partial_kernel<<<chunks, 64 * kBiasGroups, 0, s>>>(g, total, GS, n_real, chunk, scratch);
   bias_reduce_kernel<<<1, 64, 0, s>>>(scratch, chunks, n_real, gb);
   return cudaGetLastError();
 }

@@ -63,7 +63,7 @@ constexpr int kRegCin[kRegLayers] = {4, 64, 64, 64, 64, 64, 64, 64};
 constexpr int kRegCout[kRegLayers] = {64, 64, 64, 64, 64, 64, 64, 4};
 constexpr int kRegCinPad[kRegLayers] = {16, 64, 64, 64, 64, 64, 64, 64};
 constexpr int kRegCoutPad[kRegLayers] = {64, 64, 64, 64, 64, 64, 64, 8};
-constexpr int kWgradChunk = 4096;
+constexpr int kWgradChunk = 1024;  // output pixels per backward-weight CTA (multiple of 64)
 
 cudaError_t launch_conv(int cin, int nt, const ConvArgs& a, int n_sms, cudaStream_t s);
 cudaError_t launch_wgrad(int cin, int nt, const WgradArgs& a, cudaStream_t s);
