@@ -412,19 +412,21 @@ def regressor_flops_per_view():
 def learned_section(args, B, synth, torch, dev, scene, forest, world, intr, train, st, prm, stream):
     nb = TRAIN_BATCH
     pool = synth.query_poses(world, train, args.train_steps * nb, seed=77)
-    noise = torch.from_numpy(np.stack([synth.depth_noise(H, W, 9000 + k) for k in range(32)])).to(dev)
     reg = B.Regressor(seed=3, origin=REG_ORIGIN)
     depth = torch.zeros((nb, H, W), dtype=torch.int16, device=dev)
     rgba = torch.zeros((nb, H, W, 4), dtype=torch.uint8, device=dev)
     ws = torch.empty(B.regressor_workspace_size(nb, W, H, True), dtype=torch.uint8, device=dev)
+    ws_views = torch.empty(B.raycast_views_workspace_size(nb), dtype=torch.uint8, device=dev)
+    n_noise = 64  # noise images cycled over the renders (a multiple of the batch)
+    noise = torch.from_numpy(np.stack([synth.depth_noise(H, W, 9000 + k) for k in range(n_noise)])).to(dev)
     loss = torch.zeros(args.train_steps, dtype=torch.float32, device=dev)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     render_ms = train_ms = 0.0
     for s in range(args.train_steps):
         P = pool[s * nb:(s + 1) * nb]
         ev[0].record(stream)
-        for k in range(nb):
-            B.raycast_view(scene, intr, P[k], depth[k], rgba[k], noise_dev=noise[(s * nb + k) % len(noise)])
+        q = (s * nb) % n_noise
+        B.raycast_views(scene, intr, P, depth, rgba, noise_dev=noise[q:q + nb], workspace_dev=ws_views)
         ev[1].record(stream)
         lr = TRAIN_LR * (0.1 if s >= 0.75 * args.train_steps else 1.0)
         B.regressor_train_step(reg, depth, rgba, intr, P, lr, ws, loss[s:s + 1])

@@ -108,6 +108,17 @@ relo_status relo_scene_use_grid(relo_scene* scene, int32_t enable);
 relo_status relo_raycast_view(const relo_scene* scene, const relo_intrinsics* intr, const double pose_c2s[16],
                               const float* noise_dev, uint16_t* depth_dev, uint8_t* rgba_dev, relo_stream stream);
 
+/* n views of one scene in one launch (the same raycast as relo_raycast_view for each view):
+ * poses_c2s_host [n][16]; noise_dev nullable, [n][H][W]; depth_dev [n][H][W]; rgba_dev nullable,
+ * [n][H][W][4].  The per-view descriptors are copied from host memory to workspace_dev (device,
+ * 256-byte aligned, at least relo_raycast_views_workspace_size(n) bytes) on the stream, which
+ * may wait for the stream's earlier work; the renders themselves are not waited for.
+ * Errors: RELO_EINVAL (as relo_raycast_view, n < 1, workspace). */
+size_t relo_raycast_views_workspace_size(int32_t n);
+relo_status relo_raycast_views(const relo_scene* scene, const relo_intrinsics* intr, const double* poses_c2s_host,
+                               int32_t n, const float* noise_dev, uint16_t* depth_dev, uint8_t* rgba_dev,
+                               void* workspace_dev, size_t workspace_bytes, relo_stream stream);
+
 /* ---------------------------------------------------------------------------------------
  * Regression forest (the relocaliser of Sec. 3.3 (b), after Cavallari et al.).
  * n_trees complete binary trees of the given depth, stored breadth first (children of node n

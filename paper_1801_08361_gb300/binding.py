@@ -114,6 +114,9 @@ _SIGS = {
     "relo_batch_enable_timing": (c_i32, [c_vp, c_i32]),
     "relo_batch_stage_ms": (c_i32, [c_vp, ctypes.POINTER(ctypes.c_float), c_i32]),
     "relo_batch_stage_name": (ctypes.c_char_p, [c_i32]),
+    "relo_raycast_views_workspace_size": (ctypes.c_size_t, [c_i32]),
+    "relo_raycast_views": (c_i32, [c_vp, ctypes.POINTER(Intrinsics), c_vp, c_i32, c_vp, c_vp, c_vp, c_vp,
+                                   ctypes.c_size_t, c_vp]),
     "relo_batch_capture": (c_i32, [c_vp, c_vp]),
     "relo_batch_replay": (c_i32, [c_vp, c_vp]),
     "relo_batch_attempt_images": (c_i32, [c_vp, c_i32, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp),
@@ -249,6 +252,20 @@ def raycast_view(scene, intr, pose, depth_dev, rgba_dev=None, noise_dev=None, st
     ci = intrinsics(intr)
     _check(lib().relo_raycast_view(scene.handle, ctypes.byref(ci), _pose(pose), _ptr(noise_dev), _ptr(depth_dev),
                                    _ptr(rgba_dev), _stream(stream)))
+
+
+def raycast_views_workspace_size(n) -> int:
+    return int(lib().relo_raycast_views_workspace_size(int(n)))
+
+
+def raycast_views(scene, intr, poses, depth_dev, rgba_dev=None, noise_dev=None, workspace_dev=None, stream=None):
+    """n views in one launch: depth_dev [n][H][W], rgba_dev [n][H][W][4], noise_dev [n][H][W]."""
+    n = int(depth_dev.shape[0])
+    ci = intrinsics(intr)
+    ph, pp = _poses_host(poses)
+    _check(lib().relo_raycast_views(scene.handle, ctypes.byref(ci), pp, n, _ptr(noise_dev), _ptr(depth_dev),
+                                    _ptr(rgba_dev), _ptr(workspace_dev),
+                                    0 if workspace_dev is None else workspace_dev.numel(), _stream(stream)))
 
 
 def forest_eval(forest, depth_dev, rgba_dev, leaves_dev, stream=None):

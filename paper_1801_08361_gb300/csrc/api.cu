@@ -420,6 +420,34 @@ relo_status relo_raycast_view(const relo_scene* scene, const relo_intrinsics* in
   return RELO_OK;
 }
 
+size_t relo_raycast_views_workspace_size(int32_t n) { return n < 1 ? 0 : (size_t)n * sizeof(RayJob); }
+
+relo_status relo_raycast_views(const relo_scene* scene, const relo_intrinsics* intr, const double* poses, int32_t n,
+                               const float* noise, uint16_t* depth, uint8_t* rgba, void* ws, size_t ws_bytes,
+                               relo_stream stream) {
+  if (!scene || !poses || !depth || n < 1) return fail(RELO_EINVAL, "null scene, poses or depth, or n < 1");
+  relo_status st = check_intr(intr);
+  if (st) return st;
+  if (!ws || ((uintptr_t)ws & 255) != 0 || ws_bytes < relo_raycast_views_workspace_size(n))
+    return fail(RELO_EINVAL, "workspace missing, misaligned or too small");
+  const size_t n_pix = (size_t)intr->width * intr->height;
+  const int tiles = ray_tiles(intr->width, intr->height);
+  std::vector<RayJob> jobs(n);
+  for (int k = 0; k < n; ++k) {
+    RayJob& j = jobs[k];
+    j = make_ray_job(scene->view, *intr, poses + 16 * (size_t)k);
+    j.noise = noise ? noise + k * n_pix : nullptr;
+    j.depth = depth + k * n_pix;
+    j.rgba = rgba ? (uint32_t*)rgba + k * n_pix : nullptr;
+    j.tile_begin = k * tiles;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  RELO_CUDA(cudaMemcpyAsync(ws, jobs.data(), n * sizeof(RayJob), cudaMemcpyHostToDevice, s));
+  // a copy from pageable memory returns once the host buffer has been staged, so jobs may go
+  RELO_CUDA(launch_raycast((const RayJob*)ws, n, nullptr, n * tiles, rgba != nullptr, false, s));
+  return RELO_OK;
+}
+
 // ---------------------------------------------------------------------------------------------
 // Forests
 // ---------------------------------------------------------------------------------------------

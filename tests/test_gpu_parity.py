@@ -120,6 +120,29 @@ def test_raycast_grid_skips_match_the_block_walk(room, gpu_room):
         assert (np.abs(cg.astype(int) - ch.astype(int)).max(-1) <= 1).all()
 
 
+def test_raycast_views_equals_single_views(room, gpu_room):
+    """The batched render is the same raycast per view: identical images."""
+    world, _ = room
+    intr = synth.Intrinsics.for_size(96, 72)
+    poses = synth.training_poses(world, 2, seed=27)[:5]
+    n = len(poses)
+    noise = torch.from_numpy(np.stack([synth.depth_noise(72, 96, 300 + k) for k in range(n)])).to(DEV)
+    depth = torch.zeros((n, 72, 96), dtype=torch.int16, device=DEV)
+    rgba = torch.zeros((n, 72, 96, 4), dtype=torch.uint8, device=DEV)
+    ws = torch.empty(B.raycast_views_workspace_size(n), dtype=torch.uint8, device=DEV)
+    B.raycast_views(gpu_room, intr, poses, depth, rgba, noise_dev=noise, workspace_dev=ws)
+    torch.cuda.synchronize()
+    for k, P in enumerate(poses):
+        d1 = torch.zeros((72, 96), dtype=torch.int16, device=DEV)
+        c1 = torch.zeros((72, 96, 4), dtype=torch.uint8, device=DEV)
+        B.raycast_view(gpu_room, intr, P, d1, c1, noise_dev=noise[k])
+        torch.cuda.synchronize()
+        assert torch.equal(d1, depth[k]) and torch.equal(c1, rgba[k])
+    with pytest.raises(B.ReloError) as e:
+        B.raycast_views(gpu_room, intr, poses, depth, rgba, workspace_dev=ws[:64])
+    assert e.value.status == B.EINVAL
+
+
 def test_raycast_empty_scene():
     from scenes import empty_blocks
     sc = B.Scene(empty_blocks(), 8)
