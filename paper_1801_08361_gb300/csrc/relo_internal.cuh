@@ -240,8 +240,9 @@ struct RayJob {
   unsigned long long* counts;  // compare mode: {omega_a, omega_b, omega_ab, sum |D_a - D_b|}
   int32_t* err;                // device error flag (nullable)
   int32_t tile_begin;          // first 16 x 16 tile of this job in the flattened launch
-  int32_t pad;
+  int32_t pad[3];              // size: a multiple of 16 bytes (staged in shared memory)
 };
+static_assert(sizeof(RayJob) % 16 == 0, "RayJob is staged in shared memory as 16-byte words");
 
 // ---------------------------------------------------------------------------------------------
 // Forest jobs (one image through one forest)

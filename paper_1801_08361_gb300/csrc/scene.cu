@@ -103,7 +103,7 @@ __device__ __forceinline__ float trilinear_tsdf(const SceneView& s, BlockCache& 
   return y0 + fz * (y1 - y0);
 }
 
-__device__ uint32_t trilinear_rgba(const SceneView& s, BlockCache& c, float3 p, int* err) {
+__device__ __forceinline__ uint32_t trilinear_rgba(const SceneView& s, BlockCache& c, float3 p, int* err) {
   const float qx = p.x * s.inv_voxel, qy = p.y * s.inv_voxel, qz = p.z * s.inv_voxel;
   const float flx = floorf(qx), fly = floorf(qy), flz = floorf(qz);
   const int i = (int)flx, j = (int)fly, k = (int)flz;
@@ -125,7 +125,8 @@ __device__ uint32_t trilinear_rgba(const SceneView& s, BlockCache& c, float3 p, 
 }
 
 // One ray.  Returns the hit depth parameter (camera z, metres) or a negative value if none.
-__device__ float march_ray(const SceneView& s, float3 C, float3 d, float dmin, float dmax, BlockCache& c, int* err) {
+__device__ __forceinline__ float march_ray(const SceneView& s, float3 C, float3 d, float dmin, float dmax, BlockCache& c,
+                                           int* err) {
   const float dn = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
   const float inv_dn = 1.0f / dn;
   const RayExit rx = ray_exit(d);
@@ -165,9 +166,10 @@ __device__ float march_ray(const SceneView& s, float3 C, float3 d, float dmin, f
 
 constexpr int kTile = 16;
 // CTAs per SM the compiler must fit (depth-only renders; colour renders one fewer): the fastest
-// of 3, 4, 5 and 6 on the house workload
+// of 4 to 8 on the house workload; the march is latency-bound, so occupancy beats the few
+// registers this spills
 #ifndef RELO_RAYCAST_MIN_BLOCKS
-#define RELO_RAYCAST_MIN_BLOCKS 5
+#define RELO_RAYCAST_MIN_BLOCKS 8
 #endif
 
 template <bool kColour, bool kCompare>
@@ -180,7 +182,17 @@ __global__ void __launch_bounds__(kTile* kTile, kColour ? RELO_RAYCAST_MIN_BLOCK
     if (jobs[mid].tile_begin <= (int)blockIdx.x) lo = mid;
     else hi = mid - 1;
   }
-  const RayJob& job = jobs ? jobs[lo] : single;
+  // the CTA's job, staged in shared memory: the march reads its scene fields at every step
+  __shared__ __align__(16) RayJob sj;
+  if (jobs) {
+    const int4* src = reinterpret_cast<const int4*>(jobs + lo);
+    int4* dst = reinterpret_cast<int4*>(&sj);
+    for (int i = threadIdx.x; i < (int)(sizeof(RayJob) / 16); i += blockDim.x) dst[i] = src[i];
+  } else if (threadIdx.x == 0) {
+    sj = single;
+  }
+  __syncthreads();
+  const RayJob& job = sj;
   const int tiles_x = (job.W + kTile - 1) / kTile;
   const int tile = (int)blockIdx.x - job.tile_begin;
   // each warp covers an 8 x 4 footprint of the 16 x 16 tile (neighbouring rays march alike)
