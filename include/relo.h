@@ -133,7 +133,8 @@ relo_status relo_raycast_views(const relo_scene* scene, const relo_intrinsics* i
  * mode 0 the most supported.  modes_host / n_modes_host may be NULL (empty leaves) and be
  * filled later by training (relo_forest_train_*).  Copies to the device synchronously.
  * Errors: RELO_EINVAL (n_trees outside [1, 16], depth outside [1, 16], max_modes outside
- * [1, 64], null nodes), RELO_ENOMEM, RELO_ECUDA.
+ * [1, 64], null nodes, a node whose kind is not 0 or 1 or whose channel exceeds 3), RELO_ENOMEM,
+ * RELO_ECUDA.
  * ------------------------------------------------------------------------------------- */
 typedef struct relo_forest relo_forest;
 

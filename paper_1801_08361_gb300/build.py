@@ -17,9 +17,9 @@ LIB = os.path.join(HERE, "librelo.so")
 SOURCES = ["scene.cu", "forest.cu", "ransac.cu", "regressor.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
-# occupancy bounds of the raycast and hypothesis-search kernels (tuning knobs; the defaults come from a sweep of both)
-NVCC_FLAGS += [f"-D{k}={os.environ[k]}" for k in ("RELO_RAYCAST_MIN_BLOCKS", "RELO_SEARCH_MIN_BLOCKS")
-               if k in os.environ]
+# occupancy bounds of the raycast, forest and hypothesis-search kernels (tuning knobs; the defaults come from sweeps)
+NVCC_FLAGS += [f"-D{k}={os.environ[k]}" for k in ("RELO_RAYCAST_MIN_BLOCKS", "RELO_SEARCH_MIN_BLOCKS",
+                                                  "RELO_FOREST_MIN_BLOCKS") if k in os.environ]
 
 
 def _nvcc() -> str:

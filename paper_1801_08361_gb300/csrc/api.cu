@@ -460,6 +460,11 @@ relo_status relo_create_forest(const void* nodes, int32_t T, int32_t D, const fl
   if (M < 1 || M > 64) return fail(RELO_EINVAL, "max_modes outside [1, 64]");
   if (!nodes) return fail(RELO_EINVAL, "nodes is null");
   const size_t n_int = ((size_t)1 << D) - 1, L = (size_t)1 << D;
+  const int4* in_nodes = (const int4*)nodes;
+  for (size_t i = 0; i < (size_t)T * n_int; ++i) {
+    const int kind = in_nodes[i].z & 0xFF, c1 = (in_nodes[i].z >> 8) & 0xFF, c2 = (in_nodes[i].z >> 16) & 0xFF;
+    if (kind > 1 || (kind == 1 && (c1 > 3 || c2 > 3))) return fail(RELO_EINVAL, "node kind not 0/1 or channel > 3");
+  }
   relo_forest* f = new relo_forest();
   f->T = T;
   f->D = D;
@@ -472,7 +477,15 @@ relo_status relo_create_forest(const void* nodes, int32_t T, int32_t D, const fl
     relo_destroy_forest(f);
     return fail(RELO_ENOMEM, "device allocation for the forest failed");
   }
-  cudaError_t e = cudaMemcpy(f->d_nodes, nodes, (size_t)T * n_int * 16, cudaMemcpyHostToDevice);
+  // device copy of the nodes: a colour node's channels c1, c2 become the bit shifts 8 c1, 8 c2
+  std::vector<int4> dev_nodes((size_t)T * n_int);
+  std::memcpy(dev_nodes.data(), nodes, dev_nodes.size() * 16);
+  for (int4& nd : dev_nodes)
+    if ((nd.z & 0xFF) != 0) {
+      const int c1 = (nd.z >> 8) & 0xFF, c2 = (nd.z >> 16) & 0xFF;
+      nd.z = (nd.z & (int)0xFF0000FF) | ((8 * c1) & 0xFF) << 8 | ((8 * c2) & 0xFF) << 16;
+    }
+  cudaError_t e = cudaMemcpy(f->d_nodes, dev_nodes.data(), (size_t)T * n_int * 16, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = modes ? cudaMemcpy(f->d_modes, modes, modes_bytes, cudaMemcpyHostToDevice)
                                   : cudaMemset(f->d_modes, 0, modes_bytes);
   if (e == cudaSuccess) e = n_modes ? cudaMemcpy(f->d_n_modes, n_modes, n_modes_bytes, cudaMemcpyHostToDevice)

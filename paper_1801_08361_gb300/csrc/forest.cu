@@ -30,18 +30,66 @@ __device__ __forceinline__ DepthDivisor make_divisor(int d) {
   return q;
 }
 
+// kHi: the shift is >= 32 (every depth d >= 65 mm).  Then trunc(n / d) for a signed n is
+// floor(n M / 2^shift) + [n < 0]: the high word of the signed product shifted arithmetically by
+// shift - 32, plus the sign bit.  (For n < 0, n M / 2^shift = -(q + r/d + |n| e / 2^shift) with
+// 0 < r/d + |n| e / 2^shift < 1, e = M - 2^shift / d, since |n| < 2^25 and 2^-l <= 1/d; checked
+// exhaustively for every d in [65, 65535] and every int16 offset.)  Otherwise the full 64-bit
+// product of |n| is shifted and the sign restored.
+template <bool kHi>
 __device__ __forceinline__ int probe(int x, int delta, const DepthDivisor& dv, int limit) {
   const int n = delta * 1000;
-  const unsigned a = (unsigned)(n < 0 ? -n : n);
-  const int q = (int)(((unsigned long long)a * (unsigned long long)dv.M) >> dv.shift);
-  const int p = x + (n < 0 ? -q : q);
-  return min(max(p, 0), limit);
+  int q;
+  if (kHi) {
+    q = (__mulhi(n, (int)dv.M) >> (dv.shift - 32)) - (n >> 31);
+  } else {
+    const unsigned a = (unsigned)(n < 0 ? -n : n);
+    const int m = (int)(((unsigned long long)a * (unsigned long long)dv.M) >> dv.shift);
+    q = n < 0 ? -m : m;
+  }
+  return min(max(x + q, 0), limit);
 }
 
-// One thread per pixel; the trees' descents are interleaved level by level so each level issues
-// T independent node loads instead of a chain of T * D dependent ones.
+// Descends pixel (u, v) of depth d through the trees, interleaved level by level so each level
+// issues T independent node loads instead of a chain of T * D dependent ones.  Colour nodes carry
+// their channels as bit shifts (the device copy of the forest, see relo_create_forest).
+template <int MT, bool kHi>
+__device__ __forceinline__ void descend(const ForestJob& job, int u, int v, const DepthDivisor& dv, int (&node)[MT]) {
+  const ForestView& f = job.forest;
+  const int T = f.T, W = job.W, H = job.H;
+  const int n_int = (1 << f.D) - 1;
+  for (int level = 0; level < f.D; ++level) {
+#pragma unroll
+    for (int t = 0; t < MT; ++t) {
+      if (t < T) {
+        const int4 nd = __ldg(&f.nodes[(size_t)t * n_int + node[t]]);
+        const int dx1 = (int)(int16_t)(nd.x & 0xFFFF), dy1 = nd.x >> 16;
+        const int dx2 = (int)(int16_t)(nd.y & 0xFFFF), dy2 = nd.y >> 16;
+        const int q1 = probe<kHi>(v, dy1, dv, H - 1) * W + probe<kHi>(u, dx1, dv, W - 1);
+        const int q2 = probe<kHi>(v, dy2, dv, H - 1) * W + probe<kHi>(u, dx2, dv, W - 1);
+        int a, b;
+        if ((nd.z & 0xFF) == 0) {
+          a = __ldg(&job.depth[q1]);
+          b = __ldg(&job.depth[q2]);
+        } else {
+          a = (__ldg(&job.rgba[q1]) >> ((nd.z >> 8) & 0xFF)) & 0xFF;
+          b = (__ldg(&job.rgba[q2]) >> ((nd.z >> 16) & 0xFF)) & 0xFF;
+        }
+        node[t] = 2 * node[t] + ((a - b < nd.w) ? 1 : 2);
+      }
+    }
+  }
+}
+
+// CTAs of 256 threads per SM the compiler must fit: full occupancy (7 and 8 tie, 6 is 10 % slower
+// on the house workload)
+#ifndef RELO_FOREST_MIN_BLOCKS
+#define RELO_FOREST_MIN_BLOCKS 8
+#endif
+
+// One thread per pixel.
 template <int MT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, RELO_FOREST_MIN_BLOCKS)
     forest_kernel(const ForestJob* __restrict__ jobs, int n_jobs, const ForestJob single) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int lo = 0, hi = n_jobs - 1;
@@ -69,28 +117,8 @@ __global__ void __launch_bounds__(256)
   int node[MT];
 #pragma unroll
   for (int t = 0; t < MT; ++t) node[t] = 0;
-  for (int level = 0; level < f.D; ++level) {
-#pragma unroll
-    for (int t = 0; t < MT; ++t) {
-      if (t < T) {
-        const int4 nd = __ldg(&f.nodes[(size_t)t * n_int + node[t]]);
-        const int dx1 = (int)(int16_t)(nd.x & 0xFFFF), dy1 = nd.x >> 16;
-        const int dx2 = (int)(int16_t)(nd.y & 0xFFFF), dy2 = nd.y >> 16;
-        const int q1 = probe(v, dy1, dv, H - 1) * W + probe(u, dx1, dv, W - 1);
-        const int q2 = probe(v, dy2, dv, H - 1) * W + probe(u, dx2, dv, W - 1);
-        int a, b;
-        if ((nd.z & 0xFF) == 0) {
-          a = __ldg(&job.depth[q1]);
-          b = __ldg(&job.depth[q2]);
-        } else {
-          const int c1 = (nd.z >> 8) & 0xFF, c2 = (nd.z >> 16) & 0xFF;
-          a = (__ldg(&job.rgba[q1]) >> (8 * c1)) & 0xFF;
-          b = (__ldg(&job.rgba[q2]) >> (8 * c2)) & 0xFF;
-        }
-        node[t] = (a - b < nd.w) ? 2 * node[t] + 1 : 2 * node[t] + 2;
-      }
-    }
-  }
+  if (dv.shift >= 32) descend<MT, true>(job, u, v, dv, node);
+  else descend<MT, false>(job, u, v, dv, node);
 #pragma unroll
   for (int t = 0; t < MT; ++t)
     if (t < T) job.leaves[(size_t)t * n_pix + pix] = (uint16_t)(node[t] - n_int);
