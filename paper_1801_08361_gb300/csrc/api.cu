@@ -160,6 +160,7 @@ namespace {
 struct RansacPass {
   RansacJob* d_jobs = nullptr;
   int n = 0, R = 0, chunks = 0, hyps = 0, B = 0;
+  int32_t* d_counter = nullptr;  // the search's hypothesis counter
   int32_t* d_alive_prefix = nullptr;
   int32_t* d_surv_prefix = nullptr;
   std::vector<int> tot_alive, tot_surv, max_alive, max_surv;
@@ -177,7 +178,7 @@ relo_status run_pass(const RansacPass& p, cudaStream_t s, int* launches, cudaEve
   int L = 0;
   if (p.n > 0) {
     RELO_CUDA(launch_compact(p.d_jobs, p.n, p.chunks, s));
-    RELO_CUDA(launch_hypotheses(p.d_jobs, p.n, p.hyps, s));
+    RELO_CUDA(launch_hypotheses(p.d_jobs, p.n, p.hyps, p.d_counter, s));
     L += 4;
   }
   RELO_CUDA(record(ev_hyp, s, external));
@@ -671,6 +672,7 @@ namespace {
 struct Single {
   RansacJob job{};
   RansacJob* d_job = nullptr;
+  int32_t* d_counter = nullptr;
   int32_t* d_alive = nullptr;
   int32_t* d_surv = nullptr;
   size_t bytes = 0;
@@ -681,6 +683,7 @@ struct Single {
 void layout_single(char* base, int W, int H, int K, int B, int T, Single& s) {
   Carver c{base, 0};
   s.d_job = c.take<RansacJob>(1);
+  s.d_counter = c.take<int32_t>(1);
   const int R = std::max(rounds_for(K), 1);
   s.d_alive = c.take<int32_t>((size_t)R * 2);
   s.d_surv = c.take<int32_t>((size_t)R * 2);
@@ -749,6 +752,7 @@ relo_status single_run(Single& s, const relo_ransac_params* p, relo_pose_result*
   round_tables(K, std::max(b.R, 1), at, su, b.tot_alive, b.tot_surv, b.max_alive, b.max_surv);
   b.B = p->batch;
   b.d_jobs = s.d_job;
+  b.d_counter = s.d_counter;
   b.d_alive_prefix = s.d_alive;
   b.d_surv_prefix = s.d_surv;
   b.chunks = s.chunks;
@@ -824,7 +828,7 @@ relo_status relo_ransac_hypotheses(const relo_forest* f, const uint16_t* depth, 
   RELO_CUDA(cudaMemcpyAsync(s.d_job, &s.job, sizeof(RansacJob), cudaMemcpyHostToDevice, cs));
   RELO_CUDA(cudaMemsetAsync(s.job.err, 0, sizeof(int32_t), cs));
   RELO_CUDA(launch_compact(s.d_job, 1, s.chunks, cs));
-  RELO_CUDA(launch_hypotheses(s.d_job, 1, p->n_hyps, cs));
+  RELO_CUDA(launch_hypotheses(s.d_job, 1, p->n_hyps, s.d_counter, cs));
   RELO_CUDA(cudaMemcpyAsync(poses, s.job.poses, (size_t)p->n_hyps * 12 * 8, cudaMemcpyDeviceToDevice, cs));
   RELO_CUDA(cudaMemcpyAsync(valid, s.job.hyp_ok, (size_t)p->n_hyps * 4, cudaMemcpyDeviceToDevice, cs));
   RELO_CUDA(cudaMemcpyAsync(tries, s.job.tries, (size_t)p->n_hyps * 4, cudaMemcpyDeviceToDevice, cs));
@@ -1451,6 +1455,8 @@ void layout_batch(const relo_attempt* at, int n, const relo_ransac_params& p, ch
   b.d_forest = c.take<ForestJob>(std::max(nF, 1));
   b.passL.d_jobs = c.take<RansacJob>(std::max(nL, 1));
   b.passF.d_jobs = c.take<RansacJob>(std::max(nF, 1));
+  b.passL.d_counter = c.take<int32_t>(1);
+  b.passF.d_counter = c.take<int32_t>(1);
   b.d_res_L = c.take<relo_pose_result>(n);
   b.d_res_F = c.take<relo_pose_result>(n);
   b.d_res = c.take<relo_pose_result>(n);

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cfloat>
 #include <climits>
 
@@ -354,11 +355,8 @@ __device__ __forceinline__ int first_passing(const RansacJob& job, int h, int n_
 #ifndef RELO_SEARCH_MIN_BLOCKS
 #define RELO_SEARCH_MIN_BLOCKS 4
 #endif
-__global__ void __launch_bounds__(kSearchWarps * 32, RELO_SEARCH_MIN_BLOCKS)
-    search_kernel(const RansacJob* __restrict__ jobs, int n_jobs, int total) {
-  const int gw = blockIdx.x * kSearchWarps + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (gw >= total) return;
+// The search of hypothesis gw (flattened over the jobs) by one warp.
+__device__ __forceinline__ void search_one(const RansacJob* __restrict__ jobs, int n_jobs, int gw, int lane) {
   int lo = 0, hi = n_jobs - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -395,6 +393,20 @@ __global__ void __launch_bounds__(kSearchWarps * 32, RELO_SEARCH_MIN_BLOCKS)
   if (lane == 0) {
     job.hyp_ok[h] = found != INT_MAX;
     job.tries[h] = found != INT_MAX ? found : job.max_tries;
+  }
+}
+
+// Persistent: hypotheses need from one try to max_tries, so each warp takes its next hypothesis
+// from a counter when it finishes one (which warp computes a hypothesis does not change its result).
+__global__ void __launch_bounds__(kSearchWarps * 32, RELO_SEARCH_MIN_BLOCKS)
+    search_kernel(const RansacJob* __restrict__ jobs, int n_jobs, int total, int32_t* __restrict__ counter) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int gw = 0;
+    if (lane == 0) gw = atomicAdd(counter, 1);
+    gw = __shfl_sync(0xffffffffu, gw, 0);
+    if (gw >= total) return;
+    search_one(jobs, n_jobs, gw, lane);
   }
 }
 
@@ -441,9 +453,21 @@ __global__ void __launch_bounds__(128) fit_kernel(const RansacJob* __restrict__ 
   job.inliers[h] = 0;
 }
 
-cudaError_t launch_hypotheses(const RansacJob* jobs, int n_jobs, int total_hyps, cudaStream_t s) {
+cudaError_t launch_hypotheses(const RansacJob* jobs, int n_jobs, int total_hyps, int32_t* counter, cudaStream_t s) {
   if (total_hyps <= 0) return cudaSuccess;
-  search_kernel<<<(total_hyps + kSearchWarps - 1) / kSearchWarps, kSearchWarps * 32, 0, s>>>(jobs, n_jobs, total_hyps);
+  static int slots = 0;  // resident warps-worth of CTAs on this GPU (first call)
+  if (slots == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_kernel, kSearchWarps * 32, 0);
+    if (e != cudaSuccess) return e;
+    slots = std::max(1, sms * per_sm);
+  }
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
+  if (e != cudaSuccess) return e;
+  const int grid = std::min(slots, (total_hyps + kSearchWarps - 1) / kSearchWarps);
+  search_kernel<<<grid, kSearchWarps * 32, 0, s>>>(jobs, n_jobs, total_hyps, counter);
   fit_kernel<<<(total_hyps + 127) / 128, 128, 0, s>>>(jobs, n_jobs, total_hyps);
   return cudaGetLastError();
 }

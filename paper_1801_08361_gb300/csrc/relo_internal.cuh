@@ -341,7 +341,8 @@ cudaError_t launch_scene_lookup(SceneView sv, const int32_t* keys, int64_t n, in
 // RANSAC stages over a device array of jobs.
 inline int table_words(int T) { return (3 + T + 7) / 8; }
 cudaError_t launch_compact(const RansacJob* jobs, int n_jobs, int total_chunks, cudaStream_t s);
-cudaError_t launch_hypotheses(const RansacJob* jobs, int n_jobs, int total_hyps, cudaStream_t s);
+// counter_dev: one int of device scratch the search's warps take hypotheses from (zeroed here)
+cudaError_t launch_hypotheses(const RansacJob* jobs, int n_jobs, int total_hyps, int32_t* counter_dev, cudaStream_t s);
 // round r: prefix[n_jobs + 1] = flattened alive-hypothesis offsets of the jobs still running
 cudaError_t launch_round(const RansacJob* jobs, int n_jobs, int round, const int32_t* alive_prefix_dev,
                          int total_alive, int max_alive, const int32_t* surv_prefix_dev, int total_surv, int max_surv,
