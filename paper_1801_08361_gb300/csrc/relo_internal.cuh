@@ -155,30 +155,38 @@ __device__ inline void horn_pose(const double S[9], const double cbar[3], const 
                     {Szx - Sxz, Sxy + Syx, -Sxx + Syy - Szz, Syz + Szy},
                     {Sxy - Syx, Szx + Sxz, Syz + Szy, -Sxx - Syy + Szz}};
   double V[4][4] = {{1, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, 1, 0}, {0, 0, 0, 1}};
+  // every index below is a compile-time constant after unrolling, so A and V stay in registers
   for (int sweep = 0; sweep < 30; ++sweep) {
     double off = 0.0, diag = 0.0;
+#pragma unroll
     for (int p = 0; p < 4; ++p) {
       diag += A[p][p] * A[p][p];
+#pragma unroll
       for (int q = p + 1; q < 4; ++q) off += A[p][q] * A[p][q];
     }
     if (off <= 1e-30 * (diag + 1e-300)) break;
+#pragma unroll
     for (int p = 0; p < 3; ++p) {
+#pragma unroll
       for (int q = p + 1; q < 4; ++q) {
         const double apq = A[p][q];
         if (fabs(apq) < 1e-300) continue;
         const double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
         const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
         const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+#pragma unroll
         for (int k = 0; k < 4; ++k) {  // A <- J^T A J
           const double akp = A[k][p], akq = A[k][q];
           A[k][p] = c * akp - s * akq;
           A[k][q] = s * akp + c * akq;
         }
+#pragma unroll
         for (int k = 0; k < 4; ++k) {
           const double apk = A[p][k], aqk = A[q][k];
           A[p][k] = c * apk - s * aqk;
           A[q][k] = s * apk + c * aqk;
         }
+#pragma unroll
         for (int k = 0; k < 4; ++k) {
           const double vkp = V[k][p], vkq = V[k][q];
           V[k][p] = c * vkp - s * vkq;
@@ -187,10 +195,16 @@ __device__ inline void horn_pose(const double S[9], const double cbar[3], const 
       }
     }
   }
-  int best = 0;
+  double best_d = A[0][0], w = V[0][0], x = V[1][0], y = V[2][0], z = V[3][0];
+#pragma unroll
   for (int k = 1; k < 4; ++k)
-    if (A[k][k] > A[best][best]) best = k;
-  double w = V[0][best], x = V[1][best], y = V[2][best], z = V[3][best];
+    if (A[k][k] > best_d) {
+      best_d = A[k][k];
+      w = V[0][k];
+      x = V[1][k];
+      y = V[2][k];
+      z = V[3][k];
+    }
   const double n = sqrt(w * w + x * x + y * y + z * z);
   w /= n; x /= n; y /= n; z /= n;
   const double R[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - w * z),     2 * (x * z + w * y),
