@@ -515,24 +515,73 @@ __global__ void draw_kernel(const RansacJob* __restrict__ jobs, const int32_t* _
   }
 }
 
-// Best mode of a drawn pixel (its record) under x = P c, over trees then modes in order (the first
-// of equal scores wins): its score (-inf if none) and mean.  Every lane of a warp reads the same
-// record and modes, so each load is one broadcast.
-__device__ __forceinline__ float record_best(const RansacJob& job, const int4* __restrict__ rec, float3 x,
-                                             float3* mu_best) {
+// A pixel's modes, staged by its warp in shared memory: the warp copies every mode of the pixel's
+// leaves (trees in order, modes in order) with parallel loads, then every lane scores them from
+// there, instead of each mode being a dependent global load in turn.
+constexpr int kStageModes = 64;  // modes per warp slot; a pixel with more is scored from global memory
+
+struct ModeSlot {
+  float4 m[kStageModes * 3];
+};
+
+// Copies the modes of record rec into slot (all lanes of the warp take part); returns their
+// number, or -1 if they do not fit (then nothing is staged).
+__device__ __forceinline__ int stage_modes(const RansacJob& job, const int4* __restrict__ rec, ModeSlot& slot,
+                                           int lane) {
   const ForestView& f = job.forest;
+  int total = 0;
+  for (int t = 0; t < f.T; ++t) {
+    const int4 w = __ldg(&rec[1 + t / 2]);
+    total += (t & 1) ? w.w : w.y;
+  }
+  if (total > kStageModes) return -1;
+  int off = 0;
+  for (int t = 0; t < f.T; ++t) {
+    const int4 w = __ldg(&rec[1 + t / 2]);
+    const int first = (t & 1) ? w.z : w.x, nm = (t & 1) ? w.w : w.y;
+    const float4* src = reinterpret_cast<const float4*>(f.modes + (size_t)first * kModeFloats);
+    for (int i = lane; i < 3 * nm; i += 32) slot.m[3 * off + i] = __ldg(&src[i]);
+    off += nm;
+  }
+  __syncwarp();
+  return total;
+}
+
+// Gaussian score of one mode (a, b, c: its 3 float4) at x.
+__device__ __forceinline__ float mode_score(float4 a, float4 b, float4 c, float3 x) {
+  const float dx = x.x - a.x, dy = x.y - a.y, dz = x.z - a.z;
+  // a.w = inv_xx, b = (inv_xy, inv_xz, inv_yy, inv_yz), c = (inv_zz, logw - 0.5 log det, w, pad)
+  const float q = dx * (a.w * dx + b.x * dy + b.y * dz) + dy * (b.x * dx + b.z * dy + b.w * dz) +
+                  dz * (b.y * dx + b.w * dy + c.x * dz);
+  return c.y - 0.5f * q;
+}
+
+// Best mode of a drawn pixel (its record) under x = P c, over trees then modes in order (the first
+// of equal scores wins): its score (-inf if none) and mean.  n_staged >= 0: the modes are in slot
+// (same order); otherwise they are read from global memory (every lane reads the same mode, so
+// each load is one broadcast).
+__device__ __forceinline__ float record_best(const RansacJob& job, const int4* __restrict__ rec, const ModeSlot& slot,
+                                             int n_staged, float3 x, float3* mu_best) {
   float best = -INFINITY;
+  if (n_staged >= 0) {
+    for (int k = 0; k < n_staged; ++k) {
+      const float4 a = slot.m[3 * k], b = slot.m[3 * k + 1], c = slot.m[3 * k + 2];
+      const float sc = mode_score(a, b, c, x);
+      if (sc > best) {
+        best = sc;
+        if (mu_best) *mu_best = make_float3(a.x, a.y, a.z);
+      }
+    }
+    return best;
+  }
+  const ForestView& f = job.forest;
   for (int t = 0; t < f.T; ++t) {
     const int4 w = __ldg(&rec[1 + t / 2]);
     const int first = (t & 1) ? w.z : w.x, nm = (t & 1) ? w.w : w.y;
     const float4* m = reinterpret_cast<const float4*>(f.modes + (size_t)first * kModeFloats);
     for (int k = 0; k < nm; ++k) {
       const float4 a = __ldg(&m[3 * k]), b = __ldg(&m[3 * k + 1]), c = __ldg(&m[3 * k + 2]);
-      const float dx = x.x - a.x, dy = x.y - a.y, dz = x.z - a.z;
-      // a.w = inv_xx, b = (inv_xy, inv_xz, inv_yy, inv_yz), c = (inv_zz, logw - 0.5 log det, w, pad)
-      const float q = dx * (a.w * dx + b.x * dy + b.y * dz) + dy * (b.x * dx + b.z * dy + b.w * dz) +
-                      dz * (b.y * dx + b.w * dy + c.x * dz);
-      const float sc = c.y - 0.5f * q;
+      const float sc = mode_score(a, b, c, x);
       if (sc > best) {
         best = sc;
         if (mu_best) *mu_best = make_float3(a.x, a.y, a.z);
@@ -567,9 +616,12 @@ __global__ void __launch_bounds__(kRoundWarps * 32) energy_kernel(const RansacJo
   const PoseF P = pose_to_float(job.poses + 12 * (size_t)h);
   float sum = 0.f;
   const int4* recs = job.pix + (size_t)r * job.B * job.hs;
+  __shared__ ModeSlot slots[kRoundWarps];
   for (int i = warp; i < job.B; i += kRoundWarps) {
     const int4* rec = recs + (size_t)i * job.hs;
-    const float best = record_best(job, rec, apply(P, record_point(rec)), nullptr);
+    __syncwarp();  // the slot's previous pixel is scored
+    const int n_staged = stage_modes(job, rec, slots[warp], lane);
+    const float best = record_best(job, rec, slots[warp], n_staged, apply(P, record_point(rec)), nullptr);
     sum += fminf(kLogEps, -best);
   }
   __shared__ float part[kRoundWarps][32];
@@ -661,12 +713,15 @@ __global__ void __launch_bounds__(kRoundWarps * 32) refine_kernel(const RansacJo
 #pragma unroll
   for (int q = 0; q < 16; ++q) acc[q] = 0.f;
   const int p1 = min(p0 + kRefinePixels, n_drawn);
+  __shared__ ModeSlot slots[kRoundWarps];
   for (int i = p0 + warp; i < p1; i += kRoundWarps) {
     const int4* rec = job.pix + (size_t)i * job.hs;
     const float3 c = record_point(rec);
     const float3 x = apply(P, c);
     float3 mu;
-    const float best = record_best(job, rec, x, &mu);
+    __syncwarp();  // the slot's previous pixel is scored
+    const int n_staged = stage_modes(job, rec, slots[warp], lane);
+    const float best = record_best(job, rec, slots[warp], n_staged, x, &mu);
     if (best == -INFINITY) continue;
     const float dx = x.x - mu.x, dy = x.y - mu.y, dz = x.z - mu.z;
     if (dx * dx + dy * dy + dz * dz < r2) {
@@ -708,11 +763,14 @@ __global__ void __launch_bounds__(kRoundWarps * 32) refine_kernel(const RansacJo
 }
 
 // Re-fit solve: thread per survivor; the parts' sums are added in order in FP64, then FP64 Horn on
-// the centroids and cross-covariance (>= 3 inliers, else the pose is kept).
-__global__ void __launch_bounds__(128) refit_kernel(const RansacJob* __restrict__ jobs, int n_jobs,
-                                                    const int32_t* __restrict__ surv_prefix, int total, int r) {
-  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= total) return;
+// the centroids and cross-covariance (>= 3 inliers, else the pose is kept).  CTAs of one warp take
+// `per` survivors each: with few survivors (late rounds) they spread over the SMs, whose FP64 pipes
+// would otherwise run one warp's solves in series.
+__global__ void __launch_bounds__(32) refit_kernel(const RansacJob* __restrict__ jobs, int n_jobs,
+                                                   const int32_t* __restrict__ surv_prefix, int total, int r,
+                                                   int per) {
+  const int gid = blockIdx.x * per + threadIdx.x;
+  if ((int)threadIdx.x >= per || gid >= total) return;
   const int jid = find_job_by(surv_prefix, n_jobs, gid);
   const RansacJob& job = jobs[jid];
   if (job_skipped(job.skip)) return;
@@ -752,8 +810,16 @@ cudaError_t launch_round(const RansacJob* jobs, int n_jobs, int round, const int
                                                                                         round);
   const int parts = ((round + 1) * B + kRefinePixels - 1) / kRefinePixels;
   refine_kernel<<<dim3((max_surv + 31) / 32, parts, n_jobs), kRoundWarps * 32, 0, s>>>(jobs, surv_prefix_dev, round);
-  refit_kernel<<<(unsigned)((total_surv + 127) / 128), 128, 0, s>>>(jobs, n_jobs, surv_prefix_dev, total_surv,
-                                                                     round);
+  static int n_sms = 0;
+  if (n_sms == 0) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+  }
+  const int per = std::max(1, std::min(32, (total_surv + 2 * n_sms - 1) / (2 * n_sms)));
+  refit_kernel<<<(unsigned)((total_surv + per - 1) / per), 32, 0, s>>>(jobs, n_jobs, surv_prefix_dev, total_surv,
+                                                                       round, per);
   return cudaGetLastError();
 }
 
