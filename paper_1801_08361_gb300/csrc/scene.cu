@@ -62,20 +62,38 @@ __device__ __forceinline__ float cube_exit(float3 C, const RayExit& e, int bx, i
   return fminf(lx, fminf(ly, lz));
 }
 
-// Value of voxel (i, j, k): tsdf, or +1 when its block is unallocated.
-__device__ __forceinline__ float voxel_tsdf(const SceneView& s, BlockCache& c, int i, int j, int k, int* err) {
-  const int b = cached_block(s, c, i >> 3, j >> 3, k >> 3, err);
-  if (b < 0) return 1.0f;
-  return __ldg(&s.tsdf[(size_t)b * kVoxelsPerBlock + (i & 7) + 8 * (j & 7) + 64 * (k & 7)]);
+// Blocks holding the 8 corners of the voxel cell at (i, j, k) (corner n = (i + (n & 1),
+// j + (n >> 1 & 1), k + (n >> 2))), given b0 = the block of (i, j, k): a corner leaves b0 only
+// along the axes where the cell sits on b0's last voxel, so at most 7 further lookups, usually 0
+// or 1 (instead of one per corner through a one-entry cache that neighbouring corners evict).
+__device__ __forceinline__ void corner_blocks(const SceneView& s, BlockCache& c, int b0, int i, int j, int k,
+                                              int (&blk)[8], int* err) {
+  const int bx = i >> 3, by = j >> 3, bz = k >> 3;
+  const bool ex = (i & 7) == 7, ey = (j & 7) == 7, ez = (k & 7) == 7;
+  blk[0] = b0;
+  blk[1] = ex ? cached_block(s, c, bx + 1, by, bz, err) : b0;
+  blk[2] = ey ? cached_block(s, c, bx, by + 1, bz, err) : b0;
+  blk[3] = ex ? (ey ? cached_block(s, c, bx + 1, by + 1, bz, err) : blk[1]) : blk[2];
+  if (ez) {
+    blk[4] = cached_block(s, c, bx, by, bz + 1, err);
+    blk[5] = ex ? cached_block(s, c, bx + 1, by, bz + 1, err) : blk[4];
+    blk[6] = ey ? cached_block(s, c, bx, by + 1, bz + 1, err) : blk[4];
+    blk[7] = ex ? (ey ? cached_block(s, c, bx + 1, by + 1, bz + 1, err) : blk[5]) : blk[6];
+  } else {
+    blk[4] = blk[0];
+    blk[5] = blk[1];
+    blk[6] = blk[2];
+    blk[7] = blk[3];
+  }
 }
 
-__device__ __forceinline__ uint32_t voxel_rgba(const SceneView& s, BlockCache& c, int i, int j, int k, int* err) {
-  const int b = cached_block(s, c, i >> 3, j >> 3, k >> 3, err);
-  if (b < 0) return 0u;
-  return __ldg(&s.rgba[(size_t)b * kVoxelsPerBlock + (i & 7) + 8 * (j & 7) + 64 * (k & 7)]);
+// Index inside its block of corner n of the voxel cell at (i, j, k).
+__device__ __forceinline__ int corner_voxel(int i, int j, int k, int n) {
+  return ((i + (n & 1)) & 7) + 8 * ((j + ((n >> 1) & 1)) & 7) + 64 * ((k + (n >> 2)) & 7);
 }
 
-// Trilinear tsdf at voxel-space point q (= p / voxel), given the block b0 holding floor(q).
+// Trilinear tsdf at voxel-space point q (= p / voxel), given the block b0 holding floor(q);
+// corners in unallocated blocks read +1.
 __device__ __forceinline__ float trilinear_tsdf(const SceneView& s, BlockCache& c, int b0, int i, int j, int k,
                                                 float fx, float fy, float fz, int* err) {
   float v[8];
@@ -91,8 +109,11 @@ __device__ __forceinline__ float trilinear_tsdf(const SceneView& s, BlockCache& 
     v[6] = __ldg(base + 72);
     v[7] = __ldg(base + 73);
   } else {
+    int blk[8];
+    corner_blocks(s, c, b0, i, j, k, blk, err);
 #pragma unroll
-    for (int n = 0; n < 8; ++n) v[n] = voxel_tsdf(s, c, i + (n & 1), j + ((n >> 1) & 1), k + (n >> 2), err);
+    for (int n = 0; n < 8; ++n)
+      v[n] = blk[n] < 0 ? 1.0f : __ldg(&s.tsdf[(size_t)blk[n] * kVoxelsPerBlock + corner_voxel(i, j, k, n)]);
   }
   const float x00 = v[0] + fx * (v[1] - v[0]);
   const float x10 = v[2] + fx * (v[3] - v[2]);
@@ -103,17 +124,20 @@ __device__ __forceinline__ float trilinear_tsdf(const SceneView& s, BlockCache& 
   return y0 + fz * (y1 - y0);
 }
 
+// Trilinear colour at point p (corners in unallocated blocks read 0), rounded half up.
 __device__ __forceinline__ uint32_t trilinear_rgba(const SceneView& s, BlockCache& c, float3 p, int* err) {
   const float qx = p.x * s.inv_voxel, qy = p.y * s.inv_voxel, qz = p.z * s.inv_voxel;
   const float flx = floorf(qx), fly = floorf(qy), flz = floorf(qz);
   const int i = (int)flx, j = (int)fly, k = (int)flz;
   const float fx = qx - flx, fy = qy - fly, fz = qz - flz;
+  int blk[8];
+  corner_blocks(s, c, cached_block(s, c, i >> 3, j >> 3, k >> 3, err), i, j, k, blk, err);
   float acc[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int n = 0; n < 8; ++n) {
     const int dx = n & 1, dy = (n >> 1) & 1, dz = n >> 2;
     const float w = (dx ? fx : 1.f - fx) * (dy ? fy : 1.f - fy) * (dz ? fz : 1.f - fz);
-    const uint32_t col = voxel_rgba(s, c, i + dx, j + dy, k + dz, err);
+    const uint32_t col = blk[n] < 0 ? 0u : __ldg(&s.rgba[(size_t)blk[n] * kVoxelsPerBlock + corner_voxel(i, j, k, n)]);
     acc[0] += w * (float)(col & 0xFF);
     acc[1] += w * (float)((col >> 8) & 0xFF);
     acc[2] += w * (float)((col >> 16) & 0xFF);
