@@ -193,7 +193,7 @@ constexpr int kTile = 16;
 // of 4 to 8 on the house workload; the march is latency-bound, so occupancy beats the few
 // registers this spills
 #ifndef RELO_RAYCAST_MIN_BLOCKS
-#define RELO_RAYCAST_MIN_BLOCKS 8
+#define RELO_RAYCAST_MIN_BLOCKS 6
 #endif
 
 template <bool kColour, bool kCompare>
