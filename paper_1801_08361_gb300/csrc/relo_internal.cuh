@@ -155,7 +155,11 @@ __device__ inline void horn_pose(const double S[9], const double cbar[3], const 
                     {Szx - Sxz, Sxy + Syx, -Sxx + Syy - Szz, Syz + Szy},
                     {Sxy - Syx, Szx + Sxz, Syz + Szy, -Sxx - Syy + Szz}};
   double V[4][4] = {{1, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, 1, 0}, {0, 0, 0, 1}};
-  // every index below is a compile-time constant after unrolling, so A and V stay in registers
+  // Cyclic Jacobi in the parallel ordering: each sweep is three stages of two rotations on
+  // disjoint index pairs, ((0,1),(2,3)), ((0,2),(1,3)), ((0,3),(1,2)), whose angles are computed
+  // independently (two divide / square-root chains in flight instead of one).  Every index is a
+  // compile-time constant after unrolling, so A and V stay in registers.
+  constexpr int kPairs[3][2][2] = {{{0, 1}, {2, 3}}, {{0, 2}, {1, 3}}, {{0, 3}, {1, 2}}};
   for (int sweep = 0; sweep < 30; ++sweep) {
     double off = 0.0, diag = 0.0;
 #pragma unroll
@@ -166,14 +170,25 @@ __device__ inline void horn_pose(const double S[9], const double cbar[3], const 
     }
     if (off <= 1e-30 * (diag + 1e-300)) break;
 #pragma unroll
-    for (int p = 0; p < 3; ++p) {
+    for (int st = 0; st < 3; ++st) {
+      double cs[2], sn[2];
 #pragma unroll
-      for (int q = p + 1; q < 4; ++q) {
+      for (int r = 0; r < 2; ++r) {
+        const int p = kPairs[st][r][0], q = kPairs[st][r][1];
         const double apq = A[p][q];
-        if (fabs(apq) < 1e-300) continue;
-        const double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
-        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        cs[r] = 1.0;
+        sn[r] = 0.0;
+        if (fabs(apq) >= 1e-300) {
+          const double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
+          const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+          cs[r] = rsqrt(t * t + 1.0);
+          sn[r] = t * cs[r];
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const int p = kPairs[st][r][0], q = kPairs[st][r][1];
+        const double c = cs[r], s = sn[r];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {  // A <- J^T A J
           const double akp = A[k][p], akq = A[k][q];
