@@ -61,9 +61,9 @@ ALG_BYTES_PER_PIXEL = {
 # DRAM bytes (read + write) per launch of the stage's main kernel, from the ncu capture summarised
 # in profiles/attempt_kernels_house_640x480_batch128.md (None: not captured for the current code).
 PROFILED_TRAFFIC_BYTES = {
-    "query_raycast": 3.039e9 + 0.236e9,
-    "forest_eval": 0.241e9 + 0.352e9,
-    "forest_hypotheses": 0.636e9 + 0.005e9,
+    "query_raycast": 3.081e9 + 0.281e9,
+    "forest_eval": 0.240e9 + 0.359e9,
+    "forest_hypotheses": 0.638e9 + 0.005e9,
     "forest_verify": None,
 }
 
