@@ -478,14 +478,14 @@ relo_status relo_create_forest(const void* nodes, int32_t T, int32_t D, const fl
     relo_destroy_forest(f);
     return fail(RELO_ENOMEM, "device allocation for the forest failed");
   }
-  // device copy of the nodes: a colour node's channels c1, c2 become the bit shifts 8 c1, 8 c2
+  // device copy of the nodes: a colour node's channels c1, c2 become 16 + 8 c1, 16 + 8 c2 (their
+  // bit offsets in a packed pixel {depth | r << 16 | g << 24 | b << 32}), a depth node's 0
   std::vector<int4> dev_nodes((size_t)T * n_int);
   std::memcpy(dev_nodes.data(), nodes, dev_nodes.size() * 16);
-  for (int4& nd : dev_nodes)
-    if ((nd.z & 0xFF) != 0) {
-      const int c1 = (nd.z >> 8) & 0xFF, c2 = (nd.z >> 16) & 0xFF;
-      nd.z = (nd.z & (int)0xFF0000FF) | ((8 * c1) & 0xFF) << 8 | ((8 * c2) & 0xFF) << 16;
-    }
+  for (int4& nd : dev_nodes) {
+    const int kind = nd.z & 0xFF, c1 = (nd.z >> 8) & 0xFF, c2 = (nd.z >> 16) & 0xFF;
+    nd.z = kind == 0 ? 0 : (1 | (16 + 8 * c1) << 8 | (16 + 8 * c2) << 16);
+  }
   cudaError_t e = cudaMemcpy(f->d_nodes, dev_nodes.data(), (size_t)T * n_int * 16, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = modes ? cudaMemcpy(f->d_modes, modes, modes_bytes, cudaMemcpyHostToDevice)
                                   : cudaMemset(f->d_modes, 0, modes_bytes);
@@ -1588,11 +1588,15 @@ void layout_batch(const relo_attempt* at, int n, const relo_ransac_params& p, ch
       maxT = std::max(maxT, T);
       uint16_t* leaves = c.take<uint16_t>(n_pix * T);
       b.a_leaves[i] = leaves;
+      // the query raycast also writes the image packed per pixel, which the forest reads
+      uint2* packed = c.take<uint2>(n_pix);
+      h.query[i].packed = packed;
       const int32_t* skip = kind[i] == 2 ? &b.d_res_L[i].verified : nullptr;
       ForestJob& f = h.forest[j];
       f.forest = a.forest_a->view;
       f.depth = depth;
       f.rgba = rgba;
+      f.packed = packed;
       f.leaves = leaves;
       f.W = W;
       f.H = H;

@@ -51,9 +51,13 @@ __device__ __forceinline__ int probe(int x, int delta, const DepthDivisor& dv, i
 }
 
 // Descends pixel (u, v) of depth d through the trees, interleaved level by level so each level
-// issues T independent node loads instead of a chain of T * D dependent ones.  Colour nodes carry
-// their channels as bit shifts (the device copy of the forest, see relo_create_forest).
-template <int MT, bool kHi>
+// issues T independent node loads instead of a chain of T * D dependent ones.  In the device copy
+// of the forest (relo_create_forest) a colour node's probe channels c1, c2 are stored as the bit
+// offsets 16 + 8 c1, 16 + 8 c2 of the channel in a packed pixel, a depth node's as 0.
+// kPacked: probes read the packed image (one 64-bit load, then a shift and a mask: no branch on
+// the node's kind, which differs between neighbouring lanes); otherwise the depth or the colour
+// image, by kind.
+template <int MT, bool kHi, bool kPacked>
 __device__ __forceinline__ void descend(const ForestJob& job, int u, int v, const DepthDivisor& dv, int (&node)[MT]) {
   const ForestView& f = job.forest;
   const int T = f.T, W = job.W, H = job.H;
@@ -68,12 +72,17 @@ __device__ __forceinline__ void descend(const ForestJob& job, int u, int v, cons
         const int q1 = probe<kHi>(v, dy1, dv, H - 1) * W + probe<kHi>(u, dx1, dv, W - 1);
         const int q2 = probe<kHi>(v, dy2, dv, H - 1) * W + probe<kHi>(u, dx2, dv, W - 1);
         int a, b;
-        if ((nd.z & 0xFF) == 0) {
+        if (kPacked) {
+          const unsigned mask = 0xFFFFu >> ((nd.z & 0xFF) << 3), s1 = (nd.z >> 8) & 0xFF, s2 = (nd.z >> 16) & 0xFF;
+          const uint2 p1 = __ldg(&job.packed[q1]), p2 = __ldg(&job.packed[q2]);
+          a = (int)(__funnelshift_rc(p1.x, p1.y, s1) & mask);
+          b = (int)(__funnelshift_rc(p2.x, p2.y, s2) & mask);
+        } else if ((nd.z & 0xFF) == 0) {
           a = __ldg(&job.depth[q1]);
           b = __ldg(&job.depth[q2]);
         } else {
-          a = (__ldg(&job.rgba[q1]) >> ((nd.z >> 8) & 0xFF)) & 0xFF;
-          b = (__ldg(&job.rgba[q2]) >> ((nd.z >> 16) & 0xFF)) & 0xFF;
+          a = (__ldg(&job.rgba[q1]) >> (((nd.z >> 8) & 0xFF) - 16)) & 0xFF;
+          b = (__ldg(&job.rgba[q2]) >> (((nd.z >> 16) & 0xFF) - 16)) & 0xFF;
         }
         node[t] = 2 * node[t] + ((a - b < nd.w) ? 1 : 2);
       }
@@ -117,8 +126,13 @@ __global__ void __launch_bounds__(256, RELO_FOREST_MIN_BLOCKS)
   int node[MT];
 #pragma unroll
   for (int t = 0; t < MT; ++t) node[t] = 0;
-  if (dv.shift >= 32) descend<MT, true>(job, u, v, dv, node);
-  else descend<MT, false>(job, u, v, dv, node);
+  if (job.packed) {
+    if (dv.shift >= 32) descend<MT, true, true>(job, u, v, dv, node);
+    else descend<MT, false, true>(job, u, v, dv, node);
+  } else {
+    if (dv.shift >= 32) descend<MT, true, false>(job, u, v, dv, node);
+    else descend<MT, false, false>(job, u, v, dv, node);
+  }
 #pragma unroll
   for (int t = 0; t < MT; ++t)
     if (t < T) job.leaves[(size_t)t * n_pix + pix] = (uint16_t)(node[t] - n_int);

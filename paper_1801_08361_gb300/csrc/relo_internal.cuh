@@ -268,8 +268,9 @@ struct RayJob {
   const uint16_t* depth_ref;   // compare mode: reference depth (D_b)
   unsigned long long* counts;  // compare mode: {omega_a, omega_b, omega_ab, sum |D_a - D_b|}
   int32_t* err;                // device error flag (nullable)
+  uint2* packed;               // nullable, colour renders: {depth | r << 16 | g << 24, b} per pixel
   int32_t tile_begin;          // first 16 x 16 tile of this job in the flattened launch
-  int32_t pad[3];              // size: a multiple of 16 bytes (staged in shared memory)
+  int32_t pad;                 // size: a multiple of 16 bytes (staged in shared memory)
 };
 static_assert(sizeof(RayJob) % 16 == 0, "RayJob is staged in shared memory as 16-byte words");
 
@@ -280,6 +281,7 @@ struct ForestJob {
   ForestView forest;
   const uint16_t* depth;
   const uint32_t* rgba;
+  const uint2* packed;         // nullable: the same image packed per pixel (see RayJob::packed)
   uint16_t* leaves;            // [T][H][W]
   int32_t W, H;
   int64_t pixel_begin;         // first pixel of this job in the flattened launch

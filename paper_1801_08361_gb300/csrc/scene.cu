@@ -259,6 +259,7 @@ __global__ void __launch_bounds__(kTile* kTile, kColour ? RELO_RAYCAST_MIN_BLOCK
     }
     if (job.depth) job.depth[pix] = (uint16_t)depth_mm;
     if (kColour && job.rgba) job.rgba[pix] = col;
+    if (kColour && job.packed) job.packed[pix] = make_uint2((uint32_t)depth_mm | (col & 0xFFFFu) << 16, (col >> 16) & 0xFFu);
     if (err && job.err) atomicExch(job.err, RELO_EDEVICE);
   }
   if (kCompare) {
