@@ -1602,7 +1602,7 @@ void layout_batch(const relo_attempt* at, int n, const relo_ransac_params& p, ch
       f.H = H;
       f.pixel_begin = fpix;
       f.skip = skip;
-      fpix += (int64_t)n_pix;
+      fpix += ((int64_t)n_pix + 255) / 256 * 256;  // a forest CTA never spans two jobs
       RansacJob& r = h.ransac_F[j];
       fill_ransac_job(r, a.forest_a->view, depth, leaves, a.intr, p, K, a.seed);
       carve_ransac(c, r, W, H, K, p.batch, r.n_rounds, T);

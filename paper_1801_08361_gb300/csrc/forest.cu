@@ -101,13 +101,25 @@ template <int MT>
 __global__ void __launch_bounds__(256, RELO_FOREST_MIN_BLOCKS)
     forest_kernel(const ForestJob* __restrict__ jobs, int n_jobs, const ForestJob single) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // jobs start on multiples of the CTA size, so the CTA's first pixel names its job; the job is
+  // staged in shared memory (its fields are read at every node visit)
+  const int64_t first = (int64_t)blockIdx.x * blockDim.x;
   int lo = 0, hi = n_jobs - 1;
   while (jobs && lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (jobs[mid].pixel_begin <= gid) lo = mid;
+    if (jobs[mid].pixel_begin <= first) lo = mid;
     else hi = mid - 1;
   }
-  const ForestJob& job = jobs ? jobs[lo] : single;
+  __shared__ __align__(16) ForestJob sj;
+  if (jobs) {
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(jobs + lo);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(&sj);
+    for (int i = threadIdx.x; i < (int)(sizeof(ForestJob) / 8); i += blockDim.x) dst[i] = src[i];
+  } else if (threadIdx.x == 0) {
+    sj = single;
+  }
+  __syncthreads();
+  const ForestJob& job = sj;
   if (job_skipped(job.skip)) return;
   const int64_t pix = gid - job.pixel_begin;
   const int64_t n_pix = (int64_t)job.W * job.H;
@@ -143,6 +155,7 @@ cudaError_t launch_forest(const ForestJob* jobs_dev, int n_jobs, const ForestJob
   if (total_pixels <= 0) return cudaSuccess;
   ForestJob one{};
   if (single) one = *single;
+  // total_pixels counts each job's pixels rounded up to a multiple of 256 (pixel_begin)
   const unsigned grid = (unsigned)((total_pixels + 255) / 256);
   if (max_trees <= 4) forest_kernel<4><<<grid, 256, 0, s>>>(jobs_dev, n_jobs, one);
   else if (max_trees <= 8) forest_kernel<8><<<grid, 256, 0, s>>>(jobs_dev, n_jobs, one);

@@ -284,9 +284,10 @@ struct ForestJob {
   const uint2* packed;         // nullable: the same image packed per pixel (see RayJob::packed)
   uint16_t* leaves;            // [T][H][W]
   int32_t W, H;
-  int64_t pixel_begin;         // first pixel of this job in the flattened launch
+  int64_t pixel_begin;         // first pixel of this job in the flattened launch (multiple of 256)
   const int32_t* skip;         // when set and non-zero the job does nothing (fallback not needed)
 };
+static_assert(sizeof(ForestJob) % 8 == 0, "ForestJob is staged in shared memory as 8-byte words");
 
 // ---------------------------------------------------------------------------------------------
 // RANSAC jobs (one query view, one forest) and their workspace
