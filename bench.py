@@ -73,13 +73,36 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--batch", type=int, default=128, help="attempts per step")
+    ap.add_argument("--batch", type=int, default=256, help="attempts per step")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=0, help="(ncu) run this many steps and exit, no JSON")
     ap.add_argument("--train-steps", type=int, default=2000,
                     help="online training steps of the learned regressor (0: skip the learned path)")
     return ap.parse_args()
+
+
+def rank_seeds(rank, set_index, k):
+    """Seeds of attempt k of query set set_index on this rank: (query-set seed, noise seed, RANSAC
+    seed).  Ranks and sets draw disjoint seeds, so each rank relocalises attempts of its own."""
+    return (1000 * (rank + 1) + set_index, 5_000_000 + 100_000 * rank + 10_000 * set_index + k,
+            (rank << 40) + (set_index << 20) + k)
+
+
+def reduce_max(value, world_size, device="cpu"):
+    """The largest of the ranks' values (the job's time is its slowest rank's); any backend."""
+    if world_size == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(attempts_per_rank_step, steps, world_size, elapsed_s):
+    """Whole-job attempts/s: every rank's attempts over the slowest rank's time (weak scaling)."""
+    return attempts_per_rank_step * steps * world_size / elapsed_s
 
 
 def dist_env():
@@ -272,11 +295,11 @@ def run_ours(args):
     prm = B.ransac_params(n_hyps=K_HYPS, batch=B_PIX, max_tries=10000)
     sets = []
     for si in range(n_sets):
-        qs = query_set(world, train, A, seed=1000 * (rank + 1) + si)
-        noise = torch.from_numpy(np.stack([synth.depth_noise(H, W, 5000 + 1000 * rank + 100 * si + k)
+        qs = query_set(world, train, A, seed=rank_seeds(rank, si, 0)[0])
+        noise = torch.from_numpy(np.stack([synth.depth_noise(H, W, rank_seeds(rank, si, k)[1])
                                            for k in range(A)])).to(dev)
         items = [dict(scene_b=scene, forest_a=forest, scene_a=scene, intr=intr, pose_b=qs[k], noise=noise[k],
-                      seed=(rank << 40) + (si << 20) + k) for k in range(A)]
+                      seed=rank_seeds(rank, si, k)[2]) for k in range(A)]
         att = B.make_attempts(items)
         ws = torch.empty(B.batch_workspace_size(att, prm), dtype=torch.uint8, device=dev)
         bt = B.Batch(att, prm, ws)
@@ -321,12 +344,8 @@ def run_ours(args):
         results.append((st, st["res"].cpu()))
     step_ms = [a.elapsed_time(b) for a, b in ev]
     clocks = clocks_summary(clk)
-    elapsed = sum(step_ms) / 1000.0
-    if world_size > 1:
-        t = torch.tensor([elapsed], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(t.item())
-    value = A * args.steps * world_size / elapsed
+    elapsed = reduce_max(sum(step_ms) / 1000.0, world_size, dev)
+    value = job_throughput(A, args.steps, world_size, elapsed)
 
     # success (the criterion of Sec. 4.2.2: <= 5 cm and <= 5 degrees) and verification rate
     succ = ver = n = 0
@@ -358,7 +377,7 @@ def run_ours(args):
         st["noise"].copy_(host_noise[(args.warmup + s) % n_sets], non_blocking=True)
         B.relocalise_batch(st["att"], prm, st["ws"])       # prepares, runs, copies results back, syncs
         e2e_t += time.perf_counter() - t0
-    e2e_value = A * args.steps * world_size / e2e_t
+    e2e_value = job_throughput(A, args.steps, world_size, reduce_max(e2e_t, world_size, dev))
 
     # ---- roofline of the dominant stage ---------------------------------------------------
     dom = max(stage_tot, key=stage_tot.get)
