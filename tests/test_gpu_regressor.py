@@ -253,3 +253,34 @@ def test_fallback_reports_the_forest_result(room, room_training, gpu_room_scene,
         else:
             assert l["path"] == B.PATH_LEARNED and l["verified"] == 1
     assert any(l["path"] == B.PATH_FALLBACK for l in out[0])
+
+
+def test_full_size_forward_matches_oracle_on_sampled_cells(params):
+    """A 640 x 480 forward pass (the bench's view size) on sampled interior cells.  Output cell c
+    depends only on input pixels 8c - 47 .. 8c + 47 per axis (five 3x3 layers at 1/8 resolution
+    and three stride-2 layers), so the oracle's forward pass on a 128 x 128 crop whose corner is a
+    multiple of 8 gives exactly the full image's cells 6 .. 10 of that crop (same tolerance as the
+    small-view test: the oracle is given the BF16 weights and input the kernels multiply)."""
+    rng = np.random.default_rng(12)
+    n, H, W = 2, 480, 640
+    d = rng.integers(400, 9000, (n, H, W)).astype(np.uint16)
+    d[rng.random((n, H, W)) < 0.05] = 0
+    c = rng.integers(0, 256, (n, H, W, 4)).astype(np.uint8)
+    reg = B.Regressor(_flat(params), origin=ORIGIN)
+    out = torch.zeros((n, H // 8, W // 8, 4), dtype=torch.float32, device=DEV)
+    ws = torch.empty(B.regressor_workspace_size(n, W, H, False), dtype=torch.uint8, device=DEV)
+    B.regressor_forward(reg, _u16(d), torch.from_numpy(c).to(DEV), out, ws)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    pq = _operands(params, np.zeros((1, 8, 8, 4)))[0]
+    crops = [(0, 64, 96), (0, 256, 400), (1, 128, 480), (1, 320, 16)]   # (image, y0, x0)
+    g_all, w_all = [], []
+    for i, y0, x0 in crops:
+        x = _bf16(R.network_input(d[i, y0:y0 + 128, x0:x0 + 128], c[i, y0:y0 + 128, x0:x0 + 128]))[None]
+        want, _ = R.forward(pq, x)
+        cy, cx = y0 // 8, x0 // 8
+        w_all.append(want[0, 6:11, 6:11])
+        g_all.append(got[i, cy + 6:cy + 11, cx + 6:cx + 11])
+    g_all, w_all = np.stack(g_all), np.stack(w_all)
+    rel = np.linalg.norm(g_all - w_all) / np.linalg.norm(w_all)
+    assert rel <= 1e-2, rel
