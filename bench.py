@@ -79,6 +79,8 @@ def parse():
     ap.add_argument("--profile-steps", type=int, default=0, help="(ncu) run this many steps and exit, no JSON")
     ap.add_argument("--train-steps", type=int, default=2000,
                     help="online training steps of the learned regressor (0: skip the learned path)")
+    ap.add_argument("--serve-seconds", type=float, default=4.0,
+                    help="seconds per serving operating point (0: skip the serving measurement)")
     return ap.parse_args()
 
 
@@ -364,6 +366,11 @@ def run_ours(args):
         learned = learned_section(args, B, synth, torch, dev, scene, forest, world, intr, train, sets[0], prm,
                                   stream)
 
+    # ---- serving (not part of the timed steps) ----------------------------------------------
+    serving = None
+    if args.serve_seconds > 0 and rank == 0:
+        serving = serving_section(args, B, torch, dev, sets[0], prm)
+
     # ---- end to end through the public API (host buffers) ----------------------------------
     host_noise = [torch.empty((A, H, W), dtype=torch.float32, pin_memory=True) for _ in range(n_sets)]
     for si in range(n_sets):
@@ -398,7 +405,7 @@ def run_ours(args):
                            "l2": "flushed between steps (512 MiB write)",
                            "success_rate": succ / n, "verified_rate": ver / n,
                            "stage_ms_per_step": {k: v / args.steps for k, v in stage_tot.items()},
-                           "learned": learned},
+                           "learned": learned, "serving": serving},
                 "e2e": {"value": e2e_value, "unit": UNIT,
                         "h2d_bytes_per_step": A * H * W * 4 + A * ctypes_attempt_bytes(),
                         "d2h_bytes_per_step": A * B.RESULT_BYTES},
@@ -505,6 +512,72 @@ def success(r, P):
     cang = (np.trace(r["pose"][:3, :3] @ P[:3, :3].T) - 1) / 2
     dr = math.degrees(math.acos(max(-1.0, min(1.0, cang))))
     return r["status"] == 0 and dt <= 0.05 and dr <= 5.0
+
+
+# ------------------------------------------------------------------------------------------------
+# Serving: agents (threads) submit single attempts at Poisson times to relo_server; the worker
+# batches them under the workspace budget; latency = completion - submission
+# ------------------------------------------------------------------------------------------------
+SERVE_POINTS = [(8, 200.0), (16, 4000.0)]   # (agents, offered requests/s over all agents)
+SERVE_MAX_BATCH, SERVE_MAX_WAIT_US, SERVE_SLOTS = 64, 2000, 512
+
+
+def serving_section(args, B, torch, dev, st, prm):
+    import queue
+    import threading
+    atts = st["att"]
+    A = len(atts)
+    ws_bytes = B.batch_workspace_size(B.make_attempts_view(atts, SERVE_MAX_BATCH), prm) + (1 << 20)
+    points = []
+    for agents, rate in SERVE_POINTS:
+        srv = B.Server(prm, workspace_bytes=ws_bytes, max_batch=SERVE_MAX_BATCH, max_wait_us=SERVE_MAX_WAIT_US,
+                       slots=SERVE_SLOTS)
+        tickets = queue.Queue()
+        stop_at = time.perf_counter() + args.serve_seconds
+        sent = [0] * agents
+
+        def agent(a):
+            rng = np.random.default_rng(1000 + a)
+            t = time.perf_counter()
+            k = a
+            while True:
+                t += rng.exponential(agents / rate)
+                if t >= stop_at:
+                    break
+                time.sleep(max(0.0, t - time.perf_counter()))
+                try:
+                    tickets.put(srv.submit(atts[k % A]))
+                    sent[a] += 1
+                except B.ReloError as e:
+                    if e.status != B.EBUSY:
+                        raise
+                k += agents
+            tickets.put(None)
+
+        def waiter():
+            while True:
+                tk = tickets.get()
+                if tk is None:
+                    tickets.put(None)
+                    return
+                srv.wait(tk)
+
+        t0 = time.perf_counter()
+        th = [threading.Thread(target=agent, args=(a,)) for a in range(agents)]
+        wt = [threading.Thread(target=waiter) for _ in range(8)]
+        for x in th + wt:
+            x.start()
+        for x in th + wt:
+            x.join()
+        wall = time.perf_counter() - t0
+        stt = srv.stats()
+        srv.close()
+        points.append({"agents": agents, "offered_per_s": rate, "attempts_per_s": stt["completed"] / wall,
+                       "completed": stt["completed"], "discarded": stt["discarded"], "batches": stt["batches"],
+                       "mean_batch": stt["mean_batch"], "p50_ms": stt["p50_ms"], "p99_ms": stt["p99_ms"],
+                       "max_ms": stt["max_ms"]})
+    return {"max_batch": SERVE_MAX_BATCH, "max_wait_us": SERVE_MAX_WAIT_US, "slots": SERVE_SLOTS,
+            "workspace_bytes": ws_bytes, "seconds_per_point": args.serve_seconds, "points": points}
 
 
 # Hypothesis search, ALU view: each try is one Philox4x32-10 block (10 rounds of two 32 x 32 -> 64

@@ -46,6 +46,7 @@ typedef int relo_status;
 #define RELO_ETIMEOUT (-4)  /* a bounded device loop gave up */
 #define RELO_EDEVICE (-5)   /* a device-side bounds check failed */
 #define RELO_ENOTFOUND (-6) /* no valid pose hypothesis */
+#define RELO_EBUSY (-7)     /* a serving request was discarded: every request slot is in use */
 
 /* Message for the last failing call on this thread ("" if none). */
 const char* relo_last_error(void);
@@ -411,6 +412,50 @@ relo_status relo_batch_enable_timing(relo_batch* batch, int32_t enable);
 int32_t relo_batch_stage_ms(const relo_batch* batch, float* ms, int32_t capacity);
 /* Name of stage k of relo_batch_stage_ms ("" outside [0, 10)). */
 const char* relo_batch_stage_name(int32_t k);
+
+/* ---------------------------------------------------------------------------------------
+ * Serving: relocalisation attempts submitted one at a time by many agents (threads), run in
+ * batches by a worker thread that owns a stream and a workspace.  The paper attempts one
+ * relocalisation at a time in the background (Sec. 3.3.1, Sec. 4.3.1); here requests are queued
+ * in a fixed pool of slots after the pooled queue of Appendix B.1, with its discard policy: a
+ * request that finds every slot in use (queued, running, or finished but not yet collected) is
+ * not admitted (RELO_EBUSY).  The worker starts a batch when max_batch requests are queued or
+ * the oldest has waited max_wait_us, and takes requests from the front of the queue while the
+ * batch's workspace (relo_batch_workspace_size) fits the server's (workspace_bytes, allocated at
+ * creation: the HBM budget of one batch).  Latency = collection-ready time - submit time.
+ * A request's scenes, forest / regressor and noise image must stay valid until it completes.
+ * ------------------------------------------------------------------------------------- */
+typedef struct relo_server relo_server;
+typedef struct relo_server_params {
+  int32_t max_batch;          /* attempts per batch, >= 1 */
+  int32_t max_wait_us;        /* a partial batch starts once its oldest request waited this long */
+  int32_t slots;              /* request slots (pool size), >= 1 */
+  int32_t pad;
+  uint64_t workspace_bytes;   /* device workspace of one batch (the HBM budget) */
+  relo_ransac_params ransac;  /* for every request (each attempt's n_hyps / seed still apply) */
+} relo_server_params;
+
+typedef struct relo_server_stats {
+  uint64_t completed, discarded, batches;
+  double mean_batch;                     /* requests per batch */
+  double p50_ms, p99_ms, max_ms;         /* latency of the completed requests */
+} relo_server_stats;
+
+/* Allocates the workspace (cudaMalloc on the current device) and starts the worker.
+ * Errors: RELO_EINVAL (params), RELO_ENOMEM, RELO_ECUDA. */
+relo_status relo_server_create(const relo_server_params* params, relo_server** out);
+/* Queues one attempt (copied); *ticket identifies it.  Errors: RELO_EINVAL (bad attempt: it
+ * would be rejected by relo_batch_workspace_size), RELO_EBUSY (discarded, no free slot). */
+relo_status relo_server_submit(relo_server* server, const relo_attempt* attempt, uint64_t* ticket);
+/* Blocks until the request completes, copies its result (result_host; its status carries any
+ * error of the batch it ran in) and latency (nullable), and frees its slot.
+ * Errors: RELO_EINVAL (unknown ticket). */
+relo_status relo_server_wait(relo_server* server, uint64_t ticket, relo_pose_result* result_host,
+                             double* latency_ms);
+/* Counters and latency percentiles since creation. */
+relo_status relo_server_stats_get(const relo_server* server, relo_server_stats* out);
+/* Runs the requests still queued, stops the worker and frees the workspace. */
+void relo_server_destroy(relo_server* server);
 
 #ifdef __cplusplus
 }

@@ -16,9 +16,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librelo.so")
 _LIB = None
 
-OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EDEVICE, ENOTFOUND = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EDEVICE, ENOTFOUND, EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
 STATUS_NAMES = {0: "RELO_OK", -1: "RELO_EINVAL", -2: "RELO_ENOMEM", -3: "RELO_ECUDA", -4: "RELO_ETIMEOUT",
-                -5: "RELO_EDEVICE", -6: "RELO_ENOTFOUND"}
+                -5: "RELO_EDEVICE", -6: "RELO_ENOTFOUND", -7: "RELO_EBUSY"}
 
 c_i32, c_i64, c_u64, c_dbl, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p
 
@@ -64,6 +64,16 @@ class Attempt(ctypes.Structure):
 
 
 RESULT_BYTES = ctypes.sizeof(PoseResult)
+
+
+class ServerParams(ctypes.Structure):
+    _fields_ = [("max_batch", c_i32), ("max_wait_us", c_i32), ("slots", c_i32), ("pad", c_i32),
+                ("workspace_bytes", c_u64), ("ransac", RansacParams)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", c_u64), ("discarded", c_u64), ("batches", c_u64), ("mean_batch", c_dbl),
+                ("p50_ms", c_dbl), ("p99_ms", c_dbl), ("max_ms", c_dbl)]
 
 _SIGS = {
     "relo_last_error": (ctypes.c_char_p, []),
@@ -114,6 +124,11 @@ _SIGS = {
     "relo_batch_enable_timing": (c_i32, [c_vp, c_i32]),
     "relo_batch_stage_ms": (c_i32, [c_vp, ctypes.POINTER(ctypes.c_float), c_i32]),
     "relo_batch_stage_name": (ctypes.c_char_p, [c_i32]),
+    "relo_server_create": (c_i32, [ctypes.POINTER(ServerParams), ctypes.POINTER(c_vp)]),
+    "relo_server_submit": (c_i32, [c_vp, ctypes.POINTER(Attempt), ctypes.POINTER(c_u64)]),
+    "relo_server_wait": (c_i32, [c_vp, c_u64, ctypes.POINTER(PoseResult), ctypes.POINTER(c_dbl)]),
+    "relo_server_stats_get": (c_i32, [c_vp, ctypes.POINTER(ServerStats)]),
+    "relo_server_destroy": (None, [c_vp]),
     "relo_raycast_views_workspace_size": (ctypes.c_size_t, [c_i32]),
     "relo_raycast_views": (c_i32, [c_vp, ctypes.POINTER(Intrinsics), c_vp, c_i32, c_vp, c_vp, c_vp, c_vp,
                                    ctypes.c_size_t, c_vp]),
@@ -364,6 +379,14 @@ def make_attempts(items) -> "ctypes.Array":
     return arr
 
 
+def make_attempts_view(attempts, n):
+    """The first n attempts of a relo_attempt array, as an array of their own."""
+    arr = (Attempt * n)()
+    for k in range(n):
+        arr[k] = attempts[k]
+    return arr
+
+
 def batch_workspace_size(attempts, params) -> int:
     return int(lib().relo_batch_workspace_size(attempts, len(attempts), ctypes.byref(params)))
 
@@ -511,3 +534,42 @@ def regressor_relocalise(reg, depth_dev, rgba_dev, intr, params, workspace_dev, 
     _check(lib().relo_regressor_relocalise(reg.handle, _ptr(depth_dev), _ptr(rgba_dev), ctypes.byref(ci),
                                            ctypes.byref(params), _ptr(workspace_dev), workspace_dev.numel(),
                                            _ptr(result_dev), _stream(stream)))
+
+
+# ------------------------------------------------------------------------------------------------
+# Serving
+# ------------------------------------------------------------------------------------------------
+
+class Server:
+    """Batched serving of single attempts (relo_server_*): submit returns a ticket, wait blocks
+    until its result is ready.  Attempts are relo_attempt structs (make_attempts(...)[k])."""
+
+    def __init__(self, ransac, workspace_bytes, max_batch=64, max_wait_us=2000, slots=256):
+        prm = ServerParams(int(max_batch), int(max_wait_us), int(slots), 0, int(workspace_bytes), ransac)
+        h = c_vp()
+        _check(lib().relo_server_create(ctypes.byref(prm), ctypes.byref(h)))
+        self.handle = h.value
+
+    def submit(self, attempt) -> int:
+        """Ticket of the queued attempt; raises ReloError(EBUSY) when it is discarded."""
+        t = c_u64()
+        _check(lib().relo_server_submit(self.handle, ctypes.byref(attempt), ctypes.byref(t)))
+        return int(t.value)
+
+    def wait(self, ticket):
+        res, lat = PoseResult(), c_dbl()
+        _check(lib().relo_server_wait(self.handle, int(ticket), ctypes.byref(res), ctypes.byref(lat)))
+        return res.to_dict(), float(lat.value)
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().relo_server_stats_get(self.handle, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.relo_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
