@@ -457,6 +457,45 @@ relo_status relo_server_stats_get(const relo_server* server, relo_server_stats* 
 /* Runs the requests still queued, stops the worker and frees the workspace. */
 void relo_server_destroy(relo_server* server);
 
+/* ---------------------------------------------------------------------------------------
+ * Pose graph: the host consumer of relative transform samples (Sec. 3.3.2) and the candidate
+ * score of Sec. 3.3.1.  Scenes are 0 .. n-1; scene 0 is the first agent's, whose global pose is
+ * the identity.  Transforms are row-major 4x4 doubles; aT_b maps scene b's coordinates into
+ * scene a's (for a verified attempt, relo_pose_result.rel_a_b).
+ * Samples of (a, b) and (b, a) share the unordered pair's clusters.  A sample joins the first
+ * cluster holding a sample within 20 degrees and 10 cm of it (Sec. 4.2.4), else opens a new one.
+ * A pair is confident once its largest cluster holds N = 2 samples; the pose graph joins the
+ * confident pairs of scene 0's connected component, each with the dual-quaternion blend
+ * (Kavan et al. 2006, equal weights) of its largest cluster, and Levenberg-Marquardt minimises
+ * the squared components of v(gT_b^-1 gT_a aT_b) over its edges (v: imaginary quaternion part,
+ * w >= 0, then translation).  Host code; no GPU needed.
+ * ------------------------------------------------------------------------------------- */
+typedef struct relo_pose_graph relo_pose_graph;
+/* Errors: RELO_EINVAL (n_scenes outside [1, 4096], null out). */
+relo_status relo_pose_graph_create(int32_t n_scenes, relo_pose_graph** out);
+void relo_pose_graph_destroy(relo_pose_graph* graph);
+/* Adds sample aT_b; *cluster_size (nullable) receives the size of the cluster it joined (>= 2:
+ * the pair has a confident relative transform, a reason to re-optimise).
+ * Errors: RELO_EINVAL (null, scene outside [0, n), a == b). */
+relo_status relo_pose_graph_add_sample(relo_pose_graph* graph, int32_t a, int32_t b, const double aTb[16],
+                                       int32_t* cluster_size);
+/* Builds the pose graph and optimises it: global_poses [n][16] receive gT_s for the scenes in
+ * it (the identity for the others), in_graph [n] flags them; *epsilon (nullable) receives
+ * epsilon(G), the sum over edges of |v(gT_b^-1 gT_a aT_b)|.  Errors: RELO_EINVAL (null). */
+relo_status relo_pose_graph_optimise(relo_pose_graph* graph, double* global_poses, int32_t* in_graph,
+                                     double* epsilon);
+/* Records that a frame of scene b with local pose pose_in_b was tried against scene a. */
+relo_status relo_pose_graph_mark_tried(relo_pose_graph* graph, int32_t a, int32_t b, const double pose_in_b[16]);
+/* Phi of candidate (a, (b, frame)) (Sec. 3.3.1): phi_new (1 if exactly one of a, b has an optimised
+ * global pose after the last relo_pose_graph_optimise) - phi_conf (max(0, largest cluster of the
+ * pair - N)) - phi_homog (5 if a frame within 5 cm and 5 degrees of pose_in_b was tried against a). */
+relo_status relo_pose_graph_score(const relo_pose_graph* graph, int32_t a, int32_t b, const double pose_in_b[16],
+                                  double* score);
+/* Number of clusters of the pair {a, b} (-1 on bad arguments); sizes [capacity] (nullable)
+ * receives their sizes in creation order. */
+int32_t relo_pose_graph_cluster_count(const relo_pose_graph* graph, int32_t a, int32_t b, int32_t* sizes,
+                                      int32_t capacity);
+
 #ifdef __cplusplus
 }
 #endif

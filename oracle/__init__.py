@@ -18,7 +18,8 @@ vectors), block lookup (a dict), raycast (analytic plane / sphere / box-world
 depths), forest descent (hand-computed trees), verification counts (hand
 counts), Kabsch (known transforms, Horn's quaternion method), the energy
 (closed-form single Gaussian), RANSAC (exact recovery on noise-free data,
-exhaustive ranking) and mean shift (Gaussian blobs).
+exhaustive ranking) and mean shift (Gaussian blobs).  The pose graph of Sec. 3.3.2
+(``oracle/posegraph.py``) is pinned by closed-form blends, exact recovery and stationarity.
 """
 from __future__ import annotations
 

@@ -136,6 +136,13 @@ _SIGS = {
     "relo_batch_replay": (c_i32, [c_vp, c_vp]),
     "relo_batch_attempt_images": (c_i32, [c_vp, c_i32, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp),
                                           ctypes.POINTER(c_vp)]),
+    "relo_pose_graph_create": (c_i32, [c_i32, ctypes.POINTER(c_vp)]),
+    "relo_pose_graph_destroy": (None, [c_vp]),
+    "relo_pose_graph_add_sample": (c_i32, [c_vp, c_i32, c_i32, ctypes.POINTER(c_dbl), ctypes.POINTER(c_i32)]),
+    "relo_pose_graph_optimise": (c_i32, [c_vp, ctypes.POINTER(c_dbl), ctypes.POINTER(c_i32), ctypes.POINTER(c_dbl)]),
+    "relo_pose_graph_mark_tried": (c_i32, [c_vp, c_i32, c_i32, ctypes.POINTER(c_dbl)]),
+    "relo_pose_graph_score": (c_i32, [c_vp, c_i32, c_i32, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl)]),
+    "relo_pose_graph_cluster_count": (c_i32, [c_vp, c_i32, c_i32, ctypes.POINTER(c_i32), c_i32]),
 }
 
 STAGES = ["query_raycast", "learned_forward", "learned_hypotheses", "learned_rounds", "learned_verify", "forest_eval",
@@ -569,6 +576,68 @@ class Server:
     def close(self):
         if getattr(self, "handle", None) and _LIB is not None:
             _LIB.relo_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+# Pose graph (host)
+# ------------------------------------------------------------------------------------------------
+
+def _mat16(T):
+    a = np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape(16))
+    return a, a.ctypes.data_as(ctypes.POINTER(c_dbl))
+
+
+class PoseGraph:
+    """Clusters of relative transform samples per pair of scenes, the pose graph of scene 0's
+    component and the candidate score (relo_pose_graph_*).  Transforms are 4x4 arrays; aT_b maps
+    scene b's coordinates into scene a's."""
+
+    def __init__(self, n_scenes):
+        h = c_vp()
+        _check(lib().relo_pose_graph_create(int(n_scenes), ctypes.byref(h)))
+        self.handle = h.value
+        self.n = int(n_scenes)
+
+    def add_sample(self, a, b, aTb) -> int:
+        """Size of the cluster the sample joined."""
+        m, p = _mat16(aTb)
+        size = c_i32()
+        _check(lib().relo_pose_graph_add_sample(self.handle, int(a), int(b), p, ctypes.byref(size)))
+        return int(size.value)
+
+    def optimise(self):
+        """(global poses [n, 4, 4], in-graph flags [n] bool, epsilon)."""
+        poses = np.zeros((self.n, 16), dtype=np.float64)
+        flags = np.zeros(self.n, dtype=np.int32)
+        eps = c_dbl()
+        _check(lib().relo_pose_graph_optimise(self.handle, poses.ctypes.data_as(ctypes.POINTER(c_dbl)),
+                                              flags.ctypes.data_as(ctypes.POINTER(c_i32)), ctypes.byref(eps)))
+        return poses.reshape(self.n, 4, 4), flags.astype(bool), float(eps.value)
+
+    def mark_tried(self, a, b, pose_in_b):
+        m, p = _mat16(pose_in_b)
+        _check(lib().relo_pose_graph_mark_tried(self.handle, int(a), int(b), p))
+
+    def score(self, a, b, pose_in_b) -> float:
+        m, p = _mat16(pose_in_b)
+        out = c_dbl()
+        _check(lib().relo_pose_graph_score(self.handle, int(a), int(b), p, ctypes.byref(out)))
+        return float(out.value)
+
+    def cluster_sizes(self, a, b):
+        n = lib().relo_pose_graph_cluster_count(self.handle, int(a), int(b), None, 0)
+        if n < 0:
+            raise ReloError(EINVAL, "bad scene pair")
+        sizes = (c_i32 * max(n, 1))()
+        lib().relo_pose_graph_cluster_count(self.handle, int(a), int(b), sizes, n)
+        return [int(sizes[k]) for k in range(n)]
+
+    def close(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.relo_pose_graph_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
