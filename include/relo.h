@@ -120,6 +120,22 @@ relo_status relo_raycast_views(const relo_scene* scene, const relo_intrinsics* i
                                int32_t n, const float* noise_dev, uint16_t* depth_dev, uint8_t* rgba_dev,
                                void* workspace_dev, size_t workspace_bytes, relo_stream stream);
 
+/* Global map rendering (Appendix B.2): the n sub-scenes, placed by their global poses
+ * global_poses_host [n][16] (gT_a: scene a -> global, rigid, e.g. from relo_pose_graph_optimise),
+ * seen by one camera with camera -> global pose pose_global_host.  Each scene a is raycast as
+ * relo_raycast_view does (no noise) from its local pose (gT_a)^-1 * pose_global; per pixel the
+ * scene with the smallest depth in whole mm wins (ties: the lower index) and gives the pixel its
+ * depth (depth_dev u16 mm, 0 where no scene is hit) and colour (rgba_dev, nullable); owner_dev
+ * (nullable, int8 [H][W]) receives the winning index or -1.  err_dev (nullable, device int32)
+ * is set to RELO_EDEVICE if a hash walk exceeded its bound.  One launch; the descriptors go
+ * through workspace_dev (256-byte aligned, relo_render_global_workspace_size(n) bytes) as for
+ * relo_raycast_views.  Errors: RELO_EINVAL (null, n outside [1, 64], intrinsics, workspace). */
+size_t relo_render_global_workspace_size(int32_t n_scenes);
+relo_status relo_render_global(const relo_scene* const* scenes, const double* global_poses_host, int32_t n_scenes,
+                               const relo_intrinsics* intr, const double pose_global_host[16], uint16_t* depth_dev,
+                               uint8_t* rgba_dev, int8_t* owner_dev, int32_t* err_dev, void* workspace_dev,
+                               size_t workspace_bytes, relo_stream stream);
+
 /* ---------------------------------------------------------------------------------------
  * Regression forest (the relocaliser of Sec. 3.3 (b), after Cavallari et al.).
  * n_trees complete binary trees of the given depth, stored breadth first (children of node n
@@ -413,6 +429,31 @@ int32_t relo_batch_stage_ms(const relo_batch* batch, float* ms, int32_t capacity
 /* Name of stage k of relo_batch_stage_ms ("" outside [0, 10)). */
 const char* relo_batch_stage_name(int32_t k);
 
+/* Launch schedule of a batch (no counterpart in the paper): how work maps to threads and how
+ * large the grids are.  Every schedule computes the same results bit for bit; only the time
+ * differs.  A new batch starts with the defaults (8, 256, 0, 0, 0). */
+typedef struct relo_schedule {
+  int32_t ray_warp_width;     /* raycasts: each warp covers ray_warp_width x (32 / width) pixels of
+                                 its CTA's 16 x 16 tile; 2, 4, 8 or 16 */
+  int32_t forest_threads;     /* forest evaluation: threads per CTA, 128 or 256 */
+  int32_t forest_tiles;       /* forest evaluation: 0 = a CTA takes consecutive row-major pixels,
+                                 1 = it takes 32 x 8 pixel tiles */
+  int32_t search_ctas_per_sm; /* hypothesis search: persistent CTAs per SM, 0 = as many as fit */
+  int32_t refit_per;          /* round re-fits: survivors per one-warp CTA, 1..32; 0 = enough CTAs
+                                 for twice the SM count */
+} relo_schedule;
+relo_status relo_batch_get_schedule(const relo_batch* batch, relo_schedule* out);
+/* Sets the schedule of later runs and drops a captured graph (capture again).
+ * Errors: RELO_EINVAL (null, a field outside its values). */
+relo_status relo_batch_set_schedule(relo_batch* batch, const relo_schedule* schedule);
+/* Autotuner: runs the batch on its own inputs (its results are overwritten by identical ones)
+ * 1 + repeats times per candidate value of each field in turn, keeping for each field the value
+ * whose runs give the least total time of the stages it affects (stage events, as
+ * relo_batch_stage_ms); leaves the batch with the chosen schedule, written to *chosen
+ * (nullable), and drops a captured graph.  Synchronises the stream.  Errors: RELO_EINVAL (null
+ * batch, repeats outside [1, 100]), RELO_ECUDA. */
+relo_status relo_batch_autotune(relo_batch* batch, int32_t repeats, relo_schedule* chosen, relo_stream stream);
+
 /* ---------------------------------------------------------------------------------------
  * Serving: relocalisation attempts submitted one at a time by many agents (threads), run in
  * batches by a worker thread that owns a stream and a workspace.  The paper attempts one
@@ -491,6 +532,10 @@ relo_status relo_pose_graph_mark_tried(relo_pose_graph* graph, int32_t a, int32_
  * pair - N)) - phi_homog (5 if a frame within 5 cm and 5 degrees of pose_in_b was tried against a). */
 relo_status relo_pose_graph_score(const relo_pose_graph* graph, int32_t a, int32_t b, const double pose_in_b[16],
                                   double* score);
+/* Dual-quaternion blend of cluster c (creation order) of the pair {a, b}, as aT_b (the inverse
+ * of the stored blend when a > b).  Errors: RELO_EINVAL (null, scenes, c outside the clusters). */
+relo_status relo_pose_graph_cluster_blend(const relo_pose_graph* graph, int32_t a, int32_t b, int32_t c,
+                                          double aTb[16]);
 /* Number of clusters of the pair {a, b} (-1 on bad arguments); sizes [capacity] (nullable)
  * receives their sizes in creation order. */
 int32_t relo_pose_graph_cluster_count(const relo_pose_graph* graph, int32_t a, int32_t b, int32_t* sizes,

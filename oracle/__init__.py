@@ -171,6 +171,26 @@ class Scene:
         return depth, rgba
 
 
+def render_global(scenes, global_poses, intr, pose_global, pixels=None):
+    """Global map rendering (Appendix B.2): each sub-scene a is raycast from its local pose
+    (gT_a)^-1 P_g (P_g camera -> global, gT_a scene a -> global); per pixel the scene with the
+    smallest depth wins (whole mm as the depth images hold it; ties: the lower index; no hit:
+    +inf) and gives the pixel its depth and colour.  Returns (depth, rgba, owner, depths) where
+    owner is -1 where no scene is hit and depths [n, ...] holds every scene's own depth image."""
+    P_g = np.asarray(pose_global, dtype=np.float64)
+    imgs = [sc.raycast(intr, np.linalg.inv(np.asarray(g, dtype=np.float64)) @ P_g, pixels=pixels)
+            for sc, g in zip(scenes, global_poses)]
+    depths = np.stack([d for d, _ in imgs])
+    key = np.where(depths > 0, depths.astype(np.int64), np.iinfo(np.int64).max)
+    owner = np.argmin(key, axis=0)                    # first minimum: the lower index wins ties
+    hit = np.take_along_axis(depths, owner[None], 0)[0] > 0
+    depth = np.where(hit, np.take_along_axis(depths, owner[None], 0)[0], 0).astype(np.uint16)
+    cols = np.stack([c for _, c in imgs])
+    rgba = np.take_along_axis(cols, owner[None, ..., None], 0)[0]
+    rgba = np.where(hit[..., None], rgba, 0).astype(np.uint8)
+    return depth, rgba, np.where(hit, owner, -1).astype(np.int8), depths
+
+
 def raycast_touched(scene: Scene, intr, pose, with_colour: bool) -> dict:
     """Distinct data one view's raycast reads: tsdf voxels, colour voxels (query renders only)
     and block keys looked up -- the algorithmic input bytes of that raycast."""

@@ -66,6 +66,14 @@ class Attempt(ctypes.Structure):
 RESULT_BYTES = ctypes.sizeof(PoseResult)
 
 
+class Schedule(ctypes.Structure):
+    _fields_ = [("ray_warp_width", c_i32), ("forest_threads", c_i32), ("forest_tiles", c_i32),
+                ("search_ctas_per_sm", c_i32), ("refit_per", c_i32)]
+
+    def to_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
 class ServerParams(ctypes.Structure):
     _fields_ = [("max_batch", c_i32), ("max_wait_us", c_i32), ("slots", c_i32), ("pad", c_i32),
                 ("workspace_bytes", c_u64), ("ransac", RansacParams)]
@@ -136,6 +144,12 @@ _SIGS = {
     "relo_batch_replay": (c_i32, [c_vp, c_vp]),
     "relo_batch_attempt_images": (c_i32, [c_vp, c_i32, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp),
                                           ctypes.POINTER(c_vp)]),
+    "relo_render_global_workspace_size": (ctypes.c_size_t, [c_i32]),
+    "relo_render_global": (c_i32, [ctypes.POINTER(c_vp), ctypes.POINTER(c_dbl), c_i32, ctypes.POINTER(Intrinsics),
+                                   ctypes.POINTER(c_dbl), c_vp, c_vp, c_vp, c_vp, c_vp, ctypes.c_size_t, c_vp]),
+    "relo_batch_get_schedule": (c_i32, [c_vp, ctypes.POINTER(Schedule)]),
+    "relo_batch_set_schedule": (c_i32, [c_vp, ctypes.POINTER(Schedule)]),
+    "relo_batch_autotune": (c_i32, [c_vp, c_i32, ctypes.POINTER(Schedule), c_vp]),
     "relo_pose_graph_create": (c_i32, [c_i32, ctypes.POINTER(c_vp)]),
     "relo_pose_graph_destroy": (None, [c_vp]),
     "relo_pose_graph_add_sample": (c_i32, [c_vp, c_i32, c_i32, ctypes.POINTER(c_dbl), ctypes.POINTER(c_i32)]),
@@ -143,6 +157,7 @@ _SIGS = {
     "relo_pose_graph_mark_tried": (c_i32, [c_vp, c_i32, c_i32, ctypes.POINTER(c_dbl)]),
     "relo_pose_graph_score": (c_i32, [c_vp, c_i32, c_i32, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl)]),
     "relo_pose_graph_cluster_count": (c_i32, [c_vp, c_i32, c_i32, ctypes.POINTER(c_i32), c_i32]),
+    "relo_pose_graph_cluster_blend": (c_i32, [c_vp, c_i32, c_i32, c_i32, ctypes.POINTER(c_dbl)]),
 }
 
 STAGES = ["query_raycast", "learned_forward", "learned_hypotheses", "learned_rounds", "learned_verify", "forest_eval",
@@ -288,6 +303,28 @@ def raycast_views(scene, intr, poses, depth_dev, rgba_dev=None, noise_dev=None, 
     _check(lib().relo_raycast_views(scene.handle, ctypes.byref(ci), pp, n, _ptr(noise_dev), _ptr(depth_dev),
                                     _ptr(rgba_dev), _ptr(workspace_dev),
                                     0 if workspace_dev is None else workspace_dev.numel(), _stream(stream)))
+
+
+def render_global_workspace_size(n) -> int:
+    return int(lib().relo_render_global_workspace_size(int(n)))
+
+
+def render_global(scenes, global_poses, intr, pose_global, depth_dev, rgba_dev=None, owner_dev=None, err_dev=None,
+                  workspace_dev=None, stream=None):
+    """Global map rendering: the scenes placed by global_poses [n][4][4] (gT_a), seen from the
+    camera -> global pose pose_global; per pixel the nearest scene wins (owner_dev: its index)."""
+    n = len(scenes)
+    hs = (c_vp * n)(*[sc.handle for sc in scenes])
+    g = np.ascontiguousarray(np.asarray(global_poses, dtype=np.float64).reshape(n, 16))
+    pg = np.ascontiguousarray(np.asarray(pose_global, dtype=np.float64).reshape(16))
+    ci = intrinsics(intr)
+    if workspace_dev is None:
+        import torch
+        workspace_dev = torch.empty(render_global_workspace_size(n), dtype=torch.uint8, device=depth_dev.device)
+    _check(lib().relo_render_global(hs, g.ctypes.data_as(ctypes.POINTER(c_dbl)), n, ctypes.byref(ci),
+                                    pg.ctypes.data_as(ctypes.POINTER(c_dbl)), _ptr(depth_dev), _ptr(rgba_dev),
+                                    _ptr(owner_dev), _ptr(err_dev), _ptr(workspace_dev), workspace_dev.numel(),
+                                    _stream(stream)))
 
 
 def forest_eval(forest, depth_dev, rgba_dev, leaves_dev, stream=None):
@@ -457,6 +494,22 @@ class Batch:
         buf = (ctypes.c_float * len(STAGES))()
         n = lib().relo_batch_stage_ms(self.handle, buf, len(STAGES))
         return {lib().relo_batch_stage_name(k).decode(): float(buf[k]) for k in range(n)}
+
+    def schedule(self) -> dict:
+        sc = Schedule()
+        _check(lib().relo_batch_get_schedule(self.handle, ctypes.byref(sc)))
+        return sc.to_dict()
+
+    def set_schedule(self, **fields):
+        """Change schedule fields (relo_schedule); drops a captured graph."""
+        sc = Schedule(**{**self.schedule(), **fields})
+        _check(lib().relo_batch_set_schedule(self.handle, ctypes.byref(sc)))
+
+    def autotune(self, repeats=2, stream=None) -> dict:
+        """Pick the fastest schedule on this batch's own inputs (relo_batch_autotune)."""
+        sc = Schedule()
+        _check(lib().relo_batch_autotune(self.handle, int(repeats), ctypes.byref(sc), _stream(stream)))
+        return sc.to_dict()
 
     def __del__(self):
         if getattr(self, "handle", None) and _LIB is not None:
@@ -634,6 +687,13 @@ class PoseGraph:
         sizes = (c_i32 * max(n, 1))()
         lib().relo_pose_graph_cluster_count(self.handle, int(a), int(b), sizes, n)
         return [int(sizes[k]) for k in range(n)]
+
+    def cluster_blend(self, a, b, c):
+        """Blend of cluster c of the pair, as aT_b (4x4)."""
+        out = np.zeros(16, dtype=np.float64)
+        _check(lib().relo_pose_graph_cluster_blend(self.handle, int(a), int(b), int(c),
+                                                   out.ctypes.data_as(ctypes.POINTER(c_dbl))))
+        return out.reshape(4, 4)
 
     def close(self):
         if getattr(self, "handle", None) and _LIB is not None:

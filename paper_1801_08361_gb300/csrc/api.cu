@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -174,11 +175,11 @@ cudaError_t record(cudaEvent_t ev, cudaStream_t s, bool external) {
 
 // ev_hyp / ev_rounds (nullable) are recorded after the hypotheses and after the rounds.
 relo_status run_pass(const RansacPass& p, cudaStream_t s, int* launches, cudaEvent_t ev_hyp, cudaEvent_t ev_rounds,
-                     bool external = false) {
+                     bool external = false, const Schedule& sched = Schedule()) {
   int L = 0;
   if (p.n > 0) {
     RELO_CUDA(launch_compact(p.d_jobs, p.n, p.chunks, s));
-    RELO_CUDA(launch_hypotheses(p.d_jobs, p.n, p.hyps, p.d_counter, s));
+    RELO_CUDA(launch_hypotheses(p.d_jobs, p.n, p.hyps, p.d_counter, s, sched));
     L += 4;
   }
   RELO_CUDA(record(ev_hyp, s, external));
@@ -186,7 +187,7 @@ relo_status run_pass(const RansacPass& p, cudaStream_t s, int* launches, cudaEve
     if (p.tot_alive[r] == 0) continue;
     RELO_CUDA(launch_round(p.d_jobs, p.n, r, p.d_alive_prefix + (size_t)r * (p.n + 1), p.tot_alive[r],
                            p.max_alive[r], p.d_surv_prefix + (size_t)r * (p.n + 1), p.tot_surv[r], p.max_surv[r],
-                           p.B, s));
+                           p.B, s, sched));
     L += 5;
   }
   if (p.n > 0) {
@@ -421,6 +422,8 @@ relo_status relo_raycast_view(const relo_scene* scene, const relo_intrinsics* in
   return RELO_OK;
 }
 
+constexpr int kMaxGlobalScenes = 64;
+
 size_t relo_raycast_views_workspace_size(int32_t n) { return n < 1 ? 0 : (size_t)n * sizeof(RayJob); }
 
 relo_status relo_raycast_views(const relo_scene* scene, const relo_intrinsics* intr, const double* poses, int32_t n,
@@ -446,6 +449,45 @@ relo_status relo_raycast_views(const relo_scene* scene, const relo_intrinsics* i
   RELO_CUDA(cudaMemcpyAsync(ws, jobs.data(), n * sizeof(RayJob), cudaMemcpyHostToDevice, s));
   // a copy from pageable memory returns once the host buffer has been staged, so jobs may go
   RELO_CUDA(launch_raycast((const RayJob*)ws, n, nullptr, n * tiles, rgba != nullptr, false, s));
+  return RELO_OK;
+}
+
+size_t relo_render_global_workspace_size(int32_t n_scenes) {
+  return (n_scenes < 1 || n_scenes > kMaxGlobalScenes) ? 0 : (size_t)n_scenes * sizeof(RayJob) + 256;
+}
+
+relo_status relo_render_global(const relo_scene* const* scenes, const double* global_poses, int32_t n_scenes,
+                               const relo_intrinsics* intr, const double* pose_global, uint16_t* depth,
+                               uint8_t* rgba, int8_t* owner, int32_t* err_dev, void* ws, size_t ws_bytes,
+                               relo_stream stream) {
+  if (!scenes || !global_poses || !pose_global || !depth) return fail(RELO_EINVAL, "null argument");
+  if (n_scenes < 1 || n_scenes > kMaxGlobalScenes) return fail(RELO_EINVAL, "n_scenes outside [1, 64]");
+  relo_status st = check_intr(intr);
+  if (st) return st;
+  if (!ws || ((uintptr_t)ws & 255) != 0 || ws_bytes < relo_render_global_workspace_size(n_scenes))
+    return fail(RELO_EINVAL, "workspace missing, misaligned or too small");
+  std::vector<RayJob> jobs(n_scenes);
+  for (int a = 0; a < n_scenes; ++a) {
+    if (!scenes[a]) return fail(RELO_EINVAL, "null scene");
+    // local camera -> scene-a pose: (gT_a)^-1 P_g, with gT_a rigid (scene a -> global)
+    const double* g = global_poses + 16 * (size_t)a;
+    double P[16] = {0};
+    for (int r = 0; r < 3; ++r) {
+      for (int c = 0; c < 4; ++c) {
+        double acc = 0.0;
+        for (int k = 0; k < 3; ++k) acc += g[4 * k + r] * pose_global[4 * k + c];  // R_g^T column r
+        if (c == 3)
+          for (int k = 0; k < 3; ++k) acc -= g[4 * k + r] * g[4 * k + 3];
+        P[4 * r + c] = acc;
+      }
+    }
+    P[15] = 1.0;
+    jobs[a] = make_ray_job(scenes[a]->view, *intr, P);
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  RELO_CUDA(cudaMemcpyAsync(ws, jobs.data(), n_scenes * sizeof(RayJob), cudaMemcpyHostToDevice, s));
+  RELO_CUDA(launch_render_global((const RayJob*)ws, n_scenes, intr->width, intr->height, depth, (uint32_t*)rgba,
+                                 owner, err_dev, s));
   return RELO_OK;
 }
 
@@ -1381,6 +1423,7 @@ struct relo_batch {
   CellForestArgs cells{};
   bool timing = false;
   cudaEvent_t ev[kStages + 1] = {};
+  Schedule sched;  // launch schedule (relo_batch_set_schedule / relo_batch_autotune)
   // per attempt: its query images and forest leaves inside the workspace (for inspection)
   std::vector<uint16_t*> a_depth, a_leaves;
   std::vector<uint32_t*> a_rgba;
@@ -1602,7 +1645,7 @@ void layout_batch(const relo_attempt* at, int n, const relo_ransac_params& p, ch
       f.H = H;
       f.pixel_begin = fpix;
       f.skip = skip;
-      fpix += ((int64_t)n_pix + 255) / 256 * 256;  // a forest CTA never spans two jobs
+      fpix += forest_slots(W, H);  // a forest CTA never spans two jobs, in any schedule
       RansacJob& r = h.ransac_F[j];
       fill_ransac_job(r, a.forest_a->view, depth, leaves, a.intr, p, K, a.seed);
       carve_ransac(c, r, W, H, K, p.batch, r.n_rounds, T);
@@ -1669,7 +1712,7 @@ relo_status issue_batch(relo_batch* b, relo_pose_result* results, cudaStream_t s
   RELO_CUDA(cudaMemsetAsync(b->d_errs, 0, (b->nL + b->nF + 1) * sizeof(int32_t), s));
   RELO_CUDA(launch_init_results(b->d_res_F, b->n, s));
   RELO_CUDA(mark(b, 0, s, capturing));
-  RELO_CUDA(launch_raycast(b->d_query, b->n, nullptr, b->query_tiles, true, false, s));
+  RELO_CUDA(launch_raycast(b->d_query, b->n, nullptr, b->query_tiles, true, false, s, b->sched));
   L += 2;
   RELO_CUDA(mark(b, 1, s, capturing));
   // pass L: learned attempts
@@ -1681,24 +1724,24 @@ relo_status issue_batch(relo_batch* b, relo_pose_result* results, cudaStream_t s
   }
   RELO_CUDA(mark(b, 2, s, capturing));
   const bool ev = b->timing;
-  relo_status st = run_pass(b->passL, s, &L, ev ? b->ev[3] : nullptr, ev ? b->ev[4] : nullptr, capturing);
+  relo_status st = run_pass(b->passL, s, &L, ev ? b->ev[3] : nullptr, ev ? b->ev[4] : nullptr, capturing, b->sched);
   if (st) return st;
   if (b->nL > 0) {
-    RELO_CUDA(launch_raycast(b->d_verify_L, b->nL, nullptr, b->verify_L_tiles, false, true, s));
+    RELO_CUDA(launch_raycast(b->d_verify_L, b->nL, nullptr, b->verify_L_tiles, false, true, s, b->sched));
     RELO_CUDA(launch_verify_decide(b->passL.d_jobs, b->nL, s));
     L += 2;
   }
   RELO_CUDA(mark(b, 5, s, capturing));
   // pass F: forest attempts and fallbacks (skipped on the device where the learned pose verified)
   if (b->nF > 0) {
-    RELO_CUDA(launch_forest(b->d_forest, b->nF, nullptr, b->forest_pixels, s, b->max_trees));
+    RELO_CUDA(launch_forest(b->d_forest, b->nF, nullptr, b->forest_pixels, s, b->max_trees, b->sched));
     L += 1;
   }
   RELO_CUDA(mark(b, 6, s, capturing));
-  st = run_pass(b->passF, s, &L, ev ? b->ev[7] : nullptr, ev ? b->ev[8] : nullptr, capturing);
+  st = run_pass(b->passF, s, &L, ev ? b->ev[7] : nullptr, ev ? b->ev[8] : nullptr, capturing, b->sched);
   if (st) return st;
   if (b->nF > 0) {
-    RELO_CUDA(launch_raycast(b->d_verify_F, b->nF, nullptr, b->verify_F_tiles, false, true, s));
+    RELO_CUDA(launch_raycast(b->d_verify_F, b->nF, nullptr, b->verify_F_tiles, false, true, s, b->sched));
     RELO_CUDA(launch_verify_decide(b->passF.d_jobs, b->nF, s));
     L += 2;
   }
@@ -1835,6 +1878,100 @@ int32_t relo_batch_stage_ms(const relo_batch* b, float* ms, int32_t capacity) {
 }
 
 const char* relo_batch_stage_name(int32_t k) { return (k >= 0 && k < kStages) ? kStageNames[k] : ""; }
+
+// ---- launch schedules and the autotuner ------------------------------------------------------
+
+relo_status relo_batch_get_schedule(const relo_batch* b, relo_schedule* out) {
+  if (!b || !out) return fail(RELO_EINVAL, "null argument");
+  out->ray_warp_width = 1 << b->sched.ray_warp_log2w;
+  out->forest_threads = b->sched.forest_threads;
+  out->forest_tiles = b->sched.forest_tiles;
+  out->search_ctas_per_sm = b->sched.search_ctas_per_sm;
+  out->refit_per = b->sched.refit_per;
+  return RELO_OK;
+}
+
+relo_status relo_batch_set_schedule(relo_batch* b, const relo_schedule* in) {
+  if (!b || !in) return fail(RELO_EINVAL, "null argument");
+  Schedule s;
+  const int w = in->ray_warp_width;
+  if (w != 2 && w != 4 && w != 8 && w != 16) return fail(RELO_EINVAL, "ray_warp_width must be 2, 4, 8 or 16");
+  s.ray_warp_log2w = w == 2 ? 1 : w == 4 ? 2 : w == 8 ? 3 : 4;
+  if (in->forest_threads != 128 && in->forest_threads != 256) return fail(RELO_EINVAL, "forest_threads must be 128 or 256");
+  if (in->forest_tiles != 0 && in->forest_tiles != 1) return fail(RELO_EINVAL, "forest_tiles must be 0 or 1");
+  if (in->search_ctas_per_sm < 0 || in->search_ctas_per_sm > 64) return fail(RELO_EINVAL, "search_ctas_per_sm outside [0, 64]");
+  if (in->refit_per < 0 || in->refit_per > 32) return fail(RELO_EINVAL, "refit_per outside [0, 32]");
+  s.forest_threads = in->forest_threads;
+  s.forest_tiles = in->forest_tiles;
+  s.search_ctas_per_sm = in->search_ctas_per_sm;
+  s.refit_per = in->refit_per;
+  b->sched = s;
+  if (b->graph) {  // the captured launches used the old schedule
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return RELO_OK;
+}
+
+// Coordinate descent: each knob in turn takes the candidate whose runs give the smallest total
+// time of the stages it affects (the others held at their best so far).  Every candidate
+// computes the same results, so the batch may be tuned on its real inputs.
+relo_status relo_batch_autotune(relo_batch* b, int32_t repeats, relo_schedule* chosen, relo_stream stream) {
+  if (!b || repeats < 1 || repeats > 100) return fail(RELO_EINVAL, "need a batch and repeats in [1, 100]");
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool had_timing = b->timing;
+  relo_status st = relo_batch_enable_timing(b, 1);
+  if (st) return st;
+  struct Knob {
+    int Schedule::*field;
+    std::vector<int> values;
+    std::vector<int> stages;  // indices into kStageNames whose times the knob changes
+  };
+  const std::vector<Knob> knobs = {
+      {&Schedule::ray_warp_log2w, {3, 4, 2, 1}, {0, 4, 8}},
+      {&Schedule::forest_threads, {256, 128}, {5}},
+      {&Schedule::forest_tiles, {0, 1}, {5}},
+      {&Schedule::search_ctas_per_sm, {0, 1, 2, 3}, {2, 6}},
+      {&Schedule::refit_per, {0, 1, 4, 16}, {3, 7}},
+  };
+  Schedule best = b->sched;
+  for (const Knob& k : knobs) {
+    float best_ms = FLT_MAX;
+    int best_v = best.*k.field;
+    for (int v : k.values) {
+      b->sched = best;
+      b->sched.*k.field = v;
+      float total = 0.f;
+      for (int r = 0; r <= repeats && st == RELO_OK; ++r) {  // run 0 warms up
+        st = issue_batch(b, nullptr, s, false);
+        if (st == RELO_OK) {
+          cudaError_t e = cudaStreamSynchronize(s);
+          if (e != cudaSuccess) st = cuda_fail(e, "autotune run");
+        }
+        if (st == RELO_OK && r > 0) {
+          float ms[kStages];
+          if (relo_batch_stage_ms(b, ms, kStages) != kStages) st = fail(RELO_ECUDA, "autotune stage times");
+          for (int q : k.stages) total += ms[q];
+        }
+      }
+      if (st) break;
+      if (total < best_ms) {
+        best_ms = total;
+        best_v = v;
+      }
+    }
+    if (st) break;
+    best.*k.field = best_v;
+  }
+  b->sched = best;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  if (!had_timing) b->timing = false;
+  if (st) return st;
+  return chosen ? relo_batch_get_schedule(b, chosen) : RELO_OK;
+}
 
 relo_status relo_relocalise_batch(const relo_attempt* at, int32_t n, const relo_ransac_params* p, void* ws,
                                   size_t ws_bytes, relo_pose_result* results_host, relo_stream stream) {

@@ -96,10 +96,12 @@ __device__ __forceinline__ void descend(const ForestJob& job, int u, int v, cons
 #define RELO_FOREST_MIN_BLOCKS 8
 #endif
 
-// One thread per pixel.
+// One thread per pixel.  tiles == 0: a job's slot k is its pixel k (row-major); tiles == 1: its
+// slots run over 32 x 8 pixel tiles, 256 slots each, tiles row-major (neighbouring threads
+// probe neighbouring pixels in two dimensions).
 template <int MT>
 __global__ void __launch_bounds__(256, RELO_FOREST_MIN_BLOCKS)
-    forest_kernel(const ForestJob* __restrict__ jobs, int n_jobs, const ForestJob single) {
+    forest_kernel(const ForestJob* __restrict__ jobs, int n_jobs, const ForestJob single, int tiles) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   // jobs start on multiples of the CTA size, so the CTA's first pixel names its job; the job is
   // staged in shared memory (its fields are read at every node visit)
@@ -121,11 +123,22 @@ __global__ void __launch_bounds__(256, RELO_FOREST_MIN_BLOCKS)
   __syncthreads();
   const ForestJob& job = sj;
   if (job_skipped(job.skip)) return;
-  const int64_t pix = gid - job.pixel_begin;
+  const int64_t slot = gid - job.pixel_begin;
   const int64_t n_pix = (int64_t)job.W * job.H;
-  if (pix < 0 || pix >= n_pix) return;
   const int W = job.W, H = job.H;
-  const int u = (int)(pix % W), v = (int)(pix / W);
+  int u, v;
+  if (tiles) {
+    const int64_t t = slot >> 8;
+    const int i = (int)(slot & 255), tx = (W + 31) >> 5;
+    u = (int)(t % tx) * 32 + (i & 31);
+    v = (int)(t / tx) * 8 + (i >> 5);
+    if (slot < 0 || u >= W || v >= H) return;
+  } else {
+    if (slot < 0 || slot >= n_pix) return;
+    u = (int)(slot % W);
+    v = (int)(slot / W);
+  }
+  const int64_t pix = (int64_t)v * W + u;
   const ForestView& f = job.forest;
   const int T = f.T;
   const int d = __ldg(&job.depth[pix]);
@@ -151,15 +164,19 @@ __global__ void __launch_bounds__(256, RELO_FOREST_MIN_BLOCKS)
 }
 
 cudaError_t launch_forest(const ForestJob* jobs_dev, int n_jobs, const ForestJob* single, int64_t total_pixels,
-                          cudaStream_t s, int max_trees) {
+                          cudaStream_t s, int max_trees, const Schedule& sched) {
   if (total_pixels <= 0) return cudaSuccess;
+  const int threads = sched.forest_threads;
+  if ((threads != 128 && threads != 256) || (sched.forest_tiles != 0 && sched.forest_tiles != 1))
+    return cudaErrorInvalidValue;
   ForestJob one{};
   if (single) one = *single;
-  // total_pixels counts each job's pixels rounded up to a multiple of 256 (pixel_begin)
-  const unsigned grid = (unsigned)((total_pixels + 255) / 256);
-  if (max_trees <= 4) forest_kernel<4><<<grid, 256, 0, s>>>(jobs_dev, n_jobs, one);
-  else if (max_trees <= 8) forest_kernel<8><<<grid, 256, 0, s>>>(jobs_dev, n_jobs, one);
-  else forest_kernel<kMaxTrees><<<grid, 256, 0, s>>>(jobs_dev, n_jobs, one);
+  // total_pixels counts each job's slots, a multiple of 256 (pixel_begin), so no CTA spans two jobs
+  const unsigned grid = (unsigned)((total_pixels + threads - 1) / threads);
+  const int tiles = sched.forest_tiles;
+  if (max_trees <= 4) forest_kernel<4><<<grid, threads, 0, s>>>(jobs_dev, n_jobs, one, tiles);
+  else if (max_trees <= 8) forest_kernel<8><<<grid, threads, 0, s>>>(jobs_dev, n_jobs, one, tiles);
+  else forest_kernel<kMaxTrees><<<grid, threads, 0, s>>>(jobs_dev, n_jobs, one, tiles);
   return cudaGetLastError();
 }
 

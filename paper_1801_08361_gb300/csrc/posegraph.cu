@@ -474,6 +474,16 @@ relo_status relo_pose_graph_score(const relo_pose_graph* g, int32_t a, int32_t b
   return RELO_OK;
 }
 
+relo_status relo_pose_graph_cluster_blend(const relo_pose_graph* g, int32_t a, int32_t b, int32_t c,
+                                          double aTb[16]) {
+  if (!g || !aTb || a < 0 || b < 0 || a >= g->n || b >= g->n || a == b) return RELO_EINVAL;
+  const auto& cl = g->clusters[g->pair_index(std::min(a, b), std::max(a, b))];
+  if (c < 0 || c >= (int32_t)cl.size()) return RELO_EINVAL;
+  const Rigid T = blend(cl[c]);
+  to_mat(a < b ? T : inverse(T), aTb);
+  return RELO_OK;
+}
+
 int32_t relo_pose_graph_cluster_count(const relo_pose_graph* g, int32_t a, int32_t b, int32_t* sizes,
                                       int32_t capacity) {
   if (!g || a < 0 || b < 0 || a >= g->n || b >= g->n || a == b) return -1;

@@ -453,20 +453,26 @@ __global__ void __launch_bounds__(128) fit_kernel(const RansacJob* __restrict__ 
   job.inliers[h] = 0;
 }
 
-cudaError_t launch_hypotheses(const RansacJob* jobs, int n_jobs, int total_hyps, int32_t* counter, cudaStream_t s) {
+cudaError_t launch_hypotheses(const RansacJob* jobs, int n_jobs, int total_hyps, int32_t* counter, cudaStream_t s,
+                              const Schedule& sched) {
   if (total_hyps <= 0) return cudaSuccess;
-  static int slots = 0;  // resident warps-worth of CTAs on this GPU (first call)
-  if (slots == 0) {
-    int dev = 0, sms = 0, per_sm = 0;
+  static int sms = 0, per_sm = 0;  // SMs and resident search CTAs per SM on this GPU (first call)
+  if (sms == 0) {
+    int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_kernel, kSearchWarps * 32, 0);
-    if (e != cudaSuccess) return e;
-    slots = std::max(1, sms * per_sm);
+    if (e != cudaSuccess) {
+      sms = 0;
+      return e;
+    }
+    per_sm = std::max(1, per_sm);
   }
+  if (sched.search_ctas_per_sm < 0) return cudaErrorInvalidValue;
+  const int ctas = sched.search_ctas_per_sm == 0 ? per_sm : std::min(per_sm, sched.search_ctas_per_sm);
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
   if (e != cudaSuccess) return e;
-  const int grid = std::min(slots, (total_hyps + kSearchWarps - 1) / kSearchWarps);
+  const int grid = std::min(sms * ctas, (total_hyps + kSearchWarps - 1) / kSearchWarps);
   search_kernel<<<grid, kSearchWarps * 32, 0, s>>>(jobs, n_jobs, total_hyps, counter);
   fit_kernel<<<(total_hyps + 127) / 128, 128, 0, s>>>(jobs, n_jobs, total_hyps);
   return cudaGetLastError();
@@ -801,8 +807,9 @@ __global__ void __launch_bounds__(32) refit_kernel(const RansacJob* __restrict__
 
 cudaError_t launch_round(const RansacJob* jobs, int n_jobs, int round, const int32_t* alive_prefix_dev,
                          int total_alive, int max_alive, const int32_t* surv_prefix_dev, int total_surv, int max_surv,
-                         int B, cudaStream_t s) {
+                         int B, cudaStream_t s, const Schedule& sched) {
   if (total_alive <= 0) return cudaSuccess;
+  if (sched.refit_per < 0 || sched.refit_per > 32) return cudaErrorInvalidValue;
   draw_kernel<<<n_jobs, 256, 0, s>>>(jobs, alive_prefix_dev, round);
   energy_kernel<<<dim3((max_alive + 31) / 32, n_jobs), kRoundWarps * 32, 0, s>>>(jobs, alive_prefix_dev, round);
   // the largest alive set (4096) bounds the shared memory of the sort
@@ -817,7 +824,8 @@ cudaError_t launch_round(const RansacJob* jobs, int n_jobs, int round, const int
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
   }
-  const int per = std::max(1, std::min(32, (total_surv + 2 * n_sms - 1) / (2 * n_sms)));
+  const int per = sched.refit_per > 0 ? sched.refit_per
+                                     : std::max(1, std::min(32, (total_surv + 2 * n_sms - 1) / (2 * n_sms)));
   refit_kernel<<<(unsigned)((total_surv + per - 1) / per), 32, 0, s>>>(jobs, n_jobs, surv_prefix_dev, total_surv,
                                                                        round, per);
   return cudaGetLastError();

@@ -354,13 +354,33 @@ struct Carver {
 // ---------------------------------------------------------------------------------------------
 // Launchers (defined in the .cu files)
 // ---------------------------------------------------------------------------------------------
+// Launch schedule of a batch's kernels (relo_schedule): work-to-thread mappings and grid sizes
+// only, so every schedule computes the same results.
+struct Schedule {
+  int ray_warp_log2w = 3;    // raycast: each warp covers a (1 << w) x (32 >> w) footprint of its 16 x 16 tile
+  int forest_threads = 256;  // forest: CTA size (128 or 256)
+  int forest_tiles = 0;      // forest: 0 = each CTA takes consecutive pixels, 1 = 32 x 8 pixel tiles
+  int search_ctas_per_sm = 0;  // hypothesis search: persistent CTAs per SM (0: occupancy maximum)
+  int refit_per = 0;         // re-fit: survivors per one-warp CTA (0: spread over twice the SM count)
+};
+// Forest slots a job of W x H pixels takes (a multiple of 256 that also holds its 32 x 8 tiles).
+inline int64_t forest_slots(int W, int H) {
+  const int64_t rows = ((int64_t)W * H + 255) / 256 * 256;
+  const int64_t tiles = (int64_t)((W + 31) / 32) * ((H + 7) / 8) * 256;
+  return rows > tiles ? rows : tiles;
+}
+
 // jobs_dev == nullptr: the single job is passed by value.
 cudaError_t launch_raycast(const RayJob* jobs_dev, int n_jobs, const RayJob* single, int total_tiles,
-                           bool with_colour, bool compare, cudaStream_t s);
-// max_trees: the largest tree count among the jobs (selects the kernel's unrolled width)
+                           bool with_colour, bool compare, cudaStream_t s, const Schedule& sched = Schedule());
+// max_trees: the largest tree count among the jobs (selects the kernel's unrolled width).  With
+// sched.forest_tiles, each job must own forest_slots(W, H) slots from its pixel_begin.
 cudaError_t launch_forest(const ForestJob* jobs_dev, int n_jobs, const ForestJob* single, int64_t total_pixels,
-                          cudaStream_t s, int max_trees);
+                          cudaStream_t s, int max_trees, const Schedule& sched = Schedule());
 int ray_tiles(int W, int H);
+// Global map rendering over n scene jobs sharing one image size (owner, rgba, err_flag nullable).
+cudaError_t launch_render_global(const RayJob* jobs_dev, int n, int W, int H, uint16_t* depth, uint32_t* rgba,
+                                 int8_t* owner, int32_t* err_flag, cudaStream_t s);
 cudaError_t launch_verify_decide(const RansacJob* jobs, int n_jobs, cudaStream_t s);
 cudaError_t launch_verify_decide_one(relo_pose_result* res, uint64_t omega, cudaStream_t s);
 // Learned batches: mark fallback results not run, then pick each attempt's final result.
@@ -374,11 +394,12 @@ cudaError_t launch_scene_lookup(SceneView sv, const int32_t* keys, int64_t n, in
 inline int table_words(int T) { return (3 + T + 7) / 8; }
 cudaError_t launch_compact(const RansacJob* jobs, int n_jobs, int total_chunks, cudaStream_t s);
 // counter_dev: one int of device scratch the search's warps take hypotheses from (zeroed here)
-cudaError_t launch_hypotheses(const RansacJob* jobs, int n_jobs, int total_hyps, int32_t* counter_dev, cudaStream_t s);
+cudaError_t launch_hypotheses(const RansacJob* jobs, int n_jobs, int total_hyps, int32_t* counter_dev, cudaStream_t s,
+                              const Schedule& sched = Schedule());
 // round r: prefix[n_jobs + 1] = flattened alive-hypothesis offsets of the jobs still running
 cudaError_t launch_round(const RansacJob* jobs, int n_jobs, int round, const int32_t* alive_prefix_dev,
                          int total_alive, int max_alive, const int32_t* surv_prefix_dev, int total_surv, int max_surv,
-                         int B, cudaStream_t s);
+                         int B, cudaStream_t s, const Schedule& sched = Schedule());
 cudaError_t launch_finalise(const RansacJob* jobs, int n_jobs, cudaStream_t s);
 
 

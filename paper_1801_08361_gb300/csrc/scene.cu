@@ -198,7 +198,7 @@ constexpr int kTile = 16;
 
 template <bool kColour, bool kCompare>
 __global__ void __launch_bounds__(kTile* kTile, kColour ? RELO_RAYCAST_MIN_BLOCKS - 1 : RELO_RAYCAST_MIN_BLOCKS)
-    raycast_kernel(const RayJob* __restrict__ jobs, int n_jobs, const RayJob single) {
+    raycast_kernel(const RayJob* __restrict__ jobs, int n_jobs, const RayJob single, int warp_log2w) {
   // locate the job owning this tile (jobs are few; binary search on tile_begin)
   int lo = 0, hi = n_jobs - 1;
   while (jobs && lo < hi) {
@@ -219,10 +219,12 @@ __global__ void __launch_bounds__(kTile* kTile, kColour ? RELO_RAYCAST_MIN_BLOCK
   const RayJob& job = sj;
   const int tiles_x = (job.W + kTile - 1) / kTile;
   const int tile = (int)blockIdx.x - job.tile_begin;
-  // each warp covers an 8 x 4 footprint of the 16 x 16 tile (neighbouring rays march alike)
+  // each warp covers a fw x (32 / fw) footprint of the 16 x 16 tile, fw = 1 << warp_log2w in
+  // {2, 4, 8, 16} (neighbouring rays march alike); the warps tile it row by row
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int u = (tile % tiles_x) * kTile + (warp & 1) * 8 + (lane & 7);
-  const int v = (tile / tiles_x) * kTile + (warp >> 1) * 4 + (lane >> 3);
+  const int fw = 1 << warp_log2w, fh = 32 >> warp_log2w, per_row = kTile >> warp_log2w;
+  const int u = (tile % tiles_x) * kTile + (warp % per_row) * fw + (lane & (fw - 1));
+  const int v = (tile / tiles_x) * kTile + (warp / per_row) * fh + (lane >> warp_log2w);
   const bool active = u < job.W && v < job.H && (job.status_dev == nullptr || *job.status_dev == RELO_OK);
 
   int err = 0;
@@ -297,14 +299,85 @@ __global__ void __launch_bounds__(kTile* kTile, kColour ? RELO_RAYCAST_MIN_BLOCK
 }
 
 cudaError_t launch_raycast(const RayJob* jobs_dev, int n_jobs, const RayJob* single, int total_tiles,
-                           bool with_colour, bool compare, cudaStream_t s) {
+                           bool with_colour, bool compare, cudaStream_t s, const Schedule& sched) {
   if (total_tiles <= 0) return cudaSuccess;
+  if (sched.ray_warp_log2w < 1 || sched.ray_warp_log2w > 4) return cudaErrorInvalidValue;
   const dim3 grid(total_tiles), block(kTile * kTile);
   RayJob one{};
   if (single) one = *single;
-  if (compare) raycast_kernel<false, true><<<grid, block, 0, s>>>(jobs_dev, n_jobs, one);
-  else if (with_colour) raycast_kernel<true, false><<<grid, block, 0, s>>>(jobs_dev, n_jobs, one);
-  else raycast_kernel<false, false><<<grid, block, 0, s>>>(jobs_dev, n_jobs, one);
+  const int w = sched.ray_warp_log2w;
+  if (compare) raycast_kernel<false, true><<<grid, block, 0, s>>>(jobs_dev, n_jobs, one, w);
+  else if (with_colour) raycast_kernel<true, false><<<grid, block, 0, s>>>(jobs_dev, n_jobs, one, w);
+  else raycast_kernel<false, false><<<grid, block, 0, s>>>(jobs_dev, n_jobs, one, w);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Global map rendering (Appendix B.2): each scene raycast from its local pose, the nearest depth
+// wins per pixel (ties to the lower scene index) and gives the pixel its colour.  A scene's march
+// stops past the depth it would have to beat: any hit nearer than best + 1 mm is detected by a
+// sample at most one march step (<= mu) beyond it, so the cut changes no winner.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTile* kTile)
+    render_global_kernel(const RayJob* __restrict__ jobs, int n, uint16_t* __restrict__ depth,
+                         uint32_t* __restrict__ rgba, int8_t* __restrict__ owner, int32_t* __restrict__ err_flag) {
+  extern __shared__ __align__(16) int4 smem_jobs[];
+  RayJob* sj = reinterpret_cast<RayJob*>(smem_jobs);
+  {
+    const int4* src = reinterpret_cast<const int4*>(jobs);
+    for (int i = threadIdx.x; i < n * (int)(sizeof(RayJob) / 16); i += blockDim.x) smem_jobs[i] = src[i];
+  }
+  __syncthreads();
+  const int W = sj[0].W, H = sj[0].H;
+  const int tiles_x = (W + kTile - 1) / kTile;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int u = (blockIdx.x % tiles_x) * kTile + (warp & 1) * 8 + (lane & 7);
+  const int v = (blockIdx.x / tiles_x) * kTile + (warp >> 1) * 4 + (lane >> 3);
+  if (u >= W || v >= H) return;
+  int err = 0, best_mm = 0, best = -1;
+  float best_lam = 0.f;
+  for (int a = 0; a < n; ++a) {
+    const RayJob& j = sj[a];
+    const float dcx = ((float)u - j.cx) / j.fx, dcy = ((float)v - j.cy) / j.fy;
+    const float3 d = make_float3(j.R[0] * dcx + j.R[1] * dcy + j.R[2], j.R[3] * dcx + j.R[4] * dcy + j.R[5],
+                                 j.R[6] * dcx + j.R[7] * dcy + j.R[8]);
+    const float3 C = make_float3(j.t[0], j.t[1], j.t[2]);
+    const float lim = best >= 0 ? fminf(j.dmax, (float)(best_mm + 1) * 0.001f + j.scene.mu + j.scene.voxel) : j.dmax;
+    BlockCache cache{INT32_MIN, INT32_MIN, INT32_MIN, -1};
+    const float lam = march_ray(j.scene, C, d, j.dmin, lim, cache, &err);
+    if (lam >= j.dmin && lam <= j.dmax) {
+      const int mm = round_half_up_clamp(lam * 1000.0f, 1, 65535);
+      if (best < 0 || mm < best_mm) {
+        best_mm = mm;
+        best = a;
+        best_lam = lam;
+      }
+    }
+  }
+  uint32_t col = 0u;
+  if (best >= 0 && rgba) {
+    const RayJob& j = sj[best];
+    const float dcx = ((float)u - j.cx) / j.fx, dcy = ((float)v - j.cy) / j.fy;
+    const float3 d = make_float3(j.R[0] * dcx + j.R[1] * dcy + j.R[2], j.R[3] * dcx + j.R[4] * dcy + j.R[5],
+                                 j.R[6] * dcx + j.R[7] * dcy + j.R[8]);
+    BlockCache cache{INT32_MIN, INT32_MIN, INT32_MIN, -1};
+    col = trilinear_rgba(j.scene, cache,
+                         make_float3(fmaf(best_lam, d.x, j.t[0]), fmaf(best_lam, d.y, j.t[1]), fmaf(best_lam, d.z, j.t[2])),
+                         &err);
+  }
+  const size_t pix = (size_t)v * W + u;
+  depth[pix] = (uint16_t)best_mm;
+  if (rgba) rgba[pix] = col;
+  if (owner) owner[pix] = (int8_t)best;
+  if (err && err_flag) atomicExch(err_flag, RELO_EDEVICE);
+}
+
+cudaError_t launch_render_global(const RayJob* jobs_dev, int n, int W, int H, uint16_t* depth, uint32_t* rgba,
+                                 int8_t* owner, int32_t* err_flag, cudaStream_t s) {
+  if (n < 1 || W < 1 || H < 1) return cudaSuccess;
+  const size_t smem = (size_t)n * sizeof(RayJob);
+  if (smem > 48 * 1024) return cudaErrorInvalidValue;
+  render_global_kernel<<<ray_tiles(W, H), kTile * kTile, smem, s>>>(jobs_dev, n, depth, rgba, owner, err_flag);
   return cudaGetLastError();
 }
 

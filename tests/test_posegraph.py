@@ -59,6 +59,10 @@ def _compare(n, stream, seed):
         for b in range(a + 1, n):
             assert lib.cluster_sizes(a, b) == [len(c) for c in ora.clusters.get((a, b), [])]
             assert lib.cluster_sizes(b, a) == lib.cluster_sizes(a, b)
+            for c, samples in enumerate(ora.clusters.get((a, b), [])):
+                blend = PG.dq_blend(samples)
+                assert np.abs(lib.cluster_blend(a, b, c) - blend).max() < 1e-12
+                assert np.abs(lib.cluster_blend(b, a, c) - np.linalg.inv(blend)).max() < 1e-12
     pl, fl, el = lib.optimise()
     po, fo, eo = ora.optimise()
     assert list(fl) == list(fo)
