@@ -58,12 +58,13 @@ ALG_BYTES_PER_PIXEL = {
     "forest_verify": 35.87,
     "learned_verify": 35.87,
 }
-# DRAM bytes (read + write) per launch of the stage's main kernel, from the ncu capture summarised
-# in profiles/attempt_kernels_house_640x480_batch128.md (None: not captured for the current code).
-PROFILED_TRAFFIC_BYTES = {
-    "query_raycast": 3.081e9 + 0.281e9,
-    "forest_eval": 0.240e9 + 0.359e9,
-    "forest_hypotheses": 0.638e9 + 0.005e9,
+# DRAM bytes (read + write) per attempt of the stage's main kernel: the ncu capture summarised in
+# profiles/attempt_kernels_house_640x480_batch128.md (128 attempts per launch) divided by 128; a
+# launch of A attempts is reported as A times that (None: not captured for the current code).
+PROFILED_TRAFFIC_BYTES_PER_ATTEMPT = {
+    "query_raycast": (3.107e9 + 0.600e9) / 128,
+    "forest_eval": (0.398e9 + 0.361e9) / 128,
+    "forest_hypotheses": (0.637e9 + 0.005e9) / 128,
     "forest_verify": None,
 }
 
@@ -598,19 +599,24 @@ IMAD_PER_CLK_SM = 64
 N_SMS = 152
 
 
+def profiled_traffic(kernel, attempts):
+    per = PROFILED_TRAFFIC_BYTES_PER_ATTEMPT.get(kernel)
+    return None if per is None else per * attempts
+
+
 def roofline(kernel, avg_ms, attempts, tries_per_launch, clocks):
     if kernel in ("forest_hypotheses", "learned_hypotheses"):
         mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
         peak = IMAD_PER_CLK_SM * N_SMS * mhz * 1e6 / IMAD_PER_TRY / 1e9      # G tries / s
         achieved = tries_per_launch / (avg_ms / 1000.0) / 1e9
         return {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gtries/s",
-                "frac": achieved / peak, "traffic": PROFILED_TRAFFIC_BYTES.get(kernel), "ms": avg_ms,
+                "frac": achieved / peak, "traffic": profiled_traffic(kernel, attempts), "ms": avg_ms,
                 "peak_source": "derived: 64 IMAD/clk/SM x 152 SMs x max SM clock / 40 IMAD per try"}
     peak, peak_kind = measured_peaks()
     per_px = ALG_BYTES_PER_PIXEL.get(kernel)
     achieved = None if per_px is None else per_px * W * H * attempts / (avg_ms / 1000.0) / 1e9
     return {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": None if achieved is None else achieved / peak, "traffic": PROFILED_TRAFFIC_BYTES.get(kernel),
+            "frac": None if achieved is None else achieved / peak, "traffic": profiled_traffic(kernel, attempts),
             "ms": avg_ms, "peak_source": peak_kind}
 
 
