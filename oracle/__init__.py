@@ -80,6 +80,15 @@ def _lib():
                                             ctypes.c_double, ctypes.c_double, ctypes.c_int, vp]
         lib.orc_fill_modes.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_int, vp, vp]
+        lib.orc_fusion_create.restype = vp
+        lib.orc_fusion_create.argtypes = [ctypes.c_long, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+        lib.orc_fusion_destroy.argtypes = [vp]
+        lib.orc_fusion_frame.restype = ctypes.c_int
+        lib.orc_fusion_frame.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, dp,
+                                         vp, vp]
+        lib.orc_fusion_count.restype = ctypes.c_long
+        lib.orc_fusion_count.argtypes = [vp]
+        lib.orc_fusion_export.argtypes = [vp, vp, vp, vp, vp]
         _LIB = lib
     return _LIB
 
@@ -189,6 +198,56 @@ def render_global(scenes, global_poses, intr, pose_global, pixels=None):
     rgba = np.take_along_axis(cols, owner[None, ..., None], 0)[0]
     rgba = np.where(hit[..., None], rgba, 0).astype(np.uint8)
     return depth, rgba, np.where(hit, owner, -1).astype(np.int8), depths
+
+
+@dataclass
+class FusedBlocks:
+    """Blocks of a fused scene (coordinates, tsdf, colour, weights), sorted by (bz, by, bx); has
+    the fields oracle.Scene and the library's scene creation read."""
+    coords: np.ndarray
+    tsdf: np.ndarray
+    rgba: np.ndarray
+    weight: np.ndarray
+    voxel_size: float
+    mu: float
+
+
+class FusionScene:
+    """TSDF fusion of depth (+ colour) frames into a growing block scene (Sec. 3.3 (a), Appendix
+    B.3; the rules are stated above orc_fusion_frame in relo_oracle.c)."""
+
+    def __init__(self, capacity, voxel_size, mu, max_weight=100):
+        self.voxel_size, self.mu = float(voxel_size), float(mu)
+        self._h = _lib().orc_fusion_create(int(capacity), self.voxel_size, self.mu, int(max_weight))
+        if not self._h:
+            raise MemoryError("oracle fusion scene")
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib().orc_fusion_destroy(self._h)
+            self._h = None
+
+    def fuse(self, intr, pose, depth, rgba=None) -> bool:
+        """Fuse one frame (depth uint16 mm [H][W], rgba uint8 [H][W][4] or None) at camera-to-scene
+        pose; False if the block capacity ran out."""
+        K = np.array([intr.fx, intr.fy, intr.cx, intr.cy], dtype=np.float64)
+        d, pd = _c(depth, np.uint16)
+        c, pc = (None, None) if rgba is None else _c(rgba, np.uint8)
+        rc = _lib().orc_fusion_frame(self._h, intr.width, intr.height, _d(K), intr.depth_min, intr.depth_max,
+                                     _d(np.asarray(pose, dtype=np.float64).reshape(16)), pd, pc)
+        return rc == 0
+
+    def blocks(self) -> FusedBlocks:
+        n = _lib().orc_fusion_count(self._h)
+        coords = np.empty((n, 3), dtype=np.int32)
+        tsdf = np.empty((n, 512), dtype=np.float32)
+        rgba = np.empty((n, 512, 4), dtype=np.uint8)
+        weight = np.empty((n, 512), dtype=np.uint16)
+        if n:
+            _lib().orc_fusion_export(self._h, coords.ctypes.data, tsdf.ctypes.data, rgba.ctypes.data,
+                                     weight.ctypes.data)
+        order = np.lexsort((coords[:, 0], coords[:, 1], coords[:, 2]))
+        return FusedBlocks(coords[order], tsdf[order], rgba[order], weight[order], self.voxel_size, self.mu)
 
 
 def raycast_touched(scene: Scene, intr, pose, with_colour: bool) -> dict:

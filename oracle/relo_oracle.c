@@ -589,3 +589,188 @@ void orc_fill_modes(const orc_reservoirs* r, double h, double tol, int max_iter,
                                                merge_dist, cov_floor, max_modes, modes + id * max_modes * 12);
   }
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* TSDF fusion of a depth (+ colour) frame into a growing voxel-block scene: the standard       */
+/* volumetric fusion (Curless and Levoy 1996) in the voxel-hashing form of InfiniTAM, which the   */
+/* paper runs for each agent's map (Sec. 3.3 (a)) and for the single global model (Appendix     */
+/* B.3).  Unlike the rest of this file the arithmetic is float32, in the order written (this   */
+/* file is compiled without contraction): which block a sample falls in, which pixel a voxel   */
+/* projects to and whether it lies in the band are decided in float32 by the library too, so   */
+/* both sides must take those decisions in the same precision.                                  */
+/* Readings (the paper cites the pipeline, not its rules):                                       */
+/*  - depth z = D * 0.001 m, valid in [depth_min, depth_max];                                   */
+/*  - allocation: along the ray of a valid pixel, the points at camera z = z - mu + k h,        */
+/*    h = block_size / 4, k = 0 .. ceil(2 mu / h) (the last clamped to z + mu, points at z <= 0 */
+/*    skipped); every block holding such a point is allocated (if new) and updated this frame; */
+/*  - update of a voxel of those blocks (centre at its integer coordinates times the voxel      */
+/*    size): camera point q = R^T (p - t), skipped unless q.z > 0; pixel (floor(fx q.x/q.z + cx */
+/*    + 1/2), floor(fy q.y/q.z + cy + 1/2)) inside the image with a valid depth d;               */
+/*    eta = d - q.z, skipped if eta < -mu; f = min(1, eta / mu); F = (F w + f) / (w + 1),       */
+/*    each colour channel c = round_half_up((c w + c_pixel) / (w + 1)), alpha 255,              */
+/*    w = min(w + 1, max_weight).  New blocks start at F = 1, w = 0, colour 0.                  */
+/* ------------------------------------------------------------------------------------------ */
+typedef struct {
+  long n, cap;
+  int32_t* coords;      /* cap x 3 */
+  float* tsdf;          /* cap x 512 */
+  uint8_t* rgba;        /* cap x 512 x 4 */
+  uint16_t* weight;     /* cap x 512 */
+  long* stamp;          /* cap: the last frame that marked the block */
+  long* table;          /* open addressing over block coordinates -> index, -1 empty */
+  long table_size;
+  float voxel, mu;
+  int max_weight;
+  long frame;
+} orc_fusion;
+
+orc_fusion* orc_fusion_create(long cap, double voxel, double mu, int max_weight) {
+  orc_fusion* f = (orc_fusion*)calloc(1, sizeof(orc_fusion));
+  if (!f || cap < 1) { free(f); return NULL; }
+  f->cap = cap;
+  f->coords = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)cap);
+  f->tsdf = (float*)malloc(sizeof(float) * 512 * (size_t)cap);
+  f->rgba = (uint8_t*)calloc((size_t)cap * 512 * 4, 1);
+  f->weight = (uint16_t*)calloc((size_t)cap * 512, sizeof(uint16_t));
+  f->stamp = (long*)malloc(sizeof(long) * (size_t)cap);
+  f->table_size = 1;
+  while (f->table_size < 2 * cap) f->table_size *= 2;
+  f->table = (long*)malloc(sizeof(long) * (size_t)f->table_size);
+  if (!f->coords || !f->tsdf || !f->rgba || !f->weight || !f->stamp || !f->table) {
+    free(f->coords); free(f->tsdf); free(f->rgba); free(f->weight); free(f->stamp); free(f->table); free(f);
+    return NULL;
+  }
+  for (long i = 0; i < f->table_size; ++i) f->table[i] = -1;
+  f->voxel = (float)voxel;
+  f->mu = (float)mu;
+  f->max_weight = max_weight;
+  return f;
+}
+
+void orc_fusion_destroy(orc_fusion* f) {
+  if (!f) return;
+  free(f->coords); free(f->tsdf); free(f->rgba); free(f->weight); free(f->stamp); free(f->table); free(f);
+}
+
+static long fusion_slot(const orc_fusion* f, int bx, int by, int bz) {
+  uint64_t h = ((uint64_t)(uint32_t)bx * 2654435761u) ^ ((uint64_t)(uint32_t)by * 40503u) ^
+               ((uint64_t)(uint32_t)bz * 2246822519u);
+  long i = (long)(h & (uint64_t)(f->table_size - 1));
+  for (;;) {
+    long b = f->table[i];
+    if (b < 0) return i;
+    const int32_t* c = f->coords + 3 * b;
+    if (c[0] == bx && c[1] == by && c[2] == bz) return i;
+    i = (i + 1) & (f->table_size - 1);
+  }
+}
+
+/* Marks block (bx,by,bz) for this frame, allocating it if new.  Returns -1 when full. */
+static int fusion_mark(orc_fusion* f, int bx, int by, int bz) {
+  long i = fusion_slot(f, bx, by, bz);
+  long b = f->table[i];
+  if (b < 0) {
+    if (f->n >= f->cap) return -1;
+    b = f->n++;
+    f->table[i] = b;
+    f->coords[3 * b] = bx;
+    f->coords[3 * b + 1] = by;
+    f->coords[3 * b + 2] = bz;
+    for (int v = 0; v < 512; ++v) f->tsdf[512 * b + v] = 1.0f;
+  }
+  f->stamp[b] = f->frame;
+  return 0;
+}
+
+/* Fuses one frame.  K = fx, fy, cx, cy; P camera -> scene (row-major 4x4); rgba nullable.
+ * Returns 0, or -1 if the block capacity ran out (the frame is then fused into the blocks that
+ * fit). */
+int orc_fusion_frame(orc_fusion* f, int W, int H, const double K[4], double depth_min, double depth_max,
+                     const double P[16], const uint16_t* depth, const uint8_t* rgba) {
+  const float fx = (float)K[0], fy = (float)K[1], cx = (float)K[2], cy = (float)K[3];
+  const float dmin = (float)depth_min, dmax = (float)depth_max;
+  float R[9], t[3];
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 3; ++c) R[3 * r + c] = (float)P[4 * r + c];
+    t[r] = (float)P[4 * r + 3];
+  }
+  const float mu = f->mu, bs = f->voxel * 8.0f, h = bs * 0.25f;
+  int full = 0;
+  f->frame += 1;
+  /* allocation: the band around every valid pixel's depth */
+  for (int v = 0; v < H; ++v)
+    for (int u = 0; u < W; ++u) {
+      const uint16_t D = depth[(long)v * W + u];
+      if (D == 0) continue;
+      const float z = (float)D * 0.001f;
+      if (!(z >= dmin && z <= dmax)) continue;
+      const float dcx = ((float)u - cx) / fx, dcy = ((float)v - cy) / fy;
+      float dir[3];
+      for (int r = 0; r < 3; ++r) dir[r] = (R[3 * r] * dcx + R[3 * r + 1] * dcy) + R[3 * r + 2];
+      const float z0 = z - mu, z1 = z + mu;
+      const int n = (int)ceilf((z1 - z0) / h);
+      for (int k = 0; k <= n; ++k) {
+        float zk = z0 + (float)k * h;
+        if (zk > z1) zk = z1;
+        if (!(zk > 0.0f)) continue;
+        int b[3], ok = 1;
+        for (int r = 0; r < 3; ++r) {
+          const float p = t[r] + zk * dir[r];
+          const float q = floorf(p / bs);
+          if (!(q >= -32768.0f && q <= 32767.0f)) ok = 0;
+          b[r] = ok ? (int)q : 0;
+        }
+        if (ok && fusion_mark(f, b[0], b[1], b[2]) != 0) full = 1;
+      }
+    }
+  /* update: every voxel of the blocks marked this frame */
+  for (long b = 0; b < f->n; ++b) {
+    if (f->stamp[b] != f->frame) continue;
+    const int32_t* bc = f->coords + 3 * b;
+    for (int vi = 0; vi < 512; ++vi) {
+      const int X = 8 * bc[0] + (vi & 7), Y = 8 * bc[1] + ((vi >> 3) & 7), Z = 8 * bc[2] + (vi >> 6);
+      const float px = (float)X * f->voxel, py = (float)Y * f->voxel, pz = (float)Z * f->voxel;
+      const float dx = px - t[0], dy = py - t[1], dz = pz - t[2];
+      const float qx = (R[0] * dx + R[3] * dy) + R[6] * dz;
+      const float qy = (R[1] * dx + R[4] * dy) + R[7] * dz;
+      const float qz = (R[2] * dx + R[5] * dy) + R[8] * dz;
+      if (!(qz > 0.0f)) continue;
+      const float uf = fx * (qx / qz) + cx, vf = fy * (qy / qz) + cy;
+      const float fu = floorf(uf + 0.5f), fv = floorf(vf + 0.5f);
+      if (!(fu >= 0.0f && fu < (float)W && fv >= 0.0f && fv < (float)H)) continue;
+      const long pix = (long)fv * W + (long)fu;
+      const uint16_t Dm = depth[pix];
+      if (Dm == 0) continue;
+      const float dm = (float)Dm * 0.001f;
+      if (!(dm >= dmin && dm <= dmax)) continue;
+      const float eta = dm - qz;
+      if (eta < -mu) continue;
+      const float fn = fminf(1.0f, eta / mu);
+      const long at = 512 * b + vi;
+      const float w = (float)f->weight[at];
+      f->tsdf[at] = (f->tsdf[at] * w + fn) / (w + 1.0f);
+      if (rgba) {
+        for (int c = 0; c < 3; ++c) {
+          const float cc = ((float)f->rgba[4 * at + c] * w + (float)rgba[4 * pix + c]) / (w + 1.0f);
+          float r = floorf(cc + 0.5f);
+          if (r < 0.0f) r = 0.0f;
+          if (r > 255.0f) r = 255.0f;
+          f->rgba[4 * at + c] = (uint8_t)r;
+        }
+        f->rgba[4 * at + 3] = 255;
+      }
+      f->weight[at] = (uint16_t)(f->weight[at] + 1 < f->max_weight ? f->weight[at] + 1 : f->max_weight);
+    }
+  }
+  return full ? -1 : 0;
+}
+
+long orc_fusion_count(const orc_fusion* f) { return f->n; }
+
+/* Copies the blocks (in allocation order) out. */
+void orc_fusion_export(const orc_fusion* f, int32_t* coords, float* tsdf, uint8_t* rgba, uint16_t* weight) {
+  memcpy(coords, f->coords, sizeof(int32_t) * 3 * (size_t)f->n);
+  memcpy(tsdf, f->tsdf, sizeof(float) * 512 * (size_t)f->n);
+  memcpy(rgba, f->rgba, (size_t)f->n * 512 * 4);
+  memcpy(weight, f->weight, sizeof(uint16_t) * 512 * (size_t)f->n);
+}
