@@ -77,6 +77,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=256, help="attempts per step")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fusion-frames", type=int, default=96, help="frames of the TSDF fusion section (0: skip)")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the launch schedule with relo_batch_autotune (default: the default schedule, "
                          "which the tuner matches within noise on this workload)")
@@ -380,6 +381,11 @@ def run_ours(args):
     if args.serve_seconds > 0 and rank == 0:
         serving = serving_section(args, B, torch, dev, sets[0], prm)
 
+    # ---- TSDF fusion (not part of the timed steps) ------------------------------------------
+    fusion = None
+    if args.fusion_frames > 0 and rank == 0:
+        fusion = fusion_section(args, B, synth, torch, dev, scene, world, intr, train)
+
     # ---- end to end through the public API (host buffers) ----------------------------------
     host_noise = [torch.empty((A, H, W), dtype=torch.float32, pin_memory=True) for _ in range(n_sets)]
     for si in range(n_sets):
@@ -415,7 +421,7 @@ def run_ours(args):
                            "success_rate": succ / n, "verified_rate": ver / n,
                            "stage_ms_per_step": {k: v / args.steps for k, v in stage_tot.items()},
                            "schedule": dict(schedule, autotuned=bool(args.autotune)),
-                           "learned": learned, "serving": serving},
+                           "learned": learned, "serving": serving, "fusion": fusion},
                 "e2e": {"value": e2e_value, "unit": UNIT,
                         "h2d_bytes_per_step": A * H * W * 4 + A * ctypes_attempt_bytes(),
                         "d2h_bytes_per_step": A * B.RESULT_BYTES},
@@ -522,6 +528,47 @@ def success(r, P):
     cang = (np.trace(r["pose"][:3, :3] @ P[:3, :3].T) - 1) / 2
     dr = math.degrees(math.acos(max(-1.0, min(1.0, cang))))
     return r["status"] == 0 and dt <= 0.05 and dr <= 5.0
+
+
+# ------------------------------------------------------------------------------------------------
+# TSDF fusion (Sec. 3.3 (a): each agent's map; Appendix B.3): noisy renders along the house
+# trajectory fused into an empty scene, one frame per relo_fuse_frame (four launches)
+# ------------------------------------------------------------------------------------------------
+FUSION_CAPACITY = 1 << 20          # blocks (5.2 GB of tsdf, colour and weights)
+FUSION_BYTES_PER_VOXEL = 2 * (4 + 4 + 2)   # tsdf, colour, weight: read and written
+
+
+def fusion_section(args, B, synth, torch, dev, scene, world, intr, train):
+    n = args.fusion_frames
+    poses = synth.query_poses(world, train, n, seed=4242)
+    depth = torch.zeros((n, H, W), dtype=torch.int16, device=dev)
+    rgba = torch.zeros((n, H, W, 4), dtype=torch.uint8, device=dev)
+    noise = torch.from_numpy(np.stack([synth.depth_noise(H, W, 5000 + k) for k in range(n)])).to(dev)
+    ws = torch.empty(B.raycast_views_workspace_size(n), dtype=torch.uint8, device=dev)
+    B.raycast_views(scene, intr, poses, depth, rgba, noise_dev=noise, workspace_dev=ws)
+    fs = B.FusionScene(FUSION_CAPACITY, synth.VOXEL_SIZE, synth.TRUNCATION, log2_buckets=20)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms, vis, created, gbs = [], [], 0, []
+    for k in range(n):
+        e0.record()
+        fs.fuse(intr, poses[k], depth[k], rgba[k])
+        e1.record()
+        v, c = fs.last_frame_stats(intr)          # synchronises after the end event
+        t = e0.elapsed_time(e1)
+        ms.append(t)
+        vis.append(v)
+        created += c
+        gbs.append((v * 512 * FUSION_BYTES_PER_VOXEL + H * W * 6) / (t / 1000.0) / 1e9)
+    steady = slice(n // 4, n)                     # after the first quarter most blocks exist
+    peak, kind = measured_peaks()
+    g = float(np.mean(gbs[steady]))
+    return {"frames": n, "size": f"{W}x{H}", "ms_per_frame": float(np.mean(ms)),
+            "frames_per_s": 1000.0 * n / float(np.sum(ms)), "steady_ms_per_frame": float(np.mean(ms[steady])),
+            "blocks": fs.block_count(), "blocks_created": created, "visible_blocks_mean": float(np.mean(vis)),
+            "roofline": {"bound": "hbm", "achieved": g, "peak": peak, "unit": "GB/s", "frac": g / peak,
+                         "peak_source": kind,
+                         "bytes": "updated blocks x 512 voxels x 20 B (tsdf, colour, weight read and written) "
+                                  "+ 6 B per pixel (depth, colour)"}}
 
 
 # ------------------------------------------------------------------------------------------------

@@ -137,6 +137,54 @@ relo_status relo_render_global(const relo_scene* const* scenes, const double* gl
                                size_t workspace_bytes, relo_stream stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Scenes that grow by TSDF fusion: each agent's map is built by fusing its posed RGB-D frames
+ * (Sec. 3.3 (a), the InfiniTAM pipeline), and the single global model by fusing every agent's
+ * frames with their poses moved by the agent's global pose (Appendix B.3).  The standard
+ * volumetric fusion (Curless and Levoy 1996) on voxel blocks; rules, all in float32 with each
+ * operation rounded to nearest in the order written:
+ *  - depth z = D * 0.001 m, valid in [depth_min, depth_max];
+ *  - allocation: along a valid pixel's ray, the points at camera z = z - mu + k h, h = block
+ *    size / 4, k = 0 .. ceil(2 mu / h) (the last clamped to z + mu; z <= 0 skipped): every block
+ *    holding one is allocated if new and updated this frame;
+ *  - update of each voxel of those blocks (centre at its integer coordinates times the voxel
+ *    size): q = R^T (p - t), skipped unless q.z > 0; pixel (floor(fx q.x/q.z + cx + 1/2),
+ *    floor(fy q.y/q.z + cy + 1/2)) inside the image with a valid depth d; eta = d - q.z, skipped
+ *    if eta < -mu; f = min(1, eta / mu); F = (F w + f) / (w + 1); with colour, each channel
+ *    c = floor((c w + c_pixel) / (w + 1) + 1/2) and alpha 255; w = min(w + 1, max_weight).
+ *    New blocks start at F = +1, w = 0, colour 0.
+ * The scene has no dense grid: raycasts walk its hash.  Block indices follow the order in which
+ * the device allocates them; coordinates and contents do not depend on it.
+ * ------------------------------------------------------------------------------------- */
+/* An empty scene with room for capacity_blocks blocks (tsdf f32, colour u8x4 and weight u16 per
+ * voxel: 5 KB per block, allocated now) and 2^log2_buckets buckets.
+ * Errors: RELO_EINVAL (capacity outside [1, 2^24], log2_buckets outside [4, 30], voxel_size or mu
+ * <= 0, max_weight outside [1, 65535]), RELO_ENOMEM, RELO_ECUDA. */
+relo_status relo_create_fusion_scene(int64_t capacity_blocks, double voxel_size, double mu, int32_t log2_buckets,
+                                     int32_t max_weight, relo_scene** out);
+/* Workspace bytes relo_fuse_frame needs for width x height frames (0 for a bad size). */
+size_t relo_fuse_workspace_size(int32_t width, int32_t height);
+/* Fuses one frame (depth_dev u16 mm [H][W]; rgba_dev u8 [H][W][4] or NULL) seen from pose_c2s
+ * (camera -> scene), asynchronously on the stream, in four launches.  If the block pool, the
+ * chain entries (capacity_blocks) or the frame's block set (relo_fuse_workspace_size) run out,
+ * the frame is fused into what fits and the scene records RELO_ENOMEM (relo_scene_block_count).
+ * Errors: RELO_EINVAL (null, a scene not created for fusion, intrinsics, workspace). */
+relo_status relo_fuse_frame(relo_scene* scene, const relo_intrinsics* intr, const double pose_c2s[16],
+                            const uint16_t* depth_dev, const uint8_t* rgba_dev, void* workspace_dev,
+                            size_t workspace_bytes, relo_stream stream);
+/* The last frame fused with this workspace (of width x height frames): blocks it updated and blocks
+ * it created.  Synchronises the device.  Errors: RELO_EINVAL (null workspace, bad size). */
+relo_status relo_fuse_stats(const void* workspace_dev, int32_t width, int32_t height, int32_t* visible,
+                            int32_t* created);
+/* Blocks in the scene (synchronises the device).  Returns RELO_ENOMEM if a fusion ran out of room. */
+relo_status relo_scene_block_count(const relo_scene* scene, int64_t* n_blocks);
+/* Copies a fusion scene's blocks to host arrays of at least capacity blocks (any may be NULL):
+ * coords [n][3], tsdf [n][512], rgba [n][512][4], weight [n][512]; *n_out = n.  Synchronous.
+ * Errors: RELO_EINVAL (null, not a fusion scene, capacity < n); RELO_ENOMEM as above (the copy is
+ * still made). */
+relo_status relo_scene_export(const relo_scene* scene, int32_t* coords_host, float* tsdf_host, uint8_t* rgba_host,
+                              uint16_t* weight_host, int64_t capacity, int64_t* n_out);
+
+/* ---------------------------------------------------------------------------------------
  * Regression forest (the relocaliser of Sec. 3.3 (b), after Cavallari et al.).
  * n_trees complete binary trees of the given depth, stored breadth first (children of node n
  * at 2n+1, 2n+2), 2^depth - 1 split nodes of 16 bytes each:

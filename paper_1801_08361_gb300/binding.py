@@ -87,6 +87,13 @@ _SIGS = {
     "relo_last_error": (ctypes.c_char_p, []),
     "relo_create_scene": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_dbl, c_dbl, c_i32, ctypes.POINTER(c_vp)]),
     "relo_destroy_scene": (None, [c_vp]),
+    "relo_create_fusion_scene": (c_i32, [c_i64, c_dbl, c_dbl, c_i32, c_i32, ctypes.POINTER(c_vp)]),
+    "relo_fuse_workspace_size": (ctypes.c_size_t, [c_i32, c_i32]),
+    "relo_fuse_frame": (c_i32, [c_vp, ctypes.POINTER(Intrinsics), ctypes.POINTER(c_dbl), c_vp, c_vp, c_vp,
+                                ctypes.c_size_t, c_vp]),
+    "relo_scene_block_count": (c_i32, [c_vp, ctypes.POINTER(c_i64)]),
+    "relo_fuse_stats": (c_i32, [c_vp, c_i32, c_i32, ctypes.POINTER(c_i32), ctypes.POINTER(c_i32)]),
+    "relo_scene_export": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(c_i64)]),
     "relo_scene_lookup": (c_i32, [c_vp, c_vp, c_i64, c_vp, c_vp]),
     "relo_scene_use_grid": (c_i32, [c_vp, c_i32]),
     "relo_raycast_view": (c_i32, [c_vp, ctypes.POINTER(Intrinsics), ctypes.POINTER(c_dbl), c_vp, c_vp, c_vp, c_vp]),
@@ -247,6 +254,59 @@ class Scene:
         if getattr(self, "handle", None) and _LIB is not None:
             _LIB.relo_destroy_scene(self.handle)
             self.handle = None
+
+
+class FusionScene(Scene):
+    """A scene that grows by TSDF fusion (relo_create_fusion_scene / relo_fuse_frame); raycasts,
+    verification and global rendering take it like any scene."""
+
+    def __init__(self, capacity, voxel_size, mu, log2_buckets: int = 20, max_weight: int = 100):
+        h = c_vp()
+        _check(lib().relo_create_fusion_scene(int(capacity), float(voxel_size), float(mu), int(log2_buckets),
+                                              int(max_weight), ctypes.byref(h)))
+        self.handle = h.value
+        self.capacity = int(capacity)
+        self._ws = None
+
+    def fuse(self, intr, pose, depth_dev, rgba_dev=None, workspace_dev=None, stream=None):
+        """Fuse one frame (depth u16 mm [H][W] as int16 bits, rgba u8 [H][W][4] or None)."""
+        if workspace_dev is None:
+            need = int(lib().relo_fuse_workspace_size(intr.width, intr.height))
+            if self._ws is None or self._ws.numel() < need:
+                import torch
+                self._ws = torch.empty(need, dtype=torch.uint8, device=depth_dev.device)
+            workspace_dev = self._ws
+        ci = intrinsics(intr)
+        ph, pp = _poses_host([pose])
+        _check(lib().relo_fuse_frame(self.handle, ctypes.byref(ci), ctypes.cast(pp, ctypes.POINTER(c_dbl)),
+                                     _ptr(depth_dev), _ptr(rgba_dev), _ptr(workspace_dev), workspace_dev.numel(),
+                                     _stream(stream)))
+
+    def last_frame_stats(self, intr, workspace_dev=None):
+        """(blocks updated, blocks created) by the last frame fused with the workspace."""
+        ws = self._ws if workspace_dev is None else workspace_dev
+        vis, new = c_i32(), c_i32()
+        _check(lib().relo_fuse_stats(_ptr(ws), intr.width, intr.height, ctypes.byref(vis), ctypes.byref(new)))
+        return int(vis.value), int(new.value)
+
+    def block_count(self) -> int:
+        n = c_i64()
+        _check(lib().relo_scene_block_count(self.handle, ctypes.byref(n)))
+        return int(n.value)
+
+    def export(self):
+        """(coords [n, 3], tsdf [n, 512], rgba [n, 512, 4], weight [n, 512]) sorted by (bz, by, bx)."""
+        n = c_i64()
+        _check(lib().relo_scene_block_count(self.handle, ctypes.byref(n)))
+        k = int(n.value)
+        coords = np.empty((k, 3), np.int32)
+        tsdf = np.empty((k, 512), np.float32)
+        rgba = np.empty((k, 512, 4), np.uint8)
+        weight = np.empty((k, 512), np.uint16)
+        _check(lib().relo_scene_export(self.handle, coords.ctypes.data, tsdf.ctypes.data, rgba.ctypes.data,
+                                       weight.ctypes.data, k, ctypes.byref(n)))
+        order = np.lexsort((coords[:, 0], coords[:, 1], coords[:, 2]))
+        return coords[order], tsdf[order], rgba[order], weight[order]
 
 
 class Forest:

@@ -389,7 +389,185 @@ void relo_destroy_scene(relo_scene* s) {
   cudaFree(s->d_tsdf);
   cudaFree(s->d_rgba);
   cudaFree(s->d_grid);
+  cudaFree(s->d_weight);
+  cudaFree(s->d_coords);
+  cudaFree(s->d_counters);
   delete s;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Scenes that grow by TSDF fusion (Sec. 3.3 (a); Appendix B.3)
+// ---------------------------------------------------------------------------------------------
+relo_status relo_create_fusion_scene(int64_t capacity, double voxel, double mu, int32_t log2_buckets,
+                                     int32_t max_weight, relo_scene** out) {
+  if (!out) return fail(RELO_EINVAL, "out is null");
+  *out = nullptr;
+  if (capacity < 1 || capacity > ((int64_t)1 << 24)) return fail(RELO_EINVAL, "capacity outside [1, 2^24] blocks");
+  if (log2_buckets < 4 || log2_buckets > 30) return fail(RELO_EINVAL, "log2_buckets outside [4, 30]");
+  if (!(voxel > 0) || !(mu > 0)) return fail(RELO_EINVAL, "voxel_size and mu must be positive");
+  if (max_weight < 1 || max_weight > 65535) return fail(RELO_EINVAL, "max_weight outside [1, 65535]");
+  relo_scene* s = new relo_scene();
+  s->capacity = capacity;
+  s->max_weight = max_weight;
+  const size_t nb = (size_t)1 << log2_buckets, nv = (size_t)capacity * kVoxelsPerBlock;
+  cudaError_t e = cudaMalloc(&s->d_buckets, nb * sizeof(int4));
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_excess, (size_t)capacity * sizeof(int4));
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_tsdf, nv * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_rgba, nv * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_weight, nv * sizeof(uint16_t));
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_coords, (size_t)capacity * sizeof(int4));
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_counters, 4 * sizeof(int32_t));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    relo_destroy_scene(s);
+    return fail(RELO_ENOMEM, "device allocation for the fusion scene failed");
+  }
+  // empty buckets (0xFF bytes: block -1, next -1; the key words of an empty head are unused),
+  // voxels at tsdf +1, weight 0, colour 0
+  e = cudaMemset(s->d_buckets, 0xFF, nb * sizeof(int4));
+  if (e == cudaSuccess) e = cudaMemset(s->d_excess, 0xFF, (size_t)capacity * sizeof(int4));
+  if (e == cudaSuccess) e = cudaMemset(s->d_rgba, 0, nv * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(s->d_weight, 0, nv * sizeof(uint16_t));
+  if (e == cudaSuccess) e = cudaMemset(s->d_counters, 0, 4 * sizeof(int32_t));
+  if (e == cudaSuccess) e = launch_fuse_init((float*)s->d_tsdf, (int64_t)nv, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    relo_destroy_scene(s);
+    return cuda_fail(e, "fusion scene initialisation");
+  }
+  SceneView& v = s->view;
+  v.buckets = (const int4*)s->d_buckets;
+  v.excess = (const int4*)s->d_excess;
+  v.tsdf = (const float*)s->d_tsdf;
+  v.rgba = (const uint32_t*)s->d_rgba;
+  v.mask = (uint32_t)(nb - 1);
+  v.n_blocks = (int32_t)capacity;
+  v.max_chain = (int32_t)capacity + 1;  // chains grow on the device: bound walks by the pool
+  v.voxel = (float)voxel;
+  v.inv_voxel = (float)(1.0 / voxel);
+  v.mu = (float)mu;
+  v.block_size = (float)(8.0 * voxel);
+  v.inv_block = (float)(1.0 / (8.0 * voxel));
+  v.grid = nullptr;
+  *out = s;
+  return RELO_OK;
+}
+
+namespace {
+size_t fuse_set_slots(int32_t width, int32_t height) {
+  size_t s = 1024;
+  while (s < 2 * (size_t)width * height) s *= 2;
+  return s;
+}
+}  // namespace
+
+size_t relo_fuse_workspace_size(int32_t width, int32_t height) {
+  if (bad_size(width, height)) return 0;
+  const size_t S = fuse_set_slots(width, height);
+  return S * 8 + 256 + S * 8 + 256 + S * 4 + 256 + 256;
+}
+
+relo_status relo_fuse_frame(relo_scene* scene, const relo_intrinsics* intr, const double* pose, const uint16_t* depth,
+                            const uint8_t* rgba, void* ws, size_t ws_bytes, relo_stream stream) {
+  if (!scene || !pose || !depth) return fail(RELO_EINVAL, "null scene, pose or depth");
+  if (scene->capacity < 1) return fail(RELO_EINVAL, "scene was not created for fusion");
+  relo_status st = check_intr(intr);
+  if (st) return st;
+  if (!ws || ((uintptr_t)ws & 255) != 0 || ws_bytes < relo_fuse_workspace_size(intr->width, intr->height))
+    return fail(RELO_EINVAL, "workspace missing, misaligned or too small");
+  const size_t S = fuse_set_slots(intr->width, intr->height);
+  Carver c{(char*)ws, 0};
+  FuseJob j{};
+  j.set = c.take<unsigned long long>(S);
+  j.new_keys = c.take<unsigned long long>(S);
+  j.visible = c.take<int32_t>(S);
+  j.n_visible = c.take<int32_t>(2);
+  j.n_new = j.n_visible + 1;
+  j.set_mask = (uint32_t)(S - 1);
+  j.buckets = (int4*)scene->d_buckets;
+  j.excess = (int4*)scene->d_excess;
+  j.tsdf = (float*)scene->d_tsdf;
+  j.rgba = (uint32_t*)scene->d_rgba;
+  j.weight = (uint16_t*)scene->d_weight;
+  j.coords = (int4*)scene->d_coords;
+  j.counters = (int32_t*)scene->d_counters;
+  j.status = j.counters + 2;
+  j.bucket_mask = scene->view.mask;
+  j.capacity = (int32_t)scene->capacity;
+  j.max_weight = scene->max_weight;
+  j.depth = depth;
+  j.frame_rgba = (const uint32_t*)rgba;
+  j.W = intr->width;
+  j.H = intr->height;
+  j.fx = (float)intr->fx;
+  j.fy = (float)intr->fy;
+  j.cx = (float)intr->cx;
+  j.cy = (float)intr->cy;
+  j.dmin = (float)intr->depth_min;
+  j.dmax = (float)intr->depth_max;
+  for (int r = 0; r < 3; ++r) {
+    for (int q = 0; q < 3; ++q) j.R[3 * r + q] = (float)pose[4 * r + q];
+    j.t[r] = (float)pose[4 * r + 3];
+  }
+  j.voxel = scene->view.voxel;
+  j.mu = scene->view.mu;
+  RELO_CUDA(launch_fuse_frame(j, (cudaStream_t)stream));
+  return RELO_OK;
+}
+
+relo_status relo_fuse_stats(const void* ws, int32_t width, int32_t height, int32_t* visible, int32_t* created) {
+  if (!ws || bad_size(width, height)) return fail(RELO_EINVAL, "null workspace or bad size");
+  const size_t S = fuse_set_slots(width, height);
+  Carver c{(char*)ws, 0};
+  c.take<unsigned long long>(S);
+  c.take<unsigned long long>(S);
+  c.take<int32_t>(S);
+  const int32_t* counts = c.take<int32_t>(2);
+  int32_t h[2] = {0, 0};
+  RELO_CUDA(cudaDeviceSynchronize());
+  RELO_CUDA(cudaMemcpy(h, counts, sizeof(h), cudaMemcpyDeviceToHost));
+  if (visible) *visible = h[0];
+  if (created) *created = h[1];
+  return RELO_OK;
+}
+
+relo_status relo_scene_block_count(const relo_scene* scene, int64_t* n_blocks) {
+  if (!scene || !n_blocks) return fail(RELO_EINVAL, "null argument");
+  if (scene->capacity < 1) {
+    *n_blocks = scene->n_blocks;
+    return RELO_OK;
+  }
+  int32_t h[4] = {0, 0, 0, 0};
+  RELO_CUDA(cudaDeviceSynchronize());
+  RELO_CUDA(cudaMemcpy(h, scene->d_counters, sizeof(h), cudaMemcpyDeviceToHost));
+  *n_blocks = std::min<int64_t>(h[0], scene->capacity);
+  if (h[2] != RELO_OK) return fail(h[2], "fusion ran out of blocks, chain entries or its per-frame block set");
+  return RELO_OK;
+}
+
+relo_status relo_scene_export(const relo_scene* scene, int32_t* coords, float* tsdf, uint8_t* rgba, uint16_t* weight,
+                              int64_t capacity, int64_t* n_out) {
+  if (!scene || !n_out) return fail(RELO_EINVAL, "null argument");
+  if (scene->capacity < 1) return fail(RELO_EINVAL, "scene was not created for fusion");
+  int64_t n = 0;
+  relo_status st = relo_scene_block_count(scene, &n);
+  if (st != RELO_OK && st != RELO_ENOMEM) return st;
+  *n_out = n;
+  if (capacity < n) return fail(RELO_EINVAL, "capacity smaller than the block count");
+  if (n == 0) return st;
+  std::vector<int4> c4((size_t)n);
+  RELO_CUDA(cudaMemcpy(c4.data(), scene->d_coords, (size_t)n * sizeof(int4), cudaMemcpyDeviceToHost));
+  if (coords)
+    for (int64_t b = 0; b < n; ++b) {
+      coords[3 * b] = c4[b].x;
+      coords[3 * b + 1] = c4[b].y;
+      coords[3 * b + 2] = c4[b].z;
+    }
+  const size_t nv = (size_t)n * kVoxelsPerBlock;
+  if (tsdf) RELO_CUDA(cudaMemcpy(tsdf, scene->d_tsdf, nv * sizeof(float), cudaMemcpyDeviceToHost));
+  if (rgba) RELO_CUDA(cudaMemcpy(rgba, scene->d_rgba, nv * 4, cudaMemcpyDeviceToHost));
+  if (weight) RELO_CUDA(cudaMemcpy(weight, scene->d_weight, nv * sizeof(uint16_t), cudaMemcpyDeviceToHost));
+  return st;
 }
 
 relo_status relo_scene_use_grid(relo_scene* s, int32_t enable) {

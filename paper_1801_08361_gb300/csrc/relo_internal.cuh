@@ -416,6 +416,34 @@ cudaError_t launch_top_modes(const float* modes, const uint8_t* n_modes, int n_l
 // Helpers for ray jobs
 RayJob make_ray_job(const SceneView& sv, const relo_intrinsics& in, const double* pose_host);
 
+// TSDF fusion of one frame into a growing scene (fusion.cu).
+struct FuseJob {
+  int4* buckets;
+  int4* excess;
+  float* tsdf;
+  uint32_t* rgba;
+  uint16_t* weight;
+  int4* coords;                 // [capacity] block coordinates (w unused)
+  int32_t* counters;            // [0] blocks in use, [1] excess entries in use
+  int32_t* status;              // RELO_OK, or RELO_ENOMEM once the pool, the chain or the set ran out
+  uint32_t bucket_mask;
+  int32_t capacity, max_weight;
+  const uint16_t* depth;        // frame [H][W] mm
+  const uint32_t* frame_rgba;   // frame [H][W] or null
+  int32_t W, H;
+  float fx, fy, cx, cy, dmin, dmax;
+  float R[9], t[3];             // camera -> scene
+  float voxel, mu;
+  unsigned long long* set;      // per-frame block set, set_mask + 1 slots
+  uint32_t set_mask;
+  unsigned long long* new_keys; // set_mask + 1
+  int32_t* visible;             // set_mask + 1 block indices
+  int32_t* n_visible;           // n_visible[0], then n_new
+  int32_t* n_new;
+};
+cudaError_t launch_fuse_frame(const FuseJob& j, cudaStream_t s);
+cudaError_t launch_fuse_init(float* tsdf, int64_t n, cudaStream_t s);
+
 }  // namespace relo
 
 // Opaque handles (C ABI)
@@ -427,6 +455,12 @@ struct relo_scene {
   void* d_rgba;
   void* d_grid;
   int64_t n_blocks;
+  // scenes that grow by fusion (relo_create_fusion_scene): capacity > 0
+  int64_t capacity;
+  void* d_weight;      // uint16 [capacity][512]
+  void* d_coords;      // int4 [capacity]
+  void* d_counters;    // int32 [4]: blocks in use, excess entries in use, status, pad
+  int32_t max_weight;
 };
 
 struct relo_forest {
