@@ -78,6 +78,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fusion-frames", type=int, default=96, help="frames of the TSDF fusion section (0: skip)")
+    ap.add_argument("--profile-fusion", type=int, default=0, help="(ncu) fuse this many frames and exit, no JSON")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the launch schedule with relo_batch_autotune (default: the default schedule, "
                          "which the tuner matches within noise on this workload)")
@@ -285,6 +286,11 @@ def run_ours(args):
 
     world, blocks, intr, train, nodes = build_workload()
     scene = B.Scene(blocks, 20)
+    if args.profile_fusion:
+        # profiler runs of the fusion kernels: the frames sit in an NVTX range named "fusion"
+        args.fusion_frames = args.profile_fusion
+        fusion_section(args, B, synth, torch, dev, scene, world, intr, train, nvtx="fusion", capacity=1 << 18)
+        return 0
     forest = B.Forest(nodes, max_modes=MAX_MODES)
     # relocaliser training on the GPU: noisy renders along the trajectory, stride 2
     B.forest_train_begin(forest, B.train_params(capacity=CAPACITY, stride=2, seed=7))
@@ -538,7 +544,7 @@ FUSION_CAPACITY = 1 << 20          # blocks (5.2 GB of tsdf, colour and weights)
 FUSION_BYTES_PER_VOXEL = 2 * (4 + 4 + 2)   # tsdf, colour, weight: read and written
 
 
-def fusion_section(args, B, synth, torch, dev, scene, world, intr, train):
+def fusion_section(args, B, synth, torch, dev, scene, world, intr, train, nvtx=None, capacity=FUSION_CAPACITY):
     n = args.fusion_frames
     poses = synth.query_poses(world, train, n, seed=4242)
     depth = torch.zeros((n, H, W), dtype=torch.int16, device=dev)
@@ -546,27 +552,37 @@ def fusion_section(args, B, synth, torch, dev, scene, world, intr, train):
     noise = torch.from_numpy(np.stack([synth.depth_noise(H, W, 5000 + k) for k in range(n)])).to(dev)
     ws = torch.empty(B.raycast_views_workspace_size(n), dtype=torch.uint8, device=dev)
     B.raycast_views(scene, intr, poses, depth, rgba, noise_dev=noise, workspace_dev=ws)
-    fs = B.FusionScene(FUSION_CAPACITY, synth.VOXEL_SIZE, synth.TRUNCATION, log2_buckets=20)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ms, vis, created, gbs = [], [], 0, []
-    for k in range(n):
-        e0.record()
-        fs.fuse(intr, poses[k], depth[k], rgba[k])
-        e1.record()
-        v, c = fs.last_frame_stats(intr)          # synchronises after the end event
-        t = e0.elapsed_time(e1)
-        ms.append(t)
-        vis.append(v)
-        created += c
-        gbs.append((v * 512 * FUSION_BYTES_PER_VOXEL + H * W * 6) / (t / 1000.0) / 1e9)
-    steady = slice(n // 4, n)                     # after the first quarter most blocks exist
+    if nvtx:
+        torch.cuda.synchronize()
+        scene.__del__()                           # profiler runs keep little on the device
+    fs = B.FusionScene(capacity, synth.VOXEL_SIZE, synth.TRUNCATION, log2_buckets=20)
+    wsf = torch.empty(B.fuse_workspace_size(W, H), dtype=torch.uint8, device=dev)
+    # two timed regions, frames back to back on the stream: the first quarter (most blocks are
+    # created there) and the rest (mostly updates of existing blocks)
+    q = max(1, n // 4)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    updates = [0]
+    if nvtx:
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push(nvtx)
+    for lo, hi, a in ((0, q, 0), (q, n, 2)):
+        ev[a].record()
+        for k in range(lo, hi):
+            fs.fuse(intr, poses[k], depth[k], rgba[k], workspace_dev=wsf)
+        ev[a + 1].record()
+        updates.append(fs.block_updates())        # synchronises after the region's end event
+    if nvtx:
+        torch.cuda.nvtx.range_pop()
+    ms_first, ms_rest = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
     peak, kind = measured_peaks()
-    g = float(np.mean(gbs[steady]))
-    return {"frames": n, "size": f"{W}x{H}", "ms_per_frame": float(np.mean(ms)),
-            "frames_per_s": 1000.0 * n / float(np.sum(ms)), "steady_ms_per_frame": float(np.mean(ms[steady])),
-            "blocks": fs.block_count(), "blocks_created": created, "visible_blocks_mean": float(np.mean(vis)),
+    upd_rest = updates[2] - updates[1]
+    steady_bytes = upd_rest * 512 * FUSION_BYTES_PER_VOXEL + (n - q) * H * W * 6
+    g = steady_bytes / (ms_rest / 1000.0) / 1e9
+    return {"frames": n, "size": f"{W}x{H}", "ms_per_frame": (ms_first + ms_rest) / n,
+            "frames_per_s": 1000.0 * n / (ms_first + ms_rest), "steady_ms_per_frame": ms_rest / (n - q),
+            "blocks": fs.block_count(), "block_updates_per_frame": updates[2] / n,
             "roofline": {"bound": "hbm", "achieved": g, "peak": peak, "unit": "GB/s", "frac": g / peak,
-                         "peak_source": kind,
+                         "peak_source": kind, "region": f"frames {q}..{n - 1}",
                          "bytes": "updated blocks x 512 voxels x 20 B (tsdf, colour, weight read and written) "
                                   "+ 6 B per pixel (depth, colour)"}}
 

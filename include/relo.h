@@ -175,6 +175,9 @@ relo_status relo_fuse_frame(relo_scene* scene, const relo_intrinsics* intr, cons
  * it created.  Synchronises the device.  Errors: RELO_EINVAL (null workspace, bad size). */
 relo_status relo_fuse_stats(const void* workspace_dev, int32_t width, int32_t height, int32_t* visible,
                             int32_t* created);
+/* Block updates (blocks updated, summed over the frames fused so far).  Synchronises the device.
+ * Errors: RELO_EINVAL (null, not a fusion scene). */
+relo_status relo_scene_fusion_updates(const relo_scene* scene, uint64_t* updates);
 /* Blocks in the scene (synchronises the device).  Returns RELO_ENOMEM if a fusion ran out of room. */
 relo_status relo_scene_block_count(const relo_scene* scene, int64_t* n_blocks);
 /* Copies a fusion scene's blocks to host arrays of at least capacity blocks (any may be NULL):

@@ -93,6 +93,7 @@ _SIGS = {
                                 ctypes.c_size_t, c_vp]),
     "relo_scene_block_count": (c_i32, [c_vp, ctypes.POINTER(c_i64)]),
     "relo_fuse_stats": (c_i32, [c_vp, c_i32, c_i32, ctypes.POINTER(c_i32), ctypes.POINTER(c_i32)]),
+    "relo_scene_fusion_updates": (c_i32, [c_vp, ctypes.POINTER(c_u64)]),
     "relo_scene_export": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(c_i64)]),
     "relo_scene_lookup": (c_i32, [c_vp, c_vp, c_i64, c_vp, c_vp]),
     "relo_scene_use_grid": (c_i32, [c_vp, c_i32]),
@@ -256,6 +257,10 @@ class Scene:
             self.handle = None
 
 
+def fuse_workspace_size(width, height) -> int:
+    return int(lib().relo_fuse_workspace_size(int(width), int(height)))
+
+
 class FusionScene(Scene):
     """A scene that grows by TSDF fusion (relo_create_fusion_scene / relo_fuse_frame); raycasts,
     verification and global rendering take it like any scene."""
@@ -271,7 +276,7 @@ class FusionScene(Scene):
     def fuse(self, intr, pose, depth_dev, rgba_dev=None, workspace_dev=None, stream=None):
         """Fuse one frame (depth u16 mm [H][W] as int16 bits, rgba u8 [H][W][4] or None)."""
         if workspace_dev is None:
-            need = int(lib().relo_fuse_workspace_size(intr.width, intr.height))
+            need = fuse_workspace_size(intr.width, intr.height)
             if self._ws is None or self._ws.numel() < need:
                 import torch
                 self._ws = torch.empty(need, dtype=torch.uint8, device=depth_dev.device)
@@ -288,6 +293,12 @@ class FusionScene(Scene):
         vis, new = c_i32(), c_i32()
         _check(lib().relo_fuse_stats(_ptr(ws), intr.width, intr.height, ctypes.byref(vis), ctypes.byref(new)))
         return int(vis.value), int(new.value)
+
+    def block_updates(self) -> int:
+        """Blocks updated, summed over every frame fused so far."""
+        n = c_u64()
+        _check(lib().relo_scene_fusion_updates(self.handle, ctypes.byref(n)))
+        return int(n.value)
 
     def block_count(self) -> int:
         n = c_i64()

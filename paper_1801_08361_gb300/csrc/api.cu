@@ -416,7 +416,7 @@ relo_status relo_create_fusion_scene(int64_t capacity, double voxel, double mu, 
   if (e == cudaSuccess) e = cudaMalloc(&s->d_rgba, nv * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&s->d_weight, nv * sizeof(uint16_t));
   if (e == cudaSuccess) e = cudaMalloc(&s->d_coords, (size_t)capacity * sizeof(int4));
-  if (e == cudaSuccess) e = cudaMalloc(&s->d_counters, 4 * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_counters, 4 * sizeof(int32_t) + sizeof(unsigned long long));
   if (e != cudaSuccess) {
     cudaGetLastError();
     relo_destroy_scene(s);
@@ -428,7 +428,7 @@ relo_status relo_create_fusion_scene(int64_t capacity, double voxel, double mu, 
   if (e == cudaSuccess) e = cudaMemset(s->d_excess, 0xFF, (size_t)capacity * sizeof(int4));
   if (e == cudaSuccess) e = cudaMemset(s->d_rgba, 0, nv * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(s->d_weight, 0, nv * sizeof(uint16_t));
-  if (e == cudaSuccess) e = cudaMemset(s->d_counters, 0, 4 * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemset(s->d_counters, 0, 4 * sizeof(int32_t) + sizeof(unsigned long long));
   if (e == cudaSuccess) e = launch_fuse_init((float*)s->d_tsdf, (int64_t)nv, nullptr);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -464,7 +464,7 @@ size_t fuse_set_slots(int32_t width, int32_t height) {
 size_t relo_fuse_workspace_size(int32_t width, int32_t height) {
   if (bad_size(width, height)) return 0;
   const size_t S = fuse_set_slots(width, height);
-  return S * 8 + 256 + S * 8 + 256 + S * 4 + 256 + 256;
+  return S * 8 + 256 + S * 8 + 256 + S * 8 + 256 + S * 4 + 256 + 256;
 }
 
 relo_status relo_fuse_frame(relo_scene* scene, const relo_intrinsics* intr, const double* pose, const uint16_t* depth,
@@ -480,9 +480,11 @@ relo_status relo_fuse_frame(relo_scene* scene, const relo_intrinsics* intr, cons
   FuseJob j{};
   j.set = c.take<unsigned long long>(S);
   j.new_keys = c.take<unsigned long long>(S);
+  j.keys = c.take<unsigned long long>(S);
   j.visible = c.take<int32_t>(S);
-  j.n_visible = c.take<int32_t>(2);
+  j.n_visible = c.take<int32_t>(3);
   j.n_new = j.n_visible + 1;
+  j.n_keys = j.n_visible + 2;
   j.set_mask = (uint32_t)(S - 1);
   j.buckets = (int4*)scene->d_buckets;
   j.excess = (int4*)scene->d_excess;
@@ -492,6 +494,7 @@ relo_status relo_fuse_frame(relo_scene* scene, const relo_intrinsics* intr, cons
   j.coords = (int4*)scene->d_coords;
   j.counters = (int32_t*)scene->d_counters;
   j.status = j.counters + 2;
+  j.updates = (unsigned long long*)(j.counters + 4);
   j.bucket_mask = scene->view.mask;
   j.capacity = (int32_t)scene->capacity;
   j.max_weight = scene->max_weight;
@@ -521,8 +524,9 @@ relo_status relo_fuse_stats(const void* ws, int32_t width, int32_t height, int32
   Carver c{(char*)ws, 0};
   c.take<unsigned long long>(S);
   c.take<unsigned long long>(S);
+  c.take<unsigned long long>(S);
   c.take<int32_t>(S);
-  const int32_t* counts = c.take<int32_t>(2);
+  const int32_t* counts = c.take<int32_t>(3);
   int32_t h[2] = {0, 0};
   RELO_CUDA(cudaDeviceSynchronize());
   RELO_CUDA(cudaMemcpy(h, counts, sizeof(h), cudaMemcpyDeviceToHost));
@@ -542,6 +546,15 @@ relo_status relo_scene_block_count(const relo_scene* scene, int64_t* n_blocks) {
   RELO_CUDA(cudaMemcpy(h, scene->d_counters, sizeof(h), cudaMemcpyDeviceToHost));
   *n_blocks = std::min<int64_t>(h[0], scene->capacity);
   if (h[2] != RELO_OK) return fail(h[2], "fusion ran out of blocks, chain entries or its per-frame block set");
+  return RELO_OK;
+}
+
+relo_status relo_scene_fusion_updates(const relo_scene* scene, uint64_t* updates) {
+  if (!scene || !updates) return fail(RELO_EINVAL, "null argument");
+  if (scene->capacity < 1) return fail(RELO_EINVAL, "scene was not created for fusion");
+  RELO_CUDA(cudaDeviceSynchronize());
+  RELO_CUDA(cudaMemcpy(updates, (const char*)scene->d_counters + 4 * sizeof(int32_t), sizeof(uint64_t),
+                       cudaMemcpyDeviceToHost));
   return RELO_OK;
 }
 

@@ -49,13 +49,18 @@ __device__ __forceinline__ uint32_t key_slot(unsigned long long k) {
   return (uint32_t)k;
 }
 
-// Inserts key into the frame's set; false if the set is full.
-__device__ __forceinline__ bool set_insert(unsigned long long* set, uint32_t mask, unsigned long long key) {
-  uint32_t i = key_slot(key) & mask;
-  for (uint32_t probe = 0; probe <= mask; ++probe) {
-    const unsigned long long prev = atomicCAS(&set[i], 0ull, key);
-    if (prev == 0ull || prev == key) return true;
-    i = (i + 1) & mask;
+// Inserts key into the frame's set; the thread that stores it first also appends it to the
+// frame's key list.  False if the set is full.
+__device__ __forceinline__ bool set_insert(const FuseJob& j, unsigned long long key) {
+  uint32_t i = key_slot(key) & j.set_mask;
+  for (uint32_t probe = 0; probe <= j.set_mask; ++probe) {
+    const unsigned long long prev = atomicCAS(&j.set[i], 0ull, key);
+    if (prev == 0ull) {
+      j.keys[atomicAdd(j.n_keys, 1)] = key;
+      return true;
+    }
+    if (prev == key) return true;
+    i = (i + 1) & j.set_mask;
   }
   return false;
 }
@@ -96,7 +101,7 @@ __global__ void __launch_bounds__(256) fuse_mark_kernel(const FuseJob j) {
     const unsigned long long key = block_key(b[0], b[1], b[2]);
     if (key == last) continue;  // consecutive samples in one block: one insertion
     last = key;
-    if (!set_insert(j.set, j.set_mask, key)) set_status(j.status, RELO_ENOMEM);
+    if (!set_insert(j, key)) set_status(j.status, RELO_ENOMEM);
   }
 }
 
@@ -113,9 +118,9 @@ __device__ __forceinline__ int find_block(const FuseJob& j, int x, int y, int z)
 }
 
 __global__ void __launch_bounds__(256) fuse_classify_kernel(const FuseJob j) {
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= j.set_mask; i += gridDim.x * blockDim.x) {
-    const unsigned long long key = j.set[i];
-    if (key == 0ull) continue;
+  const int n_keys = *j.n_keys;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_keys; i += gridDim.x * blockDim.x) {
+    const unsigned long long key = j.keys[i];
     int x, y, z;
     key_coords(key, &x, &y, &z);
     const int b = find_block(j, x, y, z);
@@ -163,6 +168,7 @@ __global__ void __launch_bounds__(256) fuse_insert_kernel(const FuseJob j) {
 __global__ void __launch_bounds__(512) fuse_update_kernel(const FuseJob j) {
   const int n_vis = *j.n_visible;
   const int vi = threadIdx.x;
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(j.updates, (unsigned long long)n_vis);
   for (int q = blockIdx.x; q < n_vis; q += gridDim.x) {
     const int b = j.visible[q];
     const int4 bc = j.coords[b];
@@ -178,7 +184,7 @@ __global__ void __launch_bounds__(512) fuse_update_kernel(const FuseJob j) {
     const float vf = __fadd_rn(__fmul_rn(j.fy, __fdiv_rn(qy, qz)), j.cy);
     const float fu = floorf(__fadd_rn(uf, 0.5f)), fv = floorf(__fadd_rn(vf, 0.5f));
     if (!(fu >= 0.0f && fu < (float)j.W && fv >= 0.0f && fv < (float)j.H)) continue;
-    const int64_t pix = (int64_t)fv * j.W + (int64_t)fu;
+    const int pix = (int)fv * j.W + (int)fu;  // 32-bit: 64-bit float conversions run on the FP64 pipe
     const uint16_t Dm = j.depth[pix];
     if (Dm == 0) continue;
     const float dm = __fmul_rn((float)Dm, 0.001f);
@@ -233,7 +239,7 @@ cudaError_t launch_fuse_init(float* tsdf, int64_t n, cudaStream_t s) {
 cudaError_t launch_fuse_frame(const FuseJob& j, cudaStream_t s) {
   const int64_t n_pix = (int64_t)j.W * j.H;
   cudaError_t e = cudaMemsetAsync(j.set, 0, ((size_t)j.set_mask + 1) * sizeof(unsigned long long), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(j.n_visible, 0, 2 * sizeof(int32_t), s);  // n_visible, n_new
+  if (e == cudaSuccess) e = cudaMemsetAsync(j.n_visible, 0, 3 * sizeof(int32_t), s);  // n_visible, n_new, n_keys
   if (e != cudaSuccess) return e;
   fuse_mark_kernel<<<(unsigned)((n_pix + 255) / 256), 256, 0, s>>>(j);
   fuse_classify_kernel<<<grid_for((int64_t)j.set_mask + 1, 256), 256, 0, s>>>(j);

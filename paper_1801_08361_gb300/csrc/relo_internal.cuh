@@ -437,9 +437,12 @@ struct FuseJob {
   unsigned long long* set;      // per-frame block set, set_mask + 1 slots
   uint32_t set_mask;
   unsigned long long* new_keys; // set_mask + 1
+  unsigned long long* keys;     // set_mask + 1: the frame's distinct block keys, in insertion order
   int32_t* visible;             // set_mask + 1 block indices
-  int32_t* n_visible;           // n_visible[0], then n_new
+  int32_t* n_visible;           // n_visible[0], then n_new, then n_keys
   int32_t* n_new;
+  int32_t* n_keys;
+  unsigned long long* updates;  // the scene's running count of block updates
 };
 cudaError_t launch_fuse_frame(const FuseJob& j, cudaStream_t s);
 cudaError_t launch_fuse_init(float* tsdf, int64_t n, cudaStream_t s);
@@ -459,7 +462,7 @@ struct relo_scene {
   int64_t capacity;
   void* d_weight;      // uint16 [capacity][512]
   void* d_coords;      // int4 [capacity]
-  void* d_counters;    // int32 [4]: blocks in use, excess entries in use, status, pad
+  void* d_counters;    // int32 [4]: blocks in use, excess entries in use, status, pad; then uint64 block updates
   int32_t max_weight;
 };
 

@@ -110,10 +110,12 @@ def test_bad_arguments(frames):
 def test_frame_statistics_count_the_blocks(frames):
     intr, fr = frames[160]
     g = B.FusionScene(1 << 16, VOX, MU, log2_buckets=14)
-    created = 0
+    created = updated = 0
     for P, d, c in fr:
         g.fuse(intr, P, torch.from_numpy(d.view(np.int16)).to(DEV), torch.from_numpy(c).to(DEV))
         vis, new = g.last_frame_stats(intr)
         assert vis >= new >= 0 and vis > 0
         created += new
+        updated += vis
     assert created == g.block_count()
+    assert updated == g.block_updates()
