@@ -2,7 +2,7 @@
 verifier's confusion counts add up per pair, every verified sample lands in the pair's clusters,
 the safety margin is the largest cluster minus the largest incorrect one, scene 0 is the gauge,
 and where every confident pair's largest cluster is correct the optimised global poses render
-the global map like the true poses."""
+the global map like the true poses, and so does the single model fused with them."""
 import pytest
 import torch
 
@@ -36,3 +36,5 @@ def test_pose_graph_and_global_map(report):
         for s in pg:
             assert s["rot_deg"] < 5.0 and s["trans_m"] < 0.10
         assert report["render"]["median_abs_diff_mm"] <= 50
+        f = report["fused"]
+        assert f["frames"] > 0 and f["blocks"] > 0 and f["median_abs_diff_mm"] <= 50
