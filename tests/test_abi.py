@@ -34,3 +34,52 @@ def test_library_loads_and_exports_every_declared_function():
     missing = [n for n in sorted(_declared()) if not hasattr(L, n)]
     assert not missing, missing
     assert B.lib() is not None
+
+
+C_CLIENT = r"""
+#include <stdio.h>
+#include <string.h>
+#include "relo.h"
+
+int main(void) {
+  relo_pose_graph* g = NULL;
+  if (relo_pose_graph_create(0, &g) != RELO_EINVAL) return 1;      /* bad size rejected */
+  if (relo_pose_graph_create(3, &g) != RELO_OK || !g) return 2;
+  double T[16] = {1, 0, 0, 0.5, 0, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1};
+  int32_t size = 0;
+  if (relo_pose_graph_add_sample(g, 0, 1, T, &size) != RELO_OK || size != 1) return 3;
+  if (relo_pose_graph_add_sample(g, 1, 0, T, &size) != RELO_OK || size != 1) return 4;  /* inverse: other cluster */
+  T[3] = 0.52;
+  if (relo_pose_graph_add_sample(g, 0, 1, T, &size) != RELO_OK || size != 2) return 5;
+  double poses[3 * 16];
+  int32_t in_graph[3];
+  double eps = -1;
+  if (relo_pose_graph_optimise(g, poses, in_graph, &eps) != RELO_OK) return 6;
+  if (!in_graph[0] || !in_graph[1] || in_graph[2]) return 7;
+  if (poses[16 + 3] < 0.509 || poses[16 + 3] > 0.511) return 8;     /* the blend of 0.50 and 0.52 */
+  if (relo_pose_graph_add_sample(g, 1, 1, T, NULL) != RELO_EINVAL) return 9;
+  relo_pose_graph_destroy(g);
+  relo_schedule s;
+  memset(&s, 0, sizeof s);
+  if (relo_batch_set_schedule(NULL, &s) != RELO_EINVAL || strlen(relo_last_error()) == 0) return 10;
+  printf("ok\n");
+  return 0;
+}
+"""
+
+
+def test_a_c_program_uses_the_abi(tmp_path):
+    """The header is plain C99 and the library links into a C program: host-only calls (the pose
+    graph, argument errors and relo_last_error) behave as documented without a GPU."""
+    import subprocess
+    build.build()
+    src = tmp_path / "client.c"
+    src.write_text(C_CLIENT)
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(B.LIB_PATH)
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                           "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                           "-L", libdir, "-lrelo", "-Wl,-rpath," + libdir])
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, (out.returncode, out.stderr)
+    assert out.stdout.strip() == "ok"

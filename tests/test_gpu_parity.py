@@ -6,7 +6,6 @@ reservoirs bit-exact; raycast depth within 1 mm on >= 99.9 % of co-valid pixels 
 against FP64); energies within 1e-5 relative; poses within 1e-4 m / 1e-4 (rotation entries);
 survivor sets exact except at near-ties (oracle cut margin below 1e-5 relative), which the round
 test resolves by teacher forcing."""
-import math
 
 import numpy as np
 import pytest

@@ -2,7 +2,6 @@
 against the FP64 oracle: forward output, loss and per-layer gradients on the same operands
 (relative L2 <= 1e-2 forward, gradient cosine >= 0.999 per layer), a short training run, and the
 learned RANSAC against the oracle's RANSAC on the same cell grid."""
-import math
 
 import numpy as np
 import pytest

@@ -2,7 +2,6 @@
 brute-force loop over hand-made depth images (ties to the lower index, no hit = +inf); one scene
 reduces to its own raycast; and a room cut into two overlapping pieces, each sampled in its own
 random frame and placed by its true global pose, renders like the whole room."""
-import math
 
 import numpy as np
 import pytest

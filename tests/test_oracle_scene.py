@@ -4,7 +4,6 @@ and constant or linear colour fields that trilinear interpolation reproduces exa
 import math
 
 import numpy as np
-import pytest
 
 import oracle
 from paper_1801_08361_gb300 import synth
