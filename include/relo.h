@@ -104,7 +104,8 @@ relo_status relo_scene_use_grid(relo_scene* scene, int32_t enable);
  * normal per pixel, float32 [H][W]) 1.5 mm * z^2 * n is added first (the quadratic axial noise
  * model of the appendix on depth sensors).  Colour (rgba_dev may be NULL) is the trilinear
  * voxel colour at the hit, rounded half up.  Computed in FP32.
- * Errors: RELO_EINVAL (null scene/intrinsics/pose/depth, width or height outside [1, 16384]).
+ * Errors: RELO_EINVAL (null scene/intrinsics/pose/depth, width or height outside [1, 16384], a pose
+ * entry that is not finite).
  * ------------------------------------------------------------------------------------- */
 relo_status relo_raycast_view(const relo_scene* scene, const relo_intrinsics* intr, const double pose_c2s[16],
                               const float* noise_dev, uint16_t* depth_dev, uint8_t* rgba_dev, relo_stream stream);
@@ -129,7 +130,8 @@ relo_status relo_raycast_views(const relo_scene* scene, const relo_intrinsics* i
  * (nullable, int8 [H][W]) receives the winning index or -1.  err_dev (nullable, device int32)
  * is set to RELO_EDEVICE if a hash walk exceeded its bound.  One launch; the descriptors go
  * through workspace_dev (256-byte aligned, relo_render_global_workspace_size(n) bytes) as for
- * relo_raycast_views.  Errors: RELO_EINVAL (null, n outside [1, 64], intrinsics, workspace). */
+ * relo_raycast_views.  Errors: RELO_EINVAL (null, n outside [1, 64], intrinsics, a pose entry that is
+ * not finite, workspace). */
 size_t relo_render_global_workspace_size(int32_t n_scenes);
 relo_status relo_render_global(const relo_scene* const* scenes, const double* global_poses_host, int32_t n_scenes,
                                const relo_intrinsics* intr, const double pose_global_host[16], uint16_t* depth_dev,
@@ -167,7 +169,8 @@ size_t relo_fuse_workspace_size(int32_t width, int32_t height);
  * (camera -> scene), asynchronously on the stream, in four launches.  If the block pool, the
  * chain entries (capacity_blocks) or the frame's block set (relo_fuse_workspace_size) run out,
  * the frame is fused into what fits and the scene records RELO_ENOMEM (relo_scene_block_count).
- * Errors: RELO_EINVAL (null, a scene not created for fusion, intrinsics, workspace). */
+ * Errors: RELO_EINVAL (null, a scene not created for fusion, intrinsics, a pose entry that is not
+ * finite, workspace). */
 relo_status relo_fuse_frame(relo_scene* scene, const relo_intrinsics* intr, const double pose_c2s[16],
                             const uint16_t* depth_dev, const uint8_t* rgba_dev, void* workspace_dev,
                             size_t workspace_bytes, relo_stream stream);
@@ -367,6 +370,16 @@ int64_t relo_regressor_param_count(void);
 relo_status relo_create_regressor(const float* params_host, uint64_t seed, const double origin[3],
                                   relo_regressor** out);
 void relo_destroy_regressor(relo_regressor* regressor);
+/* Training checkpoint (resume mid-run): the master parameters and Adam's moments m and v (each
+ * relo_regressor_param_count() floats; NULL skips one) and Adam's step count.  get synchronises
+ * the device; set restores all four, re-derives the BF16 weights the kernels multiply and
+ * synchronises, so that training continued from a restored state (on a regressor created with the
+ * same origin) gives bit for bit the parameters of uninterrupted training.
+ * Errors: RELO_EINVAL (null regressor; for set, a null array or step outside [0, 2^31)). */
+relo_status relo_regressor_get_state(const relo_regressor* regressor, float* params_host, float* m_host,
+                                     float* v_host, int64_t* step);
+relo_status relo_regressor_set_state(relo_regressor* regressor, const float* params_host, const float* m_host,
+                                     const float* v_host, int64_t step);
 /* Copies of the master parameters and of the last computed gradients (either may be NULL). */
 relo_status relo_regressor_get_params(const relo_regressor* regressor, float* params_host, float* grads_host);
 /* Workspace bytes for n images of width x height (training != 0: with the backward pass). */
@@ -431,7 +444,11 @@ typedef struct relo_attempt {
  * Workspace bytes for a batch (includes the query images and per-attempt RANSAC scratch). */
 size_t relo_batch_workspace_size(const relo_attempt* attempts_host, int32_t n, const relo_ransac_params* p);
 
-/* Run n attempts.  results_host receives n results (the call synchronises the stream).
+/* Run n attempts.  results_host receives n results (the call synchronises the stream).  A bad
+ * attempt is one with a null scene, neither forest nor regressor, bad intrinsics, a pose_b entry
+ * that is not finite, n_hyps outside [0, 4096], or learned attempts that differ in regressor or
+ * image size.  An attempt's status is RELO_EDEVICE when a bounded hash walk of its query or
+ * verification raycast, or of its RANSAC, gave up (a corrupted scene table).
  * Errors: RELO_EINVAL (n < 1, bad attempt, workspace too small), RELO_ECUDA. */
 relo_status relo_relocalise_batch(const relo_attempt* attempts_host, int32_t n, const relo_ransac_params* p,
                                   void* workspace_dev, size_t workspace_bytes, relo_pose_result* results_host,
@@ -591,6 +608,20 @@ relo_status relo_pose_graph_cluster_blend(const relo_pose_graph* graph, int32_t 
  * receives their sizes in creation order. */
 int32_t relo_pose_graph_cluster_count(const relo_pose_graph* graph, int32_t a, int32_t b, int32_t* sizes,
                                       int32_t capacity);
+
+/* ---------------------------------------------------------------------------------------
+ * Fault injection, for tests of the error paths (no counterpart in the paper).  Nothing here
+ * faults, traps or hangs a GPU: the failures are made on the host, and corrupted data is caught
+ * by the kernels' bounded loops, which report RELO_EDEVICE.
+ * ------------------------------------------------------------------------------------- */
+/* The next n device allocations made by the library fail as if the device were out of memory
+ * (creation calls then return RELO_ENOMEM); n <= 0 cancels. */
+void relo_debug_fail_allocations(int32_t n);
+/* Makes every hash chain of the scene end in a cycle (each chain entry links to itself; empty
+ * links point at entry 0).  A hash walk for a block that is not at its bucket's head then runs into
+ * its bound: attempts that raycast the scene through the hash (relo_scene_use_grid(scene, 0))
+ * report RELO_EDEVICE.  Synchronous.  Errors: RELO_EINVAL (null scene). */
+relo_status relo_debug_corrupt_scene(relo_scene* scene);
 
 #ifdef __cplusplus
 }

@@ -152,6 +152,10 @@ _SIGS = {
     "relo_batch_replay": (c_i32, [c_vp, c_vp]),
     "relo_batch_attempt_images": (c_i32, [c_vp, c_i32, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp),
                                           ctypes.POINTER(c_vp)]),
+    "relo_debug_fail_allocations": (None, [c_i32]),
+    "relo_debug_corrupt_scene": (c_i32, [c_vp]),
+    "relo_regressor_get_state": (c_i32, [c_vp, c_vp, c_vp, c_vp, ctypes.POINTER(c_i64)]),
+    "relo_regressor_set_state": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64]),
     "relo_render_global_workspace_size": (ctypes.c_size_t, [c_i32]),
     "relo_render_global": (c_i32, [ctypes.POINTER(c_vp), ctypes.POINTER(c_dbl), c_i32, ctypes.POINTER(Intrinsics),
                                    ctypes.POINTER(c_dbl), c_vp, c_vp, c_vp, c_vp, c_vp, ctypes.c_size_t, c_vp]),
@@ -625,6 +629,23 @@ class Regressor:
         return g
 
 
+def regressor_state(reg) -> dict:
+    """Training checkpoint: {"params", "m", "v"} float32 arrays and the Adam "step"."""
+    n = regressor_param_count()
+    out = {k: np.empty(n, dtype=np.float32) for k in ("params", "m", "v")}
+    step = c_i64()
+    _check(lib().relo_regressor_get_state(reg.handle, out["params"].ctypes.data, out["m"].ctypes.data,
+                                          out["v"].ctypes.data, ctypes.byref(step)))
+    out["step"] = int(step.value)
+    return out
+
+
+def regressor_set_state(reg, state):
+    a = {k: np.ascontiguousarray(state[k], dtype=np.float32) for k in ("params", "m", "v")}
+    _check(lib().relo_regressor_set_state(reg.handle, a["params"].ctypes.data, a["m"].ctypes.data,
+                                          a["v"].ctypes.data, int(state["step"])))
+
+
 def regressor_workspace_size(n, width, height, training) -> int:
     return int(lib().relo_regressor_workspace_size(int(n), int(width), int(height), 1 if training else 0))
 
@@ -773,3 +794,16 @@ class PoseGraph:
 
     def __del__(self):
         self.close()
+
+
+# Fault injection (tests of the error paths)
+# ------------------------------------------------------------------------------------------------
+
+def debug_fail_allocations(n):
+    """The library's next n device allocations fail (RELO_ENOMEM); 0 cancels."""
+    lib().relo_debug_fail_allocations(int(n))
+
+
+def debug_corrupt_scene(scene):
+    """Every hash chain of the scene ends in a cycle: hash walks hit their bound (RELO_EDEVICE)."""
+    _check(lib().relo_debug_corrupt_scene(scene.handle))

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -20,6 +21,20 @@ using namespace relo;
 static_assert(sizeof(relo_pose_result) == 344, "relo_pose_result layout is part of the ABI");
 static_assert(sizeof(relo_attempt) == 240, "relo_attempt layout is part of the ABI");
 static_assert(sizeof(relo_intrinsics) == 56, "relo_intrinsics layout is part of the ABI");
+
+namespace relo {
+std::atomic<int> g_fail_allocations{0};
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  int n = g_fail_allocations.load();
+  while (n > 0) {
+    if (g_fail_allocations.compare_exchange_weak(n, n - 1)) {
+      *p = nullptr;
+      return cudaErrorMemoryAllocation;
+    }
+  }
+  return cudaMalloc(p, bytes);
+}
+}  // namespace relo
 
 namespace {
 
@@ -41,6 +56,13 @@ relo_status cuda_fail(cudaError_t e, const char* what) {
   } while (0)
 
 bool bad_size(int w, int h) { return w < 1 || h < 1 || w > 16384 || h > 16384; }
+
+// A pose whose rotation or translation holds a NaN or an infinity (rays would march nowhere).
+bool bad_pose(const double* P) {
+  for (int i = 0; i < 12; ++i)
+    if (!std::isfinite(P[i])) return true;
+  return false;
+}
 
 relo_status check_intr(const relo_intrinsics* in) {
   if (!in) return fail(RELO_EINVAL, "intrinsics is null");
@@ -326,6 +348,7 @@ relo_status relo_create_scene(const int32_t* coords, const float* tsdf, const ui
   }
   relo_scene* s = new relo_scene();
   s->n_blocks = n;
+  s->n_excess = (int64_t)excess.size();
   auto cleanup = [&]() {
     cudaFree(s->d_buckets);
     cudaFree(s->d_excess);
@@ -334,17 +357,17 @@ relo_status relo_create_scene(const int32_t* coords, const float* tsdf, const ui
     cudaFree(s->d_grid);
     delete s;
   };
-  if (!grid.empty() && (cudaMalloc(&s->d_grid, grid.size() * 4) != cudaSuccess ||
+  if (!grid.empty() && (relo::dev_malloc((void**)&s->d_grid, grid.size() * 4) != cudaSuccess ||
                         cudaMemcpy(s->d_grid, grid.data(), grid.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)) {
     cudaGetLastError();
     cleanup();
     return fail(RELO_ENOMEM, "device allocation for the scene grid failed");
   }
   const size_t nv = (size_t)std::max<int64_t>(n, 1) * kVoxelsPerBlock;
-  if (cudaMalloc(&s->d_buckets, nb * sizeof(int4)) != cudaSuccess ||
-      cudaMalloc(&s->d_excess, excess.size() * sizeof(int4)) != cudaSuccess ||
-      cudaMalloc(&s->d_tsdf, nv * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&s->d_rgba, nv * sizeof(uint32_t)) != cudaSuccess) {
+  if (relo::dev_malloc((void**)&s->d_buckets, nb * sizeof(int4)) != cudaSuccess ||
+      relo::dev_malloc((void**)&s->d_excess, excess.size() * sizeof(int4)) != cudaSuccess ||
+      relo::dev_malloc((void**)&s->d_tsdf, nv * sizeof(float)) != cudaSuccess ||
+      relo::dev_malloc((void**)&s->d_rgba, nv * sizeof(uint32_t)) != cudaSuccess) {
     cudaGetLastError();
     cleanup();
     return fail(RELO_ENOMEM, "device allocation for the scene failed");
@@ -408,15 +431,16 @@ relo_status relo_create_fusion_scene(int64_t capacity, double voxel, double mu, 
   if (max_weight < 1 || max_weight > 65535) return fail(RELO_EINVAL, "max_weight outside [1, 65535]");
   relo_scene* s = new relo_scene();
   s->capacity = capacity;
+  s->n_excess = capacity;
   s->max_weight = max_weight;
   const size_t nb = (size_t)1 << log2_buckets, nv = (size_t)capacity * kVoxelsPerBlock;
-  cudaError_t e = cudaMalloc(&s->d_buckets, nb * sizeof(int4));
-  if (e == cudaSuccess) e = cudaMalloc(&s->d_excess, (size_t)capacity * sizeof(int4));
-  if (e == cudaSuccess) e = cudaMalloc(&s->d_tsdf, nv * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&s->d_rgba, nv * sizeof(uint32_t));
-  if (e == cudaSuccess) e = cudaMalloc(&s->d_weight, nv * sizeof(uint16_t));
-  if (e == cudaSuccess) e = cudaMalloc(&s->d_coords, (size_t)capacity * sizeof(int4));
-  if (e == cudaSuccess) e = cudaMalloc(&s->d_counters, 4 * sizeof(int32_t) + sizeof(unsigned long long));
+  cudaError_t e = relo::dev_malloc((void**)&s->d_buckets, nb * sizeof(int4));
+  if (e == cudaSuccess) e = relo::dev_malloc((void**)&s->d_excess, (size_t)capacity * sizeof(int4));
+  if (e == cudaSuccess) e = relo::dev_malloc((void**)&s->d_tsdf, nv * sizeof(float));
+  if (e == cudaSuccess) e = relo::dev_malloc((void**)&s->d_rgba, nv * sizeof(uint32_t));
+  if (e == cudaSuccess) e = relo::dev_malloc((void**)&s->d_weight, nv * sizeof(uint16_t));
+  if (e == cudaSuccess) e = relo::dev_malloc((void**)&s->d_coords, (size_t)capacity * sizeof(int4));
+  if (e == cudaSuccess) e = relo::dev_malloc((void**)&s->d_counters, 4 * sizeof(int32_t) + sizeof(unsigned long long));
   if (e != cudaSuccess) {
     cudaGetLastError();
     relo_destroy_scene(s);
@@ -470,6 +494,7 @@ size_t relo_fuse_workspace_size(int32_t width, int32_t height) {
 relo_status relo_fuse_frame(relo_scene* scene, const relo_intrinsics* intr, const double* pose, const uint16_t* depth,
                             const uint8_t* rgba, void* ws, size_t ws_bytes, relo_stream stream) {
   if (!scene || !pose || !depth) return fail(RELO_EINVAL, "null scene, pose or depth");
+  if (bad_pose(pose)) return fail(RELO_EINVAL, "pose is not finite");
   if (scene->capacity < 1) return fail(RELO_EINVAL, "scene was not created for fusion");
   relo_status st = check_intr(intr);
   if (st) return st;
@@ -583,6 +608,24 @@ relo_status relo_scene_export(const relo_scene* scene, int32_t* coords, float* t
   return st;
 }
 
+void relo_debug_fail_allocations(int32_t n) { relo::g_fail_allocations.store(n > 0 ? n : 0); }
+
+relo_status relo_debug_corrupt_scene(relo_scene* scene) {
+  if (!scene || scene->n_excess < 1) return fail(RELO_EINVAL, "null scene");
+  const size_t nb = (size_t)scene->view.mask + 1, ne = (size_t)scene->n_excess;
+  std::vector<int4> buckets(nb), excess(ne);
+  RELO_CUDA(cudaDeviceSynchronize());
+  RELO_CUDA(cudaMemcpy(buckets.data(), scene->d_buckets, nb * sizeof(int4), cudaMemcpyDeviceToHost));
+  RELO_CUDA(cudaMemcpy(excess.data(), scene->d_excess, ne * sizeof(int4), cudaMemcpyDeviceToHost));
+  // every chain ends in a cycle through a self-linked entry (all links stay inside the table)
+  for (int4& e : buckets)
+    if (e.w < 0) e.w = 0;
+  for (size_t i = 0; i < ne; ++i) excess[i].w = (int)i;
+  RELO_CUDA(cudaMemcpy(scene->d_buckets, buckets.data(), nb * sizeof(int4), cudaMemcpyHostToDevice));
+  RELO_CUDA(cudaMemcpy(scene->d_excess, excess.data(), ne * sizeof(int4), cudaMemcpyHostToDevice));
+  return RELO_OK;
+}
+
 relo_status relo_scene_use_grid(relo_scene* s, int32_t enable) {
   if (!s) return fail(RELO_EINVAL, "scene is null");
   s->view.grid = enable ? (const int32_t*)s->d_grid : nullptr;
@@ -602,6 +645,7 @@ relo_status relo_scene_lookup(const relo_scene* scene, const int32_t* keys, int6
 relo_status relo_raycast_view(const relo_scene* scene, const relo_intrinsics* intr, const double pose[16],
                               const float* noise, uint16_t* depth, uint8_t* rgba, relo_stream stream) {
   if (!scene || !pose || !depth) return fail(RELO_EINVAL, "null scene, pose or depth");
+  if (bad_pose(pose)) return fail(RELO_EINVAL, "pose is not finite");
   relo_status st = check_intr(intr);
   if (st) return st;
   RayJob j = make_ray_job(scene->view, *intr, pose);
@@ -621,6 +665,8 @@ relo_status relo_raycast_views(const relo_scene* scene, const relo_intrinsics* i
                                const float* noise, uint16_t* depth, uint8_t* rgba, void* ws, size_t ws_bytes,
                                relo_stream stream) {
   if (!scene || !poses || !depth || n < 1) return fail(RELO_EINVAL, "null scene, poses or depth, or n < 1");
+  for (int k = 0; k < n; ++k)
+    if (bad_pose(poses + 16 * (size_t)k)) return fail(RELO_EINVAL, "a pose is not finite");
   relo_status st = check_intr(intr);
   if (st) return st;
   if (!ws || ((uintptr_t)ws & 255) != 0 || ws_bytes < relo_raycast_views_workspace_size(n))
@@ -653,6 +699,9 @@ relo_status relo_render_global(const relo_scene* const* scenes, const double* gl
                                relo_stream stream) {
   if (!scenes || !global_poses || !pose_global || !depth) return fail(RELO_EINVAL, "null argument");
   if (n_scenes < 1 || n_scenes > kMaxGlobalScenes) return fail(RELO_EINVAL, "n_scenes outside [1, 64]");
+  if (bad_pose(pose_global)) return fail(RELO_EINVAL, "pose is not finite");
+  for (int a = 0; a < n_scenes; ++a)
+    if (bad_pose(global_poses + 16 * (size_t)a)) return fail(RELO_EINVAL, "a global pose is not finite");
   relo_status st = check_intr(intr);
   if (st) return st;
   if (!ws || ((uintptr_t)ws & 255) != 0 || ws_bytes < relo_render_global_workspace_size(n_scenes))
@@ -704,9 +753,9 @@ relo_status relo_create_forest(const void* nodes, int32_t T, int32_t D, const fl
   f->D = D;
   f->M = M;
   const size_t n_modes_bytes = (size_t)T * L, modes_bytes = (size_t)T * L * M * kModeFloats * sizeof(float);
-  if (cudaMalloc(&f->d_nodes, (size_t)T * n_int * 16) != cudaSuccess ||
-      cudaMalloc(&f->d_modes, modes_bytes) != cudaSuccess || cudaMalloc(&f->d_n_modes, n_modes_bytes) != cudaSuccess ||
-      cudaMalloc(&f->d_top, (size_t)T * L * sizeof(float4)) != cudaSuccess) {
+  if (relo::dev_malloc((void**)&f->d_nodes, (size_t)T * n_int * 16) != cudaSuccess ||
+      relo::dev_malloc((void**)&f->d_modes, modes_bytes) != cudaSuccess || relo::dev_malloc((void**)&f->d_n_modes, n_modes_bytes) != cudaSuccess ||
+      relo::dev_malloc((void**)&f->d_top, (size_t)T * L * sizeof(float4)) != cudaSuccess) {
     cudaGetLastError();
     relo_destroy_forest(f);
     return fail(RELO_ENOMEM, "device allocation for the forest failed");
@@ -810,8 +859,8 @@ relo_status relo_forest_train_frame(relo_forest* f, const relo_intrinsics* intr,
   cudaStream_t s = (cudaStream_t)stream;
   uint16_t* d_leaves = nullptr;
   float* d_coords = nullptr;
-  RELO_CUDA(cudaMalloc(&d_leaves, n_pix * T * sizeof(uint16_t)));
-  if (cudaMalloc(&d_coords, (size_t)gw * gh * 3 * sizeof(float)) != cudaSuccess) {
+  RELO_CUDA(relo::dev_malloc((void**)&d_leaves, n_pix * T * sizeof(uint16_t)));
+  if (relo::dev_malloc((void**)&d_coords, (size_t)gw * gh * 3 * sizeof(float)) != cudaSuccess) {
     cudaFree(d_leaves);
     return fail(RELO_ENOMEM, "training scratch");
   }
@@ -876,8 +925,8 @@ relo_status relo_forest_train_finish(relo_forest* f, relo_stream stream) {
   cudaStream_t s = (cudaStream_t)stream;
   float* d_samples = nullptr;
   int32_t* d_count = nullptr;
-  RELO_CUDA(cudaMalloc(&d_samples, L * cap * 3 * sizeof(float)));
-  if (cudaMalloc(&d_count, L * sizeof(int32_t)) != cudaSuccess) {
+  RELO_CUDA(relo::dev_malloc((void**)&d_samples, L * cap * 3 * sizeof(float)));
+  if (relo::dev_malloc((void**)&d_count, L * sizeof(int32_t)) != cudaSuccess) {
     cudaFree(d_samples);
     return fail(RELO_ENOMEM, "training scratch");
   }
@@ -1368,12 +1417,12 @@ relo_status relo_create_regressor(const float* params, uint64_t seed, const doub
       }
     }
   }
-  bool ok = cudaMalloc(&r->d_p, r->n_params * 4) == cudaSuccess && cudaMalloc(&r->d_g, r->n_params * 4) == cudaSuccess &&
-            cudaMalloc(&r->d_m, r->n_params * 4) == cudaSuccess && cudaMalloc(&r->d_v, r->n_params * 4) == cudaSuccess;
+  bool ok = relo::dev_malloc((void**)&r->d_p, r->n_params * 4) == cudaSuccess && relo::dev_malloc((void**)&r->d_g, r->n_params * 4) == cudaSuccess &&
+            relo::dev_malloc((void**)&r->d_m, r->n_params * 4) == cudaSuccess && relo::dev_malloc((void**)&r->d_v, r->n_params * 4) == cudaSuccess;
   for (int l = 0; ok && l < kRegLayers; ++l) {
-    ok = cudaMalloc(&r->d_wk[l], 9LL * kRegCoutPad[l] * kRegCinPad[l] * sizeof(bf16)) == cudaSuccess &&
-         cudaMalloc(&r->d_bias[l], 64 * sizeof(float)) == cudaSuccess;
-    if (ok && l > 0) ok = cudaMalloc(&r->d_wt[l], 9LL * kRegCin[l] * cout_pad_t(l) * sizeof(bf16)) == cudaSuccess;
+    ok = relo::dev_malloc((void**)&r->d_wk[l], 9LL * kRegCoutPad[l] * kRegCinPad[l] * sizeof(bf16)) == cudaSuccess &&
+         relo::dev_malloc((void**)&r->d_bias[l], 64 * sizeof(float)) == cudaSuccess;
+    if (ok && l > 0) ok = relo::dev_malloc((void**)&r->d_wt[l], 9LL * kRegCin[l] * cout_pad_t(l) * sizeof(bf16)) == cudaSuccess;
   }
   if (!ok) {
     cudaGetLastError();
@@ -1410,6 +1459,31 @@ void relo_destroy_regressor(relo_regressor* r) {
     cudaFree(r->d_bias[l]);
   }
   delete r;
+}
+
+relo_status relo_regressor_get_state(const relo_regressor* r, float* params, float* m, float* v, int64_t* step) {
+  if (!r) return fail(RELO_EINVAL, "regressor is null");
+  RELO_CUDA(cudaDeviceSynchronize());
+  if (params) RELO_CUDA(cudaMemcpy(params, r->d_p, r->n_params * 4, cudaMemcpyDeviceToHost));
+  if (m) RELO_CUDA(cudaMemcpy(m, r->d_m, r->n_params * 4, cudaMemcpyDeviceToHost));
+  if (v) RELO_CUDA(cudaMemcpy(v, r->d_v, r->n_params * 4, cudaMemcpyDeviceToHost));
+  if (step) *step = r->t;
+  return RELO_OK;
+}
+
+relo_status relo_regressor_set_state(relo_regressor* r, const float* params, const float* m, const float* v,
+                                     int64_t step) {
+  if (!r || !params || !m || !v) return fail(RELO_EINVAL, "null regressor or state array");
+  if (step < 0 || step > INT32_MAX) return fail(RELO_EINVAL, "step outside [0, 2^31)");
+  RELO_CUDA(cudaDeviceSynchronize());
+  RELO_CUDA(cudaMemcpy(r->d_p, params, r->n_params * 4, cudaMemcpyHostToDevice));
+  RELO_CUDA(cudaMemcpy(r->d_m, m, r->n_params * 4, cudaMemcpyHostToDevice));
+  RELO_CUDA(cudaMemcpy(r->d_v, v, r->n_params * 4, cudaMemcpyHostToDevice));
+  r->t = (int)step;
+  relo_status st = reg_pack(r, 0);  // the BF16 copies the kernels multiply
+  if (st) return st;
+  RELO_CUDA(cudaDeviceSynchronize());
+  return RELO_OK;
 }
 
 relo_status relo_regressor_get_params(const relo_regressor* r, float* params, float* grads) {
@@ -1641,6 +1715,7 @@ relo_status check_attempts(const relo_attempt* at, int n, const relo_ransac_para
     if (!a.forest_a && !a.regressor_a) return fail(RELO_EINVAL, "attempt has neither a forest nor a regressor");
     st = check_intr(&a.intr);
     if (st) return st;
+    if (bad_pose(a.pose_b)) return fail(RELO_EINVAL, "attempt pose_b is not finite");
     if (a.n_hyps < 0 || a.n_hyps > 4096) return fail(RELO_EINVAL, "attempt n_hyps outside [0, 4096]");
     if (a.regressor_a) {
       st = reg_check_size(1, a.intr.width, a.intr.height);
@@ -1840,7 +1915,8 @@ void layout_batch(const relo_attempt* at, int n, const relo_ransac_params& p, ch
       RansacJob& r = h.ransac_F[j];
       fill_ransac_job(r, a.forest_a->view, depth, leaves, a.intr, p, K, a.seed);
       carve_ransac(c, r, W, H, K, p.batch, r.n_rounds, T);
-      r.err = b.d_errs + nL + j;
+      // one error word per attempt: a learned attempt's forest fallback shares the learned word
+      r.err = iL[i] >= 0 ? b.d_errs + iL[i] : b.d_errs + nL + j;
       r.result = b.d_res_F + i;
       r.chunk_begin = chF;
       r.hyp_begin = hyF;
@@ -1860,6 +1936,8 @@ void layout_batch(const relo_attempt* at, int n, const relo_ransac_params& p, ch
       vtF += ray_tiles(W, H);
     }
   }
+  for (int i = 0; i < n; ++i)  // the query raycast reports bound failures into the attempt's error word
+    h.query[i].err = iL[i] >= 0 ? b.d_errs + iL[i] : (iF[i] >= 0 ? b.d_errs + nL + iF[i] : nullptr);
   b.query_tiles = qt;
   b.verify_L_tiles = vtL;
   b.verify_F_tiles = vtF;

@@ -890,6 +890,8 @@ __device__ __forceinline__ void decide(relo_pose_result* res, unsigned long long
 __global__ void verify_decide_kernel(const RansacJob* __restrict__ jobs, int n_jobs) {
   const int jid = blockIdx.x * blockDim.x + threadIdx.x;
   if (jid >= n_jobs || job_skipped(jobs[jid].skip)) return;
+  // a bound failure in the verification raycast (it reports into the job's word) voids the result
+  if (jobs[jid].err && *jobs[jid].err) jobs[jid].result->status = RELO_EDEVICE;
   decide(jobs[jid].result, (unsigned long long)jobs[jid].vW * jobs[jid].vH);
 }
 

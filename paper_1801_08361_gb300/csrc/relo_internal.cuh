@@ -416,6 +416,10 @@ cudaError_t launch_top_modes(const float* modes, const uint8_t* n_modes, int n_l
 // Helpers for ray jobs
 RayJob make_ray_job(const SceneView& sv, const relo_intrinsics& in, const double* pose_host);
 
+// Every device allocation of the library goes through here, so that tests can make the next
+// allocations fail (relo_debug_fail_allocations) and check the error paths.
+cudaError_t dev_malloc(void** p, size_t bytes);
+
 // TSDF fusion of one frame into a growing scene (fusion.cu).
 struct FuseJob {
   int4* buckets;
@@ -464,6 +468,7 @@ struct relo_scene {
   void* d_coords;      // int4 [capacity]
   void* d_counters;    // int32 [4]: blocks in use, excess entries in use, status, pad; then uint64 block updates
   int32_t max_weight;
+  int64_t n_excess;    // excess entries allocated (the chains' storage)
 };
 
 struct relo_forest {

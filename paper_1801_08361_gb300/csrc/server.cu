@@ -20,6 +20,10 @@
 
 #include "../../include/relo.h"
 
+namespace relo {
+cudaError_t dev_malloc(void** p, size_t bytes);  // the library's device allocations (api.cu)
+}
+
 namespace {
 
 using Clock = std::chrono::steady_clock;
@@ -139,7 +143,7 @@ relo_status relo_server_create(const relo_server_params* params, relo_server** o
     delete s;
     return RELO_ECUDA;
   }
-  if (cudaMalloc(&s->ws, (size_t)params->workspace_bytes) != cudaSuccess) {
+  if (relo::dev_malloc((void**)&s->ws, (size_t)params->workspace_bytes) != cudaSuccess) {
     cudaGetLastError();
     delete s;
     return RELO_ENOMEM;

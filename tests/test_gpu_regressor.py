@@ -159,6 +159,32 @@ def test_training_reduces_loss(views):
     assert float(loss.item()) < first - 1.0
 
 
+def test_training_resumes_from_a_checkpoint(views):
+    """Checkpoint (parameters, Adam moments, step) after 4 steps, restore it into a regressor
+    created from another seed, train 4 more steps on both: the parameters agree bit for bit."""
+    intr, poses, d, c = views
+    n = d.shape[0]
+    ws = torch.empty(B.regressor_workspace_size(n, 64, 48, True), dtype=torch.uint8, device=DEV)
+    dd, cc = _u16(d), torch.from_numpy(c).to(DEV)
+    a = B.Regressor(seed=5, origin=ORIGIN)
+    for _ in range(4):
+        B.regressor_train_step(a, dd, cc, intr, poses, 1e-3, ws)
+    state = B.regressor_state(a)
+    assert state["step"] == 4 and np.any(state["m"] != 0) and np.any(state["v"] != 0)
+    b = B.Regressor(seed=6, origin=ORIGIN)
+    B.regressor_set_state(b, state)
+    for reg in (a, b):
+        for _ in range(4):
+            B.regressor_train_step(reg, dd, cc, intr, poses, 1e-3, ws)
+    torch.cuda.synchronize()
+    sa, sb = B.regressor_state(a), B.regressor_state(b)
+    assert sa["step"] == sb["step"] == 8
+    for k in ("params", "m", "v"):
+        assert np.array_equal(sa[k].view(np.uint32), sb[k].view(np.uint32)), k
+    with pytest.raises(B.ReloError):
+        B.regressor_set_state(b, dict(state, step=-1))
+
+
 def test_learned_ransac_matches_oracle_on_the_cell_grid(room, oracle_room):
     """The learned path's RANSAC (relo_regressor_relocalise) against the oracle's RANSAC on the
     cell forest built from the same network output."""
