@@ -206,8 +206,11 @@ __global__ void __launch_bounds__(kTile* kTile, kColour ? RELO_RAYCAST_MIN_BLOCK
     if (jobs[mid].tile_begin <= (int)blockIdx.x) lo = mid;
     else hi = mid - 1;
   }
-  // the CTA's job, staged in shared memory: the march reads its scene fields at every step
+  // the CTA's job, staged in shared memory: the march reads its scene fields at every step; a
+  // device pose is converted to float once per CTA (double conversions use the FP64 pipe)
   __shared__ __align__(16) RayJob sj;
+  __shared__ float s_pose[12];
+  __shared__ unsigned s_counts[4], s_arrived;
   if (jobs) {
     const int4* src = reinterpret_cast<const int4*>(jobs + lo);
     int4* dst = reinterpret_cast<int4*>(&sj);
@@ -215,6 +218,12 @@ __global__ void __launch_bounds__(kTile* kTile, kColour ? RELO_RAYCAST_MIN_BLOCK
   } else if (threadIdx.x == 0) {
     sj = single;
   }
+  if (threadIdx.x < 12) {
+    const double* pd = jobs ? jobs[lo].pose_dev : single.pose_dev;
+    if (pd) s_pose[threadIdx.x] = (float)pd[threadIdx.x];
+  }
+  if (kCompare && threadIdx.x < 4) s_counts[threadIdx.x] = 0u;
+  if (kCompare && threadIdx.x == 0) s_arrived = 0u;
   __syncthreads();
   const RayJob& job = sj;
   const int tiles_x = (job.W + kTile - 1) / kTile;
@@ -235,8 +244,8 @@ __global__ void __launch_bounds__(kTile* kTile, kColour ? RELO_RAYCAST_MIN_BLOCK
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
 #pragma unroll
-        for (int q = 0; q < 3; ++q) R[3 * r + q] = (float)job.pose_dev[4 * r + q];
-        t[r] = (float)job.pose_dev[4 * r + 3];
+        for (int q = 0; q < 3; ++q) R[3 * r + q] = s_pose[4 * r + q];
+        t[r] = s_pose[4 * r + 3];
       }
     } else {
 #pragma unroll
@@ -281,19 +290,23 @@ __global__ void __launch_bounds__(kTile* kTile, kColour ? RELO_RAYCAST_MIN_BLOCK
       oab += __shfl_xor_sync(0xffffffffu, oab, o);
       sum += __shfl_xor_sync(0xffffffffu, sum, o);
     }
-    __shared__ unsigned red[4][kTile * kTile / 32];
-    const int w = threadIdx.x >> 5;
+    // per-warp totals into shared counters; the last warp to arrive adds the CTA's totals to the
+    // job's counters (no CTA-wide barrier: warps whose rays ended early do not wait)
     if ((threadIdx.x & 31) == 0) {
-      red[0][w] = oa;
-      red[1][w] = ob;
-      red[2][w] = oab;
-      red[3][w] = sum;
-    }
-    __syncthreads();
-    if (threadIdx.x < 4) {
-      unsigned long long acc = 0;
-      for (int q = 0; q < kTile * kTile / 32; ++q) acc += red[threadIdx.x][q];
-      if (acc && (job.status_dev == nullptr || *job.status_dev == RELO_OK)) atomicAdd(&job.counts[threadIdx.x], acc);
+      atomicAdd(&s_counts[0], oa);
+      atomicAdd(&s_counts[1], ob);
+      atomicAdd(&s_counts[2], oab);
+      atomicAdd(&s_counts[3], sum);
+      __threadfence_block();
+      if (atomicAdd(&s_arrived, 1u) == kTile * kTile / 32 - 1 &&
+          (job.status_dev == nullptr || *job.status_dev == RELO_OK)) {
+        __threadfence_block();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const unsigned acc = atomicAdd(&s_counts[q], 0u);
+          if (acc) atomicAdd(&job.counts[q], (unsigned long long)acc);
+        }
+      }
     }
   }
 }
