@@ -67,10 +67,10 @@ ALG_BYTES_PER_PIXEL = {
 # profiles/attempt_kernels_house_640x480_batch128.md (128 attempts per launch) divided by 128; a
 # launch of A attempts is reported as A times that (None: not captured for the current code).
 PROFILED_TRAFFIC_BYTES_PER_ATTEMPT = {
-    "query_raycast": (3.107e9 + 0.600e9) / 128,
+    "query_raycast": (3.115e9 + 0.615e9) / 128,
     "forest_eval": (0.398e9 + 0.361e9) / 128,
     "forest_hypotheses": (0.637e9 + 0.005e9) / 128,
-    "forest_verify": None,
+    "forest_verify": (1.868e9 + 0.032e9) / 128,
 }
 
 
