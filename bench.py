@@ -599,8 +599,7 @@ def fusion_section(args, B, synth, torch, dev, scene, world, intr, train, nvtx=N
         torch.cuda.nvtx.range_push(nvtx)
     for lo, hi, a in ((0, q, 0), (q, n, 2)):
         ev[a].record()
-        for k in range(lo, hi):
-            fs.fuse(intr, poses[k], depth[k], rgba[k], workspace_dev=wsf)
+        fs.fuse_many(intr, poses[lo:hi], depth[lo:hi], rgba[lo:hi], workspace_dev=wsf)
         ev[a + 1].record()
         updates.append(fs.block_updates())        # synchronises after the region's end event
     if nvtx:

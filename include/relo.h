@@ -174,6 +174,12 @@ size_t relo_fuse_workspace_size(int32_t width, int32_t height);
 relo_status relo_fuse_frame(relo_scene* scene, const relo_intrinsics* intr, const double pose_c2s[16],
                             const uint16_t* depth_dev, const uint8_t* rgba_dev, void* workspace_dev,
                             size_t workspace_bytes, relo_stream stream);
+/* n frames fused in order in one call (the host issues every launch, so a frame's launches are not
+ * held up by the caller): poses_c2s_host [n][16], depth_dev [n][H][W], rgba_dev [n][H][W][4] or
+ * NULL.  Same rules and errors as relo_fuse_frame; stops at the first frame that is rejected. */
+relo_status relo_fuse_frames(relo_scene* scene, const relo_intrinsics* intr, const double* poses_c2s_host,
+                             int32_t n, const uint16_t* depth_dev, const uint8_t* rgba_dev, void* workspace_dev,
+                             size_t workspace_bytes, relo_stream stream);
 /* The last frame fused with this workspace (of width x height frames): blocks it updated and blocks
  * it created.  Synchronises the device.  Errors: RELO_EINVAL (null workspace, bad size). */
 relo_status relo_fuse_stats(const void* workspace_dev, int32_t width, int32_t height, int32_t* visible,

@@ -91,6 +91,8 @@ _SIGS = {
     "relo_fuse_workspace_size": (ctypes.c_size_t, [c_i32, c_i32]),
     "relo_fuse_frame": (c_i32, [c_vp, ctypes.POINTER(Intrinsics), ctypes.POINTER(c_dbl), c_vp, c_vp, c_vp,
                                 ctypes.c_size_t, c_vp]),
+    "relo_fuse_frames": (c_i32, [c_vp, ctypes.POINTER(Intrinsics), ctypes.POINTER(c_dbl), c_i32, c_vp, c_vp, c_vp,
+                                 ctypes.c_size_t, c_vp]),
     "relo_scene_block_count": (c_i32, [c_vp, ctypes.POINTER(c_i64)]),
     "relo_fuse_stats": (c_i32, [c_vp, c_i32, c_i32, ctypes.POINTER(c_i32), ctypes.POINTER(c_i32)]),
     "relo_scene_fusion_updates": (c_i32, [c_vp, ctypes.POINTER(c_u64)]),
@@ -290,6 +292,20 @@ class FusionScene(Scene):
         _check(lib().relo_fuse_frame(self.handle, ctypes.byref(ci), ctypes.cast(pp, ctypes.POINTER(c_dbl)),
                                      _ptr(depth_dev), _ptr(rgba_dev), _ptr(workspace_dev), workspace_dev.numel(),
                                      _stream(stream)))
+
+    def fuse_many(self, intr, poses, depth_dev, rgba_dev=None, workspace_dev=None, stream=None):
+        """Fuse n frames in order in one call (depth [n][H][W], rgba [n][H][W][4] or None)."""
+        if workspace_dev is None:
+            need = fuse_workspace_size(intr.width, intr.height)
+            if self._ws is None or self._ws.numel() < need:
+                import torch
+                self._ws = torch.empty(need, dtype=torch.uint8, device=depth_dev.device)
+            workspace_dev = self._ws
+        ci = intrinsics(intr)
+        ph, pp = _poses_host(poses)
+        _check(lib().relo_fuse_frames(self.handle, ctypes.byref(ci), ctypes.cast(pp, ctypes.POINTER(c_dbl)),
+                                      len(ph), _ptr(depth_dev), _ptr(rgba_dev), _ptr(workspace_dev),
+                                      workspace_dev.numel(), _stream(stream)))
 
     def last_frame_stats(self, intr, workspace_dev=None):
         """(blocks updated, blocks created) by the last frame fused with the workspace."""

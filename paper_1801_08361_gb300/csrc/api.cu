@@ -491,6 +491,22 @@ size_t relo_fuse_workspace_size(int32_t width, int32_t height) {
   return S * 8 + 256 + S * 8 + 256 + S * 8 + 256 + S * 4 + 256 + 256;
 }
 
+relo_status relo_fuse_frames(relo_scene* scene, const relo_intrinsics* intr, const double* poses, int32_t n,
+                             const uint16_t* depth, const uint8_t* rgba, void* ws, size_t ws_bytes,
+                             relo_stream stream) {
+  if (!poses || n < 1) return fail(RELO_EINVAL, "null poses or n < 1");
+  for (int k = 0; k < n; ++k)
+    if (bad_pose(poses + 16 * (size_t)k)) return fail(RELO_EINVAL, "a pose is not finite");
+  if (!intr || bad_size(intr->width, intr->height)) return fail(RELO_EINVAL, "bad intrinsics");
+  const size_t n_pix = (size_t)intr->width * intr->height;
+  for (int k = 0; k < n; ++k) {  // in order: each frame sees the blocks of the frames before it
+    const relo_status st = relo_fuse_frame(scene, intr, poses + 16 * (size_t)k, depth ? depth + k * n_pix : nullptr,
+                                           rgba ? rgba + k * n_pix * 4 : nullptr, ws, ws_bytes, stream);
+    if (st) return st;
+  }
+  return RELO_OK;
+}
+
 relo_status relo_fuse_frame(relo_scene* scene, const relo_intrinsics* intr, const double* pose, const uint16_t* depth,
                             const uint8_t* rgba, void* ws, size_t ws_bytes, relo_stream stream) {
   if (!scene || !pose || !depth) return fail(RELO_EINVAL, "null scene, pose or depth");

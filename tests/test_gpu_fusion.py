@@ -119,3 +119,17 @@ def test_frame_statistics_count_the_blocks(frames):
         updated += vis
     assert created == g.block_count()
     assert updated == g.block_updates()
+
+
+def test_many_frames_in_one_call_equal_frame_by_frame(frames):
+    intr, fr = frames[160]
+    g1 = B.FusionScene(1 << 16, VOX, MU, log2_buckets=14)
+    g2 = B.FusionScene(1 << 16, VOX, MU, log2_buckets=14)
+    d = torch.from_numpy(np.stack([f[1] for f in fr]).view(np.int16)).to(DEV)
+    c = torch.from_numpy(np.stack([f[2] for f in fr])).to(DEV)
+    for k, (P, _, _) in enumerate(fr):
+        g1.fuse(intr, P, d[k], c[k])
+    g2.fuse_many(intr, [f[0] for f in fr], d, c)
+    torch.cuda.synchronize()
+    for a, b in zip(g1.export(), g2.export()):
+        assert np.array_equal(a, b)
