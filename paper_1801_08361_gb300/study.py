@@ -206,21 +206,19 @@ def run(n_fragments=8, frames=64, n_pairs=8, seed=3, n_views=4, dev=None, log=pr
     fused = None
     if len(members) >= 2:
         fs = B.FusionScene(1 << 21, synth.VOXEL_SIZE, synth.TRUNCATION, log2_buckets=21)
-        depth = torch.zeros((H, W), dtype=torch.int16, device=dev)
-        rgba = torch.zeros((H, W, 4), dtype=torch.uint8, device=dev)
+        seq = [(s_, synth.world_to_scene_pose(Pw, frags[s_]["scene_to_world"]))
+               for s_ in members for Pw in frags[s_]["train_w"][::2]]
+        n_frames = len(seq)
+        depth = torch.zeros((n_frames, H, W), dtype=torch.int16, device=dev)
+        rgba = torch.zeros((n_frames, H, W, 4), dtype=torch.uint8, device=dev)
+        for k, (s_, P) in enumerate(seq):       # the agents' saved sequences, re-rendered
+            B.raycast_view(frags[s_]["scene"], intr, P, depth[k], rgba[k])
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        n_frames, fuse_ms = 0, 0.0
-        for s_ in members:
-            S = frags[s_]["scene_to_world"]
-            for Pw in frags[s_]["train_w"][::2]:
-                P = synth.world_to_scene_pose(Pw, S)
-                B.raycast_view(frags[s_]["scene"], intr, P, depth, rgba)
-                e0.record()
-                fs.fuse(intr, poses[s_] @ P, depth, rgba)
-                e1.record()
-                torch.cuda.synchronize()
-                fuse_ms += e0.elapsed_time(e1)
-                n_frames += 1
+        e0.record()
+        fs.fuse_many(intr, [poses[s_] @ P for s_, P in seq], depth, rgba)
+        e1.record()
+        torch.cuda.synchronize()
+        fuse_ms = e0.elapsed_time(e1)
         diffs = []
         for Pw in views:
             Pg = S0_inv @ Pw
