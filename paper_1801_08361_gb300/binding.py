@@ -526,10 +526,15 @@ def batch_workspace_size(attempts, params) -> int:
     return int(lib().relo_batch_workspace_size(attempts, len(attempts), ctypes.byref(params)))
 
 
-def relocalise_batch(attempts, params, workspace_dev, stream=None):
-    res = (PoseResult * len(attempts))()
+def relocalise_batch_into(attempts, params, workspace_dev, results, stream=None):
+    """relo_relocalise_batch into a caller-owned host array of PoseResult (no conversion)."""
     _check(lib().relo_relocalise_batch(attempts, len(attempts), ctypes.byref(params), _ptr(workspace_dev),
-                                       workspace_dev.numel(), res, _stream(stream)))
+                                       workspace_dev.numel(), results, _stream(stream)))
+    return results
+
+
+def relocalise_batch(attempts, params, workspace_dev, stream=None):
+    res = relocalise_batch_into(attempts, params, workspace_dev, (PoseResult * len(attempts))(), stream)
     return [r.to_dict() for r in res]
 
 
