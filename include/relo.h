@@ -623,6 +623,11 @@ int32_t relo_pose_graph_cluster_count(const relo_pose_graph* graph, int32_t a, i
 /* The next n device allocations made by the library fail as if the device were out of memory
  * (creation calls then return RELO_ENOMEM); n <= 0 cancels. */
 void relo_debug_fail_allocations(int32_t n);
+/* Checked builds (the library built with RELO_CHECKED=1, the stand-in for a device memory
+ * checker): the number of guarded accesses whose index check failed (and which were skipped)
+ * since the library loaded; -1 in a normal build, -2 if the device could not be read.
+ * Synchronises the device. */
+int64_t relo_debug_check_failures(void);
 /* Makes every hash chain of the scene end in a cycle (each chain entry links to itself; empty
  * links point at entry 0).  A hash walk for a block that is not at its bucket's head then runs into
  * its bound: attempts that raycast the scene through the hash (relo_scene_use_grid(scene, 0))

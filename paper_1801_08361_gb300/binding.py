@@ -13,7 +13,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "librelo.so")
+# RELO_CHECKED=1 in the environment loads the bounds-checked build (build.build_cuda(checked=True))
+LIB_PATH = os.path.join(_HERE, "librelo_checked.so" if os.environ.get("RELO_CHECKED") == "1" else "librelo.so")
 _LIB = None
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EDEVICE, ENOTFOUND, EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
@@ -155,6 +156,7 @@ _SIGS = {
     "relo_batch_attempt_images": (c_i32, [c_vp, c_i32, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp),
                                           ctypes.POINTER(c_vp)]),
     "relo_debug_fail_allocations": (None, [c_i32]),
+    "relo_debug_check_failures": (c_i64, []),
     "relo_debug_corrupt_scene": (c_i32, [c_vp]),
     "relo_regressor_get_state": (c_i32, [c_vp, c_vp, c_vp, c_vp, ctypes.POINTER(c_i64)]),
     "relo_regressor_set_state": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64]),

@@ -14,6 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "librelo.so")
+CHECKED_LIB = os.path.join(HERE, "librelo_checked.so")
 SOURCES = ["scene.cu", "forest.cu", "ransac.cu", "regressor.cu", "api.cu", "server.cu", "posegraph.cu", "fusion.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
@@ -36,20 +37,24 @@ def _stale(out: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build_cuda(force: bool = False, verbose: bool = False) -> str:
+def build_cuda(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """librelo.so; with checked=True the bounds-checked variant librelo_checked.so (RELO_CHECKED:
+    guarded accesses count their failed index checks, relo_debug_check_failures)."""
     hdrs = [os.path.join(CSRC, "relo_internal.cuh"), os.path.join(CSRC, "regressor.cuh"), os.path.join(ROOT, "include", "relo.h")]
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    bdir = os.path.join(ROOT, "_build", "relo")
+    bdir = os.path.join(ROOT, "_build", "relo_checked" if checked else "relo")
+    lib_path = CHECKED_LIB if checked else LIB
+    nvcc_flags = NVCC_FLAGS + (["-DRELO_CHECKED=1"] if checked else [])
     # the objects depend on the compile flags too: a change of flags rebuilds everything
     stamp = os.path.join(bdir, "flags")
-    flags = " ".join(NVCC_FLAGS)
+    flags = " ".join(nvcc_flags)
     try:
         with open(stamp) as f:
             force = force or f.read() != flags
     except OSError:
         force = True
-    if not force and not _stale(LIB, srcs + hdrs):
-        return LIB
+    if not force and not _stale(lib_path, srcs + hdrs):
+        return lib_path
     os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
     procs, objs = [], []
@@ -57,7 +62,7 @@ def build_cuda(force: bool = False, verbose: bool = False) -> str:
         o = os.path.join(bdir, os.path.basename(s).replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + hdrs):
-            cmd = [nvcc] + NVCC_FLAGS + ["-c", s, "-o", o]
+            cmd = [nvcc] + nvcc_flags + ["-c", s, "-o", o]
             if verbose:
                 print(" ".join(cmd), file=sys.stderr)
             procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -65,13 +70,13 @@ def build_cuda(force: bool = False, verbose: bool = False) -> str:
         out, _ = p.communicate()
         if p.returncode != 0:
             raise RuntimeError("nvcc failed: " + " ".join(cmd) + "\n" + out.decode(errors="replace"))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
     subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib_path)
     with open(stamp, "w") as f:
         f.write(flags)
-    return LIB
+    return lib_path
 
 
 def build(force: bool = False, verbose: bool = False) -> None:

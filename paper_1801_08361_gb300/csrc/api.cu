@@ -626,6 +626,21 @@ relo_status relo_scene_export(const relo_scene* scene, int32_t* coords, float* t
 
 void relo_debug_fail_allocations(int32_t n) { relo::g_fail_allocations.store(n > 0 ? n : 0); }
 
+int64_t relo_debug_check_failures(void) {
+#ifdef RELO_CHECKED
+  if (cudaDeviceSynchronize() != cudaSuccess) return -2;
+  unsigned long long total = 0;
+  for (unsigned long long v : {check_failures_scene(), check_failures_forest(), check_failures_ransac(),
+                               check_failures_fusion()}) {
+    if (v == ~0ull) return -2;
+    total += v;
+  }
+  return (int64_t)total;
+#else
+  return -1;
+#endif
+}
+
 relo_status relo_debug_corrupt_scene(relo_scene* scene) {
   if (!scene || scene->n_excess < 1) return fail(RELO_EINVAL, "null scene");
   const size_t nb = (size_t)scene->view.mask + 1, ne = (size_t)scene->n_excess;

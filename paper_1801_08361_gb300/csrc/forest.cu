@@ -66,12 +66,17 @@ __device__ __forceinline__ void descend(const ForestJob& job, int u, int v, cons
 #pragma unroll
     for (int t = 0; t < MT; ++t) {
       if (t < T) {
-        const int4 nd = __ldg(&f.nodes[(size_t)t * n_int + node[t]]);
+        const int4 nd = RELO_CHECK(node[t] >= 0 && node[t] < n_int) ? __ldg(&f.nodes[(size_t)t * n_int + node[t]])
+                                                                    : make_int4(0, 0, 0, 0);
         const int dx1 = (int)(int16_t)(nd.x & 0xFFFF), dy1 = nd.x >> 16;
         const int dx2 = (int)(int16_t)(nd.y & 0xFFFF), dy2 = nd.y >> 16;
         const int q1 = probe<kHi>(v, dy1, dv, H - 1) * W + probe<kHi>(u, dx1, dv, W - 1);
         const int q2 = probe<kHi>(v, dy2, dv, H - 1) * W + probe<kHi>(u, dx2, dv, W - 1);
         int a, b;
+        if (!RELO_CHECK((unsigned)q1 < (unsigned)(W * H) && (unsigned)q2 < (unsigned)(W * H))) {
+          node[t] = 2 * node[t] + 1;
+          continue;
+        }
         if (kPacked) {
           const unsigned mask = 0xFFFFu >> ((nd.z & 0xFF) << 3), s1 = (nd.z >> 8) & 0xFF, s2 = (nd.z >> 16) & 0xFF;
           const uint2 p1 = __ldg(&job.packed[q1]), p2 = __ldg(&job.packed[q2]);
@@ -160,8 +165,11 @@ __global__ void __launch_bounds__(256, RELO_FOREST_MIN_BLOCKS)
   }
 #pragma unroll
   for (int t = 0; t < MT; ++t)
-    if (t < T) job.leaves[(size_t)t * n_pix + pix] = (uint16_t)(node[t] - n_int);
+    if (t < T && RELO_CHECK(node[t] >= n_int && node[t] < 2 * n_int + 1))
+      job.leaves[(size_t)t * n_pix + pix] = (uint16_t)(node[t] - n_int);
 }
+
+RELO_DEFINE_CHECK_READER(check_failures_forest)
 
 cudaError_t launch_forest(const ForestJob* jobs_dev, int n_jobs, const ForestJob* single, int64_t total_pixels,
                           cudaStream_t s, int max_trees, const Schedule& sched) {

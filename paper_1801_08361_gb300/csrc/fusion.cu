@@ -171,6 +171,7 @@ __global__ void __launch_bounds__(512) fuse_update_kernel(const FuseJob j) {
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(j.updates, (unsigned long long)n_vis);
   for (int q = blockIdx.x; q < n_vis; q += gridDim.x) {
     const int b = j.visible[q];
+    if (!RELO_CHECK(b >= 0 && b < j.capacity)) continue;
     const int4 bc = j.coords[b];
     const int X = 8 * bc.x + (vi & 7), Y = 8 * bc.y + ((vi >> 3) & 7), Z = 8 * bc.z + (vi >> 6);
     const float dx = __fsub_rn(__fmul_rn((float)X, j.voxel), j.t[0]);
@@ -185,6 +186,7 @@ __global__ void __launch_bounds__(512) fuse_update_kernel(const FuseJob j) {
     const float fu = floorf(__fadd_rn(uf, 0.5f)), fv = floorf(__fadd_rn(vf, 0.5f));
     if (!(fu >= 0.0f && fu < (float)j.W && fv >= 0.0f && fv < (float)j.H)) continue;
     const int pix = (int)fv * j.W + (int)fu;  // 32-bit: 64-bit float conversions run on the FP64 pipe
+    if (!RELO_CHECK(pix >= 0 && pix < j.W * j.H)) continue;
     const uint16_t Dm = j.depth[pix];
     if (Dm == 0) continue;
     const float dm = __fmul_rn((float)Dm, 0.001f);
@@ -247,5 +249,7 @@ cudaError_t launch_fuse_frame(const FuseJob& j, cudaStream_t s) {
   fuse_update_kernel<<<grid_for((int64_t)(j.set_mask + 1) * 512, 512) , 512, 0, s>>>(j);
   return cudaGetLastError();
 }
+
+RELO_DEFINE_CHECK_READER(check_failures_fusion)
 
 }  // namespace relo

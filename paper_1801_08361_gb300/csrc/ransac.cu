@@ -48,6 +48,7 @@ struct TableEntry {
 
 __device__ __forceinline__ TableEntry load_entry(const RansacJob& job, int idx) {
   TableEntry e;
+  if (!RELO_CHECK(idx >= 0 && idx < *job.n_valid)) idx = 0;
   e.w0 = __ldg(&job.table[(size_t)idx * job.nv]);
   e.u = (int)(e.w0.x & 0xFFFFu);
   e.v = (int)(e.w0.x >> 16);
@@ -489,7 +490,7 @@ __device__ __forceinline__ int32_t* alive_out(const RansacJob& j, int r) { retur
 __device__ __forceinline__ int2 tree_modes(const RansacJob& job, int idx, const TableEntry& e, int t, int L) {
   const ForestView& f = job.forest;
   const int leaf = entry_leaf(job, idx, e, t);
-  if (leaf >= L) return make_int2(0, 0);
+  if (leaf >= L || !RELO_CHECK(t >= 0 && t < f.T)) return make_int2(0, 0);
   const int node = t * L + leaf;
   return make_int2(node * f.M, min((int)__ldg(&f.n_modes[node]), f.M));
 }
@@ -950,5 +951,7 @@ cudaError_t launch_merge_results(const relo_pose_result* learned, const relo_pos
   merge_results_kernel<<<(n + 127) / 128, 128, 0, s>>>(learned, fallback, kind, n, out);
   return cudaGetLastError();
 }
+
+RELO_DEFINE_CHECK_READER(check_failures_ransac)
 
 }  // namespace relo

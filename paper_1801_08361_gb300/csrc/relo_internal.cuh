@@ -416,6 +416,28 @@ cudaError_t launch_top_modes(const float* modes, const uint8_t* n_modes, int n_l
 // Helpers for ray jobs
 RayJob make_ray_job(const SceneView& sv, const relo_intrinsics& in, const double* pose_host);
 
+// Checked builds (built with RELO_CHECKED=1): guarded accesses first check their index; a failed
+// check is counted, once per translation unit, and the access is skipped.  The stand-in for a
+// device memory checker.  In normal builds a check is the constant true and costs nothing.
+#ifdef RELO_CHECKED
+static __device__ unsigned int g_check_failures;
+#define RELO_CHECK(cond) ((cond) ? true : (atomicAdd(&g_check_failures, 1u), false))
+#define RELO_DEFINE_CHECK_READER(name)                                    \
+  unsigned long long name() {                                             \
+    unsigned int v = 0;                                                   \
+    if (cudaMemcpyFromSymbol(&v, g_check_failures, sizeof v) != cudaSuccess) return ~0ull; \
+    return v;                                                             \
+  }
+#else
+#define RELO_CHECK(cond) true
+#define RELO_DEFINE_CHECK_READER(name) \
+  unsigned long long name() { return 0; }
+#endif
+unsigned long long check_failures_scene();
+unsigned long long check_failures_forest();
+unsigned long long check_failures_ransac();
+unsigned long long check_failures_fusion();
+
 // Every device allocation of the library goes through here, so that tests can make the next
 // allocations fail (relo_debug_fail_allocations) and check the error paths.
 cudaError_t dev_malloc(void** p, size_t bytes);

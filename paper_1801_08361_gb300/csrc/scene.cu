@@ -97,6 +97,7 @@ __device__ __forceinline__ int corner_voxel(int i, int j, int k, int n) {
 __device__ __forceinline__ float trilinear_tsdf(const SceneView& s, BlockCache& c, int b0, int i, int j, int k,
                                                 float fx, float fy, float fz, int* err) {
   float v[8];
+  if (!RELO_CHECK(b0 < s.n_blocks)) return 1.0f;
   if ((i & 7) != 7 && (j & 7) != 7 && (k & 7) != 7) {
     // all eight corners inside block b0: one contiguous neighbourhood
     const float* base = s.tsdf + (size_t)b0 * kVoxelsPerBlock + (i & 7) + 8 * (j & 7) + 64 * (k & 7);
@@ -113,7 +114,9 @@ __device__ __forceinline__ float trilinear_tsdf(const SceneView& s, BlockCache& 
     corner_blocks(s, c, b0, i, j, k, blk, err);
 #pragma unroll
     for (int n = 0; n < 8; ++n)
-      v[n] = blk[n] < 0 ? 1.0f : __ldg(&s.tsdf[(size_t)blk[n] * kVoxelsPerBlock + corner_voxel(i, j, k, n)]);
+      v[n] = (blk[n] < 0 || !RELO_CHECK(blk[n] < s.n_blocks))
+                 ? 1.0f
+                 : __ldg(&s.tsdf[(size_t)blk[n] * kVoxelsPerBlock + corner_voxel(i, j, k, n)]);
   }
   const float x00 = v[0] + fx * (v[1] - v[0]);
   const float x10 = v[2] + fx * (v[3] - v[2]);
@@ -137,7 +140,9 @@ __device__ __forceinline__ uint32_t trilinear_rgba(const SceneView& s, BlockCach
   for (int n = 0; n < 8; ++n) {
     const int dx = n & 1, dy = (n >> 1) & 1, dz = n >> 2;
     const float w = (dx ? fx : 1.f - fx) * (dy ? fy : 1.f - fy) * (dz ? fz : 1.f - fz);
-    const uint32_t col = blk[n] < 0 ? 0u : __ldg(&s.rgba[(size_t)blk[n] * kVoxelsPerBlock + corner_voxel(i, j, k, n)]);
+    const uint32_t col = (blk[n] < 0 || !RELO_CHECK(blk[n] < s.n_blocks))
+                             ? 0u
+                             : __ldg(&s.rgba[(size_t)blk[n] * kVoxelsPerBlock + corner_voxel(i, j, k, n)]);
     acc[0] += w * (float)(col & 0xFF);
     acc[1] += w * (float)((col >> 8) & 0xFF);
     acc[2] += w * (float)((col >> 16) & 0xFF);
@@ -431,5 +436,7 @@ RayJob make_ray_job(const SceneView& sv, const relo_intrinsics& in, const double
 }
 
 int ray_tiles(int W, int H) { return ((W + kTile - 1) / kTile) * ((H + kTile - 1) / kTile); }
+
+RELO_DEFINE_CHECK_READER(check_failures_scene)
 
 }  // namespace relo

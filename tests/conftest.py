@@ -55,3 +55,13 @@ def room_forest(room_training):
     from paper_1801_08361_gb300 import synth
     nodes = synth.random_forest_nodes(5, 10, seed=5, depth_tau=100, colour_tau=32)
     return oracle.train_forest(nodes, room_training, oracle.LeafParams(capacity=64, max_modes=10, seed=7))
+
+
+def pytest_sessionfinish(session, exitstatus):
+    """With RELO_CHECK_REPORT set (runs against the bounds-checked build), write the number of
+    failed index checks the library counted during the session to that file."""
+    path = os.environ.get("RELO_CHECK_REPORT")
+    if path:
+        from paper_1801_08361_gb300 import binding as B
+        with open(path, "w") as f:
+            f.write(str(int(B.lib().relo_debug_check_failures())))
