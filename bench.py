@@ -43,10 +43,12 @@ METRIC = "reloc attempts/s at 640x480 (forest vs learned, same success); % HBM r
 UNIT = "attempts/s"
 WORKLOAD = "house 10x8x3 m, 5 mm voxels, 2^20 buckets; 640x480 queries, depth noise 1.5 mm z^2; forest T=5 D=15, " \
            "reservoir 1024, <=10 modes; preemptive RANSAC K=1024, B=64"
-W, H = 640, 480
-T_TREES, DEPTH, MAX_MODES, CAPACITY = 5, 15, 10, 1024
-K_HYPS, B_PIX = 1024, 64
-TRAIN_PER_ROOM = 16
+from paper_1801_08361_gb300.presets import HOUSE, LEARNED, SERVING  # noqa: E402
+
+W, H = HOUSE.sizes[0]
+T_TREES, DEPTH, MAX_MODES, CAPACITY = HOUSE.trees, HOUSE.depth, HOUSE.max_modes, HOUSE.reservoir
+K_HYPS, B_PIX = HOUSE.hypotheses[0], HOUSE.batch_pixels
+TRAIN_PER_ROOM = HOUSE.train_per_room
 L2_FLUSH_BYTES = 512 << 20
 
 # Algorithmic bytes per unit: per query pixel the raycast must write depth (2 B) + colour (4 B)
@@ -477,8 +479,8 @@ def run_ours(args):
 # Learned path: online training of the regressor on renders of the house, then the same attempts
 # relocalised with it (learned only, and with the forest as fallback)
 # ------------------------------------------------------------------------------------------------
-TRAIN_BATCH, TRAIN_LR = 16, 3e-4
-REG_ORIGIN = (5.0, 4.0, 1.5)   # centre of the house
+TRAIN_BATCH, TRAIN_LR = LEARNED.extra["train_batch"], LEARNED.extra["lr"]
+REG_ORIGIN = LEARNED.extra["origin"]   # centre of the house
 
 
 def regressor_flops_per_view():
@@ -624,8 +626,9 @@ def fusion_section(args, B, synth, torch, dev, scene, world, intr, train, nvtx=N
 # Serving: agents (threads) submit single attempts at Poisson times to relo_server; the worker
 # batches them under the workspace budget; latency = completion - submission
 # ------------------------------------------------------------------------------------------------
-SERVE_POINTS = [(8, 200.0), (16, 4000.0)]   # (agents, offered requests/s over all agents)
-SERVE_MAX_BATCH, SERVE_MAX_WAIT_US, SERVE_SLOTS = 64, 2000, 512
+# (agents, offered requests/s over all agents)
+SERVE_POINTS = list(zip(SERVING.extra["agents"], SERVING.extra["offered_per_s"]))
+SERVE_MAX_BATCH, SERVE_MAX_WAIT_US, SERVE_SLOTS = (SERVING.extra[k] for k in ("max_batch", "max_wait_us", "slots"))
 
 
 def serving_section(args, B, torch, dev, st, prm):
