@@ -5,4 +5,4 @@ The compute path lives in ``csrc/`` (sm_103a CUDA behind a C ABI declared in
 device pointers and streams.  Importing this package does not load the CUDA
 library: ``binding.lib()`` does, and fails loudly when it is missing.
 """
-__all__ = ["binding", "synth", "presets", "study"]
+__all__ = ["binding", "synth", "presets", "study", "checkpoint"]
