@@ -315,14 +315,6 @@ relo_status relo_ransac_relocalise(const relo_forest* forest, const uint16_t* de
                                    const relo_intrinsics* intr, const relo_ransac_params* p, void* workspace_dev,
                                    size_t workspace_bytes, relo_pose_result* result_dev, relo_stream stream);
 
-/* Stage-isolated RANSAC steps (the same kernels as relo_ransac_relocalise), for checking each
- * step against the oracle under teacher forcing.  Workspace as above.
- * relo_ransac_hypotheses: poses_dev [K][12] (row-major R | t, camera -> scene), valid_dev [K],
- * tries_dev [K] (index of the kept try, max_tries if none).
- * relo_ransac_round: one round r from the given state: alive_dev [n_alive] hypothesis indices,
- * poses_dev [K][12] and energy_dev [K] updated in place, drawn_dev [(r+1) * batch] positions in
- * the valid-pixel list (depth > 0, raster order) of the pixels drawn in rounds 0..r (only
- * round r's slice is written), survivors_dev [ceil(n_alive/2)] and inliers_dev [K] written. */
 /* Allocation-free variant of relo_ransac_relocalise (the paper has no counterpart; this serves
  * callers, not the method).  Some callers may not allocate device memory when they relocalise:
  * a process whose device memory is owned and budgeted by another allocator, or a latency-bound
@@ -344,6 +336,14 @@ relo_status relo_ransac_relocalise_noalloc(const relo_forest* forest, const uint
                                            const relo_ransac_params* p, relo_pose_result* result_dev,
                                            relo_stream stream);
 
+/* Stage-isolated RANSAC steps (the same kernels as relo_ransac_relocalise), for checking each
+ * step against the oracle under teacher forcing.  Workspace as above.
+ * relo_ransac_hypotheses: poses_dev [K][12] (row-major R | t, camera -> scene), valid_dev [K],
+ * tries_dev [K] (index of the kept try, max_tries if none).
+ * relo_ransac_round: one round r from the given state: alive_dev [n_alive] hypothesis indices,
+ * poses_dev [K][12] and energy_dev [K] updated in place, drawn_dev [(r+1) * batch] positions in
+ * the valid-pixel list (depth > 0, raster order) of the pixels drawn in rounds 0..r (only
+ * round r's slice is written), survivors_dev [ceil(n_alive/2)] and inliers_dev [K] written. */
 relo_status relo_ransac_hypotheses(const relo_forest* forest, const uint16_t* depth_dev, const uint16_t* leaves_dev,
                                    const relo_intrinsics* intr, const relo_ransac_params* p, void* workspace_dev,
                                    size_t workspace_bytes, double* poses_dev, int32_t* valid_dev, int32_t* tries_dev,
