@@ -41,7 +41,7 @@ typedef struct CUstream_st* relo_stream; /* same object as cudaStream_t; NULL = 
 typedef int relo_status;
 #define RELO_OK 0
 #define RELO_EINVAL (-1)    /* bad argument (size, pointer, alignment) */
-#define RELO_ENOMEM (-2)    /* device allocation failed (scene / forest creation only) */
+#define RELO_ENOMEM (-2)    /* device allocation failed (creation calls) */
 #define RELO_ECUDA (-3)     /* a CUDA runtime call failed */
 #define RELO_ETIMEOUT (-4)  /* a bounded device loop gave up */
 #define RELO_EDEVICE (-5)   /* a device-side bounds check failed */
@@ -50,6 +50,26 @@ typedef int relo_status;
 
 /* Message for the last failing call on this thread ("" if none). */
 const char* relo_last_error(void);
+
+/* Device memory.  By default the library takes the device memory behind its handles (scenes,
+ * forests, regressors, batches, servers) and its temporary buffers from cudaMalloc and returns it
+ * with cudaFree.  relo_set_allocator routes every later allocation through the caller's functions
+ * instead, e.g. a framework's caching allocator, so that one allocator owns and budgets the
+ * process's device memory:
+ *   alloc(bytes, ctx) returns a device pointer of the current device, aligned to 256 bytes,
+ *     usable from any stream, or NULL when it cannot; the library call then fails as it does
+ *     when cudaMalloc fails (RELO_ENOMEM from creation calls).  A pointer that is not 256-byte
+ *     aligned is handed straight back to free and counts as a failed allocation;
+ *   free(ptr, ctx) takes back a pointer that alloc returned.  The library synchronises the
+ *     device before it calls free, as cudaFree would, so no launch still uses the block.
+ * Each block goes back to the functions that gave it: memory allocated before a change of
+ * allocator is still returned to the old one, so the old functions and ctx must stay valid until
+ * every handle created under them is destroyed.  alloc and free NULL restore cudaMalloc /
+ * cudaFree.  Calls to alloc and free come from the thread of the library call that needs them.
+ * Errors: RELO_EINVAL (exactly one of alloc and free is NULL). */
+typedef void* (*relo_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*relo_free_fn)(void* ptr, void* ctx);
+relo_status relo_set_allocator(relo_alloc_fn alloc, relo_free_fn free_fn, void* ctx);
 
 /* Pinhole camera.  The ray through pixel (u, v) is C + lam * R ((u-cx)/fx, (v-cy)/fy, 1),
  * lam = camera-space z, marched over [depth_min, depth_max] metres. */

@@ -67,6 +67,11 @@ class Attempt(ctypes.Structure):
 RESULT_BYTES = ctypes.sizeof(PoseResult)
 
 
+# relo_set_allocator's callbacks: alloc(bytes, ctx) -> device pointer or NULL; free(ptr, ctx)
+ALLOC_FN = ctypes.CFUNCTYPE(c_vp, ctypes.c_size_t, c_vp)
+FREE_FN = ctypes.CFUNCTYPE(None, c_vp, c_vp)
+
+
 class Schedule(ctypes.Structure):
     _fields_ = [("ray_warp_width", c_i32), ("forest_threads", c_i32), ("forest_tiles", c_i32),
                 ("search_ctas_per_sm", c_i32), ("refit_per", c_i32)]
@@ -155,6 +160,7 @@ _SIGS = {
     "relo_batch_replay": (c_i32, [c_vp, c_vp]),
     "relo_batch_attempt_images": (c_i32, [c_vp, c_i32, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp),
                                           ctypes.POINTER(c_vp)]),
+    "relo_set_allocator": (c_i32, [ALLOC_FN, FREE_FN, c_vp]),
     "relo_debug_fail_allocations": (None, [c_i32]),
     "relo_debug_check_failures": (c_i64, []),
     "relo_debug_corrupt_scene": (c_i32, [c_vp]),
@@ -817,6 +823,45 @@ class PoseGraph:
 
     def __del__(self):
         self.close()
+
+
+# Device memory (relo_set_allocator)
+# ------------------------------------------------------------------------------------------------
+# Every callback pair handed to the library stays referenced for the life of the process: blocks
+# go back to the functions that gave them, even after the allocator changed.
+_ALLOCATORS = []
+
+
+def set_allocator(alloc=None, free=None):
+    """Route the library's device allocations through alloc(nbytes) -> int device pointer (0 or an
+    exception: the allocation fails) and free(ptr), both Python callables; set_allocator() goes
+    back to cudaMalloc / cudaFree.  Blocks allocated earlier go back to the allocator that gave
+    them; the library synchronises the device before it calls free."""
+    if (alloc is None) != (free is None):
+        raise ValueError("give both alloc and free, or neither")
+    if alloc is None:
+        _check(lib().relo_set_allocator(ALLOC_FN(), FREE_FN(), None))
+        return
+
+    def _alloc(nbytes, _ctx):
+        try:
+            return int(alloc(int(nbytes))) or None
+        except Exception:     # noqa: BLE001 -- reported to the library as a failed allocation
+            return None
+
+    def _free(ptr, _ctx):
+        free(int(ptr))
+
+    pair = (ALLOC_FN(_alloc), FREE_FN(_free))
+    _ALLOCATORS.append(pair)
+    _check(lib().relo_set_allocator(pair[0], pair[1], None))
+
+
+def use_torch_allocator(device=None):
+    """The library's device memory from torch's caching allocator (torch.cuda.memory_allocated
+    then counts scenes, forests, regressors and servers)."""
+    import torch
+    set_allocator(lambda n: torch.cuda.caching_allocator_alloc(n, device), torch.cuda.caching_allocator_delete)
 
 
 # Fault injection (tests of the error paths)

@@ -11,6 +11,7 @@
 #include <string>
 #include <atomic>
 #include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include "regressor.cuh"
@@ -24,15 +25,64 @@ static_assert(sizeof(relo_intrinsics) == 56, "relo_intrinsics layout is part of 
 
 namespace relo {
 std::atomic<int> g_fail_allocations{0};
+
+// The caller's allocator (relo_set_allocator), and every block it gave the library, with the
+// functions that gave it: a block goes back to those even after the allocator has changed.
+struct Allocator {
+  relo_alloc_fn alloc = nullptr;
+  relo_free_fn free = nullptr;
+  void* ctx = nullptr;
+};
+std::mutex g_alloc_mu;
+Allocator g_alloc;
+std::unordered_map<void*, Allocator> g_alloc_owned;
+
 cudaError_t dev_malloc(void** p, size_t bytes) {
+  *p = nullptr;
   int n = g_fail_allocations.load();
   while (n > 0) {
-    if (g_fail_allocations.compare_exchange_weak(n, n - 1)) {
-      *p = nullptr;
-      return cudaErrorMemoryAllocation;
+    if (g_fail_allocations.compare_exchange_weak(n, n - 1)) return cudaErrorMemoryAllocation;
+  }
+  Allocator a;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    a = g_alloc;
+  }
+  if (!a.alloc) return cudaMalloc(p, bytes);
+  if (bytes == 0) return cudaSuccess;
+  void* q = a.alloc(bytes, a.ctx);
+  if (!q) return cudaErrorMemoryAllocation;
+  if (((uintptr_t)q & 255) != 0) {
+    a.free(q, a.ctx);
+    return cudaErrorMemoryAllocation;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc_owned[q] = a;
+  }
+  *p = q;
+  return cudaSuccess;
+}
+
+void dev_free(void* p) {
+  if (!p) return;
+  Allocator a;
+  bool theirs = false;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    auto it = g_alloc_owned.find(p);
+    if (it != g_alloc_owned.end()) {
+      a = it->second;
+      g_alloc_owned.erase(it);
+      theirs = true;
     }
   }
-  return cudaMalloc(p, bytes);
+  if (!theirs) {
+    cudaFree(p);
+    return;
+  }
+  cudaDeviceSynchronize();  // as cudaFree does: no launch may still use the block
+  a.free(p, a.ctx);
 }
 }  // namespace relo
 
@@ -350,11 +400,11 @@ relo_status relo_create_scene(const int32_t* coords, const float* tsdf, const ui
   s->n_blocks = n;
   s->n_excess = (int64_t)excess.size();
   auto cleanup = [&]() {
-    cudaFree(s->d_buckets);
-    cudaFree(s->d_excess);
-    cudaFree(s->d_tsdf);
-    cudaFree(s->d_rgba);
-    cudaFree(s->d_grid);
+    relo::dev_free(s->d_buckets);
+    relo::dev_free(s->d_excess);
+    relo::dev_free(s->d_tsdf);
+    relo::dev_free(s->d_rgba);
+    relo::dev_free(s->d_grid);
     delete s;
   };
   if (!grid.empty() && (relo::dev_malloc((void**)&s->d_grid, grid.size() * 4) != cudaSuccess ||
@@ -407,14 +457,14 @@ relo_status relo_create_scene(const int32_t* coords, const float* tsdf, const ui
 
 void relo_destroy_scene(relo_scene* s) {
   if (!s) return;
-  cudaFree(s->d_buckets);
-  cudaFree(s->d_excess);
-  cudaFree(s->d_tsdf);
-  cudaFree(s->d_rgba);
-  cudaFree(s->d_grid);
-  cudaFree(s->d_weight);
-  cudaFree(s->d_coords);
-  cudaFree(s->d_counters);
+  relo::dev_free(s->d_buckets);
+  relo::dev_free(s->d_excess);
+  relo::dev_free(s->d_tsdf);
+  relo::dev_free(s->d_rgba);
+  relo::dev_free(s->d_grid);
+  relo::dev_free(s->d_weight);
+  relo::dev_free(s->d_coords);
+  relo::dev_free(s->d_counters);
   delete s;
 }
 
@@ -624,6 +674,15 @@ relo_status relo_scene_export(const relo_scene* scene, int32_t* coords, float* t
   return st;
 }
 
+relo_status relo_set_allocator(relo_alloc_fn alloc, relo_free_fn free_fn, void* ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) return fail(RELO_EINVAL, "alloc and free must both be set or both be null");
+  std::lock_guard<std::mutex> lk(relo::g_alloc_mu);
+  relo::g_alloc.alloc = alloc;
+  relo::g_alloc.free = free_fn;
+  relo::g_alloc.ctx = alloc ? ctx : nullptr;
+  return RELO_OK;
+}
+
 void relo_debug_fail_allocations(int32_t n) { relo::g_fail_allocations.store(n > 0 ? n : 0); }
 
 int64_t relo_debug_check_failures(void) {
@@ -824,10 +883,10 @@ relo_status relo_create_forest(const void* nodes, int32_t T, int32_t D, const fl
 
 void relo_destroy_forest(relo_forest* f) {
   if (!f) return;
-  cudaFree(f->d_nodes);
-  cudaFree(f->d_modes);
-  cudaFree(f->d_n_modes);
-  cudaFree(f->d_top);
+  relo::dev_free(f->d_nodes);
+  relo::dev_free(f->d_modes);
+  relo::dev_free(f->d_n_modes);
+  relo::dev_free(f->d_top);
   free(f->res_samples);
   free(f->res_count);
   free(f->res_seen);
@@ -892,7 +951,7 @@ relo_status relo_forest_train_frame(relo_forest* f, const relo_intrinsics* intr,
   float* d_coords = nullptr;
   RELO_CUDA(relo::dev_malloc((void**)&d_leaves, n_pix * T * sizeof(uint16_t)));
   if (relo::dev_malloc((void**)&d_coords, (size_t)gw * gh * 3 * sizeof(float)) != cudaSuccess) {
-    cudaFree(d_leaves);
+    relo::dev_free(d_leaves);
     return fail(RELO_ENOMEM, "training scratch");
   }
   ForestJob j{};
@@ -910,8 +969,8 @@ relo_status relo_forest_train_frame(relo_forest* f, const relo_intrinsics* intr,
   if (e == cudaSuccess) e = cudaMemcpyAsync(dep.data(), depth, n_pix * 2, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(coords.data(), d_coords, coords.size() * 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaFree(d_leaves);
-  cudaFree(d_coords);
+  relo::dev_free(d_leaves);
+  relo::dev_free(d_coords);
   if (e != cudaSuccess) return cuda_fail(e, "training frame");
   // Algorithm R per leaf, offers in raster order, trees in order (host, sequential by definition)
   const int cap = f->train.capacity;
@@ -958,7 +1017,7 @@ relo_status relo_forest_train_finish(relo_forest* f, relo_stream stream) {
   int32_t* d_count = nullptr;
   RELO_CUDA(relo::dev_malloc((void**)&d_samples, L * cap * 3 * sizeof(float)));
   if (relo::dev_malloc((void**)&d_count, L * sizeof(int32_t)) != cudaSuccess) {
-    cudaFree(d_samples);
+    relo::dev_free(d_samples);
     return fail(RELO_ENOMEM, "training scratch");
   }
   cudaError_t e = cudaMemcpyAsync(d_samples, f->res_samples, L * cap * 3 * sizeof(float), cudaMemcpyHostToDevice, s);
@@ -971,8 +1030,8 @@ relo_status relo_forest_train_finish(relo_forest* f, relo_stream stream) {
   if (e == cudaSuccess) e = launch_top_modes((const float*)f->d_modes, (const uint8_t*)f->d_n_modes, (int)L, f->M,
                                              (float4*)f->d_top, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaFree(d_samples);
-  cudaFree(d_count);
+  relo::dev_free(d_samples);
+  relo::dev_free(d_count);
   if (e != cudaSuccess) return cuda_fail(e, "mean shift");
   return RELO_OK;
 }
@@ -1480,14 +1539,14 @@ relo_status relo_create_regressor(const float* params, uint64_t seed, const doub
 
 void relo_destroy_regressor(relo_regressor* r) {
   if (!r) return;
-  cudaFree(r->d_p);
-  cudaFree(r->d_g);
-  cudaFree(r->d_m);
-  cudaFree(r->d_v);
+  relo::dev_free(r->d_p);
+  relo::dev_free(r->d_g);
+  relo::dev_free(r->d_m);
+  relo::dev_free(r->d_v);
   for (int l = 0; l < kRegLayers; ++l) {
-    cudaFree(r->d_wk[l]);
-    cudaFree(r->d_wt[l]);
-    cudaFree(r->d_bias[l]);
+    relo::dev_free(r->d_wk[l]);
+    relo::dev_free(r->d_wt[l]);
+    relo::dev_free(r->d_bias[l]);
   }
   delete r;
 }

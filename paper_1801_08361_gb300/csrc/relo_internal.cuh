@@ -438,9 +438,12 @@ unsigned long long check_failures_forest();
 unsigned long long check_failures_ransac();
 unsigned long long check_failures_fusion();
 
-// Every device allocation of the library goes through here, so that tests can make the next
-// allocations fail (relo_debug_fail_allocations) and check the error paths.
+// Every device allocation of the library goes through here: from cudaMalloc, or from the
+// caller's allocator (relo_set_allocator); tests can make the next allocations fail
+// (relo_debug_fail_allocations) and check the error paths.  dev_free returns a block to
+// whichever of the two gave it (null is ignored).
 cudaError_t dev_malloc(void** p, size_t bytes);
+void dev_free(void* p);
 
 // TSDF fusion of one frame into a growing scene (fusion.cu).
 struct FuseJob {

@@ -22,6 +22,7 @@
 
 namespace relo {
 cudaError_t dev_malloc(void** p, size_t bytes);  // the library's device allocations (api.cu)
+void dev_free(void* p);
 }
 
 namespace {
@@ -149,7 +150,7 @@ relo_status relo_server_create(const relo_server_params* params, relo_server** o
     return RELO_ENOMEM;
   }
   if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
-    cudaFree(s->ws);
+    relo::dev_free(s->ws);
     delete s;
     return RELO_ECUDA;
   }
@@ -229,7 +230,7 @@ void relo_server_destroy(relo_server* s) {
   s->cv_work.notify_all();
   if (s->worker.joinable()) s->worker.join();
   cudaStreamDestroy(s->stream);
-  cudaFree(s->ws);
+  relo::dev_free(s->ws);
   delete s;
 }
 

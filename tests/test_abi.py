@@ -41,6 +41,9 @@ C_CLIENT = r"""
 #include <string.h>
 #include "relo.h"
 
+static void* fake_alloc(size_t bytes, void* ctx) { (void)bytes; (void)ctx; return NULL; }
+static void fake_free(void* ptr, void* ctx) { (void)ptr; (void)ctx; }
+
 int main(void) {
   relo_pose_graph* g = NULL;
   if (relo_pose_graph_create(0, &g) != RELO_EINVAL) return 1;      /* bad size rejected */
@@ -62,6 +65,11 @@ int main(void) {
   relo_schedule s;
   memset(&s, 0, sizeof s);
   if (relo_batch_set_schedule(NULL, &s) != RELO_EINVAL || strlen(relo_last_error()) == 0) return 10;
+  if (relo_set_allocator(NULL, NULL, NULL) != RELO_OK) return 11;          /* back to cudaMalloc */
+  if (relo_set_allocator(fake_alloc, NULL, NULL) != RELO_EINVAL) return 12; /* both or neither */
+  if (relo_set_allocator(NULL, fake_free, NULL) != RELO_EINVAL) return 13;
+  if (relo_set_allocator(fake_alloc, fake_free, &s) != RELO_OK) return 14;
+  if (relo_set_allocator(NULL, NULL, NULL) != RELO_OK) return 15;
   printf("ok\n");
   return 0;
 }
@@ -70,7 +78,8 @@ int main(void) {
 
 def test_a_c_program_uses_the_abi(tmp_path):
     """The header is plain C99 and the library links into a C program: host-only calls (the pose
-    graph, argument errors and relo_last_error) behave as documented without a GPU."""
+    graph, argument errors, relo_last_error and relo_set_allocator) behave as documented without
+    a GPU."""
     import subprocess
     build.build()
     src = tmp_path / "client.c"
@@ -83,3 +92,14 @@ def test_a_c_program_uses_the_abi(tmp_path):
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0, (out.returncode, out.stderr)
     assert out.stdout.strip() == "ok"
+
+
+def test_set_allocator_arguments():
+    """Host side of relo_set_allocator: both callbacks or neither (no allocation is made here)."""
+    import pytest
+    with pytest.raises(ValueError):
+        B.set_allocator(lambda n: 0)
+    L = B.lib()
+    assert L.relo_set_allocator(B.ALLOC_FN(lambda n, c: None), B.FREE_FN(), None) == B.EINVAL
+    B.set_allocator(lambda n: 0, lambda p: None)
+    B.set_allocator()
