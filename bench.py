@@ -75,6 +75,16 @@ PROFILED_TRAFFIC_BYTES_PER_ATTEMPT = {
     "forest_hypotheses": (0.637e9 + 0.005e9) / 128,
     "forest_verify": (1.868e9 + 0.032e9) / 128,
 }
+# What limits each stage's main kernel in the same capture (the roofline fraction divides by DRAM
+# bandwidth or an integer-issue peak; these kernels gather from L2 and are bound elsewhere).
+PROFILED_LIMITER = {
+    "query_raycast": "instruction issue (71 % active; 17.1 of 32 lanes per instruction as rays end at "
+                     "different steps); L2 throughput 9 %",
+    "forest_eval": "instruction issue (68 % active at 98 % warps active) and long-scoreboard stalls on "
+                   "node and probe loads (L2 hit 98 %, L2 throughput 44 %)",
+    "forest_hypotheses": "L2 throughput (63 %, L2 hit 98 %): four random 16-byte gathers per try",
+    "forest_verify": "instruction issue (73 % active; 16.7 of 32 lanes per instruction); L2 throughput 12 %",
+}
 
 
 def parse():
@@ -740,13 +750,14 @@ def roofline(kernel, avg_ms, attempts, tries_per_launch, clocks):
         achieved = tries_per_launch / (avg_ms / 1000.0) / 1e9
         return {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gtries/s",
                 "frac": achieved / peak, "traffic": profiled_traffic(kernel, attempts), "ms": avg_ms,
-                "peak_source": "derived: 64 IMAD/clk/SM x 152 SMs x max SM clock / 40 IMAD per try"}
+                "peak_source": "derived: 64 IMAD/clk/SM x 152 SMs x max SM clock / 40 IMAD per try",
+                "limiter": PROFILED_LIMITER.get(kernel)}
     peak, peak_kind = measured_peaks()
     per_px = ALG_BYTES_PER_PIXEL.get(kernel)
     achieved = None if per_px is None else per_px * W * H * attempts / (avg_ms / 1000.0) / 1e9
     return {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": None if achieved is None else achieved / peak, "traffic": profiled_traffic(kernel, attempts),
-            "ms": avg_ms, "peak_source": peak_kind}
+            "ms": avg_ms, "peak_source": peak_kind, "limiter": PROFILED_LIMITER.get(kernel)}
 
 
 def ctypes_attempt_bytes():
