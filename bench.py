@@ -204,6 +204,16 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def bf16_peaks():
+    """(burst, sustained) dense BF16 TFLOP/s: measured, else the fallback figures."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["bf16_tflops"]), float(p["bf16_tflops_sustained"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, 1700.0, "fallback"
+
+
 # ------------------------------------------------------------------------------------------------
 # CPU oracle baseline (bounded sample)
 # ------------------------------------------------------------------------------------------------
@@ -562,9 +572,13 @@ def learned_section(args, B, synth, torch, dev, scene, forest, world, intr, trai
     train_step_ms = train_ms / args.train_steps
     # forward + backward-data + backward-weight: about 3 forward passes of work per view
     train_tflops = 3 * regressor_flops_per_view() * nb / (train_step_ms / 1000.0) / 1e12
+    burst, sustained, peak_kind = bf16_peaks()
+    # the training loop runs for seconds (the sustained peak); a forward runs inside one batch (burst)
     out = {"train_steps": args.train_steps, "train_batch": nb, "lr": TRAIN_LR,
            "train_ms_per_step": train_step_ms, "render_ms_per_step": render_ms / args.train_steps,
-           "train_tflops": train_tflops, "loss_first_last_100": [float(L[:100].mean()), float(L[-100:].mean())]}
+           "train_tflops": train_tflops, "train_frac": train_tflops / sustained,
+           "bf16_peaks": {"burst": burst, "sustained": sustained, "source": peak_kind},
+           "loss_first_last_100": [float(L[:100].mean()), float(L[-100:].mean())]}
     A = len(st["qs"])
     for name, with_forest in (("learned_only", False), ("learned_with_fallback", True)):
         items = [dict(scene_b=scene, forest_a=forest if with_forest else None, scene_a=scene, regressor_a=reg,
@@ -601,6 +615,7 @@ def learned_section(args, B, synth, torch, dev, scene, forest, world, intr, trai
                      "verified_rate": ver / A, "paths_forest_learned_fallback": paths,
                      "learned_forward_ms": stages.get("learned_forward", 0.0),
                      "learned_forward_tflops": regressor_flops_per_view() * A / max(stages.get("learned_forward", 0.0), 1e-9) / 1e9}
+        out[name]["learned_forward_frac"] = out[name]["learned_forward_tflops"] / burst
     return out
 
 
