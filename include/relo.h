@@ -17,7 +17,8 @@
  *     colour uint8 RGBA (4 bytes per pixel; alpha 255 where depth is valid).
  *   - "_dev" pointers are CUDA device pointers, "_host" pointers host memory.
  *     The caller owns every buffer it passes and the stream; the library owns
- *     its opaque handles (scene, forest) and the device memory behind them.
+ *     its opaque handles (scene, forest, ...) and the device memory behind them
+ *     (from cudaMalloc, or from the caller's allocator: relo_set_allocator).
  *   - Calls are asynchronous on the given stream unless stated otherwise.
  *     Outputs are valid once the stream has synchronised.
  *   - Every call returns RELO_OK (0) or a negative relo_status; on error the
