@@ -103,3 +103,33 @@ def test_set_allocator_arguments():
     assert L.relo_set_allocator(B.ALLOC_FN(lambda n, c: None), B.FREE_FN(), None) == B.EINVAL
     B.set_allocator(lambda n: 0, lambda p: None)
     B.set_allocator()
+
+
+LAYOUTS = {"relo_intrinsics": B.Intrinsics, "relo_train_params": B.TrainParams,
+           "relo_ransac_params": B.RansacParams, "relo_pose_result": B.PoseResult, "relo_attempt": B.Attempt,
+           "relo_schedule": B.Schedule, "relo_server_params": B.ServerParams, "relo_server_stats": B.ServerStats}
+
+
+def test_binding_structs_match_the_header_layouts(tmp_path):
+    """Every struct the binding passes by pointer has the header's size and field offsets, as a C
+    compiler lays them out (a C program prints sizeof / offsetof)."""
+    import subprocess
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "relo.h"', "int main(void) {"]
+    for cname, cls in LAYOUTS.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                           "-o", str(exe)])
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        name, field, value = line.split()
+        got[(name, field)] = int(value)
+    for cname, cls in LAYOUTS.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
