@@ -1,0 +1,158 @@
+"""Planted mistakes: each test swaps one oracle function for a copy with one plausible error (a
+dropped term, a wrong sign, a transposed operand, an off-by-one comparison) and checks that one of
+the oracle's pins then fails.  The mistakes live only here, on the CPU, for the length of a test
+(monkeypatch restores the oracle); they show that the pins can tell a wrong oracle from a right one."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.posegraph as PG
+from oracle import regressor as R
+
+import test_oracle_forest_verify as pins_verify
+import test_oracle_posegraph as pins_pg
+import test_oracle_ransac as pins_ransac
+import test_oracle_regressor as pins_reg
+
+
+def _fails(pin, *args):
+    with pytest.raises(AssertionError):
+        pin(*args)
+
+
+# -- Kabsch ----------------------------------------------------------------------------------------
+
+def test_kabsch_without_the_reflection_fix(monkeypatch):
+    def kabsch(c, w):
+        c, w = np.asarray(c, np.float64), np.asarray(w, np.float64)
+        cb, wb = c.mean(0), w.mean(0)
+        U, _, Vt = np.linalg.svd((c - cb).T @ (w - wb))
+        Rm = Vt.T @ U.T                       # mistake: det(R) may be -1
+        return Rm, wb - Rm @ cb
+    monkeypatch.setattr(oracle, "kabsch", kabsch)
+    _fails(pins_ransac.test_kabsch_returns_proper_rotation_for_mirrored_points)
+
+
+def test_kabsch_with_a_transposed_rotation(monkeypatch):
+    right = oracle.kabsch
+
+    def kabsch(c, w):
+        Rm, _ = right(c, w)
+        c, w = np.asarray(c, np.float64), np.asarray(w, np.float64)
+        return Rm.T, w.mean(0) - Rm.T @ c.mean(0)   # mistake: R^T for R
+    monkeypatch.setattr(oracle, "kabsch", kabsch)
+    _fails(pins_ransac.test_kabsch_recovers_known_transform)
+
+
+# -- pixel energy ----------------------------------------------------------------------------------
+
+def test_energy_without_the_covariance_cross_terms(monkeypatch):
+    right = oracle.pixel_energies
+
+    def pixel_energies(pose, cam, pix, leaves, forest):
+        modes = forest.modes.copy()
+        modes[..., [4, 5, 7]] = 0.0           # mistake: the off-diagonal inverse-covariance terms dropped
+        return right(pose, cam, pix, leaves, dataclasses.replace(forest, modes=modes))
+    monkeypatch.setattr(oracle, "pixel_energies", pixel_energies)
+    _fails(pins_ransac.test_pixel_energy_matches_gaussian_density)
+
+
+def test_energy_with_the_wrong_floor(monkeypatch):
+    monkeypatch.setattr(oracle, "LOG_EPS", -np.log(1e-20))     # mistake: a density floor of 1e-20
+    _fails(pins_ransac.test_pixel_energy_single_isotropic_gaussian_closed_form)
+
+
+# -- verification ----------------------------------------------------------------------------------
+
+def test_verification_accepting_half_valid(monkeypatch):
+    def verify_accept(counts, valid_fraction=0.5, max_mean_mm=50):
+        n, oa, _, oab, s = (int(x) for x in counts)
+        if not oa >= valid_fraction * n:     # mistake: >= where the paper's test is strict
+            return False
+        return oab > 0 and s < max_mean_mm * oab
+    monkeypatch.setattr(oracle, "verify_accept", verify_accept)
+    _fails(pins_verify.test_verification_decision_rules)
+
+
+def test_verification_with_an_inclusive_mean_bound(monkeypatch):
+    def verify_accept(counts, valid_fraction=0.5, max_mean_mm=50):
+        n, oa, _, oab, s = (int(x) for x in counts)
+        if not oa > valid_fraction * n:
+            return False
+        return oab > 0 and s <= max_mean_mm * oab   # mistake: mean <= 5 cm accepted
+    monkeypatch.setattr(oracle, "verify_accept", verify_accept)
+    _fails(pins_verify.test_verification_decision_rules)
+
+
+# -- pose graph ------------------------------------------------------------------------------------
+
+def test_blend_without_quaternion_sign_alignment(monkeypatch):
+    def dq_blend(samples):
+        real, dual = np.zeros(4), np.zeros(4)
+        for T in samples:
+            q = PG.quat_wxyz(T[:3, :3])      # mistake: q and -q not brought to one hemisphere
+            real += q
+            dual += 0.5 * PG.qmul(np.concatenate([[0.0], T[:3, 3]]), q)
+        n = np.linalg.norm(real)
+        real, dual = real / n, dual / n
+        out = np.eye(4)
+        w, x, y, z = real
+        from scipy.spatial.transform import Rotation
+        out[:3, :3] = Rotation.from_quat([x, y, z, w]).as_matrix()
+        out[:3, 3] = 2.0 * PG.qmul(dual, real * np.array([1, -1, -1, -1]))[1:]
+        return out
+    monkeypatch.setattr(PG, "dq_blend", dq_blend)
+    _fails(pins_pg.test_blend_aligns_quaternion_signs)
+
+
+def test_quaternion_product_with_a_flipped_cross_term(monkeypatch):
+    def qmul(a, b):
+        w1, x1, y1, z1 = a
+        w2, x2, y2, z2 = b
+        return np.array([w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2, w1 * x2 + x1 * w2 - y1 * z2 + z1 * y2,
+                         w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2, w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2])
+    monkeypatch.setattr(PG, "qmul", qmul)   # mistake: y1 z2 - z1 y2 with the wrong sign
+    _fails(pins_pg.test_blend_of_opposite_rotations_about_an_offset_axis_is_the_identity)
+
+
+# -- regressor -------------------------------------------------------------------------------------
+
+def test_convolution_instead_of_correlation(monkeypatch):
+    right = R.conv3x3
+    monkeypatch.setattr(R, "conv3x3", lambda x, w, b, stride: right(x, w[::-1, ::-1], b, stride))
+    _fails(pins_reg.test_conv_matches_scipy_correlation, 1, (9, 7))
+
+
+def test_loss_gradient_that_ignores_the_mask(monkeypatch):
+    def loss_and_grad_output(out, target, mask):
+        n = max(int(mask.sum()), 1)
+        s = out[..., 3]
+        err = out[..., :3] - target
+        sq = (err * err).sum(-1)
+        e = np.exp(-s)
+        loss = float(((0.5 * sq * e + 1.5 * s) * mask).sum() / n)
+        g = np.zeros_like(out)
+        g[..., :3] = err * (e / n)[..., None]          # mistake: unscored cells get a gradient
+        g[..., 3] = (-0.5 * sq * e + 1.5) * mask / n
+        return loss, g
+    monkeypatch.setattr(R, "loss_and_grad_output", loss_and_grad_output)
+    _fails(pins_reg.test_gradients_match_central_differences)
+
+
+def test_adam_without_bias_correction(monkeypatch):
+    def step(self, params, grads):
+        ps, gs = params.flat(), grads.flat()
+        if self.m is None:
+            self.m = [np.zeros_like(p) for p in ps]
+            self.v = [np.zeros_like(p) for p in ps]
+        self.t += 1
+        for p, g, m, v in zip(ps, gs, self.m, self.v):
+            m *= self.b1
+            m += (1 - self.b1) * g
+            v *= self.b2
+            v += (1 - self.b2) * g * g
+            p -= self.lr * m / (np.sqrt(v) + self.eps)    # mistake: raw moments
+    monkeypatch.setattr(R.Adam, "step", step)
+    _fails(pins_reg.test_adam_first_step_closed_form)

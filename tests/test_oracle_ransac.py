@@ -93,11 +93,14 @@ def test_pixel_energy_matches_gaussian_density():
     # stored fields are float32: rebuild the density from what is stored
     st = forest.modes[0, 0].astype(np.float64)
     n = 40
-    cam = rng.uniform(-1, 1, (n, 3))
-    leaves = np.zeros((1, 1, n), np.uint16)
+    # scene points within a few standard deviations of the modes (far points would all sit at the
+    # density floor and leave the Gaussian untested); camera points through a random pose
     pose = _random_pose(rng)
-    cam_t = cam  # pose applied inside
-    e, mu, found, x = oracle.pixel_energies(pose, cam_t, np.arange(n), leaves, forest)
+    near = np.array([modes[k % 3][0] for k in range(n)]) + rng.normal(0, 0.04, (n, 3))
+    cam = (near - pose[:3, 3]) @ pose[:3, :3]
+    leaves = np.zeros((1, 1, n), np.uint16)
+    e, mu, found, x = oracle.pixel_energies(pose, cam, np.arange(n), leaves, forest)
+    assert (e < oracle.LOG_EPS - 5.0).all()
     for i in range(n):
         dens = []
         for k in range(3):
