@@ -53,44 +53,47 @@ def build(force: bool = False) -> str:
 def _lib():
     global _LIB
     if _LIB is None:
-        path = build()
-        lib = ctypes.CDLL(path)
-        vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
-        lib.orc_philox4x32_10.argtypes = [vp, vp, vp]
-        lib.orc_philox_many.argtypes = [vp, ctypes.c_long, vp, vp]
-        lib.orc_scene_create.restype = vp
-        lib.orc_scene_create.argtypes = [vp, vp, vp, ctypes.c_long, ctypes.c_double, ctypes.c_double]
-        lib.orc_scene_destroy.argtypes = [vp]
-        lib.orc_scene_find_many.argtypes = [vp, vp, ctypes.c_long, vp]
-        lib.orc_raycast.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, dp, vp, vp,
-                                    ctypes.c_long, vp, vp]
-        lib.orc_raycast_touched.restype = ctypes.c_int
-        lib.orc_raycast_touched.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, dp,
-                                            ctypes.c_int, vp]
-        lib.orc_forest_eval.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, vp]
-        lib.orc_verify_counts.argtypes = [vp, vp, ctypes.c_long, vp]
-        lib.orc_reservoirs_create.restype = vp
-        lib.orc_reservoirs_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint32,
-                                              ctypes.c_uint32]
-        lib.orc_reservoirs_destroy.argtypes = [vp]
-        lib.orc_reservoirs_add_frame.argtypes = [vp, vp, vp, vp, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int]
-        lib.orc_reservoirs_get.argtypes = [vp, vp, vp]
-        lib.orc_mean_shift_leaf.restype = ctypes.c_int
-        lib.orc_mean_shift_leaf.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
-                                            ctypes.c_double, ctypes.c_double, ctypes.c_int, vp]
-        lib.orc_fill_modes.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
-                                       ctypes.c_double, ctypes.c_int, vp, vp]
-        lib.orc_fusion_create.restype = vp
-        lib.orc_fusion_create.argtypes = [ctypes.c_long, ctypes.c_double, ctypes.c_double, ctypes.c_int]
-        lib.orc_fusion_destroy.argtypes = [vp]
-        lib.orc_fusion_frame.restype = ctypes.c_int
-        lib.orc_fusion_frame.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, dp,
-                                         vp, vp]
-        lib.orc_fusion_count.restype = ctypes.c_long
-        lib.orc_fusion_count.argtypes = [vp]
-        lib.orc_fusion_export.argtypes = [vp, vp, vp, vp, vp]
-        _LIB = lib
+        _LIB = declare(ctypes.CDLL(build()))
     return _LIB
+
+
+def declare(lib):
+    """Argument and result types of the C oracle's functions on a loaded copy of it."""
+    vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+    lib.orc_philox4x32_10.argtypes = [vp, vp, vp]
+    lib.orc_philox_many.argtypes = [vp, ctypes.c_long, vp, vp]
+    lib.orc_scene_create.restype = vp
+    lib.orc_scene_create.argtypes = [vp, vp, vp, ctypes.c_long, ctypes.c_double, ctypes.c_double]
+    lib.orc_scene_destroy.argtypes = [vp]
+    lib.orc_scene_find_many.argtypes = [vp, vp, ctypes.c_long, vp]
+    lib.orc_raycast.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, dp, vp, vp,
+                                ctypes.c_long, vp, vp]
+    lib.orc_raycast_touched.restype = ctypes.c_int
+    lib.orc_raycast_touched.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, dp,
+                                        ctypes.c_int, vp]
+    lib.orc_forest_eval.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, vp]
+    lib.orc_verify_counts.argtypes = [vp, vp, ctypes.c_long, vp]
+    lib.orc_reservoirs_create.restype = vp
+    lib.orc_reservoirs_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint32,
+                                          ctypes.c_uint32]
+    lib.orc_reservoirs_destroy.argtypes = [vp]
+    lib.orc_reservoirs_add_frame.argtypes = [vp, vp, vp, vp, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int]
+    lib.orc_reservoirs_get.argtypes = [vp, vp, vp]
+    lib.orc_mean_shift_leaf.restype = ctypes.c_int
+    lib.orc_mean_shift_leaf.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_int, vp]
+    lib.orc_fill_modes.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_int, vp, vp]
+    lib.orc_fusion_create.restype = vp
+    lib.orc_fusion_create.argtypes = [ctypes.c_long, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+    lib.orc_fusion_destroy.argtypes = [vp]
+    lib.orc_fusion_frame.restype = ctypes.c_int
+    lib.orc_fusion_frame.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, dp,
+                                     vp, vp]
+    lib.orc_fusion_count.restype = ctypes.c_long
+    lib.orc_fusion_count.argtypes = [vp]
+    lib.orc_fusion_export.argtypes = [vp, vp, vp, vp, vp]
+    return lib
 
 
 def _d(a):

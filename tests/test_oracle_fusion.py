@@ -25,22 +25,26 @@ def voxel_z(fb):
 
 
 def test_plane_closed_form():
+    # the plane at 1.51 m does not sit on a block boundary, so the allocated blocks hold voxels more
+    # than mu in front of it, where the truncated distance is clamped to 1
+    Z0 = 1.51
     intr = synth.Intrinsics.for_size(64, 48)
     fs = oracle.FusionScene(4096, VOX, MU)
-    assert fs.fuse(intr, np.eye(4), plane(intr, 1500))
+    assert fs.fuse(intr, np.eye(4), plane(intr, 1510))
     fb = fs.blocks()
     assert len(fb.coords) > 0
-    # every allocated block meets the band [1.5 - mu, 1.5 + mu] in z
-    assert np.all(fb.coords[:, 2] * BS <= 1.5 + MU + 1e-6) and np.all((fb.coords[:, 2] + 1) * BS >= 1.5 - MU - 1e-6)
+    # every allocated block meets the band [Z0 - mu, Z0 + mu] in z
+    assert np.all(fb.coords[:, 2] * BS <= Z0 + MU + 1e-6) and np.all((fb.coords[:, 2] + 1) * BS >= Z0 - MU - 1e-6)
     z = voxel_z(fb)
     upd = fb.weight == 1
     assert np.all((fb.weight == 0) | upd)
-    want = np.minimum(1.0, (1.5 - z) / MU)
+    want = np.minimum(1.0, (Z0 - z) / MU)
     assert np.abs(fb.tsdf[upd] - want[upd]).max() < 1e-5
+    assert np.any(upd & (Z0 - z > MU + 1e-6))              # the clamp is exercised
     # voxels more than mu behind the surface were not updated; those in front of it mostly were
-    assert not np.any(upd & (z > 1.5 + MU + 1e-6))
+    assert not np.any(upd & (z > Z0 + MU + 1e-6))
     assert np.all(fb.tsdf[~upd] == 1.0)
-    assert upd[np.abs(z - 1.5) < MU / 2].mean() > 0.5
+    assert upd[np.abs(z - Z0) < MU / 2].mean() > 0.5
 
 
 def test_equal_frames_average_to_themselves_and_weights_stop_at_the_cap():

@@ -90,6 +90,22 @@ def test_reservoir_inclusion_is_uniform():
     assert abs(hits.sum() - trials * cap) == 0
 
 
+def test_reservoir_of_one_keeps_the_second_of_two_samples_half_the_time():
+    """Algorithm R with capacity 1: the second sample replaces the first with probability 1/2
+    (a draw over [0, n) instead of [0, n] would always replace it)."""
+    intr, d, rgb = _frame(2, 4)
+    second = oracle.camera_points(d, intr, np.array([1])).astype(np.float32)[0]
+    trials = 400
+    kept = 0
+    for s in range(trials):
+        r = oracle.Reservoirs(_one_leaf_nodes(), oracle.LeafParams(capacity=1, seed=s))
+        r.add_frame(intr, np.eye(4), d, rgb)
+        samples, count = r.contents()
+        assert count[0, 0] == 1
+        kept += int(np.array_equal(samples[0, 0, 0], second))
+    assert abs(kept - trials / 2) < 4 * np.sqrt(trials / 4)        # binomial, 4 standard deviations
+
+
 def test_stride_and_invalid_pixels_are_skipped():
     intr, d, rgb = _frame(1000, 3)
     d = d.copy()

@@ -156,3 +156,65 @@ def test_adam_without_bias_correction(monkeypatch):
             p -= self.lr * m / (np.sqrt(v) + self.eps)    # mistake: raw moments
     monkeypatch.setattr(R.Adam, "step", step)
     _fails(pins_reg.test_adam_first_step_closed_form)
+
+
+# -- the C part of the oracle ----------------------------------------------------------------------
+# Each case compiles a copy of relo_oracle.c with one edit into a temporary library, points the
+# oracle at it for the test, and runs a pin that must then fail.
+
+import ctypes                                    # noqa: E402
+import os                                        # noqa: E402
+import subprocess                                # noqa: E402
+
+import test_oracle_fusion as pins_fusion        # noqa: E402
+import test_oracle_leaves as pins_leaves        # noqa: E402
+import test_oracle_philox as pins_philox        # noqa: E402
+import test_oracle_scene as pins_scene          # noqa: E402
+
+C_SOURCE = os.path.join(os.path.dirname(oracle.__file__), "relo_oracle.c")
+
+C_MUTATIONS = [
+    # (name, original text, mistaken text, pin that must fail)
+    ("trilinear corner by truncation", "base[a] = (long)floor(q[a]);", "base[a] = (long)q[a];",
+     pins_scene.test_shift_by_whole_blocks_into_negative_coordinates),
+    ("secant root with a wrong sign", "f_prev / (f_prev - f);", "f_prev / (f_prev + f);",
+     pins_scene.test_plane_depth_exact_to_rounding),
+    ("depth rounded down", "double zr = round_half_up(z_mm);", "double zr = floor(z_mm);",
+     pins_scene.test_plane_depth_exact_to_rounding),
+    ("colour channel off by one", "rgb[c] = (double)s->rgba[(b * 512 + li) * 4 + c];",
+     "rgb[c] = (double)s->rgba[(b * 512 + li) * 4 + (c + 1) % 3];", pins_scene.test_linear_colour_is_reproduced),
+    ("forest children swapped", "? 2 * n + 1 : 2 * n + 2;", "? 2 * n + 2 : 2 * n + 1;",
+     pins_verify.test_depth_split_by_hand),
+    ("forest split not strict", "n = (a - b < nd->tau)", "n = (a - b <= nd->tau)",
+     pins_verify.test_offset_truncates_toward_zero_and_invalid_probe_reads_zero),
+    ("forest offset rounded down", "int q1x = clampi(u + (int)(((int32_t)nd->dx1 * 1000) / d), 0, W - 1);",
+     "int q1x = clampi(u + (int)floor(((double)nd->dx1 * 1000) / d), 0, W - 1);",
+     pins_verify.test_offset_truncates_toward_zero_and_invalid_probe_reads_zero),
+    ("verification difference one-sided", "sum += (uint64_t)(da[i] > db[i] ? da[i] - db[i] : db[i] - da[i]);",
+     "sum += (uint64_t)(da[i] > db[i] ? da[i] - db[i] : 0);", pins_verify.test_verification_counts_by_hand),
+    ("Philox key schedule", "k1 += 0xBB67AE85u;", "k1 += 0xBB67AE87u;", pins_philox.test_known_answer_vectors),
+    ("reservoir draw over [0, n)", "uint64_t j = ((uint64_t)o[0] * (uint64_t)(n + 1)) >> 32;",
+     "uint64_t j = ((uint64_t)o[0] * (uint64_t)n) >> 32;",
+     pins_leaves.test_reservoir_of_one_keeps_the_second_of_two_samples_half_the_time),
+    ("mode weight over n + 1 samples", "double weight = (double)cnt / n;", "double weight = (double)cnt / (n + 1);",
+     pins_leaves.test_mean_shift_recovers_blob_centres_and_weights),
+    ("fusion without the truncation clamp", "const float fn = fminf(1.0f, eta / mu);", "const float fn = eta / mu;",
+     pins_fusion.test_plane_closed_form),
+    ("fusion weight without its cap",
+     "f->weight[at] = (uint16_t)(f->weight[at] + 1 < f->max_weight ? f->weight[at] + 1 : f->max_weight);",
+     "f->weight[at] = (uint16_t)(f->weight[at] + 1);",
+     pins_fusion.test_equal_frames_average_to_themselves_and_weights_stop_at_the_cap),
+]
+
+
+@pytest.mark.parametrize("name,right,wrong,pin", C_MUTATIONS, ids=[m[0] for m in C_MUTATIONS])
+def test_c_oracle_mistake_is_caught(name, right, wrong, pin, tmp_path, monkeypatch):
+    src = open(C_SOURCE).read()
+    assert src.count(right) == 1, name
+    c_file = tmp_path / "mutant.c"
+    c_file.write_text(src.replace(right, wrong))
+    so = tmp_path / "mutant.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", str(c_file), "-o",
+                           str(so), "-lm"])
+    monkeypatch.setattr(oracle, "_LIB", oracle.declare(ctypes.CDLL(str(so))))
+    _fails(pin)

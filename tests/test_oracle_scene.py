@@ -1,6 +1,9 @@
 """Pins of the oracle's voxel lookup and raycast against definitions outside it:
 a Python dict of the block list, analytic ray-plane / ray-sphere / ray-box depths,
-and constant or linear colour fields that trilinear interpolation reproduces exactly."""
+constant or linear colour fields that trilinear interpolation reproduces exactly, and the
+invariance of a render under a shift of scene and camera by whole blocks (into negative
+coordinates)."""
+import functools
 import math
 
 import numpy as np
@@ -134,3 +137,29 @@ def test_noise_model_adds_quadratic_term():
     want = np.floor(1000 * lam + 1.5 * lam * lam * 2.0 + 0.5)
     assert np.abs(d1 - want).max() <= 1
     assert (d1.astype(int) - d0.astype(int) >= 11).all()
+
+
+@functools.lru_cache(maxsize=1)
+def _room_blocks():
+    return synth.sample_scene(synth.room_world(1))
+
+
+def test_shift_by_whole_blocks_into_negative_coordinates():
+    """Moving the scene and the camera by -120 blocks in x and y (-4.8 m: every voxel of the room
+    then has negative x and y) leaves the render unchanged up to last-bit rounding of positions:
+    the voxel grid, block lookups and trilinear corners must treat negative coordinates like
+    positive ones (floor, not truncation)."""
+    blocks = _room_blocks()
+    shift = np.array([-120, -120, 0])
+    moved = synth.SceneBlocks(np.ascontiguousarray(blocks.coords + shift.astype(np.int32)), blocks.tsdf,
+                              blocks.rgba, blocks.voxel_size, blocks.mu, blocks.scene_to_world)
+    intr = synth.Intrinsics.for_size(80, 60)
+    pose = synth.look_pose(np.array([1.3, 1.1, 1.4]), math.radians(35.0), math.radians(-10.0))
+    pose_moved = pose.copy()
+    pose_moved[:3, 3] += shift * 8 * blocks.voxel_size
+    d0, c0 = oracle.Scene(blocks).raycast(intr, pose)
+    d1, c1 = oracle.Scene(moved).raycast(intr, pose_moved)
+    assert (d0 > 0).mean() > 0.9 and (moved.coords[:, :2] < 0).all()
+    assert np.mean(d0 != d1) <= 1e-3 and np.abs(d0.astype(int) - d1).max() <= 1
+    dc = np.abs(c0.astype(int) - c1)
+    assert np.mean(dc > 0) <= 1e-3 and dc.max() <= 1
