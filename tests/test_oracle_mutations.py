@@ -64,6 +64,25 @@ def test_energy_with_the_wrong_floor(monkeypatch):
     _fails(pins_ransac.test_pixel_energy_single_isotropic_gaussian_closed_form)
 
 
+def test_distance_without_its_z_term(monkeypatch):
+    def dist(a, b):
+        return np.sqrt((a[..., 0] - b[..., 0]) ** 2 + (a[..., 1] - b[..., 1]) ** 2)   # mistake: no z term
+    monkeypatch.setattr(oracle, "_dist", dist)
+    _fails(pins_ransac.test_first_passing_try_is_the_first_triple_of_distinct_inliers)
+
+
+def test_camera_points_with_swapped_principal_point(monkeypatch):
+    def camera_points(depth_img, intr, pixels):
+        W = intr.width
+        pixels = np.asarray(pixels, dtype=np.int64)
+        u = (pixels % W).astype(np.float64)
+        v = (pixels // W).astype(np.float64)
+        z = depth_img.reshape(-1)[pixels].astype(np.float64) / 1000.0
+        return np.stack([z * (u - intr.cy) / intr.fx, z * (v - intr.cx) / intr.fy, z], axis=-1)   # mistake
+    monkeypatch.setattr(oracle, "camera_points", camera_points)
+    _fails(pins_ransac.test_camera_points_project_back_to_their_pixels)
+
+
 # -- verification ----------------------------------------------------------------------------------
 
 def test_verification_accepting_half_valid(monkeypatch):

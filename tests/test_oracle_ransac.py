@@ -209,3 +209,47 @@ def test_hypotheses_use_first_passing_try():
         wld = forest.modes[0, np.array(pix), 0, :3].astype(np.float64)
         R, t = oracle.kabsch(cam, wld)
         assert np.abs(poses[h][:3, :3] - R).max() < 1e-12
+
+
+def test_first_passing_try_is_the_first_triple_of_distinct_inliers():
+    """Built so the answer is almost always known: inliers carry their exact scene coordinates and
+    outliers are uniform in a 10 m cube, so a try passes the rigidity test when its three pixels are
+    distinct inliers and, but for rare coincidences (an outlier within 5 cm of the right distance
+    to both inliers of its triple), fails otherwise.  The kept try of a hypothesis is then the first
+    all-inlier triple of its Philox stream for all but a few hypotheses."""
+    intr, depth, leaves, forest, P = _exact_setup(0.5, seed=9)
+    K = 32
+    prm = oracle.RansacParams(n_hyps=K, batch=10, seed=11, max_tries=20000)
+    _, ok, tries = oracle.generate_hypotheses(depth, intr, leaves, forest, prm)
+    valid = oracle.valid_pixels(depth)
+    exact = oracle.camera_points(depth, intr, valid) @ P[:3, :3].T + P[:3, 3]
+    inlier = np.abs(forest.modes[0, valid, 0, :3] - exact).max(1) < 1e-3
+    assert 0.4 < inlier.mean() < 0.6
+    key = oracle.seed_key(11)
+    same = 0
+    for h in range(K):
+        j = 0
+        while True:
+            x = oracle.philox(np.array([1, h, j, 0], np.uint32), key)[0]
+            idx = [(int(x[k]) * len(valid)) >> 32 for k in range(3)]
+            if len(set(idx)) == 3 and inlier[idx].all():
+                break
+            j += 1
+        assert ok[h]
+        same += int(tries[h] == j)
+    assert same >= K - 2
+
+
+def test_camera_points_project_back_to_their_pixels():
+    """The pinhole projection u = fx x / z + cx, v = fy y / z + cy of each back-projected point
+    returns its pixel, with z the depth in metres (unequal focal lengths and an off-centre
+    principal point, so swapped axes show)."""
+    intr = synth.Intrinsics(37, 23, 41.5, 57.25, 15.2, 13.7)
+    rng = np.random.default_rng(12)
+    depth = rng.integers(1, 9000, (23, 37)).astype(np.uint16)
+    pix = np.arange(37 * 23)
+    X = oracle.camera_points(depth, intr, pix)
+    u, v = pix % 37, pix // 37
+    assert np.allclose(X[:, 2], depth.reshape(-1) / 1000.0, rtol=0, atol=1e-15)
+    assert np.allclose(intr.fx * X[:, 0] / X[:, 2] + intr.cx, u, rtol=0, atol=1e-9)
+    assert np.allclose(intr.fy * X[:, 1] / X[:, 2] + intr.cy, v, rtol=0, atol=1e-9)
