@@ -92,6 +92,20 @@ def test_uniform_colour_is_kept():
     assert np.all(fb.rgba[~upd] == 0)
 
 
+def test_colour_average_rounds_half_up():
+    """Colours 10 then 11: the running average after the second frame is 10.5, stored as 11."""
+    intr = synth.Intrinsics.for_size(32, 24)
+    fs = oracle.FusionScene(4096, VOX, MU)
+    for c in (10, 11):
+        rgba = np.zeros((24, 32, 4), np.uint8)
+        rgba[..., :3] = c
+        fs.fuse(intr, np.eye(4), plane(intr, 1000), rgba)
+    fb = fs.blocks()
+    both = fb.weight == 2
+    assert both.any()
+    assert np.all(fb.rgba[both][:, :3] == 11)
+
+
 def test_full_scene_reports_it():
     intr = synth.Intrinsics.for_size(64, 48)
     fs = oracle.FusionScene(5, VOX, MU)

@@ -30,6 +30,21 @@ def test_mean_shift_recovers_blob_centres_and_weights():
     assert len(m2) == 2 and np.allclose(m2, modes[:2])
 
 
+def test_mean_shift_bandwidth_decides_when_two_clusters_merge():
+    """A Gaussian kernel of width h over two equal point masses a distance d apart gives a density
+    with one maximum when d <= 2 h and two when d > 2 h (h = 5 cm): at 8.5 cm one mode at the
+    midpoint holds all samples, at 13 cm each cluster is a mode of half the weight."""
+    p = oracle.LeafParams()
+    assert p.bandwidth == 0.05
+    for d, n_modes in ((0.085, 1), (0.13, 2)):
+        pts = np.array([[0.0, 0.0, 1.0]] * 25 + [[d, 0.0, 1.0]] * 25, np.float32)
+        m = oracle.mean_shift_leaf(pts, p)
+        assert len(m) == n_modes, d
+        assert np.allclose(m[:, 10], 1.0 / n_modes)
+        if n_modes == 1:
+            assert np.allclose(m[0, :3], [d / 2, 0.0, 1.0], atol=1e-6)
+
+
 def test_mean_shift_single_point_and_empty():
     p = oracle.LeafParams()
     m = oracle.mean_shift_leaf(np.array([[1.0, 2.0, 3.0]], np.float32), p)

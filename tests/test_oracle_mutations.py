@@ -136,6 +136,28 @@ def test_quaternion_product_with_a_flipped_cross_term(monkeypatch):
     _fails(pins_pg.test_blend_of_opposite_rotations_about_an_offset_axis_is_the_identity)
 
 
+def test_clustering_with_a_tighter_rotation_threshold(monkeypatch):
+    monkeypatch.setattr(PG, "CLUSTER_DEG", 10.0)                 # mistake: 10 degrees for 20
+    _fails(pins_pg.test_clustering_thresholds_and_chains)
+
+
+def test_clustering_with_a_looser_translation_threshold(monkeypatch):
+    monkeypatch.setattr(PG, "CLUSTER_M", 0.2)                    # mistake: 20 cm for 10 cm
+    _fails(pins_pg.test_clustering_thresholds_and_chains)
+
+
+def test_candidate_score_with_the_wrong_penalty(monkeypatch):
+    monkeypatch.setattr(PG, "HOMOG_PENALTY", 1.0)                # mistake: a penalty of 1 for 5
+    _fails(pins_pg.test_phi_terms)
+
+
+def test_halving_that_keeps_the_floor(monkeypatch):
+    import math
+    import types
+    monkeypatch.setattr(oracle, "math", types.SimpleNamespace(**{**vars(math), "ceil": math.floor}))   # mistake
+    _fails(pins_ransac.test_halving_keeps_the_ceiling_of_half)
+
+
 # -- regressor -------------------------------------------------------------------------------------
 
 def test_convolution_instead_of_correlation(monkeypatch):
@@ -219,6 +241,13 @@ C_MUTATIONS = [
      pins_leaves.test_mean_shift_recovers_blob_centres_and_weights),
     ("fusion without the truncation clamp", "const float fn = fminf(1.0f, eta / mu);", "const float fn = eta / mu;",
      pins_fusion.test_plane_closed_form),
+    ("free-space restart 3 cm past the block exit", "lam = lam_prev + 1e-5;", "lam = lam_prev + 3e-2;",
+     pins_scene.test_sphere_depth_within_interpolation_bound),
+    ("mean-shift kernel twice as narrow", "double k = exp(-(dx * dx + dy * dy + dz * dz) / (2.0 * h * h));",
+     "double k = exp(-(dx * dx + dy * dy + dz * dz) / (h * h));",
+     pins_leaves.test_mean_shift_bandwidth_decides_when_two_clusters_merge),
+    ("fusion colour rounded down", "float r = floorf(cc + 0.5f);", "float r = floorf(cc);",
+     pins_fusion.test_colour_average_rounds_half_up),
     ("fusion weight without its cap",
      "f->weight[at] = (uint16_t)(f->weight[at] + 1 < f->max_weight ? f->weight[at] + 1 : f->max_weight);",
      "f->weight[at] = (uint16_t)(f->weight[at] + 1);",

@@ -109,7 +109,8 @@ def test_clustering_thresholds_and_chains():
     assert g.add_sample(0, 1, rigid(rot([0, 0, 1], 38.0))) == 4               # 19 deg from a member
     assert g.add_sample(0, 1, rigid(rot([1, 0, 0], 25.0))) == 1               # 25 deg from all
     assert g.add_sample(0, 1, rigid(t=(0.0, 0.25, 0))) == 1                  # 25 cm from all
-    assert [len(c) for c in g.clusters[(0, 1)]] == [4, 1, 1]
+    assert g.add_sample(0, 1, rigid(t=(0.0, -0.15, 0))) == 1                 # 15 cm from the nearest
+    assert [len(c) for c in g.clusters[(0, 1)]] == [4, 1, 1, 1]
 
 
 def test_reversed_samples_are_inverted_into_the_pair():

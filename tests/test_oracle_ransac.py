@@ -253,3 +253,11 @@ def test_camera_points_project_back_to_their_pixels():
     assert np.allclose(X[:, 2], depth.reshape(-1) / 1000.0, rtol=0, atol=1e-15)
     assert np.allclose(intr.fx * X[:, 0] / X[:, 2] + intr.cx, u, rtol=0, atol=1e-9)
     assert np.allclose(intr.fy * X[:, 1] / X[:, 2] + intr.cy, v, rtol=0, atol=1e-9)
+
+
+def test_halving_keeps_the_ceiling_of_half():
+    """Preemptive halving keeps ceil(K_r / 2) hypotheses per round: 12 -> 6 -> 3 -> 2 -> 1."""
+    intr, depth, leaves, forest, P = _exact_setup(0.3, seed=10)
+    prm = oracle.RansacParams(n_hyps=12, batch=20, seed=6, max_tries=20000)
+    res = oracle.preemptive_ransac(depth, intr, leaves, forest, prm, trace=True)
+    assert [len(r["survivors"]) for r in res["trace"].rounds] == [6, 3, 2, 1]
