@@ -13,6 +13,7 @@ from oracle import regressor as R
 
 import test_oracle_forest_verify as pins_verify
 import test_oracle_posegraph as pins_pg
+import test_oracle_render_global as pins_global
 import test_oracle_ransac as pins_ransac
 import test_oracle_regressor as pins_reg
 
@@ -197,6 +198,41 @@ def test_adam_without_bias_correction(monkeypatch):
             p -= self.lr * m / (np.sqrt(v) + self.eps)    # mistake: raw moments
     monkeypatch.setattr(R.Adam, "step", step)
     _fails(pins_reg.test_adam_first_step_closed_form)
+
+
+def test_backward_data_that_drops_a_stride_offset(monkeypatch):
+    right = R.col2im
+
+    def col2im(cols, shape, stride):
+        g = right(cols, shape, stride)
+        return np.roll(g, 1, axis=1)           # mistake: the input gradient lands one row off
+    monkeypatch.setattr(R, "col2im", col2im)
+    _fails(pins_reg.test_gradients_match_central_differences)
+
+
+def test_global_render_where_the_farther_surface_wins(monkeypatch):
+    right = oracle.render_global
+
+    class Reversed:
+        def __init__(self, sc):
+            self.sc = sc
+
+        def raycast(self, intr, pose, pixels=None):
+            d, c = self.sc.raycast(intr, pose, pixels=pixels)
+            return np.where(d > 0, 65535 - d, 0).astype(np.uint16), c
+
+    def render_global(scenes, global_poses, intr, pose_global, pixels=None):
+        # mistake: the per-pixel depth test keeps the farthest hit
+        d, c, o, ds = right([Reversed(sc) for sc in scenes], global_poses, intr, pose_global, pixels)
+        back = lambda x: np.where(x > 0, 65535 - x.astype(np.int64), 0).astype(np.uint16)   # noqa: E731
+        return back(d), c, o, back(ds)
+    monkeypatch.setattr(oracle, "render_global", render_global)
+    _fails(pins_global.test_depth_test_against_a_brute_force_loop)
+
+
+def test_vee_with_the_quaternion_sign_left_free(monkeypatch):
+    monkeypatch.setattr(PG, "vee", lambda T: np.concatenate([-PG.quat_wxyz(T[:3, :3])[1:], T[:3, 3]]))   # mistake
+    _fails(pins_pg.test_vee_takes_the_quaternion_with_nonnegative_w, 30.0)
 
 
 # -- the C part of the oracle ----------------------------------------------------------------------
