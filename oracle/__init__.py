@@ -15,11 +15,21 @@ with the CUDA library, and the two exchange nothing but seeded inputs from
 
 Parity is pinned (tests/test_oracle_*.py) for: Philox (published known-answer
 vectors), block lookup (a dict), raycast (analytic plane / sphere / box-world
-depths), forest descent (hand-computed trees), verification counts (hand
-counts), Kabsch (known transforms, Horn's quaternion method), the energy
-(closed-form single Gaussian), RANSAC (exact recovery on noise-free data,
-exhaustive ranking) and mean shift (Gaussian blobs).  The pose graph of Sec. 3.3.2
-(``oracle/posegraph.py``) is pinned by closed-form blends, exact recovery and stationarity.
+depths, invariance under a shift by whole blocks into negative coordinates),
+forest descent (hand-computed trees), verification counts (hand counts), camera
+points (pinhole projection back to the pixel), Kabsch (known transforms, Horn's
+quaternion method), the energy (scipy's Gaussian density near the modes, the
+closed-form single Gaussian), hypotheses (the first all-inlier triple on
+constructed data), RANSAC (exact recovery on noise-free data, exhaustive
+ranking, ceil(K/2) halving), reservoirs (Algorithm R's inclusion probabilities),
+mean shift (Gaussian blobs, the two-cluster merge bound), TSDF fusion (closed-form
+plane with its clamp, averages, colour rounding, weight cap), global rendering (a
+brute-force depth test) and the count of data a raycast reads (exact colour voxels
+on a wall).  The pose graph of Sec. 3.3.2 (``oracle/posegraph.py``) is pinned by
+closed-form blends, clustering thresholds, exact recovery and stationarity; the
+regressor (``oracle/regressor.py``) by scipy's correlation, central differences and
+closed forms.  tests/test_oracle_mutations.py plants plausible mistakes in copies of
+this oracle and checks that a pin fails for each.
 """
 from __future__ import annotations
 
