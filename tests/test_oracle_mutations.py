@@ -72,6 +72,12 @@ def test_distance_without_its_z_term(monkeypatch):
     _fails(pins_ransac.test_first_passing_try_is_the_first_triple_of_distinct_inliers)
 
 
+def test_uniform_draw_by_modulo(monkeypatch):
+    monkeypatch.setattr(oracle, "uniform_below",                   # mistake: x mod n for floor(x n / 2^32)
+                        lambda x, n: (np.asarray(x, np.uint64) % np.asarray(n, np.uint64)).astype(np.int64))
+    _fails(pins_ransac.test_hypotheses_use_first_passing_try)
+
+
 def test_camera_points_with_swapped_principal_point(monkeypatch):
     def camera_points(depth_img, intr, pixels):
         W = intr.width
