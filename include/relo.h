@@ -349,8 +349,12 @@ relo_status relo_ransac_relocalise(const relo_forest* forest, const uint16_t* de
  * that may overlap on the GPU -- on different streams, or from different host threads -- race,
  * so serialise them.  Results equal relo_ransac_relocalise's for the same inputs.
  * Errors: as relo_ransac_relocalise, plus RELO_EINVAL when the view needs more scratch than the
- * array holds (for T <= 5 trees: about 16 bytes per pixel plus 230 bytes per hypothesis, e.g.
- * 640 x 480 with 1024 hypotheses fits) or the device ordinal is 64 or more. */
+ * array holds, or the device ordinal is 64 or more.  The scratch a view needs, for a forest of
+ * T <= 5 trees, K hypotheses, B pixels per round and R = ceil(log2 K) rounds: 16 bytes per pixel,
+ * plus 160 + 128 * ceil(R * B / 64) bytes per hypothesis (the re-fit sums take the second term),
+ * plus 68 bytes per drawn pixel (R * B of them), each array rounded up to 256 bytes; e.g.
+ * 640 x 480 with K = 1024, B = 64 needs about 6.4 MB and fits, 1280 x 960 does not.
+ * relo_ransac_workspace_size(width, height, p) is an upper bound for any forest. */
 #define RELO_STATIC_SCRATCH_BYTES (8u << 20)
 relo_status relo_ransac_relocalise_noalloc(const relo_forest* forest, const uint16_t* depth_dev,
                                            const uint16_t* leaves_dev, const relo_intrinsics* intr,
@@ -435,6 +439,18 @@ size_t relo_regressor_relocalise_workspace_size(int32_t width, int32_t height, c
 relo_status relo_regressor_relocalise(relo_regressor* regressor, const uint16_t* depth_dev, const uint8_t* rgba_dev,
                                       const relo_intrinsics* intr, const relo_ransac_params* p, void* workspace_dev,
                                       size_t workspace_bytes, relo_pose_result* result_dev, relo_stream stream);
+
+/* The second half of relo_regressor_relocalise on cell outputs the caller supplies instead of the
+ * network's (stage isolation, for checking the cell-grid RANSAC against a reference):
+ * cells_dev [height/8][width/8][4] float (scene coordinate - origin, log-variance s per cell),
+ * origin[3] (host), depth_dev [height][width] mm (the full-resolution view whose cell-centre
+ * depths form the coarse view).  Workspace: relo_regressor_relocalise_workspace_size.
+ * Errors: RELO_EINVAL (null argument, width or height not a positive multiple of 8, bad params,
+ * misaligned or small workspace). */
+relo_status relo_regressor_relocalise_cells(const float* cells_dev, const double origin[3], const uint16_t* depth_dev,
+                                            const relo_intrinsics* intr, const relo_ransac_params* p,
+                                            void* workspace_dev, size_t workspace_bytes, relo_pose_result* result_dev,
+                                            relo_stream stream);
 
 /* ---------------------------------------------------------------------------------------
  * Depth-difference verification (Sec. 3.3.1): raycast scene a's depth from the proposed pose

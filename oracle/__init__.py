@@ -94,6 +94,8 @@ def declare(lib):
                                         ctypes.c_double, ctypes.c_double, ctypes.c_int, vp]
     lib.orc_fill_modes.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                    ctypes.c_double, ctypes.c_int, vp, vp]
+    lib.orc_fill_modes_range.argtypes = [vp, ctypes.c_long, ctypes.c_long, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, vp, vp]
     lib.orc_fusion_create.restype = vp
     lib.orc_fusion_create.argtypes = [ctypes.c_long, ctypes.c_double, ctypes.c_double, ctypes.c_int]
     lib.orc_fusion_destroy.argtypes = [vp]
@@ -371,13 +373,27 @@ class Reservoirs:
         _lib().orc_reservoirs_get(self._h, samples.ctypes.data, count.ctypes.data)
         return samples, count
 
-    def modes(self) -> Forest:
+    def modes(self, threads: int = 1) -> Forest:
+        """Mean-shift modes of every leaf.  With threads > 1 the leaves are split into ranges that
+        threads fill concurrently (the C call releases the GIL; every leaf is computed exactly as
+        in the one-thread call, only the order in which leaves are visited differs)."""
         L = 1 << self.D
         modes = np.zeros((self.T, L, self.p.max_modes, 12), dtype=np.float32)
         n_modes = np.zeros((self.T, L), dtype=np.uint8)
         p = self.p
-        _lib().orc_fill_modes(self._h, p.bandwidth, p.tol, p.max_iter, p.merge_dist, p.cov_floor, p.max_modes,
-                              modes.ctypes.data, n_modes.ctypes.data)
+        total = self.T * L
+
+        def fill(lo, hi):
+            _lib().orc_fill_modes_range(self._h, lo, hi, p.bandwidth, p.tol, p.max_iter, p.merge_dist, p.cov_floor,
+                                        p.max_modes, modes.ctypes.data, n_modes.ctypes.data)
+
+        if threads <= 1:
+            fill(0, total)
+        else:
+            from concurrent.futures import ThreadPoolExecutor
+            step = max(1, total // (64 * threads))
+            with ThreadPoolExecutor(threads) as ex:
+                list(ex.map(lambda lo: fill(lo, min(total, lo + step)), range(0, total, step)))
         return Forest(self.nodes, modes, n_modes)
 
 
@@ -390,12 +406,13 @@ def mean_shift_leaf(samples, p: LeafParams) -> np.ndarray:
     return out[:k]
 
 
-def train_forest(nodes, frames, p: LeafParams) -> Forest:
-    """Fill the leaves of a forest from training frames [(intr, pose, depth, rgba), ...] in order."""
+def train_forest(nodes, frames, p: LeafParams, threads: int = 1) -> Forest:
+    """Fill the leaves of a forest from training frames [(intr, pose, depth, rgba), ...] in order
+    (``threads``: how many threads compute the leaves' modes)."""
     r = Reservoirs(nodes, p)
     for intr, pose, depth, rgba in frames:
         r.add_frame(intr, pose, depth, rgba)
-    return r.modes()
+    return r.modes(threads)
 
 
 # ------------------------------------------------------------------------------------------------

@@ -580,14 +580,22 @@ int orc_mean_shift_leaf(const float* x, int n, double h, double tol, int max_ite
   return kept;
 }
 
-/* All leaves of a reservoir set: modes [T][L][max_modes][12], n_modes [T][L]. */
-void orc_fill_modes(const orc_reservoirs* r, double h, double tol, int max_iter, double merge_dist, double cov_floor,
-                    int max_modes, float* modes, uint8_t* n_modes) {
-  long total = (long)r->T * r->n_leaves;
-  for (long id = 0; id < total; ++id) {
+/* Leaves [lo, hi) (flat index tree * L + leaf) of a reservoir set: modes [T][L][max_modes][12],
+ * n_modes [T][L].  Each leaf is independent of the others, so callers may fill disjoint ranges
+ * from several threads. */
+void orc_fill_modes_range(const orc_reservoirs* r, long lo, long hi, double h, double tol, int max_iter,
+                          double merge_dist, double cov_floor, int max_modes, float* modes, uint8_t* n_modes) {
+  for (long id = lo; id < hi; ++id) {
     n_modes[id] = (uint8_t)orc_mean_shift_leaf(r->samples + id * r->capacity * 3, r->count[id], h, tol, max_iter,
                                                merge_dist, cov_floor, max_modes, modes + id * max_modes * 12);
   }
+}
+
+/* All leaves of a reservoir set. */
+void orc_fill_modes(const orc_reservoirs* r, double h, double tol, int max_iter, double merge_dist, double cov_floor,
+                    int max_modes, float* modes, uint8_t* n_modes) {
+  orc_fill_modes_range(r, 0, (long)r->T * r->n_leaves, h, tol, max_iter, merge_dist, cov_floor, max_modes, modes,
+                       n_modes);
 }
 
 /* ------------------------------------------------------------------------------------------ */

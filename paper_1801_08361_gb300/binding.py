@@ -145,6 +145,8 @@ _SIGS = {
     "relo_regressor_relocalise_workspace_size": (ctypes.c_size_t, [c_i32, c_i32, ctypes.POINTER(RansacParams)]),
     "relo_regressor_relocalise": (c_i32, [c_vp, c_vp, c_vp, ctypes.POINTER(Intrinsics), ctypes.POINTER(RansacParams),
                                           c_vp, ctypes.c_size_t, c_vp, c_vp]),
+    "relo_regressor_relocalise_cells": (c_i32, [c_vp, ctypes.POINTER(ctypes.c_double), c_vp, ctypes.POINTER(Intrinsics),
+                                                ctypes.POINTER(RansacParams), c_vp, ctypes.c_size_t, c_vp, c_vp]),
     "relo_batch_enable_timing": (c_i32, [c_vp, c_i32]),
     "relo_batch_stage_ms": (c_i32, [c_vp, ctypes.POINTER(ctypes.c_float), c_i32]),
     "relo_batch_stage_name": (ctypes.c_char_p, [c_i32]),
@@ -715,6 +717,16 @@ def regressor_relocalise(reg, depth_dev, rgba_dev, intr, params, workspace_dev, 
     _check(lib().relo_regressor_relocalise(reg.handle, _ptr(depth_dev), _ptr(rgba_dev), ctypes.byref(ci),
                                            ctypes.byref(params), _ptr(workspace_dev), workspace_dev.numel(),
                                            _ptr(result_dev), _stream(stream)))
+
+
+def regressor_relocalise_cells(cells_dev, origin, depth_dev, intr, params, workspace_dev, result_dev, stream=None):
+    """The cell-grid RANSAC of the learned path on given cell outputs cells_dev [H/8][W/8][4]
+    (scene coordinate - origin, log-variance)."""
+    ci = intrinsics(intr)
+    o = (ctypes.c_double * 3)(*[float(x) for x in origin])
+    _check(lib().relo_regressor_relocalise_cells(_ptr(cells_dev), o, _ptr(depth_dev), ctypes.byref(ci),
+                                                 ctypes.byref(params), _ptr(workspace_dev), workspace_dev.numel(),
+                                                 _ptr(result_dev), _stream(stream)))
 
 
 # ------------------------------------------------------------------------------------------------

@@ -148,7 +148,7 @@ void carve_ransac(Carver& c, RansacJob& j, int W, int H, int K, int B, int n_rou
   const int R = std::max(n_rounds, 1);
   j.hs = 1 + (T + 1) / 2;
   j.refit_parts = (R * B + kRefinePixels - 1) / kRefinePixels;
-  j.refit = c.take<float>((size_t)K * j.refit_parts * 16);
+  j.refit = c.take<double>((size_t)K * j.refit_parts * 16);
   j.refit_ref = c.take<float>((size_t)K * 8);
   j.pix = c.take<int4>((size_t)R * B * j.hs);
   j.chunk_count = c.take<int32_t>((n_pix + kCompactChunk - 1) / kCompactChunk);
@@ -1669,6 +1669,10 @@ void learned_layout(char* base, int W, int H, const relo_ransac_params& p, Learn
   l.bytes = l.ransac_off + l.ransac.bytes;
 }
 
+relo_status learned_ransac(const LearnedLayout& l, const float* cells, int ostride, const double origin[3],
+                           const uint16_t* depth, const relo_intrinsics* intr, const relo_ransac_params* p, void* ws,
+                           size_t ws_bytes, relo_pose_result* result, cudaStream_t s);
+
 relo_intrinsics coarse_intrinsics(const relo_intrinsics& in) {
   relo_intrinsics c = in;
   c.width = in.width / 8;
@@ -1706,8 +1710,38 @@ relo_status relo_regressor_relocalise(relo_regressor* r, const uint16_t* depth, 
   cudaStream_t s = (cudaStream_t)stream;
   st = reg_forward(r, l.reg, depth, rgba, 1, intr->width, intr->height, s);
   if (st) return st;
+  return learned_ransac(l, l.reg.head, 8, r->origin, depth, intr, p, ws, ws_bytes, result, s);
+}
+
+relo_status relo_regressor_relocalise_cells(const float* cells, const double origin[3], const uint16_t* depth,
+                                            const relo_intrinsics* intr, const relo_ransac_params* p, void* ws,
+                                            size_t ws_bytes, relo_pose_result* result, relo_stream stream) {
+  if (!cells || !origin || !depth || !intr || !p || !ws || !result) return fail(RELO_EINVAL, "null argument");
+  relo_status st = check_intr(intr);
+  if (st) return st;
+  if (intr->width < 8 || intr->height < 8 || intr->width % 8 || intr->height % 8)
+    return fail(RELO_EINVAL, "width and height must be positive multiples of 8");
+  st = check_params(p);
+  if (st) return st;
+  if (((uintptr_t)ws & 255) != 0) return fail(RELO_EINVAL, "workspace must be 256-byte aligned");
+  LearnedLayout l;
+  learned_layout(nullptr, intr->width, intr->height, *p, l);
+  if (l.bytes > ws_bytes) return fail(RELO_EINVAL, "workspace too small");
+  learned_layout((char*)ws, intr->width, intr->height, *p, l);
+  return learned_ransac(l, cells, 4, origin, depth, intr, p, ws, ws_bytes, result, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+namespace {
+// The learned path's RANSAC from cell outputs (scene coordinate - origin, log-variance; ostride
+// floats per cell): the cell forest, the coarse view, then the RANSAC of one view.
+relo_status learned_ransac(const LearnedLayout& l, const float* cells, int ostride, const double origin[3],
+                           const uint16_t* depth, const relo_intrinsics* intr, const relo_ransac_params* p, void* ws,
+                           size_t ws_bytes, relo_pose_result* result, cudaStream_t s) {
   CellForestArgs ca{};
-  ca.out = l.reg.head;
+  ca.out = cells;
+  ca.ostride = ostride;
   ca.depth = depth;
   ca.n = 1;
   ca.W = intr->width;
@@ -1715,9 +1749,9 @@ relo_status relo_regressor_relocalise(relo_regressor* r, const uint16_t* depth, 
   ca.Wc = intr->width / 8;
   ca.Hc = intr->height / 8;
   ca.L = l.L;
-  ca.ox = (float)r->origin[0];
-  ca.oy = (float)r->origin[1];
-  ca.oz = (float)r->origin[2];
+  ca.ox = (float)origin[0];
+  ca.oy = (float)origin[1];
+  ca.oz = (float)origin[2];
   ca.modes = l.modes;
   ca.n_modes = l.n_modes;
   ca.top = l.top;
@@ -1733,12 +1767,12 @@ relo_status relo_regressor_relocalise(relo_regressor* r, const uint16_t* depth, 
   fv.M = 1;
   const relo_intrinsics ci = coarse_intrinsics(*intr);
   Single sr;
-  st = single_setup_view(fv, l.depth_lr, l.leaves, &ci, p, (char*)ws + l.ransac_off, ws_bytes - l.ransac_off, sr);
+  const relo_status st =
+      single_setup_view(fv, l.depth_lr, l.leaves, &ci, p, (char*)ws + l.ransac_off, ws_bytes - l.ransac_off, sr);
   if (st) return st;
   return single_run(sr, p, result, s);
 }
-
-}  // extern "C"
+}  // namespace
 
 // =============================================================================================
 // Batches of whole attempts (Fig. 3 end to end).  Pass L (learned attempts): regressor forward,

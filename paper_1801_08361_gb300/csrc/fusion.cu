@@ -220,13 +220,8 @@ __global__ void fuse_init_kernel(float* tsdf, int64_t n) {
 }
 
 int grid_for(int64_t work, int threads) {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
-                                                   cudaSuccess)
-      sms = 152;
-  }
+  int sms = 0;
+  if (device_sms(&sms) != cudaSuccess) sms = 152;
   const int64_t want = (work + threads - 1) / threads;
   return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 8));
 }

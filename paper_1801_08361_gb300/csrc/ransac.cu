@@ -457,21 +457,19 @@ __global__ void __launch_bounds__(128) fit_kernel(const RansacJob* __restrict__ 
 cudaError_t launch_hypotheses(const RansacJob* jobs, int n_jobs, int total_hyps, int32_t* counter, cudaStream_t s,
                               const Schedule& sched) {
   if (total_hyps <= 0) return cudaSuccess;
-  static int sms = 0, per_sm = 0;  // SMs and resident search CTAs per SM on this GPU (first call)
-  if (sms == 0) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_kernel, kSearchWarps * 32, 0);
-    if (e != cudaSuccess) {
-      sms = 0;
-      return e;
-    }
-    per_sm = std::max(1, per_sm);
-  }
+  static PerDevice resident;  // resident search CTAs per SM on each device
+  int sms = 0, per_sm = 0;
+  cudaError_t e = device_sms(&sms);
+  if (e == cudaSuccess)
+    e = per_device(resident, &per_sm, [](int, int* v) {
+      cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(v, search_kernel, kSearchWarps * 32, 0);
+      *v = std::max(1, *v);
+      return r;
+    });
+  if (e != cudaSuccess) return e;
   if (sched.search_ctas_per_sm < 0) return cudaErrorInvalidValue;
   const int ctas = sched.search_ctas_per_sm == 0 ? per_sm : std::min(per_sm, sched.search_ctas_per_sm);
-  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
+  e = cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
   if (e != cudaSuccess) return e;
   const int grid = std::min(sms * ctas, (total_hyps + kSearchWarps - 1) / kSearchWarps);
   search_kernel<<<grid, kSearchWarps * 32, 0, s>>>(jobs, n_jobs, total_hyps, counter);
@@ -699,6 +697,15 @@ __global__ void __launch_bounds__(1024) select_kernel(const RansacJob* __restric
 // pixels, jobs).  Sums are taken about a reference correspondence (the first drawn pixel and its
 // predicted scene point) so one FP32 pass gives well-conditioned centroids and cross-covariance:
 //   refit[h][part] = {n, sum dc (3), sum dw (3), sum dc dw^T (9)},  refit_ref[h] = {c_ref, w_ref}.
+// s + e accumulates x: the rounding error of each addition is carried in e (Neumaier 1974), with
+// explicitly rounded operations so that no contraction changes the error terms.
+__device__ __forceinline__ void comp_add(float& s, float& e, float x) {
+  const float t = __fadd_rn(s, x);
+  const float err = fabsf(s) >= fabsf(x) ? __fadd_rn(__fsub_rn(s, t), x) : __fadd_rn(__fsub_rn(x, t), s);
+  e = __fadd_rn(e, err);
+  s = t;
+}
+
 __global__ void __launch_bounds__(kRoundWarps * 32) refine_kernel(const RansacJob* __restrict__ jobs,
                                                                   const int32_t* __restrict__ surv_prefix, int r) {
   const int jid = blockIdx.z, part = blockIdx.y;
@@ -716,9 +723,14 @@ __global__ void __launch_bounds__(kRoundWarps * 32) refine_kernel(const RansacJo
   const float r2 = (float)(job.inlier_dist * job.inlier_dist);
   const float3 cref = record_point(job.pix);
   const float3 wref = apply(P, cref);
-  float acc[16];
+  // Each sum is carried as hi + lo in FP32, compensated: products are split exactly into their
+  // rounded value and its error (fmaf), and every addition's rounding error is kept (Neumaier's
+  // variant of Kahan summation), so the sums hold about twice FP32's precision.  The sums are taken
+  // relative to the first drawn pixel; with plain FP32 sums their cancellation against the small
+  // spread of a few inliers moved ill-conditioned re-fits by ~1e-4 rad.
+  float acc[16], lo[16];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+  for (int q = 0; q < 16; ++q) acc[q] = lo[q] = 0.f;
   const int p1 = min(p0 + kRefinePixels, n_drawn);
   __shared__ ModeSlot slots[kRoundWarps];
   for (int i = p0 + warp; i < p1; i += kRoundWarps) {
@@ -737,26 +749,44 @@ __global__ void __launch_bounds__(kRoundWarps * 32) refine_kernel(const RansacJo
       acc[0] += 1.f;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        acc[1 + k] += u[k];
-        acc[4 + k] += w[k];
+        comp_add(acc[1 + k], lo[1 + k], u[k]);
+        comp_add(acc[4 + k], lo[4 + k], w[k]);
       }
 #pragma unroll
       for (int p = 0; p < 3; ++p)
 #pragma unroll
-        for (int q = 0; q < 3; ++q) acc[7 + 3 * p + q] = fmaf(u[p], w[q], acc[7 + 3 * p + q]);
+        for (int q = 0; q < 3; ++q) {
+          const float pr = __fmul_rn(u[p], w[q]);
+          comp_add(acc[7 + 3 * p + q], lo[7 + 3 * p + q], pr);
+          lo[7 + 3 * p + q] = __fadd_rn(lo[7 + 3 * p + q], __fmaf_rn(u[p], w[q], -pr));
+        }
     }
   }
+  // warps w then write sums q = w, w + kRoundWarps: the kRoundWarps partials added in warp order in
+  // FP64, first their high parts, then their low parts (one shared buffer, two passes)
   __shared__ float red[kRoundWarps][16][32];
+  double tot[(16 + kRoundWarps - 1) / kRoundWarps];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) red[warp][q][lane] = acc[q];
-  __syncthreads();
+  for (int i = 0; i < (16 + kRoundWarps - 1) / kRoundWarps; ++i) tot[i] = 0.0;
+#pragma unroll
+  for (int pass = 0; pass < 2; ++pass) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) red[warp][q][lane] = pass ? lo[q] : acc[q];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < (16 + kRoundWarps - 1) / kRoundWarps; ++i) {
+      const int q = warp + i * kRoundWarps;
+      if (q < 16)
+#pragma unroll
+        for (int w = 0; w < kRoundWarps; ++w) tot[i] += (double)red[w][q][lane];
+    }
+    __syncthreads();
+  }
   if (!valid) return;
-  // warps w then write one sum each: sum q over the kRoundWarps partials, in warp order
-  for (int q = warp; q < 16; q += kRoundWarps) {
-    float v = 0.f;
 #pragma unroll
-    for (int w = 0; w < kRoundWarps; ++w) v += red[w][q][lane];
-    job.refit[((size_t)h * job.refit_parts + part) * 16 + q] = v;
+  for (int i = 0; i < (16 + kRoundWarps - 1) / kRoundWarps; ++i) {
+    const int q = warp + i * kRoundWarps;
+    if (q < 16) job.refit[((size_t)h * job.refit_parts + part) * 16 + q] = tot[i];
   }
   if (part == 0 && warp == 0) {
     float* ref = job.refit_ref + (size_t)h * 8;
@@ -787,8 +817,8 @@ __global__ void __launch_bounds__(32) refit_kernel(const RansacJob* __restrict__
   double f[16];
   for (int q = 0; q < 16; ++q) f[q] = 0.0;
   for (int p = 0; p < parts; ++p) {
-    const float* src = job.refit + ((size_t)h * job.refit_parts + p) * 16;
-    for (int q = 0; q < 16; ++q) f[q] += (double)src[q];
+    const double* src = job.refit + ((size_t)h * job.refit_parts + p) * 16;
+    for (int q = 0; q < 16; ++q) f[q] += src[q];
   }
   job.inliers[h] = (int)f[0];
   const double n = f[0];
@@ -818,13 +848,9 @@ cudaError_t launch_round(const RansacJob* jobs, int n_jobs, int round, const int
                                                                                         round);
   const int parts = ((round + 1) * B + kRefinePixels - 1) / kRefinePixels;
   refine_kernel<<<dim3((max_surv + 31) / 32, parts, n_jobs), kRoundWarps * 32, 0, s>>>(jobs, surv_prefix_dev, round);
-  static int n_sms = 0;
-  if (n_sms == 0) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-  }
+  int n_sms = 0;
+  const cudaError_t e = device_sms(&n_sms);
+  if (e != cudaSuccess) return e;
   const int per = sched.refit_per > 0 ? sched.refit_per
                                      : std::max(1, std::min(32, (total_surv + 2 * n_sms - 1) / (2 * n_sms)));
   refit_kernel<<<(unsigned)((total_surv + per - 1) / per), 32, 0, s>>>(jobs, n_jobs, surv_prefix_dev, total_surv,

@@ -189,14 +189,15 @@ template <int CIN, int NT>
 cudaError_t launch_conv_t(const ConvArgs& a, int n_sms, cudaStream_t s) {
   constexpr int N = NT * 8, RS = CIN + 8;
   const size_t smem = (size_t)(9 * N + kConvTile) * RS * sizeof(bf16);
-  static int per_sm = 0;  // resident CTAs per SM (first call)
-  if (per_sm == 0) {
-    cudaError_t e = cudaFuncSetAttribute(conv_kernel<CIN, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_kernel<CIN, NT>, kConvThreads, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-  }
+  static PerDevice resident;  // resident CTAs per SM on each device
+  int per_sm = 0;
+  const cudaError_t e = per_device(resident, &per_sm, [smem](int, int* v) {
+    cudaError_t r = cudaFuncSetAttribute(conv_kernel<CIN, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (r == cudaSuccess) r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(v, conv_kernel<CIN, NT>, kConvThreads, smem);
+    if (*v < 1) *v = 1;
+    return r;
+  });
+  if (e != cudaSuccess) return e;
   const long total = (long)a.B * a.Ho * a.Wo;
   const long tiles = (total + kConvTile - 1) / kConvTile;
   const long slots = (long)n_sms * per_sm;
@@ -597,7 +598,7 @@ __global__ void cell_forest_kernel(CellForestArgs a) {
   }
   const int cx = i % a.Wc, cy = i / a.Wc;
   const int d = a.depth[(size_t)img * a.W * a.H + (size_t)(cy * 8 + 4) * a.W + cx * 8 + 4];
-  const float* o = a.out + ((size_t)img * n + i) * 8;
+  const float* o = a.out + ((size_t)img * n + i) * a.ostride;
   const float s = o[3], inv = expf(-s);
   const float mx = o[0] + a.ox, my = o[1] + a.oy, mz = o[2] + a.oz;
   m[0] = mx;

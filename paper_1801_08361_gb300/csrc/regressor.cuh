@@ -46,7 +46,8 @@ struct CellArgs {
 
 // Cell forest (see cell_forest_kernel)
 struct CellForestArgs {
-  const float* out;        // [n][Hc][Wc][8] head output
+  const float* out;        // [n][Hc][Wc][ostride]: head output (ostride 8) or given cells (4)
+  int ostride = 8;
   const uint16_t* depth;   // [n][H][W] full-resolution depth
   int n, W, H, Wc, Hc, L;  // L = leaves per tree (power of two >= Wc Hc)
   float ox, oy, oz;

@@ -6,9 +6,50 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "../../include/relo.h"
 
 namespace relo {
+
+// ---------------------------------------------------------------------------------------------
+// A launch parameter that depends only on the device (its SM count, a kernel's resident CTAs per
+// SM): computed once per device ordinal, with that device current, and shared by every host
+// thread.  The lock makes a value and its "ready" mark appear together, so no thread launches
+// with a half-published pair.
+// ---------------------------------------------------------------------------------------------
+struct PerDevice {
+  static constexpr int kMaxDevices = 64;
+  std::mutex m;
+  int value[kMaxDevices] = {};
+  bool ready[kMaxDevices] = {};
+};
+
+template <class F>
+cudaError_t per_device(PerDevice& c, int* out, F&& compute) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= PerDevice::kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(c.m);
+  if (!c.ready[dev]) {
+    int v = 0;
+    e = compute(dev, &v);
+    if (e != cudaSuccess) return e;
+    c.value[dev] = v;
+    c.ready[dev] = true;
+  }
+  *out = c.value[dev];
+  return cudaSuccess;
+}
+
+// SMs of the current device.
+inline cudaError_t device_sms(int* out) {
+  static PerDevice cache;
+  return per_device(cache, out, [](int dev, int* v) {
+    return cudaDeviceGetAttribute(v, cudaDevAttrMultiProcessorCount, dev);
+  });
+}
 
 constexpr int kBlockSide = 8;
 constexpr int kVoxelsPerBlock = 512;
@@ -315,7 +356,7 @@ struct RansacJob {
   int32_t* alive_b;            // [K]
   int32_t* drawn;              // [n_rounds * B] positions in the valid-pixel table
   int32_t* inliers;            // [K]
-  float* refit;                // [K][refit_parts][16] per-survivor inlier sums, one block per part of
+  double* refit;               // [K][refit_parts][16] per-survivor inlier sums, one block per part of
                                // kRefinePixels drawn pixels (summed in order by the FP64 re-fit)
   float* refit_ref;            // [K][8] reference correspondence of those sums: c_ref (3), w_ref (3)
   int4* pix;                   // [n_rounds * B][hs] drawn pixels: camera point (FP32 bits), then

@@ -329,6 +329,38 @@ def world_to_scene_pose(cam_to_world: np.ndarray, scene_to_world: np.ndarray) ->
     return np.linalg.inv(scene_to_world) @ cam_to_world
 
 
+def fragment_trajectories(world: World, frags: list, n_per_room: int = 12) -> None:
+    """Each fragment's agent trajectory (camera-to-world poses, n_per_room views in each of its
+    rooms, seed 40 + k), stored as frags[k]["train_w"]."""
+    for k, f in enumerate(frags):
+        f["train_w"] = training_poses(world, n_per_room, seed=40 + k, rooms=f["rooms"])
+
+
+def fragment_pairs(world: World, frags: list, sizes: list, seed: int = 17) -> list:
+    """All ordered pairs (a, b), a != b, of fragments with trajectories: the query of (a, b) is a
+    perturbed view of b's trajectory at a size drawn from ``sizes``, with its depth-noise seed, a
+    hypothesis count from 256-1024 and a RANSAC seed.  Each pair: a, b, width, height, noise_seed,
+    n_hyps, seed, pose_b (in b's frame), pose_a (the same camera in a's frame), covered (the
+    query's room lies in fragment a)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for a in range(len(frags)):
+        for b in range(len(frags)):
+            if a == b:
+                continue
+            W, H = sizes[rng.integers(len(sizes))]
+            Pw = query_poses(world, frags[b]["train_w"], 1, seed=int(rng.integers(1 << 30)))[0]
+            Sa, Sb = frags[a]["scene_to_world"], frags[b]["scene_to_world"]
+            noise_seed = int(rng.integers(1 << 30))
+            n_hyps = int(rng.integers(256, 1025))
+            rseed = int(rng.integers(1 << 40))
+            room = int(np.argmin([np.linalg.norm(Pw[:2, 3] - c) for c in world.room_centres]))
+            out.append(dict(a=a, b=b, width=int(W), height=int(H), noise_seed=noise_seed, n_hyps=n_hyps, seed=rseed,
+                            pose_b=world_to_scene_pose(Pw, Sb), pose_a=world_to_scene_pose(Pw, Sa),
+                            covered=room in frags[a]["rooms"]))
+    return out
+
+
 def random_rigid(rng, max_angle=math.pi, max_t=2.0) -> np.ndarray:
     """A random rigid transform: yaw about z up to max_angle and a translation up to max_t per axis."""
     a = rng.uniform(-max_angle, max_angle)

@@ -19,20 +19,20 @@ KEYS = {"bound", "achieved", "peak", "unit", "frac", "traffic"}
 
 @pytest.mark.parametrize("stage", ["query_raycast", "forest_eval", "forest_hypotheses", "forest_verify"])
 def test_roofline_entries_carry_the_promised_keys(stage):
-    r = bench.roofline(stage, 12.5, 256, 1.3e9, {"sm_max_mhz": 2070.0})
+    r = bench.roofline(stage, 12.5, 256, 1.3e9, {"sm_max_mhz": 2070.0}, 152)
     assert KEYS <= set(r) and r["bound"] in ("hbm", "alu") and r["limiter"]
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     json.dumps(r)                                        # serialisable as it stands
 
 
 def test_alu_view_counts_tries_against_the_derived_peak():
-    r = bench.roofline("forest_hypotheses", 20.0, 256, 2.0e9, {"sm_max_mhz": 2000.0})
+    r = bench.roofline("forest_hypotheses", 20.0, 256, 2.0e9, {"sm_max_mhz": 2000.0}, 148)
     assert r["unit"] == "Gtries/s" and r["achieved"] == pytest.approx(2.0e9 / 0.02 / 1e9)
-    assert r["peak"] == pytest.approx(bench.IMAD_PER_CLK_SM * bench.N_SMS * 2000e6 / bench.IMAD_PER_TRY / 1e9)
+    assert r["peak"] == pytest.approx(bench.IMAD_PER_CLK_SM * 148 * 2000e6 / bench.IMAD_PER_TRY / 1e9)
 
 
 def test_hbm_view_counts_algorithmic_bytes_per_pixel():
-    r = bench.roofline("query_raycast", 10.0, 100, 0, None)
+    r = bench.roofline("query_raycast", 10.0, 100, 0, None, 152)
     want = bench.ALG_BYTES_PER_PIXEL["query_raycast"] * bench.W * bench.H * 100 / 0.01 / 1e9
     assert r["unit"] == "GB/s" and r["achieved"] == pytest.approx(want)
     assert r["traffic"] == pytest.approx(bench.PROFILED_TRAFFIC_BYTES_PER_ATTEMPT["query_raycast"] * 100)

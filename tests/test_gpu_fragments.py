@@ -7,7 +7,6 @@ query depth and colour on sampled pixels match the oracle's raycast and the fore
 whole query image match the oracle's forest bit for bit; verified poses agree with the known
 relative transforms of the fragments (Sec. 3.3.1: aT_b)."""
 import math
-from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 import pytest
@@ -15,54 +14,18 @@ import torch
 
 import oracle
 from paper_1801_08361_gb300 import binding as B
-from paper_1801_08361_gb300 import synth
+from paper_1801_08361_gb300 import fragments as F
 
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda:0")
-SIZES = [(320, 240), (480, 360), (640, 480)]
-N_FRAG = 8
-T, DEPTH = 5, 13
+T = F.TREES
 ORACLE_FRAG = 7          # the fragment whose host blocks are kept for the oracle checks
 
 
 @pytest.fixture(scope="module")
 def fragments():
-    world = synth.house_world(2)
-    frags = synth.house_fragments(world, N_FRAG, seed=3)
-
-    def sample(f):
-        return synth.sample_scene(world, scene_to_world=f["scene_to_world"], crop=f["crop"])
-
-    scenes, forests, oracle_blocks = [], [], None
-    # each training frame is rendered at all three query sizes: a feature's pixel offsets are
-    # divided by depth but not scaled by the focal length, so a forest trained at one image size
-    # sees other responses at another
-    views = []
-    for W, H in SIZES:
-        views.append((synth.Intrinsics.for_size(W, H, 12.0), torch.zeros((H, W), dtype=torch.int16, device=DEV),
-                      torch.zeros((H, W, 4), dtype=torch.uint8, device=DEV)))
-    with ThreadPoolExecutor(4) as ex:           # the sampler is C code called without the GIL
-        for k, blocks in enumerate(ex.map(sample, frags)):
-            sc = B.Scene(blocks, 19)
-            if k == ORACLE_FRAG:
-                oracle_blocks = blocks
-            del blocks
-            f = frags[k]
-            S = f["scene_to_world"]
-            f["train_w"] = synth.training_poses(world, 12, seed=40 + k, rooms=f["rooms"])
-            f["nodes"] = synth.random_forest_nodes(T, DEPTH, seed=60 + k, depth_tau=100, colour_tau=32)
-            fo = B.Forest(f["nodes"], max_modes=10)
-            B.forest_train_begin(fo, B.train_params(capacity=512, stride=2, seed=k))
-            for i, Pw in enumerate(f["train_w"]):
-                P = synth.world_to_scene_pose(Pw, S)
-                for j, (intr, depth, rgba) in enumerate(views):
-                    nz = torch.from_numpy(synth.depth_noise(intr.height, intr.width, 7000 + 100 * k + 3 * i + j)).to(DEV)
-                    B.raycast_view(sc, intr, P, depth, rgba, noise_dev=nz)
-                    B.forest_train_frame(fo, intr, P, depth, rgba)
-            B.forest_train_finish(fo)
-            scenes.append(sc)
-            forests.append(fo)
-    return world, frags, scenes, forests, oracle_blocks
+    world, frags, scenes, forests, kept = F.build(DEV, keep_blocks=(ORACLE_FRAG,))
+    return world, frags, scenes, forests, kept[ORACLE_FRAG]
 
 
 @pytest.fixture(scope="module")
@@ -70,26 +33,10 @@ def pairs(fragments):
     """The 56 ordered pairs: query of b (a perturbed view of b's trajectory), relocalised with a's
     forest and verified against a."""
     world, frags, scenes, forests, _ = fragments
-    rng = np.random.default_rng(17)
-    items, meta = [], []
-    for a in range(N_FRAG):
-        for b in range(N_FRAG):
-            if a == b:
-                continue
-            W, H = SIZES[rng.integers(len(SIZES))]
-            intr = synth.Intrinsics.for_size(W, H, 12.0)
-            Pw = synth.query_poses(world, frags[b]["train_w"], 1, seed=int(rng.integers(1 << 30)))[0]
-            Sa, Sb = frags[a]["scene_to_world"], frags[b]["scene_to_world"]
-            noise = torch.from_numpy(synth.depth_noise(H, W, int(rng.integers(1 << 30)))).to(DEV)
-            items.append(dict(scene_b=scenes[b], forest_a=forests[a], scene_a=scenes[a], intr=intr,
-                              pose_b=synth.world_to_scene_pose(Pw, Sb), noise=noise,
-                              n_hyps=int(rng.integers(256, 1025)), seed=int(rng.integers(1 << 40))))
-            room = int(np.argmin([np.linalg.norm(Pw[:2, 3] - c) for c in world.room_centres]))
-            meta.append(dict(a=a, b=b, pose_a=synth.world_to_scene_pose(Pw, Sa), covered=room in frags[a]["rooms"]))
-    return items, meta
+    return F.pairs(world, frags, scenes, forests, DEV)
 
 
-PRM = dict(batch=64, max_tries=10000)
+PRM = dict(batch=F.BATCH_PIXELS, max_tries=F.MAX_TRIES)
 
 
 def _batch(items):

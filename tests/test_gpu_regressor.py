@@ -1,7 +1,8 @@
 """GPU parity of the learned regressor (BF16 tensor-core convolutions, FP32 accumulation)
 against the FP64 oracle: forward output, loss and per-layer gradients on the same operands
 (relative L2 <= 1e-2 forward, gradient cosine >= 0.999 per layer), a short training run, and the
-learned RANSAC against the oracle's RANSAC on the same cell grid."""
+learned RANSAC against the oracle's RANSAC on the same (constructed) cells, and a fit of fixed views
+to centimetres."""
 
 import numpy as np
 import pytest
@@ -185,34 +186,96 @@ def test_training_resumes_from_a_checkpoint(views):
         B.regressor_set_state(b, dict(state, step=-1))
 
 
-def test_learned_ransac_matches_oracle_on_the_cell_grid(room, oracle_room):
-    """The learned path's RANSAC (relo_regressor_relocalise) against the oracle's RANSAC on the
-    cell forest built from the same network output."""
+def _near_tie_in_trace(tr):
+    """True when some round's cut between kept and dropped hypotheses is within the energy
+    tolerance (FP32 may then keep either side)."""
+    for rd in tr.rounds:
+        E, alive = rd["energy"], rd["alive_before"]
+        srt = sorted(alive.tolist(), key=lambda h: (E[h], h))
+        keep = (len(srt) + 1) // 2
+        if keep < len(srt):
+            a, b = E[srt[keep - 1]], E[srt[keep]]
+            if np.isfinite(a) and np.isfinite(b) and abs(b - a) <= 1e-5 * max(abs(a), abs(b)) + 1e-6:
+                return True
+    return False
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_learned_ransac_matches_oracle_on_constructed_cells(room, oracle_room, seed):
+    """The cell-grid RANSAC of the learned path (relo_regressor_relocalise_cells: cell forest,
+    coarse view, preemptive RANSAC) against the oracle's RANSAC on the cell forest of the same
+    cells.  The cells are built so that hypotheses exist: each cell's value is the true scene
+    coordinate of its centre pixel plus 1 cm Gaussian noise, with 15 % of the cells replaced by
+    coordinates up to 2 m away (outliers), and log-variances around log(0.03^2)."""
     world, _ = room
     intr = synth.Intrinsics.for_size(320, 240)
-    reg = B.Regressor(seed=4, origin=ORIGIN)
-    P = synth.training_poses(world, 2, seed=93)[0]
-    d, c = oracle_room.raycast(intr, P)
-    dd, cc = _u16(d)[None], torch.from_numpy(c).to(DEV)[None]
-    out = torch.zeros((1, 30, 40, 4), dtype=torch.float32, device=DEV)
-    ws = torch.empty(B.regressor_workspace_size(1, 320, 240, False), dtype=torch.uint8, device=DEV)
-    B.regressor_forward(reg, dd, cc, out, ws)
-    prm = B.ransac_params(n_hyps=32, batch=64, seed=2, max_tries=2000)
-    wsr = torch.empty(B.regressor_relocalise_workspace_size(320, 240, prm), dtype=torch.uint8, device=DEV)
+    P = synth.training_poses(world, 3, seed=93 + seed)[seed]
+    d, _ = oracle_room.raycast(intr, P)
+    y, m = R.cell_targets(d, intr, P, ORIGIN)
+    rng = np.random.default_rng(100 + seed)
+    cells = np.zeros(y.shape[:2] + (4,), np.float64)
+    cells[..., :3] = y + 0.01 * rng.standard_normal(y.shape)
+    out = rng.random(y.shape[:2]) < 0.15
+    cells[out, :3] += rng.uniform(-2.0, 2.0, (int(out.sum()), 3))
+    cells[..., 3] = np.log(0.03 ** 2) + 0.3 * rng.standard_normal(y.shape[:2])
+    cells = cells.astype(np.float32)
+    prm = B.ransac_params(n_hyps=64, batch=64, seed=seed, max_tries=2000)
+    ws = torch.empty(B.regressor_relocalise_workspace_size(320, 240, prm), dtype=torch.uint8, device=DEV)
     res = torch.zeros(B.RESULT_BYTES, dtype=torch.uint8, device=DEV)
-    B.regressor_relocalise(reg, dd[0], cc[0], intr, prm, wsr, res)
+    B.regressor_relocalise_cells(torch.from_numpy(cells).to(DEV), ORIGIN, _u16(d), intr, prm, ws, res)
     torch.cuda.synchronize()
     r = B.result_from_bytes(res)
-    o = out.cpu().numpy()[0].astype(np.float64)
     dl, ci = R.cell_view(d, intr)
-    forest, leaves = R.cell_forest(o, ORIGIN, dl > 0)
-    ro = oracle.preemptive_ransac(dl, ci, leaves, forest, oracle.RansacParams(n_hyps=32, batch=64, seed=2,
-                                                                              max_tries=2000))
+    forest, leaves = R.cell_forest(cells.astype(np.float64), ORIGIN, dl > 0)
+    ro = oracle.preemptive_ransac(dl, ci, leaves, forest, oracle.RansacParams(n_hyps=64, batch=64, seed=seed,
+                                                                              max_tries=2000), trace=True)
+    assert ro["valid"] and r["status"] == 0
     assert r["n_valid"] == int((dl > 0).sum())
-    assert bool(r["status"] == 0) == ro["valid"]
-    if ro["valid"]:
+    dt, dr = oracle.pose_error(ro["pose"], P)
+    assert dt <= 0.05 and dr <= 5.0
+    if not _near_tie_in_trace(ro["trace"]):
         assert r["hypothesis"] == ro["index"]
-        assert np.abs(r["pose"][:3] - ro["pose"][:3]).max() < 1e-3
+        assert np.abs(r["pose"][:3] - ro["pose"][:3]).max() < 1e-4
+        assert abs(r["energy"] - ro["energy"]) <= 1e-5 * abs(ro["energy"])
+
+
+def test_training_fits_fixed_views_to_centimetres(room, oracle_room):
+    """Trained long enough on four fixed views, the regressor fits their cells to centimetres and
+    its RANSAC relocalises them: the optimiser, the loss and the data path work, so a
+    generalisation gap elsewhere is a matter of data or capacity, not of a broken training loop."""
+    world, _ = room
+    intr = synth.Intrinsics.for_size(320, 240)
+    poses = synth.training_poses(world, 2, seed=95)[:4]
+    ds, cs = zip(*[oracle_room.raycast(intr, P) for P in poses])
+    d, c = np.stack(ds), np.stack(cs)
+    reg = B.Regressor(seed=8, origin=ORIGIN)
+    n = len(poses)
+    ws = torch.empty(B.regressor_workspace_size(n, 320, 240, True), dtype=torch.uint8, device=DEV)
+    dd, cc = _u16(d), torch.from_numpy(c).to(DEV)
+    steps = 3000
+    for k in range(steps):
+        lr = 1e-3 * (0.5 * (1 + np.cos(np.pi * k / steps)))
+        B.regressor_train_step(reg, dd, cc, intr, poses, max(lr, 1e-5), ws)
+    out = torch.zeros((n, 30, 40, 4), dtype=torch.float32, device=DEV)
+    wsf = torch.empty(B.regressor_workspace_size(n, 320, 240, False), dtype=torch.uint8, device=DEV)
+    B.regressor_forward(reg, dd, cc, out, wsf)
+    torch.cuda.synchronize()
+    o = out.cpu().numpy().astype(np.float64)
+    errs = []
+    for k, P in enumerate(poses):
+        y, m = R.cell_targets(d[k], intr, P, ORIGIN)
+        errs.append(np.linalg.norm(o[k, ..., :3] - y, axis=-1)[m])
+    err = np.concatenate(errs)
+    assert np.median(err) < 0.05, np.median(err)
+    prm = B.ransac_params(n_hyps=256, batch=64, seed=1, max_tries=2000)
+    wsr = torch.empty(B.regressor_relocalise_workspace_size(320, 240, prm), dtype=torch.uint8, device=DEV)
+    for k, P in enumerate(poses):
+        res = torch.zeros(B.RESULT_BYTES, dtype=torch.uint8, device=DEV)
+        B.regressor_relocalise(reg, dd[k], cc[k], intr, prm, wsr, res)
+        torch.cuda.synchronize()
+        r = B.result_from_bytes(res)
+        dt, dr = oracle.pose_error(r["pose"], P)
+        assert r["status"] == 0 and dt <= 0.05 and dr <= 5.0, (k, dt, dr)
 
 
 @pytest.fixture(scope="module")

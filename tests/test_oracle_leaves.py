@@ -130,3 +130,18 @@ def test_stride_and_invalid_pixels_are_skipped():
     _, count = r.contents()
     v, u = np.mgrid[0:25, 0:40]
     assert count[0, 0] == int(((d > 0) & (u % 2 == 0) & (v % 2 == 0)).sum())
+
+
+def test_threaded_mode_fill_equals_one_thread(room, oracle_room):
+    """Filling the leaves' modes from several threads (disjoint leaf ranges) gives the modes of the
+    one-thread fill bit for bit."""
+    world, _ = room
+    intr = synth.Intrinsics.for_size(160, 120)
+    frames = [(intr, P) + oracle_room.raycast(intr, P) for P in synth.training_poses(world, 3, seed=12)]
+    nodes = synth.random_forest_nodes(2, 6, seed=3, depth_tau=100, colour_tau=32)
+    p = oracle.LeafParams(capacity=32, max_modes=4, seed=1)
+    one = oracle.train_forest(nodes, frames, p)
+    many = oracle.train_forest(nodes, frames, p, threads=4)
+    assert one.n_modes.sum() > 20
+    assert np.array_equal(one.n_modes, many.n_modes)
+    assert np.array_equal(one.modes.view(np.uint32), many.modes.view(np.uint32))

@@ -5,10 +5,11 @@ Some callers cannot allocate device memory while they relocalise (their memory b
 another allocator, or an allocation could stall a latency-bound loop), so the library offers a
 variant whose scratch is a fixed array inside the library.  This file is collected last so
 that a run stopping at the first failure has already run every other test; it also passes on
-its own in a fresh process.  Two calls in a row must each match relo_ransac_relocalise on the
-same inputs (the library's RANSAC tolerances: poses 1e-4, energies 1e-5 relative; integer
-fields exact), which also shows that the second call is not disturbed by what the first left
-in the shared array."""
+its own in a fresh process.  Both entry points run the same kernels on the same inputs, so every
+call must give the workspace entry point's result byte for byte.  The calls run in a row with
+changing sizes -- a small view, a larger hypothesis count, a 640 x 480 view with 1024 hypotheses
+(the largest the header says fits), then the first view again -- which also shows that no call
+is disturbed by what the previous one left in the shared array."""
 import numpy as np
 import pytest
 import torch
@@ -25,12 +26,12 @@ def _u16(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint16).view(np.int16)).to(DEV)
 
 
-def _views(room, oracle_room, room_forest, room_training, n):
+def _views(room, oracle_room, room_forest, room_training, sizes):
     world, _ = room
-    intr = synth.Intrinsics.for_size(320, 240)
-    poses = synth.query_poses(world, [f[1] for f in room_training], n, seed=77)
     out = []
-    for P in poses:
+    for k, (W, H) in enumerate(sizes):
+        intr = synth.Intrinsics.for_size(W, H)
+        P = synth.query_poses(world, [f[1] for f in room_training], len(sizes), seed=77)[k]
         d, c = oracle_room.raycast(intr, P)
         out.append((intr, d, oracle.forest_eval(room_forest.nodes, d, c)))
     return out
@@ -38,9 +39,13 @@ def _views(room, oracle_room, room_forest, room_training, n):
 
 def test_noalloc_matches_workspace_entry_point(room, oracle_room, room_forest, room_training):
     forest = B.Forest(room_forest.nodes, room_forest.modes, room_forest.n_modes, max_modes=10)
-    views = _views(room, oracle_room, room_forest, room_training, 2)
-    for call, (intr, d, leaves) in enumerate(views):       # two calls in a row
-        prm = B.ransac_params(n_hyps=64 + 32 * call, batch=200 + 100 * call, seed=5 + call)
+    small, large = _views(room, oracle_room, room_forest, room_training, [(320, 240), (640, 480)])
+    calls = [(small, dict(n_hyps=64, batch=200, seed=5)),
+             (small, dict(n_hyps=96, batch=300, seed=6)),
+             (large, dict(n_hyps=1024, batch=64, seed=7)),
+             (small, dict(n_hyps=64, batch=200, seed=5))]
+    for call, ((intr, d, leaves), kw) in enumerate(calls):    # calls in a row on the shared array
+        prm = B.ransac_params(**kw)
         dd, ld = _u16(d), _u16(leaves)
         got = torch.zeros(B.RESULT_BYTES, dtype=torch.uint8, device=DEV)
         want = torch.zeros_like(got)
@@ -49,11 +54,8 @@ def test_noalloc_matches_workspace_entry_point(room, oracle_room, room_forest, r
         B.ransac_relocalise(forest, dd, ld, intr, prm, ws, want)
         torch.cuda.synchronize()
         g, w = B.result_from_bytes(got), B.result_from_bytes(want)
-        assert g["status"] == w["status"] == B.OK
-        for k in ("hypothesis", "n_inliers", "n_valid", "n_rounds", "tries"):
-            assert g[k] == w[k], k
-        assert np.abs(g["pose"] - w["pose"]).max() <= 1e-4
-        assert abs(g["energy"] - w["energy"]) <= 1e-5 * abs(w["energy"])
+        assert w["status"] == B.OK and w["n_valid"] > 0, call
+        assert torch.equal(got, want), (call, g, w)
 
 
 def test_noalloc_rejects_views_beyond_its_scratch(room_forest):
