@@ -14,8 +14,7 @@ A step = one batch of ``--batch`` attempts: one replay of the CUDA graph relo_ba
 recorded from relo_batch_run (inputs resident in HBM; the L2 is flushed between steps; each step
 timed with CUDA events on the launching stream).
 ``e2e`` = the same metric through relo_relocalise_batch with the query noise images copied from
-pinned host memory and the results copied back inside the timed region; the next step's noise copy
-overlaps the current step on a second stream (``serial_value``: one step after another).
+pinned host memory and the results copied back inside the timed region, one step after another.
 ``--impl reference`` times the CPU oracle (the deliberately slow FP64 reference) instead.
 """
 from __future__ import annotations
@@ -452,45 +451,28 @@ def run_ours(args):
     # ---- end to end through the public API (host buffers) ----------------------------------
     # Every step copies its query noise from pinned host memory, relocalises through the C-ABI
     # call (which prepares the batch, runs it, copies the results into host memory and waits) and
-    # flushes the L2 first.  Measured right after the device-timed steps, with its own clock
-    # samples.  Serial: one step after another.  Pipelined: step s + 1's noise copy runs on a copy
-    # stream while step s relocalises (the input sets alternate, and a set's buffer is rewritten
-    # only after the call that last read it returned).
+    # flushes the L2 first; one step after another.  Measured right after the device-timed steps,
+    # with its own clock samples.  (Copying the next step's noise on a second stream did not
+    # overlap: the call's own descriptor uploads queue behind the copy.)
     host_noise = [torch.empty((A, H, W), dtype=torch.float32, pin_memory=True) for _ in range(n_sets)]
     for si in range(n_sets):
         host_noise[si].copy_(sets[si]["noise"].cpu())
     host_results = (B.PoseResult * A)()
-    copy_stream = torch.cuda.Stream(dev)
-    copied = [torch.cuda.Event() for _ in range(n_sets)]
 
-    def stage_noise(s, on):
-        i = (args.warmup + s) % n_sets
-        with torch.cuda.stream(on):
-            sets[i]["noise"].copy_(host_noise[i], non_blocking=True)
-            copied[i].record(on)
-
-    def e2e_steps(pipelined):
+    def e2e_steps():
         if world_size > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        overlap = pipelined and n_sets > 1
-        if overlap:
-            stage_noise(0, copy_stream)
         for s in range(args.steps):
             i = (args.warmup + s) % n_sets
-            if overlap and s + 1 < args.steps:
-                stage_noise(s + 1, copy_stream)
-            elif not overlap:
-                stage_noise(s, stream)
-            stream.wait_event(copied[i])
+            sets[i]["noise"].copy_(host_noise[i], non_blocking=True)
             flush.zero_()
             B.relocalise_batch_into(sets[i]["att"], prm, sets[i]["ws"], host_results)
         return reduce_max(time.perf_counter() - t0, world_size, dev)
 
     clk_e2e = clocks_sampler(local)
-    e2e_serial = job_throughput(A, args.steps, world_size, e2e_steps(False))
-    e2e_value = job_throughput(A, args.steps, world_size, e2e_steps(True))
+    e2e_value = job_throughput(A, args.steps, world_size, e2e_steps())
     e2e_clocks = clocks_summary(clk_e2e)
 
     # ---- the learned path (not part of the timed forest steps) -----------------------------
@@ -538,9 +520,7 @@ def run_ours(args):
                            "fragments": frag},
                 "e2e": {"value": e2e_value, "unit": UNIT,
                         "h2d_bytes_per_step": A * H * W * 4 + A * ctypes_attempt_bytes(),
-                        "d2h_bytes_per_step": A * B.RESULT_BYTES, "serial_value": e2e_serial,
-                        "overlap": "the next step's noise copy runs on a second stream" if n_sets > 1 else None,
-                        "clocks": e2e_clocks},
+                        "d2h_bytes_per_step": A * B.RESULT_BYTES, "clocks": e2e_clocks},
                 "gpu_launches": sets[0]["batch"].launch_count * args.steps,
                 "roofline": roof, "roofline_stages": roofs, "cpu_baseline": cpu, "clocks": clocks}
         print(json.dumps(line), flush=True)

@@ -670,6 +670,17 @@ int64_t relo_debug_check_failures(void);
  * its bound: attempts that raycast the scene through the hash (relo_scene_use_grid(scene, 0))
  * report RELO_EDEVICE.  Synchronous.  Errors: RELO_EINVAL (null scene). */
 relo_status relo_debug_corrupt_scene(relo_scene* scene);
+/* The regressor's 64 -> 64-channel forward convolutions run on the tcgen05 tensor cores
+ * (TMA-fed, TMEM accumulators) by default; use_tcgen05 = 0 switches them to the mma.sync kernel
+ * that the other layers use, so that tests can compare the two on the same operands.  Applies to
+ * launches issued (or captured) afterwards. */
+void relo_debug_conv_path(int32_t use_tcgen05);
+/* Makes the tcgen05 convolution's load producer withhold the loads of output tile `tile` of every
+ * later launch (tile < 0: none), and sets the limit of its bounded waits to timeout_ms (<= 0: the
+ * default of 2 s).  The consumer's wait for the withheld tile then runs out: the launch stops,
+ * frees its tensor memory and records RELO_ETIMEOUT, which the learned path reports as the
+ * result's status.  The GPU context stays usable. */
+void relo_debug_conv_stall(int32_t tile, int32_t timeout_ms);
 
 #ifdef __cplusplus
 }

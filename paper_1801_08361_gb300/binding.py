@@ -164,6 +164,8 @@ _SIGS = {
                                           ctypes.POINTER(c_vp)]),
     "relo_set_allocator": (c_i32, [ALLOC_FN, FREE_FN, c_vp]),
     "relo_debug_fail_allocations": (None, [c_i32]),
+    "relo_debug_conv_path": (None, [c_i32]),
+    "relo_debug_conv_stall": (None, [c_i32, c_i32]),
     "relo_debug_check_failures": (c_i64, []),
     "relo_debug_corrupt_scene": (c_i32, [c_vp]),
     "relo_regressor_get_state": (c_i32, [c_vp, c_vp, c_vp, c_vp, ctypes.POINTER(c_i64)]),
@@ -878,6 +880,14 @@ def use_torch_allocator(device=None):
 
 # Fault injection (tests of the error paths)
 # ------------------------------------------------------------------------------------------------
+
+def debug_conv_path(use_tcgen05: bool):
+    lib().relo_debug_conv_path(1 if use_tcgen05 else 0)
+
+
+def debug_conv_stall(tile: int, timeout_ms: int = 0):
+    lib().relo_debug_conv_stall(int(tile), int(timeout_ms))
+
 
 def debug_fail_allocations(n):
     """The library's next n device allocations fail (RELO_ENOMEM); 0 cancels."""

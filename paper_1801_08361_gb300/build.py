@@ -15,7 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "librelo.so")
 CHECKED_LIB = os.path.join(HERE, "librelo_checked.so")
-SOURCES = ["scene.cu", "forest.cu", "ransac.cu", "regressor.cu", "api.cu", "server.cu", "posegraph.cu", "fusion.cu"]
+SOURCES = ["scene.cu", "forest.cu", "ransac.cu", "regressor.cu", "conv_tc.cu", "api.cu", "server.cu", "posegraph.cu",
+           "fusion.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 # occupancy bounds of the raycast, forest and hypothesis-search kernels (tuning knobs; the defaults come from sweeps)

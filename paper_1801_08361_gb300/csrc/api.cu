@@ -25,6 +25,10 @@ static_assert(sizeof(relo_intrinsics) == 56, "relo_intrinsics layout is part of 
 
 namespace relo {
 std::atomic<int> g_fail_allocations{0};
+// test hooks of the tcgen05 convolution (relo_debug_conv_path / relo_debug_conv_stall)
+std::atomic<bool> g_conv_tcgen05{true};
+std::atomic<int> g_conv_stall_tile{-1};
+std::atomic<unsigned long long> g_conv_timeout_ns{2000000000ull};
 
 // The caller's allocator (relo_set_allocator), and every block it gave the library, with the
 // functions that gave it: a block goes back to those even after the allocator has changed.
@@ -683,6 +687,13 @@ relo_status relo_set_allocator(relo_alloc_fn alloc, relo_free_fn free_fn, void* 
   return RELO_OK;
 }
 
+void relo_debug_conv_path(int32_t use_tcgen05) { relo::g_conv_tcgen05.store(use_tcgen05 != 0); }
+
+void relo_debug_conv_stall(int32_t tile, int32_t timeout_ms) {
+  relo::g_conv_stall_tile.store(tile);
+  relo::g_conv_timeout_ns.store(timeout_ms > 0 ? (unsigned long long)timeout_ms * 1000000ull : 2000000000ull);
+}
+
 void relo_debug_fail_allocations(int32_t n) { relo::g_fail_allocations.store(n > 0 ? n : 0); }
 
 int64_t relo_debug_check_failures(void) {
@@ -1281,6 +1292,7 @@ struct relo_regressor {
   int t = 0;
   int n_sms = 148;
   double origin[3] = {0, 0, 0};
+  int32_t* d_status = nullptr;    // RELO_ETIMEOUT when a tcgen05 convolution's bounded wait ran out
 };
 
 namespace {
@@ -1369,7 +1381,15 @@ relo_status reg_forward(relo_regressor* r, const RegBuffers& b, const uint16_t* 
   int Hs[kRegLayers + 1], Ws[kRegLayers + 1];
   reg_sizes(W, H, Hs, Ws);
   RELO_CUDA(launch_input(depth, (const uint32_t*)rgba, (long)n * H * W, b.x, s));
+  RELO_CUDA(cudaMemsetAsync(r->d_status, 0, sizeof(int32_t), s));
   for (int l = 0; l < kRegLayers; ++l) {
+    if (kRegCinPad[l] == 64 && kRegCoutPad[l] == 64 && g_conv_tcgen05.load()) {
+      // the 64 -> 64-channel layers on the tcgen05 tensor cores (TMA-fed implicit GEMM)
+      RELO_CUDA(launch_conv_tc(b.act[l], n, Hs[l], Ws[l], r->d_wk[l], r->d_bias[l], b.act[l + 1], Hs[l + 1],
+                               Ws[l + 1], kRegStride[l], 1, 1, r->d_status, r->n_sms, s, g_conv_timeout_ns.load(),
+                               g_conv_stall_tile.load()));
+      continue;
+    }
     ConvArgs a{};
     a.in = l == 0 ? b.x : b.act[l];
     a.w = r->d_wk[l];
@@ -1508,7 +1528,8 @@ relo_status relo_create_regressor(const float* params, uint64_t seed, const doub
     }
   }
   bool ok = relo::dev_malloc((void**)&r->d_p, r->n_params * 4) == cudaSuccess && relo::dev_malloc((void**)&r->d_g, r->n_params * 4) == cudaSuccess &&
-            relo::dev_malloc((void**)&r->d_m, r->n_params * 4) == cudaSuccess && relo::dev_malloc((void**)&r->d_v, r->n_params * 4) == cudaSuccess;
+            relo::dev_malloc((void**)&r->d_m, r->n_params * 4) == cudaSuccess && relo::dev_malloc((void**)&r->d_v, r->n_params * 4) == cudaSuccess &&
+            relo::dev_malloc((void**)&r->d_status, sizeof(int32_t)) == cudaSuccess;
   for (int l = 0; ok && l < kRegLayers; ++l) {
     ok = relo::dev_malloc((void**)&r->d_wk[l], 9LL * kRegCoutPad[l] * kRegCinPad[l] * sizeof(bf16)) == cudaSuccess &&
          relo::dev_malloc((void**)&r->d_bias[l], 64 * sizeof(float)) == cudaSuccess;
@@ -1523,6 +1544,7 @@ relo_status relo_create_regressor(const float* params, uint64_t seed, const doub
   if (e == cudaSuccess) e = cudaMemset(r->d_m, 0, r->n_params * 4);
   if (e == cudaSuccess) e = cudaMemset(r->d_v, 0, r->n_params * 4);
   if (e == cudaSuccess) e = cudaMemset(r->d_g, 0, r->n_params * 4);
+  if (e == cudaSuccess) e = cudaMemset(r->d_status, 0, sizeof(int32_t));
   if (e != cudaSuccess) {
     relo_destroy_regressor(r);
     return cuda_fail(e, "regressor upload");
@@ -1543,6 +1565,7 @@ void relo_destroy_regressor(relo_regressor* r) {
   relo::dev_free(r->d_g);
   relo::dev_free(r->d_m);
   relo::dev_free(r->d_v);
+  relo::dev_free(r->d_status);
   for (int l = 0; l < kRegLayers; ++l) {
     relo::dev_free(r->d_wk[l]);
     relo::dev_free(r->d_wt[l]);
@@ -1670,8 +1693,9 @@ void learned_layout(char* base, int W, int H, const relo_ransac_params& p, Learn
 }
 
 relo_status learned_ransac(const LearnedLayout& l, const float* cells, int ostride, const double origin[3],
-                           const uint16_t* depth, const relo_intrinsics* intr, const relo_ransac_params* p, void* ws,
-                           size_t ws_bytes, relo_pose_result* result, cudaStream_t s);
+                           const int32_t* upstream, const uint16_t* depth, const relo_intrinsics* intr,
+                           const relo_ransac_params* p, void* ws, size_t ws_bytes, relo_pose_result* result,
+                           cudaStream_t s);
 
 relo_intrinsics coarse_intrinsics(const relo_intrinsics& in) {
   relo_intrinsics c = in;
@@ -1710,7 +1734,7 @@ relo_status relo_regressor_relocalise(relo_regressor* r, const uint16_t* depth, 
   cudaStream_t s = (cudaStream_t)stream;
   st = reg_forward(r, l.reg, depth, rgba, 1, intr->width, intr->height, s);
   if (st) return st;
-  return learned_ransac(l, l.reg.head, 8, r->origin, depth, intr, p, ws, ws_bytes, result, s);
+  return learned_ransac(l, l.reg.head, 8, r->origin, r->d_status, depth, intr, p, ws, ws_bytes, result, s);
 }
 
 relo_status relo_regressor_relocalise_cells(const float* cells, const double origin[3], const uint16_t* depth,
@@ -1728,7 +1752,7 @@ relo_status relo_regressor_relocalise_cells(const float* cells, const double ori
   learned_layout(nullptr, intr->width, intr->height, *p, l);
   if (l.bytes > ws_bytes) return fail(RELO_EINVAL, "workspace too small");
   learned_layout((char*)ws, intr->width, intr->height, *p, l);
-  return learned_ransac(l, cells, 4, origin, depth, intr, p, ws, ws_bytes, result, (cudaStream_t)stream);
+  return learned_ransac(l, cells, 4, origin, nullptr, depth, intr, p, ws, ws_bytes, result, (cudaStream_t)stream);
 }
 
 }  // extern "C"
@@ -1737,8 +1761,9 @@ namespace {
 // The learned path's RANSAC from cell outputs (scene coordinate - origin, log-variance; ostride
 // floats per cell): the cell forest, the coarse view, then the RANSAC of one view.
 relo_status learned_ransac(const LearnedLayout& l, const float* cells, int ostride, const double origin[3],
-                           const uint16_t* depth, const relo_intrinsics* intr, const relo_ransac_params* p, void* ws,
-                           size_t ws_bytes, relo_pose_result* result, cudaStream_t s) {
+                           const int32_t* upstream, const uint16_t* depth, const relo_intrinsics* intr,
+                           const relo_ransac_params* p, void* ws, size_t ws_bytes, relo_pose_result* result,
+                           cudaStream_t s) {
   CellForestArgs ca{};
   ca.out = cells;
   ca.ostride = ostride;
@@ -1770,6 +1795,7 @@ relo_status learned_ransac(const LearnedLayout& l, const float* cells, int ostri
   const relo_status st =
       single_setup_view(fv, l.depth_lr, l.leaves, &ci, p, (char*)ws + l.ransac_off, ws_bytes - l.ransac_off, sr);
   if (st) return st;
+  sr.job.upstream = upstream;
   return single_run(sr, p, result, s);
 }
 }  // namespace
@@ -1998,6 +2024,7 @@ void layout_batch(const relo_attempt* at, int n, const relo_ransac_params& p, ch
       r.vW = W;
       r.vH = H;
       r.err = b.d_errs + j;
+      r.upstream = reg->d_status;
       r.result = b.d_res_L + i;
       r.chunk_begin = chL;
       r.hyp_begin = hyL;

@@ -874,7 +874,8 @@ __global__ void finalise_kernel(const RansacJob* __restrict__ jobs, int n_jobs) 
   res->pose_c2s[15] = 1.0;
   res->energy = job.energy[h];
   res->n_inliers = job.inliers[h];
-  res->status = *job.err ? RELO_EDEVICE : (job.hyp_ok[h] ? RELO_OK : RELO_ENOTFOUND);
+  const int32_t up = job.upstream ? *job.upstream : 0;
+  res->status = up ? up : (*job.err ? RELO_EDEVICE : (job.hyp_ok[h] ? RELO_OK : RELO_ENOTFOUND));
   res->verified = 0;
   res->n_valid = *job.n_valid;
   res->hypothesis = h;

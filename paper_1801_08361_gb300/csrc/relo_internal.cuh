@@ -364,6 +364,8 @@ struct RansacJob {
   int32_t hs;                  // int4 words per drawn-pixel record: 1 + ceil(T / 2)
   int32_t refit_parts;         // blocks per hypothesis in refit: ceil(n_rounds * B / kRefinePixels)
   int32_t* err;                // [1]
+  const int32_t* upstream;     // nullable: status of the stage that made this job's input (the
+                               // learned path's network); when nonzero it becomes the result's status
   relo_pose_result* result;    // device
   int32_t chunk_begin;         // flattened compaction chunks
   int32_t hyp_begin;           // flattened hypotheses

@@ -95,10 +95,27 @@ def test_house_leaves_and_hypotheses_bit_exact(house):
     assert np.abs(pg[ok] - tr.poses0[ok, :3, :]).max() < 1e-9
 
 
+def _refit_is_ill_posed(pose_in, cam, drawn, leaves, forest, inlier_dist):
+    """True when the oracle's own re-fit moves by more than 1e-5 if its camera points are rounded
+    to FP32 (the precision the library holds them in): then the re-fit is not determined at the
+    pose tolerance.  This happens for inlier sets of rank one -- pixels are drawn with
+    replacement, so "three inliers" can be two distinct points, whose rotation about their line is
+    arbitrary."""
+    _, mu, found, x = oracle.pixel_energies(pose_in, cam, drawn, leaves, forest)
+    dist = np.where(found, np.linalg.norm(x - mu, axis=1), np.inf)
+    m = dist < inlier_dist
+    if m.sum() < 3:
+        return False
+    R0, t0 = oracle.kabsch(cam[m], mu[m])
+    R1, t1 = oracle.kabsch(cam[m].astype(np.float32).astype(np.float64), mu[m])
+    return max(np.abs(R1 - R0).max(), np.abs(t1 - t0).max()) > 1e-5
+
+
 def test_house_rounds_teacher_forced(house):
     """Each of the 10 rounds on the GPU starts from the oracle's state (alive set, poses, energies,
     earlier draws) and must reproduce the oracle's draws, energies, survivors, inlier counts and
-    re-fits."""
+    re-fits (re-fits that FP32 rounding of the oracle's own inputs moves beyond the tolerance are
+    not compared)."""
     intr, d, leaves_o, forest = house["intr"], house["d"], house["leaves"], house["forest"]
     tr = house["res"]["trace"]
     prm = B.ransac_params(n_hyps=K, batch=BPIX, seed=9)
@@ -109,7 +126,7 @@ def test_house_rounds_teacher_forced(house):
     E_prev = np.where(tr.valid0, 0.0, np.inf)
     drawn_prev = np.zeros(0, np.int64)
     vpix = oracle.valid_pixels(d)
-    strict_rounds = refits = 0
+    strict_rounds = refits = ill_posed = 0
     assert len(tr.rounds) == 10
     for r, rd in enumerate(tr.rounds):
         alive = rd["alive_before"]
@@ -148,13 +165,16 @@ def test_house_rounds_teacher_forced(house):
             if dm.min() < 1e-4 or am.min() < 1e-3:
                 continue
             assert ig[h] == rd["inliers"][h], (r, h)
+            if _refit_is_ill_posed(pose_in, cam, all_drawn, leaves_o, forest, house["prm_o"].inlier_dist):
+                ill_posed += 1
+                continue
             assert np.abs(pg[h] - rd["poses"][h][:3, :]).max() < 1e-4, (r, h)
             refits += 1
         poses_prev = rd["poses"][:, :3, :].copy()
         E_prev = rd["energy"].copy()
         drawn_prev = all_drawn
     assert strict_rounds >= len(tr.rounds) - 1
-    assert refits >= 100
+    assert refits >= 100 and ill_posed <= refits // 20, (refits, ill_posed)
 
 
 def test_house_relocalise_matches_oracle_end_to_end(house):
