@@ -5,15 +5,18 @@ fully-convolutional network as an alternative relocaliser for a scene, trained o
 rendered from the scene's own voxel map and used inside the same preemptive RANSAC.  Nothing in
 the paper fixes its details; the readings here are implemented identically by the CUDA library:
 
-- input: 4 channels per pixel, depth in metres (0 where invalid) and R, G, B / 255;
+- input: 4 channels per pixel, centred and scaled: (depth in metres - 3) / 2 (depth 0 where
+  invalid) and (R, G, B / 255 - 1/2) x 4;
 - layers: eight 3x3 convolutions with zero padding 1, 64 channels; the first three have stride
   2 (so the output grid has one cell per 8 x 8 pixels), the rest stride 1; ReLU after layers
   1-7; layer 8 outputs 4 channels per cell: a scene coordinate relative to a fixed origin o and
   a log-variance s;
 - target of cell (cx, cy): the scene coordinate of its centre pixel (8 cx + 4, 8 cy + 4),
   P * backproject(depth) - o, when that pixel has depth (else the cell is not scored);
-- loss: mean over scored cells of 1/2 |y - y_hat|^2 exp(-s) + 3/2 s (the negative log-likelihood
-  of an isotropic Gaussian up to a constant);
+- loss: mean over scored cells of rho(e) + 1/2 e^2 exp(-s) + 3/2 s, e = |y - y_hat|,
+  rho(e) = sqrt(e^2 + 1e-6 m^2): the coordinates are fitted by their (smoothed) Euclidean error,
+  which no value of s can discount, and s by the negative log-likelihood of an isotropic
+  Gaussian with the error held fixed (that term's gradient does not reach y_hat);
 - optimiser: Adam (Kingma and Ba 2015), beta = (0.9, 0.999), eps = 1e-8, FP64 here.
 
 Every operation is the plain definition: a convolution is im2col (a gather) followed by a matrix
@@ -29,6 +32,9 @@ import numpy as np
 
 STRIDES = (2, 2, 2, 1, 1, 1, 1, 1)
 CHANNELS = 64
+DEPTH_CENTRE, DEPTH_SCALE = 3.0, 0.5       # input channel 0: (depth m - 3) x 0.5
+COLOUR_CENTRE, COLOUR_SCALE = 0.5, 4.0     # input channels 1-3: (colour / 255 - 0.5) x 4
+RHO_EPS2 = 1e-6                            # m^2: smoothing of the Euclidean coordinate error
 
 
 def out_size(n: int, stride: int) -> int:
@@ -108,18 +114,32 @@ def forward(params: Params, x, strides=STRIDES):
 
 
 def loss_and_grad_output(out, target, mask):
-    """Mean Gaussian NLL over scored cells and its gradient with respect to the output."""
+    """Mean over scored cells of rho(e) + 1/2 e^2 exp(-s) + 3/2 s and the gradient the training
+    follows: d rho / d y_hat for the coordinates, the NLL's derivative for s (the error in the
+    variance term held fixed).  That gradient is the exact gradient of surrogate_loss at
+    sq_fixed = the current squared errors."""
     n = max(int(mask.sum()), 1)
     s = out[..., 3]
     err = out[..., :3] - target
     sq = (err * err).sum(-1)
+    rho = np.sqrt(sq + RHO_EPS2)
     e = np.exp(-s)
-    per = 0.5 * sq * e + 1.5 * s
+    per = rho + 0.5 * sq * e + 1.5 * s
     loss = float((per * mask).sum() / n)
     g = np.zeros_like(out)
-    g[..., :3] = err * (e * mask / n)[..., None]
+    g[..., :3] = err * (mask / (n * rho))[..., None]
     g[..., 3] = (-0.5 * sq * e + 1.5) * mask / n
     return loss, g
+
+
+def surrogate_loss(out, target, mask, sq_fixed):
+    """The loss with the squared error of the variance term held at sq_fixed: a plain function of
+    the output whose gradient at sq_fixed = the current squared errors is the training gradient."""
+    n = max(int(mask.sum()), 1)
+    s = out[..., 3]
+    err = out[..., :3] - target
+    rho = np.sqrt((err * err).sum(-1) + RHO_EPS2)
+    return float(((rho + 0.5 * sq_fixed * np.exp(-s) + 1.5 * s) * mask).sum() / n)
 
 
 def backward(params: Params, acts, g_out, strides=STRIDES):
@@ -170,10 +190,11 @@ class Adam:
 
 
 def network_input(depth_mm, rgba):
-    """[H, W] uint16 depth and [H, W, 4] uint8 colour -> [H, W, 4] float input channels."""
+    """[H, W] uint16 depth and [H, W, 4] uint8 colour -> [H, W, 4] float input channels, centred
+    and scaled to about [-2, 2]."""
     x = np.zeros(depth_mm.shape + (4,), dtype=np.float64)
-    x[..., 0] = depth_mm.astype(np.float64) / 1000.0
-    x[..., 1:] = rgba[..., :3].astype(np.float64) / 255.0
+    x[..., 0] = (depth_mm.astype(np.float64) / 1000.0 - DEPTH_CENTRE) * DEPTH_SCALE
+    x[..., 1:] = (rgba[..., :3].astype(np.float64) / 255.0 - COLOUR_CENTRE) * COLOUR_SCALE
     return x
 
 

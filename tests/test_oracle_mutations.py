@@ -179,14 +179,37 @@ def test_loss_gradient_that_ignores_the_mask(monkeypatch):
         s = out[..., 3]
         err = out[..., :3] - target
         sq = (err * err).sum(-1)
+        rho = np.sqrt(sq + R.RHO_EPS2)
         e = np.exp(-s)
-        loss = float(((0.5 * sq * e + 1.5 * s) * mask).sum() / n)
+        loss = float(((rho + 0.5 * sq * e + 1.5 * s) * mask).sum() / n)
         g = np.zeros_like(out)
-        g[..., :3] = err * (e / n)[..., None]          # mistake: unscored cells get a gradient
+        g[..., :3] = err / (n * rho)[..., None]        # mistake: unscored cells get a gradient
         g[..., 3] = (-0.5 * sq * e + 1.5) * mask / n
         return loss, g
     monkeypatch.setattr(R, "loss_and_grad_output", loss_and_grad_output)
     _fails(pins_reg.test_gradients_match_central_differences)
+
+
+def test_variance_term_that_pulls_the_coordinates(monkeypatch):
+    def loss_and_grad_output(out, target, mask):
+        n = max(int(mask.sum()), 1)
+        s = out[..., 3]
+        err = out[..., :3] - target
+        sq = (err * err).sum(-1)
+        rho = np.sqrt(sq + R.RHO_EPS2)
+        e = np.exp(-s)
+        loss = float(((rho + 0.5 * sq * e + 1.5 * s) * mask).sum() / n)
+        g = np.zeros_like(out)
+        g[..., :3] = err * (mask * (1.0 / rho + e) / n)[..., None]    # mistake: the NLL's pull on y_hat kept
+        g[..., 3] = (-0.5 * sq * e + 1.5) * mask / n
+        return loss, g
+    monkeypatch.setattr(R, "loss_and_grad_output", loss_and_grad_output)
+    _fails(pins_reg.test_coordinate_gradient_ignores_the_variance)
+
+
+def test_network_input_without_its_centring(monkeypatch):
+    monkeypatch.setattr(R, "DEPTH_CENTRE", 0.0)                    # mistake: depth not centred
+    _fails(pins_reg.test_network_input_centres_and_scales)
 
 
 def test_adam_without_bias_correction(monkeypatch):

@@ -48,12 +48,14 @@ def test_gradients_match_central_differences():
     target = rng.normal(size=out.shape[:3] + (3,))
     mask = rng.random(out.shape[:3]) < 0.8
 
-    def f():
-        o, _ = R.forward(params, x, strides)
-        return R.loss_and_grad_output(o, target, mask)[0]
-
     out, acts = R.forward(params, x, strides)
     _, g = R.loss_and_grad_output(out, target, mask)
+    sq_fixed = ((out[..., :3] - target) ** 2).sum(-1)
+
+    def f():
+        o, _ = R.forward(params, x, strides)
+        return R.surrogate_loss(o, target, mask, sq_fixed)
+
     grads = R.backward(params, acts, g, strides)
     h = 1e-6
     for p, gp in zip(params.flat(), grads.flat()):
@@ -76,9 +78,38 @@ def test_loss_closed_form():
     target = np.zeros((1, 1, 2, 3))
     mask = np.array([[[True, False]]])
     loss, g = R.loss_and_grad_output(out, target, mask)
-    assert loss == pytest.approx(0.5 * 14 * math.exp(-0.5) + 0.75)
+    rho = math.sqrt(14 + 1e-6)
+    assert loss == pytest.approx(rho + 0.5 * 14 * math.exp(-0.5) + 0.75)
     assert np.allclose(g[0, 0, 1], 0)
     assert g[0, 0, 0, 3] == pytest.approx(-0.5 * 14 * math.exp(-0.5) + 1.5)
+    assert np.allclose(g[0, 0, 0, :3], np.array([1.0, 2.0, 3.0]) / rho)
+
+
+def test_coordinate_gradient_ignores_the_variance():
+    """The coordinates follow the Euclidean error alone: a unit vector along the error for errors
+    well above the smoothing, whatever the predicted log-variance."""
+    rng = np.random.default_rng(5)
+    out = rng.normal(size=(1, 3, 4, 4))
+    target = out[..., :3] + rng.normal(size=(1, 3, 4, 3))
+    mask = np.ones((1, 3, 4), bool)
+    _, g1 = R.loss_and_grad_output(out, target, mask)
+    out2 = out.copy()
+    out2[..., 3] += 3.0
+    _, g2 = R.loss_and_grad_output(out2, target, mask)
+    assert np.allclose(g1[..., :3], g2[..., :3], atol=1e-15)
+    unit = (out[..., :3] - target) / np.linalg.norm(out[..., :3] - target, axis=-1, keepdims=True) / 12
+    assert np.allclose(g1[..., :3], unit, atol=1e-6)
+
+
+def test_network_input_centres_and_scales():
+    d = np.array([[0, 3000, 5000]], np.uint16)
+    c = np.zeros((1, 3, 4), np.uint8)
+    c[0, 1, :3] = 255
+    c[0, 2, :3] = [0, 51, 204]
+    x = R.network_input(d, c)
+    assert np.allclose(x[0, :, 0], [-1.5, 0.0, 1.0])
+    assert np.allclose(x[0, 0, 1:], -2.0) and np.allclose(x[0, 1, 1:], 2.0)
+    assert np.allclose(x[0, 2, 1:], [-2.0, -1.2, 1.2])
 
 
 def test_adam_first_step_closed_form():
