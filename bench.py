@@ -43,7 +43,7 @@ METRIC = "reloc attempts/s at 640x480 (forest vs learned, same success); % HBM r
 UNIT = "attempts/s"
 WORKLOAD = "house 10x8x3 m, 5 mm voxels, 2^20 buckets; 640x480 queries, depth noise 1.5 mm z^2; forest T=5 D=15, " \
            "reservoir 1024, <=10 modes; preemptive RANSAC K=1024, B=64"
-from paper_1801_08361_gb300.presets import HOUSE, LEARNED, SERVING  # noqa: E402
+from paper_1801_08361_gb300.presets import HOUSE, LEARNED, SERVING, learning_rate  # noqa: E402
 
 W, H = HOUSE.sizes[0]
 T_TREES, DEPTH, MAX_MODES, CAPACITY = HOUSE.trees, HOUSE.depth, HOUSE.max_modes, HOUSE.reservoir
@@ -101,6 +101,8 @@ def parse():
                     help="pick the launch schedule with relo_batch_autotune (default: the default schedule, "
                          "which the tuner matches within noise on this workload)")
     ap.add_argument("--profile-steps", type=int, default=0, help="(ncu) run this many steps and exit, no JSON")
+    ap.add_argument("--profile-learned", type=int, default=0,
+                    help="(ncu) this many regressor forward passes over 16 house views, then exit, no JSON")
     ap.add_argument("--train-steps", type=int, default=2000,
                     help="online training steps of the learned regressor (0: skip the learned path)")
     ap.add_argument("--serve-seconds", type=float, default=4.0,
@@ -363,6 +365,10 @@ def run_ours(args):
         args.fusion_frames = args.profile_fusion
         fusion_section(args, B, synth, torch, dev, scene, world, intr, train, nvtx="fusion", capacity=1 << 18)
         return 0
+    if args.profile_learned:
+        # profiler runs of the regressor's forward pass: the passes sit in an NVTX range "learned"
+        profile_learned(args, B, synth, torch, dev, scene, world, intr, train)
+        return 0
     forest = B.Forest(nodes, max_modes=MAX_MODES)
     # relocaliser training on the GPU: noisy renders along the trajectory, stride 2
     B.forest_train_begin(forest, B.train_params(capacity=CAPACITY, stride=2, seed=7))
@@ -475,6 +481,11 @@ def run_ours(args):
     e2e_value = job_throughput(A, args.steps, world_size, e2e_steps())
     e2e_clocks = clocks_summary(clk_e2e)
 
+    # ---- the RANSAC of each pass in one persistent launch (schedule option), same batch ------
+    persistent = None
+    if rank == 0:
+        persistent = persistent_section(args, B, torch, sets[0], schedule, flush, stream)
+
     # ---- the learned path (not part of the timed forest steps) -----------------------------
     learned = None
     if args.train_steps > 0 and rank == 0:
@@ -517,7 +528,7 @@ def run_ours(args):
                            "stage_ms_per_step": {k: v / args.steps for k, v in stage_tot.items()},
                            "schedule": dict(schedule, autotuned=bool(args.autotune)),
                            "learned": learned, "serving": serving, "fusion": fusion, "precision": precision,
-                           "fragments": frag},
+                           "fragments": frag, "persistent_schedule": persistent},
                 "e2e": {"value": e2e_value, "unit": UNIT,
                         "h2d_bytes_per_step": A * H * W * 4 + A * ctypes_attempt_bytes(),
                         "d2h_bytes_per_step": A * B.RESULT_BYTES, "clocks": e2e_clocks},
@@ -547,6 +558,55 @@ def regressor_flops_per_view():
     return fl
 
 
+def timed_replays(bt, torch, flush, stream, n):
+    """ms per replay of a captured batch over n replays (L2 flushed before each)."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    for e in ev:
+        flush.zero_()
+        e[0].record(stream)
+        bt.replay()
+        e[1].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / n
+
+
+def persistent_section(args, B, torch, st, schedule, flush, stream, n=5):
+    """The step's batch with its RANSAC in one persistent launch against the per-stage launches:
+    ms per batch (same results, checked), launches per batch."""
+    bt = st["batch"]
+    ref = st["res"].cpu()
+    out = {}
+    for name, persistent in (("stage_launches", 0), ("persistent", 1)):
+        bt.set_schedule(**dict(schedule, persistent=persistent))
+        bt.capture(st["res"])
+        bt.replay()
+        torch.cuda.synchronize()
+        same = bool(torch.equal(st["res"].cpu(), ref))
+        ms = timed_replays(bt, torch, flush, stream, n)
+        out[name] = {"ms_per_batch": ms, "attempts_per_s": len(st["qs"]) / (ms / 1000.0),
+                     "launches": bt.launch_count, "results_equal_default": same}
+    bt.set_schedule(**schedule)
+    bt.capture(st["res"])
+    return out
+
+
+def profile_learned(args, B, synth, torch, dev, scene, world, intr, train, n=16):
+    poses = synth.query_poses(world, train, n, seed=77)
+    depth = torch.zeros((n, H, W), dtype=torch.int16, device=dev)
+    rgba = torch.zeros((n, H, W, 4), dtype=torch.uint8, device=dev)
+    wsv = torch.empty(B.raycast_views_workspace_size(n), dtype=torch.uint8, device=dev)
+    B.raycast_views(scene, intr, poses, depth, rgba, workspace_dev=wsv)
+    reg = B.Regressor(seed=3, origin=REG_ORIGIN)
+    out = torch.zeros((n, H // 8, W // 8, 4), dtype=torch.float32, device=dev)
+    ws = torch.empty(B.regressor_workspace_size(n, W, H, False), dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("learned")
+    for _ in range(args.profile_learned):
+        B.regressor_forward(reg, depth, rgba, out, ws)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+
+
 def learned_section(args, B, synth, torch, dev, scene, forest, world, intr, train, st, prm, stream):
     nb = TRAIN_BATCH
     pool = synth.query_poses(world, train, args.train_steps * nb, seed=77)
@@ -566,7 +626,7 @@ def learned_section(args, B, synth, torch, dev, scene, forest, world, intr, trai
         q = (s * nb) % n_noise
         B.raycast_views(scene, intr, P, depth, rgba, noise_dev=noise[q:q + nb], workspace_dev=ws_views)
         ev[1].record(stream)
-        lr = TRAIN_LR * (0.1 if s >= 0.75 * args.train_steps else 1.0)
+        lr = learning_rate(s, args.train_steps, TRAIN_LR, LEARNED.extra["warmup"])
         B.regressor_train_step(reg, depth, rgba, intr, P, lr, ws, loss[s:s + 1])
         ev[2].record(stream)
         ev[2].synchronize()
@@ -664,6 +724,15 @@ def fragments_section(args, B, torch, dev, stream, flush):
             stages[k] = stages.get(k, 0.0) + v / FRAG_STEPS
     ms = [a.elapsed_time(b) for a, b in ev]
     raw = res.cpu()
+    # the same batch with its RANSAC in one persistent launch
+    bt.set_schedule(persistent=1)
+    bt.capture(res)
+    bt.replay()
+    torch.cuda.synchronize()
+    pers_same = bool(torch.equal(res.cpu(), raw))
+    pers_ms = timed_replays(bt, torch, flush, stream, FRAG_STEPS)
+    pers_launches = bt.launch_count
+    bt.set_schedule(persistent=0)
     covered = ok = verified = 0
     for k, m in enumerate(meta):
         r = B.result_from_bytes(raw[k * B.RESULT_BYTES:(k + 1) * B.RESULT_BYTES])
@@ -693,7 +762,10 @@ def fragments_section(args, B, torch, dev, stream, flush):
             "l2": "flushed between steps (512 MiB write)", "steps": FRAG_STEPS,
             "stage_ms_per_batch": stages, "roofline_stages": roofs,
             "success_covered": f"{ok}/{covered} (pairs whose query room lies in fragment a; <= 5 cm, <= 5 deg "
-                               f"of the known aT_b)", "verified": verified, "build_s": t_build}
+                               f"of the known aT_b)", "verified": verified, "build_s": t_build,
+            "launches": bt.launch_count,
+            "persistent_schedule": {"ms_per_batch": pers_ms, "attempts_per_s": n / (pers_ms / 1000.0),
+                                    "launches": pers_launches, "results_equal": pers_same}}
 
 
 # ------------------------------------------------------------------------------------------------

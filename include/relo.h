@@ -383,12 +383,15 @@ relo_status relo_ransac_round(const relo_forest* forest, const uint16_t* depth_d
  * Learned scene-coordinate regressor: an alternative relocaliser for one scene, trained online
  * on renders of its own voxel map (the paper uses a forest, Sec. 3.3 (b); this network and its
  * details are readings of the workload, stated identically in the CPU oracle).
- * Input per pixel: depth in metres (0 where invalid) and R, G, B / 255.  Eight 3x3 convolutions
- * (zero padding 1, 64 channels; strides 2, 2, 2, 1, 1, 1, 1, 1; ReLU after layers 1-7) give
- * one cell per 8 x 8 pixels with 4 outputs: the scene coordinate of the cell's centre pixel
- * (8 cx + 4, 8 cy + 4) minus `origin`, and a log-variance s.  Loss: mean over cells whose
- * centre pixel has depth of 1/2 |y - y_hat|^2 exp(-s) + 3/2 s; Adam (0.9, 0.999, 1e-8).
- * Computed with BF16 tensor-core convolutions accumulating in FP32 (FP32 master weights).
+ * Input per pixel: (depth in metres - 3) / 2 (depth 0 where invalid) and (R, G, B / 255 - 1/2)
+ * x 4.  Eight 3x3 convolutions (zero padding 1, 64 channels; strides 2, 2, 2, 1, 1, 1, 1, 1;
+ * ReLU after layers 1-7) give one cell per 8 x 8 pixels with 4 outputs: the scene coordinate of
+ * the cell's centre pixel (8 cx + 4, 8 cy + 4) minus `origin`, and a log-variance s.  Loss: mean
+ * over cells whose centre pixel has depth of rho(e) + 1/2 e^2 exp(-s) + 3/2 s, e = |y - y_hat|,
+ * rho(e) = sqrt(e^2 + 1e-6 m^2); the gradient holds the error of the variance term fixed (the
+ * coordinates follow rho alone).  Adam (0.9, 0.999, 1e-8).  Computed with BF16 tensor-core
+ * convolutions accumulating in FP32 (FP32 master weights): the 64 -> 64-channel forward layers on
+ * tcgen05 (TMA-fed, TMEM accumulators), the rest with mma.sync.
  * Parameters, flat FP32, per layer l: w [3][3][cin][cout] then b [cout], cin = 4, 64, ...,
  * cout = 64, ..., 4 (relo_regressor_param_count() values in all).  Images must have sides that
  * are multiples of 8.  Errors: RELO_EINVAL (sizes, null pointers, workspace), RELO_ENOMEM.
@@ -552,6 +555,11 @@ typedef struct relo_schedule {
   int32_t search_ctas_per_sm; /* hypothesis search: persistent CTAs per SM, 0 = as many as fit */
   int32_t refit_per;          /* round re-fits: survivors per one-warp CTA, 1..32; 0 = enough CTAs
                                  for twice the SM count */
+  int32_t persistent;         /* RANSAC (search, fits, every round, results) of each pass: 0 = one
+                                 launch per stage; 1 = one persistent launch whose CTAs take the
+                                 stages of every attempt from a dependency-ordered list, waiting
+                                 (bounded in time) on per-attempt counters, so that one attempt's
+                                 rounds run while another is still searching.  Same results. */
 } relo_schedule;
 relo_status relo_batch_get_schedule(const relo_batch* batch, relo_schedule* out);
 /* Sets the schedule of later runs and drops a captured graph (capture again).
@@ -681,6 +689,12 @@ void relo_debug_conv_path(int32_t use_tcgen05);
  * frees its tensor memory and records RELO_ETIMEOUT, which the learned path reports as the
  * result's status.  The GPU context stays usable. */
 void relo_debug_conv_stall(int32_t tile, int32_t timeout_ms);
+/* For batches prepared afterwards: stall != 0 makes one item of the persistent RANSAC launch (the
+ * first attempt's first selection) wait for a counter that never reaches its target; timeout_ms
+ * (<= 0: 2 s) bounds that launch's waits.  With the persistent schedule the wait runs out, the
+ * launch stops, and the attempts it did not finish report RELO_ETIMEOUT (unverified).  The GPU
+ * context stays usable. */
+void relo_debug_persistent_stall(int32_t stall, int32_t timeout_ms);
 
 #ifdef __cplusplus
 }

@@ -74,7 +74,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, c_vp, c_vp)
 
 class Schedule(ctypes.Structure):
     _fields_ = [("ray_warp_width", c_i32), ("forest_threads", c_i32), ("forest_tiles", c_i32),
-                ("search_ctas_per_sm", c_i32), ("refit_per", c_i32)]
+                ("search_ctas_per_sm", c_i32), ("refit_per", c_i32), ("persistent", c_i32)]
 
     def to_dict(self) -> dict:
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -166,6 +166,7 @@ _SIGS = {
     "relo_debug_fail_allocations": (None, [c_i32]),
     "relo_debug_conv_path": (None, [c_i32]),
     "relo_debug_conv_stall": (None, [c_i32, c_i32]),
+    "relo_debug_persistent_stall": (None, [c_i32, c_i32]),
     "relo_debug_check_failures": (c_i64, []),
     "relo_debug_corrupt_scene": (c_i32, [c_vp]),
     "relo_regressor_get_state": (c_i32, [c_vp, c_vp, c_vp, c_vp, ctypes.POINTER(c_i64)]),
@@ -887,6 +888,10 @@ def debug_conv_path(use_tcgen05: bool):
 
 def debug_conv_stall(tile: int, timeout_ms: int = 0):
     lib().relo_debug_conv_stall(int(tile), int(timeout_ms))
+
+
+def debug_persistent_stall(stall: bool, timeout_ms: int = 0):
+    lib().relo_debug_persistent_stall(1 if stall else 0, int(timeout_ms))
 
 
 def debug_fail_allocations(n):

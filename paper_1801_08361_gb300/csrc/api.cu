@@ -29,6 +29,9 @@ std::atomic<int> g_fail_allocations{0};
 std::atomic<bool> g_conv_tcgen05{true};
 std::atomic<int> g_conv_stall_tile{-1};
 std::atomic<unsigned long long> g_conv_timeout_ns{2000000000ull};
+// test hooks of the persistent RANSAC launch (relo_debug_persistent_stall)
+std::atomic<bool> g_persist_stall{false};
+std::atomic<unsigned long long> g_persist_timeout_ns{2000000000ull};
 
 // The caller's allocator (relo_set_allocator), and every block it gave the library, with the
 // functions that gave it: a block goes back to those even after the allocator has changed.
@@ -152,7 +155,7 @@ void carve_ransac(Carver& c, RansacJob& j, int W, int H, int K, int B, int n_rou
   const int R = std::max(n_rounds, 1);
   j.hs = 1 + (T + 1) / 2;
   j.refit_parts = (R * B + kRefinePixels - 1) / kRefinePixels;
-  j.refit = c.take<double>((size_t)K * j.refit_parts * 16);
+  j.refit = c.take<float2>((size_t)K * j.refit_parts * 16);
   j.refit_ref = c.take<float>((size_t)K * 8);
   j.pix = c.take<int4>((size_t)R * B * j.hs);
   j.chunk_count = c.take<int32_t>((n_pix + kCompactChunk - 1) / kCompactChunk);
@@ -241,7 +244,69 @@ struct RansacPass {
   int32_t* d_alive_prefix = nullptr;
   int32_t* d_surv_prefix = nullptr;
   std::vector<int> tot_alive, tot_surv, max_alive, max_surv;
+  // the persistent schedule (batches): its items, control words + completion counters
+  PItem* d_items = nullptr;
+  int n_items = 0;
+  int32_t* d_ctrl = nullptr;
+  int ctrl_words = 0, final_base = 0;
 };
+
+// The persistent launch's items for jobs with K[j] hypotheses, B pixels per round, in dependency
+// order (every job's fits, then round by round every job's draw, energy chunks, selection, re-fit
+// sum parts and re-fits, then the finalisations), and the layout of its completion counters:
+// done[g * n + j] for group g of job j -- 0 searched hypotheses, 1 fits, 2 + 5 r + (0 draw,
+// 1 energy, 2 select, 3 refine, 4 refit) for round r, then finalisation.  stall (test hook): the
+// first selection item waits for one chunk more than exists.
+void build_items(const std::vector<int>& K, int B, bool stall, std::vector<PItem>& items, int* n_done,
+                 int* final_base) {
+  const int n = (int)K.size();
+  int R = 0;
+  for (int k : K) R = std::max(R, rounds_for(k));
+  const int g_final = 2 + 5 * R;
+  auto idx = [n](int g, int j) { return g * n + j; };
+  items.clear();
+  std::vector<int> dep(n), need(n), cur(K);
+  for (int j = 0; j < n; ++j) {
+    const int nf = (K[j] + kPersistThreadsHost - 1) / kPersistThreadsHost;
+    for (int c = 0; c < nf; ++c) items.push_back(PItem{kItemFit, j, c, 0, 0, idx(0, j), K[j], idx(1, j)});
+    dep[j] = idx(1, j);
+    need[j] = nf;
+  }
+  for (int r = 0; r < R; ++r) {
+    const int gd = 2 + 5 * r;
+    const int parts = ((r + 1) * B + kRefinePixels - 1) / kRefinePixels;
+    std::vector<int> alive(n, 0);
+    for (int j = 0; j < n; ++j) alive[j] = cur[j] > 1 ? cur[j] : 0;
+    for (int j = 0; j < n; ++j)
+      if (alive[j]) items.push_back(PItem{kItemDraw, j, 0, 0, r, dep[j], need[j], idx(gd, j)});
+    for (int j = 0; j < n; ++j)
+      for (int c = 0; c < (alive[j] + 31) / 32; ++c)
+        items.push_back(PItem{kItemEnergy, j, c, 0, r, idx(gd, j), 1, idx(gd + 1, j)});
+    for (int j = 0; j < n; ++j)
+      if (alive[j]) items.push_back(PItem{kItemSelect, j, 0, 0, r, idx(gd + 1, j), (alive[j] + 31) / 32, idx(gd + 2, j)});
+    for (int j = 0; j < n; ++j)
+      for (int c = 0; c < ((alive[j] + 1) / 2 + 31) / 32; ++c)
+        for (int q = 0; q < parts; ++q) items.push_back(PItem{kItemRefine, j, c, q, r, idx(gd + 2, j), 1, idx(gd + 3, j)});
+    for (int j = 0; j < n; ++j) {
+      if (!alive[j]) continue;
+      const int surv = (alive[j] + 1) / 2, nref = (surv + 31) / 32 * parts;
+      const int nfit = (surv + kPersistThreadsHost - 1) / kPersistThreadsHost;
+      for (int c = 0; c < nfit; ++c) items.push_back(PItem{kItemRefit, j, c, 0, r, idx(gd + 3, j), nref, idx(gd + 4, j)});
+      dep[j] = idx(gd + 4, j);
+      need[j] = nfit;
+      cur[j] = surv;
+    }
+  }
+  for (int j = 0; j < n; ++j) items.push_back(PItem{kItemFinal, j, 0, 0, 0, dep[j], need[j], idx(g_final, j)});
+  if (stall)
+    for (PItem& it : items)
+      if (it.kind == kItemSelect) {
+        it.need += 1;
+        break;
+      }
+  *n_done = (g_final + 1) * n;
+  *final_base = g_final * n;
+}
 
 // Records ev (nullable) on s; external: as an event-record node when s is being captured.
 cudaError_t record(cudaEvent_t ev, cudaStream_t s, bool external) {
@@ -253,6 +318,28 @@ cudaError_t record(cudaEvent_t ev, cudaStream_t s, bool external) {
 relo_status run_pass(const RansacPass& p, cudaStream_t s, int* launches, cudaEvent_t ev_hyp, cudaEvent_t ev_rounds,
                      bool external = false, const Schedule& sched = Schedule()) {
   int L = 0;
+  if (sched.persistent && p.d_items && p.n > 0) {
+    // one launch (plus the compaction before it and the timeout report after it); the stage
+    // events bracket the compaction + persistent launch (hypotheses) and the report (rounds)
+    RELO_CUDA(launch_compact(p.d_jobs, p.n, p.chunks, s));
+    PersistArgs a{};
+    a.jobs = p.d_jobs;
+    a.n_jobs = p.n;
+    a.total_hyps = p.hyps;
+    a.ctrl = p.d_ctrl;
+    a.items = p.d_items;
+    a.n_items = p.n_items;
+    a.done = p.d_ctrl + 4;
+    a.final_base = p.final_base;
+    a.alive_prefix = p.d_alive_prefix;
+    a.surv_prefix = p.d_surv_prefix;
+    a.timeout_ns = g_persist_timeout_ns.load();
+    RELO_CUDA(launch_persistent(a, p.ctrl_words, s));
+    RELO_CUDA(record(ev_hyp, s, external));
+    RELO_CUDA(record(ev_rounds, s, external));
+    *launches += 4;
+    return RELO_OK;
+  }
   if (p.n > 0) {
     RELO_CUDA(launch_compact(p.d_jobs, p.n, p.chunks, s));
     RELO_CUDA(launch_hypotheses(p.d_jobs, p.n, p.hyps, p.d_counter, s, sched));
@@ -275,7 +362,8 @@ relo_status run_pass(const RansacPass& p, cudaStream_t s, int* launches, cudaEve
   return RELO_OK;
 }
 
-int pass_launches(const RansacPass& p) {
+int pass_launches(const RansacPass& p, const Schedule& sched = Schedule()) {
+  if (sched.persistent && p.d_items && p.n > 0) return 4;
   int L = p.n > 0 ? 5 : 0;
   for (int r = 0; r < p.R; ++r)
     if (p.tot_alive[r] > 0) L += 5;
@@ -688,6 +776,11 @@ relo_status relo_set_allocator(relo_alloc_fn alloc, relo_free_fn free_fn, void* 
 }
 
 void relo_debug_conv_path(int32_t use_tcgen05) { relo::g_conv_tcgen05.store(use_tcgen05 != 0); }
+
+void relo_debug_persistent_stall(int32_t stall, int32_t timeout_ms) {
+  relo::g_persist_stall.store(stall != 0);
+  relo::g_persist_timeout_ns.store(timeout_ms > 0 ? (unsigned long long)timeout_ms * 1000000ull : 2000000000ull);
+}
 
 void relo_debug_conv_stall(int32_t tile, int32_t timeout_ms) {
   relo::g_conv_stall_tile.store(tile);
@@ -1839,6 +1932,9 @@ struct relo_batch {
   bool timing = false;
   cudaEvent_t ev[kStages + 1] = {};
   Schedule sched;  // launch schedule (relo_batch_set_schedule / relo_batch_autotune)
+  // the persistent schedule's item lists, uploaded the first time that schedule is chosen
+  std::vector<PItem> items_L, items_F;
+  bool items_uploaded = false;
   // per attempt: its query images and forest leaves inside the workspace (for inspection)
   std::vector<uint16_t*> a_depth, a_leaves;
   std::vector<uint32_t*> a_rgba;
@@ -1884,6 +1980,7 @@ struct HostJobs {
   std::vector<RayJob> query, verify_L, verify_F;
   std::vector<ForestJob> forest;
   std::vector<RansacJob> ransac_L, ransac_F;
+  std::vector<PItem> items_L, items_F;
   std::vector<int32_t> alive_L, surv_L, alive_F, surv_F, kind;
 };
 
@@ -1934,6 +2031,22 @@ void layout_batch(const relo_attempt* at, int n, const relo_ransac_params& p, ch
   b.passL.d_surv_prefix = c.take<int32_t>((size_t)std::max(RL, 1) * (nL + 1));
   b.passF.d_alive_prefix = c.take<int32_t>((size_t)std::max(RF, 1) * (nF + 1));
   b.passF.d_surv_prefix = c.take<int32_t>((size_t)std::max(RF, 1) * (nF + 1));
+  // the persistent schedule's items and counters (used when the schedule asks for it)
+  std::vector<PItem> items_L, items_F;
+  {
+    const bool stall = g_persist_stall.load();
+    int nd = 0;
+    build_items(KL, p.batch, stall, items_L, &nd, &b.passL.final_base);
+    b.passL.n_items = (int)items_L.size();
+    b.passL.ctrl_words = 4 + nd;
+    b.passL.d_items = c.take<PItem>(std::max<size_t>(items_L.size(), 1));
+    b.passL.d_ctrl = c.take<int32_t>(b.passL.ctrl_words);
+    build_items(KF, p.batch, stall, items_F, &nd, &b.passF.final_base);
+    b.passF.n_items = (int)items_F.size();
+    b.passF.ctrl_words = 4 + nd;
+    b.passF.d_items = c.take<PItem>(std::max<size_t>(items_F.size(), 1));
+    b.passF.d_ctrl = c.take<int32_t>(b.passF.ctrl_words);
+  }
   // learned images first (contiguous for the batched forward), then the rest
   uint16_t* depth_L = nullptr;
   uint32_t* rgba_L = nullptr;
@@ -1973,6 +2086,8 @@ void layout_batch(const relo_attempt* at, int n, const relo_ransac_params& p, ch
     ca.depth_lr = c.take<uint16_t>((size_t)nL * cells);
   }
   h = HostJobs{};
+  h.items_L = std::move(items_L);
+  h.items_F = std::move(items_F);
   b.a_depth.assign(n, nullptr);
   b.a_rgba.assign(n, nullptr);
   b.a_leaves.assign(n, nullptr);
@@ -2201,6 +2316,8 @@ relo_status relo_batch_prepare(const relo_attempt* at, int32_t n, const relo_ran
     layout_batch(at, n, *p, nullptr, &bytes, probe, h);
   }
   if (bytes > ws_bytes) return fail(RELO_EINVAL, "workspace too small");
+  int grid = 0;
+  RELO_CUDA(persistent_grid(&grid));  // device set-up of the persistent schedule, outside any capture
   relo_batch* b = new relo_batch();
   HostJobs h;
   layout_batch(at, n, *p, (char*)ws, &bytes, *b, h);
@@ -2215,6 +2332,8 @@ relo_status relo_batch_prepare(const relo_attempt* at, int32_t n, const relo_ran
   if (e == cudaSuccess) e = upload(b->passF.d_alive_prefix, h.alive_F);
   if (e == cudaSuccess) e = upload(b->passF.d_surv_prefix, h.surv_F);
   if (e == cudaSuccess) e = upload(b->d_kind, h.kind);
+  b->items_L = std::move(h.items_L);
+  b->items_F = std::move(h.items_F);
   if (e != cudaSuccess) {
     delete b;
     return cuda_fail(e, "batch descriptors");
@@ -2273,8 +2392,8 @@ relo_status relo_batch_attempt_images(const relo_batch* b, int32_t k, const uint
 int32_t relo_batch_launch_count(const relo_batch* b) {
   if (!b) return 0;
   int L = 2 + 1;  // result init + query raycast, merge
-  if (b->nL > 0) L += 1 + kRegLayers + 1 + 2 + pass_launches(b->passL);
-  if (b->nF > 0) L += 1 + 2 + pass_launches(b->passF);
+  if (b->nL > 0) L += 1 + kRegLayers + 1 + 2 + pass_launches(b->passL, b->sched);
+  if (b->nF > 0) L += 1 + 2 + pass_launches(b->passF, b->sched);
   return L;
 }
 
@@ -2301,6 +2420,18 @@ const char* relo_batch_stage_name(int32_t k) { return (k >= 0 && k < kStages) ? 
 
 // ---- launch schedules and the autotuner ------------------------------------------------------
 
+namespace {
+// The persistent schedule's items go to the device the first time a batch may use them.
+relo_status ensure_items(relo_batch* b) {
+  if (b->items_uploaded) return RELO_OK;
+  cudaError_t e = upload(b->passL.d_items, b->items_L);
+  if (e == cudaSuccess) e = upload(b->passF.d_items, b->items_F);
+  if (e != cudaSuccess) return cuda_fail(e, "persistent schedule items");
+  b->items_uploaded = true;
+  return RELO_OK;
+}
+}  // namespace
+
 relo_status relo_batch_get_schedule(const relo_batch* b, relo_schedule* out) {
   if (!b || !out) return fail(RELO_EINVAL, "null argument");
   out->ray_warp_width = 1 << b->sched.ray_warp_log2w;
@@ -2308,6 +2439,7 @@ relo_status relo_batch_get_schedule(const relo_batch* b, relo_schedule* out) {
   out->forest_tiles = b->sched.forest_tiles;
   out->search_ctas_per_sm = b->sched.search_ctas_per_sm;
   out->refit_per = b->sched.refit_per;
+  out->persistent = b->sched.persistent;
   return RELO_OK;
 }
 
@@ -2321,6 +2453,12 @@ relo_status relo_batch_set_schedule(relo_batch* b, const relo_schedule* in) {
   if (in->forest_tiles != 0 && in->forest_tiles != 1) return fail(RELO_EINVAL, "forest_tiles must be 0 or 1");
   if (in->search_ctas_per_sm < 0 || in->search_ctas_per_sm > 64) return fail(RELO_EINVAL, "search_ctas_per_sm outside [0, 64]");
   if (in->refit_per < 0 || in->refit_per > 32) return fail(RELO_EINVAL, "refit_per outside [0, 32]");
+  if (in->persistent != 0 && in->persistent != 1) return fail(RELO_EINVAL, "persistent must be 0 or 1");
+  s.persistent = in->persistent;
+  if (s.persistent) {
+    const relo_status st = ensure_items(b);
+    if (st) return st;
+  }
   s.forest_threads = in->forest_threads;
   s.forest_tiles = in->forest_tiles;
   s.search_ctas_per_sm = in->search_ctas_per_sm;
@@ -2340,7 +2478,9 @@ relo_status relo_batch_autotune(relo_batch* b, int32_t repeats, relo_schedule* c
   if (!b || repeats < 1 || repeats > 100) return fail(RELO_EINVAL, "need a batch and repeats in [1, 100]");
   cudaStream_t s = (cudaStream_t)stream;
   const bool had_timing = b->timing;
-  relo_status st = relo_batch_enable_timing(b, 1);
+  relo_status st = ensure_items(b);
+  if (st) return st;
+  st = relo_batch_enable_timing(b, 1);
   if (st) return st;
   struct Knob {
     int Schedule::*field;
@@ -2353,6 +2493,7 @@ relo_status relo_batch_autotune(relo_batch* b, int32_t repeats, relo_schedule* c
       {&Schedule::forest_tiles, {0, 1}, {5}},
       {&Schedule::search_ctas_per_sm, {0, 1, 2, 3}, {2, 6}},
       {&Schedule::refit_per, {0, 1, 4, 16}, {3, 7}},
+      {&Schedule::persistent, {0, 1}, {2, 3, 6, 7}},
   };
   Schedule best = b->sched;
   for (const Knob& k : knobs) {

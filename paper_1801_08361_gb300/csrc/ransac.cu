@@ -357,7 +357,7 @@ __device__ __forceinline__ int first_passing(const RansacJob& job, int h, int n_
 #define RELO_SEARCH_MIN_BLOCKS 4
 #endif
 // The search of hypothesis gw (flattened over the jobs) by one warp.
-__device__ __forceinline__ void search_one(const RansacJob* __restrict__ jobs, int n_jobs, int gw, int lane) {
+__device__ __forceinline__ int search_one(const RansacJob* __restrict__ jobs, int n_jobs, int gw, int lane) {
   int lo = 0, hi = n_jobs - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -366,7 +366,7 @@ __device__ __forceinline__ void search_one(const RansacJob* __restrict__ jobs, i
   }
   const RansacJob& job = jobs[lo];
   const int h = gw - job.hyp_begin;
-  if (h >= job.K || job_skipped(job.skip)) return;
+  if (h >= job.K || job_skipped(job.skip)) return lo;
   const int n_valid = *job.n_valid;
   const float rig = (float)job.rigidity, area = (float)job.min_area;
   // the area test |cross| >= area with its guard band, on squares (both sides non-negative)
@@ -395,6 +395,7 @@ __device__ __forceinline__ void search_one(const RansacJob* __restrict__ jobs, i
     job.hyp_ok[h] = found != INT_MAX;
     job.tries[h] = found != INT_MAX ? found : job.max_tries;
   }
+  return lo;
 }
 
 // Persistent: hypotheses need from one try to max_tries, so each warp takes its next hypothesis
@@ -412,18 +413,8 @@ __global__ void __launch_bounds__(kSearchWarps * 32, RELO_SEARCH_MIN_BLOCKS)
 }
 
 // FP64 Kabsch (Horn) of each hypothesis's kept try; also initialises the round state.
-__global__ void __launch_bounds__(128) fit_kernel(const RansacJob* __restrict__ jobs, int n_jobs, int total) {
-  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= total) return;
-  int lo = 0, hi = n_jobs - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (jobs[mid].hyp_begin <= gid) lo = mid;
-    else hi = mid - 1;
-  }
-  const RansacJob& job = jobs[lo];
-  const int h = gid - job.hyp_begin;
-  if (h >= job.K || job_skipped(job.skip)) return;
+// FP64 Kabsch of hypothesis h's kept try; also initialises its round state.
+__device__ __forceinline__ void fit_one(const RansacJob& job, int h) {
   double* pose = job.poses + 12 * (size_t)h;
   const bool ok = job.hyp_ok[h] != 0;
   if (ok) {
@@ -452,6 +443,21 @@ __global__ void __launch_bounds__(128) fit_kernel(const RansacJob* __restrict__ 
   job.energy[h] = ok ? 0.0 : (double)INFINITY;
   job.alive_a[h] = h;
   job.inliers[h] = 0;
+}
+
+__global__ void __launch_bounds__(128) fit_kernel(const RansacJob* __restrict__ jobs, int n_jobs, int total) {
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= total) return;
+  int lo = 0, hi = n_jobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].hyp_begin <= gid) lo = mid;
+    else hi = mid - 1;
+  }
+  const RansacJob& job = jobs[lo];
+  const int h = gid - job.hyp_begin;
+  if (h >= job.K || job_skipped(job.skip)) return;
+  fit_one(job, h);
 }
 
 cudaError_t launch_hypotheses(const RansacJob* jobs, int n_jobs, int total_hyps, int32_t* counter, cudaStream_t s,
@@ -495,8 +501,8 @@ __device__ __forceinline__ int2 tree_modes(const RansacJob& job, int idx, const 
 
 // Draw round r's B pixels (positions in the valid table), one CTA per job, and write each drawn
 // pixel's record (camera point and where its modes are), which every hypothesis then reads.
-__global__ void draw_kernel(const RansacJob* __restrict__ jobs, const int32_t* __restrict__ alive_prefix, int r) {
-  const int jid = blockIdx.x;
+__device__ __forceinline__ void draw_block(const RansacJob* __restrict__ jobs, const int32_t* __restrict__ alive_prefix,
+                                           int r, int jid) {
   if (alive_prefix[jid + 1] - alive_prefix[jid] == 0) return;
   const RansacJob& job = jobs[jid];
   if (job_skipped(job.skip)) return;
@@ -518,6 +524,10 @@ __global__ void draw_kernel(const RansacJob* __restrict__ jobs, const int32_t* _
       rec[1 + t / 2] = make_int4(a.x, a.y, b.x, b.y);
     }
   }
+}
+
+__global__ void draw_kernel(const RansacJob* __restrict__ jobs, const int32_t* __restrict__ alive_prefix, int r) {
+  draw_block(jobs, alive_prefix, r, blockIdx.x);
 }
 
 // A pixel's modes, staged by its warp in shared memory: the warp copies every mode of the pixel's
@@ -606,22 +616,20 @@ __device__ __forceinline__ float3 record_point(const int4* __restrict__ rec) {
 // warp order, so the result does not depend on scheduling.
 constexpr int kRoundWarps = 8;
 
-// Energies of round r: grid (hypothesis chunks, jobs).
-__global__ void __launch_bounds__(kRoundWarps * 32) energy_kernel(const RansacJob* __restrict__ jobs,
-                                                                  const int32_t* __restrict__ alive_prefix, int r) {
-  const int jid = blockIdx.y;
+// Energies of round r for hypotheses chunk * 32 .. + 31 of job jid.
+__device__ __forceinline__ void energy_block(const RansacJob* __restrict__ jobs, const int32_t* __restrict__ alive_prefix,
+                                             int r, int chunk, int jid, ModeSlot* slots, float (*part)[32]) {
   const int n_alive = alive_prefix[jid + 1] - alive_prefix[jid];
-  if ((int)blockIdx.x * 32 >= n_alive) return;
+  if (chunk * 32 >= n_alive) return;
   const RansacJob& job = jobs[jid];
   if (job_skipped(job.skip) || *job.n_valid == 0) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int a = (int)blockIdx.x * 32 + lane;
+  const int a = chunk * 32 + lane;
   const int h = a < n_alive ? alive_in(job, r)[a] : 0;
   const bool valid = a < n_alive && job.hyp_ok[h];
   const PoseF P = pose_to_float(job.poses + 12 * (size_t)h);
   float sum = 0.f;
   const int4* recs = job.pix + (size_t)r * job.B * job.hs;
-  __shared__ ModeSlot slots[kRoundWarps];
   for (int i = warp; i < job.B; i += kRoundWarps) {
     const int4* rec = recs + (size_t)i * job.hs;
     __syncwarp();  // the slot's previous pixel is scored
@@ -629,7 +637,6 @@ __global__ void __launch_bounds__(kRoundWarps * 32) energy_kernel(const RansacJo
     const float best = record_best(job, rec, slots[warp], n_staged, apply(P, record_point(rec)), nullptr);
     sum += fminf(kLogEps, -best);
   }
-  __shared__ float part[kRoundWarps][32];
   part[warp][lane] = sum;
   __syncthreads();
   if (warp == 0 && valid) {
@@ -639,16 +646,22 @@ __global__ void __launch_bounds__(kRoundWarps * 32) energy_kernel(const RansacJo
     job.energy[h] += (double)e;
   }
 }
+
+// Energies of round r: grid (hypothesis chunks, jobs).
+__global__ void __launch_bounds__(kRoundWarps * 32) energy_kernel(const RansacJob* __restrict__ jobs,
+                                                                  const int32_t* __restrict__ alive_prefix, int r) {
+  __shared__ ModeSlot slots[kRoundWarps];
+  __shared__ float part[kRoundWarps][32];
+  energy_block(jobs, alive_prefix, r, blockIdx.x, blockIdx.y, slots, part);
+}
 __device__ __forceinline__ unsigned long long order_key(double e) {
   unsigned long long b = (unsigned long long)__double_as_longlong(e);
   return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
 
 // Halving: CTA per job, bitonic sort of (energy key, index) ascending; keep ceil(n/2).
-__global__ void __launch_bounds__(1024) select_kernel(const RansacJob* __restrict__ jobs,
-                                                      const int32_t* __restrict__ alive_prefix, int r) {
-  extern __shared__ unsigned long long skey[];
-  const int jid = blockIdx.x;
+__device__ __forceinline__ void select_block(const RansacJob* __restrict__ jobs, const int32_t* __restrict__ alive_prefix,
+                                             int r, int jid, unsigned long long* skey) {
   const int n = alive_prefix[jid + 1] - alive_prefix[jid];
   if (n == 0) return;
   const RansacJob& job = jobs[jid];
@@ -693,6 +706,12 @@ __global__ void __launch_bounds__(1024) select_kernel(const RansacJob* __restric
   for (int i = threadIdx.x; i < keep; i += blockDim.x) out[i] = sidx[i];
 }
 
+__global__ void __launch_bounds__(1024) select_kernel(const RansacJob* __restrict__ jobs,
+                                                      const int32_t* __restrict__ alive_prefix, int r) {
+  extern __shared__ unsigned long long skey[];
+  select_block(jobs, alive_prefix, r, blockIdx.x, skey);
+}
+
 // Re-fit sums over all pixels drawn in rounds 0..r: grid (survivor chunks, parts of kRefinePixels
 // pixels, jobs).  Sums are taken about a reference correspondence (the first drawn pixel and its
 // predicted scene point) so one FP32 pass gives well-conditioned centroids and cross-covariance:
@@ -706,17 +725,17 @@ __device__ __forceinline__ void comp_add(float& s, float& e, float x) {
   s = t;
 }
 
-__global__ void __launch_bounds__(kRoundWarps * 32) refine_kernel(const RansacJob* __restrict__ jobs,
-                                                                  const int32_t* __restrict__ surv_prefix, int r) {
-  const int jid = blockIdx.z, part = blockIdx.y;
+__device__ __forceinline__ void refine_block(const RansacJob* __restrict__ jobs, const int32_t* __restrict__ surv_prefix,
+                                             int r, int chunk, int part, int jid, ModeSlot* slots,
+                                             float (*red)[16][32]) {
   const int n_surv = surv_prefix[jid + 1] - surv_prefix[jid];
-  if ((int)blockIdx.x * 32 >= n_surv) return;
+  if (chunk * 32 >= n_surv) return;
   const RansacJob& job = jobs[jid];
   const int n_drawn = (r + 1) * job.B;
   const int p0 = part * kRefinePixels;
   if (p0 >= n_drawn || job_skipped(job.skip) || *job.n_valid == 0) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int a = (int)blockIdx.x * 32 + lane;
+  const int a = chunk * 32 + lane;
   const int h = a < n_surv ? alive_out(job, r)[a] : 0;
   const bool valid = a < n_surv && job.hyp_ok[h];
   const PoseF P = pose_to_float(job.poses + 12 * (size_t)h);
@@ -732,7 +751,6 @@ __global__ void __launch_bounds__(kRoundWarps * 32) refine_kernel(const RansacJo
 #pragma unroll
   for (int q = 0; q < 16; ++q) acc[q] = lo[q] = 0.f;
   const int p1 = min(p0 + kRefinePixels, n_drawn);
-  __shared__ ModeSlot slots[kRoundWarps];
   for (int i = p0 + warp; i < p1; i += kRoundWarps) {
     const int4* rec = job.pix + (size_t)i * job.hs;
     const float3 c = record_point(rec);
@@ -762,31 +780,35 @@ __global__ void __launch_bounds__(kRoundWarps * 32) refine_kernel(const RansacJo
         }
     }
   }
-  // warps w then write sums q = w, w + kRoundWarps: the kRoundWarps partials added in warp order in
-  // FP64, first their high parts, then their low parts (one shared buffer, two passes)
-  __shared__ float red[kRoundWarps][16][32];
-  double tot[(16 + kRoundWarps - 1) / kRoundWarps];
+  // warps w then write sums q = w, w + kRoundWarps: the kRoundWarps partials added in warp order,
+  // compensated as above (first their high parts, then their low parts: one shared buffer, two
+  // passes), kept as a (high, low) pair that the re-fit adds in FP64
+  constexpr int kPer = (16 + kRoundWarps - 1) / kRoundWarps;
+  float sh[kPer], sl[kPer];
 #pragma unroll
-  for (int i = 0; i < (16 + kRoundWarps - 1) / kRoundWarps; ++i) tot[i] = 0.0;
+  for (int i = 0; i < kPer; ++i) sh[i] = sl[i] = 0.f;
 #pragma unroll
   for (int pass = 0; pass < 2; ++pass) {
 #pragma unroll
     for (int q = 0; q < 16; ++q) red[warp][q][lane] = pass ? lo[q] : acc[q];
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < (16 + kRoundWarps - 1) / kRoundWarps; ++i) {
+    for (int i = 0; i < kPer; ++i) {
       const int q = warp + i * kRoundWarps;
       if (q < 16)
 #pragma unroll
-        for (int w = 0; w < kRoundWarps; ++w) tot[i] += (double)red[w][q][lane];
+        for (int w = 0; w < kRoundWarps; ++w) {
+          if (pass == 0) comp_add(sh[i], sl[i], red[w][q][lane]);
+          else sl[i] = __fadd_rn(sl[i], red[w][q][lane]);
+        }
     }
     __syncthreads();
   }
   if (!valid) return;
 #pragma unroll
-  for (int i = 0; i < (16 + kRoundWarps - 1) / kRoundWarps; ++i) {
+  for (int i = 0; i < kPer; ++i) {
     const int q = warp + i * kRoundWarps;
-    if (q < 16) job.refit[((size_t)h * job.refit_parts + part) * 16 + q] = tot[i];
+    if (q < 16) job.refit[((size_t)h * job.refit_parts + part) * 16 + q] = make_float2(sh[i], sl[i]);
   }
   if (part == 0 && warp == 0) {
     float* ref = job.refit_ref + (size_t)h * 8;
@@ -799,26 +821,28 @@ __global__ void __launch_bounds__(kRoundWarps * 32) refine_kernel(const RansacJo
   }
 }
 
+__global__ void __launch_bounds__(kRoundWarps * 32) refine_kernel(const RansacJob* __restrict__ jobs,
+                                                                  const int32_t* __restrict__ surv_prefix, int r) {
+  __shared__ ModeSlot slots[kRoundWarps];
+  __shared__ float red[kRoundWarps][16][32];
+  refine_block(jobs, surv_prefix, r, blockIdx.x, blockIdx.y, blockIdx.z, slots, red);
+}
+
 // Re-fit solve: thread per survivor; the parts' sums are added in order in FP64, then FP64 Horn on
 // the centroids and cross-covariance (>= 3 inliers, else the pose is kept).  CTAs of one warp take
 // `per` survivors each: with few survivors (late rounds) they spread over the SMs, whose FP64 pipes
 // would otherwise run one warp's solves in series.
-__global__ void __launch_bounds__(32) refit_kernel(const RansacJob* __restrict__ jobs, int n_jobs,
-                                                   const int32_t* __restrict__ surv_prefix, int total, int r,
-                                                   int per) {
-  const int gid = blockIdx.x * per + threadIdx.x;
-  if ((int)threadIdx.x >= per || gid >= total) return;
-  const int jid = find_job_by(surv_prefix, n_jobs, gid);
-  const RansacJob& job = jobs[jid];
+// Re-fit of survivor k of job `job` after round r.
+__device__ __forceinline__ void refit_one(const RansacJob& job, int k, int r) {
   if (job_skipped(job.skip)) return;
-  const int h = alive_out(job, r)[gid - surv_prefix[jid]];
+  const int h = alive_out(job, r)[k];
   if (!job.hyp_ok[h] || *job.n_valid == 0) return;
   const int parts = ((r + 1) * job.B + kRefinePixels - 1) / kRefinePixels;
   double f[16];
   for (int q = 0; q < 16; ++q) f[q] = 0.0;
   for (int p = 0; p < parts; ++p) {
-    const double* src = job.refit + ((size_t)h * job.refit_parts + p) * 16;
-    for (int q = 0; q < 16; ++q) f[q] += src[q];
+    const float2* src = job.refit + ((size_t)h * job.refit_parts + p) * 16;
+    for (int q = 0; q < 16; ++q) f[q] += (double)src[q].x + (double)src[q].y;
   }
   job.inliers[h] = (int)f[0];
   const double n = f[0];
@@ -834,6 +858,15 @@ __global__ void __launch_bounds__(32) refit_kernel(const RansacJob* __restrict__
   for (int p = 0; p < 3; ++p)
     for (int q = 0; q < 3; ++q) S[3 * p + q] = f[7 + 3 * p + q] - n * mc[p] * mw[q];
   horn_pose(S, cb, wb, job.poses + 12 * (size_t)h);
+}
+
+__global__ void __launch_bounds__(32) refit_kernel(const RansacJob* __restrict__ jobs, int n_jobs,
+                                                   const int32_t* __restrict__ surv_prefix, int total, int r,
+                                                   int per) {
+  const int gid = blockIdx.x * per + threadIdx.x;
+  if ((int)threadIdx.x >= per || gid >= total) return;
+  const int jid = find_job_by(surv_prefix, n_jobs, gid);
+  refit_one(jobs[jid], gid - surv_prefix[jid], r);
 }
 
 cudaError_t launch_round(const RansacJob* jobs, int n_jobs, int round, const int32_t* alive_prefix_dev,
@@ -859,10 +892,7 @@ cudaError_t launch_round(const RansacJob* jobs, int n_jobs, int round, const int
 }
 
 // Final hypothesis -> result (one thread per job).
-__global__ void finalise_kernel(const RansacJob* __restrict__ jobs, int n_jobs) {
-  const int jid = blockIdx.x * blockDim.x + threadIdx.x;
-  if (jid >= n_jobs) return;
-  const RansacJob& job = jobs[jid];
+__device__ __forceinline__ void finalise_one(const RansacJob& job) {
   if (job_skipped(job.skip)) return;
   const int32_t* fin = (job.n_rounds & 1) ? job.alive_b : job.alive_a;
   const int h = fin[0];
@@ -902,6 +932,170 @@ __global__ void finalise_kernel(const RansacJob* __restrict__ jobs, int n_jobs) 
         res->rel_a_b[4 * i + q] = acc;
       }
   }
+}
+
+__global__ void finalise_kernel(const RansacJob* __restrict__ jobs, int n_jobs) {
+  const int jid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (jid >= n_jobs) return;
+  finalise_one(jobs[jid]);
+}
+
+// ---------------------------------------------------------------------------------------------
+// One persistent launch for a pass's hypotheses, rounds and results (schedule option).  Warps
+// first search hypotheses taken from a counter (as search_kernel); a CTA whose warps find the
+// search queue empty then takes items -- (fit | round stage | finalise) x job x chunk -- from a
+// host-built list in dependency order.  Before an item runs, one thread waits until the counter of
+// the item it depends on (same job) reaches the number of that item's chunks; after it, the CTA
+// adds one to its own counter.  An item depends only on items earlier in the list, which threads
+// that have started took, so the waits always end -- unless a counter never reaches its target:
+// the wait is bounded in time, and one that runs out raises an abort flag that stops every CTA
+// (persist_timeout_kernel then reports RELO_ETIMEOUT for the jobs not finalised).  Each item runs
+// the same device code as the per-stage kernels, so results are bit-identical.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int ld_acquire_gpu(const int32_t* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+constexpr int kPersistThreads = kRoundWarps * 32;
+static_assert(kPersistThreads == kPersistThreadsHost, "the host's item chunks match the CTA size");
+constexpr size_t kPersistSmem = 4096 * (sizeof(unsigned long long) + sizeof(int));  // the largest sort
+static_assert(kRoundWarps * sizeof(ModeSlot) + sizeof(float) * kRoundWarps * 16 * 32 <= kPersistSmem,
+              "round stages fit the persistent kernel's shared memory");
+
+__global__ void __launch_bounds__(kPersistThreads, 2) persistent_kernel(PersistArgs a) {
+  extern __shared__ __align__(16) unsigned char psm[];
+  __shared__ int s_item, s_go;
+  const int lane = threadIdx.x & 31;
+  volatile int32_t* abort = a.ctrl + 2;
+  // phase 1: hypothesis search, one warp per hypothesis
+  for (;;) {
+    int gw = 0;
+    if (lane == 0) gw = *abort ? a.total_hyps : atomicAdd(a.ctrl + 0, 1);
+    gw = __shfl_sync(0xffffffffu, gw, 0);
+    if (gw >= a.total_hyps) break;
+    const int jid = search_one(a.jobs, a.n_jobs, gw, lane);
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) atomicAdd(a.done + jid, 1);
+  }
+  __syncthreads();
+  // phase 2: CTA items
+  ModeSlot* slots = reinterpret_cast<ModeSlot*>(psm);
+  float(*part)[32] = reinterpret_cast<float(*)[32]>(psm + kRoundWarps * sizeof(ModeSlot));
+  float(*red)[16][32] = reinterpret_cast<float(*)[16][32]>(psm + kRoundWarps * sizeof(ModeSlot));
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int it = atomicAdd(a.ctrl + 1, 1);
+      int go = it < a.n_items && !*abort;
+      if (go) {
+        const PItem pi = a.items[it];
+        const unsigned long long t0 = global_ns();
+        for (unsigned n = 1; ld_acquire_gpu(a.done + pi.dep) < pi.need; ++n) {
+          if ((n & 63) == 0) {
+            if (*abort) {
+              go = 0;
+              break;
+            }
+            if (global_ns() - t0 > a.timeout_ns) {
+              atomicExch(a.ctrl + 2, 1);
+              go = 0;
+              break;
+            }
+          }
+        }
+      }
+      s_item = it;
+      s_go = go;
+    }
+    __syncthreads();
+    if (!s_go) break;
+    __threadfence();
+    const PItem it = a.items[s_item];
+    const RansacJob& job = a.jobs[it.job];
+    const int np = a.n_jobs + 1;
+    switch (it.kind) {
+      case kItemFit: {
+        const int h = it.sub * kPersistThreads + threadIdx.x;
+        if (h < job.K && !job_skipped(job.skip)) fit_one(job, h);
+        break;
+      }
+      case kItemDraw:
+        draw_block(a.jobs, a.alive_prefix + (size_t)it.round * np, it.round, it.job);
+        break;
+      case kItemEnergy:
+        energy_block(a.jobs, a.alive_prefix + (size_t)it.round * np, it.round, it.sub, it.job, slots, part);
+        break;
+      case kItemSelect:
+        select_block(a.jobs, a.alive_prefix + (size_t)it.round * np, it.round, it.job,
+                     reinterpret_cast<unsigned long long*>(psm));
+        break;
+      case kItemRefine:
+        refine_block(a.jobs, a.surv_prefix + (size_t)it.round * np, it.round, it.sub, it.part, it.job, slots, red);
+        break;
+      case kItemRefit: {
+        const int32_t* sp = a.surv_prefix + (size_t)it.round * np;
+        const int k = it.sub * kPersistThreads + threadIdx.x;
+        if (k < sp[it.job + 1] - sp[it.job]) refit_one(job, k, it.round);
+        break;
+      }
+      default:
+        if (threadIdx.x == 0) finalise_one(job);
+        break;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(a.done + it.done, 1);
+  }
+}
+
+// After an aborted persistent launch: the jobs it did not finalise report RELO_ETIMEOUT.
+__global__ void persist_timeout_kernel(const RansacJob* __restrict__ jobs, int n_jobs, const int32_t* __restrict__ ctrl,
+                                       const int32_t* __restrict__ final_done) {
+  const int jid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (jid >= n_jobs || !ctrl[2]) return;
+  const RansacJob& job = jobs[jid];
+  if (job_skipped(job.skip) || final_done[jid] != 0) return;
+  job.result->status = RELO_ETIMEOUT;
+  job.result->verified = 0;
+}
+
+// The persistent kernel's CTAs: as many as are resident on the device at once (its shared-memory
+// limit is raised here, once per device; batches call this when they are prepared, so that a
+// launch inside a stream capture finds it done).
+cudaError_t persistent_grid(int* grid) {
+  static PerDevice resident;  // resident persistent CTAs per SM on each device
+  int sms = 0, per_sm = 0;
+  cudaError_t e = device_sms(&sms);
+  if (e == cudaSuccess)
+    e = per_device(resident, &per_sm, [](int, int* v) {
+      cudaError_t r = cudaFuncSetAttribute(persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kPersistSmem);
+      if (r == cudaSuccess)
+        r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(v, persistent_kernel, kPersistThreads, kPersistSmem);
+      *v = std::max(1, *v);
+      return r;
+    });
+  *grid = sms * per_sm;
+  return e;
+}
+
+cudaError_t launch_persistent(const PersistArgs& a, int ctrl_words, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(a.ctrl, 0, (size_t)ctrl_words * sizeof(int32_t), s);
+  if (e != cudaSuccess) return e;
+  int grid = 0;
+  e = persistent_grid(&grid);
+  if (e != cudaSuccess) return e;
+  persistent_kernel<<<grid, kPersistThreads, kPersistSmem, s>>>(a);
+  persist_timeout_kernel<<<(a.n_jobs + 127) / 128, 128, 0, s>>>(a.jobs, a.n_jobs, a.ctrl, a.done + a.final_base);
+  return cudaGetLastError();
 }
 
 // Verification decision (Sec. 3.3.1) from the counts the compare raycast accumulated:

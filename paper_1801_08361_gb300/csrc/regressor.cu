@@ -4,11 +4,12 @@
 //
 // The paper relocalises with a forest (Sec. 3.3 (b)); this network is the workload's alternative
 // relocaliser for a scene, trained online on renders of the scene's own voxel map.  Readings
-// (identical in the CPU oracle): 4 input channels (depth in metres, RGB / 255), eight 3x3
-// convolutions with zero padding, 64 channels, strides 2, 2, 2, 1, 1, 1, 1, 1, ReLU after
+// (identical in the CPU oracle): 4 input channels ((depth m - 3) / 2, (RGB / 255 - 1/2) x 4), eight
+// 3x3 convolutions with zero padding, 64 channels, strides 2, 2, 2, 1, 1, 1, 1, 1, ReLU after
 // layers 1-7, 4 outputs per 8 x 8-pixel cell (scene coordinate - origin, log-variance s); the
 // target of a cell is the scene coordinate of its centre pixel; loss = mean over scored cells of
-// 1/2 |y - y_hat|^2 exp(-s) + 3/2 s; Adam (0.9, 0.999, 1e-8).
+// rho(e) + 1/2 e^2 exp(-s) + 3/2 s with e = |y - y_hat|, rho(e) = sqrt(e^2 + 1e-6), the error in the
+// variance term held fixed for the gradient; Adam (0.9, 0.999, 1e-8).
 //
 // Layout: activations NHWC in BF16 (channels contiguous); layer 1's input is padded to 16
 // channels and the head's output to 8 (its gradient to 16) so every contraction is a multiple
@@ -451,18 +452,19 @@ cudaError_t launch_pack(const float* w, int cin, int cout, int cin_pad, int cout
 // ---------------------------------------------------------------------------------------------
 // Input, targets, loss, Adam
 // ---------------------------------------------------------------------------------------------
-// [n][H][W] depth + colour -> [n][H][W][16] BF16: depth in metres, R, G, B / 255, zeros.
+// [n][H][W] depth + colour -> [n][H][W][16] BF16: (depth m - 3) / 2, (R, G, B / 255 - 1/2) x 4, zeros.
 __global__ void input_kernel(const uint16_t* __restrict__ depth, const uint32_t* __restrict__ rgba, long n_pix,
                              bf16* __restrict__ x) {
   const long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n_pix) return;
-  const float d = (float)depth[p] * 0.001f;
+  // centred and scaled: (depth m - 3) / 2, (colour / 255 - 1/2) x 4
+  const float d = ((float)depth[p] * 0.001f - 3.0f) * 0.5f;
   const uint32_t c = rgba[p];
   __align__(16) bf16 v[16];
   v[0] = __float2bfloat16(d);
-  v[1] = __float2bfloat16((float)(c & 0xFF) / 255.f);
-  v[2] = __float2bfloat16((float)((c >> 8) & 0xFF) / 255.f);
-  v[3] = __float2bfloat16((float)((c >> 16) & 0xFF) / 255.f);
+  v[1] = __float2bfloat16(((float)(c & 0xFF) / 255.f - 0.5f) * 4.0f);
+  v[2] = __float2bfloat16(((float)((c >> 8) & 0xFF) / 255.f - 0.5f) * 4.0f);
+  v[3] = __float2bfloat16(((float)((c >> 16) & 0xFF) / 255.f - 0.5f) * 4.0f);
   for (int k = 4; k < 16; ++k) v[k] = __float2bfloat16(0.f);
   uint4* dst = reinterpret_cast<uint4*>(x + (size_t)p * 16);
   dst[0] = *reinterpret_cast<uint4*>(&v[0]);
@@ -530,12 +532,15 @@ __global__ void __launch_bounds__(1024) loss_kernel(const float* __restrict__ ou
     __align__(16) bf16 gv[16];
     for (int k = 0; k < 16; ++k) gv[k] = __float2bfloat16(0.f);
     if (y.w > 0.5f) {
+      // rho(e) + 1/2 e^2 exp(-s) + 3/2 s, rho(e) = sqrt(e^2 + 1e-6): the coordinates follow d rho,
+      // s the NLL's derivative with the error held fixed
       const float e0 = o[0] - y.x, e1 = o[1] - y.y, e2 = o[2] - y.z, s = o[3];
-      const float sq = e0 * e0 + e1 * e1 + e2 * e2, es = expf(-s);
-      acc += 0.5f * sq * es + 1.5f * s;
-      gv[0] = __float2bfloat16(e0 * es * inv);
-      gv[1] = __float2bfloat16(e1 * es * inv);
-      gv[2] = __float2bfloat16(e2 * es * inv);
+      const float sq = e0 * e0 + e1 * e1 + e2 * e2, es = expf(-s), rho = sqrtf(sq + 1e-6f);
+      acc += rho + 0.5f * sq * es + 1.5f * s;
+      const float gc = inv / rho;
+      gv[0] = __float2bfloat16(e0 * gc);
+      gv[1] = __float2bfloat16(e1 * gc);
+      gv[2] = __float2bfloat16(e2 * gc);
       gv[3] = __float2bfloat16((-0.5f * sq * es + 1.5f) * inv);
     }
     uint4* dst = reinterpret_cast<uint4*>(grad + (size_t)i * 16);

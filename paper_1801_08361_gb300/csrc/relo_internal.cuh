@@ -356,8 +356,9 @@ struct RansacJob {
   int32_t* alive_b;            // [K]
   int32_t* drawn;              // [n_rounds * B] positions in the valid-pixel table
   int32_t* inliers;            // [K]
-  double* refit;               // [K][refit_parts][16] per-survivor inlier sums, one block per part of
-                               // kRefinePixels drawn pixels (summed in order by the FP64 re-fit)
+  float2* refit;               // [K][refit_parts][16] per-survivor inlier sums as compensated (high,
+                               // low) FP32 pairs, one block per part of kRefinePixels drawn pixels
+                               // (summed in order by the FP64 re-fit)
   float* refit_ref;            // [K][8] reference correspondence of those sums: c_ref (3), w_ref (3)
   int4* pix;                   // [n_rounds * B][hs] drawn pixels: camera point (FP32 bits), then
                                // (first mode, mode count) of the pixel's leaf in each tree, two per word
@@ -405,6 +406,7 @@ struct Schedule {
   int forest_tiles = 0;      // forest: 0 = each CTA takes consecutive pixels, 1 = 32 x 8 pixel tiles
   int search_ctas_per_sm = 0;  // hypothesis search: persistent CTAs per SM (0: occupancy maximum)
   int refit_per = 0;         // re-fit: survivors per one-warp CTA (0: spread over twice the SM count)
+  int persistent = 0;        // RANSAC of a batch: 0 = one launch per stage, 1 = one persistent launch
 };
 // Forest slots a job of W x H pixels takes (a multiple of 256 that also holds its 32 x 8 tiles).
 inline int64_t forest_slots(int W, int H) {
@@ -444,6 +446,31 @@ cudaError_t launch_round(const RansacJob* jobs, int n_jobs, int round, const int
                          int total_alive, int max_alive, const int32_t* surv_prefix_dev, int total_surv, int max_surv,
                          int B, cudaStream_t s, const Schedule& sched = Schedule());
 cudaError_t launch_finalise(const RansacJob* jobs, int n_jobs, cudaStream_t s);
+
+// One persistent launch for a pass's search, fit, rounds and finalise (ransac.cu): items in
+// dependency order, per-(stage, job) completion counters, bounded waits.
+enum PItemKind { kItemFit = 0, kItemDraw, kItemEnergy, kItemSelect, kItemRefine, kItemRefit, kItemFinal };
+constexpr int kPersistThreadsHost = 256;  // threads of a persistent CTA (fit and re-fit chunk sizes)
+struct PItem {
+  int32_t kind, job, sub, part, round;
+  int32_t dep, need;  // wait until done[dep] >= need
+  int32_t done;       // then add one to done[done]
+};
+struct PersistArgs {
+  const RansacJob* jobs;
+  int n_jobs, total_hyps;
+  int32_t* ctrl;                  // [0] search counter, [1] item counter, [2] abort flag
+  const PItem* items;
+  int n_items;
+  int32_t* done;                  // completion counters; done[j] = job j's searched hypotheses
+  int final_base;                 // done[final_base + j] = job j finalised
+  const int32_t* alive_prefix;    // [rounds][n_jobs + 1], as launch_round
+  const int32_t* surv_prefix;
+  unsigned long long timeout_ns;
+};
+// ctrl_words: words zeroed from ctrl (ctrl[0..2] and the done counters that follow them)
+cudaError_t launch_persistent(const PersistArgs& a, int ctrl_words, cudaStream_t s);
+cudaError_t persistent_grid(int* grid);
 
 
 // Training

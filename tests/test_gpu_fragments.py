@@ -159,3 +159,24 @@ def test_verified_poses_match_the_fragment_transforms(pairs, batch_run):
     assert covered >= 10
     assert ok_cov >= 0.5 * covered
     assert wrong_verified <= max(1, verified // 4)
+
+
+def test_persistent_schedule_equals_stage_launches(pairs, batch_run):
+    """The RANSAC of the 56 attempts in one persistent launch (schedule persistent = 1: the CTAs take
+    every attempt's search, fits, rounds and finalisation from a dependency-ordered list, waiting on
+    per-attempt counters) gives the per-stage launches' results bit for bit, eagerly and from a
+    captured graph, with fewer launches."""
+    items, _ = pairs
+    staged, _, want = batch_run
+    bt, _ = _batch(items)
+    bt.set_schedule(persistent=1)
+    assert bt.launch_count < staged.launch_count
+    res = torch.zeros(len(items) * B.RESULT_BYTES, dtype=torch.uint8, device=DEV)
+    bt.run(res)
+    torch.cuda.synchronize()
+    assert np.array_equal(res.cpu().numpy(), want)
+    res.zero_()
+    bt.capture(res)
+    bt.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(res.cpu().numpy(), want)
