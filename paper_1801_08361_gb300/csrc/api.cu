@@ -1476,11 +1476,11 @@ relo_status reg_forward(relo_regressor* r, const RegBuffers& b, const uint16_t* 
   RELO_CUDA(launch_input(depth, (const uint32_t*)rgba, (long)n * H * W, b.x, s));
   RELO_CUDA(cudaMemsetAsync(r->d_status, 0, sizeof(int32_t), s));
   for (int l = 0; l < kRegLayers; ++l) {
-    if (kRegCinPad[l] == 64 && kRegCoutPad[l] == 64 && g_conv_tcgen05.load()) {
-      // the 64 -> 64-channel layers on the tcgen05 tensor cores (TMA-fed implicit GEMM)
-      RELO_CUDA(launch_conv_tc(b.act[l], n, Hs[l], Ws[l], r->d_wk[l], r->d_bias[l], b.act[l + 1], Hs[l + 1],
-                               Ws[l + 1], kRegStride[l], 1, 1, r->d_status, r->n_sms, s, g_conv_timeout_ns.load(),
-                               g_conv_stall_tile.load()));
+    if (kRegCoutPad[l] == 64 && g_conv_tcgen05.load()) {
+      // every layer but the head on the tcgen05 tensor cores (TMA-fed implicit GEMM)
+      RELO_CUDA(launch_conv_tc(kRegCinPad[l], l == 0 ? b.x : b.act[l], n, Hs[l], Ws[l], r->d_wk[l], r->d_bias[l],
+                               nullptr, b.act[l + 1], Hs[l + 1], Ws[l + 1], kRegStride[l], 1, 1, r->d_status, r->n_sms,
+                               s, g_conv_timeout_ns.load(), g_conv_stall_tile.load()));
       continue;
     }
     ConvArgs a{};
@@ -1544,7 +1544,14 @@ relo_status reg_backward(relo_regressor* r, const RegBuffers& b, int n, int W, i
         a.Hi = Hs[l + 1];
         a.Wi = Ws[l + 1];
       }
-      RELO_CUDA(launch_conv(gs, 8, a, r->n_sms, s));
+      if (!a.upsample && g_conv_tcgen05.load()) {
+        // a stride-1 layer's backward-data pass is a forward convolution with the flipped,
+        // transposed weights, masked by the ReLU of the layer's input: tcgen05 as well
+        RELO_CUDA(launch_conv_tc(gs, g, n, a.Hi, a.Wi, r->d_wt[l], nullptr, b.act[l], b.gpre[l - 1], Hs[l], Ws[l], 1,
+                                 1, 0, r->d_status, r->n_sms, s, g_conv_timeout_ns.load(), g_conv_stall_tile.load()));
+      } else {
+        RELO_CUDA(launch_conv(gs, 8, a, r->n_sms, s));
+      }
       g = b.gpre[l - 1];
       gs = 64;
     }

@@ -34,16 +34,30 @@ namespace relo {
 namespace {
 
 constexpr int kTcThreads = 192;             // 6 warps
-constexpr int kTcStages = 4;                // A-operand ring
-constexpr int kTcM = 128, kTcN = 64, kTcC = 64;
-constexpr int kTcABytes = kTcM * kTcC * 2;  // 16 KB per stage
-constexpr int kTcWBytes = 9 * kTcN * kTcC * 2;
+constexpr int kTcM = 128, kTcN = 64;
 constexpr int kTcAccCols = 64;              // FP32 columns of one accumulator
 constexpr int kTcTmemCols = 2 * kTcAccCols;
-constexpr size_t kTcSmem = 1024 + (size_t)kTcWBytes + (size_t)kTcStages * kTcABytes;
+
+// Per input-channel count CIN (64: the inner layers; 16: the first layer, its 4 channels padded):
+// a pixel row is CIN x 2 bytes, which is also the swizzle span of the operand layout (128 B or 32 B;
+// 8-row atoms of 1024 B or 256 B).
+template <int CIN>
+struct TcShape {
+  static constexpr int kRowBytes = CIN * 2;
+  static constexpr int kABytes = kTcM * kRowBytes;           // one tap's tile: 16 KB or 4 KB
+  static constexpr int kWBytes = 9 * kTcN * kRowBytes;
+  static constexpr int kAtomBytes = 8 * kRowBytes;           // stride between 8-row atoms
+  static constexpr int kChunks = kRowBytes / 16;             // 16-byte chunks per row
+  static constexpr uint64_t kLayout = CIN == 64 ? 2 : 6;     // descriptor swizzle: 128 B / 32 B
+  // A-operand ring: 64 KB of tap tiles in flight (4 stages of 16 KB, or 16 of 4 KB)
+  static constexpr int kStages = CIN == 64 ? 4 : 16;
+  static constexpr size_t kSmem = 1024 + (size_t)kWBytes + (size_t)kStages * kABytes;
+  static_assert(CIN == 16 || CIN == 64, "64 -> 64 and 16 -> 64 channels");
+};
 
 struct TcArgs {
-  const float* bias;      // [64]
+  const float* bias;      // [64] or null
+  const bf16* mask;       // [B][Ho][Wo][64]: outputs where mask <= 0 are zeroed (ReLU derivative), or null
   const bf16* w;          // [9][64 out][64 in]
   bf16* out;              // [B][Ho][Wo][64]
   int32_t* status;        // RELO_ETIMEOUT when a wait ran out (else untouched)
@@ -110,12 +124,23 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-// Shared-memory matrix descriptor of a K-major operand in the 128-B swizzled layout: start address,
-// stride between 8-row atoms 1024 B (the leading offset is unused with this swizzle), descriptor
-// version 1 (bits 46-47), swizzle mode 2 = 128 B (bits 61-63).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
-  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+// Shared-memory matrix descriptor of a K-major operand in a swizzled layout whose span equals a
+// row: start address, stride between 8-row atoms (the leading offset is unused with these
+// swizzles), descriptor version 1 (bits 46-47), swizzle mode (bits 61-63: 2 = 128 B, 6 = 32 B).
+template <int CIN>
+__device__ __forceinline__ uint64_t operand_desc(uint32_t addr) {
+  using S = TcShape<CIN>;
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(S::kAtomBytes >> 4) << 32) |
+         ((uint64_t)1 << 46) | (S::kLayout << 61);
+}
+
+// Offset of 16-byte chunk j of row r in the swizzled layout: the chunk index XOR the row's position
+// in its 8-row atom (128 B: 3 bits), or its bit 2 (32 B: 1 bit), as the TMA unit writes it.
+template <int CIN>
+__device__ __forceinline__ int swizzled(int r, int j) {
+  using S = TcShape<CIN>;
+  const int x = CIN == 64 ? (r & 7) : ((r >> 2) & 1);
+  return r * S::kRowBytes + ((j ^ x) << 4);
 }
 
 // Instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16 (bits 7-9, 10-12 = 1),
@@ -162,25 +187,28 @@ __device__ __forceinline__ void tile_origin(const TcArgs& a, int t, int& b, int&
   ox0 = (r % a.tiles_x) * a.Wt;
 }
 
+template <int CIN>
 __global__ void __launch_bounds__(kTcThreads, 1) conv_tc_kernel(const __grid_constant__ CUtensorMap in_map, TcArgs a) {
+  using S = TcShape<CIN>;
+  constexpr int kTcStages = S::kStages;
   extern __shared__ uint8_t tc_smem_raw[];
   __shared__ uint64_t bars[2 * kTcStages + 5];     // full[s], empty[s], acc_full[2], acc_empty[2], drain
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
   uint8_t* base = reinterpret_cast<uint8_t*>(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* sW = base;                    // [9][64][128 B] swizzled
-  uint8_t* sA = base + kTcWBytes;        // [kTcStages][128][128 B] swizzled
+  uint8_t* sW = base;                    // [9][64][row] swizzled
+  uint8_t* sA = base + S::kWBytes;       // [kStages][128][row] swizzled
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[kTcStages]);
   const uint32_t accf0 = smem_u32(&bars[2 * kTcStages]), acce0 = smem_u32(&bars[2 * kTcStages + 2]);
   const uint32_t drain = smem_u32(&bars[2 * kTcStages + 4]);
   volatile int* abort = &abort_sh;
 
-  // weights -> shared memory in the 128-B swizzled K-major layout: 16-B chunk j of row r at j ^ (r & 7)
-  for (int v = threadIdx.x; v < 9 * kTcN * 8; v += kTcThreads) {
-    const int row = v >> 3, j = v & 7;
+  // weights -> shared memory in the swizzled K-major layout
+  for (int v = threadIdx.x; v < 9 * kTcN * S::kChunks; v += kTcThreads) {
+    const int row = v / S::kChunks, j = v % S::kChunks;
     const uint4 x = __ldg(reinterpret_cast<const uint4*>(a.w) + v);
-    *reinterpret_cast<uint4*>(sW + row * 128 + ((j ^ (row & 7)) << 4)) = x;
+    *reinterpret_cast<uint4*>(sW + swizzled<CIN>(row, j)) = x;
   }
   if (threadIdx.x == 0) {
     abort_sh = 0;
@@ -229,8 +257,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) conv_tc_kernel(const __grid_con
           issued[s] = 0;
           if (t == a.stall_tile) continue;   // test hook: the consumer's wait for this stage runs out
           const int ky = tap / 3, kx = tap % 3;
-          mbar_expect_tx(full0 + 8 * s, kTcABytes);
-          tma_load_4d(smem_u32(sA + s * kTcABytes), &in_map, full0 + 8 * s, 0, ox0 * a.stride + (kx - 1) * a.dil,
+          mbar_expect_tx(full0 + 8 * s, S::kABytes);
+          tma_load_4d(smem_u32(sA + s * S::kABytes), &in_map, full0 + 8 * s, 0, ox0 * a.stride + (kx - 1) * a.dil,
                       oy0 * a.stride + (ky - 1) * a.dil, b);
           issued[s] = 1;
           phase[s] = round & 1;
@@ -264,10 +292,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) conv_tc_kernel(const __grid_con
             break;
           }
           tc_fence_after();
-          const uint32_t a0 = smem_u32(sA + s * kTcABytes), b0 = smem_u32(sW + tap * (kTcN * 128));
+          const uint32_t a0 = smem_u32(sA + s * S::kABytes), b0 = smem_u32(sW + tap * (kTcN * S::kRowBytes));
 #pragma unroll
-          for (int kk = 0; kk < kTcC / 16; ++kk)
-            umma_bf16(d, sw128_desc(a0 + 32 * kk), sw128_desc(b0 + 32 * kk), (tap > 0 || kk > 0) ? 1u : 0u);
+          for (int kk = 0; kk < CIN / 16; ++kk)
+            umma_bf16(d, operand_desc<CIN>(a0 + 32 * kk), operand_desc<CIN>(b0 + 32 * kk), (tap > 0 || kk > 0) ? 1u : 0u);
           umma_commit(empty0 + 8 * s);      // the stage is free once these MMAs have read it
         }
         if (ok) umma_commit(accf0 + 8 * buf);
@@ -303,18 +331,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) conv_tc_kernel(const __grid_con
       tile_origin(a, t, b, oy0, ox0);
       const int oy = oy0 + m / a.Wt, ox = ox0 + m % a.Wt;
       if (oy < a.Ho && ox < a.Wo) {
-        uint4* dst = reinterpret_cast<uint4*>(a.out + (((size_t)b * a.Ho + oy) * a.Wo + ox) * kTcN);
+        const size_t px = ((size_t)b * a.Ho + oy) * a.Wo + ox;
+        uint4* dst = reinterpret_cast<uint4*>(a.out + px * kTcN);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
+          uint4 mk = make_uint4(0u, 0u, 0u, 0u);
+          if (a.mask) mk = __ldg(reinterpret_cast<const uint4*>(a.mask + px * kTcN) + j);
+          const uint32_t mw[4] = {mk.x, mk.y, mk.z, mk.w};
           uint32_t pk[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             const int n = 8 * j + 2 * e;
             const float* v = n < 32 ? v0 : v1;
-            float x0 = v[n & 31] + __ldg(&a.bias[n]), x1 = v[(n & 31) + 1] + __ldg(&a.bias[n + 1]);
+            float x0 = v[n & 31], x1 = v[(n & 31) + 1];
+            if (a.bias) {
+              x0 += __ldg(&a.bias[n]);
+              x1 += __ldg(&a.bias[n + 1]);
+            }
             if (a.relu) {
               x0 = fmaxf(x0, 0.f);
               x1 = fmaxf(x1, 0.f);
+            }
+            if (a.mask) {
+              const __nv_bfloat162 mm = *reinterpret_cast<const __nv_bfloat162*>(&mw[e]);
+              if (!(__bfloat162float(mm.x) > 0.f)) x0 = 0.f;
+              if (!(__bfloat162float(mm.y) > 0.f)) x1 = 0.f;
             }
             const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
             pk[e] = *reinterpret_cast<const uint32_t*>(&h);
@@ -347,8 +388,6 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-}  // namespace
-
 int conv_tc_tile_width(int Wo) {
   // output tiles of Wt x (128 / Wt) pixels: the widest of 128, 64, 32, 16 that wastes no column,
   // else 16
@@ -357,16 +396,20 @@ int conv_tc_tile_width(int Wo) {
   return 16;
 }
 
-cudaError_t launch_conv_tc(const bf16* in, int B, int Hi, int Wi, const bf16* w, const float* bias, bf16* out, int Ho,
-                           int Wo, int stride, int dil, int relu, int32_t* status, int n_sms, cudaStream_t s,
-                           unsigned long long timeout_ns, int stall_tile) {
+template <int CIN>
+cudaError_t launch_conv_tc_t(const bf16* in, int B, int Hi, int Wi, const bf16* w, const float* bias, const bf16* mask,
+                             bf16* out, int Ho, int Wo, int stride, int dil, int relu, int32_t* status, int n_sms,
+                             cudaStream_t s, unsigned long long timeout_ns, int stall_tile) {
+  using S = TcShape<CIN>;
   if (B <= 0 || Ho <= 0 || Wo <= 0) return cudaSuccess;
   if ((stride != 1 && stride != 2) || dil < 1 || dil > 8 || !status) return cudaErrorInvalidValue;
   if (((uintptr_t)in & 15) || ((uintptr_t)out & 15) || ((uintptr_t)w & 15)) return cudaErrorMisalignedAddress;
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
+  if (mask && ((uintptr_t)mask & 15)) return cudaErrorMisalignedAddress;
   TcArgs a{};
   a.bias = bias;
+  a.mask = mask;
   a.w = w;
   a.out = out;
   a.status = status;
@@ -383,28 +426,43 @@ cudaError_t launch_conv_tc(const bf16* in, int B, int Hi, int Wi, const bf16* w,
   a.n_tiles = B * a.tiles_x * a.tiles_y;
   a.timeout_ns = timeout_ns;
   a.stall_tile = stall_tile;
-  // 4-D map: (channel, x, y, image), box 64 x Wt*stride x Ht*stride x 1 walked with element strides
-  // (1, stride, stride, 1): Wt x Ht pixels of 128 B
+  // 4-D map: (channel, x, y, image), box CIN x Wt*stride x Ht*stride x 1 walked with element strides
+  // (1, stride, stride, 1): Wt x Ht pixel rows of CIN x 2 bytes
   CUtensorMap map;
-  const cuuint64_t dims[4] = {(cuuint64_t)kTcC, (cuuint64_t)Wi, (cuuint64_t)Hi, (cuuint64_t)B};
-  const cuuint64_t strides[3] = {(cuuint64_t)kTcC * 2, (cuuint64_t)Wi * kTcC * 2, (cuuint64_t)Hi * Wi * kTcC * 2};
-  const cuuint32_t box[4] = {(cuuint32_t)kTcC, (cuuint32_t)(a.Wt * stride), (cuuint32_t)(a.Ht * stride), 1};
+  const cuuint64_t dims[4] = {(cuuint64_t)CIN, (cuuint64_t)Wi, (cuuint64_t)Hi, (cuuint64_t)B};
+  const cuuint64_t strides[3] = {(cuuint64_t)CIN * 2, (cuuint64_t)Wi * CIN * 2, (cuuint64_t)Hi * Wi * CIN * 2};
+  const cuuint32_t box[4] = {(cuuint32_t)CIN, (cuuint32_t)(a.Wt * stride), (cuuint32_t)(a.Ht * stride), 1};
   const cuuint32_t estr[4] = {1, (cuuint32_t)stride, (cuuint32_t)stride, 1};
   if (box[1] > 256 || box[2] > 256) return cudaErrorInvalidValue;
   const CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(in), dims, strides, box, estr,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CIN == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_32B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   static PerDevice configured;
   int dummy = 0;
   cudaError_t e = per_device(configured, &dummy, [](int, int* v) {
     *v = 1;
-    return cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    return cudaFuncSetAttribute(conv_tc_kernel<CIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kSmem);
   });
   if (e != cudaSuccess) return e;
   const int grid = std::min(a.n_tiles, n_sms);
-  conv_tc_kernel<<<grid, kTcThreads, kTcSmem, s>>>(map, a);
+  conv_tc_kernel<CIN><<<grid, kTcThreads, S::kSmem, s>>>(map, a);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_conv_tc(int cin, const bf16* in, int B, int Hi, int Wi, const bf16* w, const float* bias,
+                           const bf16* mask, bf16* out, int Ho, int Wo, int stride, int dil, int relu, int32_t* status,
+                           int n_sms, cudaStream_t s, unsigned long long timeout_ns, int stall_tile) {
+  if (cin == 64)
+    return launch_conv_tc_t<64>(in, B, Hi, Wi, w, bias, mask, out, Ho, Wo, stride, dil, relu, status, n_sms, s,
+                                timeout_ns, stall_tile);
+  if (cin == 16)
+    return launch_conv_tc_t<16>(in, B, Hi, Wi, w, bias, mask, out, Ho, Wo, stride, dil, relu, status, n_sms, s,
+                                timeout_ns, stall_tile);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace relo

@@ -79,13 +79,14 @@ cudaError_t launch_loss(const float* out, const float4* tgt, int n_cells, bf16* 
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long n, float lr, int t, cudaStream_t s);
 cudaError_t launch_cell_forest(const CellForestArgs& a, cudaStream_t s);
 
-// Forward 3x3 convolution of a 64 -> 64-channel layer on the tcgen05 tensor cores (conv_tc.cu):
-// in [B][Hi][Wi][64], w [9][64][64], bias [64], out [B][Ho][Wo][64] BF16 NHWC; stride 1 or 2,
+// Forward 3x3 convolution of a cin -> 64-channel layer (cin 16 or 64) on the tcgen05 tensor cores
+// (conv_tc.cu): in [B][Hi][Wi][cin], w [9][64][cin], bias [64] (nullable), mask [B][Ho][Wo][64]
+// (nullable: outputs where mask <= 0 become 0), out [B][Ho][Wo][64] BF16 NHWC; stride 1 or 2,
 // dilation 1-8, zero padding = dilation.  A bounded wait that runs out sets *status = RELO_ETIMEOUT.
 // stall_tile >= 0 (test hook) withholds that tile's loads so that the wait for them runs out.
-cudaError_t launch_conv_tc(const bf16* in, int B, int Hi, int Wi, const bf16* w, const float* bias, bf16* out, int Ho,
-                           int Wo, int stride, int dil, int relu, int32_t* status, int n_sms, cudaStream_t s,
-                           unsigned long long timeout_ns, int stall_tile);
+cudaError_t launch_conv_tc(int cin, const bf16* in, int B, int Hi, int Wi, const bf16* w, const float* bias,
+                           const bf16* mask, bf16* out, int Ho, int Wo, int stride, int dil, int relu, int32_t* status,
+                           int n_sms, cudaStream_t s, unsigned long long timeout_ns, int stall_tile);
 cudaError_t launch_head_copy(const float* head, long n_cells, float* out4, cudaStream_t s);
 
 }  // namespace relo

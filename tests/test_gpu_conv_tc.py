@@ -1,5 +1,6 @@
-"""The tcgen05 forward convolution of the regressor's 64 -> 64-channel layers (TMA tile loads,
-MMAs into tensor memory) against the mma.sync kernel on the same operands, and its bounded waits:
+"""The tcgen05 convolutions of the regressor (the forward of every layer but the head, the
+backward-data pass of the stride-1 layers; TMA tile loads, MMAs into tensor memory) against the
+mma.sync kernel on the same operands, and their bounded waits:
 a launch whose loads are withheld gives up within its time limit, reports RELO_ETIMEOUT through
 the learned path's result, frees what it holds and leaves the context usable.
 
@@ -82,3 +83,34 @@ def test_tcgen05_bounded_wait_reports_timeout(room, oracle_room):
     assert B.result_from_bytes(torch.from_numpy(stalled))["status"] == B.ETIMEOUT
     after = run()
     assert np.array_equal(after, before)
+
+
+def test_tcgen05_gradients_match_mma_sync(room, oracle_room):
+    """Training's gradients with the tcgen05 kernels (the forward of every layer but the head, the
+    backward-data pass of the stride-1 layers, masked by the ReLU) against the mma.sync kernels on
+    the same operands: relative L2 of the whole gradient <= 2e-2 (BF16 activation and gradient
+    storage turns FP32 ordering differences into BF16 rounding flips), losses within 1e-3."""
+    world, _ = room
+    intr = synth.Intrinsics.for_size(160, 120)
+    poses = synth.training_poses(world, 2, seed=96)[:3]
+    ds, cs = zip(*[oracle_room.raycast(intr, P) for P in poses])
+    dd, cc = _u16(np.stack(ds)), torch.from_numpy(np.stack(cs)).to(DEV)
+    n = len(poses)
+
+    def grads(tcgen05):
+        B.debug_conv_path(tcgen05)
+        try:
+            reg = B.Regressor(seed=14, origin=ORIGIN)
+            ws = torch.empty(B.regressor_workspace_size(n, 160, 120, True), dtype=torch.uint8, device=DEV)
+            loss = torch.zeros(1, dtype=torch.float32, device=DEV)
+            B.regressor_gradients(reg, dd, cc, intr, poses, ws, loss)
+            torch.cuda.synchronize()
+            return float(loss.item()), reg.grads().astype(np.float64)
+        finally:
+            B.debug_conv_path(True)
+
+    la, ga = grads(True)
+    lb, gb = grads(False)
+    assert abs(la - lb) <= 1e-3 * abs(lb)
+    rel = np.linalg.norm(ga - gb) / np.linalg.norm(gb)
+    assert rel <= 2e-2, rel
