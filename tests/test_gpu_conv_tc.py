@@ -4,9 +4,11 @@ mma.sync kernel on the same operands, and their bounded waits:
 a launch whose loads are withheld gives up within its time limit, reports RELO_ETIMEOUT through
 the learned path's result, frees what it holds and leaves the context usable.
 
-Both kernels multiply the same BF16 operands and accumulate in FP32, in different orders, so the
-network outputs agree to FP32 rounding carried through BF16 activations (relative L2 <= 5e-3);
-parity with the FP64 oracle is checked in test_gpu_regressor.py with the tcgen05 path on."""
+Both kernels multiply the same BF16 operands and accumulate them in FP32 in the same order (taps in
+turn, 16 channels per instruction), and the two instruction forms round alike: the network outputs
+and gradients come out bit for bit equal (the 2000-step online training follows the same
+trajectory with either).  Parity with the FP64 oracle is checked in test_gpu_regressor.py with the
+tcgen05 path on."""
 import numpy as np
 import pytest
 import torch
@@ -49,9 +51,8 @@ def test_tcgen05_forward_matches_mma_sync(room, oracle_room, size):
     reg = B.Regressor(seed=12, origin=ORIGIN)
     a = _forward(reg, dd, cc, True)
     b = _forward(reg, dd, cc, False)
-    assert np.isfinite(a).all()
-    rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
-    assert rel <= 5e-3, rel
+    assert np.isfinite(a).all() and np.abs(a).max() > 0
+    assert np.array_equal(a, b), np.abs(a - b).max()
 
 
 def test_tcgen05_bounded_wait_reports_timeout(room, oracle_room):
@@ -88,8 +89,7 @@ def test_tcgen05_bounded_wait_reports_timeout(room, oracle_room):
 def test_tcgen05_gradients_match_mma_sync(room, oracle_room):
     """Training's gradients with the tcgen05 kernels (the forward of every layer but the head, the
     backward-data pass of the stride-1 layers, masked by the ReLU) against the mma.sync kernels on
-    the same operands: relative L2 of the whole gradient <= 2e-2 (BF16 activation and gradient
-    storage turns FP32 ordering differences into BF16 rounding flips), losses within 1e-3."""
+    the same operands: the loss and every gradient bit for bit."""
     world, _ = room
     intr = synth.Intrinsics.for_size(160, 120)
     poses = synth.training_poses(world, 2, seed=96)[:3]
@@ -111,6 +111,5 @@ def test_tcgen05_gradients_match_mma_sync(room, oracle_room):
 
     la, ga = grads(True)
     lb, gb = grads(False)
-    assert abs(la - lb) <= 1e-3 * abs(lb)
-    rel = np.linalg.norm(ga - gb) / np.linalg.norm(gb)
-    assert rel <= 2e-2, rel
+    assert la == lb and np.abs(gb).max() > 0
+    assert np.array_equal(ga, gb), np.abs(ga - gb).max()
