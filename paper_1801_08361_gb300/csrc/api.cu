@@ -308,6 +308,27 @@ void build_items(const std::vector<int>& K, int B, bool stall, std::vector<PItem
   *final_base = g_final * n;
 }
 
+// The size of build_items' list and of its counter block, without building it.
+void count_items(const std::vector<int>& K, int B, int* n_items, int* n_done, int* final_base) {
+  const int n = (int)K.size();
+  int R = 0;
+  for (int k : K) R = std::max(R, rounds_for(k));
+  long items = 0;
+  for (int j = 0; j < n; ++j) {
+    items += (K[j] + kPersistThreadsHost - 1) / kPersistThreadsHost + 1;  // fits, finalisation
+    int cur = K[j];
+    for (int r = 0; r < R && cur > 1; ++r) {
+      const int parts = ((r + 1) * B + kRefinePixels - 1) / kRefinePixels, surv = (cur + 1) / 2;
+      items += 1 + (cur + 31) / 32 + 1 + (long)(surv + 31) / 32 * parts +
+               (surv + kPersistThreadsHost - 1) / kPersistThreadsHost;
+      cur = surv;
+    }
+  }
+  *n_items = (int)items;
+  *n_done = (2 + 5 * R + 1) * n;
+  *final_base = (2 + 5 * R) * n;
+}
+
 // Records ev (nullable) on s; external: as an event-record node when s is being captured.
 cudaError_t record(cudaEvent_t ev, cudaStream_t s, bool external) {
   if (!ev) return cudaSuccess;
@@ -1939,8 +1960,10 @@ struct relo_batch {
   bool timing = false;
   cudaEvent_t ev[kStages + 1] = {};
   Schedule sched;  // launch schedule (relo_batch_set_schedule / relo_batch_autotune)
-  // the persistent schedule's item lists, uploaded the first time that schedule is chosen
-  std::vector<PItem> items_L, items_F;
+  // the persistent schedule's item lists, built and uploaded the first time it is chosen
+  std::vector<int> KL, KF;  // hypotheses per job of each pass
+  int batch_pixels = 0;
+  bool stall_items = false;
   bool items_uploaded = false;
   // per attempt: its query images and forest leaves inside the workspace (for inspection)
   std::vector<uint16_t*> a_depth, a_leaves;
@@ -1987,7 +2010,6 @@ struct HostJobs {
   std::vector<RayJob> query, verify_L, verify_F;
   std::vector<ForestJob> forest;
   std::vector<RansacJob> ransac_L, ransac_F;
-  std::vector<PItem> items_L, items_F;
   std::vector<int32_t> alive_L, surv_L, alive_F, surv_F, kind;
 };
 
@@ -2039,20 +2061,21 @@ void layout_batch(const relo_attempt* at, int n, const relo_ransac_params& p, ch
   b.passF.d_alive_prefix = c.take<int32_t>((size_t)std::max(RF, 1) * (nF + 1));
   b.passF.d_surv_prefix = c.take<int32_t>((size_t)std::max(RF, 1) * (nF + 1));
   // the persistent schedule's items and counters (used when the schedule asks for it)
-  std::vector<PItem> items_L, items_F;
+  // (the lists themselves are built when the persistent schedule is first chosen)
   {
-    const bool stall = g_persist_stall.load();
     int nd = 0;
-    build_items(KL, p.batch, stall, items_L, &nd, &b.passL.final_base);
-    b.passL.n_items = (int)items_L.size();
+    count_items(KL, p.batch, &b.passL.n_items, &nd, &b.passL.final_base);
     b.passL.ctrl_words = 4 + nd;
-    b.passL.d_items = c.take<PItem>(std::max<size_t>(items_L.size(), 1));
+    b.passL.d_items = c.take<PItem>(std::max(b.passL.n_items, 1));
     b.passL.d_ctrl = c.take<int32_t>(b.passL.ctrl_words);
-    build_items(KF, p.batch, stall, items_F, &nd, &b.passF.final_base);
-    b.passF.n_items = (int)items_F.size();
+    count_items(KF, p.batch, &b.passF.n_items, &nd, &b.passF.final_base);
     b.passF.ctrl_words = 4 + nd;
-    b.passF.d_items = c.take<PItem>(std::max<size_t>(items_F.size(), 1));
+    b.passF.d_items = c.take<PItem>(std::max(b.passF.n_items, 1));
     b.passF.d_ctrl = c.take<int32_t>(b.passF.ctrl_words);
+    b.KL = KL;
+    b.KF = KF;
+    b.batch_pixels = p.batch;
+    b.stall_items = g_persist_stall.load();
   }
   // learned images first (contiguous for the batched forward), then the rest
   uint16_t* depth_L = nullptr;
@@ -2093,8 +2116,6 @@ void layout_batch(const relo_attempt* at, int n, const relo_ransac_params& p, ch
     ca.depth_lr = c.take<uint16_t>((size_t)nL * cells);
   }
   h = HostJobs{};
-  h.items_L = std::move(items_L);
-  h.items_F = std::move(items_F);
   b.a_depth.assign(n, nullptr);
   b.a_rgba.assign(n, nullptr);
   b.a_leaves.assign(n, nullptr);
@@ -2339,8 +2360,6 @@ relo_status relo_batch_prepare(const relo_attempt* at, int32_t n, const relo_ran
   if (e == cudaSuccess) e = upload(b->passF.d_alive_prefix, h.alive_F);
   if (e == cudaSuccess) e = upload(b->passF.d_surv_prefix, h.surv_F);
   if (e == cudaSuccess) e = upload(b->d_kind, h.kind);
-  b->items_L = std::move(h.items_L);
-  b->items_F = std::move(h.items_F);
   if (e != cudaSuccess) {
     delete b;
     return cuda_fail(e, "batch descriptors");
@@ -2431,8 +2450,14 @@ namespace {
 // The persistent schedule's items go to the device the first time a batch may use them.
 relo_status ensure_items(relo_batch* b) {
   if (b->items_uploaded) return RELO_OK;
-  cudaError_t e = upload(b->passL.d_items, b->items_L);
-  if (e == cudaSuccess) e = upload(b->passF.d_items, b->items_F);
+  std::vector<PItem> items_L, items_F;
+  int nd = 0, fb = 0;
+  build_items(b->KL, b->batch_pixels, b->stall_items, items_L, &nd, &fb);
+  build_items(b->KF, b->batch_pixels, b->stall_items, items_F, &nd, &fb);
+  if ((int)items_L.size() != b->passL.n_items || (int)items_F.size() != b->passF.n_items)
+    return fail(RELO_EINVAL, "persistent schedule: item count mismatch");
+  cudaError_t e = upload(b->passL.d_items, items_L);
+  if (e == cudaSuccess) e = upload(b->passF.d_items, items_F);
   if (e != cudaSuccess) return cuda_fail(e, "persistent schedule items");
   b->items_uploaded = true;
   return RELO_OK;

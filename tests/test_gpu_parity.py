@@ -309,7 +309,10 @@ def test_relocalise_matches_oracle(room, oracle_room, room_forest, gpu_forest, g
     for i, P in enumerate(queries):
         d, c = oracle_room.raycast(intr, P)
         leaves = oracle.forest_eval(room_forest.nodes, d, c)
-        ro = oracle.preemptive_ransac(d, intr, leaves, room_forest, oracle.RansacParams(n_hyps=64, batch=500, seed=i))
+        ro = oracle.preemptive_ransac(d, intr, leaves, room_forest, oracle.RansacParams(n_hyps=64, batch=500, seed=i),
+                                      trace=True)
+        tied = any(_cut_is_near_tie(rd["energy"], rd["alive_before"], (len(rd["alive_before"]) + 1) // 2)
+                   for rd in ro["trace"].rounds)
         prm = B.ransac_params(n_hyps=64, batch=500, seed=i)
         res = torch.zeros(B.RESULT_BYTES, dtype=torch.uint8, device=DEV)
         dd = u16_dev(d)
@@ -319,6 +322,8 @@ def test_relocalise_matches_oracle(room, oracle_room, room_forest, gpu_forest, g
         torch.cuda.synchronize()
         r = B.result_from_bytes(res)
         assert r["status"] == 0 and r["n_valid"] == int((d > 0).sum())
+        if not tied:
+            assert r["hypothesis"] == ro["index"], i
         if r["hypothesis"] == ro["index"]:
             same += 1
             assert np.abs(r["pose"][:3] - ro["pose"][:3]).max() < 1e-4
