@@ -466,6 +466,10 @@ def run_ours(args):
     host_results = (B.PoseResult * A)()
 
     def e2e_steps():
+        # untimed warm-up calls first (the call's host-side buffers and caches settle)
+        for s in range(min(args.warmup, n_sets)):
+            sets[s]["noise"].copy_(host_noise[s], non_blocking=True)
+            B.relocalise_batch_into(sets[s]["att"], prm, sets[s]["ws"], host_results)
         if world_size > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()

@@ -545,7 +545,7 @@ const char* relo_batch_stage_name(int32_t k);
 
 /* Launch schedule of a batch (no counterpart in the paper): how work maps to threads and how
  * large the grids are.  Every schedule computes the same results bit for bit; only the time
- * differs.  A new batch starts with the defaults (8, 256, 0, 0, 0). */
+ * differs.  A new batch starts with the defaults (8, 256, 0, 0, 0, 0, 0). */
 typedef struct relo_schedule {
   int32_t ray_warp_width;     /* raycasts: each warp covers ray_warp_width x (32 / width) pixels of
                                  its CTA's 16 x 16 tile; 2, 4, 8 or 16 */
@@ -560,6 +560,9 @@ typedef struct relo_schedule {
                                  stages of every attempt from a dependency-ordered list, waiting
                                  (bounded in time) on per-attempt counters, so that one attempt's
                                  rounds run while another is still searching.  Same results. */
+  int32_t forest_smem_levels; /* forest evaluation: each CTA first copies the top levels of its
+                                 forest's trees (up to this many, at most 48 KB) into shared
+                                 memory and reads them there; 0..10, 0 = none */
 } relo_schedule;
 relo_status relo_batch_get_schedule(const relo_batch* batch, relo_schedule* out);
 /* Sets the schedule of later runs and drops a captured graph (capture again).

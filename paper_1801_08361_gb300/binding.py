@@ -74,7 +74,8 @@ FREE_FN = ctypes.CFUNCTYPE(None, c_vp, c_vp)
 
 class Schedule(ctypes.Structure):
     _fields_ = [("ray_warp_width", c_i32), ("forest_threads", c_i32), ("forest_tiles", c_i32),
-                ("search_ctas_per_sm", c_i32), ("refit_per", c_i32), ("persistent", c_i32)]
+                ("search_ctas_per_sm", c_i32), ("refit_per", c_i32), ("persistent", c_i32),
+                ("forest_smem_levels", c_i32)]
 
     def to_dict(self) -> dict:
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

@@ -2472,6 +2472,7 @@ relo_status relo_batch_get_schedule(const relo_batch* b, relo_schedule* out) {
   out->search_ctas_per_sm = b->sched.search_ctas_per_sm;
   out->refit_per = b->sched.refit_per;
   out->persistent = b->sched.persistent;
+  out->forest_smem_levels = b->sched.forest_smem_levels;
   return RELO_OK;
 }
 
@@ -2486,6 +2487,8 @@ relo_status relo_batch_set_schedule(relo_batch* b, const relo_schedule* in) {
   if (in->search_ctas_per_sm < 0 || in->search_ctas_per_sm > 64) return fail(RELO_EINVAL, "search_ctas_per_sm outside [0, 64]");
   if (in->refit_per < 0 || in->refit_per > 32) return fail(RELO_EINVAL, "refit_per outside [0, 32]");
   if (in->persistent != 0 && in->persistent != 1) return fail(RELO_EINVAL, "persistent must be 0 or 1");
+  if (in->forest_smem_levels < 0 || in->forest_smem_levels > kMaxSmemLevels)
+    return fail(RELO_EINVAL, "forest_smem_levels outside [0, 10]");
   s.persistent = in->persistent;
   if (s.persistent) {
     const relo_status st = ensure_items(b);
@@ -2495,6 +2498,7 @@ relo_status relo_batch_set_schedule(relo_batch* b, const relo_schedule* in) {
   s.forest_tiles = in->forest_tiles;
   s.search_ctas_per_sm = in->search_ctas_per_sm;
   s.refit_per = in->refit_per;
+  s.forest_smem_levels = in->forest_smem_levels;
   b->sched = s;
   if (b->graph) {  // the captured launches used the old schedule
     cudaGraphExecDestroy(b->graph);
@@ -2523,6 +2527,7 @@ relo_status relo_batch_autotune(relo_batch* b, int32_t repeats, relo_schedule* c
       {&Schedule::ray_warp_log2w, {3, 4, 2, 1}, {0, 4, 8}},
       {&Schedule::forest_threads, {256, 128}, {5}},
       {&Schedule::forest_tiles, {0, 1}, {5}},
+      {&Schedule::forest_smem_levels, {0, 4, 6, 8}, {5}},
       {&Schedule::search_ctas_per_sm, {0, 1, 2, 3}, {2, 6}},
       {&Schedule::refit_per, {0, 1, 4, 16}, {3, 7}},
       {&Schedule::persistent, {0, 1}, {2, 3, 6, 7}},

@@ -57,17 +57,22 @@ __device__ __forceinline__ int probe(int x, int delta, const DepthDivisor& dv, i
 // kPacked: probes read the packed image (one 64-bit load, then a shift and a mask: no branch on
 // the node's kind, which differs between neighbouring lanes); otherwise the depth or the colour
 // image, by kind.
-template <int MT, bool kHi, bool kPacked>
-__device__ __forceinline__ void descend(const ForestJob& job, int u, int v, const DepthDivisor& dv, int (&node)[MT]) {
-  const ForestView& f = job.forest;
-  const int T = f.T, W = job.W, H = job.H;
-  const int n_int = (1 << f.D) - 1;
-  for (int level = 0; level < f.D; ++level) {
+// The CTA's shared-memory copy of the top levels of its forest's trees ([T][2^levels - 1]).
+extern __shared__ int4 s_forest_top[];
+
+// Levels [level_begin, level_end) with nodes from the forest in global memory, or (kShared) from
+// s_forest_top, which holds n_nodes of each tree.
+template <int MT, bool kHi, bool kPacked, bool kShared>
+__device__ __forceinline__ void descend_levels(const ForestJob& job, int u, int v, const DepthDivisor& dv,
+                                               int (&node)[MT], int n_nodes, int level_begin, int level_end) {
+  const int T = job.forest.T, W = job.W, H = job.H;
+  for (int level = level_begin; level < level_end; ++level) {
 #pragma unroll
     for (int t = 0; t < MT; ++t) {
       if (t < T) {
-        const int4 nd = RELO_CHECK(node[t] >= 0 && node[t] < n_int) ? __ldg(&f.nodes[(size_t)t * n_int + node[t]])
-                                                                    : make_int4(0, 0, 0, 0);
+        int4 nd = make_int4(0, 0, 0, 0);
+        if (RELO_CHECK(node[t] >= 0 && node[t] < n_nodes))
+          nd = kShared ? s_forest_top[t * n_nodes + node[t]] : __ldg(&job.forest.nodes[(size_t)t * n_nodes + node[t]]);
         const int dx1 = (int)(int16_t)(nd.x & 0xFFFF), dy1 = nd.x >> 16;
         const int dx2 = (int)(int16_t)(nd.y & 0xFFFF), dy2 = nd.y >> 16;
         const int q1 = probe<kHi>(v, dy1, dv, H - 1) * W + probe<kHi>(u, dx1, dv, W - 1);
@@ -95,6 +100,15 @@ __device__ __forceinline__ void descend(const ForestJob& job, int u, int v, cons
   }
 }
 
+// The first top_levels levels from s_forest_top, the rest from global memory.
+template <int MT, bool kHi, bool kPacked>
+__device__ __forceinline__ void descend(const ForestJob& job, int u, int v, const DepthDivisor& dv, int (&node)[MT],
+                                        int top_levels) {
+  if (top_levels > 0)
+    descend_levels<MT, kHi, kPacked, true>(job, u, v, dv, node, (1 << top_levels) - 1, 0, top_levels);
+  descend_levels<MT, kHi, kPacked, false>(job, u, v, dv, node, (1 << job.forest.D) - 1, top_levels, job.forest.D);
+}
+
 // CTAs of 256 threads per SM the compiler must fit: full occupancy (7 and 8 tie, 6 is 10 % slower
 // on the house workload)
 #ifndef RELO_FOREST_MIN_BLOCKS
@@ -104,9 +118,12 @@ __device__ __forceinline__ void descend(const ForestJob& job, int u, int v, cons
 // One thread per pixel.  tiles == 0: a job's slot k is its pixel k (row-major); tiles == 1: its
 // slots run over 32 x 8 pixel tiles, 256 slots each, tiles row-major (neighbouring threads
 // probe neighbouring pixels in two dimensions).
+// levels > 0: the CTA first copies the top min(levels, D) levels of its job's trees into shared
+// memory (dynamic, top_trees x (2^levels - 1) nodes), so those node visits read shared memory.
 template <int MT>
 __global__ void __launch_bounds__(256, RELO_FOREST_MIN_BLOCKS)
-    forest_kernel(const ForestJob* __restrict__ jobs, int n_jobs, const ForestJob single, int tiles) {
+    forest_kernel(const ForestJob* __restrict__ jobs, int n_jobs, const ForestJob single, int tiles, int levels,
+                  int top_trees) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   // jobs start on multiples of the CTA size, so the CTA's first pixel names its job; the job is
   // staged in shared memory (its fields are read at every node visit)
@@ -128,6 +145,16 @@ __global__ void __launch_bounds__(256, RELO_FOREST_MIN_BLOCKS)
   __syncthreads();
   const ForestJob& job = sj;
   if (job_skipped(job.skip)) return;
+  // s_forest_top holds top_trees trees of 2^levels - 1 nodes
+  const int top_levels = job.forest.T <= top_trees ? min(levels, job.forest.D) : 0;
+  if (top_levels > 0) {
+    const int n_top = (1 << top_levels) - 1, n_int = (1 << job.forest.D) - 1;
+    for (int i = threadIdx.x; i < job.forest.T * n_top; i += blockDim.x) {
+      const int t = i / n_top;
+      s_forest_top[i] = __ldg(&job.forest.nodes[(size_t)t * n_int + (i - t * n_top)]);
+    }
+    __syncthreads();
+  }
   const int64_t slot = gid - job.pixel_begin;
   const int64_t n_pix = (int64_t)job.W * job.H;
   const int W = job.W, H = job.H;
@@ -157,11 +184,11 @@ __global__ void __launch_bounds__(256, RELO_FOREST_MIN_BLOCKS)
 #pragma unroll
   for (int t = 0; t < MT; ++t) node[t] = 0;
   if (job.packed) {
-    if (dv.shift >= 32) descend<MT, true, true>(job, u, v, dv, node);
-    else descend<MT, false, true>(job, u, v, dv, node);
+    if (dv.shift >= 32) descend<MT, true, true>(job, u, v, dv, node, top_levels);
+    else descend<MT, false, true>(job, u, v, dv, node, top_levels);
   } else {
-    if (dv.shift >= 32) descend<MT, true, false>(job, u, v, dv, node);
-    else descend<MT, false, false>(job, u, v, dv, node);
+    if (dv.shift >= 32) descend<MT, true, false>(job, u, v, dv, node, top_levels);
+    else descend<MT, false, false>(job, u, v, dv, node, top_levels);
   }
 #pragma unroll
   for (int t = 0; t < MT; ++t)
@@ -175,16 +202,27 @@ cudaError_t launch_forest(const ForestJob* jobs_dev, int n_jobs, const ForestJob
                           cudaStream_t s, int max_trees, const Schedule& sched) {
   if (total_pixels <= 0) return cudaSuccess;
   const int threads = sched.forest_threads;
-  if ((threads != 128 && threads != 256) || (sched.forest_tiles != 0 && sched.forest_tiles != 1))
+  if ((threads != 128 && threads != 256) || (sched.forest_tiles != 0 && sched.forest_tiles != 1) ||
+      sched.forest_smem_levels < 0 || sched.forest_smem_levels > kMaxSmemLevels)
     return cudaErrorInvalidValue;
   ForestJob one{};
   if (single) one = *single;
   // total_pixels counts each job's slots, a multiple of 256 (pixel_begin), so no CTA spans two jobs
   const unsigned grid = (unsigned)((total_pixels + threads - 1) / threads);
   const int tiles = sched.forest_tiles;
-  if (max_trees <= 4) forest_kernel<4><<<grid, threads, 0, s>>>(jobs_dev, n_jobs, one, tiles);
-  else if (max_trees <= 8) forest_kernel<8><<<grid, threads, 0, s>>>(jobs_dev, n_jobs, one, tiles);
-  else forest_kernel<kMaxTrees><<<grid, threads, 0, s>>>(jobs_dev, n_jobs, one, tiles);
+  // the unrolled width: the smallest instance that holds every job's trees (5, the usual forest
+  // size, has its own: no idle unrolled slots, no spills at 32 registers)
+  const int mt = max_trees <= 4 ? 4 : max_trees <= 5 ? 5 : max_trees <= 6 ? 6 : max_trees <= 8 ? 8 : kMaxTrees;
+  // the staged levels take at most 48 KB of shared memory per CTA (fewer levels for many trees)
+  const size_t trees = (size_t)max(1, min(max_trees, mt));
+  int levels = sched.forest_smem_levels;
+  while (levels > 0 && trees * ((1u << levels) - 1) * sizeof(int4) > 48 * 1024) --levels;
+  const size_t smem = levels > 0 ? trees * ((1u << levels) - 1) * sizeof(int4) : 0;
+  if (mt == 4) forest_kernel<4><<<grid, threads, smem, s>>>(jobs_dev, n_jobs, one, tiles, levels, (int)trees);
+  else if (mt == 5) forest_kernel<5><<<grid, threads, smem, s>>>(jobs_dev, n_jobs, one, tiles, levels, (int)trees);
+  else if (mt == 6) forest_kernel<6><<<grid, threads, smem, s>>>(jobs_dev, n_jobs, one, tiles, levels, (int)trees);
+  else if (mt == 8) forest_kernel<8><<<grid, threads, smem, s>>>(jobs_dev, n_jobs, one, tiles, levels, (int)trees);
+  else forest_kernel<kMaxTrees><<<grid, threads, smem, s>>>(jobs_dev, n_jobs, one, tiles, levels, (int)trees);
   return cudaGetLastError();
 }
 

@@ -404,10 +404,12 @@ struct Schedule {
   int ray_warp_log2w = 3;    // raycast: each warp covers a (1 << w) x (32 >> w) footprint of its 16 x 16 tile
   int forest_threads = 256;  // forest: CTA size (128 or 256)
   int forest_tiles = 0;      // forest: 0 = each CTA takes consecutive pixels, 1 = 32 x 8 pixel tiles
+  int forest_smem_levels = 0;  // forest: top levels of the trees each CTA copies to shared memory (0: none)
   int search_ctas_per_sm = 0;  // hypothesis search: persistent CTAs per SM (0: occupancy maximum)
   int refit_per = 0;         // re-fit: survivors per one-warp CTA (0: spread over twice the SM count)
   int persistent = 0;        // RANSAC of a batch: 0 = one launch per stage, 1 = one persistent launch
 };
+constexpr int kMaxSmemLevels = 10;
 // Forest slots a job of W x H pixels takes (a multiple of 256 that also holds its 32 x 8 tiles).
 inline int64_t forest_slots(int W, int H) {
   const int64_t rows = ((int64_t)W * H + 255) / 256 * 256;

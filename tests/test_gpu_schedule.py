@@ -13,7 +13,8 @@ pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda:0")
 SIZES = [(200, 152), (150, 101), (96, 72), (320, 240)]
 VALUES = {"ray_warp_width": [2, 4, 8, 16], "forest_threads": [128, 256], "forest_tiles": [0, 1],
-          "search_ctas_per_sm": [0, 1, 2, 3], "refit_per": [0, 1, 4, 16, 32], "persistent": [0, 1]}
+          "search_ctas_per_sm": [0, 1, 2, 3], "refit_per": [0, 1, 4, 16, 32], "persistent": [0, 1],
+          "forest_smem_levels": [0, 1, 4, 6, 8, 10]}
 
 
 @pytest.fixture(scope="module")
@@ -64,7 +65,7 @@ def test_every_schedule_value_gives_the_default_results(batch):
     bt, items, _ = batch
     default = bt.schedule()
     assert default == {"ray_warp_width": 8, "forest_threads": 256, "forest_tiles": 0, "search_ctas_per_sm": 0,
-                       "refit_per": 0, "persistent": 0}
+                       "refit_per": 0, "persistent": 0, "forest_smem_levels": 0}
     ref = _run(bt, items)
     assert sum(B.result_from_bytes(ref[0][k * B.RESULT_BYTES:(k + 1) * B.RESULT_BYTES])["status"] == 0
                for k in range(len(items))) >= 3
@@ -73,7 +74,7 @@ def test_every_schedule_value_gives_the_default_results(batch):
             bt.set_schedule(**{**default, field: v})
             _equal(_run(bt, items), ref)
     bt.set_schedule(ray_warp_width=16, forest_threads=128, forest_tiles=1, search_ctas_per_sm=1, refit_per=32,
-                    persistent=1)
+                    persistent=1, forest_smem_levels=7)
     _equal(_run(bt, items), ref)
     bt.set_schedule(**default)
 
@@ -97,7 +98,8 @@ def test_invalid_schedules_are_rejected(batch):
     bt, _, _ = batch
     before = bt.schedule()
     for bad in (dict(ray_warp_width=3), dict(ray_warp_width=32), dict(forest_threads=64), dict(forest_tiles=2),
-                dict(search_ctas_per_sm=-1), dict(refit_per=33), dict(persistent=2)):
+                dict(search_ctas_per_sm=-1), dict(refit_per=33), dict(persistent=2), dict(forest_smem_levels=-1),
+                dict(forest_smem_levels=11)):
         with pytest.raises(B.ReloError):
             bt.set_schedule(**bad)
     assert bt.schedule() == before
