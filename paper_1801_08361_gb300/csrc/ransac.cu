@@ -611,6 +611,45 @@ __device__ __forceinline__ float3 record_point(const int4* __restrict__ rec) {
   return make_float3(__int_as_float(w.x), __int_as_float(w.y), __int_as_float(w.z));
 }
 
+// record_best over staged modes with the whole warp on one point x (every lane passes the same x):
+// lane l scores modes l, l + 32, ..., then the warp keeps the largest score and, among equal ones,
+// the lowest index -- the mode that the scan in order with a strict comparison keeps (a NaN score
+// never wins in either).  Returns the score (-inf if none) and, in every lane, the mode's mean.
+__device__ __forceinline__ float warp_best_staged(const ModeSlot& slot, int n_staged, float3 x, int lane,
+                                                  float3* mu_best) {
+  float best = -INFINITY;
+  int bi = -1;
+  for (int k = lane; k < n_staged; k += 32) {
+    const float sc = mode_score(slot.m[3 * k], slot.m[3 * k + 1], slot.m[3 * k + 2], x);
+    if (sc > best) {
+      best = sc;
+      bi = k;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi >= 0 && (bi < 0 || oi < bi))) {
+      best = ob;
+      bi = oi;
+    }
+  }
+  if (bi >= 0) {
+    const float4 a = slot.m[3 * bi];
+    *mu_best = make_float3(a.x, a.y, a.z);
+  }
+  return best;
+}
+
+// Chunks with at most this many hypotheses score each staged pixel with the whole warp per
+// hypothesis (warp_best_staged) instead of one lane per hypothesis scanning every mode: the last
+// rounds, where a job keeps one or two survivors and the lanes of a chunk would mostly idle.
+// Measured on the house batch: faster for 1 and 2 hypotheses (re-fit sums 457 -> 309 us in the
+// last round), slower from 4 (the warp pass's shuffle reductions are a dependent chain, while the
+// per-lane scan overlaps its independent mode scores).  Both give the same scores and modes.
+constexpr int kFewHyps = 2;
+
 // Round kernels: a CTA takes 32 hypotheses of one job (one per lane) and its warps split the
 // pixels, each warp walking every kRoundWarps-th pixel; per-warp partial sums are combined in
 // warp order, so the result does not depend on scheduling.
@@ -630,12 +669,24 @@ __device__ __forceinline__ void energy_block(const RansacJob* __restrict__ jobs,
   const PoseF P = pose_to_float(job.poses + 12 * (size_t)h);
   float sum = 0.f;
   const int4* recs = job.pix + (size_t)r * job.B * job.hs;
+  const int n_here = min(32, n_alive - chunk * 32);
   for (int i = warp; i < job.B; i += kRoundWarps) {
     const int4* rec = recs + (size_t)i * job.hs;
     __syncwarp();  // the slot's previous pixel is scored
     const int n_staged = stage_modes(job, rec, slots[warp], lane);
-    const float best = record_best(job, rec, slots[warp], n_staged, apply(P, record_point(rec)), nullptr);
-    sum += fminf(kLogEps, -best);
+    const float3 x = apply(P, record_point(rec));
+    if (n_here <= kFewHyps && n_staged >= 0) {
+      for (int j = 0; j < n_here; ++j) {
+        const float3 xj = make_float3(__shfl_sync(0xffffffffu, x.x, j), __shfl_sync(0xffffffffu, x.y, j),
+                                      __shfl_sync(0xffffffffu, x.z, j));
+        float3 mu;
+        const float best = warp_best_staged(slots[warp], n_staged, xj, lane, &mu);
+        if (lane == j) sum += fminf(kLogEps, -best);
+      }
+    } else {
+      const float best = record_best(job, rec, slots[warp], n_staged, x, nullptr);
+      sum += fminf(kLogEps, -best);
+    }
   }
   part[warp][lane] = sum;
   __syncthreads();
@@ -750,16 +801,8 @@ __device__ __forceinline__ void refine_block(const RansacJob* __restrict__ jobs,
   float acc[16], lo[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) acc[q] = lo[q] = 0.f;
-  const int p1 = min(p0 + kRefinePixels, n_drawn);
-  for (int i = p0 + warp; i < p1; i += kRoundWarps) {
-    const int4* rec = job.pix + (size_t)i * job.hs;
-    const float3 c = record_point(rec);
-    const float3 x = apply(P, c);
-    float3 mu;
-    __syncwarp();  // the slot's previous pixel is scored
-    const int n_staged = stage_modes(job, rec, slots[warp], lane);
-    const float best = record_best(job, rec, slots[warp], n_staged, x, &mu);
-    if (best == -INFINITY) continue;
+  // adds pixel c (its point x under this lane's hypothesis, best mode mean mu) when it is an inlier
+  auto add_inlier = [&](float3 c, float3 x, float3 mu) {
     const float dx = x.x - mu.x, dy = x.y - mu.y, dz = x.z - mu.z;
     if (dx * dx + dy * dy + dz * dz < r2) {
       const float u[3] = {c.x - cref.x, c.y - cref.y, c.z - cref.z};
@@ -778,6 +821,27 @@ __device__ __forceinline__ void refine_block(const RansacJob* __restrict__ jobs,
           comp_add(acc[7 + 3 * p + q], lo[7 + 3 * p + q], pr);
           lo[7 + 3 * p + q] = __fadd_rn(lo[7 + 3 * p + q], __fmaf_rn(u[p], w[q], -pr));
         }
+    }
+  };
+  const int n_here = min(32, n_surv - chunk * 32);
+  const int p1 = min(p0 + kRefinePixels, n_drawn);
+  for (int i = p0 + warp; i < p1; i += kRoundWarps) {
+    const int4* rec = job.pix + (size_t)i * job.hs;
+    const float3 c = record_point(rec);
+    const float3 x = apply(P, c);
+    float3 mu;
+    __syncwarp();  // the slot's previous pixel is scored
+    const int n_staged = stage_modes(job, rec, slots[warp], lane);
+    if (n_here <= kFewHyps && n_staged >= 0) {
+      for (int j = 0; j < n_here; ++j) {
+        const float3 xj = make_float3(__shfl_sync(0xffffffffu, x.x, j), __shfl_sync(0xffffffffu, x.y, j),
+                                      __shfl_sync(0xffffffffu, x.z, j));
+        const float best = warp_best_staged(slots[warp], n_staged, xj, lane, &mu);
+        if (lane == j && best != -INFINITY) add_inlier(c, x, mu);
+      }
+    } else {
+      const float best = record_best(job, rec, slots[warp], n_staged, x, &mu);
+      if (best != -INFINITY) add_inlier(c, x, mu);
     }
   }
   // warps w then write sums q = w, w + kRoundWarps: the kRoundWarps partials added in warp order,

@@ -172,16 +172,17 @@ def test_forest_bit_exact_on_query(room, oracle_room, room_forest, gpu_forest):
     assert np.array_equal(u16_np(leaves), oracle.forest_eval(room_forest.nodes, d, c))
 
 
-@pytest.mark.parametrize("depth", [1, 7, 15])
-def test_forest_bit_exact_ragged_random(depth):
-    rng = np.random.default_rng(depth)
+@pytest.mark.parametrize("trees,depth", [(3, 1), (3, 7), (3, 15), (5, 15), (6, 9), (8, 12), (11, 15)])
+def test_forest_bit_exact_ragged_random(trees, depth):
+    """Every unrolled width of the kernel (4, 5, 6, 8 and 16 tree slots) on ragged random images."""
+    rng = np.random.default_rng(depth + 100 * trees)
     H, W = 23, 37
     d = rng.integers(200, 9000, (H, W)).astype(np.uint16)
     d[rng.random((H, W)) < 0.2] = 0
     c = rng.integers(0, 256, (H, W, 4)).astype(np.uint8)
-    nodes = synth.random_forest_nodes(3, depth, seed=depth)
+    nodes = synth.random_forest_nodes(trees, depth, seed=depth + 100 * trees)
     f = B.Forest(nodes, max_modes=4)
-    leaves = torch.zeros((3, H, W), dtype=torch.int16, device=DEV)
+    leaves = torch.zeros((trees, H, W), dtype=torch.int16, device=DEV)
     B.forest_eval(f, u16_dev(d), torch.from_numpy(c).to(DEV), leaves)
     torch.cuda.synchronize()
     want = oracle.forest_eval(nodes, d, c)
