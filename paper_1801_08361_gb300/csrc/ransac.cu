@@ -351,10 +351,11 @@ __device__ __forceinline__ int first_passing(const RansacJob& job, int h, int n_
   return -1;
 }
 
-// CTAs per SM for the search (4 x 128 threads, i.e. up to 128 registers for the two tries in
-// flight per lane: the fastest of 4, 5, 6 and 8 on the house workload)
+// CTAs per SM for the search (5 x 128 threads: 96 registers for the two tries in flight per lane,
+// with about 60 bytes spilled): on the house batch the hypotheses stage takes 18.68 ms at 5, 18.98
+// at 4 (128 registers, no spills) and 21.89 at 6 (80 registers, 128-byte spills)
 #ifndef RELO_SEARCH_MIN_BLOCKS
-#define RELO_SEARCH_MIN_BLOCKS 4
+#define RELO_SEARCH_MIN_BLOCKS 5
 #endif
 // The search of hypothesis gw (flattened over the jobs) by one warp.
 __device__ __forceinline__ int search_one(const RansacJob* __restrict__ jobs, int n_jobs, int gw, int lane) {

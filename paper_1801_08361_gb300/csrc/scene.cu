@@ -194,15 +194,18 @@ __device__ __forceinline__ float march_ray(const SceneView& s, float3 C, float3 
 }
 
 constexpr int kTile = 16;
-// CTAs per SM the compiler must fit (depth-only renders; colour renders one fewer): the fastest
-// of 4 to 8 on the house workload; the march is latency-bound, so occupancy beats the few
-// registers this spills
+// CTAs per SM the compiler must fit, depth-only and colour renders: the march is latency-bound,
+// so occupancy beats the few registers this spills.  On the house batch: depth-only 12.08 / 11.94
+// / 12.99 ms at 5 / 6 / 7, colour 13.53 / 12.86 / 12.40 / 12.57 ms at 4 / 5 / 6 / 7
 #ifndef RELO_RAYCAST_MIN_BLOCKS
 #define RELO_RAYCAST_MIN_BLOCKS 6
 #endif
+#ifndef RELO_RAYCAST_COLOUR_MIN_BLOCKS
+#define RELO_RAYCAST_COLOUR_MIN_BLOCKS 6
+#endif
 
 template <bool kColour, bool kCompare>
-__global__ void __launch_bounds__(kTile* kTile, kColour ? RELO_RAYCAST_MIN_BLOCKS - 1 : RELO_RAYCAST_MIN_BLOCKS)
+__global__ void __launch_bounds__(kTile* kTile, kColour ? RELO_RAYCAST_COLOUR_MIN_BLOCKS : RELO_RAYCAST_MIN_BLOCKS)
     raycast_kernel(const RayJob* __restrict__ jobs, int n_jobs, const RayJob single, int warp_log2w) {
   // locate the job owning this tile (jobs are few; binary search on tile_begin)
   int lo = 0, hi = n_jobs - 1;
