@@ -66,21 +66,23 @@ ALG_BYTES_PER_PIXEL = {
     "learned_verify": 35.87,
 }
 # DRAM bytes (read + write) per attempt of the stage's main kernel: the ncu capture summarised in
-# profiles/attempt_kernels_house_640x480_batch128.md (128 attempts per launch) divided by 128; a
-# launch of A attempts is reported as A times that (None: not captured for the current code).
+# profiles/attempt_dram_house_640x480_batch32.md (32 attempts per launch, the current kernels)
+# divided by 32; a launch of A attempts is reported as A times that (attempts are independent, so
+# the traffic grows with their number; None: not captured for the current code).
 PROFILED_TRAFFIC_BYTES_PER_ATTEMPT = {
-    "query_raycast": (3.115e9 + 0.615e9) / 128,
-    "forest_eval": (0.398e9 + 0.361e9) / 128,
-    "forest_hypotheses": (0.637e9 + 0.005e9) / 128,
-    "forest_verify": (1.868e9 + 0.032e9) / 128,
+    "query_raycast": (761931264 + 148813824) / 32,
+    "forest_eval": (101214976 + 62725632) / 32,
+    "forest_hypotheses": (161393152 + 7238400) / 32,
+    "forest_verify": (454581248 + 5998848) / 32,
 }
-# What limits each stage's main kernel in the same capture (the roofline fraction divides by DRAM
+# What limits each stage's main kernel (profiles/attempt_kernels_house_640x480_batch128.md and
+# profiles/forest_kernel_house_640x480_batch32.md; the roofline fraction divides by DRAM
 # bandwidth or an integer-issue peak; these kernels gather from L2 and are bound elsewhere).
 PROFILED_LIMITER = {
     "query_raycast": "instruction issue (71 % active; 17.1 of 32 lanes per instruction as rays end at "
                      "different steps); L2 throughput 9 %",
-    "forest_eval": "instruction issue (68 % active at 98 % warps active) and long-scoreboard stalls on "
-                   "node and probe loads (L2 hit 98 %, L2 throughput 44 %)",
+    "forest_eval": "instruction issue (69 % active at 98 % warps active, about 72 instructions per node "
+                   "visit) and long-scoreboard stalls on node and probe loads (L2 hit 98 %, L2 throughput 47 %)",
     "forest_hypotheses": "L2 throughput (63 %, L2 hit 98 %): four random 16-byte gathers per try",
     "forest_verify": "instruction issue (73 % active; 16.7 of 32 lanes per instruction); L2 throughput 12 %",
 }
