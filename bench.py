@@ -105,6 +105,9 @@ def parse():
     ap.add_argument("--profile-steps", type=int, default=0, help="(ncu) run this many steps and exit, no JSON")
     ap.add_argument("--profile-learned", type=int, default=0,
                     help="(ncu) this many regressor forward passes over 16 house views, then exit, no JSON")
+    ap.add_argument("--learned-fragments", type=int, default=0,
+                    help="train a regressor on each house fragment for this many steps and relocalise within it "
+                         "(0: skip)")
     ap.add_argument("--train-steps", type=int, default=2000,
                     help="online training steps of the learned regressor (0: skip the learned path)")
     ap.add_argument("--serve-seconds", type=float, default=4.0,
@@ -539,6 +542,11 @@ def run_ours(args):
     if args.serve_seconds > 0 and rank == 0:
         serving = serving_section(args, B, torch, dev, sets[0], prm)
 
+    # ---- the learned path on each fragment (optional, not part of the timed steps) --------------
+    learned_frag = None
+    if args.learned_fragments > 0 and rank == 0:
+        learned_frag = learned_fragments_section(args, B, synth, torch, dev, stream)
+
     # ---- the batched configuration (not part of the timed steps) ------------------------------
     frag = None
     if args.fragments and rank == 0:
@@ -570,7 +578,8 @@ def run_ours(args):
                            "stage_ms_per_step": {k: v / args.steps for k, v in stage_tot.items()},
                            "schedule": dict(schedule, autotuned=bool(args.autotune)),
                            "learned": learned, "serving": serving, "fusion": fusion, "precision": precision,
-                           "fragments": frag, "persistent_schedule": persistent},
+                           "fragments": frag, "persistent_schedule": persistent,
+                           "learned_fragments": learned_frag},
                 "e2e": {"value": e2e_value, "unit": UNIT,
                         "h2d_bytes_per_step": A * H * W * 4 + A * ctypes_attempt_bytes(),
                         "d2h_bytes_per_step": A * B.RESULT_BYTES, "clocks": e2e_clocks,
@@ -725,6 +734,71 @@ def learned_section(args, B, synth, torch, dev, scene, forest, world, intr, trai
                      "learned_forward_tflops": regressor_flops_per_view() * A / max(stages.get("learned_forward", 0.0), 1e-9) / 1e9}
         out[name]["learned_forward_frac"] = out[name]["learned_forward_tflops"] / burst
     return out
+
+
+LEARNED_FRAG_QUERIES = 32
+
+
+def learned_fragments_section(args, B, synth, torch, dev, stream):
+    """The learned regressor on each of the 8 house fragments (1-3 rooms, 13-40 m^2, each in its
+    own frame): trained online on noisy 640x480 renders near the fragment's own trajectory
+    (args.learned_fragments steps of 16 views, the learned workload's schedule), then relocalising
+    32 queries near that trajectory in the same fragment -- the learned path alone, and the
+    fragment's forest alone on the same attempts."""
+    from paper_1801_08361_gb300 import fragments as F
+    world, frags, scenes, forests, _ = F.build(dev)
+    intr = synth.Intrinsics.for_size(W, H, 12.0)
+    nb, steps = TRAIN_BATCH, args.learned_fragments
+    prm = B.ransac_params(n_hyps=K_HYPS, batch=B_PIX, max_tries=10000)
+    depth = torch.zeros((nb, H, W), dtype=torch.int16, device=dev)
+    rgba = torch.zeros((nb, H, W, 4), dtype=torch.uint8, device=dev)
+    ws = torch.empty(B.regressor_workspace_size(nb, W, H, True), dtype=torch.uint8, device=dev)
+    ws_views = torch.empty(B.raycast_views_workspace_size(nb), dtype=torch.uint8, device=dev)
+    n_noise = 64
+    noise = torch.from_numpy(np.stack([synth.depth_noise(H, W, 9100 + k) for k in range(n_noise)])).to(dev)
+    loss = torch.zeros(steps, dtype=torch.float32, device=dev)
+    rows = []
+    for k, f in enumerate(frags):
+        S = f["scene_to_world"]
+        centre_w = np.append((f["crop"][:3] + f["crop"][3:]) / 2.0, 1.0)
+        reg = B.Regressor(seed=3, origin=tuple(float(x) for x in (np.linalg.inv(S) @ centre_w)[:3]))
+        pool = [synth.world_to_scene_pose(P, S) for P in synth.query_poses(world, f["train_w"], steps * nb,
+                                                                             seed=500 + k)]
+        for s in range(steps):
+            q = (s * nb) % n_noise
+            B.raycast_views(scenes[k], intr, pool[s * nb:(s + 1) * nb], depth, rgba, noise_dev=noise[q:q + nb],
+                            workspace_dev=ws_views)
+            B.regressor_train_step(reg, depth, rgba, intr, pool[s * nb:(s + 1) * nb],
+                                   learning_rate(s, steps, TRAIN_LR, LEARNED.extra["warmup"]), ws, loss[s:s + 1])
+        torch.cuda.synchronize()
+        L = loss.cpu().numpy()
+        qs = [synth.world_to_scene_pose(P, S) for P in synth.query_poses(world, f["train_w"], LEARNED_FRAG_QUERIES,
+                                                                           seed=900 + k)]
+        qn = torch.from_numpy(np.stack([synth.depth_noise(H, W, 9500 + 100 * k + i)
+                                        for i in range(LEARNED_FRAG_QUERIES)])).to(dev)
+        row = {"fragment": k, "rooms": len(f["rooms"]), "loss_first_last_100": [float(L[:100].mean()),
+                                                                                 float(L[-100:].mean())]}
+        for name, learned in (("learned_only", True), ("forest_only", False)):
+            items = [dict(scene_b=scenes[k], forest_a=None if learned else forests[k], scene_a=scenes[k],
+                          regressor_a=reg if learned else None, intr=intr, pose_b=qs[i], noise=qn[i], seed=i)
+                     for i in range(LEARNED_FRAG_QUERIES)]
+            att = B.make_attempts(items)
+            wsb = torch.empty(B.batch_workspace_size(att, prm), dtype=torch.uint8, device=dev)
+            bt = B.Batch(att, prm, wsb)
+            res = torch.zeros(len(items) * B.RESULT_BYTES, dtype=torch.uint8, device=dev)
+            bt.run(res, stream=stream)
+            torch.cuda.synchronize()
+            raw = res.cpu()
+            rs = [B.result_from_bytes(raw[i * B.RESULT_BYTES:(i + 1) * B.RESULT_BYTES]) for i in range(len(items))]
+            row[name] = {"success": sum(int(success(r, qs[i])) for i, r in enumerate(rs)) / len(rs),
+                         "verified": sum(int(r["verified"]) for r in rs) / len(rs)}
+            del bt
+        rows.append(row)
+    n = len(rows)
+    return {"train_steps": steps, "train_batch": nb, "queries_per_fragment": LEARNED_FRAG_QUERIES, "size": f"{W}x{H}",
+            "per_fragment": rows,
+            "learned_only_success": sum(r["learned_only"]["success"] for r in rows) / n,
+            "forest_only_success": sum(r["forest_only"]["success"] for r in rows) / n}
 
 
 # ------------------------------------------------------------------------------------------------
