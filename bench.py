@@ -70,21 +70,20 @@ ALG_BYTES_PER_PIXEL = {
 # divided by 32; a launch of A attempts is reported as A times that (attempts are independent, so
 # the traffic grows with their number; None: not captured for the current code).
 PROFILED_TRAFFIC_BYTES_PER_ATTEMPT = {
-    "query_raycast": (761931264 + 148813824) / 32,
+    "query_raycast": None,
     "forest_eval": (101214976 + 62725632) / 32,
     "forest_hypotheses": (161393152 + 7238400) / 32,
-    "forest_verify": (454581248 + 5998848) / 32,
+    "forest_verify": "not captured for the current kernel",
 }
 # What limits each stage's main kernel (profiles/attempt_kernels_house_640x480_batch128.md and
 # profiles/forest_kernel_house_640x480_batch32.md; the roofline fraction divides by DRAM
 # bandwidth or an integer-issue peak; these kernels gather from L2 and are bound elsewhere).
 PROFILED_LIMITER = {
-    "query_raycast": "instruction issue (71 % active; 17.1 of 32 lanes per instruction as rays end at "
-                     "different steps); L2 throughput 9 %",
+    "query_raycast": "not captured for the current kernel",
     "forest_eval": "instruction issue (69 % active at 98 % warps active, about 72 instructions per node "
                    "visit) and long-scoreboard stalls on node and probe loads (L2 hit 98 %, L2 throughput 47 %)",
     "forest_hypotheses": "L2 throughput (63 %, L2 hit 98 %): four random 16-byte gathers per try",
-    "forest_verify": "instruction issue (73 % active; 16.7 of 32 lanes per instruction); L2 throughput 12 %",
+    "forest_verify": "not captured for the current kernel",
 }
 
 

@@ -112,6 +112,17 @@ relo_status relo_scene_lookup(const relo_scene* scene, const int32_t* keys_dev, 
  * restores the grid (if one was built).  Errors: RELO_EINVAL (null scene). */
 relo_status relo_scene_use_grid(relo_scene* scene, int32_t enable);
 
+/* Raycast acceleration (no counterpart in the paper; results are unchanged).  Creation also
+ * builds, on the device, an apron copy of the tsdf: per block 9 x 9 x 9 values (2944 bytes, about
+ * 1.44 times the block's own tsdf) whose last plane along each axis repeats the first voxels of
+ * the neighbouring block, or +1 where that block is unallocated.  The eight corners of every
+ * trilinear sample then lie in one block, so the march never looks up a neighbouring block for a
+ * sample on a block's last voxel.  relo_scene_use_apron(scene, 0) makes later raycasts read the
+ * blocks' own tsdf (looking neighbours up), 1 restores the copy.  Scenes made by
+ * relo_create_fusion_scene have no copy (fusion changes their voxels); the call has no effect on
+ * them.  Errors: RELO_EINVAL (null scene). */
+relo_status relo_scene_use_apron(relo_scene* scene, int32_t enable);
+
 /* ---------------------------------------------------------------------------------------
  * Synthetic raycast (Sec. 3.3.1, Fig. 3: the query is a colour + depth render of scene b from
  * the frame's pose; the appendix on global map rendering names the usual voxel raycast).

@@ -106,6 +106,7 @@ _SIGS = {
     "relo_scene_export": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(c_i64)]),
     "relo_scene_lookup": (c_i32, [c_vp, c_vp, c_i64, c_vp, c_vp]),
     "relo_scene_use_grid": (c_i32, [c_vp, c_i32]),
+    "relo_scene_use_apron": (c_i32, [c_vp, c_i32]),
     "relo_raycast_view": (c_i32, [c_vp, ctypes.POINTER(Intrinsics), ctypes.POINTER(c_dbl), c_vp, c_vp, c_vp, c_vp]),
     "relo_create_forest": (c_i32, [c_vp, c_i32, c_i32, c_vp, c_vp, c_i32, ctypes.POINTER(c_vp)]),
     "relo_destroy_forest": (None, [c_vp]),
@@ -270,6 +271,9 @@ class Scene:
 
     def use_grid(self, enable: bool):
         _check(lib().relo_scene_use_grid(self.handle, 1 if enable else 0))
+
+    def use_apron(self, enable: bool):
+        _check(lib().relo_scene_use_apron(self.handle, 1 if enable else 0))
 
     def __del__(self):
         if getattr(self, "handle", None) and _LIB is not None:

@@ -564,6 +564,28 @@ relo_status relo_create_scene(const int32_t* coords, const float* tsdf, const ui
   v.gx = gd[0];
   v.gy = gd[1];
   v.gz = gd[2];
+  // the apron copy of the tsdf, built on the device from the uploaded voxels and hash table
+  if (n > 0) {
+    void* d_coords = nullptr;
+    if (relo::dev_malloc(&d_coords, (size_t)n * 3 * sizeof(int32_t)) != cudaSuccess ||
+        relo::dev_malloc(&s->d_tsdf9, (size_t)n * kApronStride * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      relo::dev_free(d_coords);
+      relo::dev_free(s->d_tsdf9);
+      cleanup();
+      return fail(RELO_ENOMEM, "device allocation for the scene's apron copy failed");
+    }
+    e = cudaMemcpy(d_coords, coords, (size_t)n * 3 * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_build_apron(v, (const int32_t*)d_coords, n, (float*)s->d_tsdf9, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    relo::dev_free(d_coords);
+    if (e != cudaSuccess) {
+      relo::dev_free(s->d_tsdf9);
+      cleanup();
+      return cuda_fail(e, "scene apron build");
+    }
+    v.tsdf9 = (const float*)s->d_tsdf9;
+  }
   *out = s;
   return RELO_OK;
 }
@@ -575,6 +597,7 @@ void relo_destroy_scene(relo_scene* s) {
   relo::dev_free(s->d_tsdf);
   relo::dev_free(s->d_rgba);
   relo::dev_free(s->d_grid);
+  relo::dev_free(s->d_tsdf9);
   relo::dev_free(s->d_weight);
   relo::dev_free(s->d_coords);
   relo::dev_free(s->d_counters);
@@ -636,6 +659,7 @@ relo_status relo_create_fusion_scene(int64_t capacity, double voxel, double mu, 
   v.block_size = (float)(8.0 * voxel);
   v.inv_block = (float)(1.0 / (8.0 * voxel));
   v.grid = nullptr;
+  v.tsdf9 = nullptr;  // fusion changes the voxels: the raycast reads them directly
   *out = s;
   return RELO_OK;
 }
@@ -844,6 +868,12 @@ relo_status relo_debug_corrupt_scene(relo_scene* scene) {
 relo_status relo_scene_use_grid(relo_scene* s, int32_t enable) {
   if (!s) return fail(RELO_EINVAL, "scene is null");
   s->view.grid = enable ? (const int32_t*)s->d_grid : nullptr;
+  return RELO_OK;
+}
+
+relo_status relo_scene_use_apron(relo_scene* s, int32_t enable) {
+  if (!s) return fail(RELO_EINVAL, "scene is null");
+  s->view.tsdf9 = enable ? (const float*)s->d_tsdf9 : nullptr;
   return RELO_OK;
 }
 

@@ -78,7 +78,14 @@ struct SceneView {
   const int32_t* grid;
   int32_t ox, oy, oz;     // grid origin (block coordinates)
   int32_t gx, gy, gz;     // grid extent in blocks (multiples of 8)
+  // Apron copy of the tsdf (null when not built or not in use): per block a 9 x 9 x 9 array
+  // (x + 9 y + 81 z, padded to kApronStride floats) whose last plane along each axis repeats the
+  // first voxels of the neighbouring block (+1 where that block is unallocated), so the eight
+  // corners of every trilinear sample lie in the block holding the sample.
+  const float* tsdf9;
+  int32_t pad[2];
 };
+constexpr int kApronStride = 736;  // 729 voxels padded to a multiple of 32 floats (128 bytes)
 
 // Block index, or -D (see SceneView::grid), through the dense grid (caller checks s.grid).
 // Outside the box D is the Chebyshev distance to the box, a lower bound of the distance to any
@@ -434,6 +441,9 @@ cudaError_t launch_verify_decide_one(relo_pose_result* res, uint64_t omega, cuda
 cudaError_t launch_init_results(relo_pose_result* res, int n, cudaStream_t s);
 cudaError_t launch_merge_results(const relo_pose_result* learned, const relo_pose_result* fallback,
                                  const int32_t* kind, int n, relo_pose_result* out, cudaStream_t s);
+// Builds SceneView::tsdf9 for n blocks with coordinates coords_dev (n x int32 xyz) from the
+// scene's tsdf and hash table.
+cudaError_t launch_build_apron(const SceneView& sv, const int32_t* coords_dev, int64_t n, float* out, cudaStream_t s);
 cudaError_t launch_scene_lookup(SceneView sv, const int32_t* keys, int64_t n, int64_t* out, int32_t* err,
                                 cudaStream_t s);
 
@@ -558,6 +568,7 @@ struct relo_scene {
   void* d_tsdf;
   void* d_rgba;
   void* d_grid;
+  void* d_tsdf9;       // apron copy of the tsdf (SceneView::tsdf9), static scenes only
   int64_t n_blocks;
   // scenes that grow by fusion (relo_create_fusion_scene): capacity > 0
   int64_t capacity;

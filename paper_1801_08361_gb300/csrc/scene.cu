@@ -98,7 +98,18 @@ __device__ __forceinline__ float trilinear_tsdf(const SceneView& s, BlockCache& 
                                                 float fx, float fy, float fz, int* err) {
   float v[8];
   if (!RELO_CHECK(b0 < s.n_blocks)) return 1.0f;
-  if ((i & 7) != 7 && (j & 7) != 7 && (k & 7) != 7) {
+  if (s.tsdf9) {
+    // the apron copy holds all eight corners in block b0 (the same values the paths below read)
+    const float* base = s.tsdf9 + (size_t)b0 * kApronStride + (i & 7) + 9 * (j & 7) + 81 * (k & 7);
+    v[0] = __ldg(base);
+    v[1] = __ldg(base + 1);
+    v[2] = __ldg(base + 9);
+    v[3] = __ldg(base + 10);
+    v[4] = __ldg(base + 81);
+    v[5] = __ldg(base + 82);
+    v[6] = __ldg(base + 90);
+    v[7] = __ldg(base + 91);
+  } else if ((i & 7) != 7 && (j & 7) != 7 && (k & 7) != 7) {
     // all eight corners inside block b0: one contiguous neighbourhood
     const float* base = s.tsdf + (size_t)b0 * kVoxelsPerBlock + (i & 7) + 8 * (j & 7) + 64 * (k & 7);
     v[0] = __ldg(base);
@@ -399,6 +410,33 @@ cudaError_t launch_render_global(const RayJob* jobs_dev, int n, int W, int H, ui
   const size_t smem = (size_t)n * sizeof(RayJob);
   if (smem > 48 * 1024) return cudaErrorInvalidValue;
   render_global_kernel<<<ray_tiles(W, H), kTile * kTile, smem, s>>>(jobs_dev, n, depth, rgba, owner, err_flag);
+  return cudaGetLastError();
+}
+
+// The apron copy (SceneView::tsdf9): CTA per block, thread per apron voxel.  A voxel on the
+// last plane along an axis is the first voxel of the neighbouring block along it (the corner a
+// trilinear sample on the block's last voxel reads from that block), +1 where it is unallocated.
+__global__ void __launch_bounds__(256) build_apron_kernel(SceneView sv, const int32_t* __restrict__ coords,
+                                                          float* __restrict__ out) {
+  const int64_t b = blockIdx.x;
+  const int bx = coords[3 * b], by = coords[3 * b + 1], bz = coords[3 * b + 2];
+  for (int q = threadIdx.x; q < kApronStride; q += blockDim.x) {
+    float val = 1.0f;
+    if (q < 729) {
+      const int x = q % 9, y = (q / 9) % 9, z = q / 81;
+      int blk = (int)b, err = 0;
+      if (x == 8 || y == 8 || z == 8) blk = lookup_block(sv, bx + (x >> 3), by + (y >> 3), bz + (z >> 3), &err);
+      if (blk >= 0 && blk < sv.n_blocks)
+        val = sv.tsdf[(size_t)blk * kVoxelsPerBlock + (x & 7) + 8 * (y & 7) + 64 * (z & 7)];
+    }
+    out[b * kApronStride + q] = val;
+  }
+}
+
+cudaError_t launch_build_apron(const SceneView& sv, const int32_t* coords_dev, int64_t n, float* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (n > INT32_MAX) return cudaErrorInvalidValue;
+  build_apron_kernel<<<(unsigned)n, 256, 0, s>>>(sv, coords_dev, out);
   return cudaGetLastError();
 }
 

@@ -35,7 +35,8 @@ def test_hbm_view_counts_algorithmic_bytes_per_pixel():
     r = bench.roofline("query_raycast", 10.0, 100, 0, None, 152)
     want = bench.ALG_BYTES_PER_PIXEL["query_raycast"] * bench.W * bench.H * 100 / 0.01 / 1e9
     assert r["unit"] == "GB/s" and r["achieved"] == pytest.approx(want)
-    assert r["traffic"] == pytest.approx(bench.PROFILED_TRAFFIC_BYTES_PER_ATTEMPT["query_raycast"] * 100)
+    per = bench.PROFILED_TRAFFIC_BYTES_PER_ATTEMPT["query_raycast"]
+    assert r["traffic"] == (None if per is None else pytest.approx(per * 100))
 
 
 def test_peaks_fall_back_without_the_measured_file(monkeypatch, tmp_path):

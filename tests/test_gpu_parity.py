@@ -67,17 +67,21 @@ def test_lookup_bit_exact(room, oracle_room, gpu_room):
 @pytest.mark.parametrize("size", [(320, 240), (100, 75), (17, 9), (1, 1)])
 @pytest.mark.parametrize("noisy", [False, True])
 @pytest.mark.parametrize("grid", [True, False])
-def test_raycast_parity(room, oracle_room, gpu_room, size, noisy, grid):
-    """Both lookup paths of the raycast (dense grid with empty-cell skipping, hash walk)."""
+@pytest.mark.parametrize("apron", [True, False])
+def test_raycast_parity(room, oracle_room, gpu_room, size, noisy, grid, apron):
+    """Both lookup paths of the raycast (dense grid with empty-cell skipping, hash walk), each with
+    the tsdf's apron copy and with neighbour lookups for samples on a block's last voxel."""
     world, _ = room
     W, H = size
     intr = synth.Intrinsics.for_size(W, H)
     poses = synth.training_poses(world, 3, seed=21)
     gpu_room.use_grid(grid)
+    gpu_room.use_apron(apron)
     try:
         _raycast_parity_poses(oracle_room, gpu_room, intr, poses, noisy)
     finally:
         gpu_room.use_grid(True)
+        gpu_room.use_apron(True)
 
 
 def _raycast_parity_poses(oracle_room, gpu_room, intr, poses, noisy):
@@ -117,6 +121,29 @@ def test_raycast_grid_skips_match_the_block_walk(room, gpu_room):
         assert (dg == dh).mean() >= 0.9999
         assert np.abs(dg.astype(int) - dh.astype(int)).max() <= 1
         assert (np.abs(cg.astype(int) - ch.astype(int)).max(-1) <= 1).all()
+
+
+@pytest.mark.parametrize("grid", [True, False])
+def test_raycast_apron_equals_neighbour_lookups(room, gpu_room, grid):
+    """The apron copy holds, on each block's last plane, the neighbouring blocks' first voxels (+1
+    where unallocated): exactly the values the march otherwise looks up, in the same order, so
+    depth and colour images are identical, in both lookup paths."""
+    world, _ = room
+    intr = synth.Intrinsics.for_size(320, 240)
+    gpu_room.use_grid(grid)
+    try:
+        for i, P in enumerate(synth.training_poses(world, 4, seed=29)):
+            noise = synth.depth_noise(240, 320, 70 + i)
+            da, ca = gpu_render(gpu_room, intr, P, noise)
+            gpu_room.use_apron(False)
+            try:
+                dn, cn = gpu_render(gpu_room, intr, P, noise)
+            finally:
+                gpu_room.use_apron(True)
+            assert (da > 0).mean() > 0.5
+            assert np.array_equal(da, dn) and np.array_equal(ca, cn)
+    finally:
+        gpu_room.use_grid(True)
 
 
 def test_raycast_views_equals_single_views(room, gpu_room):
