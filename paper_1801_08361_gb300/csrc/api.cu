@@ -930,7 +930,8 @@ relo_status relo_raycast_views(const relo_scene* scene, const relo_intrinsics* i
   cudaStream_t s = (cudaStream_t)stream;
   RELO_CUDA(cudaMemcpyAsync(ws, jobs.data(), n * sizeof(RayJob), cudaMemcpyHostToDevice, s));
   // a copy from pageable memory returns once the host buffer has been staged, so jobs may go
-  RELO_CUDA(launch_raycast((const RayJob*)ws, n, nullptr, n * tiles, rgba != nullptr, false, s));
+  RELO_CUDA(launch_raycast((const RayJob*)ws, n, nullptr, n * tiles, rgba != nullptr, false, s, Schedule(),
+                           scene->view.tsdf9 != nullptr));
   return RELO_OK;
 }
 
@@ -952,8 +953,10 @@ relo_status relo_render_global(const relo_scene* const* scenes, const double* gl
   if (!ws || ((uintptr_t)ws & 255) != 0 || ws_bytes < relo_render_global_workspace_size(n_scenes))
     return fail(RELO_EINVAL, "workspace missing, misaligned or too small");
   std::vector<RayJob> jobs(n_scenes);
+  bool all_apron = true;
   for (int a = 0; a < n_scenes; ++a) {
     if (!scenes[a]) return fail(RELO_EINVAL, "null scene");
+    all_apron = all_apron && scenes[a]->view.tsdf9 != nullptr;
     // local camera -> scene-a pose: (gT_a)^-1 P_g, with gT_a rigid (scene a -> global)
     const double* g = global_poses + 16 * (size_t)a;
     double P[16] = {0};
@@ -972,7 +975,7 @@ relo_status relo_render_global(const relo_scene* const* scenes, const double* gl
   cudaStream_t s = (cudaStream_t)stream;
   RELO_CUDA(cudaMemcpyAsync(ws, jobs.data(), n_scenes * sizeof(RayJob), cudaMemcpyHostToDevice, s));
   RELO_CUDA(launch_render_global((const RayJob*)ws, n_scenes, intr->width, intr->height, depth, (uint32_t*)rgba,
-                                 owner, err_dev, s));
+                                 owner, err_dev, s, all_apron));
   return RELO_OK;
 }
 
@@ -1979,6 +1982,7 @@ struct relo_batch {
   int32_t* d_kind = nullptr;
   int32_t* d_errs = nullptr;  // nL + nF words
   int query_tiles = 0, verify_L_tiles = 0, verify_F_tiles = 0, max_trees = 1;
+  bool query_apron = false, verify_apron = false;  // every query / verification scene has its apron copy
   int64_t forest_pixels = 0;
   // learned pass
   relo_regressor* reg = nullptr;
@@ -2265,6 +2269,11 @@ void layout_batch(const relo_attempt* at, int n, const relo_ransac_params& p, ch
   b.query_tiles = qt;
   b.verify_L_tiles = vtL;
   b.verify_F_tiles = vtF;
+  b.query_apron = b.verify_apron = true;
+  for (int i = 0; i < n; ++i) {
+    b.query_apron = b.query_apron && h.query[i].scene.tsdf9 != nullptr;
+    b.verify_apron = b.verify_apron && at[i].scene_a->view.tsdf9 != nullptr;
+  }
   b.forest_pixels = fpix;
   b.max_trees = maxT;
   b.passL.n = nL;
@@ -2305,7 +2314,7 @@ relo_status issue_batch(relo_batch* b, relo_pose_result* results, cudaStream_t s
   RELO_CUDA(cudaMemsetAsync(b->d_errs, 0, (b->nL + b->nF + 1) * sizeof(int32_t), s));
   RELO_CUDA(launch_init_results(b->d_res_F, b->n, s));
   RELO_CUDA(mark(b, 0, s, capturing));
-  RELO_CUDA(launch_raycast(b->d_query, b->n, nullptr, b->query_tiles, true, false, s, b->sched));
+  RELO_CUDA(launch_raycast(b->d_query, b->n, nullptr, b->query_tiles, true, false, s, b->sched, b->query_apron));
   L += 2;
   RELO_CUDA(mark(b, 1, s, capturing));
   // pass L: learned attempts
@@ -2320,7 +2329,8 @@ relo_status issue_batch(relo_batch* b, relo_pose_result* results, cudaStream_t s
   relo_status st = run_pass(b->passL, s, &L, ev ? b->ev[3] : nullptr, ev ? b->ev[4] : nullptr, capturing, b->sched);
   if (st) return st;
   if (b->nL > 0) {
-    RELO_CUDA(launch_raycast(b->d_verify_L, b->nL, nullptr, b->verify_L_tiles, false, true, s, b->sched));
+    RELO_CUDA(launch_raycast(b->d_verify_L, b->nL, nullptr, b->verify_L_tiles, false, true, s, b->sched,
+                             b->verify_apron));
     RELO_CUDA(launch_verify_decide(b->passL.d_jobs, b->nL, s));
     L += 2;
   }
@@ -2334,7 +2344,8 @@ relo_status issue_batch(relo_batch* b, relo_pose_result* results, cudaStream_t s
   st = run_pass(b->passF, s, &L, ev ? b->ev[7] : nullptr, ev ? b->ev[8] : nullptr, capturing, b->sched);
   if (st) return st;
   if (b->nF > 0) {
-    RELO_CUDA(launch_raycast(b->d_verify_F, b->nF, nullptr, b->verify_F_tiles, false, true, s, b->sched));
+    RELO_CUDA(launch_raycast(b->d_verify_F, b->nF, nullptr, b->verify_F_tiles, false, true, s, b->sched,
+                             b->verify_apron));
     RELO_CUDA(launch_verify_decide(b->passF.d_jobs, b->nF, s));
     L += 2;
   }

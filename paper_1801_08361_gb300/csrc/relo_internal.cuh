@@ -424,9 +424,12 @@ inline int64_t forest_slots(int W, int H) {
   return rows > tiles ? rows : tiles;
 }
 
-// jobs_dev == nullptr: the single job is passed by value.
+// jobs_dev == nullptr: the single job is passed by value.  all_apron: every job of jobs_dev has
+// its scene's apron copy (SceneView::tsdf9), so the launch samples it (a single job's own scene
+// decides for itself).
 cudaError_t launch_raycast(const RayJob* jobs_dev, int n_jobs, const RayJob* single, int total_tiles,
-                           bool with_colour, bool compare, cudaStream_t s, const Schedule& sched = Schedule());
+                           bool with_colour, bool compare, cudaStream_t s, const Schedule& sched = Schedule(),
+                           bool all_apron = false);
 // max_trees: the largest tree count among the jobs (selects the kernel's unrolled width).  With
 // sched.forest_tiles, each job must own forest_slots(W, H) slots from its pixel_begin.
 cudaError_t launch_forest(const ForestJob* jobs_dev, int n_jobs, const ForestJob* single, int64_t total_pixels,
@@ -434,7 +437,7 @@ cudaError_t launch_forest(const ForestJob* jobs_dev, int n_jobs, const ForestJob
 int ray_tiles(int W, int H);
 // Global map rendering over n scene jobs sharing one image size (owner, rgba, err_flag nullable).
 cudaError_t launch_render_global(const RayJob* jobs_dev, int n, int W, int H, uint16_t* depth, uint32_t* rgba,
-                                 int8_t* owner, int32_t* err_flag, cudaStream_t s);
+                                 int8_t* owner, int32_t* err_flag, cudaStream_t s, bool all_apron);
 cudaError_t launch_verify_decide(const RansacJob* jobs, int n_jobs, cudaStream_t s);
 cudaError_t launch_verify_decide_one(relo_pose_result* res, uint64_t omega, cudaStream_t s);
 // Learned batches: mark fallback results not run, then pick each attempt's final result.

@@ -93,13 +93,15 @@ __device__ __forceinline__ int corner_voxel(int i, int j, int k, int n) {
 }
 
 // Trilinear tsdf at voxel-space point q (= p / voxel), given the block b0 holding floor(q);
-// corners in unallocated blocks read +1.
+// corners in unallocated blocks read +1.  kApron: from the scene's apron copy (s.tsdf9, which
+// every job of the launch has), where all eight corners lie in block b0 and hold the values the
+// neighbour lookups below would read; otherwise from the blocks' own tsdf.
+template <bool kApron>
 __device__ __forceinline__ float trilinear_tsdf(const SceneView& s, BlockCache& c, int b0, int i, int j, int k,
                                                 float fx, float fy, float fz, int* err) {
   float v[8];
   if (!RELO_CHECK(b0 < s.n_blocks)) return 1.0f;
-  if (s.tsdf9) {
-    // the apron copy holds all eight corners in block b0 (the same values the paths below read)
+  if (kApron) {
     const float* base = s.tsdf9 + (size_t)b0 * kApronStride + (i & 7) + 9 * (j & 7) + 81 * (k & 7);
     v[0] = __ldg(base);
     v[1] = __ldg(base + 1);
@@ -165,6 +167,7 @@ __device__ __forceinline__ uint32_t trilinear_rgba(const SceneView& s, BlockCach
 }
 
 // One ray.  Returns the hit depth parameter (camera z, metres) or a negative value if none.
+template <bool kApron>
 __device__ __forceinline__ float march_ray(const SceneView& s, float3 C, float3 d, float dmin, float dmax, BlockCache& c,
                                            int* err) {
   const float dn = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
@@ -191,7 +194,7 @@ __device__ __forceinline__ float march_ray(const SceneView& s, float3 C, float3 
       lam = lam_prev + 1e-5f;
       continue;
     }
-    const float f = trilinear_tsdf(s, c, b, i, j, k, qx - flx, qy - fly, qz - flz, err);
+    const float f = trilinear_tsdf<kApron>(s, c, b, i, j, k, qx - flx, qy - fly, qz - flz, err);
     if (f <= 0.0f) {
       if (!have_prev) return -1.0f;
       return lam_prev + (lam - lam_prev) * f_prev / (f_prev - f);
@@ -215,7 +218,7 @@ constexpr int kTile = 16;
 #define RELO_RAYCAST_COLOUR_MIN_BLOCKS 6
 #endif
 
-template <bool kColour, bool kCompare>
+template <bool kColour, bool kCompare, bool kApron>
 __global__ void __launch_bounds__(kTile* kTile, kColour ? RELO_RAYCAST_COLOUR_MIN_BLOCKS : RELO_RAYCAST_MIN_BLOCKS)
     raycast_kernel(const RayJob* __restrict__ jobs, int n_jobs, const RayJob single, int warp_log2w) {
   // locate the job owning this tile (jobs are few; binary search on tile_begin)
@@ -277,7 +280,7 @@ __global__ void __launch_bounds__(kTile* kTile, kColour ? RELO_RAYCAST_COLOUR_MI
                                  R[6] * dcx + R[7] * dcy + R[8]);
     const float3 C = make_float3(t[0], t[1], t[2]);
     BlockCache cache{INT32_MIN, INT32_MIN, INT32_MIN, -1};
-    const float lam = march_ray(job.scene, C, d, job.dmin, job.dmax, cache, &err);
+    const float lam = march_ray<kApron>(job.scene, C, d, job.dmin, job.dmax, cache, &err);
     const size_t pix = (size_t)v * job.W + u;
     uint32_t col = 0u;
     if (lam >= job.dmin && lam <= job.dmax) {
@@ -330,17 +333,25 @@ __global__ void __launch_bounds__(kTile* kTile, kColour ? RELO_RAYCAST_COLOUR_MI
   }
 }
 
+template <bool kApron>
+void launch_raycast_t(const RayJob* jobs_dev, int n_jobs, const RayJob& one, int total_tiles, bool with_colour,
+                      bool compare, cudaStream_t s, int w) {
+  const dim3 grid(total_tiles), block(kTile * kTile);
+  if (compare) raycast_kernel<false, true, kApron><<<grid, block, 0, s>>>(jobs_dev, n_jobs, one, w);
+  else if (with_colour) raycast_kernel<true, false, kApron><<<grid, block, 0, s>>>(jobs_dev, n_jobs, one, w);
+  else raycast_kernel<false, false, kApron><<<grid, block, 0, s>>>(jobs_dev, n_jobs, one, w);
+}
+
 cudaError_t launch_raycast(const RayJob* jobs_dev, int n_jobs, const RayJob* single, int total_tiles,
-                           bool with_colour, bool compare, cudaStream_t s, const Schedule& sched) {
+                           bool with_colour, bool compare, cudaStream_t s, const Schedule& sched, bool all_apron) {
   if (total_tiles <= 0) return cudaSuccess;
   if (sched.ray_warp_log2w < 1 || sched.ray_warp_log2w > 4) return cudaErrorInvalidValue;
-  const dim3 grid(total_tiles), block(kTile * kTile);
   RayJob one{};
   if (single) one = *single;
-  const int w = sched.ray_warp_log2w;
-  if (compare) raycast_kernel<false, true><<<grid, block, 0, s>>>(jobs_dev, n_jobs, one, w);
-  else if (with_colour) raycast_kernel<true, false><<<grid, block, 0, s>>>(jobs_dev, n_jobs, one, w);
-  else raycast_kernel<false, false><<<grid, block, 0, s>>>(jobs_dev, n_jobs, one, w);
+  // a single job's own scene decides; a job array's scenes were checked by the caller
+  const bool apron = single ? one.scene.tsdf9 != nullptr : all_apron;
+  if (apron) launch_raycast_t<true>(jobs_dev, n_jobs, one, total_tiles, with_colour, compare, s, sched.ray_warp_log2w);
+  else launch_raycast_t<false>(jobs_dev, n_jobs, one, total_tiles, with_colour, compare, s, sched.ray_warp_log2w);
   return cudaGetLastError();
 }
 
@@ -350,6 +361,7 @@ cudaError_t launch_raycast(const RayJob* jobs_dev, int n_jobs, const RayJob* sin
 // stops past the depth it would have to beat: any hit nearer than best + 1 mm is detected by a
 // sample at most one march step (<= mu) beyond it, so the cut changes no winner.
 // ---------------------------------------------------------------------------------------------
+template <bool kApron>
 __global__ void __launch_bounds__(kTile* kTile)
     render_global_kernel(const RayJob* __restrict__ jobs, int n, uint16_t* __restrict__ depth,
                          uint32_t* __restrict__ rgba, int8_t* __restrict__ owner, int32_t* __restrict__ err_flag) {
@@ -376,7 +388,7 @@ __global__ void __launch_bounds__(kTile* kTile)
     const float3 C = make_float3(j.t[0], j.t[1], j.t[2]);
     const float lim = best >= 0 ? fminf(j.dmax, (float)(best_mm + 1) * 0.001f + j.scene.mu + j.scene.voxel) : j.dmax;
     BlockCache cache{INT32_MIN, INT32_MIN, INT32_MIN, -1};
-    const float lam = march_ray(j.scene, C, d, j.dmin, lim, cache, &err);
+    const float lam = march_ray<kApron>(j.scene, C, d, j.dmin, lim, cache, &err);
     if (lam >= j.dmin && lam <= j.dmax) {
       const int mm = round_half_up_clamp(lam * 1000.0f, 1, 65535);
       if (best < 0 || mm < best_mm) {
@@ -405,11 +417,14 @@ __global__ void __launch_bounds__(kTile* kTile)
 }
 
 cudaError_t launch_render_global(const RayJob* jobs_dev, int n, int W, int H, uint16_t* depth, uint32_t* rgba,
-                                 int8_t* owner, int32_t* err_flag, cudaStream_t s) {
+                                 int8_t* owner, int32_t* err_flag, cudaStream_t s, bool all_apron) {
   if (n < 1 || W < 1 || H < 1) return cudaSuccess;
   const size_t smem = (size_t)n * sizeof(RayJob);
   if (smem > 48 * 1024) return cudaErrorInvalidValue;
-  render_global_kernel<<<ray_tiles(W, H), kTile * kTile, smem, s>>>(jobs_dev, n, depth, rgba, owner, err_flag);
+  if (all_apron)
+    render_global_kernel<true><<<ray_tiles(W, H), kTile * kTile, smem, s>>>(jobs_dev, n, depth, rgba, owner, err_flag);
+  else
+    render_global_kernel<false><<<ray_tiles(W, H), kTile * kTile, smem, s>>>(jobs_dev, n, depth, rgba, owner, err_flag);
   return cudaGetLastError();
 }
 
