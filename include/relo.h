@@ -341,7 +341,10 @@ size_t relo_ransac_workspace_size(int32_t width, int32_t height, const relo_rans
 
 /* Relocalise one view: depth_dev + leaves_dev (from relo_forest_eval) -> result_dev (device
  * relo_pose_result; the verification fields are zero).  workspace_dev (256-byte aligned, at
- * least relo_ransac_workspace_size bytes) is scratch the call overwrites.
+ * least relo_ransac_workspace_size bytes) is scratch the call overwrites.  The call uploads its
+ * job descriptor and round tables with cudaMemcpyAsync from host memory that lives only for the
+ * call, so it is for eager use: a CUDA graph of relocalisation attempts is recorded with
+ * relo_batch_capture, whose uploads happen at relo_batch_prepare.
  * Errors: RELO_EINVAL (bad sizes/params/pointers or workspace too small). */
 relo_status relo_ransac_relocalise(const relo_forest* forest, const uint16_t* depth_dev, const uint16_t* leaves_dev,
                                    const relo_intrinsics* intr, const relo_ransac_params* p, void* workspace_dev,
