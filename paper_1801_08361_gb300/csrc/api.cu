@@ -7,6 +7,7 @@
 #include <cfloat>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <atomic>
@@ -1012,9 +1013,14 @@ relo_status relo_create_forest(const void* nodes, int32_t T, int32_t D, const fl
   // bit offsets in a packed pixel {depth | r << 16 | g << 24 | b << 32}), a depth node's 0
   std::vector<int4> dev_nodes((size_t)T * n_int);
   std::memcpy(dev_nodes.data(), nodes, dev_nodes.size() * 16);
+  int max_offset = 0;  // the largest |offset| of any probe: bounds how far a probe can leave its pixel
   for (int4& nd : dev_nodes) {
     const int kind = nd.z & 0xFF, c1 = (nd.z >> 8) & 0xFF, c2 = (nd.z >> 16) & 0xFF;
     nd.z = kind == 0 ? 0 : (1 | (16 + 8 * c1) << 8 | (16 + 8 * c2) << 16);
+    for (const int w : {nd.x, nd.y}) {
+      max_offset = std::max(max_offset, std::abs((int)(int16_t)(w & 0xFFFF)));
+      max_offset = std::max(max_offset, std::abs((int)(int16_t)((uint32_t)w >> 16)));
+    }
   }
   cudaError_t e = cudaMemcpy(f->d_nodes, dev_nodes.data(), (size_t)T * n_int * 16, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = modes ? cudaMemcpy(f->d_modes, modes, modes_bytes, cudaMemcpyHostToDevice)
@@ -1035,6 +1041,7 @@ relo_status relo_create_forest(const void* nodes, int32_t T, int32_t D, const fl
   f->view.T = T;
   f->view.D = D;
   f->view.M = M;
+  f->view.probe_reach = 1 + max_offset;
   *out = f;
   return RELO_OK;
 }

@@ -36,7 +36,9 @@ __device__ __forceinline__ DepthDivisor make_divisor(int d) {
 // 0 < r/d + |n| e / 2^shift < 1, e = M - 2^shift / d, since |n| < 2^25 and 2^-l <= 1/d; checked
 // exhaustively for every d in [65, 65535] and every int16 offset.)  Otherwise the full 64-bit
 // product of |n| is shifted and the sign restored.
-template <bool kHi>
+// kClamp = false: the caller has shown that x + q stays in [0, limit] for every node (the pixel is
+// at least the forest's probe reach away from the image edges), so no clamp is needed.
+template <bool kHi, bool kClamp = true>
 __device__ __forceinline__ int probe(int x, int delta, const DepthDivisor& dv, int limit) {
   const int n = delta * 1000;
   int q;
@@ -47,7 +49,7 @@ __device__ __forceinline__ int probe(int x, int delta, const DepthDivisor& dv, i
     const int m = (int)(((unsigned long long)a * (unsigned long long)dv.M) >> dv.shift);
     q = n < 0 ? -m : m;
   }
-  return min(max(x + q, 0), limit);
+  return kClamp ? min(max(x + q, 0), limit) : x + q;
 }
 
 // Descends pixel (u, v) of depth d through the trees, interleaved level by level so each level
@@ -62,7 +64,7 @@ extern __shared__ int4 s_forest_top[];
 
 // Levels [level_begin, level_end) with nodes from the forest in global memory, or (kShared) from
 // s_forest_top, which holds n_nodes of each tree.
-template <int MT, bool kHi, bool kPacked, bool kShared>
+template <int MT, bool kHi, bool kPacked, bool kShared, bool kClamp>
 __device__ __forceinline__ void descend_levels(const ForestJob& job, int u, int v, const DepthDivisor& dv,
                                                int (&node)[MT], int n_nodes, int level_begin, int level_end) {
   const int T = job.forest.T, W = job.W, H = job.H;
@@ -75,8 +77,8 @@ __device__ __forceinline__ void descend_levels(const ForestJob& job, int u, int 
           nd = kShared ? s_forest_top[t * n_nodes + node[t]] : __ldg(&job.forest.nodes[(size_t)t * n_nodes + node[t]]);
         const int dx1 = (int)(int16_t)(nd.x & 0xFFFF), dy1 = nd.x >> 16;
         const int dx2 = (int)(int16_t)(nd.y & 0xFFFF), dy2 = nd.y >> 16;
-        const int q1 = probe<kHi>(v, dy1, dv, H - 1) * W + probe<kHi>(u, dx1, dv, W - 1);
-        const int q2 = probe<kHi>(v, dy2, dv, H - 1) * W + probe<kHi>(u, dx2, dv, W - 1);
+        const int q1 = probe<kHi, kClamp>(v, dy1, dv, H - 1) * W + probe<kHi, kClamp>(u, dx1, dv, W - 1);
+        const int q2 = probe<kHi, kClamp>(v, dy2, dv, H - 1) * W + probe<kHi, kClamp>(u, dx2, dv, W - 1);
         int a, b;
         if (!RELO_CHECK((unsigned)q1 < (unsigned)(W * H) && (unsigned)q2 < (unsigned)(W * H))) {
           node[t] = 2 * node[t] + 1;
@@ -101,12 +103,29 @@ __device__ __forceinline__ void descend_levels(const ForestJob& job, int u, int 
 }
 
 // The first top_levels levels from s_forest_top, the rest from global memory.
-template <int MT, bool kHi, bool kPacked>
+template <int MT, bool kHi, bool kPacked, bool kClamp>
 __device__ __forceinline__ void descend(const ForestJob& job, int u, int v, const DepthDivisor& dv, int (&node)[MT],
                                         int top_levels) {
   if (top_levels > 0)
-    descend_levels<MT, kHi, kPacked, true>(job, u, v, dv, node, (1 << top_levels) - 1, 0, top_levels);
-  descend_levels<MT, kHi, kPacked, false>(job, u, v, dv, node, (1 << job.forest.D) - 1, top_levels, job.forest.D);
+    descend_levels<MT, kHi, kPacked, true, kClamp>(job, u, v, dv, node, (1 << top_levels) - 1, 0, top_levels);
+  descend_levels<MT, kHi, kPacked, false, kClamp>(job, u, v, dv, node, (1 << job.forest.D) - 1, top_levels,
+                                                  job.forest.D);
+}
+
+// Descent with or without probe clamping: a warp whose pixels all lie at least the forest's probe
+// reach trunc((max |offset|) * 1000 / d) from every image edge takes the clamp-free instance (its
+// probes cannot leave the image, so both give the same leaves); any other warp clamps.  Instances
+// for more than 6 trees always clamp (a second copy of their descent would spill registers).
+template <int MT, bool kHi, bool kPacked>
+__device__ __forceinline__ void descend_any(const ForestJob& job, int u, int v, int d, const DepthDivisor& dv,
+                                            int (&node)[MT], int top_levels) {
+  bool inside = false;
+  if (MT <= 6 && job.forest.probe_reach > 0) {
+    const int reach = (int)(((long long)(job.forest.probe_reach - 1) * 1000) / d);
+    inside = u >= reach && u + reach <= job.W - 1 && v >= reach && v + reach <= job.H - 1;
+  }
+  if (MT <= 6 && __all_sync(__activemask(), inside)) descend<MT, kHi, kPacked, false>(job, u, v, dv, node, top_levels);
+  else descend<MT, kHi, kPacked, true>(job, u, v, dv, node, top_levels);
 }
 
 // CTAs of 256 threads per SM the compiler must fit: full occupancy (7 and 8 tie, 6 is 10 % slower
@@ -184,11 +203,11 @@ __global__ void __launch_bounds__(256, RELO_FOREST_MIN_BLOCKS)
 #pragma unroll
   for (int t = 0; t < MT; ++t) node[t] = 0;
   if (job.packed) {
-    if (dv.shift >= 32) descend<MT, true, true>(job, u, v, dv, node, top_levels);
-    else descend<MT, false, true>(job, u, v, dv, node, top_levels);
+    if (dv.shift >= 32) descend_any<MT, true, true>(job, u, v, d, dv, node, top_levels);
+    else descend_any<MT, false, true>(job, u, v, d, dv, node, top_levels);
   } else {
-    if (dv.shift >= 32) descend<MT, true, false>(job, u, v, dv, node, top_levels);
-    else descend<MT, false, false>(job, u, v, dv, node, top_levels);
+    if (dv.shift >= 32) descend_any<MT, true, false>(job, u, v, d, dv, node, top_levels);
+    else descend_any<MT, false, false>(job, u, v, d, dv, node, top_levels);
   }
 #pragma unroll
   for (int t = 0; t < MT; ++t)

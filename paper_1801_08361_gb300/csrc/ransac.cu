@@ -956,8 +956,19 @@ cudaError_t launch_round(const RansacJob* jobs, int n_jobs, int round, const int
   return cudaGetLastError();
 }
 
-// Final hypothesis -> result (one thread per job).
-__device__ __forceinline__ void finalise_one(const RansacJob& job) {
+// Tries of every hypothesis of the job (a kept try j counts j + 1, a failed hypothesis max_tries),
+// summed by the 32 lanes of a warp; every lane returns the total.
+__device__ __forceinline__ unsigned long long job_tries(const RansacJob& job, int lane) {
+  unsigned long long tries = 0;
+  for (int q = lane; q < job.K; q += 32)
+    tries += job.hyp_ok[q] ? (unsigned long long)job.tries[q] + 1 : job.max_tries;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tries += __shfl_xor_sync(0xffffffffu, tries, o);
+  return tries;
+}
+
+// Final hypothesis -> result (one thread per job; tries from job_tries).
+__device__ __forceinline__ void finalise_one(const RansacJob& job, unsigned long long tries) {
   if (job_skipped(job.skip)) return;
   const int32_t* fin = (job.n_rounds & 1) ? job.alive_b : job.alive_a;
   const int h = fin[0];
@@ -976,8 +987,6 @@ __device__ __forceinline__ void finalise_one(const RansacJob& job) {
   res->hypothesis = h;
   res->n_rounds = job.n_rounds;
   res->omega = res->omega_a = res->omega_b = res->omega_ab = res->sum_absdiff_mm = 0;
-  unsigned long long tries = 0;
-  for (int q = 0; q < job.K; ++q) tries += job.hyp_ok[q] ? (unsigned long long)job.tries[q] + 1 : job.max_tries;
   res->tries = tries;
   res->path = RELO_PATH_FOREST;
   res->pad = 0;
@@ -999,10 +1008,14 @@ __device__ __forceinline__ void finalise_one(const RansacJob& job) {
   }
 }
 
-__global__ void finalise_kernel(const RansacJob* __restrict__ jobs, int n_jobs) {
-  const int jid = blockIdx.x * blockDim.x + threadIdx.x;
+// Warp per job.
+__global__ void __launch_bounds__(128) finalise_kernel(const RansacJob* __restrict__ jobs, int n_jobs) {
+  const int jid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (jid >= n_jobs) return;
-  finalise_one(jobs[jid]);
+  const RansacJob& job = jobs[jid];
+  if (job_skipped(job.skip)) return;
+  const unsigned long long tries = job_tries(job, lane);
+  if (lane == 0) finalise_one(job, tries);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1112,7 +1125,10 @@ __global__ void __launch_bounds__(kPersistThreads, 2) persistent_kernel(PersistA
         break;
       }
       default:
-        if (threadIdx.x == 0) finalise_one(job);
+        if (threadIdx.x < 32 && !job_skipped(job.skip)) {
+          const unsigned long long tries = job_tries(job, threadIdx.x);
+          if (threadIdx.x == 0) finalise_one(job, tries);
+        }
         break;
     }
     __threadfence();
@@ -1195,7 +1211,8 @@ cudaError_t launch_verify_decide_one(relo_pose_result* res, uint64_t omega, cuda
 }
 
 cudaError_t launch_finalise(const RansacJob* jobs, int n_jobs, cudaStream_t s) {
-  finalise_kernel<<<(n_jobs + 127) / 128, 128, 0, s>>>(jobs, n_jobs);
+  if (n_jobs <= 0) return cudaSuccess;
+  finalise_kernel<<<(n_jobs + 3) / 4, 128, 0, s>>>(jobs, n_jobs);
   return cudaGetLastError();
 }
 

@@ -139,6 +139,7 @@ struct ForestView {
   const uint8_t* n_modes;   // [T][2^D]
   const float4* top;        // [T][2^D]: mode 0 mean xyz, w = number of modes
   int32_t T, D, M;
+  int32_t probe_reach;      // 1 + the largest |offset| of any node (0: not known, every probe clamped)
 };
 
 // ---------------------------------------------------------------------------------------------
