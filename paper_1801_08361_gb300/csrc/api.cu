@@ -1022,6 +1022,16 @@ relo_status relo_create_forest(const void* nodes, int32_t T, int32_t D, const fl
       max_offset = std::max(max_offset, std::abs((int)(int16_t)((uint32_t)w >> 16)));
     }
   }
+  // offsets of at most 255 in magnitude are stored times 128 (still int16), which the evaluation's
+  // division by depth takes as they are (forest.cu, probe)
+  if (max_offset <= 255)
+    for (int4& nd : dev_nodes) {
+      int* w[2] = {&nd.x, &nd.y};
+      for (int* p : w) {
+        const int lo = (int)(int16_t)(*p & 0xFFFF) * 128, hi = (int)(int16_t)((uint32_t)*p >> 16) * 128;
+        *p = (int)((uint32_t)(uint16_t)(int16_t)lo | (uint32_t)(uint16_t)(int16_t)hi << 16);
+      }
+    }
   cudaError_t e = cudaMemcpy(f->d_nodes, dev_nodes.data(), (size_t)T * n_int * 16, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = modes ? cudaMemcpy(f->d_modes, modes, modes_bytes, cudaMemcpyHostToDevice)
                                   : cudaMemset(f->d_modes, 0, modes_bytes);
@@ -1042,6 +1052,7 @@ relo_status relo_create_forest(const void* nodes, int32_t T, int32_t D, const fl
   f->view.D = D;
   f->view.M = M;
   f->view.probe_reach = 1 + max_offset;
+  f->view.offset_shift = max_offset <= 255 ? 7 : 0;
   *out = f;
   return RELO_OK;
 }

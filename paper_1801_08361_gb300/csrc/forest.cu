@@ -30,7 +30,23 @@ __device__ __forceinline__ DepthDivisor make_divisor(int d) {
   return q;
 }
 
-// kHi: the shift is >= 32 (every depth d >= 65 mm).  Then trunc(n / d) for a signed n is
+// Offsets stored times 128 (every |delta| <= 255, ForestView::offset_shift = 7) and d >= 16:
+// trunc(delta * 1000 / d) = mulhi(128 delta, M7) + [delta < 0] with M7 = floor(2^25 * 1000 / d) + 1,
+// the same round-up method with the factor 1000 folded into the multiplier.  With e = M7 -
+// 2^25 * 1000 / d in (0, 1], 128 delta M7 / 2^32 = delta * 1000 / d + 128 delta e / 2^32.  Since
+// |delta| d <= 255 * 65535 < 2^25, the added term is below 1/d in magnitude, and 1/d is the
+// smallest distance from a non-integer delta * 1000 / d to the next integer: for delta >= 0 the
+// floor is the quotient; for delta < 0 the term pushes the value just below -q, so the floor is
+// one less than the truncation.  d >= 16 keeps M7 below 2^31 (a positive signed multiplier).
+// Checked exhaustively for every d in [16, 65535] and |delta| <= 255 (tests/test_probe_division.py).
+__device__ __forceinline__ DepthDivisor make_divisor7(int d) {
+  DepthDivisor q;
+  q.shift = 0;
+  q.M = (uint32_t)((1000ull << 25) / (unsigned long long)d + 1ull);
+  return q;
+}
+
+// kDiv == 1: the shift is >= 32 (every depth d >= 65 mm).  Then trunc(n / d) for a signed n is
 // floor(n M / 2^shift) + [n < 0]: the high word of the signed product shifted arithmetically by
 // shift - 32, plus the sign bit.  (For n < 0, n M / 2^shift = -(q + r/d + |n| e / 2^shift) with
 // 0 < r/d + |n| e / 2^shift < 1, e = M - 2^shift / d, since |n| < 2^25 and 2^-l <= 1/d; checked
@@ -38,11 +54,17 @@ __device__ __forceinline__ DepthDivisor make_divisor(int d) {
 // product of |n| is shifted and the sign restored.
 // kClamp = false: the caller has shown that x + q stays in [0, limit] for every node (the pixel is
 // at least the forest's probe reach away from the image edges), so no clamp is needed.
-template <bool kHi, bool kClamp = true>
-__device__ __forceinline__ int probe(int x, int delta, const DepthDivisor& dv, int limit) {
-  const int n = delta * 1000;
+// kDiv: 2 = the shifted-offset form above (raw = 128 delta); 1 = kHi, 0 = the 64-bit product
+// (raw = delta << oshift).
+template <int kDiv, bool kClamp = true>
+__device__ __forceinline__ int probe(int x, int raw, const DepthDivisor& dv, int limit, int oshift) {
+  if (kDiv == 2) {
+    const int q = __mulhi(raw, (int)dv.M) - (raw >> 31);
+    return kClamp ? min(max(x + q, 0), limit) : x + q;
+  }
+  const int n = (raw >> oshift) * 1000;
   int q;
-  if (kHi) {
+  if (kDiv == 1) {
     q = (__mulhi(n, (int)dv.M) >> (dv.shift - 32)) - (n >> 31);
   } else {
     const unsigned a = (unsigned)(n < 0 ? -n : n);
@@ -64,10 +86,10 @@ extern __shared__ int4 s_forest_top[];
 
 // Levels [level_begin, level_end) with nodes from the forest in global memory, or (kShared) from
 // s_forest_top, which holds n_nodes of each tree.
-template <int MT, bool kHi, bool kPacked, bool kShared, bool kClamp>
+template <int MT, int kDiv, bool kPacked, bool kShared, bool kClamp>
 __device__ __forceinline__ void descend_levels(const ForestJob& job, int u, int v, const DepthDivisor& dv,
                                                int (&node)[MT], int n_nodes, int level_begin, int level_end) {
-  const int T = job.forest.T, W = job.W, H = job.H;
+  const int T = job.forest.T, W = job.W, H = job.H, os = job.forest.offset_shift;
   for (int level = level_begin; level < level_end; ++level) {
 #pragma unroll
     for (int t = 0; t < MT; ++t) {
@@ -77,8 +99,8 @@ __device__ __forceinline__ void descend_levels(const ForestJob& job, int u, int 
           nd = kShared ? s_forest_top[t * n_nodes + node[t]] : __ldg(&job.forest.nodes[(size_t)t * n_nodes + node[t]]);
         const int dx1 = (int)(int16_t)(nd.x & 0xFFFF), dy1 = nd.x >> 16;
         const int dx2 = (int)(int16_t)(nd.y & 0xFFFF), dy2 = nd.y >> 16;
-        const int q1 = probe<kHi, kClamp>(v, dy1, dv, H - 1) * W + probe<kHi, kClamp>(u, dx1, dv, W - 1);
-        const int q2 = probe<kHi, kClamp>(v, dy2, dv, H - 1) * W + probe<kHi, kClamp>(u, dx2, dv, W - 1);
+        const int q1 = probe<kDiv, kClamp>(v, dy1, dv, H - 1, os) * W + probe<kDiv, kClamp>(u, dx1, dv, W - 1, os);
+        const int q2 = probe<kDiv, kClamp>(v, dy2, dv, H - 1, os) * W + probe<kDiv, kClamp>(u, dx2, dv, W - 1, os);
         int a, b;
         if (!RELO_CHECK((unsigned)q1 < (unsigned)(W * H) && (unsigned)q2 < (unsigned)(W * H))) {
           node[t] = 2 * node[t] + 1;
@@ -103,20 +125,20 @@ __device__ __forceinline__ void descend_levels(const ForestJob& job, int u, int 
 }
 
 // The first top_levels levels from s_forest_top, the rest from global memory.
-template <int MT, bool kHi, bool kPacked, bool kClamp>
+template <int MT, int kDiv, bool kPacked, bool kClamp>
 __device__ __forceinline__ void descend(const ForestJob& job, int u, int v, const DepthDivisor& dv, int (&node)[MT],
                                         int top_levels) {
   if (top_levels > 0)
-    descend_levels<MT, kHi, kPacked, true, kClamp>(job, u, v, dv, node, (1 << top_levels) - 1, 0, top_levels);
-  descend_levels<MT, kHi, kPacked, false, kClamp>(job, u, v, dv, node, (1 << job.forest.D) - 1, top_levels,
-                                                  job.forest.D);
+    descend_levels<MT, kDiv, kPacked, true, kClamp>(job, u, v, dv, node, (1 << top_levels) - 1, 0, top_levels);
+  descend_levels<MT, kDiv, kPacked, false, kClamp>(job, u, v, dv, node, (1 << job.forest.D) - 1, top_levels,
+                                                   job.forest.D);
 }
 
 // Descent with or without probe clamping: a warp whose pixels all lie at least the forest's probe
 // reach trunc((max |offset|) * 1000 / d) from every image edge takes the clamp-free instance (its
 // probes cannot leave the image, so both give the same leaves); any other warp clamps.  Instances
 // for more than 6 trees always clamp (a second copy of their descent would spill registers).
-template <int MT, bool kHi, bool kPacked>
+template <int MT, int kDiv, bool kPacked>
 __device__ __forceinline__ void descend_any(const ForestJob& job, int u, int v, int d, const DepthDivisor& dv,
                                             int (&node)[MT], int top_levels) {
   bool inside = false;
@@ -124,8 +146,8 @@ __device__ __forceinline__ void descend_any(const ForestJob& job, int u, int v, 
     const int reach = (int)(((long long)(job.forest.probe_reach - 1) * 1000) / d);
     inside = u >= reach && u + reach <= job.W - 1 && v >= reach && v + reach <= job.H - 1;
   }
-  if (MT <= 6 && __all_sync(__activemask(), inside)) descend<MT, kHi, kPacked, false>(job, u, v, dv, node, top_levels);
-  else descend<MT, kHi, kPacked, true>(job, u, v, dv, node, top_levels);
+  if (MT <= 6 && __all_sync(__activemask(), inside)) descend<MT, kDiv, kPacked, false>(job, u, v, dv, node, top_levels);
+  else descend<MT, kDiv, kPacked, true>(job, u, v, dv, node, top_levels);
 }
 
 // CTAs of 256 threads per SM the compiler must fit: full occupancy (7 and 8 tie, 6 is 10 % slower
@@ -197,17 +219,23 @@ __global__ void __launch_bounds__(256, RELO_FOREST_MIN_BLOCKS)
     for (int t = 0; t < T; ++t) job.leaves[(size_t)t * n_pix + pix] = 0xFFFF;
     return;
   }
-  const DepthDivisor dv = make_divisor(d);
   const int n_int = (1 << f.D) - 1;
   int node[MT];
 #pragma unroll
   for (int t = 0; t < MT; ++t) node[t] = 0;
-  if (job.packed) {
-    if (dv.shift >= 32) descend_any<MT, true, true>(job, u, v, d, dv, node, top_levels);
-    else descend_any<MT, false, true>(job, u, v, d, dv, node, top_levels);
+  if (f.offset_shift == 7 && d >= 16) {
+    const DepthDivisor dv = make_divisor7(d);
+    if (job.packed) descend_any<MT, 2, true>(job, u, v, d, dv, node, top_levels);
+    else descend_any<MT, 2, false>(job, u, v, d, dv, node, top_levels);
   } else {
-    if (dv.shift >= 32) descend_any<MT, true, false>(job, u, v, d, dv, node, top_levels);
-    else descend_any<MT, false, false>(job, u, v, d, dv, node, top_levels);
+    const DepthDivisor dv = make_divisor(d);
+    if (job.packed) {
+      if (dv.shift >= 32) descend_any<MT, 1, true>(job, u, v, d, dv, node, top_levels);
+      else descend_any<MT, 0, true>(job, u, v, d, dv, node, top_levels);
+    } else {
+      if (dv.shift >= 32) descend_any<MT, 1, false>(job, u, v, d, dv, node, top_levels);
+      else descend_any<MT, 0, false>(job, u, v, d, dv, node, top_levels);
+    }
   }
 #pragma unroll
   for (int t = 0; t < MT; ++t)

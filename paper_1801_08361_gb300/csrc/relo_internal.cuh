@@ -140,6 +140,7 @@ struct ForestView {
   const float4* top;        // [T][2^D]: mode 0 mean xyz, w = number of modes
   int32_t T, D, M;
   int32_t probe_reach;      // 1 + the largest |offset| of any node (0: not known, every probe clamped)
+  int32_t offset_shift;     // the device nodes hold offset << offset_shift (7 when every |offset| <= 255, else 0)
 };
 
 // ---------------------------------------------------------------------------------------------
