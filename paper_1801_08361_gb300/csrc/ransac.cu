@@ -886,7 +886,12 @@ __device__ __forceinline__ void refine_block(const RansacJob* __restrict__ jobs,
   }
 }
 
-__global__ void __launch_bounds__(kRoundWarps * 32) refine_kernel(const RansacJob* __restrict__ jobs,
+// CTAs per SM the compiler must fit for the re-fit sums (the 16 compensated sums per lane take
+// registers; the fewer a thread holds, the more pixels' loads are in flight per SM)
+#ifndef RELO_REFINE_MIN_BLOCKS
+#define RELO_REFINE_MIN_BLOCKS 2
+#endif
+__global__ void __launch_bounds__(kRoundWarps * 32, RELO_REFINE_MIN_BLOCKS) refine_kernel(const RansacJob* __restrict__ jobs,
                                                                   const int32_t* __restrict__ surv_prefix, int r) {
   __shared__ ModeSlot slots[kRoundWarps];
   __shared__ float red[kRoundWarps][16][32];
