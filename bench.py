@@ -66,13 +66,14 @@ ALG_BYTES_PER_PIXEL = {
     "learned_verify": 35.87,
 }
 # DRAM bytes (read + write) per attempt of the stage's main kernel: the ncu captures summarised in
-# profiles/attempt_dram_house_640x480_batch32.md and profiles/raycast_apron_house_640x480_batch32.md
+# profiles/attempt_dram_house_640x480_batch32.md, profiles/raycast_apron_house_640x480_batch32.md
+# and profiles/forest_kernel_house_640x480_batch32.md
 # (32 attempts per launch, the current kernels)
 # divided by 32; a launch of A attempts is reported as A times that (attempts are independent, so
 # the traffic grows with their number; None: not captured for the current code).
 PROFILED_TRAFFIC_BYTES_PER_ATTEMPT = {
     "query_raycast": (974674688 + 151929344) / 32,
-    "forest_eval": (101214976 + 62725632) / 32,
+    "forest_eval": (101216000 + 64267264) / 32,
     "forest_hypotheses": (161393152 + 7238400) / 32,
     "forest_verify": (654187520 + 6215424) / 32,
 }
@@ -82,8 +83,8 @@ PROFILED_TRAFFIC_BYTES_PER_ATTEMPT = {
 PROFILED_LIMITER = {
     "query_raycast": "instruction issue (74 % active at 63 % warps active; 23.5 of 32 lanes per instruction as rays "
                      "end at different steps); DRAM 17 % of peak, L2 hit 51 %",
-    "forest_eval": "instruction issue (69 % active at 98 % warps active, about 72 instructions per node "
-                   "visit) and long-scoreboard stalls on node and probe loads (L2 hit 98 %, L2 throughput 47 %)",
+    "forest_eval": "instruction issue (69 % active at 97 % warps active, about 63 instructions per node "
+                   "visit) and dependent node and probe loads (L1 hit 23 %, L2 hit 98 %)",
     "forest_hypotheses": "L2 throughput (63 %, L2 hit 98 %): four random 16-byte gathers per try",
     "forest_verify": "instruction issue (74 % active at 61 % warps active; 23.2 of 32 lanes per instruction); "
                      "DRAM 11 % of peak, L2 hit 54 %",
