@@ -649,7 +649,10 @@ __device__ __forceinline__ float warp_best_staged(const ModeSlot& slot, int n_st
 // Measured on the house batch: faster for 1 and 2 hypotheses (re-fit sums 457 -> 309 us in the
 // last round), slower from 4 (the warp pass's shuffle reductions are a dependent chain, while the
 // per-lane scan overlaps its independent mode scores).  Both give the same scores and modes.
-constexpr int kFewHyps = 2;
+#ifndef RELO_FEW_HYPS
+#define RELO_FEW_HYPS 2
+#endif
+constexpr int kFewHyps = RELO_FEW_HYPS;
 
 // Round kernels: a CTA takes 32 hypotheses of one job (one per lane) and its warps split the
 // pixels, each warp walking every kRoundWarps-th pixel; per-warp partial sums are combined in
