@@ -101,6 +101,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fusion-frames", type=int, default=96, help="frames of the TSDF fusion section (0: skip)")
     ap.add_argument("--fragments", type=int, default=1, help="measure the batched 8-fragment configuration (0: skip)")
+    ap.add_argument("--tiny", type=int, default=1, help="measure the tiny-room configuration (0: skip)")
     ap.add_argument("--profile-fusion", type=int, default=0, help="(ncu) fuse this many frames and exit, no JSON")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the launch schedule with relo_batch_autotune (default: the default schedule, "
@@ -550,6 +551,11 @@ def run_ours(args):
     if args.learned_fragments > 0 and rank == 0:
         learned_frag = learned_fragments_section(args, B, synth, torch, dev, stream)
 
+    # ---- the tiny configuration (not part of the timed steps) ---------------------------------
+    tiny = None
+    if args.tiny and rank == 0:
+        tiny = tiny_section(args, B, synth, torch, dev, stream, flush)
+
     # ---- the batched configuration (not part of the timed steps) ------------------------------
     frag = None
     if args.fragments and rank == 0:
@@ -581,7 +587,7 @@ def run_ours(args):
                            "stage_ms_per_step": {k: v / args.steps for k, v in stage_tot.items()},
                            "schedule": dict(schedule, autotuned=bool(args.autotune)),
                            "learned": learned, "serving": serving, "fusion": fusion, "precision": precision,
-                           "fragments": frag, "persistent_schedule": persistent,
+                           "fragments": frag, "tiny": tiny, "persistent_schedule": persistent,
                            "learned_fragments": learned_frag},
                 "e2e": {"value": e2e_value, "unit": UNIT,
                         "h2d_bytes_per_step": A * H * W * 4 + A * ctypes_attempt_bytes(),
@@ -812,6 +818,72 @@ def learned_fragments_section(args, B, synth, torch, dev, stream):
 # exact count of the distinct voxels and hash entries each raycast touches, plus the images read
 # and written; the forest stage reads depth and colour and writes 5 leaf ids per pixel).
 FRAG_ALG_BYTES = {"query_raycast": 1189722832, "forest_eval": 172339200, "forest_verify": 4181876800}
+TINY_STEPS = 20
+TINY_ATTEMPTS = 256
+
+
+def tiny_section(args, B, synth, torch, dev, stream, flush):
+    """The tiny configuration: the 4 x 4 x 3 m room with 20 boxes (2^16 buckets), 320 x 240 queries
+    near its trajectory (no depth noise), a forest of 5 trees of depth 10 filled on the GPU from 10
+    noisy training renders (reservoirs of 64, <= 10 modes), preemptive RANSAC with 64 hypotheses
+    and 500 pixels per round, Philox seed 0; 256 attempts per batch, one graph replay per step."""
+    from paper_1801_08361_gb300.presets import TINY
+    w1, h1 = TINY.sizes[0]
+    world = synth.room_world(1)
+    scene = B.Scene(synth.sample_scene(world), TINY.log2_buckets)
+    intr = synth.Intrinsics.for_size(w1, h1)
+    train = synth.training_poses(world, TINY.train_per_room, seed=11)
+    nodes = synth.random_forest_nodes(TINY.trees, TINY.depth, seed=5, depth_tau=100, colour_tau=32)
+    forest = B.Forest(nodes, max_modes=TINY.max_modes)
+    B.forest_train_begin(forest, B.train_params(capacity=TINY.reservoir, stride=1, seed=7))
+    depth = torch.zeros((h1, w1), dtype=torch.int16, device=dev)
+    rgba = torch.zeros((h1, w1, 4), dtype=torch.uint8, device=dev)
+    for i, P in enumerate(train):
+        nz = torch.from_numpy(synth.depth_noise(h1, w1, 100 + i)).to(dev)
+        B.raycast_view(scene, intr, P, depth, rgba, noise_dev=nz)
+        B.forest_train_frame(forest, intr, P, depth, rgba)
+    B.forest_train_finish(forest)
+    qs = synth.query_poses(world, train, TINY_ATTEMPTS, seed=31)
+    prm = B.ransac_params(n_hyps=TINY.hypotheses[0], batch=TINY.batch_pixels, max_tries=TINY.max_tries)
+    items = [dict(scene_b=scene, forest_a=forest, scene_a=scene, intr=intr, pose_b=qs[k], noise=None, seed=0)
+             for k in range(TINY_ATTEMPTS)]
+    att = B.make_attempts(items)
+    ws = torch.empty(B.batch_workspace_size(att, prm), dtype=torch.uint8, device=dev)
+    bt = B.Batch(att, prm, ws)
+    bt.enable_timing(True)
+    res = torch.zeros(TINY_ATTEMPTS * B.RESULT_BYTES, dtype=torch.uint8, device=dev)
+    bt.capture(res)
+    for _ in range(3):
+        flush.zero_()
+        bt.replay()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(TINY_STEPS)]
+    stages = {}
+    for e in ev:
+        flush.zero_()
+        e[0].record(stream)
+        bt.replay()
+        e[1].record(stream)
+        torch.cuda.synchronize()
+        for k, v in bt.stage_ms().items():
+            if v > 0.01:
+                stages[k] = stages.get(k, 0.0) + v / TINY_STEPS
+    ms = sum(a.elapsed_time(b) for a, b in ev) / TINY_STEPS
+    raw = res.cpu()
+    ok = ver = 0
+    for k in range(TINY_ATTEMPTS):
+        r = B.result_from_bytes(raw[k * B.RESULT_BYTES:(k + 1) * B.RESULT_BYTES])
+        ok += int(success(r, qs[k]))
+        ver += int(r["verified"])
+    return {"workload": "room 4x4x3 m + 20 boxes, 5 mm voxels, 2^16 buckets; 320x240 queries (no noise); forest "
+                        "T=5 D=10, reservoir 64, <=10 modes, filled on the GPU from 10 noisy renders; preemptive "
+                        "RANSAC K=64, B=500, Philox seed 0",
+            "attempts_per_batch": TINY_ATTEMPTS, "steps": TINY_STEPS, "l2": "flushed between steps (512 MiB write)",
+            "attempts_per_s": TINY_ATTEMPTS / (ms / 1000.0), "ms_per_batch": ms, "stage_ms_per_batch": stages,
+            "success_rate": ok / TINY_ATTEMPTS, "verified_rate": ver / TINY_ATTEMPTS,
+            "launches": bt.launch_count}
+
+
 FRAG_STEPS = 20
 
 
