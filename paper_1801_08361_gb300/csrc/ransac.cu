@@ -780,6 +780,13 @@ __device__ __forceinline__ void comp_add(float& s, float& e, float x) {
   s = t;
 }
 
+// Squared distance with explicitly rounded operations, so that every kernel taking the inlier
+// decision takes it on the same bits.
+__device__ __forceinline__ float dist2_rn(float3 a, float3 b) {
+  const float dx = __fsub_rn(a.x, b.x), dy = __fsub_rn(a.y, b.y), dz = __fsub_rn(a.z, b.z);
+  return __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+}
+
 __device__ __forceinline__ void refine_block(const RansacJob* __restrict__ jobs, const int32_t* __restrict__ surv_prefix,
                                              int r, int chunk, int part, int jid, ModeSlot* slots,
                                              float (*red)[16][32]) {
@@ -807,8 +814,7 @@ __device__ __forceinline__ void refine_block(const RansacJob* __restrict__ jobs,
   for (int q = 0; q < 16; ++q) acc[q] = lo[q] = 0.f;
   // adds pixel c (its point x under this lane's hypothesis, best mode mean mu) when it is an inlier
   auto add_inlier = [&](float3 c, float3 x, float3 mu) {
-    const float dx = x.x - mu.x, dy = x.y - mu.y, dz = x.z - mu.z;
-    if (dx * dx + dy * dy + dz * dz < r2) {
+    if (dist2_rn(x, mu) < r2) {
       const float u[3] = {c.x - cref.x, c.y - cref.y, c.z - cref.z};
       const float w[3] = {mu.x - wref.x, mu.y - wref.y, mu.z - wref.z};
       acc[0] += 1.f;
@@ -901,6 +907,124 @@ __global__ void __launch_bounds__(kRoundWarps * 32, RELO_REFINE_MIN_BLOCKS) refi
   refine_block(jobs, surv_prefix, r, blockIdx.x, blockIdx.y, blockIdx.z, slots, red);
 }
 
+// Re-fit sums of rounds whose chunks hold at most kFewHyps hypotheses (the last rounds): the same
+// sums as refine_block's, taken with the sixteen sums of hypothesis j spread over lanes 16 j ..
+// 16 j + 15 (lane 16 j + q carries sum q) instead of all sixteen in lane j, so a thread holds one
+// compensated pair instead of sixteen and more CTAs fit an SM.  Every sum sees the same additions
+// in the same order as in refine_block (the pixels of a warp in turn, then the warps in order), so
+// the results are identical.
+__device__ __forceinline__ void refine_few_block(const RansacJob* __restrict__ jobs,
+                                                 const int32_t* __restrict__ surv_prefix, int r, int part, int jid,
+                                                 ModeSlot* slots, float (*red)[16][32]) {
+  const int n_surv = surv_prefix[jid + 1] - surv_prefix[jid];
+  if (n_surv == 0) return;
+  const RansacJob& job = jobs[jid];
+  const int n_drawn = (r + 1) * job.B;
+  const int p0 = part * kRefinePixels;
+  if (p0 >= n_drawn || job_skipped(job.skip) || *job.n_valid == 0) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = lane >> 4, q = lane & 15;  // this lane's hypothesis and sum
+  const int n_here = min(kFewHyps, n_surv);
+  const int h = j < n_here ? alive_out(job, r)[j] : 0;
+  const PoseF P = pose_to_float(job.poses + 12 * (size_t)h);
+  const float r2 = (float)(job.inlier_dist * job.inlier_dist);
+  const float3 cref = record_point(job.pix);
+  const float3 wref = apply(P, cref);
+  float acc = 0.f, lo = 0.f;
+  const int p1 = min(p0 + kRefinePixels, n_drawn);
+  for (int i = p0 + warp; i < p1; i += kRoundWarps) {
+    const int4* rec = job.pix + (size_t)i * job.hs;
+    const float3 c = record_point(rec);
+    const float3 x = apply(P, c);  // this lane's hypothesis
+    __syncwarp();  // the slot's previous pixel is scored
+    const int n_staged = stage_modes(job, rec, slots[warp], lane);
+    for (int k = 0; k < n_here; ++k) {
+      float best;
+      float3 mu = make_float3(0.f, 0.f, 0.f);
+      if (n_staged >= 0) {
+        const float3 xk = make_float3(__shfl_sync(0xffffffffu, x.x, 16 * k), __shfl_sync(0xffffffffu, x.y, 16 * k),
+                                      __shfl_sync(0xffffffffu, x.z, 16 * k));
+        best = warp_best_staged(slots[warp], n_staged, xk, lane, &mu);
+      } else {
+        // more modes than a slot holds: the scan of refine_block's per-lane path, by lane 16 k
+        float b = -INFINITY;
+        if (lane == 16 * k) b = record_best(job, rec, slots[warp], -1, x, &mu);
+        best = __shfl_sync(0xffffffffu, b, 16 * k);
+        mu = make_float3(__shfl_sync(0xffffffffu, mu.x, 16 * k), __shfl_sync(0xffffffffu, mu.y, 16 * k),
+                         __shfl_sync(0xffffffffu, mu.z, 16 * k));
+      }
+      if (j == k && best != -INFINITY && dist2_rn(x, mu) < r2) {
+        const float u[3] = {c.x - cref.x, c.y - cref.y, c.z - cref.z};
+        const float w[3] = {mu.x - wref.x, mu.y - wref.y, mu.z - wref.z};
+        if (q == 0) {
+          acc += 1.f;
+        } else if (q < 4) {
+          comp_add(acc, lo, u[q - 1]);
+        } else if (q < 7) {
+          comp_add(acc, lo, w[q - 4]);
+        } else {
+          const float a = u[(q - 7) / 3], b = w[(q - 7) % 3];
+          const float pr = __fmul_rn(a, b);
+          comp_add(acc, lo, pr);
+          lo = __fadd_rn(lo, __fmaf_rn(a, b, -pr));
+        }
+      }
+    }
+  }
+  // the warps' partials combined as in refine_block: sums q = w, w + kRoundWarps of hypothesis
+  // `lane` by warp w, added in warp order
+  constexpr int kPer = (16 + kRoundWarps - 1) / kRoundWarps;
+  float sh[kPer], sl[kPer];
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) sh[i] = sl[i] = 0.f;
+#pragma unroll
+  for (int pass = 0; pass < 2; ++pass) {
+    if (j < n_here) red[warp][q][j] = pass ? lo : acc;
+    __syncthreads();
+    if (lane < n_here) {
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) {
+        const int qq = warp + i * kRoundWarps;
+        if (qq < 16)
+#pragma unroll
+          for (int w = 0; w < kRoundWarps; ++w) {
+            if (pass == 0) comp_add(sh[i], sl[i], red[w][qq][lane]);
+            else sl[i] = __fadd_rn(sl[i], red[w][qq][lane]);
+          }
+      }
+    }
+    __syncthreads();
+  }
+  if (part == 0 && warp == 0 && q == 0 && j < n_here && job.hyp_ok[h]) {
+    float* ref = job.refit_ref + (size_t)h * 8;  // written by the hypothesis's first lane
+    ref[0] = cref.x;
+    ref[1] = cref.y;
+    ref[2] = cref.z;
+    ref[3] = wref.x;
+    ref[4] = wref.y;
+    ref[5] = wref.z;
+  }
+  if (lane >= n_here) return;
+  const int hl = alive_out(job, r)[lane];
+  if (!job.hyp_ok[hl]) return;
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    const int qq = warp + i * kRoundWarps;
+    if (qq < 16) job.refit[((size_t)hl * job.refit_parts + part) * 16 + qq] = make_float2(sh[i], sl[i]);
+  }
+}
+
+// CTAs per SM for refine_few_kernel (one compensated pair per thread)
+#ifndef RELO_REFINE_FEW_MIN_BLOCKS
+#define RELO_REFINE_FEW_MIN_BLOCKS 4
+#endif
+__global__ void __launch_bounds__(kRoundWarps * 32, RELO_REFINE_FEW_MIN_BLOCKS)
+    refine_few_kernel(const RansacJob* __restrict__ jobs, const int32_t* __restrict__ surv_prefix, int r) {
+  __shared__ ModeSlot slots[kRoundWarps];
+  __shared__ float red[kRoundWarps][16][32];
+  refine_few_block(jobs, surv_prefix, r, blockIdx.y, blockIdx.z, slots, red);
+}
+
 // Re-fit solve: thread per survivor; the parts' sums are added in order in FP64, then FP64 Horn on
 // the centroids and cross-covariance (>= 3 inliers, else the pose is kept).  CTAs of one warp take
 // `per` survivors each: with few survivors (late rounds) they spread over the SMs, whose FP64 pipes
@@ -953,7 +1077,10 @@ cudaError_t launch_round(const RansacJob* jobs, int n_jobs, int round, const int
   select_kernel<<<n_jobs, 1024, 4096 * (sizeof(unsigned long long) + sizeof(int)), s>>>(jobs, alive_prefix_dev,
                                                                                         round);
   const int parts = ((round + 1) * B + kRefinePixels - 1) / kRefinePixels;
-  refine_kernel<<<dim3((max_surv + 31) / 32, parts, n_jobs), kRoundWarps * 32, 0, s>>>(jobs, surv_prefix_dev, round);
+  if (max_surv <= kFewHyps)
+    refine_few_kernel<<<dim3(1, parts, n_jobs), kRoundWarps * 32, 0, s>>>(jobs, surv_prefix_dev, round);
+  else
+    refine_kernel<<<dim3((max_surv + 31) / 32, parts, n_jobs), kRoundWarps * 32, 0, s>>>(jobs, surv_prefix_dev, round);
   int n_sms = 0;
   const cudaError_t e = device_sms(&n_sms);
   if (e != cudaSuccess) return e;
