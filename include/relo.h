@@ -88,7 +88,8 @@ typedef struct relo_intrinsics {
  * in the list read tsdf +1 and colour 0.  Block coordinates must lie in [-32768, 32767];
  * a repeated block coordinate keeps its first occurrence.  The library builds a spatial
  * hash with 2^log2_buckets buckets (chained, entries of 16 bytes) and copies everything to
- * the device (synchronously; about 4 KB per block plus 16 B per bucket).
+ * the device (synchronously; about 4 KB per block plus 16 B per bucket, and 2.9 KB per block
+ * for the raycast's apron copy of the tsdf, relo_scene_use_apron).
  * Errors: RELO_EINVAL (n_blocks < 0, null arrays with n_blocks > 0, log2_buckets outside
  * [4, 30], voxel_size or mu <= 0, coordinates out of range), RELO_ENOMEM, RELO_ECUDA.
  * ------------------------------------------------------------------------------------- */
