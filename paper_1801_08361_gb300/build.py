@@ -23,7 +23,7 @@ NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-
 NVCC_FLAGS += [f"-D{k}={os.environ[k]}" for k in ("RELO_RAYCAST_MIN_BLOCKS", "RELO_RAYCAST_COLOUR_MIN_BLOCKS",
                                                   "RELO_SEARCH_MIN_BLOCKS", "RELO_FOREST_MIN_BLOCKS",
                                                   "RELO_REFINE_MIN_BLOCKS", "RELO_FEW_HYPS",
-                                                  "RELO_REFINE_FEW_MIN_BLOCKS")
+                                                  "RELO_REFINE_FEW_MIN_BLOCKS", "RELO_ENERGY_MIN_BLOCKS")
                if k in os.environ]
 
 

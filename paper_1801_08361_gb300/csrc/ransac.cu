@@ -703,7 +703,14 @@ __device__ __forceinline__ void energy_block(const RansacJob* __restrict__ jobs,
 }
 
 // Energies of round r: grid (hypothesis chunks, jobs).
-__global__ void __launch_bounds__(kRoundWarps * 32) energy_kernel(const RansacJob* __restrict__ jobs,
+// CTAs per SM the compiler must fit for the energies, when set (otherwise the compiler's choice:
+// 64 registers, four CTAs per SM)
+#ifdef RELO_ENERGY_MIN_BLOCKS
+#define RELO_ENERGY_BOUNDS __launch_bounds__(kRoundWarps * 32, RELO_ENERGY_MIN_BLOCKS)
+#else
+#define RELO_ENERGY_BOUNDS __launch_bounds__(kRoundWarps * 32)
+#endif
+__global__ void RELO_ENERGY_BOUNDS energy_kernel(const RansacJob* __restrict__ jobs,
                                                                   const int32_t* __restrict__ alive_prefix, int r) {
   __shared__ ModeSlot slots[kRoundWarps];
   __shared__ float part[kRoundWarps][32];
