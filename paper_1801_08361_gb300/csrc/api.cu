@@ -1009,14 +1009,15 @@ relo_status relo_create_forest(const void* nodes, int32_t T, int32_t D, const fl
     relo_destroy_forest(f);
     return fail(RELO_ENOMEM, "device allocation for the forest failed");
   }
-  // device copy of the nodes: a colour node's channels c1, c2 become 16 + 8 c1, 16 + 8 c2 (their
-  // bit offsets in a packed pixel {depth | r << 16 | g << 24 | b << 32}), a depth node's 0
+  // device copy of the nodes: the third word becomes {value mask (16 bits), bit offset of probe 1
+  // (8 bits), of probe 2 (8 bits)} in a packed pixel {depth | r << 16 | g << 24 | b << 32}: a depth
+  // node's mask 0xFFFF and offsets 0, a colour node's mask 0xFF and offsets 16 + 8 c1, 16 + 8 c2
   std::vector<int4> dev_nodes((size_t)T * n_int);
   std::memcpy(dev_nodes.data(), nodes, dev_nodes.size() * 16);
   int max_offset = 0;  // the largest |offset| of any probe: bounds how far a probe can leave its pixel
   for (int4& nd : dev_nodes) {
     const int kind = nd.z & 0xFF, c1 = (nd.z >> 8) & 0xFF, c2 = (nd.z >> 16) & 0xFF;
-    nd.z = kind == 0 ? 0 : (1 | (16 + 8 * c1) << 8 | (16 + 8 * c2) << 16);
+    nd.z = kind == 0 ? 0xFFFF : (0xFF | (16 + 8 * c1) << 16 | (16 + 8 * c2) << 24);
     for (const int w : {nd.x, nd.y}) {
       max_offset = std::max(max_offset, std::abs((int)(int16_t)(w & 0xFFFF)));
       max_offset = std::max(max_offset, std::abs((int)(int16_t)((uint32_t)w >> 16)));

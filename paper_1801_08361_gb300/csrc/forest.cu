@@ -76,8 +76,9 @@ __device__ __forceinline__ int probe(int x, int raw, const DepthDivisor& dv, int
 
 // Descends pixel (u, v) of depth d through the trees, interleaved level by level so each level
 // issues T independent node loads instead of a chain of T * D dependent ones.  In the device copy
-// of the forest (relo_create_forest) a colour node's probe channels c1, c2 are stored as the bit
-// offsets 16 + 8 c1, 16 + 8 c2 of the channel in a packed pixel, a depth node's as 0.
+// of the forest (relo_create_forest) a node's third word holds the mask of a probe's value (0xFFFF
+// for depth, 0xFF for a colour channel) and the bit offsets of its two probes' values in a packed
+// pixel (0 for depth, 16 + 8 c for colour channel c), ready to use.
 // kPacked: probes read the packed image (one 64-bit load, then a shift and a mask: no branch on
 // the node's kind, which differs between neighbouring lanes); otherwise the depth or the colour
 // image, by kind.
@@ -107,16 +108,16 @@ __device__ __forceinline__ void descend_levels(const ForestJob& job, int u, int 
           continue;
         }
         if (kPacked) {
-          const unsigned mask = 0xFFFFu >> ((nd.z & 0xFF) << 3), s1 = (nd.z >> 8) & 0xFF, s2 = (nd.z >> 16) & 0xFF;
+          const unsigned mask = (unsigned)nd.z & 0xFFFFu, s1 = ((unsigned)nd.z >> 16) & 0xFFu, s2 = (unsigned)nd.z >> 24;
           const uint2 p1 = __ldg(&job.packed[q1]), p2 = __ldg(&job.packed[q2]);
           a = (int)(__funnelshift_rc(p1.x, p1.y, s1) & mask);
           b = (int)(__funnelshift_rc(p2.x, p2.y, s2) & mask);
-        } else if ((nd.z & 0xFF) == 0) {
+        } else if ((nd.z & 0xFFFF) == 0xFFFF) {
           a = __ldg(&job.depth[q1]);
           b = __ldg(&job.depth[q2]);
         } else {
-          a = (__ldg(&job.rgba[q1]) >> (((nd.z >> 8) & 0xFF) - 16)) & 0xFF;
-          b = (__ldg(&job.rgba[q2]) >> (((nd.z >> 16) & 0xFF) - 16)) & 0xFF;
+          a = (__ldg(&job.rgba[q1]) >> ((((unsigned)nd.z >> 16) & 0xFFu) - 16)) & 0xFF;
+          b = (__ldg(&job.rgba[q2]) >> (((unsigned)nd.z >> 24) - 16)) & 0xFF;
         }
         node[t] = 2 * node[t] + ((a - b < nd.w) ? 1 : 2);
       }
