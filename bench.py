@@ -73,7 +73,7 @@ ALG_BYTES_PER_PIXEL = {
 # the traffic grows with their number; None: not captured for the current code).
 PROFILED_TRAFFIC_BYTES_PER_ATTEMPT = {
     "query_raycast": (974674688 + 151929344) / 32,
-    "forest_eval": (101216000 + 64267264) / 32,
+    "forest_eval": (101758464 + 64701440) / 32,
     "forest_hypotheses": (161393152 + 7238400) / 32,
     "forest_verify": (654187520 + 6215424) / 32,
 }
@@ -83,7 +83,7 @@ PROFILED_TRAFFIC_BYTES_PER_ATTEMPT = {
 PROFILED_LIMITER = {
     "query_raycast": "instruction issue (74 % active at 63 % warps active; 23.5 of 32 lanes per instruction as rays "
                      "end at different steps); DRAM 17 % of peak, L2 hit 51 %",
-    "forest_eval": "instruction issue (69 % active at 97 % warps active, about 63 instructions per node "
+    "forest_eval": "instruction issue (65 % active at 97 % warps active, about 58 instructions per node "
                    "visit) and dependent node and probe loads (L1 hit 23 %, L2 hit 98 %)",
     "forest_hypotheses": "L2 throughput (63 %, L2 hit 98 %): four random 16-byte gathers per try",
     "forest_verify": "instruction issue (74 % active at 61 % warps active; 23.2 of 32 lanes per instruction); "
