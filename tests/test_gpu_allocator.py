@@ -55,6 +55,7 @@ def test_handles_live_in_the_callers_allocator(room, room_training, room_forest)
     ref = _attempts(room, room_training, B.Scene(blocks, 16),
                     B.Forest(room_forest.nodes, room_forest.modes, room_forest.n_modes, max_modes=10))
     a = Counting()
+    gc.collect()  # garbage of earlier tests may hold torch memory: free it before the baseline
     torch.cuda.synchronize()
     before = torch.cuda.memory_allocated()
     B.set_allocator(a.alloc, a.free)
